@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the direct-sum boundary-integral PB hot path on GB300.
+
+One step = one pass of the whole hot path on one charge configuration that
+is already resident on the device: source term, mixed-precision GMRES(10)
+solve (FP32 mat-vecs inside, FP64 refinement residual) to a true relative
+residual of 1e-8, solvation energy (read back to the host).
+
+Default workload: the Kirkwood sphere (icosphere level 5, N = 20480
+triangles, 2N = 40960 unknowns, radius 20 A, 50 charges, eps 1/80,
+kappa 0.1257 1/A).  ``--workload protein_like`` selects the displaced
+level-6 sphere (N = 81920, 2000 charges).
+
+value = pair interactions evaluated per second over the step (every mat-vec
+pair N(N-1), plus the N*Nc source and energy pairs), in Gpairs/s.  The JSON
+line also carries the FP64 GMRES solve time of the same system, single
+mat-vec throughputs, the roofline of the dominant kernel, the CPU oracle
+baseline, the end-to-end number through the host API and the SM clocks.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BIE matvec Gpairs/s; GMRES solve time at 1e-8 rel. residual, mixed vs FP64"
+TOL = 1e-8
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+# Algorithmic work per pair of the mat-vec ("Roofline"): flops
+# of the pair formula (an FMA counts 2) and FP32/FP64 pipe instructions.
+PAIR_FLOPS = 56
+PAIR_PIPE_INSTR = 39
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM per clock
+FP64_LANES_PER_SM = 2    # FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein_like"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def workload(name):
+    import synth
+
+    p = synth.problem_by_name(name)
+    desc = {
+        "kirkwood": "Kirkwood sphere: icosphere level 5 (N=20480 triangles, 40960 unknowns), R=20 A, 50 charges "
+                    "in r<16 A, eps 1/80, kappa 0.1257/A; source + mixed FP32/FP64 GMRES(10) to 1e-8 + energy",
+        "protein_like": "protein-like surface: displaced icosphere level 6 (N=81920), R=25 A, 2000 charges, "
+                        "eps 1/80, kappa 0.1257/A; source + mixed FP32/FP64 GMRES(10) to 1e-8 + energy",
+    }[name]
+    return p, desc
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception as e:  # nvidia-smi missing: report no clocks
+            log("clock sampling unavailable:", e)
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(prob, budget_s=10.0):
+    """Oracle FP64 mat-vec pair rate on this host: full mat-vecs until the budget is used."""
+    import oracle
+
+    oracle.build()
+    eps = prob.eps_out / prob.eps_in
+    u = np.random.default_rng(0).standard_normal(2 * prob.n)
+    n = prob.n
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.matvec(prob.centroids, prob.normals, prob.areas, eps, prob.kappa, u)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el / reps * (reps + 1) > 2.5 * budget_s:
+            break
+    pairs = reps * n * (n - 1)
+    return {"value": pairs / el / 1e9, "unit": "Gpairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{reps} full FP64 oracle mat-vec(s) of the workload ({n}x{n - 1} pairs each), {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob, desc = workload(args.workload)
+    import oracle
+
+    oracle.build()
+    eps = prob.eps_out / prob.eps_in
+    n = prob.n
+    rows = max(64, int(2e9 / 2.0 / n) // 16 * 16)  # ~1e9 pairs per step
+    rows = min(rows, 2 * n)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal(2 * n)
+    sel = np.sort(rng.choice(2 * n, rows, replace=False))
+    for _ in range(args.warmup):
+        oracle.matvec_rows(prob.centroids, prob.normals, prob.areas, eps, prob.kappa, u, sel[:64])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.matvec_rows(prob.centroids, prob.normals, prob.areas, eps, prob.kappa, u, sel)
+    el = time.perf_counter() - t0
+    value = args.steps * rows * (n - 1) / el / 1e9
+    sample = f"{rows} sampled rows of the FP64 mat-vec per step ({rows * (n - 1):.3g} pairs)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "n": n, "nc": prob.nc},
+            "cpu_baseline": {"value": value, "unit": "Gpairs/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Gpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2312_10044_gb300.build import build
+
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_2312_10044_gb300 as bipb
+
+    prob, desc = workload(args.workload)
+    n, nc = prob.n, prob.nc
+    params = bipb.solve_params(prob.eps_in, prob.eps_out, prob.kappa, tol=TOL, restart=10, precision=bipb.MIXED)
+    s = bipb.Surface(prob.centroids, prob.normals, prob.areas)
+    s.set_charges(prob.charge_pos, prob.q)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        info = s.solve(params)
+        e = s.energy()
+        return info[0], e[0]
+
+    for _ in range(args.warmup):
+        info, e = step()
+    log(f"warm-up: {info} E={e:.6f} kcal/mol")
+
+    # ---- timed region: K steps, events per step, L2 flushed between steps
+    cs = ClockSampler(local)
+    bipb.timer_enable(s, True)
+    launches0 = bipb.launch_count(s)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    cs.start()
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record()
+        infos.append(step())
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    clocks = cs.stop()
+    if world > 1:
+        dist.barrier()
+    launches = bipb.launch_count(s) - launches0
+    timers = bipb.timer_read(s)
+    bipb.timer_enable(s, False)
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    info0 = infos[-1][0]
+    mv = info0["matvecs32"] + info0["matvecs64"]
+    pairs_step = mv * n * (n - 1) + 2 * n * nc
+    value = world * args.steps * pairs_step / (total_ms / 1e3) / 1e9
+
+    # ---- dominant kernel and its roofline (from the events around each launch)
+    dom = max(timers, key=lambda k: timers[k][1])
+    cnt, tms = timers[dom]
+    avg_ms = tms / max(cnt, 1)
+    f_mhz = clocks["sm_mhz"] if clocks else 2070.0
+    lanes = FP32_LANES_PER_SM if dom.startswith("matvec32") else FP64_LANES_PER_SM
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    pairs_launch = n * (n - 1)
+    achieved = pairs_launch * PAIR_FLOPS / (avg_ms / 1e3) / 1e12
+    peak = nsm * lanes * 2 * f_mhz * 1e6 / 1e12
+    pipe_frac = pairs_launch * PAIR_PIPE_INSTR / (avg_ms / 1e3) / (nsm * lanes * f_mhz * 1e6)
+    roofline = {"bound": "alu", "kernel": f"{dom} pair kernel", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "pipe": "fp32" if lanes == FP32_LANES_PER_SM else "fp64", "pipe_frac": pipe_frac,
+                "peak_basis": f"{nsm} SMs x {lanes} {('FP32' if lanes == 128 else 'FP64')} FMA lanes x 2 flop x "
+                              f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+                "avg_launch_ms": avg_ms, "launches": cnt,
+                "kernel_ms": {k: v[1] for k, v in timers.items() if v[0]},
+                "kernel_launches": {k: v[0] for k, v in timers.items() if v[0]}}
+
+    extra = {}
+    # ---- single mat-vec throughputs (device-resident, events around 10 launches each)
+    u = torch.randn(2 * n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(u)
+    med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
+    for prec, name, reps in ((bipb.FP32, "fp32", 20), (bipb.FP64, "fp64", 3)):
+        s.matvec(u, y, precision=prec, med=med)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            s.matvec(u, y, precision=prec, med=med)
+        b.record()
+        torch.cuda.synchronize()
+        extra[f"matvec_{name}_gpairs"] = reps * n * (n - 1) / (a.elapsed_time(b) / 1e3) / 1e9
+    # ---- FP64 GMRES solve of the same system
+    if not args.no_fp64:
+        p64 = bipb.solve_params(prob.eps_in, prob.eps_out, prob.kappa, tol=TOL, restart=10, precision=bipb.FP64)
+        s.solve(p64)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        i64 = s.solve(p64)[0]
+        b.record()
+        torch.cuda.synchronize()
+        extra["solve_ms_fp64"] = a.elapsed_time(b)
+        extra["fp64_info"] = i64
+    extra["solve_ms_mixed"] = total_ms / args.steps
+    extra["mixed_info"] = info0
+    extra["energy_kcal"] = infos[-1][1]
+
+    # ---- end to end through the host API: geometry + charges from pinned host
+    # memory, create, solve, energy back to the host, destroy
+    cen = torch.from_numpy(prob.centroids).pin_memory()
+    nrm = torch.from_numpy(prob.normals).pin_memory()
+    area = torch.from_numpy(prob.areas).pin_memory()
+    pos = torch.from_numpy(np.ascontiguousarray(prob.charge_pos)).pin_memory()
+    qq = torch.from_numpy(np.ascontiguousarray(prob.q)).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with bipb.Surface(cen.numpy(), nrm.numpy(), area.numpy()) as s2:
+            s2.set_charges(pos.numpy(), qq.numpy())
+            s2.solve(params)
+            s2.energy()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = cen.numel() * 8 + nrm.numel() * 8 + area.numel() * 8 + pos.numel() * 8 + qq.numel() * 8
+    e2e = {"value": world * pairs_step / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": 8, "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_oracle_rate(prob)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gpairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": desc, "n": n, "nc": nc, "tol": TOL, "restart": 10, "l2": "flushed",
+                           "parallelism": f"replicas{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks}
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * bipb.h -- C ABI of libbipb, a single-GPU (GB300, sm_103a) direct-sum
+ * boundary-integral Poisson-Boltzmann solver.
+ *
+ * Method (Yang, Sliheet, Iriye, Reynolds, Geng, "Optimized Parallelization of
+ * Boundary Integral Poisson-Boltzmann Solvers", arXiv 2312.10044):
+ *   - model and units: Sec. 2.1 (linearised PB, eps_in inside, eps_out
+ *     outside, inverse Debye length kappa, lengths in Angstrom, potentials
+ *     times 332.0716 give kcal/mol/e);
+ *   - boundary integral equations, kernels K1..K4 and source terms S1, S2:
+ *     Sec. 2.2.1 (Eqs. for the well-conditioned BIE, K1..K4, S1/S2);
+ *   - centroid collocation with the self term j = i omitted, and the linear
+ *     system A u = b solved by GMRES: Sec. 2.2.2 (Eqs. 5-6);
+ *   - solvation energy E_sol = 1/2 sum_k q_k phi_reac(y_k): Sec. 2.2.1
+ *     (Eq. for E_sol);
+ *   - GPU direct-sum pipeline (source, mat-vec inside GMRES, energy):
+ *     Sec. 2.4 (Table "Pseudocode for DSBI-PB solver using GPU").
+ *
+ * Unknowns: u = [phi_1..phi_N ; psi_1..psi_N], psi = dphi/dnu on the inner
+ * side of the surface, in the internal units of the paper's equations
+ * (G0 = 1/(4 pi r)); entry points that return physical values say so.
+ *
+ * Conventions for every entry point:
+ *   - Return a bipb_status; on failure bipb_last_error() (thread-local) holds
+ *     a message.  No C++ exception crosses this boundary.
+ *   - Host pointers ("host") are read or written synchronously and never
+ *     retained; the library copies what it keeps.  Device pointers ("device")
+ *     must be CUDA device memory of the current device; the library reads and
+ *     writes them on the handle's stream and does not retain them.
+ *   - Array layouts are row-major: an "n x 3" array holds x0 y0 z0 x1 y1 z1 ..
+ *   - All work runs on the stream given at creation (NULL = legacy default
+ *     stream).  Calls with host outputs synchronise that stream before they
+ *     return; calls with only device outputs are asynchronous.
+ *   - A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef BIPB_H
+#define BIPB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bipb_surface_s* bipb_surface; /* opaque; owns all its device memory */
+
+typedef enum {
+  BIPB_OK = 0,
+  BIPB_ERR_INVALID_ARG = 1,   /* bad size, pointer, value; nothing launched */
+  BIPB_ERR_CUDA = 2,          /* a CUDA call failed; message in bipb_last_error() */
+  BIPB_ERR_OOM = 3,           /* device allocation failed */
+  BIPB_ERR_NOT_CONVERGED = 4, /* solve hit max_iter; best iterate kept, info filled */
+  BIPB_ERR_STATE = 5          /* call order violated (e.g. energy before solve) or stale handle */
+} bipb_status;
+
+typedef enum {
+  BIPB_FP64 = 0,  /* all pair arithmetic in FP64 */
+  BIPB_MIXED = 1, /* FP32 pair arithmetic inside GMRES, FP64 refinement residual */
+  BIPB_FP32 = 2   /* mat-vec only: FP32 pair arithmetic, FP64 sums across tiles */
+} bipb_precision;
+
+/* Dielectric medium (Sec. 2.1): eps_in > 0 inside, eps_out > 0 outside, kappa >= 0 (1/A). */
+typedef struct {
+  double eps_in;
+  double eps_out;
+  double kappa;
+} bipb_medium;
+
+typedef struct {
+  bipb_medium medium;
+  double tol;          /* target ||b - A u||_2 / ||b||_2, 0 < tol < 1 */
+  int restart;         /* GMRES restart length m, 1..64 (10 if 0) */
+  int max_iter;        /* cap on GMRES iterations summed over restarts and refinement steps (1000 if 0) */
+  int precision;       /* bipb_precision: BIPB_FP64 or BIPB_MIXED */
+  int inner_max_iter;  /* MIXED: cap on inner iterations per refinement step (200 if 0) */
+  double inner_tol;    /* MIXED: inner relative tolerance per refinement step (1e-6 if 0) */
+  const double* x0;    /* optional warm start, host, n_rhs x 2N internal units, or NULL (zero) */
+} bipb_solve_params;
+
+typedef struct {
+  int converged;       /* 1 if rel_residual <= tol */
+  int iters;           /* GMRES iterations (inner iterations for MIXED) */
+  int refine_steps;    /* MIXED: refinement steps taken (0 for FP64) */
+  int matvecs64;       /* FP64 mat-vecs applied to this right-hand side */
+  int matvecs32;       /* FP32 mat-vecs applied to this right-hand side */
+  int reserved;
+  double rel_residual; /* final ||b - A u|| / ||b||, FP64 true residual */
+  double seconds;      /* wall time of the whole bipb_solve call */
+} bipb_solve_info;
+
+/*
+ * Create a surface from N flat triangles (centroid collocation, Sec. 2.2.2).
+ *   centroids: host, n x 3, Angstrom.  normals: host, n x 3, unit, outward
+ *   (re-normalised; |n| must be within 1e-6 of 1).  areas: host, n, > 0, A^2.
+ *   cuda_stream: a cudaStream_t or NULL.
+ * Validation (BIPB_ERR_INVALID_ARG, nothing allocated): n >= 2, every value
+ * finite, areas > 0, no two centroids equal in FP64 or after rounding to
+ * FP32 about the mean centroid.
+ */
+bipb_status bipb_surface_create(int64_t n, const double* centroids, const double* normals,
+                                const double* areas, void* cuda_stream, bipb_surface* out);
+
+/* Free every device allocation of the handle; the handle value becomes invalid. */
+bipb_status bipb_surface_destroy(bipb_surface s);
+
+/* Number of triangles N of the handle (0 for an invalid handle). */
+int64_t bipb_surface_size(bipb_surface s);
+
+/*
+ * Set n_rhs charge configurations (the point charges of Sec. 2.1, Eq. for rho).
+ *   pos: host, (n_pos_sets x nc x 3) Angstrom with n_pos_sets = 1 (shared by
+ *        all configurations) or n_rhs (one position set per configuration).
+ *   q:   host, n_rhs x nc, units of e.
+ * Charges must lie off every centroid.  Invalidates any previous solution.
+ */
+bipb_status bipb_charges_set(bipb_surface s, int64_t nc, const double* pos, int n_pos_sets,
+                             int n_rhs, const double* q);
+
+/*
+ * Solve A u = b for every configuration (GMRES, Sec. 2.2.2; Eqs. 5-6), where
+ * b = [S1; S2] of the charges (Eq. for S1, S2).  info: host array of n_rhs
+ * (may be NULL).  Returns BIPB_ERR_NOT_CONVERGED if any configuration missed
+ * tol within max_iter; its best iterate is kept and can still be read.
+ */
+bipb_status bipb_solve(bipb_surface s, const bipb_solve_params* p, bipb_solve_info* info);
+
+/* Solvation energy per configuration, kcal/mol, host array of n_rhs (Eq. for E_sol). */
+bipb_status bipb_energy(bipb_surface s, double* e_sol);
+
+/*
+ * Surface potential phi (kcal/mol/e) and its inner normal derivative
+ * (kcal/mol/e/A), host arrays n_rhs x N each; dphi_dn may be NULL.
+ */
+bipb_status bipb_surface_potential(bipb_surface s, double* phi, double* dphi_dn);
+
+/*
+ * Gradient of the solvation energy (kcal/mol) of every configuration with
+ * respect to its charges (host, n_rhs x nc, kcal/mol/e) and charge positions
+ * (host, n_rhs x nc x 3, kcal/mol/A), at fixed surface, from one adjoint
+ * solve A^T lam = c per configuration (c: the energy row, E = 1/2 c.u).
+ * Requires a successful bipb_solve; p gives the adjoint solve's settings.
+ */
+bipb_status bipb_energy_grad(bipb_surface s, const bipb_solve_params* p, double* dE_dq,
+                             double* dE_dpos);
+
+/* ---------------------------------------------------------------------------
+ * Hot-path building blocks on device memory (asynchronous on the handle's
+ * stream).  They expose the passes of the paper's GPU pipeline (Sec. 2.4)
+ * one by one, for parity testing, benchmarking and custom drivers.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * y = A u (transpose = 0) or y = A^T u (transpose = 1) for n_vec vectors.
+ *   u, y: device, n_vec x 2N doubles, internal units; y must not alias u.
+ *   precision: BIPB_FP64 or BIPB_FP32 (FP32 pair arithmetic per source tile,
+ *   FP64 sums across tiles and for the diagonal).
+ */
+bipb_status bipb_matvec(bipb_surface s, const bipb_medium* m, int precision, int transpose,
+                        int n_vec, const double* u, double* y);
+
+/* b = [S1; S2] for every configuration: device, n_rhs x 2N doubles (FP64). */
+bipb_status bipb_source(bipb_surface s, const bipb_medium* m, double* b);
+
+/*
+ * Reaction potential at every charge of every configuration from surface
+ * values u (device, n_rhs x 2N, internal units):
+ *   phi_reac(y_k) = sum_j ds_j [K1(y_k, x_j) psi_j + K2(y_k, x_j) phi_j]
+ * written to phi_reac (device, n_rhs x nc, internal units), and
+ * e_sol (device, n_rhs, kcal/mol) = 4 pi 332.0716 * 1/2 sum_k q_k phi_reac(y_k).
+ * Either output may be NULL.  FP64.
+ */
+bipb_status bipb_reaction(bipb_surface s, const bipb_medium* m, const double* u,
+                          double* phi_reac, double* e_sol);
+
+/* ---------------------------------------------------------------------------
+ * Kernel timing.  The paper reports the mean time of one mat-vec per GMRES
+ * iteration (Sec. 3, Eq. for the average mat-vec time); these calls expose
+ * the same quantity per pair kernel, from CUDA events recorded around every
+ * launch of the kind on the handle's stream (inside recorded CUDA graphs too).
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  BIPB_KERNEL_MATVEC64 = 0,   /* FP64 mat-vec pair kernel */
+  BIPB_KERNEL_MATVEC32 = 1,   /* FP32 mat-vec pair kernel */
+  BIPB_KERNEL_MATVEC64_T = 2, /* FP64 transposed mat-vec pair kernel */
+  BIPB_KERNEL_MATVEC32_T = 3, /* FP32 transposed mat-vec pair kernel */
+  BIPB_KERNEL_SOURCE = 4,     /* source-term pair kernel */
+  BIPB_KERNEL_REACTION = 5,   /* reaction-potential / energy pair kernel */
+  BIPB_KERNEL_ENERGY_ROW = 6, /* energy-row pair kernel (adjoint right-hand side) */
+  BIPB_KERNEL_GRAD = 7,       /* energy-gradient pair kernel */
+  BIPB_KERNEL_KINDS = 8
+} bipb_kernel_kind;
+
+/* Turn timing on (1) or off (0); turning it on clears the totals. */
+bipb_status bipb_timer_enable(bipb_surface s, int on);
+
+/* Launch count and summed duration (ms) of one kernel kind since the timer
+ * was turned on (host outputs; synchronises the handle's stream). */
+bipb_status bipb_timer_read(bipb_surface s, int kind, int64_t* launches, double* total_ms);
+
+/* Number of CUDA kernels this handle has launched since creation (kernels
+ * inside replayed CUDA graphs included).  Host output; no synchronisation. */
+bipb_status bipb_launch_count(bipb_surface s, int64_t* launches);
+
+/* Most recent error message of this thread ("" if none). */
+const char* bipb_last_error(void);
+const char* bipb_status_string(bipb_status st);
+
+/* Library version string. */
+const char* bipb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIPB_H */

@@ -60,6 +60,7 @@ def lib():
         L.orc_source.argtypes = [I, P, P, I, P, P, D, P]
         L.orc_matvec.argtypes = [I, P, P, P, D, D, P, P]
         L.orc_matvec_t.argtypes = [I, P, P, P, D, D, P, P]
+        L.orc_matvec_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
         L.orc_assemble.argtypes = [I, P, P, P, D, D, P]
         L.orc_gesv.argtypes = [I, P, I, P]
         L.orc_gesv.restype = ctypes.c_int
@@ -122,6 +123,16 @@ def matvec(x, nrm, area, eps, kappa, u):
     n = x.shape[0]
     out = np.zeros(2 * n)
     lib().orc_matvec(n, _p(x), _p(nrm), _p(area), eps, kappa, _p(u), _p(out))
+    return out
+
+
+def matvec_rows(x, nrm, area, eps, kappa, u, rows):
+    """Rows ``rows`` (indices into [0, 2N)) of A u, each summed on its own."""
+    x, nrm, area, u = _c(x), _c(nrm), _c(area), _c(u)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(rows.shape[0])
+    lib().orc_matvec_rows(x.shape[0], _p(x), _p(nrm), _p(area), eps, kappa, _p(u), rows.shape[0],
+                          rows.ctypes.data_as(ctypes.c_void_p), _p(out))
     return out
 
 

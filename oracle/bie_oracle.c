@@ -152,6 +152,26 @@ void orc_matvec(int64_t n, const double* x, const double* nrm, const double* are
   }
 }
 
+/* Selected rows of A u: out[r] = row rows[r] of orc_matvec (0 <= rows[r] < 2n). */
+void orc_matvec_rows(int64_t n, const double* x, const double* nrm, const double* area, double eps,
+                     double kappa, const double* u, int64_t nrows, const int64_t* rows, double* out) {
+  const double* phi = u;
+  const double* psi = u + n;
+  int64_t r;
+#pragma omp parallel for schedule(static)
+  for (r = 0; r < nrows; ++r) {
+    int64_t row = rows[r];
+    int64_t i = row < n ? row : row - n;
+    double acc = 0.0, K[4];
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      orc_kernels(x + 3 * i, nrm + 3 * i, x + 3 * j, nrm + 3 * j, eps, kappa, K);
+      acc += (row < n ? (K[0] * psi[j] + K[1] * phi[j]) : (K[2] * psi[j] + K[3] * phi[j])) * area[j];
+    }
+    out[r] = row < n ? 0.5 * (1.0 + eps) * phi[i] - acc : 0.5 * (1.0 + 1.0 / eps) * psi[i] - acc;
+  }
+}
+
 /* out = A^T w: the transpose of the operator of orc_matvec. */
 void orc_matvec_t(int64_t n, const double* x, const double* nrm, const double* area, double eps,
                   double kappa, const double* w, double* out) {

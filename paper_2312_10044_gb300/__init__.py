@@ -1,0 +1,298 @@
+"""Python binding of libbipb, the GB300 direct-sum boundary-integral PB solver.
+
+Argument marshalling only: every step of the path runs in the CUDA kernels
+of ``libbipb.so`` (built in-tree by :func:`paper_2312_10044_gb300.build.build`).
+There is no CPU fallback; importing this package fails if the library is
+missing.  The names follow the C ABI in ``include/bipb.h``.
+
+Host arrays are numpy FP64; device arrays are CUDA torch tensors (FP64,
+contiguous), used only as device memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbipb.so")
+
+BIPB_OK = 0
+BIPB_ERR_INVALID_ARG = 1
+BIPB_ERR_CUDA = 2
+BIPB_ERR_OOM = 3
+BIPB_ERR_NOT_CONVERGED = 4
+BIPB_ERR_STATE = 5
+
+FP64 = 0
+MIXED = 1
+FP32 = 2
+
+KCAL = 4.0 * np.pi * 332.0716  # internal units -> kcal/mol (per e)
+
+EXPORTED = (
+    "bipb_surface_create", "bipb_surface_destroy", "bipb_surface_size", "bipb_charges_set",
+    "bipb_solve", "bipb_energy", "bipb_surface_potential", "bipb_energy_grad", "bipb_matvec",
+    "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
+    "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count",
+)
+
+KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad")
+
+
+class bipb_medium(ctypes.Structure):
+    _fields_ = [("eps_in", ctypes.c_double), ("eps_out", ctypes.c_double), ("kappa", ctypes.c_double)]
+
+
+class bipb_solve_params(ctypes.Structure):
+    _fields_ = [
+        ("medium", bipb_medium),
+        ("tol", ctypes.c_double),
+        ("restart", ctypes.c_int),
+        ("max_iter", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("inner_max_iter", ctypes.c_int),
+        ("inner_tol", ctypes.c_double),
+        ("x0", ctypes.c_void_p),
+    ]
+
+
+class bipb_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("converged", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("refine_steps", ctypes.c_int),
+        ("matvecs64", ctypes.c_int),
+        ("matvecs32", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("rel_residual", ctypes.c_double),
+        ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class BipbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library():
+    """Load libbipb.so (ctypes); raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbipb.so not found at {LIB_PATH}: run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "bipb_surface_create": ([I64, P, P, P, P, P], st),
+        "bipb_surface_destroy": ([P], st),
+        "bipb_surface_size": ([P], I64),
+        "bipb_charges_set": ([P, I64, P, I, I, P], st),
+        "bipb_solve": ([P, P, P], st),
+        "bipb_energy": ([P, P], st),
+        "bipb_surface_potential": ([P, P, P], st),
+        "bipb_energy_grad": ([P, P, P, P], st),
+        "bipb_matvec": ([P, P, I, I, I, P, P], st),
+        "bipb_source": ([P, P, P], st),
+        "bipb_reaction": ([P, P, P, P, P], st),
+        "bipb_last_error": ([], ctypes.c_char_p),
+        "bipb_status_string": ([I], ctypes.c_char_p),
+        "bipb_version": ([], ctypes.c_char_p),
+        "bipb_timer_enable": ([P, I], st),
+        "bipb_timer_read": ([P, I, P, P], st),
+        "bipb_launch_count": ([P, P], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != BIPB_OK:
+        L = load_library()
+        raise BipbError(status, L.bipb_last_error().decode())
+
+
+def _host(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _hp(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _dp(t):
+    """Device pointer of a CUDA FP64 contiguous torch tensor."""
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def medium(eps_in=1.0, eps_out=80.0, kappa=0.1257):
+    return bipb_medium(eps_in, eps_out, kappa)
+
+
+def solve_params(eps_in=1.0, eps_out=80.0, kappa=0.1257, tol=1e-8, restart=10, max_iter=1000,
+                 precision=MIXED, inner_max_iter=0, inner_tol=0.0, x0=None):
+    p = bipb_solve_params(bipb_medium(eps_in, eps_out, kappa), tol, restart, max_iter, precision,
+                          inner_max_iter, inner_tol, None)
+    return p
+
+
+class Surface:
+    """A triangulated surface on the GPU (one bipb_surface handle)."""
+
+    def __init__(self, centroids, normals, areas, stream=None):
+        self._L = load_library()
+        c = _host(centroids, (-1, 3))
+        n = _host(normals, (-1, 3))
+        a = _host(areas, (-1,))
+        if not (c.shape[0] == n.shape[0] == a.shape[0]):
+            raise ValueError("centroids, normals and areas differ in length")
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except Exception:  # pragma: no cover - torch is optional for the host API
+                stream = 0
+        h = ctypes.c_void_p()
+        _check(self._L.bipb_surface_create(c.shape[0], _hp(c), _hp(n), _hp(a), ctypes.c_void_p(stream),
+                                           ctypes.byref(h)))
+        self._h = h
+        self.n = c.shape[0]
+        self.nc = 0
+        self.n_rhs = 0
+
+    # -------------------------------------------------------------- lifetime
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(self._L.bipb_surface_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -------------------------------------------------------------- charges
+    def set_charges(self, pos, q):
+        """pos: (Nc, 3) or (B, Nc, 3); q: (Nc,) or (B, Nc)."""
+        q = _host(q)
+        if q.ndim == 1:
+            q = q[None, :]
+        n_rhs, nc = q.shape
+        pos = _host(pos)
+        n_pos = 1 if pos.ndim == 2 else pos.shape[0]
+        pos = _host(pos, (n_pos, nc, 3))
+        _check(self._L.bipb_charges_set(self._h, nc, _hp(pos), n_pos, n_rhs, _hp(q)))
+        self.nc, self.n_rhs = nc, n_rhs
+
+    # -------------------------------------------------------------- solve / outputs
+    def solve(self, params=None, x0=None, raise_on_not_converged=True, **kw):
+        p = params if params is not None else solve_params(**kw)
+        x0h = None
+        if x0 is not None:
+            x0h = _host(x0, (self.n_rhs, 2 * self.n))
+            p.x0 = x0h.ctypes.data
+        info = (bipb_solve_info * self.n_rhs)()
+        st = self._L.bipb_solve(self._h, ctypes.byref(p), info)
+        p.x0 = None
+        if st != BIPB_OK and not (st == BIPB_ERR_NOT_CONVERGED and not raise_on_not_converged):
+            _check(st)
+        return [i.as_dict() for i in info]
+
+    def energy(self):
+        e = np.zeros(self.n_rhs)
+        _check(self._L.bipb_energy(self._h, _hp(e)))
+        return e
+
+    def surface_potential(self):
+        phi = np.zeros((self.n_rhs, self.n))
+        dphi = np.zeros((self.n_rhs, self.n))
+        _check(self._L.bipb_surface_potential(self._h, _hp(phi), _hp(dphi)))
+        return phi, dphi
+
+    def energy_grad(self, params=None, **kw):
+        p = params if params is not None else solve_params(**kw)
+        dq = np.zeros((self.n_rhs, self.nc))
+        dy = np.zeros((self.n_rhs, self.nc, 3))
+        _check(self._L.bipb_energy_grad(self._h, ctypes.byref(p), _hp(dq), _hp(dy)))
+        return dq, dy
+
+    # -------------------------------------------------------------- device passes
+    def matvec(self, u, y, precision=FP64, transpose=False, med=None):
+        """y = A u (or A^T u); u, y CUDA float64 tensors of shape (k, 2N) or (2N,)."""
+        m = med if med is not None else medium()
+        n_vec = u.numel() // (2 * self.n)
+        if u.numel() != n_vec * 2 * self.n or y.numel() != u.numel():
+            raise ValueError("u and y must hold k * 2N values")
+        _check(self._L.bipb_matvec(self._h, ctypes.byref(m), precision, int(transpose), n_vec, _dp(u), _dp(y)))
+        return y
+
+    def source(self, b, med=None):
+        m = med if med is not None else medium()
+        _check(self._L.bipb_source(self._h, ctypes.byref(m), _dp(b)))
+        return b
+
+    def reaction(self, u, phi_reac=None, e_sol=None, med=None):
+        m = med if med is not None else medium()
+        _check(self._L.bipb_reaction(self._h, ctypes.byref(m), _dp(u),
+                                     _dp(phi_reac) if phi_reac is not None else None,
+                                     _dp(e_sol) if e_sol is not None else None))
+
+
+def timer_enable(surface, on=True):
+    _check(load_library().bipb_timer_enable(surface.handle, int(on)))
+
+
+def timer_read(surface):
+    """{kind: (launches, total_ms)} for every pair-kernel kind."""
+    L = load_library()
+    out = {}
+    for k, name in enumerate(KERNEL_KINDS):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        _check(L.bipb_timer_read(surface.handle, k, ctypes.byref(n), ctypes.byref(ms)))
+        out[name] = (n.value, ms.value)
+    return out
+
+
+def launch_count(surface):
+    n = ctypes.c_int64()
+    _check(load_library().bipb_launch_count(surface.handle, ctypes.byref(n)))
+    return n.value
+
+
+def version():
+    return load_library().bipb_version().decode()

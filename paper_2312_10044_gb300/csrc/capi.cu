@@ -1,0 +1,476 @@
+// The C ABI of libbipb (declared in include/bipb.h): handles, validation,
+// and the solve / energy / potential / gradient drivers.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <unordered_set>
+
+#include "internal.cuh"
+
+namespace bipb {
+
+namespace {
+
+constexpr uint64_t kMagic = 0x62697062534652ull;  // "bipbSFR"
+thread_local std::string g_last_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Orders the handle's private stream after the caller's stream on entry and
+// the caller's stream after the private one on exit.
+struct StreamJoin {
+  Surface* s;
+  explicit StreamJoin(Surface* sf) : s(sf) {
+    BIPB_CUDA(cudaEventRecord(s->ev_in, s->user_stream));
+    BIPB_CUDA(cudaStreamWaitEvent(s->stream, s->ev_in, 0));
+  }
+  ~StreamJoin() {
+    if (cudaEventRecord(s->ev_out, s->stream) == cudaSuccess) cudaStreamWaitEvent(s->user_stream, s->ev_out, 0);
+  }
+};
+
+template <class F>
+bipb_status guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return BIPB_OK;
+  } catch (const Error& e) {
+    g_last_error = e.what();
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return BIPB_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return BIPB_ERR_CUDA;
+  }
+}
+
+bool finite3(const double* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+struct KeyHash {
+  size_t operator()(const std::array<uint64_t, 3>& k) const {
+    return (size_t)(k[0] * 0x9E3779B97F4A7C15ull ^ (k[1] + 0x632BE59BD9B4E019ull) * 31 ^ k[2] * 0x94D049BB133111EBull);
+  }
+};
+std::array<uint64_t, 3> key_of(const double* p) {
+  std::array<uint64_t, 3> k;
+  for (int i = 0; i < 3; ++i) {
+    double v = p[i] == 0.0 ? 0.0 : p[i];  // -0 == +0
+    std::memcpy(&k[i], &v, 8);
+  }
+  return k;
+}
+
+void validate_medium(const bipb_medium* m) {
+  BIPB_REQUIRE(m != nullptr, "medium is NULL");
+  BIPB_REQUIRE(std::isfinite(m->eps_in) && m->eps_in > 0, "eps_in must be finite and > 0");
+  BIPB_REQUIRE(std::isfinite(m->eps_out) && m->eps_out > 0, "eps_out must be finite and > 0");
+  BIPB_REQUIRE(std::isfinite(m->kappa) && m->kappa >= 0, "kappa must be finite and >= 0");
+}
+
+void validate_params(const bipb_solve_params* p) {
+  BIPB_REQUIRE(p != nullptr, "params is NULL");
+  validate_medium(&p->medium);
+  BIPB_REQUIRE(std::isfinite(p->tol) && p->tol > 0 && p->tol < 1, "tol must lie in (0, 1)");
+  BIPB_REQUIRE(p->restart >= 0 && p->restart <= kMaxRestart, "restart must lie in [1, 64] (0 = 10)");
+  BIPB_REQUIRE(p->max_iter >= 0, "max_iter must be >= 0 (0 = 1000)");
+  BIPB_REQUIRE(p->precision == BIPB_FP64 || p->precision == BIPB_MIXED, "precision must be FP64 or MIXED");
+  BIPB_REQUIRE(p->inner_max_iter >= 0, "inner_max_iter must be >= 0");
+  BIPB_REQUIRE(std::isfinite(p->inner_tol) && p->inner_tol >= 0 && p->inner_tol < 1, "inner_tol must lie in [0, 1)");
+}
+
+}  // namespace
+
+// Live handles: a handle is dereferenced only after it is found here, so a
+// destroyed or made-up handle is rejected instead of being read.
+std::mutex g_live_mu;
+std::unordered_set<const Surface*> g_live;
+
+void register_handle(const Surface* s) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  g_live.insert(s);
+}
+bool unregister_handle(const Surface* s) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  return g_live.erase(s) == 1;
+}
+bool is_live(const Surface* s) {
+  std::lock_guard<std::mutex> lk(g_live_mu);
+  return g_live.count(s) == 1;
+}
+
+Surface* checked(bipb_surface h) {
+  Surface* s = reinterpret_cast<Surface*>(h);
+  if (s == nullptr || !is_live(s) || s->magic != kMagic)
+    throw Error(BIPB_ERR_STATE, "invalid or destroyed surface handle");
+  return s;
+}
+
+}  // namespace bipb
+
+using namespace bipb;
+
+extern "C" {
+
+const char* bipb_version(void) { return "bipb 0.1 (sm_103a)"; }
+
+const char* bipb_last_error(void) { return g_last_error.c_str(); }
+
+const char* bipb_status_string(bipb_status st) {
+  switch (st) {
+    case BIPB_OK: return "ok";
+    case BIPB_ERR_INVALID_ARG: return "invalid argument";
+    case BIPB_ERR_CUDA: return "CUDA error";
+    case BIPB_ERR_OOM: return "out of device memory";
+    case BIPB_ERR_NOT_CONVERGED: return "not converged";
+    case BIPB_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+int64_t bipb_surface_size(bipb_surface h) {
+  Surface* s = reinterpret_cast<Surface*>(h);
+  return (s && is_live(s)) ? s->n : 0;
+}
+
+bipb_status bipb_surface_create(int64_t n, const double* centroids, const double* normals, const double* areas,
+                                void* cuda_stream, bipb_surface* out) {
+  return guarded([&] {
+    BIPB_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    BIPB_REQUIRE(n >= 2, "need at least 2 triangles");
+    BIPB_REQUIRE(n <= (int64_t)1 << 28, "at most 2^28 triangles");
+    BIPB_REQUIRE(centroids && normals && areas, "NULL input array");
+    std::vector<double> nrm(3 * n);
+    double c[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+      BIPB_REQUIRE(finite3(centroids + 3 * i), "non-finite centroid");
+      BIPB_REQUIRE(finite3(normals + 3 * i), "non-finite normal");
+      BIPB_REQUIRE(std::isfinite(areas[i]) && areas[i] > 0, "areas must be finite and > 0");
+      const double* v = normals + 3 * i;
+      double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      BIPB_REQUIRE(std::fabs(len - 1.0) <= 1e-6, "normals must have unit length (within 1e-6)");
+      for (int k = 0; k < 3; ++k) {
+        nrm[3 * i + k] = v[k] / len;
+        c[k] += centroids[3 * i + k];
+      }
+    }
+    for (int k = 0; k < 3; ++k) c[k] /= (double)n;
+    // duplicates: exact in FP64, and after centring and rounding to FP32
+    {
+      std::unordered_set<std::array<uint64_t, 3>, KeyHash> seen64, seen32;
+      seen64.reserve(2 * n);
+      seen32.reserve(2 * n);
+      for (int64_t i = 0; i < n; ++i) {
+        BIPB_REQUIRE(seen64.insert(key_of(centroids + 3 * i)).second, "two centroids coincide");
+        double f[3];
+        for (int k = 0; k < 3; ++k) f[k] = (double)(float)(centroids[3 * i + k] - c[k]);
+        BIPB_REQUIRE(seen32.insert(key_of(f)).second, "two centroids coincide after rounding to FP32");
+      }
+    }
+    int dev = 0;
+    BIPB_CUDA(cudaGetDevice(&dev));
+    auto* s = new Surface();
+    try {
+      s->device = dev;
+      BIPB_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev));
+      s->user_stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+      BIPB_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+      BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+      BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+      s->n = n;
+      std::memcpy(s->center, c, sizeof(c));
+      std::vector<double4_32a> geo(n), nv(n), tgt(2 * n);
+      std::vector<float4> tgt32(2 * n);
+      for (int64_t i = 0; i < n; ++i) {
+        const double* p = centroids + 3 * i;
+        geo[i] = make_double4_32a(p[0] - c[0], p[1] - c[1], p[2] - c[2], areas[i]);
+        nv[i] = make_double4_32a(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], 0.0);
+        tgt[2 * i] = geo[i];
+        tgt[2 * i + 1] = nv[i];
+        tgt32[2 * i] = make_float4((float)geo[i].x, (float)geo[i].y, (float)geo[i].z, (float)areas[i]);
+        tgt32[2 * i + 1] = make_float4((float)nv[i].x, (float)nv[i].y, (float)nv[i].z, 0.f);
+      }
+      s->geo64.ensure(n);
+      s->nrm64.ensure(n);
+      s->tgt64.ensure(2 * n);
+      s->tgt32.ensure(2 * n);
+      BIPB_CUDA(cudaMemcpy(s->geo64.p, geo.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
+      BIPB_CUDA(cudaMemcpy(s->nrm64.p, nv.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
+      BIPB_CUDA(cudaMemcpy(s->tgt64.p, tgt.data(), 2 * n * sizeof(double4_32a), cudaMemcpyHostToDevice));
+      BIPB_CUDA(cudaMemcpy(s->tgt32.p, tgt32.data(), 2 * n * sizeof(float4), cudaMemcpyHostToDevice));
+      s->magic = kMagic;
+    } catch (...) {
+      if (s->stream) cudaStreamDestroy(s->stream);
+      if (s->ev_in) cudaEventDestroy(s->ev_in);
+      if (s->ev_out) cudaEventDestroy(s->ev_out);
+      delete s;
+      throw;
+    }
+    register_handle(s);
+    *out = reinterpret_cast<bipb_surface>(s);
+  });
+}
+
+bipb_status bipb_surface_destroy(bipb_surface h) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    if (!unregister_handle(s)) throw Error(BIPB_ERR_STATE, "invalid or destroyed surface handle");
+    DeviceGuard dg(s->device);
+    cudaStreamSynchronize(s->stream);
+    gmres_free(s);
+    s->magic = 0;
+    cudaStreamDestroy(s->stream);
+    cudaEventDestroy(s->ev_in);
+    cudaEventDestroy(s->ev_out);
+    delete s;
+  });
+}
+
+bipb_status bipb_charges_set(bipb_surface h, int64_t nc, const double* pos, int n_pos_sets, int n_rhs,
+                             const double* q) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(nc >= 1 && nc <= (int64_t)1 << 26, "nc must lie in [1, 2^26]");
+    BIPB_REQUIRE(n_rhs >= 1 && n_rhs <= 4096, "n_rhs must lie in [1, 4096]");
+    BIPB_REQUIRE(n_pos_sets == 1 || n_pos_sets == n_rhs, "n_pos_sets must be 1 or n_rhs");
+    BIPB_REQUIRE(pos && q, "NULL input array");
+    // centroid keys in the caller's frame, to reject charges sitting on a centroid
+    std::vector<double4_32a> geo(s->n);
+    DeviceGuard dg(s->device);
+    BIPB_CUDA(cudaMemcpy(geo.data(), s->geo64.p, s->n * sizeof(double4_32a), cudaMemcpyDeviceToHost));
+    std::unordered_set<std::array<uint64_t, 3>, KeyHash> cent;
+    cent.reserve(2 * s->n);
+    for (int64_t i = 0; i < s->n; ++i) {
+      double p[3] = {geo[i].x, geo[i].y, geo[i].z};
+      cent.insert(key_of(p));
+    }
+    std::vector<double4_32a> rec((size_t)n_rhs * nc);
+    for (int r = 0; r < n_rhs; ++r) {
+      const double* pr = pos + (size_t)(n_pos_sets == 1 ? 0 : r) * nc * 3;
+      for (int64_t k = 0; k < nc; ++k) {
+        BIPB_REQUIRE(finite3(pr + 3 * k), "non-finite charge position");
+        double qk = q[(size_t)r * nc + k];
+        BIPB_REQUIRE(std::isfinite(qk), "non-finite charge");
+        double p[3] = {pr[3 * k] - s->center[0], pr[3 * k + 1] - s->center[1], pr[3 * k + 2] - s->center[2]};
+        BIPB_REQUIRE(cent.find(key_of(p)) == cent.end(), "a charge sits on a centroid");
+        rec[(size_t)r * nc + k] = make_double4_32a(p[0], p[1], p[2], qk);
+      }
+    }
+    s->grow(s->chg, rec.size());
+    BIPB_CUDA(cudaMemcpy(s->chg.p, rec.data(), rec.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+    s->q_host.assign(q, q + (size_t)n_rhs * nc);
+    s->nc = nc;
+    s->n_rhs = n_rhs;
+    s->n_pos_sets = n_pos_sets;
+    s->have_solution = false;
+  });
+}
+
+bipb_status bipb_source(bipb_surface h, const bipb_medium* m, double* b) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    validate_medium(m);
+    BIPB_REQUIRE(b != nullptr, "b is NULL");
+    BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    for (int r = 0; r < s->n_rhs; ++r) source_pass(s, *m, r, b + (size_t)r * 2 * s->n);
+  });
+}
+
+bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int transpose, int n_vec,
+                        const double* u, double* y) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    validate_medium(m);
+    BIPB_REQUIRE(precision == BIPB_FP64 || precision == BIPB_FP32, "precision must be FP64 or FP32");
+    BIPB_REQUIRE(n_vec >= 1, "n_vec must be >= 1");
+    BIPB_REQUIRE(u && y, "NULL vector");
+    BIPB_REQUIRE(u != y, "y must not alias u");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    const size_t len = 2 * (size_t)s->n;
+    for (int v = 0; v < n_vec; ++v) matvec(s, *m, precision, transpose != 0, u + v * len, y + v * len, nullptr);
+  });
+}
+
+bipb_status bipb_reaction(bipb_surface h, const bipb_medium* m, const double* u, double* phi_reac,
+                          double* e_sol) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    validate_medium(m);
+    BIPB_REQUIRE(u != nullptr, "u is NULL");
+    BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    for (int r = 0; r < s->n_rhs; ++r)
+      reaction_pass(s, *m, r, u + (size_t)r * 2 * s->n, phi_reac ? phi_reac + (size_t)r * s->nc : nullptr,
+                    e_sol ? e_sol + r : nullptr);
+  });
+}
+
+bipb_status bipb_solve(bipb_surface h, const bipb_solve_params* p, bipb_solve_info* info) {
+  bipb_status st = BIPB_OK;
+  bipb_status rc = guarded([&] {
+    auto t0 = std::chrono::steady_clock::now();
+    Surface* s = checked(h);
+    validate_params(p);
+    BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    const size_t len = 2 * (size_t)s->n;
+    s->grow(s->u, s->n_rhs * len);
+    s->grow(s->b, s->n_rhs * len);
+    s->grow(s->e_dev, s->n_rhs);
+    if (p->x0) {
+      for (size_t i = 0; i < s->n_rhs * len; ++i) BIPB_REQUIRE(std::isfinite(p->x0[i]), "non-finite x0");
+      BIPB_CUDA(cudaMemcpyAsync(s->u.p, p->x0, s->n_rhs * len * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    }
+    s->have_solution = false;
+    std::vector<SolveResult> res(s->n_rhs);
+    for (int r = 0; r < s->n_rhs; ++r) {
+      source_pass(s, p->medium, r, s->b.p + r * len);
+      res[r] = gmres_solve(s, p->medium, *p, false, s->b.p + r * len, s->u.p + r * len, p->x0 != nullptr);
+      reaction_pass(s, p->medium, r, s->u.p + r * len, nullptr, s->e_dev.p + r);
+      if (!res[r].converged) st = BIPB_ERR_NOT_CONVERGED;
+    }
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    s->have_solution = true;
+    s->solved_medium = p->medium;
+    double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) {
+      for (int r = 0; r < s->n_rhs; ++r) {
+        info[r].converged = res[r].converged;
+        info[r].iters = res[r].iters;
+        info[r].refine_steps = res[r].refine_steps;
+        info[r].matvecs64 = res[r].matvecs64;
+        info[r].matvecs32 = res[r].matvecs32;
+        info[r].reserved = 0;
+        info[r].rel_residual = res[r].rel_residual;
+        info[r].seconds = secs;
+      }
+    }
+  });
+  if (rc != BIPB_OK) return rc;
+  if (st != BIPB_OK) g_last_error = "at least one right-hand side did not reach tol within max_iter";
+  return st;
+}
+
+bipb_status bipb_energy(bipb_surface h, double* e_sol) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(e_sol != nullptr, "e_sol is NULL");
+    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+    DeviceGuard dg(s->device);
+    BIPB_CUDA(cudaMemcpyAsync(e_sol, s->e_dev.p, s->n_rhs * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+  });
+}
+
+bipb_status bipb_surface_potential(bipb_surface h, double* phi, double* dphi_dn) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(phi != nullptr, "phi is NULL");
+    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+    DeviceGuard dg(s->device);
+    const size_t n = s->n, len = 2 * n;
+    std::vector<double> u(s->n_rhs * len);
+    BIPB_CUDA(cudaMemcpyAsync(u.data(), s->u.p, u.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    for (int r = 0; r < s->n_rhs; ++r)
+      for (size_t i = 0; i < n; ++i) {
+        phi[r * n + i] = kKcal * u[r * len + i];
+        if (dphi_dn) dphi_dn[r * n + i] = kKcal * u[r * len + n + i];
+      }
+  });
+}
+
+bipb_status bipb_energy_grad(bipb_surface h, const bipb_solve_params* p, double* dE_dq, double* dE_dpos) {
+  bipb_status st = BIPB_OK;
+  bipb_status rc = guarded([&] {
+    Surface* s = checked(h);
+    validate_params(p);
+    BIPB_REQUIRE(dE_dq || dE_dpos, "both outputs are NULL");
+    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+    const bipb_medium& m = s->solved_medium;
+    BIPB_REQUIRE(p->medium.eps_in == m.eps_in && p->medium.eps_out == m.eps_out && p->medium.kappa == m.kappa,
+                 "params.medium differs from the medium of the last solve");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    const size_t len = 2 * (size_t)s->n, nc = s->nc;
+    DevBuf<double> c, lam, dq, dy;
+    c.ensure(len);
+    lam.ensure(len);
+    dq.ensure(nc);
+    dy.ensure(3 * nc);
+    std::vector<double> hq(nc), hy(3 * nc);
+    bipb_solve_params pa = *p;
+    pa.x0 = nullptr;
+    for (int r = 0; r < s->n_rhs; ++r) {
+      energy_row_pass(s, m, r, c.p);
+      SolveResult res = gmres_solve(s, m, pa, true, c.p, lam.p, false);
+      if (!res.converged) st = BIPB_ERR_NOT_CONVERGED;
+      grad_pass(s, m, r, s->u.p + r * len, lam.p, dq.p, dy.p);
+      BIPB_CUDA(cudaMemcpyAsync(hq.data(), dq.p, nc * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      BIPB_CUDA(cudaMemcpyAsync(hy.data(), dy.p, 3 * nc * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+      BIPB_CUDA(cudaStreamSynchronize(s->stream));
+      for (size_t k = 0; k < nc; ++k) {
+        if (dE_dq) dE_dq[r * nc + k] = kKcal * hq[k];
+        if (dE_dpos)
+          for (int a = 0; a < 3; ++a) dE_dpos[(r * nc + k) * 3 + a] = kKcal * hy[3 * k + a];
+      }
+    }
+  });
+  if (rc != BIPB_OK) return rc;
+  if (st != BIPB_OK) g_last_error = "an adjoint solve did not reach tol within max_iter";
+  return st;
+}
+
+bipb_status bipb_timer_enable(bipb_surface h, int on) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    DeviceGuard dg(s->device);
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    s->timer.collect();
+    s->timer.reset();
+    s->timer.on = on != 0;
+  });
+}
+
+bipb_status bipb_launch_count(bipb_surface h, int64_t* launches) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(launches != nullptr, "launches is NULL");
+    *launches = s->launches;
+  });
+}
+
+bipb_status bipb_timer_read(bipb_surface h, int kind, int64_t* launches, double* total_ms) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(kind >= 0 && kind < kTKinds, "unknown kernel kind");
+    DeviceGuard dg(s->device);
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    s->timer.collect();
+    if (launches) *launches = s->timer.count[kind];
+    if (total_ms) *total_ms = s->timer.total_ms[kind];
+  });
+}
+
+}  // extern "C"

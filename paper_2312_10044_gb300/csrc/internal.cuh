@@ -1,0 +1,233 @@
+// Internal declarations of libbipb (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "bipb.h"
+#include "pair.cuh"
+
+namespace bipb {
+
+struct Error : std::runtime_error {
+  bipb_status st;
+  Error(bipb_status s, const std::string& m) : std::runtime_error(m), st(s) {}
+};
+
+#define BIPB_CUDA(call)                                                                          \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      throw ::bipb::Error(e_ == cudaErrorMemoryAllocation ? BIPB_ERR_OOM : BIPB_ERR_CUDA,        \
+                          std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+// After every kernel launch: check the launch and count it (a launch issued
+// while a graph is being recorded counts toward the graph, not the handle).
+#define BIPB_LAUNCHED(sf)                     \
+  do {                                        \
+    BIPB_CUDA(cudaGetLastError());            \
+    if ((sf)->recording)                      \
+      ++(sf)->recorded_launches;              \
+    else                                      \
+      ++(sf)->launches;                       \
+  } while (0)
+#define BIPB_REQUIRE(cond, msg)                                     \
+  do {                                                              \
+    if (!(cond)) throw ::bipb::Error(BIPB_ERR_INVALID_ARG, (msg));  \
+  } while (0)
+
+// Owning device buffer that only grows.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t cap = 0;
+  // returns true when the buffer moved
+  bool ensure(size_t count) {
+    if (count <= cap) return false;
+    release();
+    BIPB_CUDA(cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T)));
+    cap = count;
+    return true;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  ~DevBuf() { release(); }
+};
+
+// Tiling of one pair pass: targets split into tiles of nt*tpt, sources into
+// chunks of ch staged in shared memory, chunks grouped into splits.
+struct PassTiling {
+  int n_tiles = 0;
+  int n_chunks = 0;  // source chunks (sources padded to n_chunks * ch)
+  int n_splits = 0;
+  int chunks_per_split = 0;
+};
+
+// Kernel-variant selection for the FP32 mat-vec (the autotuned knob).
+struct Matvec32Variant {
+  int nt = 256;   // threads per CTA
+  int tpt = 2;    // targets per thread
+  int ch = 128;   // sources per shared-memory chunk
+  int waves = 8;  // target CTAs per SM-slot (sets the source split count)
+};
+
+constexpr int kMaxRestart = 64;
+
+// Per-kernel CUDA-event timing of the pair kernels (off by default).
+enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTKinds };
+
+struct EventPair {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<EventPair> pending;   // recorded by direct launches, read once
+  std::vector<EventPair>* capture = nullptr;  // while recording a graph: where its pairs go
+  double total_ms[kTKinds] = {0};
+  long long count[kTKinds] = {0};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    BIPB_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  // accumulate finished pairs (the stream has been synchronised)
+  void add(const EventPair& p) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      total_ms[p.kind] += ms;
+      count[p.kind] += 1;
+    }
+  }
+  void collect() {
+    for (auto& p : pending) {
+      add(p);
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  void reset() {
+    for (int k = 0; k < kTKinds; ++k) total_ms[k] = 0, count[k] = 0;
+  }
+  ~KernelTimer() {
+    for (auto e : pool) cudaEventDestroy(e);
+    for (auto& p : pending) cudaEventDestroy(p.a), cudaEventDestroy(p.b);
+  }
+};
+
+struct GmresWork;  // gmres.cu
+
+struct Surface {
+  uint64_t magic = 0;
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;  // private, non-blocking; joined to user_stream per call
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
+  int64_t n = 0;
+  double center[3] = {0, 0, 0};  // all device coordinates are relative to the mean centroid
+
+  DevBuf<double4_32a> geo64;  // n: (x, y, z, area), centred
+  DevBuf<double4_32a> nrm64;  // n: (nx, ny, nz, 0)
+  DevBuf<double4_32a> tgt64;  // 2n: (x, y, z, area), (nx, ny, nz, 0), centred
+  DevBuf<float4> tgt32;   // the same in FP32
+
+  // per-pass scratch
+  DevBuf<float4> rec32;
+  DevBuf<double4_32a> rec64;
+  DevBuf<float> part32;
+  DevBuf<double> part64;
+
+  // charges
+  int64_t nc = 0;
+  int n_rhs = 0;
+  int n_pos_sets = 0;
+  DevBuf<double4_32a> chg;     // n_rhs * nc: (y - center, q)
+  std::vector<double> q_host;  // n_rhs * nc
+
+  // solution state
+  DevBuf<double> u;  // n_rhs * 2n
+  DevBuf<double> b;  // n_rhs * 2n
+  DevBuf<double> e_dev;
+  DevBuf<double> phi_reac;
+  bool have_solution = false;
+  bipb_medium solved_medium{0, 0, 0};
+
+  Matvec32Variant mv32;
+  GmresWork* gw = nullptr;
+  KernelTimer timer;
+  uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves (recorded graphs go stale)
+  long long launches = 0;           // kernels launched on this handle (graph replays included)
+  bool recording = false;           // a CUDA graph is being recorded
+  long long recorded_launches = 0;  // kernels in the graph being recorded
+
+  template <typename T>
+  void grow(DevBuf<T>& buf, size_t count) {
+    if (buf.ensure(count)) ++alloc_gen;
+  }
+};
+
+Surface* checked(bipb_surface s);
+
+// Brackets one kernel launch with timing events when the timer is on.
+struct TimedLaunch {
+  Surface* s;
+  EventPair ev{0, nullptr, nullptr};
+  TimedLaunch(Surface* sf, int kind) : s(sf) {
+    if (!s->timer.on) return;
+    ev = EventPair{kind, s->timer.get(), s->timer.get()};
+    BIPB_CUDA(cudaEventRecord(ev.a, s->stream));
+  }
+  ~TimedLaunch() {
+    if (!ev.a) return;
+    if (cudaEventRecord(ev.b, s->stream) != cudaSuccess) return;
+    if (s->timer.capture)
+      s->timer.capture->push_back(ev);
+    else
+      s->timer.pending.push_back(ev);
+  }
+};
+
+// ---- kernels.cu: passes on device memory, all on s->stream ----
+// y = A u or A^T u for one vector (u, y: 2n doubles), `skip` (device int or
+// nullptr) makes every kernel return at once when it holds a nonzero value.
+void matvec(Surface* s, const bipb_medium& m, int precision, bool transpose, const double* u,
+            double* y, const int* skip);
+// b (2n) for right-hand side r
+void source_pass(Surface* s, const bipb_medium& m, int r, double* b);
+// reaction potential (nc, internal units) and E (kcal/mol, device scalar) for rhs r
+void reaction_pass(Surface* s, const bipb_medium& m, int r, const double* u, double* phi_reac,
+                   double* e_out);
+// energy row c (2n) for rhs r: E = 1/2 c.u
+void energy_row_pass(Surface* s, const bipb_medium& m, int r, double* c);
+// gradient passes for rhs r given u and the adjoint lam: dE/dq (nc), dE/dy (3 nc), internal units
+void grad_pass(Surface* s, const bipb_medium& m, int r, const double* u, const double* lam,
+               double* dq, double* dy);
+
+// ---- gmres.cu ----
+struct SolveResult {
+  int converged = 0, iters = 0, refine_steps = 0, matvecs64 = 0, matvecs32 = 0;
+  double rel_residual = 0.0;
+};
+// Solve op(A) x = rhs for one right-hand side; x holds the initial guess
+// (zero if !warm) and receives the solution.  op = A or A^T.
+SolveResult gmres_solve(Surface* s, const bipb_medium& m, const bipb_solve_params& p, bool transpose,
+                        const double* rhs, double* x, bool warm);
+void gmres_free(Surface* s);
+
+}  // namespace bipb

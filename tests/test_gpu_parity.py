@@ -1,0 +1,248 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (derivations in the design doc):
+* FP64 passes (mat-vec, transpose, source, reaction): 1e-12 relative to the
+  largest output (reordered FP64 sums over N <= 20480 terms).
+* FP32 mat-vec: 3e-6 in the 2-norm and 2e-5 of the largest output per
+  element (FP32 pair arithmetic with 2^-22 MUFU approximations, FP32 sums
+  over one source split, FP64 across splits).
+* Solves: energies and potentials within 1e-10 (FP64, both sides solved to
+  1e-12) and within 1e-7 (mixed, refined to 1e-8 ... 1e-10).
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bipb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_10044_gb300.build import build
+
+    build()
+    import paper_2312_10044_gb300 as b
+
+    b.load_library()
+    return b
+
+
+def _med(bipb, p):
+    return bipb.medium(p.eps_in, p.eps_out, p.kappa)
+
+
+def _ragged(level=3, drop=43, seed=6):
+    """A displaced surface whose size is not a multiple of any tile."""
+    p = synth.protein_like_problem(level=level, n_charges=7, seed=seed)
+    keep = np.ones(p.n, bool)
+    keep[np.random.default_rng(1).choice(p.n, drop, replace=False)] = False
+    p.centroids, p.normals, p.areas = p.centroids[keep], p.normals[keep], p.areas[keep]
+    return p
+
+
+PROBLEMS = {
+    "born_l2": lambda: synth.born_problem(level=2),
+    "ragged_l3": lambda: _ragged(3),
+    "kirkwood_l3": lambda: synth.kirkwood_problem(level=3),
+}
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+@pytest.mark.parametrize("transpose", [False, True])
+def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
+    p = PROBLEMS[name]()
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(3)
+    U = rng.standard_normal((2, 2 * p.n))
+    f = orc.matvec_t if transpose else orc.matvec
+    ref = np.stack([f(p.centroids, p.normals, p.areas, eps, p.kappa, u) for u in U])
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        for prec in (bipb.FP64, bipb.FP32):
+            yd = torch.full_like(ud, float("nan"))
+            s.matvec(ud, yd, precision=prec, transpose=transpose, med=_med(bipb, p))
+            y = yd.cpu().numpy()
+            assert np.all(np.isfinite(y))
+            scale = np.abs(ref).max()
+            if prec == bipb.FP64:
+                np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * scale)
+            else:
+                assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 3e-6
+                assert np.abs(y - ref).max() < 2e-5 * scale
+
+
+def test_matvec_is_deterministic(bipb):
+    p = _ragged(3)
+    u = _dev(np.random.default_rng(0).standard_normal(2 * p.n))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        for prec in (bipb.FP64, bipb.FP32):
+            a, b = torch.empty_like(u), torch.empty_like(u)
+            s.matvec(u, a, precision=prec)
+            s.matvec(u, b, precision=prec)
+            assert torch.equal(a, b)
+
+
+def test_two_triangle_surface(bipb, orc):
+    p = synth.born_problem(level=0)
+    c, n, a = p.centroids[:2], p.normals[:2], p.areas[:2]
+    u = np.array([0.3, -1.2, 0.7, 2.0])
+    ref = orc.matvec(c, n, a, 80.0, 0.1257, u)
+    with bipb.Surface(c, n, a) as s:
+        ud = _dev(u)
+        yd = torch.empty_like(ud)
+        s.matvec(ud, yd, precision=bipb.FP64)
+        np.testing.assert_allclose(yd.cpu().numpy(), ref, rtol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["ragged_l3", "kirkwood_l3"])
+def test_source_and_reaction_fp64(bipb, orc, name):
+    p = PROBLEMS[name]()
+    eps = p.eps_out / p.eps_in
+    b_ref = orc.source(p.centroids, p.normals, p.charge_pos, p.q[0], p.eps_in)
+    u = np.random.default_rng(5).standard_normal(2 * p.n)
+    e_ref, pr_ref = orc.energy(p.centroids, p.normals, p.areas, eps, p.kappa, p.charge_pos, p.q[0], u)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        bd = torch.full((2 * p.n,), float("nan"), dtype=torch.float64, device="cuda")
+        s.source(bd, med=_med(bipb, p))
+        np.testing.assert_allclose(bd.cpu().numpy(), b_ref, rtol=0, atol=1e-12 * np.abs(b_ref).max())
+        pr = torch.empty(p.nc, dtype=torch.float64, device="cuda")
+        e = torch.empty(1, dtype=torch.float64, device="cuda")
+        s.reaction(_dev(u), pr, e, med=_med(bipb, p))
+        np.testing.assert_allclose(pr.cpu().numpy(), pr_ref, rtol=0, atol=1e-12 * np.abs(pr_ref).max())
+        assert e.item() == pytest.approx(orc.KCAL * e_ref, rel=1e-11)
+
+
+def test_born_fp64_solve_matches_direct_solution(bipb, orc):
+    p = synth.born_problem(level=3)
+    ref = orc.solve(p, method="direct")
+    phi_ref, dphi_ref = ref.surface_potential()
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-12, precision=bipb.FP64)
+        assert info[0]["converged"] and info[0]["rel_residual"] <= 1e-12
+        e = s.energy()[0]
+        phi, dphi = s.surface_potential()
+    assert e == pytest.approx(ref.energy_kcal, rel=1e-10)
+    np.testing.assert_allclose(phi[0], phi_ref, rtol=1e-10)
+    np.testing.assert_allclose(dphi[0], dphi_ref, rtol=1e-10)
+
+
+def test_born_iteration_count_matches_oracle_gmres(bipb, orc):
+    p = synth.born_problem(level=3)
+    ref = orc.solve(p, method="gmres", tol=1e-8)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-8, precision=bipb.FP64)
+    assert abs(info[0]["iters"] - ref.info["iters"]) <= 1
+    assert info[0]["rel_residual"] <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_kirkwood_solve(bipb, orc, prec):
+    p = synth.kirkwood_problem(level=4)
+    ref = orc.solve(p, method="gmres", tol=1e-12)
+    phi_ref, dphi_ref = ref.surface_potential()
+    P = bipb.FP64 if prec == "fp64" else bipb.MIXED
+    tol = 1e-12 if prec == "fp64" else 1e-8
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=tol, precision=P)[0]
+        e = s.energy()[0]
+        phi, dphi = s.surface_potential()
+    assert info["converged"] and info["rel_residual"] <= tol
+    rt = 1e-10 if prec == "fp64" else 1e-7
+    assert e == pytest.approx(ref.energy_kcal, rel=rt)
+    assert np.linalg.norm(phi[0] - phi_ref) / np.linalg.norm(phi_ref) < rt
+    assert np.linalg.norm(dphi[0] - dphi_ref) / np.linalg.norm(dphi_ref) < rt
+    if prec == "mixed":
+        assert info["refine_steps"] >= 1 and info["matvecs32"] > info["matvecs64"]
+
+
+def test_multiple_charge_sets_match_single_solves(bipb):
+    base = synth.protein_like_problem(level=3, n_charges=20)
+    batch = synth.batched_charges(base, n_rhs=3, n_charges=20)
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.set_charges(batch.charge_pos, batch.q)
+        s.solve(tol=1e-11, precision=bipb.FP64)
+        e_all = s.energy()
+        phi_all, _ = s.surface_potential()
+        for r in range(3):
+            s.set_charges(batch.charge_pos[r], batch.q[r])
+            s.solve(tol=1e-11, precision=bipb.FP64)
+            assert s.energy()[0] == pytest.approx(e_all[r], rel=1e-9)
+            np.testing.assert_allclose(s.surface_potential()[0][0], phi_all[r], rtol=1e-8, atol=1e-9)
+
+
+def test_gradient_matches_oracle_adjoint(bipb, orc):
+    p = synth.kirkwood_problem(level=3, radius=10.0, n_charges=6, charge_radius=7.0)
+    e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="direct")
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-12, precision=bipb.FP64)
+        dq, dy = s.energy_grad(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-12,
+                               precision=bipb.FP64)
+    np.testing.assert_allclose(dq[0], dq_ref, rtol=1e-8)
+    np.testing.assert_allclose(dy[0], dy_ref, rtol=1e-7, atol=1e-8 * np.abs(dy_ref).max())
+
+
+def test_energy_before_solve_is_a_state_error(bipb):
+    p = synth.born_problem(level=1)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        with pytest.raises(bipb.BipbError) as ei:
+            s.energy()
+        assert ei.value.status == bipb.BIPB_ERR_STATE
+
+
+def test_iteration_cap_reports_not_converged(bipb):
+    p = synth.kirkwood_problem(level=3)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(tol=1e-12, max_iter=3, precision=bipb.FP64, raise_on_not_converged=False)[0]
+        assert not info["converged"] and info["iters"] == 3 and info["rel_residual"] > 1e-12
+        with pytest.raises(bipb.BipbError) as ei:
+            s.solve(tol=1e-12, max_iter=3, precision=bipb.FP64)
+        assert ei.value.status == bipb.BIPB_ERR_NOT_CONVERGED
+        assert np.isfinite(s.energy()[0])  # the best iterate is kept
+
+
+def test_warm_start_from_solution_needs_no_iterations(bipb):
+    p = synth.born_problem(level=2)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        s.solve(tol=1e-11, precision=bipb.FP64)
+        phi, dphi = s.surface_potential()
+        u = np.concatenate([phi[0], dphi[0]]) / bipb.KCAL
+        info = s.solve(tol=1e-9, precision=bipb.FP64, x0=u[None, :])[0]
+        assert info["iters"] == 0 and info["converged"]
+
+
+# ---------------------------------------------------------------- full-size sampled checks
+@pytest.mark.parametrize("cfg", ["kirkwood", "protein_like"])
+def test_full_size_matvec_sampled_rows(bipb, orc, cfg):
+    """The benchmark's mat-vec launch at full size, checked on sampled rows."""
+    p = synth.problem_by_name(cfg)
+    eps = p.eps_out / p.eps_in
+    u = np.random.default_rng(9).standard_normal(2 * p.n)
+    rows = np.sort(np.random.default_rng(10).choice(2 * p.n, 48, replace=False))
+    rows = np.concatenate([rows, [0, p.n - 1, p.n, 2 * p.n - 1]])
+    ref = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(u)
+        y64, y32 = torch.empty_like(ud), torch.empty_like(ud)
+        s.matvec(ud, y64, precision=bipb.FP64, med=_med(bipb, p))
+        s.matvec(ud, y32, precision=bipb.FP32, med=_med(bipb, p))
+        a64, a32 = y64.cpu().numpy(), y32.cpu().numpy()
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(a64[rows], ref, rtol=0, atol=1e-12 * scale)
+    assert np.abs(a32[rows] - ref).max() < 2e-5 * scale

@@ -99,6 +99,15 @@ def test_dense_matches_matrix_free(orc, small):
                                rtol=1e-13, atol=1e-13)
 
 
+def test_sampled_rows_match_full_matvec(orc, small):
+    p = small
+    eps = p.eps_out / p.eps_in
+    u = np.random.default_rng(8).standard_normal(2 * p.n)
+    full = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u)
+    rows = np.array([0, 5, p.n - 1, p.n, 2 * p.n - 1])
+    np.testing.assert_array_equal(orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows), full[rows])
+
+
 def test_dense_entries_brute_force(orc, small):
     """Every entry of A rebuilt pair by pair from the kernels (Eqs. 5-6)."""
     p = small
