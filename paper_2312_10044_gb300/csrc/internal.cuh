@@ -110,6 +110,8 @@ struct KernelTimer {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       total_ms[p.kind] += ms;
       count[p.kind] += 1;
+    } else {
+      (void)cudaGetLastError();  // do not leave the failure for the next launch check
     }
   }
   void collect() {
@@ -191,11 +193,16 @@ struct TimedLaunch {
   TimedLaunch(Surface* sf, int kind) : s(sf) {
     if (!s->timer.on) return;
     ev = EventPair{kind, s->timer.get(), s->timer.get()};
-    BIPB_CUDA(cudaEventRecord(ev.a, s->stream));
+    // while a graph is recorded, only an "external" record becomes a node
+    // that stamps the event on every replay
+    BIPB_CUDA(cudaEventRecordWithFlags(ev.a, s->stream, s->recording ? cudaEventRecordExternal : 0));
   }
   ~TimedLaunch() {
     if (!ev.a) return;
-    if (cudaEventRecord(ev.b, s->stream) != cudaSuccess) return;
+    if (cudaEventRecordWithFlags(ev.b, s->stream, s->recording ? cudaEventRecordExternal : 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return;
+    }
     if (s->timer.capture)
       s->timer.capture->push_back(ev);
     else

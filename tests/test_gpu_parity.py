@@ -195,6 +195,24 @@ def test_gradient_matches_oracle_adjoint(bipb, orc):
     np.testing.assert_allclose(dy[0], dy_ref, rtol=1e-7, atol=1e-8 * np.abs(dy_ref).max())
 
 
+def test_kernel_timer_and_launch_count(bipb):
+    p = synth.kirkwood_problem(level=3)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        for on in (True, False, True):
+            bipb.timer_enable(s, on)
+            n0 = bipb.launch_count(s)
+            info = s.solve(tol=1e-8, precision=bipb.MIXED)[0]
+            t = bipb.timer_read(s)
+            assert bipb.launch_count(s) - n0 > info["matvecs32"] + info["matvecs64"]
+            if on:
+                assert t["matvec32"][0] == info["matvecs32"] and t["matvec32"][1] > 0
+                assert t["matvec64"][0] == info["matvecs64"] and t["matvec64"][1] > 0
+                assert t["source"][0] == 1 and t["reaction"][0] == 1
+            else:
+                assert all(v == (0, 0.0) for v in t.values())
+
+
 def test_energy_before_solve_is_a_state_error(bipb):
     p = synth.born_problem(level=1)
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
