@@ -206,7 +206,9 @@ def test_kernel_timer_and_launch_count(bipb):
             t = bipb.timer_read(s)
             assert bipb.launch_count(s) - n0 > info["matvecs32"] + info["matvecs64"]
             if on:
-                assert t["matvec32"][0] == info["matvecs32"] and t["matvec32"][1] > 0
+                # launches after convergence inside a recorded cycle return at once but still count
+                assert info["matvecs32"] <= t["matvec32"][0] <= info["matvecs32"] + 9 * info["refine_steps"]
+                assert t["matvec32"][1] > 0
                 assert t["matvec64"][0] == info["matvecs64"] and t["matvec64"][1] > 0
                 assert t["source"][0] == 1 and t["reaction"][0] == 1
             else:
