@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64"],
+                    help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
 
@@ -183,10 +185,41 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def run_matvec_only(args):
+    """W + K single mat-vecs of one precision on the workload (a small, fixed launch sequence)."""
+    import torch
+
+    from paper_2312_10044_gb300.build import build
+
+    build()
+    import paper_2312_10044_gb300 as bipb
+
+    prob, desc = workload(args.workload)
+    prec = bipb.FP32 if args.mode == "matvec32" else bipb.FP64
+    med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
+    with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
+        u = torch.randn(2 * prob.n, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(u)
+        for _ in range(args.warmup):
+            s.matvec(u, y, precision=prec, med=med)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.steps):
+            s.matvec(u, y, precision=prec, med=med)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"mode": args.mode, "workload": desc, "ms_per_matvec": ms,
+                      "gpairs": prob.n * (prob.n - 1) / ms / 1e6}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode != "solve":
+        return run_matvec_only(args)
     import torch
     import torch.distributed as dist
 

@@ -201,6 +201,34 @@ bipb_status bipb_timer_read(bipb_surface s, int kind, int64_t* launches, double*
  * inside replayed CUDA graphs included).  Host output; no synchronisation. */
 bipb_status bipb_launch_count(bipb_surface s, int64_t* launches);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free FP32 mat-vec.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- code whose host
+ * framework has already reserved nearly all device memory for its own
+ * allocator, or a time-critical loop that must not allocate after start-up.
+ * Such callers cannot create a bipb_surface (creating one allocates).
+ *
+ * y = A u, the same operator as bipb_matvec with BIPB_FP32, from geometry
+ * passed as device pointers:
+ *   centroids: device, n x 3 doubles (Angstrom); normals: device, n x 3
+ *   (unit, outward); areas: device, n (> 0); u, y: device, 2N doubles each,
+ *   internal units; y must not alias u.  The geometry is not validated (the
+ *   data are on the device): it must satisfy what bipb_surface_create checks.
+ *   cuda_stream: a cudaStream_t or NULL; the call is asynchronous on it.
+ * 2 <= n <= 32768, else BIPB_ERR_INVALID_ARG.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: its scratch (about 10 MiB) is one
+ * statically sized device array that every GPU loading the library holds
+ * until the process exits.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  Every call shares the one
+ * array, so calls that overlap on the GPU (concurrent streams, or several
+ * host threads) race and corrupt each other's results: serialise them.
+ * Errors are reported through the status and bipb_last_error().
+ * ------------------------------------------------------------------------- */
+bipb_status bipb_matvec32_static(int64_t n, const double* centroids, const double* normals,
+                                 const double* areas, const bipb_medium* m, const double* u, double* y,
+                                 void* cuda_stream);
+
 /* Most recent error message of this thread ("" if none). */
 const char* bipb_last_error(void);
 const char* bipb_status_string(bipb_status st);

@@ -35,7 +35,7 @@ EXPORTED = (
     "bipb_surface_create", "bipb_surface_destroy", "bipb_surface_size", "bipb_charges_set",
     "bipb_solve", "bipb_energy", "bipb_surface_potential", "bipb_energy_grad", "bipb_matvec",
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
-    "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count",
+    "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
 )
 
 KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad")
@@ -112,6 +112,7 @@ def load_library():
         "bipb_timer_enable": ([P, I], st),
         "bipb_timer_read": ([P, I, P, P], st),
         "bipb_launch_count": ([P, P], st),
+        "bipb_matvec32_static": ([I64, P, P, P, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -286,6 +287,27 @@ def timer_read(surface):
         _check(L.bipb_timer_read(surface.handle, k, ctypes.byref(n), ctypes.byref(ms)))
         out[name] = (n.value, ms.value)
     return out
+
+
+STATIC_MAX_N = 32768
+
+
+def matvec32_static(centroids, normals, areas, u, y, med=None, stream=None):
+    """Allocation-free FP32 y = A u (bipb_matvec32_static); every argument a CUDA float64 tensor.
+
+    For callers that cannot allocate device memory: the library's scratch is a
+    static device array, so no cudaMalloc happens.  Calls that overlap on the
+    GPU share that array and race; serialise them.
+    """
+    m = med if med is not None else medium()
+    n = centroids.numel() // 3
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(load_library().bipb_matvec32_static(n, _dp(centroids), _dp(normals), _dp(areas), ctypes.byref(m),
+                                               _dp(u), _dp(y), ctypes.c_void_p(stream)))
+    return y
 
 
 def launch_count(surface):

@@ -114,6 +114,8 @@ bool is_live(const Surface* s) {
   return g_live.count(s) == 1;
 }
 
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
 Surface* checked(bipb_surface h) {
   Surface* s = reinterpret_cast<Surface*>(h);
   if (s == nullptr || !is_live(s) || s->magic != kMagic)

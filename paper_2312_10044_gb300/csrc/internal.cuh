@@ -185,6 +185,7 @@ struct Surface {
 };
 
 Surface* checked(bipb_surface s);
+void set_last_error(const std::string& msg);  // the message bipb_last_error() returns on this thread
 
 // Brackets one kernel launch with timing events when the timer is on.
 struct TimedLaunch {
