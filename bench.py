@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
+    ap.add_argument("--variant", type=int, default=-1, help="FP32 mat-vec variant for --mode matvec32")
     ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
@@ -198,6 +199,8 @@ def run_matvec_only(args):
     prec = bipb.FP32 if args.mode == "matvec32" else bipb.FP64
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
     with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
+        if args.variant >= 0:
+            s.set_variant(args.variant)
         u = torch.randn(2 * prob.n, dtype=torch.float64, device="cuda")
         y = torch.empty_like(u)
         for _ in range(args.warmup):
@@ -251,6 +254,8 @@ def main():
         e = s.energy()
         return info[0], e[0]
 
+    variant, mv_ms = s.autotune(bipb.medium(prob.eps_in, prob.eps_out, prob.kappa), reps=3)
+    log(f"autotune: FP32 mat-vec variant {variant}, {mv_ms:.4f} ms")
     for _ in range(args.warmup):
         info, e = step()
     log(f"warm-up: {info} E={e:.6f} kcal/mol")
@@ -369,7 +374,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": {"workload": desc, "n": n, "nc": nc, "tol": TOL, "restart": 10, "l2": "flushed",
-                           "parallelism": f"replicas{world}"},
+                           "parallelism": f"replicas{world}", "matvec32_variant": variant},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         line.update(extra)

@@ -197,6 +197,21 @@ bipb_status bipb_timer_enable(bipb_surface s, int on);
  * was turned on (host outputs; synchronises the handle's stream). */
 bipb_status bipb_timer_read(bipb_surface s, int kind, int64_t* launches, double* total_ms);
 
+/*
+ * Autotuner of the FP32 mat-vec tiling (threads per CTA, targets per thread,
+ * sources per shared-memory chunk): times every compiled variant, reps
+ * launches each, on this surface and medium, keeps the fastest for the
+ * handle, and returns its index (host, may be NULL) and its time per mat-vec
+ * in ms (host, may be NULL).  Synchronises the handle's stream.  Variants
+ * differ only in summation order, not in the operator.
+ */
+bipb_status bipb_autotune(bipb_surface s, const bipb_medium* m, int reps, int* variant,
+                          double* ms_per_matvec);
+
+/* Select an FP32 mat-vec variant by index, 0 <= variant < BIPB_MATVEC32_VARIANTS. */
+#define BIPB_MATVEC32_VARIANTS 7
+bipb_status bipb_matvec_variant(bipb_surface s, int variant);
+
 /* Number of CUDA kernels this handle has launched since creation (kernels
  * inside replayed CUDA graphs included).  Host output; no synchronisation. */
 bipb_status bipb_launch_count(bipb_surface s, int64_t* launches);

@@ -36,7 +36,9 @@ EXPORTED = (
     "bipb_solve", "bipb_energy", "bipb_surface_potential", "bipb_energy_grad", "bipb_matvec",
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
+    "bipb_autotune", "bipb_matvec_variant",
 )
+MATVEC32_VARIANTS = 7
 
 KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad")
 
@@ -113,6 +115,8 @@ def load_library():
         "bipb_timer_read": ([P, I, P, P], st),
         "bipb_launch_count": ([P, P], st),
         "bipb_matvec32_static": ([I64, P, P, P, P, P, P, P], st),
+        "bipb_autotune": ([P, P, I, P, P], st),
+        "bipb_matvec_variant": ([P, I], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -260,6 +264,17 @@ class Surface:
             raise ValueError("u and y must hold k * 2N values")
         _check(self._L.bipb_matvec(self._h, ctypes.byref(m), precision, int(transpose), n_vec, _dp(u), _dp(y)))
         return y
+
+    def autotune(self, med=None, reps=3):
+        """Pick the fastest FP32 mat-vec variant for this surface; returns (index, ms per mat-vec)."""
+        m = med if med is not None else medium()
+        v = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check(self._L.bipb_autotune(self._h, ctypes.byref(m), reps, ctypes.byref(v), ctypes.byref(ms)))
+        return v.value, ms.value
+
+    def set_variant(self, variant):
+        _check(self._L.bipb_matvec_variant(self._h, int(variant)))
 
     def source(self, b, med=None):
         m = med if med is not None else medium()

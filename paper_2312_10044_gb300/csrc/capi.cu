@@ -455,6 +455,26 @@ bipb_status bipb_timer_enable(bipb_surface h, int on) {
   });
 }
 
+bipb_status bipb_autotune(bipb_surface h, const bipb_medium* m, int reps, int* variant, double* ms_per_matvec) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    validate_medium(m);
+    BIPB_REQUIRE(reps >= 1 && reps <= 1000, "reps must lie in [1, 1000]");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    int v = autotune_matvec32(s, *m, reps, ms_per_matvec);
+    if (variant) *variant = v;
+  });
+}
+
+bipb_status bipb_matvec_variant(bipb_surface h, int variant) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(variant >= 0 && variant < kNumMv32Variants, "unknown FP32 mat-vec variant");
+    s->mv32_variant = variant;
+  });
+}
+
 bipb_status bipb_launch_count(bipb_surface h, int64_t* launches) {
   return guarded([&] {
     Surface* s = checked(h);

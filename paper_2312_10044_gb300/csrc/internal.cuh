@@ -60,22 +60,17 @@ struct DevBuf {
   ~DevBuf() { release(); }
 };
 
-// Tiling of one pair pass: targets split into tiles of nt*tpt, sources into
-// chunks of ch staged in shared memory, chunks grouped into splits.
+// Tiling of one pair pass: targets in tiles of nt*tpt, sources in n_splits
+// equal ranges (each CTA = one tile against one range).
 struct PassTiling {
   int n_tiles = 0;
-  int n_chunks = 0;  // source chunks (sources padded to n_chunks * ch)
   int n_splits = 0;
-  int chunks_per_split = 0;
 };
 
-// Kernel-variant selection for the FP32 mat-vec (the autotuned knob).
-struct Matvec32Variant {
-  int nt = 256;   // threads per CTA
-  int tpt = 2;    // targets per thread
-  int ch = 128;   // sources per shared-memory chunk
-  int waves = 8;  // target CTAs per SM-slot (sets the source split count)
-};
+// FP32 mat-vec kernel variants (threads per CTA, targets per thread,
+// sources per shared-memory chunk): 0 (256,2,128) 1 (256,1,128)
+// 2 (128,2,128) 3 (256,4,128) 4 (128,4,64) 5 (512,1,128) 6 (256,2,64).
+constexpr int kNumMv32Variants = 7;
 
 constexpr int kMaxRestart = 64;
 
@@ -170,7 +165,7 @@ struct Surface {
   bool have_solution = false;
   bipb_medium solved_medium{0, 0, 0};
 
-  Matvec32Variant mv32;
+  int mv32_variant = 0;  // index into the FP32 mat-vec variants (set by the autotuner)
   GmresWork* gw = nullptr;
   KernelTimer timer;
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves (recorded graphs go stale)
@@ -216,6 +211,9 @@ struct TimedLaunch {
 // nullptr) makes every kernel return at once when it holds a nonzero value.
 void matvec(Surface* s, const bipb_medium& m, int precision, bool transpose, const double* u,
             double* y, const int* skip);
+// Time every FP32 mat-vec variant on this surface (reps launches each) and
+// keep the fastest; returns its index and its time per mat-vec in best_ms.
+int autotune_matvec32(Surface* s, const bipb_medium& m, int reps, double* best_ms);
 // b (2n) for right-hand side r
 void source_pass(Surface* s, const bipb_medium& m, int r, double* b);
 // reaction potential (nc, internal units) and E (kcal/mol, device scalar) for rhs r

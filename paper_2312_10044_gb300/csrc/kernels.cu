@@ -230,11 +230,11 @@ struct GradPolicy {
 // ------------------------------------------------------------------ tiled driver
 // grid = (n_tiles, n_splits).  CTA (x, y) handles targets
 // [x*NT*TPT, (x+1)*NT*TPT) (thread t owns x*NT*TPT + k*NT + t, k < TPT)
-// against source chunks [y*cps, min((y+1)*cps, n_chunks)).
+// against sources [y*ns/S, (y+1)*ns/S) with S = n_splits, staged through
+// shared memory CH records at a time (the last chunk of a split may be short).
 template <class P, typename V4, int NT, int TPT, int CH>
-__global__ void __launch_bounds__(NT) k_tiled(typename P::Args a, int n_targets, int n_chunks,
-                                              int chunks_per_split, const V4* __restrict__ rec,
-                                              const int* __restrict__ skip) {
+__global__ void __launch_bounds__(NT) k_tiled(typename P::Args a, int n_targets, int n_sources, int n_splits,
+                                              const V4* __restrict__ rec, const int* __restrict__ skip) {
   __shared__ V4 sh[CH * P::RW];
   if (skipped(skip)) return;
   const int t0 = blockIdx.x * NT * TPT;
@@ -247,23 +247,30 @@ __global__ void __launch_bounds__(NT) k_tiled(typename P::Args a, int n_targets,
     P::load(a, min(idx[k], n_targets - 1), tg[k]);
     P::zero(acc[k]);
   }
-  const int c0 = blockIdx.y * chunks_per_split;
-  const int c1 = min(c0 + chunks_per_split, n_chunks);
-  for (int ch = c0; ch < c1; ++ch) {
+  const int s0 = (int)((int64_t)blockIdx.y * n_sources / n_splits);
+  const int s1 = (int)((int64_t)(blockIdx.y + 1) * n_sources / n_splits);
+  for (int j0 = s0; j0 < s1; j0 += CH) {
+    const int cnt = min(CH, s1 - j0);
     __syncthreads();
-    const V4* src = rec + (size_t)ch * CH * P::RW;
-    for (int q = threadIdx.x; q < CH * P::RW; q += NT) sh[q] = src[q];
+    const V4* src = rec + (size_t)j0 * P::RW;
+    for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
     __syncthreads();
-    const int j0 = ch * CH;
-    const bool diag = P::SELF && (j0 < t0 + NT * TPT) && (j0 + CH > t0);
+    const bool diag = P::SELF && (j0 < t0 + NT * TPT) && (j0 + cnt > t0);
     if (!diag) {
+      if (cnt == CH) {
 #pragma unroll 2
-      for (int jj = 0; jj < CH; ++jj) {
+        for (int jj = 0; jj < CH; ++jj) {
 #pragma unroll
-        for (int k = 0; k < TPT; ++k) P::template pair<false>(a, tg[k], sh + jj * P::RW, false, acc[k]);
+          for (int k = 0; k < TPT; ++k) P::template pair<false>(a, tg[k], sh + jj * P::RW, false, acc[k]);
+        }
+      } else {
+        for (int jj = 0; jj < cnt; ++jj) {
+#pragma unroll
+          for (int k = 0; k < TPT; ++k) P::template pair<false>(a, tg[k], sh + jj * P::RW, false, acc[k]);
+        }
       }
     } else {
-      for (int jj = 0; jj < CH; ++jj) {
+      for (int jj = 0; jj < cnt; ++jj) {
 #pragma unroll
         for (int k = 0; k < TPT; ++k)
           P::template pair<true>(a, tg[k], sh + jj * P::RW, j0 + jj == idx[k], acc[k]);
@@ -275,17 +282,27 @@ __global__ void __launch_bounds__(NT) k_tiled(typename P::Args a, int n_targets,
     if (idx[k] < n_targets) P::store(a, blockIdx.y, idx[k], acc[k]);
 }
 
-PassTiling make_tiling(int64_t n_targets, int64_t n_sources, int targets_per_cta, int ch, int num_sms,
-                       int waves) {
+// Source split count: every split gets the same number of sources (+-1), and
+// the CTA count fills whole waves of resident CTAs (slots = SMs x CTAs per SM)
+// as closely as possible, so that no SM idles while others finish a tail.
+PassTiling make_tiling(int64_t n_targets, int64_t n_sources, int targets_per_cta, int slots, int min_src) {
   PassTiling t;
   t.n_tiles = (int)((n_targets + targets_per_cta - 1) / targets_per_cta);
-  t.n_chunks = (int)((n_sources + ch - 1) / ch);
-  // enough CTAs for `waves` per SM, but at least 4 chunks per split
-  long want = (long)num_sms * waves;
-  int splits = (int)std::max<long>(1, (want + t.n_tiles - 1) / t.n_tiles);
-  splits = std::min(splits, std::max(1, t.n_chunks / 4));
-  t.chunks_per_split = (t.n_chunks + splits - 1) / splits;
-  t.n_splits = (t.n_chunks + t.chunks_per_split - 1) / t.chunks_per_split;
+  const int max_s = (int)std::max<int64_t>(1, std::min<int64_t>(n_sources / std::max(min_src, 1), 4096));
+  auto eff = [&](int sp) {
+    const long ctas = (long)t.n_tiles * sp;
+    const long waves = (ctas + slots - 1) / slots;
+    return (double)ctas / ((double)waves * slots);
+  };
+  double best = 0.0;
+  for (int sp = 1; sp <= max_s; ++sp) best = std::max(best, eff(sp));
+  int best_s = 1;
+  for (int sp = 1; sp <= max_s; ++sp)
+    if (eff(sp) >= 0.98 * best) {  // the fewest splits within 2 % of the best fill
+      best_s = sp;
+      break;
+    }
+  t.n_splits = best_s;
   return t;
 }
 
@@ -467,39 +484,51 @@ __global__ void k_charge_records(int nc, int nc_pad, const double4_32a* __restri
   rec[k] = k < nc ? chg[k] : make_double4_32a(kFar, kFar, kFar, 0.0);
 }
 
-// Launch of one tiled pass; returns the tiling used.
+// Resident CTAs per SM of one tiled-kernel instantiation (queried once).
 template <class P, typename V4, int NT, int TPT, int CH>
-PassTiling launch_tiled(Surface* s, int kind, const typename P::Args& a, int64_t n_targets, int64_t n_sources,
-                        const V4* rec, const int* skip, int waves) {
-  PassTiling tl = make_tiling(n_targets, n_sources, NT * TPT, CH, s->num_sms, waves);
-  dim3 grid(tl.n_tiles, tl.n_splits);
-  TimedLaunch tlaunch(s, kind);
-  k_tiled<P, V4, NT, TPT, CH><<<grid, NT, 0, s->stream>>>(a, (int)n_targets, tl.n_chunks,
-                                                          tl.chunks_per_split, rec, skip);
-  BIPB_LAUNCHED(s);
-  return tl;
+int tiled_occupancy() {
+  static int occ = [] {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tiled<P, V4, NT, TPT, CH>, NT, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      o = 1;
+    }
+    return std::max(o, 1);
+  }();
+  return occ;
 }
 
 template <class P, typename V4, int NT, int TPT, int CH>
-PassTiling plan_tiled(Surface* s, int64_t n_targets, int64_t n_sources, int waves) {
-  return make_tiling(n_targets, n_sources, NT * TPT, CH, s->num_sms, waves);
+PassTiling plan_tiled(Surface* s, int64_t n_targets, int64_t n_sources, int min_src) {
+  return make_tiling(n_targets, n_sources, NT * TPT, s->num_sms * tiled_occupancy<P, V4, NT, TPT, CH>(), min_src);
+}
+
+// Launch of one tiled pass with a tiling from plan_tiled.
+template <class P, typename V4, int NT, int TPT, int CH>
+void launch_tiled(Surface* s, int kind, const PassTiling& tl, const typename P::Args& a, int64_t n_targets,
+                  int64_t n_sources, const V4* rec, const int* skip) {
+  dim3 grid(tl.n_tiles, tl.n_splits);
+  TimedLaunch tlaunch(s, kind);
+  k_tiled<P, V4, NT, TPT, CH><<<grid, NT, 0, s->stream>>>(a, (int)n_targets, (int)n_sources, tl.n_splits, rec,
+                                                          skip);
+  BIPB_LAUNCHED(s);
 }
 
 // FP32 forward / transpose mat-vec variants (the autotuner picks one).
 template <bool TRANS, int NT, int TPT, int CH>
 void run_matvec32(Surface* s, const PairConst<float>& c, const double* u, double* y, double dphi,
-                  double dpsi, const int* skip, int waves) {
+                  double dpsi, const int* skip) {
   const int n = (int)s->n;
   using P = MatvecPolicy<float, TRANS>;
-  PassTiling tl = plan_tiled<P, float4, NT, TPT, CH>(s, n, n, waves);
-  const int n_pad = tl.n_chunks * CH;
+  PassTiling tl = plan_tiled<P, float4, NT, TPT, CH>(s, n, n, CH);
+  const int n_pad = n;
   s->grow(s->rec32, (size_t)2 * n_pad);
   s->grow(s->part32, (size_t)tl.n_splits * 2 * n);
   k_pack<float4, float><<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(
       n, n_pad, TRANS, s->geo64.p, s->nrm64.p, u, s->rec32.p, skip);
   BIPB_LAUNCHED(s);
   typename P::Args a{s->tgt32.p, s->rec32.p, s->part32.p, n, c};
-  launch_tiled<P, float4, NT, TPT, CH>(s, TRANS ? kTMv32T : kTMv32, a, n, n, s->rec32.p, skip, waves);
+  launch_tiled<P, float4, NT, TPT, CH>(s, TRANS ? kTMv32T : kTMv32, tl, a, n, n, s->rec32.p, skip);
   k_reduce_matvec<float><<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(
       n, tl.n_splits, s->part32.p, u, y, dphi, dpsi, TRANS ? s->geo64.p : nullptr, skip);
   BIPB_LAUNCHED(s);
@@ -511,15 +540,15 @@ void run_matvec64(Surface* s, const PairConst<double>& c, const double* u, doubl
   constexpr int NT = 128, TPT = 2, CH = 64;
   const int n = (int)s->n;
   using P = MatvecPolicy<double, TRANS>;
-  PassTiling tl = plan_tiled<P, double4_32a, NT, TPT, CH>(s, n, n, 4);
-  const int n_pad = tl.n_chunks * CH;
+  PassTiling tl = plan_tiled<P, double4_32a, NT, TPT, CH>(s, n, n, CH);
+  const int n_pad = n;
   s->grow(s->rec64, (size_t)2 * n_pad);
   s->grow(s->part64, (size_t)tl.n_splits * 2 * n);
   k_pack<double4_32a, double><<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(
       n, n_pad, TRANS, s->geo64.p, s->nrm64.p, u, s->rec64.p, skip);
   BIPB_LAUNCHED(s);
   typename P::Args a{s->tgt64.p, s->rec64.p, s->part64.p, n, c};
-  launch_tiled<P, double4_32a, NT, TPT, CH>(s, TRANS ? kTMv64T : kTMv64, a, n, n, s->rec64.p, skip, 4);
+  launch_tiled<P, double4_32a, NT, TPT, CH>(s, TRANS ? kTMv64T : kTMv64, tl, a, n, n, s->rec64.p, skip);
   k_reduce_matvec<double><<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(
       n, tl.n_splits, s->part64.p, u, y, dphi, dpsi, TRANS ? s->geo64.p : nullptr, skip);
   BIPB_LAUNCHED(s);
@@ -540,38 +569,86 @@ void matvec(Surface* s, const bipb_medium& m, int precision, bool transpose, con
     return;
   }
   PairConst<float> c = pair_const<float>(m);
-  const Matvec32Variant& v = s->mv32;
-  const int w = v.waves;
-#define BIPB_MV32(NT_, TPT_, CH_)                                                      \
-  if (v.nt == NT_ && v.tpt == TPT_ && v.ch == CH_) {                                   \
-    if (transpose)                                                                     \
-      run_matvec32<true, NT_, TPT_, CH_>(s, c, u, y, dphi, dpsi, skip, w);             \
-    else                                                                               \
-      run_matvec32<false, NT_, TPT_, CH_>(s, c, u, y, dphi, dpsi, skip, w);            \
-    return;                                                                            \
-  }
-  BIPB_MV32(256, 2, 128)
-  BIPB_MV32(256, 1, 128)
-  BIPB_MV32(128, 2, 128)
-  BIPB_MV32(256, 4, 128)
-  BIPB_MV32(128, 4, 64)
+  switch (s->mv32_variant) {
+#define BIPB_MV32(I_, NT_, TPT_, CH_)                                    \
+  case I_:                                                               \
+    if (transpose)                                                       \
+      run_matvec32<true, NT_, TPT_, CH_>(s, c, u, y, dphi, dpsi, skip);  \
+    else                                                                 \
+      run_matvec32<false, NT_, TPT_, CH_>(s, c, u, y, dphi, dpsi, skip); \
+    return;
+    BIPB_MV32(0, 256, 2, 128)
+    BIPB_MV32(1, 256, 1, 128)
+    BIPB_MV32(2, 128, 2, 128)
+    BIPB_MV32(3, 256, 4, 128)
+    BIPB_MV32(4, 128, 4, 64)
+    BIPB_MV32(5, 512, 1, 128)
+    BIPB_MV32(6, 256, 2, 64)
 #undef BIPB_MV32
-  throw Error(BIPB_ERR_INVALID_ARG, "unknown FP32 mat-vec variant");
+    default:
+      throw Error(BIPB_ERR_INVALID_ARG, "unknown FP32 mat-vec variant");
+  }
+}
+
+namespace {
+__global__ void k_fill_test_vector(int len, double* u) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) u[i] = 0.5 + 0.25 * sin(0.37 * i) + (i & 7) * 0.01;
+}
+}  // namespace
+
+int autotune_matvec32(Surface* s, const bipb_medium& m, int reps, double* best_ms) {
+  const int len = (int)(2 * s->n);
+  DevBuf<double> u, y;
+  u.ensure(len);
+  y.ensure(len);
+  k_fill_test_vector<<<blocks_for(len, 256), 256, 0, s->stream>>>(len, u.p);
+  BIPB_LAUNCHED(s);
+  cudaEvent_t a, b;
+  BIPB_CUDA(cudaEventCreate(&a));
+  BIPB_CUDA(cudaEventCreate(&b));
+  const bool timer_was_on = s->timer.on;
+  s->timer.on = false;
+  int best = s->mv32_variant;
+  double best_t = 1e300;
+  try {
+    for (int v = 0; v < kNumMv32Variants; ++v) {
+      s->mv32_variant = v;
+      matvec(s, m, BIPB_FP32, false, u.p, y.p, nullptr);  // warm-up (and buffer growth)
+      BIPB_CUDA(cudaEventRecord(a, s->stream));
+      for (int r = 0; r < reps; ++r) matvec(s, m, BIPB_FP32, false, u.p, y.p, nullptr);
+      BIPB_CUDA(cudaEventRecord(b, s->stream));
+      BIPB_CUDA(cudaEventSynchronize(b));
+      float ms = 0.f;
+      BIPB_CUDA(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_t) best_t = ms, best = v;
+    }
+  } catch (...) {
+    s->timer.on = timer_was_on;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    throw;
+  }
+  s->timer.on = timer_was_on;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  s->mv32_variant = best;
+  if (best_ms) *best_ms = best_t / reps;
+  return best;
 }
 
 void source_pass(Surface* s, const bipb_medium& m, int r, double* b) {
   constexpr int NT = 128, TPT = 1, CH = 64;
   const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<SourcePolicy, double4_32a, NT, TPT, CH>(s, n, nc, 4);
-  // charge records of rhs r, padded to whole chunks with zero charges far away
-  const int nc_pad = tl.n_chunks * CH;
+  PassTiling tl = plan_tiled<SourcePolicy, double4_32a, NT, TPT, CH>(s, n, nc, CH);
+  const int nc_pad = nc;
   s->grow(s->rec64, (size_t)nc_pad);
   k_charge_records<<<blocks_for(nc_pad, 256), 256, 0, s->stream>>>(nc, nc_pad, s->chg.p + (size_t)r * nc,
                                                                    s->rec64.p);
   BIPB_LAUNCHED(s);
   s->grow(s->part64, (size_t)tl.n_splits * 2 * n);
   SourcePolicy::Args a{s->geo64.p, s->nrm64.p, s->rec64.p, s->part64.p, n};
-  launch_tiled<SourcePolicy, double4_32a, NT, TPT, CH>(s, kTSource, a, n, nc, s->rec64.p, nullptr, 4);
+  launch_tiled<SourcePolicy, double4_32a, NT, TPT, CH>(s, kTSource, tl, a, n, nc, s->rec64.p, nullptr);
   k_reduce_source<<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(n, tl.n_splits, s->part64.p,
                                                                  kInv4Pi / m.eps_in, b);
   BIPB_LAUNCHED(s);
@@ -581,15 +658,15 @@ void reaction_pass(Surface* s, const bipb_medium& m, int r, const double* u, dou
                    double* e_out) {
   constexpr int NT = 128, TPT = 1, CH = 64;
   const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<ReactionPolicy, double4_32a, NT, TPT, CH>(s, nc, n, 4);
-  const int n_pad = tl.n_chunks * CH;
+  PassTiling tl = plan_tiled<ReactionPolicy, double4_32a, NT, TPT, CH>(s, nc, n, CH);
+  const int n_pad = n;
   s->grow(s->rec64, (size_t)2 * n_pad);
   k_pack<double4_32a, double><<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(
       n, n_pad, false, s->geo64.p, s->nrm64.p, u, s->rec64.p, nullptr);
   BIPB_LAUNCHED(s);
   s->grow(s->part64, (size_t)tl.n_splits * nc);
   ReactionPolicy::Args a{s->chg.p + (size_t)r * nc, s->rec64.p, s->part64.p, nc, pair_const<double>(m)};
-  launch_tiled<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kTReaction, a, nc, n, s->rec64.p, nullptr, 4);
+  launch_tiled<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kTReaction, tl, a, nc, n, s->rec64.p, nullptr);
   k_reduce_reaction<<<1, 1024, 0, s->stream>>>(nc, tl.n_splits, s->part64.p, s->chg.p + (size_t)r * nc,
                                                phi_reac, e_out);
   BIPB_LAUNCHED(s);
@@ -598,15 +675,15 @@ void reaction_pass(Surface* s, const bipb_medium& m, int r, const double* u, dou
 void energy_row_pass(Surface* s, const bipb_medium& m, int r, double* c) {
   constexpr int NT = 128, TPT = 1, CH = 64;
   const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, n, nc, 4);
-  const int nc_pad = tl.n_chunks * CH;
+  PassTiling tl = plan_tiled<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, n, nc, CH);
+  const int nc_pad = nc;
   s->grow(s->rec64, (size_t)nc_pad);
   k_charge_records<<<blocks_for(nc_pad, 256), 256, 0, s->stream>>>(nc, nc_pad, s->chg.p + (size_t)r * nc,
                                                                    s->rec64.p);
   BIPB_LAUNCHED(s);
   s->grow(s->part64, (size_t)tl.n_splits * 2 * n);
   EnergyRowPolicy::Args a{s->geo64.p, s->nrm64.p, s->part64.p, n, pair_const<double>(m)};
-  launch_tiled<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kTRow, a, n, nc, s->rec64.p, nullptr, 4);
+  launch_tiled<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kTRow, tl, a, n, nc, s->rec64.p, nullptr);
   k_energy_row_reduce<<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(n, tl.n_splits, s->part64.p,
                                                                       s->geo64.p, c);
   BIPB_LAUNCHED(s);
@@ -616,15 +693,15 @@ void grad_pass(Surface* s, const bipb_medium& m, int r, const double* u, const d
                double* dy) {
   constexpr int NT = 128, TPT = 1, CH = 32;
   const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<GradPolicy, double4_32a, NT, TPT, CH>(s, nc, n, 4);
-  const int n_pad = tl.n_chunks * CH;
+  PassTiling tl = plan_tiled<GradPolicy, double4_32a, NT, TPT, CH>(s, nc, n, CH);
+  const int n_pad = n;
   s->grow(s->rec64, (size_t)3 * n_pad);
   k_pack_grad<<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(n, n_pad, s->geo64.p, s->nrm64.p, u, lam,
                                                              s->rec64.p);
   BIPB_LAUNCHED(s);
   s->grow(s->part64, (size_t)tl.n_splits * 8 * nc);
   GradPolicy::Args a{s->chg.p + (size_t)r * nc, s->rec64.p, s->part64.p, nc, pair_const<double>(m)};
-  launch_tiled<GradPolicy, double4_32a, NT, TPT, CH>(s, kTGrad, a, nc, n, s->rec64.p, nullptr, 4);
+  launch_tiled<GradPolicy, double4_32a, NT, TPT, CH>(s, kTGrad, tl, a, nc, n, s->rec64.p, nullptr);
   k_reduce_grad<<<blocks_for(nc, 256), 256, 0, s->stream>>>(nc, tl.n_splits, s->part64.p,
                                                             s->chg.p + (size_t)r * nc, 1.0 / m.eps_in,
                                                             dq, dy);

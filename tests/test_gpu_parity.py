@@ -67,7 +67,9 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
     ref = np.stack([f(p.centroids, p.normals, p.areas, eps, p.kappa, u) for u in U])
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
-        for prec in (bipb.FP64, bipb.FP32):
+        cases = [(bipb.FP64, 0)] + [(bipb.FP32, v) for v in range(bipb.MATVEC32_VARIANTS)]
+        for prec, variant in cases:
+            s.set_variant(variant)
             yd = torch.full_like(ud, float("nan"))
             s.matvec(ud, yd, precision=prec, transpose=transpose, med=_med(bipb, p))
             y = yd.cpu().numpy()
@@ -76,8 +78,15 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
             if prec == bipb.FP64:
                 np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * scale)
             else:
-                assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 3e-6
-                assert np.abs(y - ref).max() < 2e-5 * scale
+                assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 3e-6, variant
+                assert np.abs(y - ref).max() < 2e-5 * scale, variant
+
+
+def test_autotune_picks_a_variant(bipb):
+    p = synth.kirkwood_problem(level=3)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        v, ms = s.autotune(reps=2)
+        assert 0 <= v < bipb.MATVEC32_VARIANTS and ms > 0
 
 
 def test_matvec_is_deterministic(bipb):
