@@ -100,6 +100,21 @@ typedef struct {
 bipb_status bipb_surface_create(int64_t n, const double* centroids, const double* normals,
                                 const double* areas, void* cuda_stream, bipb_surface* out);
 
+/*
+ * Create one handle for n_surf surfaces of uneven size, solved together
+ * (one system per surface: every pass and every GMRES step covers all of
+ * them in one launch).  Surface k: n_tri[k] triangles, centroids[k] (n x 3),
+ * normals[k] (n x 3), areas[k] (n), all host, validated as in
+ * bipb_surface_create.  Charges come through bipb_charges_set_batch.
+ * Batched vectors (bipb_matvec with n_vec = 1, bipb_source, bipb_reaction,
+ * bipb_surface_potential) hold the surfaces back to back, surface k's
+ * 2 n_tri[k] unknowns [phi_k; psi_k] after those of surfaces 0 .. k-1.
+ * The paper solves one molecule at a time; this batching is an extension.
+ */
+bipb_status bipb_surface_create_batch(int n_surf, const int64_t* n_tri, const double* const* centroids,
+                                      const double* const* normals, const double* const* areas,
+                                      void* cuda_stream, bipb_surface* out);
+
 /* Free every device allocation of the handle; the handle value becomes invalid. */
 bipb_status bipb_surface_destroy(bipb_surface s);
 
@@ -117,6 +132,15 @@ bipb_status bipb_charges_set(bipb_surface s, int64_t nc, const double* pos, int 
                              int n_rhs, const double* q);
 
 /*
+ * Charges of a batch handle: surface k gets nc[k] charges at pos[k]
+ * (host, nc[k] x 3, Angstrom) with values q[k] (host, nc[k], e).
+ * Charge-indexed outputs (bipb_reaction, bipb_energy_grad) list them surface
+ * by surface.
+ */
+bipb_status bipb_charges_set_batch(bipb_surface s, const int64_t* nc, const double* const* pos,
+                                   const double* const* q);
+
+/*
  * Solve A u = b for every configuration (GMRES, Sec. 2.2.2; Eqs. 5-6), where
  * b = [S1; S2] of the charges (Eq. for S1, S2).  info: host array of n_rhs
  * (may be NULL).  Returns BIPB_ERR_NOT_CONVERGED if any configuration missed
@@ -124,7 +148,8 @@ bipb_status bipb_charges_set(bipb_surface s, int64_t nc, const double* pos, int 
  */
 bipb_status bipb_solve(bipb_surface s, const bipb_solve_params* p, bipb_solve_info* info);
 
-/* Solvation energy per configuration, kcal/mol, host array of n_rhs (Eq. for E_sol). */
+/* Solvation energy per configuration (or per surface of a batch handle),
+ * kcal/mol, host array (Eq. for E_sol). */
 bipb_status bipb_energy(bipb_surface s, double* e_sol);
 
 /*
@@ -152,6 +177,8 @@ bipb_status bipb_energy_grad(bipb_surface s, const bipb_solve_params* p, double*
 /*
  * y = A u (transpose = 0) or y = A^T u (transpose = 1) for n_vec vectors.
  *   u, y: device, n_vec x 2N doubles, internal units; y must not alias u.
+ *   For a batch handle n_vec must be 1 and u, y are batched vectors (the
+ *   block-diagonal operator of all surfaces).
  *   precision: BIPB_FP64 or BIPB_FP32 (FP32 pair arithmetic per source tile,
  *   FP64 sums across tiles and for the diagonal).
  */

@@ -36,7 +36,7 @@ EXPORTED = (
     "bipb_solve", "bipb_energy", "bipb_surface_potential", "bipb_energy_grad", "bipb_matvec",
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
-    "bipb_autotune", "bipb_matvec_variant",
+    "bipb_autotune", "bipb_matvec_variant", "bipb_surface_create_batch", "bipb_charges_set_batch",
 )
 MATVEC32_VARIANTS = 7
 
@@ -116,6 +116,8 @@ def load_library():
         "bipb_launch_count": ([P, P], st),
         "bipb_matvec32_static": ([I64, P, P, P, P, P, P, P], st),
         "bipb_autotune": ([P, P, I, P, P], st),
+        "bipb_surface_create_batch": ([I, P, P, P, P, P, P], st),
+        "bipb_charges_set_batch": ([P, P, P, P], st),
         "bipb_matvec_variant": ([P, I], st),
     }
     for name, (args, res) in sig.items():
@@ -152,6 +154,17 @@ def _dp(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _stream(stream):
+    if stream is not None:
+        return stream
+    try:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+    except Exception:  # pragma: no cover - torch is optional for the host API
+        return 0
+
+
 def medium(eps_in=1.0, eps_out=80.0, kappa=0.1257):
     return bipb_medium(eps_in, eps_out, kappa)
 
@@ -173,20 +186,24 @@ class Surface:
         a = _host(areas, (-1,))
         if not (c.shape[0] == n.shape[0] == a.shape[0]):
             raise ValueError("centroids, normals and areas differ in length")
-        if stream is None:
-            try:
-                import torch
-
-                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
-            except Exception:  # pragma: no cover - torch is optional for the host API
-                stream = 0
         h = ctypes.c_void_p()
-        _check(self._L.bipb_surface_create(c.shape[0], _hp(c), _hp(n), _hp(a), ctypes.c_void_p(stream),
+        _check(self._L.bipb_surface_create(c.shape[0], _hp(c), _hp(n), _hp(a), ctypes.c_void_p(_stream(stream)),
                                            ctypes.byref(h)))
         self._h = h
         self.n = c.shape[0]
+        self.sizes = [self.n]
         self.nc = 0
         self.n_rhs = 0
+        self.n_charges_total = 0
+
+    @property
+    def n_systems(self):
+        return self.n_rhs
+
+    @property
+    def unknowns(self):
+        """Length of the batched unknown vector of the systems bipb_solve works on."""
+        return 2 * self.n * self.n_rhs
 
     # -------------------------------------------------------------- lifetime
     def close(self):
@@ -222,15 +239,16 @@ class Surface:
         pos = _host(pos, (n_pos, nc, 3))
         _check(self._L.bipb_charges_set(self._h, nc, _hp(pos), n_pos, n_rhs, _hp(q)))
         self.nc, self.n_rhs = nc, n_rhs
+        self.n_charges_total = nc * n_rhs
 
     # -------------------------------------------------------------- solve / outputs
     def solve(self, params=None, x0=None, raise_on_not_converged=True, **kw):
         p = params if params is not None else solve_params(**kw)
         x0h = None
         if x0 is not None:
-            x0h = _host(x0, (self.n_rhs, 2 * self.n))
+            x0h = _host(x0, (self.unknowns,))
             p.x0 = x0h.ctypes.data
-        info = (bipb_solve_info * self.n_rhs)()
+        info = (bipb_solve_info * self.n_systems)()
         st = self._L.bipb_solve(self._h, ctypes.byref(p), info)
         p.x0 = None
         if st != BIPB_OK and not (st == BIPB_ERR_NOT_CONVERGED and not raise_on_not_converged):
@@ -238,22 +256,29 @@ class Surface:
         return [i.as_dict() for i in info]
 
     def energy(self):
-        e = np.zeros(self.n_rhs)
+        e = np.zeros(self.n_systems)
         _check(self._L.bipb_energy(self._h, _hp(e)))
         return e
 
     def surface_potential(self):
-        phi = np.zeros((self.n_rhs, self.n))
-        dphi = np.zeros((self.n_rhs, self.n))
+        """(phi, dphi/dnu): (n_rhs, N) arrays, or lists per surface for a batch handle."""
+        phi = np.zeros(self.unknowns // 2)
+        dphi = np.zeros(self.unknowns // 2)
         _check(self._L.bipb_surface_potential(self._h, _hp(phi), _hp(dphi)))
-        return phi, dphi
+        return self._split_elems(phi), self._split_elems(dphi)
+
+    def _split_elems(self, v):
+        return v.reshape(self.n_rhs, self.n)
 
     def energy_grad(self, params=None, **kw):
         p = params if params is not None else solve_params(**kw)
-        dq = np.zeros((self.n_rhs, self.nc))
-        dy = np.zeros((self.n_rhs, self.nc, 3))
+        dq = np.zeros(self.n_charges_total)
+        dy = np.zeros((self.n_charges_total, 3))
         _check(self._L.bipb_energy_grad(self._h, ctypes.byref(p), _hp(dq), _hp(dy)))
-        return dq, dy
+        return self._split_charges(dq), self._split_charges(dy)
+
+    def _split_charges(self, v):
+        return v.reshape((self.n_rhs, self.nc) + v.shape[1:])
 
     # -------------------------------------------------------------- device passes
     def matvec(self, u, y, precision=FP64, transpose=False, med=None):
@@ -302,6 +327,60 @@ def timer_read(surface):
         _check(L.bipb_timer_read(surface.handle, k, ctypes.byref(n), ctypes.byref(ms)))
         out[name] = (n.value, ms.value)
     return out
+
+
+class BatchSurface(Surface):
+    """Several surfaces of uneven size in one handle (bipb_surface_create_batch).
+
+    One system per surface; every pass and every GMRES step covers all of
+    them in one launch.  Outputs are lists with one entry per surface.
+    """
+
+    def __init__(self, surfaces, stream=None):
+        self._L = load_library()
+        geo = [(_host(c, (-1, 3)), _host(n, (-1, 3)), _host(a, (-1,))) for c, n, a in surfaces]
+        k = len(geo)
+        ns = (ctypes.c_int64 * k)(*[g[0].shape[0] for g in geo])
+        arr = lambda i: (ctypes.c_void_p * k)(*[g[i].ctypes.data for g in geo])  # noqa: E731
+        h = ctypes.c_void_p()
+        _check(self._L.bipb_surface_create_batch(k, ns, arr(0), arr(1), arr(2), ctypes.c_void_p(_stream(stream)),
+                                                 ctypes.byref(h)))
+        self._h = h
+        self._geo = geo
+        self.sizes = [g[0].shape[0] for g in geo]
+        self.n = sum(self.sizes)
+        self.nc = 0
+        self.n_rhs = 0
+        self.ncs = []
+        self.n_charges_total = 0
+
+    @property
+    def n_systems(self):
+        return len(self.sizes)
+
+    @property
+    def unknowns(self):
+        return 2 * self.n
+
+    def set_charges(self, charges):
+        """charges: one (pos (Nc_k, 3), q (Nc_k,)) pair per surface."""
+        if len(charges) != self.n_systems:
+            raise ValueError("one charge set per surface")
+        pos = [_host(p, (-1, 3)) for p, _ in charges]
+        q = [_host(v, (-1,)) for _, v in charges]
+        k = self.n_systems
+        nc = (ctypes.c_int64 * k)(*[v.shape[0] for v in q])
+        _check(self._L.bipb_charges_set_batch(self._h, nc, (ctypes.c_void_p * k)(*[p.ctypes.data for p in pos]),
+                                              (ctypes.c_void_p * k)(*[v.ctypes.data for v in q])))
+        self.ncs = [v.shape[0] for v in q]
+        self.n_charges_total = sum(self.ncs)
+        self.n_rhs = k
+
+    def _split_elems(self, v):
+        return np.split(v, np.cumsum(self.sizes)[:-1])
+
+    def _split_charges(self, v):
+        return np.split(v, np.cumsum(self.ncs)[:-1])
 
 
 STATIC_MAX_N = 32768

@@ -150,6 +150,146 @@ int64_t bipb_surface_size(bipb_surface h) {
   return (s && is_live(s)) ? s->n : 0;
 }
 
+namespace {
+
+struct PartIn {
+  int64_t n;
+  const double *c, *nrm, *area;
+};
+
+// Validate one surface and append it (centred on its own mean centroid) to
+// the host geometry arrays.
+void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::vector<float4>& tgt32) {
+  BIPB_REQUIRE(P.n >= 2, "need at least 2 triangles per surface");
+  BIPB_REQUIRE(P.c && P.nrm && P.area, "NULL input array");
+  double c[3] = {0, 0, 0};
+  for (int64_t i = 0; i < P.n; ++i) {
+    BIPB_REQUIRE(finite3(P.c + 3 * i), "non-finite centroid");
+    BIPB_REQUIRE(finite3(P.nrm + 3 * i), "non-finite normal");
+    BIPB_REQUIRE(std::isfinite(P.area[i]) && P.area[i] > 0, "areas must be finite and > 0");
+    const double* v = P.nrm + 3 * i;
+    double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    BIPB_REQUIRE(std::fabs(len - 1.0) <= 1e-6, "normals must have unit length (within 1e-6)");
+    for (int k = 0; k < 3; ++k) c[k] += P.c[3 * i + k];
+  }
+  for (int k = 0; k < 3; ++k) c[k] /= (double)P.n;
+  // duplicates: exact in FP64, and after centring and rounding to FP32
+  std::unordered_set<std::array<uint64_t, 3>, KeyHash> seen64, seen32;
+  seen64.reserve(2 * P.n);
+  seen32.reserve(2 * P.n);
+  for (int64_t i = 0; i < P.n; ++i) {
+    BIPB_REQUIRE(seen64.insert(key_of(P.c + 3 * i)).second, "two centroids coincide");
+    double f[3];
+    for (int k = 0; k < 3; ++k) f[k] = (double)(float)(P.c[3 * i + k] - c[k]);
+    BIPB_REQUIRE(seen32.insert(key_of(f)).second, "two centroids coincide after rounding to FP32");
+  }
+  s->part_off.push_back((int)s->n);
+  s->part_n.push_back((int)P.n);
+  for (int k = 0; k < 3; ++k) s->part_center.push_back(c[k]);
+  for (int64_t i = 0; i < P.n; ++i) {
+    const double* p = P.c + 3 * i;
+    const double* v = P.nrm + 3 * i;
+    double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double4_32a g = make_double4_32a(p[0] - c[0], p[1] - c[1], p[2] - c[2], P.area[i]);
+    double4_32a nv = make_double4_32a(v[0] / len, v[1] / len, v[2] / len, 0.0);
+    tgt.push_back(g);
+    tgt.push_back(nv);
+    tgt32.push_back(make_float4((float)g.x, (float)g.y, (float)g.z, (float)g.w));
+    tgt32.push_back(make_float4((float)nv.x, (float)nv.y, (float)nv.z, 0.f));
+  }
+  s->n += P.n;
+}
+
+bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream, bool batch) {
+  auto* s = new Surface();
+  try {
+    std::vector<double4_32a> tgt;
+    std::vector<float4> tgt32;
+    int64_t total = 0;
+    for (auto& P : parts) total += std::max<int64_t>(P.n, 0);
+    BIPB_REQUIRE(total <= (int64_t)1 << 28, "at most 2^28 triangles");
+    tgt.reserve(2 * total);
+    tgt32.reserve(2 * total);
+    for (auto& P : parts) add_part(s, P, tgt, tgt32);
+    s->batch = batch;
+    int dev = 0;
+    BIPB_CUDA(cudaGetDevice(&dev));
+    s->device = dev;
+    BIPB_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    s->user_stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    BIPB_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
+    BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
+    s->tgt64.ensure(tgt.size());
+    s->tgt32.ensure(tgt32.size());
+    BIPB_CUDA(cudaMemcpy(s->tgt64.p, tgt.data(), tgt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+    BIPB_CUDA(cudaMemcpy(s->tgt32.p, tgt32.data(), tgt32.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    s->magic = kMagic;
+  } catch (...) {
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    delete s;
+    throw;
+  }
+  register_handle(s);
+  return reinterpret_cast<bipb_surface>(s);
+}
+
+// Charge records of one system, centred like its surface; rejects charges on a centroid.
+void append_charges(Surface* s, int part, int64_t nc, const double* pos, const double* q,
+                    const std::unordered_set<std::array<uint64_t, 3>, KeyHash>& cent, std::vector<double4_32a>& rec) {
+  const double* c = &s->part_center[3 * part];
+  for (int64_t k = 0; k < nc; ++k) {
+    BIPB_REQUIRE(finite3(pos + 3 * k), "non-finite charge position");
+    BIPB_REQUIRE(std::isfinite(q[k]), "non-finite charge");
+    double p[3] = {pos[3 * k] - c[0], pos[3 * k + 1] - c[1], pos[3 * k + 2] - c[2]};
+    BIPB_REQUIRE(cent.find(key_of(p)) == cent.end(), "a charge sits on a centroid");
+    rec.push_back(make_double4_32a(p[0], p[1], p[2], q[k]));
+  }
+}
+
+// Centred centroid keys of one surface (to reject charges that sit on a centroid).
+std::unordered_set<std::array<uint64_t, 3>, KeyHash> centroid_keys(Surface* s, int part) {
+  const int n = s->part_n[part];
+  std::vector<double4_32a> g(2 * (size_t)n);
+  BIPB_CUDA(cudaMemcpy(g.data(), s->tgt64.p + 2 * (size_t)s->part_off[part], g.size() * sizeof(double4_32a),
+                       cudaMemcpyDeviceToHost));
+  std::unordered_set<std::array<uint64_t, 3>, KeyHash> cent;
+  cent.reserve(2 * n);
+  for (int i = 0; i < n; ++i) {
+    double p[3] = {g[2 * i].x, g[2 * i].y, g[2 * i].z};
+    cent.insert(key_of(p));
+  }
+  return cent;
+}
+
+void store_charges(Surface* s, const std::vector<double4_32a>& rec, SysLayout lay) {
+  s->grow(s->chg, rec.size());
+  BIPB_CUDA(cudaMemcpy(s->chg.p, rec.data(), rec.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+  s->lay = std::move(lay);
+  s->n_rhs = s->lay.K;
+  s->have_solution = false;
+}
+
+// Layout of n_vec vectors for the device mat-vec entry point: replicas of a
+// single surface, or (n_vec = 1) the surfaces of a batch handle.
+SysLayout matvec_layout(Surface* s, int n_vec) {
+  std::vector<int> go, n, co, nc;
+  if (s->batch) {
+    for (size_t k = 0; k < s->part_n.size(); ++k) go.push_back(s->part_off[k]), n.push_back(s->part_n[k]);
+  } else {
+    for (int v = 0; v < n_vec; ++v) go.push_back(0), n.push_back((int)s->n);
+  }
+  co.assign(go.size(), 0);
+  nc.assign(go.size(), 0);
+  return make_layout(go, n, co, nc);
+}
+
+void require_charges(Surface* s) { BIPB_REQUIRE(s->n_rhs > 0, "no charges set"); }
+
+}  // namespace
+
 bipb_status bipb_surface_create(int64_t n, const double* centroids, const double* normals, const double* areas,
                                 void* cuda_stream, bipb_surface* out) {
   return guarded([&] {
@@ -157,75 +297,21 @@ bipb_status bipb_surface_create(int64_t n, const double* centroids, const double
     *out = nullptr;
     BIPB_REQUIRE(n >= 2, "need at least 2 triangles");
     BIPB_REQUIRE(n <= (int64_t)1 << 28, "at most 2^28 triangles");
-    BIPB_REQUIRE(centroids && normals && areas, "NULL input array");
-    std::vector<double> nrm(3 * n);
-    double c[3] = {0, 0, 0};
-    for (int64_t i = 0; i < n; ++i) {
-      BIPB_REQUIRE(finite3(centroids + 3 * i), "non-finite centroid");
-      BIPB_REQUIRE(finite3(normals + 3 * i), "non-finite normal");
-      BIPB_REQUIRE(std::isfinite(areas[i]) && areas[i] > 0, "areas must be finite and > 0");
-      const double* v = normals + 3 * i;
-      double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-      BIPB_REQUIRE(std::fabs(len - 1.0) <= 1e-6, "normals must have unit length (within 1e-6)");
-      for (int k = 0; k < 3; ++k) {
-        nrm[3 * i + k] = v[k] / len;
-        c[k] += centroids[3 * i + k];
-      }
-    }
-    for (int k = 0; k < 3; ++k) c[k] /= (double)n;
-    // duplicates: exact in FP64, and after centring and rounding to FP32
-    {
-      std::unordered_set<std::array<uint64_t, 3>, KeyHash> seen64, seen32;
-      seen64.reserve(2 * n);
-      seen32.reserve(2 * n);
-      for (int64_t i = 0; i < n; ++i) {
-        BIPB_REQUIRE(seen64.insert(key_of(centroids + 3 * i)).second, "two centroids coincide");
-        double f[3];
-        for (int k = 0; k < 3; ++k) f[k] = (double)(float)(centroids[3 * i + k] - c[k]);
-        BIPB_REQUIRE(seen32.insert(key_of(f)).second, "two centroids coincide after rounding to FP32");
-      }
-    }
-    int dev = 0;
-    BIPB_CUDA(cudaGetDevice(&dev));
-    auto* s = new Surface();
-    try {
-      s->device = dev;
-      BIPB_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev));
-      s->user_stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-      BIPB_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
-      BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
-      BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
-      s->n = n;
-      std::memcpy(s->center, c, sizeof(c));
-      std::vector<double4_32a> geo(n), nv(n), tgt(2 * n);
-      std::vector<float4> tgt32(2 * n);
-      for (int64_t i = 0; i < n; ++i) {
-        const double* p = centroids + 3 * i;
-        geo[i] = make_double4_32a(p[0] - c[0], p[1] - c[1], p[2] - c[2], areas[i]);
-        nv[i] = make_double4_32a(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2], 0.0);
-        tgt[2 * i] = geo[i];
-        tgt[2 * i + 1] = nv[i];
-        tgt32[2 * i] = make_float4((float)geo[i].x, (float)geo[i].y, (float)geo[i].z, (float)areas[i]);
-        tgt32[2 * i + 1] = make_float4((float)nv[i].x, (float)nv[i].y, (float)nv[i].z, 0.f);
-      }
-      s->geo64.ensure(n);
-      s->nrm64.ensure(n);
-      s->tgt64.ensure(2 * n);
-      s->tgt32.ensure(2 * n);
-      BIPB_CUDA(cudaMemcpy(s->geo64.p, geo.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
-      BIPB_CUDA(cudaMemcpy(s->nrm64.p, nv.data(), n * sizeof(double4_32a), cudaMemcpyHostToDevice));
-      BIPB_CUDA(cudaMemcpy(s->tgt64.p, tgt.data(), 2 * n * sizeof(double4_32a), cudaMemcpyHostToDevice));
-      BIPB_CUDA(cudaMemcpy(s->tgt32.p, tgt32.data(), 2 * n * sizeof(float4), cudaMemcpyHostToDevice));
-      s->magic = kMagic;
-    } catch (...) {
-      if (s->stream) cudaStreamDestroy(s->stream);
-      if (s->ev_in) cudaEventDestroy(s->ev_in);
-      if (s->ev_out) cudaEventDestroy(s->ev_out);
-      delete s;
-      throw;
-    }
-    register_handle(s);
-    *out = reinterpret_cast<bipb_surface>(s);
+    *out = create_surface({PartIn{n, centroids, normals, areas}}, cuda_stream, false);
+  });
+}
+
+bipb_status bipb_surface_create_batch(int n_surf, const int64_t* n_tri, const double* const* centroids,
+                                      const double* const* normals, const double* const* areas, void* cuda_stream,
+                                      bipb_surface* out) {
+  return guarded([&] {
+    BIPB_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    BIPB_REQUIRE(n_surf >= 1 && n_surf <= 4096, "n_surf must lie in [1, 4096]");
+    BIPB_REQUIRE(n_tri && centroids && normals && areas, "NULL input array");
+    std::vector<PartIn> parts;
+    for (int k = 0; k < n_surf; ++k) parts.push_back(PartIn{n_tri[k], centroids[k], normals[k], areas[k]});
+    *out = create_surface(parts, cuda_stream, true);
   });
 }
 
@@ -248,39 +334,49 @@ bipb_status bipb_charges_set(bipb_surface h, int64_t nc, const double* pos, int 
                              const double* q) {
   return guarded([&] {
     Surface* s = checked(h);
+    BIPB_REQUIRE(!s->batch, "a batch handle takes its charges through bipb_charges_set_batch");
     BIPB_REQUIRE(nc >= 1 && nc <= (int64_t)1 << 26, "nc must lie in [1, 2^26]");
     BIPB_REQUIRE(n_rhs >= 1 && n_rhs <= 4096, "n_rhs must lie in [1, 4096]");
     BIPB_REQUIRE(n_pos_sets == 1 || n_pos_sets == n_rhs, "n_pos_sets must be 1 or n_rhs");
     BIPB_REQUIRE(pos && q, "NULL input array");
-    // centroid keys in the caller's frame, to reject charges sitting on a centroid
-    std::vector<double4_32a> geo(s->n);
+    BIPB_REQUIRE((int64_t)n_rhs * nc <= (int64_t)1 << 28, "too many charges in total");
     DeviceGuard dg(s->device);
-    BIPB_CUDA(cudaMemcpy(geo.data(), s->geo64.p, s->n * sizeof(double4_32a), cudaMemcpyDeviceToHost));
-    std::unordered_set<std::array<uint64_t, 3>, KeyHash> cent;
-    cent.reserve(2 * s->n);
-    for (int64_t i = 0; i < s->n; ++i) {
-      double p[3] = {geo[i].x, geo[i].y, geo[i].z};
-      cent.insert(key_of(p));
-    }
-    std::vector<double4_32a> rec((size_t)n_rhs * nc);
+    auto cent = centroid_keys(s, 0);
+    std::vector<double4_32a> rec;
+    rec.reserve((size_t)n_rhs * nc);
+    std::vector<int> go(n_rhs, 0), n(n_rhs, (int)s->n), co(n_rhs), ncv(n_rhs, (int)nc);
     for (int r = 0; r < n_rhs; ++r) {
-      const double* pr = pos + (size_t)(n_pos_sets == 1 ? 0 : r) * nc * 3;
-      for (int64_t k = 0; k < nc; ++k) {
-        BIPB_REQUIRE(finite3(pr + 3 * k), "non-finite charge position");
-        double qk = q[(size_t)r * nc + k];
-        BIPB_REQUIRE(std::isfinite(qk), "non-finite charge");
-        double p[3] = {pr[3 * k] - s->center[0], pr[3 * k + 1] - s->center[1], pr[3 * k + 2] - s->center[2]};
-        BIPB_REQUIRE(cent.find(key_of(p)) == cent.end(), "a charge sits on a centroid");
-        rec[(size_t)r * nc + k] = make_double4_32a(p[0], p[1], p[2], qk);
-      }
+      co[r] = (int)(r * nc);
+      append_charges(s, 0, nc, pos + (size_t)(n_pos_sets == 1 ? 0 : r) * nc * 3, q + (size_t)r * nc, cent, rec);
     }
-    s->grow(s->chg, rec.size());
-    BIPB_CUDA(cudaMemcpy(s->chg.p, rec.data(), rec.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
-    s->q_host.assign(q, q + (size_t)n_rhs * nc);
     s->nc = nc;
-    s->n_rhs = n_rhs;
     s->n_pos_sets = n_pos_sets;
-    s->have_solution = false;
+    store_charges(s, rec, make_layout(go, n, co, ncv));
+  });
+}
+
+bipb_status bipb_charges_set_batch(bipb_surface h, const int64_t* nc, const double* const* pos,
+                                   const double* const* q) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(s->batch, "bipb_charges_set_batch needs a batch handle");
+    BIPB_REQUIRE(nc && pos && q, "NULL input array");
+    const int K = (int)s->part_n.size();
+    DeviceGuard dg(s->device);
+    std::vector<double4_32a> rec;
+    std::vector<int> co(K), ncv(K);
+    for (int k = 0; k < K; ++k) {
+      BIPB_REQUIRE(nc[k] >= 1 && nc[k] <= (int64_t)1 << 26, "every surface needs 1 .. 2^26 charges");
+      BIPB_REQUIRE(pos[k] && q[k], "NULL charge array");
+      co[k] = (int)rec.size();
+      ncv[k] = (int)nc[k];
+      auto cent = centroid_keys(s, k);
+      append_charges(s, k, nc[k], pos[k], q[k], cent, rec);
+      BIPB_REQUIRE(rec.size() <= ((size_t)1 << 28), "too many charges in total");
+    }
+    s->nc = 0;
+    s->n_pos_sets = 0;
+    store_charges(s, rec, make_layout(s->part_off, s->part_n, co, ncv));
   });
 }
 
@@ -289,10 +385,10 @@ bipb_status bipb_source(bipb_surface h, const bipb_medium* m, double* b) {
     Surface* s = checked(h);
     validate_medium(m);
     BIPB_REQUIRE(b != nullptr, "b is NULL");
-    BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+    require_charges(s);
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    for (int r = 0; r < s->n_rhs; ++r) source_pass(s, *m, r, b + (size_t)r * 2 * s->n);
+    source_pass(s, s->lay, *m, b);
   });
 }
 
@@ -302,13 +398,13 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
     Surface* s = checked(h);
     validate_medium(m);
     BIPB_REQUIRE(precision == BIPB_FP64 || precision == BIPB_FP32, "precision must be FP64 or FP32");
-    BIPB_REQUIRE(n_vec >= 1, "n_vec must be >= 1");
+    BIPB_REQUIRE(n_vec >= 1 && n_vec <= 4096, "n_vec must lie in [1, 4096]");
+    BIPB_REQUIRE(!s->batch || n_vec == 1, "a batch handle takes one batched vector (n_vec = 1)");
     BIPB_REQUIRE(u && y, "NULL vector");
     BIPB_REQUIRE(u != y, "y must not alias u");
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    const size_t len = 2 * (size_t)s->n;
-    for (int v = 0; v < n_vec; ++v) matvec(s, *m, precision, transpose != 0, u + v * len, y + v * len, nullptr);
+    matvec(s, matvec_layout(s, n_vec), *m, precision, transpose != 0, u, y, nullptr, 0);
   });
 }
 
@@ -318,12 +414,10 @@ bipb_status bipb_reaction(bipb_surface h, const bipb_medium* m, const double* u,
     Surface* s = checked(h);
     validate_medium(m);
     BIPB_REQUIRE(u != nullptr, "u is NULL");
-    BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+    require_charges(s);
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    for (int r = 0; r < s->n_rhs; ++r)
-      reaction_pass(s, *m, r, u + (size_t)r * 2 * s->n, phi_reac ? phi_reac + (size_t)r * s->nc : nullptr,
-                    e_sol ? e_sol + r : nullptr);
+    reaction_pass(s, s->lay, *m, u, phi_reac, e_sol);
   });
 }
 
@@ -333,31 +427,29 @@ bipb_status bipb_solve(bipb_surface h, const bipb_solve_params* p, bipb_solve_in
     auto t0 = std::chrono::steady_clock::now();
     Surface* s = checked(h);
     validate_params(p);
-    BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+    require_charges(s);
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    const size_t len = 2 * (size_t)s->n;
-    s->grow(s->u, s->n_rhs * len);
-    s->grow(s->b, s->n_rhs * len);
-    s->grow(s->e_dev, s->n_rhs);
+    const SysLayout& L = s->lay;
+    s->grow(s->u, L.len);
+    s->grow(s->b, L.len);
+    s->grow(s->e_dev, L.K);
     if (p->x0) {
-      for (size_t i = 0; i < s->n_rhs * len; ++i) BIPB_REQUIRE(std::isfinite(p->x0[i]), "non-finite x0");
-      BIPB_CUDA(cudaMemcpyAsync(s->u.p, p->x0, s->n_rhs * len * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      for (int64_t i = 0; i < L.len; ++i) BIPB_REQUIRE(std::isfinite(p->x0[i]), "non-finite x0");
+      BIPB_CUDA(cudaMemcpyAsync(s->u.p, p->x0, L.len * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     }
     s->have_solution = false;
-    std::vector<SolveResult> res(s->n_rhs);
-    for (int r = 0; r < s->n_rhs; ++r) {
-      source_pass(s, p->medium, r, s->b.p + r * len);
-      res[r] = gmres_solve(s, p->medium, *p, false, s->b.p + r * len, s->u.p + r * len, p->x0 != nullptr);
-      reaction_pass(s, p->medium, r, s->u.p + r * len, nullptr, s->e_dev.p + r);
-      if (!res[r].converged) st = BIPB_ERR_NOT_CONVERGED;
-    }
+    source_pass(s, L, p->medium, s->b.p);
+    std::vector<SolveResult> res = gmres_solve(s, L, p->medium, *p, false, s->b.p, s->u.p, p->x0 != nullptr);
+    reaction_pass(s, L, p->medium, s->u.p, nullptr, s->e_dev.p);
+    for (auto& r : res)
+      if (!r.converged) st = BIPB_ERR_NOT_CONVERGED;
     BIPB_CUDA(cudaStreamSynchronize(s->stream));
     s->have_solution = true;
     s->solved_medium = p->medium;
     double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) {
-      for (int r = 0; r < s->n_rhs; ++r) {
+      for (int r = 0; r < L.K; ++r) {
         info[r].converged = res[r].converged;
         info[r].iters = res[r].iters;
         info[r].refine_steps = res[r].refine_steps;
@@ -380,7 +472,7 @@ bipb_status bipb_energy(bipb_surface h, double* e_sol) {
     BIPB_REQUIRE(e_sol != nullptr, "e_sol is NULL");
     if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
     DeviceGuard dg(s->device);
-    BIPB_CUDA(cudaMemcpyAsync(e_sol, s->e_dev.p, s->n_rhs * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaMemcpyAsync(e_sol, s->e_dev.p, s->lay.K * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     BIPB_CUDA(cudaStreamSynchronize(s->stream));
   });
 }
@@ -391,15 +483,19 @@ bipb_status bipb_surface_potential(bipb_surface h, double* phi, double* dphi_dn)
     BIPB_REQUIRE(phi != nullptr, "phi is NULL");
     if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
     DeviceGuard dg(s->device);
-    const size_t n = s->n, len = 2 * n;
-    std::vector<double> u(s->n_rhs * len);
+    const SysLayout& L = s->lay;
+    std::vector<double> u(L.len);
     BIPB_CUDA(cudaMemcpyAsync(u.data(), s->u.p, u.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     BIPB_CUDA(cudaStreamSynchronize(s->stream));
-    for (int r = 0; r < s->n_rhs; ++r)
+    size_t out = 0;
+    for (int k = 0; k < L.K; ++k) {
+      const size_t n = L.n[k], v = L.vec_off[k];
       for (size_t i = 0; i < n; ++i) {
-        phi[r * n + i] = kKcal * u[r * len + i];
-        if (dphi_dn) dphi_dn[r * n + i] = kKcal * u[r * len + n + i];
+        phi[out + i] = kKcal * u[v + i];
+        if (dphi_dn) dphi_dn[out + i] = kKcal * u[v + n + i];
       }
+      out += n;
+    }
   });
 }
 
@@ -415,44 +511,34 @@ bipb_status bipb_energy_grad(bipb_surface h, const bipb_solve_params* p, double*
                  "params.medium differs from the medium of the last solve");
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    const size_t len = 2 * (size_t)s->n, nc = s->nc;
+    const SysLayout& L = s->lay;
+    size_t n_chg = 0;
+    for (int k = 0; k < L.K; ++k) n_chg += L.nc[k];
     DevBuf<double> c, lam, dq, dy;
-    c.ensure(len);
-    lam.ensure(len);
-    dq.ensure(nc);
-    dy.ensure(3 * nc);
-    std::vector<double> hq(nc), hy(3 * nc);
+    c.ensure(L.len);
+    lam.ensure(L.len);
+    dq.ensure(n_chg);
+    dy.ensure(3 * n_chg);
     bipb_solve_params pa = *p;
     pa.x0 = nullptr;
-    for (int r = 0; r < s->n_rhs; ++r) {
-      energy_row_pass(s, m, r, c.p);
-      SolveResult res = gmres_solve(s, m, pa, true, c.p, lam.p, false);
-      if (!res.converged) st = BIPB_ERR_NOT_CONVERGED;
-      grad_pass(s, m, r, s->u.p + r * len, lam.p, dq.p, dy.p);
-      BIPB_CUDA(cudaMemcpyAsync(hq.data(), dq.p, nc * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-      BIPB_CUDA(cudaMemcpyAsync(hy.data(), dy.p, 3 * nc * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-      BIPB_CUDA(cudaStreamSynchronize(s->stream));
-      for (size_t k = 0; k < nc; ++k) {
-        if (dE_dq) dE_dq[r * nc + k] = kKcal * hq[k];
-        if (dE_dpos)
-          for (int a = 0; a < 3; ++a) dE_dpos[(r * nc + k) * 3 + a] = kKcal * hy[3 * k + a];
-      }
+    energy_row_pass(s, L, m, c.p);
+    std::vector<SolveResult> res = gmres_solve(s, L, m, pa, true, c.p, lam.p, false);
+    for (auto& r : res)
+      if (!r.converged) st = BIPB_ERR_NOT_CONVERGED;
+    grad_pass(s, L, m, s->u.p, lam.p, dq.p, dy.p);
+    std::vector<double> hq(n_chg), hy(3 * n_chg);
+    BIPB_CUDA(cudaMemcpyAsync(hq.data(), dq.p, n_chg * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaMemcpyAsync(hy.data(), dy.p, 3 * n_chg * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    for (size_t k = 0; k < n_chg; ++k) {
+      if (dE_dq) dE_dq[k] = kKcal * hq[k];
+      if (dE_dpos)
+        for (int a = 0; a < 3; ++a) dE_dpos[3 * k + a] = kKcal * hy[3 * k + a];
     }
   });
   if (rc != BIPB_OK) return rc;
   if (st != BIPB_OK) g_last_error = "an adjoint solve did not reach tol within max_iter";
   return st;
-}
-
-bipb_status bipb_timer_enable(bipb_surface h, int on) {
-  return guarded([&] {
-    Surface* s = checked(h);
-    DeviceGuard dg(s->device);
-    BIPB_CUDA(cudaStreamSynchronize(s->stream));
-    s->timer.collect();
-    s->timer.reset();
-    s->timer.on = on != 0;
-  });
 }
 
 bipb_status bipb_autotune(bipb_surface h, const bipb_medium* m, int reps, int* variant, double* ms_per_matvec) {
@@ -462,7 +548,8 @@ bipb_status bipb_autotune(bipb_surface h, const bipb_medium* m, int reps, int* v
     BIPB_REQUIRE(reps >= 1 && reps <= 1000, "reps must lie in [1, 1000]");
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    int v = autotune_matvec32(s, *m, reps, ms_per_matvec);
+    const SysLayout L = s->n_rhs > 0 ? s->lay : matvec_layout(s, 1);
+    int v = autotune_matvec32(s, L, *m, reps, ms_per_matvec);
     if (variant) *variant = v;
   });
 }
@@ -480,6 +567,17 @@ bipb_status bipb_launch_count(bipb_surface h, int64_t* launches) {
     Surface* s = checked(h);
     BIPB_REQUIRE(launches != nullptr, "launches is NULL");
     *launches = s->launches;
+  });
+}
+
+bipb_status bipb_timer_enable(bipb_surface h, int on) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    DeviceGuard dg(s->device);
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    s->timer.collect();
+    s->timer.reset();
+    s->timer.on = on != 0;
   });
 }
 

@@ -1,22 +1,27 @@
 // Device-resident restarted GMRES (Saad & Schultz; the Krylov solver of
-// Sec. 2.2.2) and mixed-precision iterative refinement.
+// Sec. 2.2.2) over a batch of independent systems, and mixed-precision
+// iterative refinement.
 //
 // Unlike the paper's GPU pipeline (Sec. 2.4), which copies x and y across
 // PCIe and runs the Arnoldi process on the host every iteration, every step
 // here stays on the device: mat-vec, classical Gram-Schmidt with one
 // re-orthogonalisation (CGS2, the same Krylov basis as modified Gram-Schmidt
 // in exact arithmetic, but as matrix-vector shaped passes), Givens rotations
-// and the convergence test.  The host reads one small status record per
-// restart cycle.  One cycle (m Arnoldi steps, the least-squares update and
-// the restart vector) is recorded once as a CUDA graph and replayed.
+// and the convergence test.  K systems (right-hand sides of one surface, or
+// surfaces of uneven size) advance together: one Krylov vector is the
+// concatenation of the K systems' vectors, every kernel covers all of them,
+// and a system that has converged skips its share.  The host reads one small
+// status record per system per restart cycle.  One cycle (m Arnoldi steps,
+// the least-squares update and the restart vector) is recorded once as a
+// CUDA graph and replayed.
 //
 // Restart vector: after k steps the residual of the new iterate is
 // r = V_{k+1} Q^T (g_k e_{k+1}) (Q the product of the Givens rotations), so
 // the next cycle starts from it without another mat-vec; the true residual
-// b - A x is computed once when the recurrence reports convergence.
+// b - A x is computed when the recurrence reports convergence.
 #include <algorithm>
-#include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <map>
 
 #include "internal.cuh"
@@ -28,19 +33,21 @@ namespace {
 constexpr int kBS = 256;
 
 struct DevState {
-  int k;        // Arnoldi steps done in this cycle
-  int skip;     // nonzero: the rest of the cycle does nothing
-  int conv;     // recurrence residual <= tol
-  int stop;     // iteration cap reached
-  int iters;    // total Arnoldi steps
+  int k;       // Arnoldi steps done in this cycle
+  int skip;    // nonzero: the rest of the cycle does nothing for this system
+  int conv;    // recurrence residual <= tol
+  int stop;    // iteration cap reached
+  int iters;   // Arnoldi steps in this call
   int max_iter;
   int m;
-  int pad;
+  int active;  // the system takes part in this call
   double tol;    // relative to bnorm
-  double bnorm;  // ||rhs||
+  double bnorm;  // norm of the right-hand side of this call
   double beta;   // norm of the current cycle's start residual
   double est;    // latest |g_k| / bnorm
 };
+constexpr int kStateInts = (int)(sizeof(DevState) / sizeof(int));
+static_assert(offsetof(DevState, skip) == sizeof(int), "skip must be the second int");
 
 __device__ double block_sum(double v) {
   __shared__ double red[kBS / 32];
@@ -57,178 +64,212 @@ __device__ double block_sum(double v) {
   return t;  // valid in thread 0
 }
 
-// part[blockIdx.x * (m+1) + i] = sum over this block's range of V_i . w, i <= j
-__global__ void k_dots(int len, int j, int m1, const double* __restrict__ V, const double* __restrict__ w,
-                       double* __restrict__ part, const DevState* st) {
-  if (st->skip) return;
+// Block table: blk[b] = {system, start, end, first block of the system},
+// sysb[k] = {first block, end block, 0, 0}.  Every block covers one
+// contiguous range of one system's unknowns.
+
+// part[b * m1 + i] = V_i . w over block b's range, i <= j
+__global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V, const double* __restrict__ w,
+                       double* __restrict__ part, const DevState* st, const int4* __restrict__ blk) {
+  const int4 B = blk[blockIdx.x];
+  if (st[B.x].skip) return;
   for (int i = 0; i <= j; ++i) {
     const double* v = V + (size_t)i * len;
     double acc = 0.0;
-    for (int x = blockIdx.x * kBS + threadIdx.x; x < len; x += gridDim.x * kBS) acc += v[x] * w[x];
+    for (int x = B.y + threadIdx.x; x < B.z; x += kBS) acc += v[x] * w[x];
     acc = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x * m1 + i] = acc;
+    if (threadIdx.x == 0) part[(size_t)blockIdx.x * m1 + i] = acc;
   }
 }
 
-// h_i = sum_b part[b][i]; w -= sum_i h_i V_i; H[:, j] (+)= h
-__global__ void k_orth(int len, int j, int m1, int nblk, const double* __restrict__ V, double* __restrict__ w,
-                       const double* __restrict__ part, double* __restrict__ H, int accumulate,
-                       const DevState* st) {
-  if (st->skip) return;
+// h_i = sum over the system's blocks of part[.][i]; w -= sum_i h_i V_i; H[:, j] (+)= h
+__global__ void k_orth(int j, int m, int64_t len, const double* __restrict__ V, double* __restrict__ w,
+                       const double* __restrict__ part, double* __restrict__ H, int accumulate, const DevState* st,
+                       const int4* __restrict__ blk, const int4* __restrict__ sysb) {
+  const int4 B = blk[blockIdx.x];
+  if (st[B.x].skip) return;
+  const int m1 = m + 1;
+  const int4 S = sysb[B.x];
   __shared__ double h[kMaxRestart + 1];
   for (int i = threadIdx.x; i <= j; i += kBS) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[b * m1 + i];
+    for (int b = S.x; b < S.y; ++b) s += part[(size_t)b * m1 + i];
     h[i] = s;
   }
   __syncthreads();
-  if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i <= j; i += kBS) H[(size_t)j * m1 + i] = accumulate ? H[(size_t)j * m1 + i] + h[i] : h[i];
-  for (int x = blockIdx.x * kBS + threadIdx.x; x < len; x += gridDim.x * kBS) {
+  if ((int)blockIdx.x == S.x) {
+    double* Hs = H + (size_t)B.x * m1 * m + (size_t)j * m1;
+    for (int i = threadIdx.x; i <= j; i += kBS) Hs[i] = accumulate ? Hs[i] + h[i] : h[i];
+  }
+  for (int x = B.y + threadIdx.x; x < B.z; x += kBS) {
     double acc = w[x];
     for (int i = 0; i <= j; ++i) acc -= h[i] * V[(size_t)i * len + x];
     w[x] = acc;
   }
 }
 
-__global__ void k_sumsq(int len, const double* __restrict__ w, double* __restrict__ part, const DevState* st,
-                        int ignore_skip) {
-  if (!ignore_skip && st->skip) return;
+// part1[b] = sum of w^2 over block b's range (mode 0: systems not skipped,
+// mode 1: active systems, mode 2: every system)
+__global__ void k_sumsq(const double* __restrict__ w, double* __restrict__ part1, const DevState* st,
+                        const int4* __restrict__ blk, int mode) {
+  const int4 B = blk[blockIdx.x];
+  if ((mode == 0 && st[B.x].skip) || (mode == 1 && !st[B.x].active)) return;
   double acc = 0.0;
-  for (int x = blockIdx.x * kBS + threadIdx.x; x < len; x += gridDim.x * kBS) acc += w[x] * w[x];
+  for (int x = B.y + threadIdx.x; x < B.z; x += kBS) acc += w[x] * w[x];
   acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  if (threadIdx.x == 0) part1[blockIdx.x] = acc;
 }
 
-// out = w / ||w|| with ||w||^2 = sum_b part[b]; H[j+1, j] = ||w|| (j >= 0), or
-// start a cycle (j < 0): beta = ||w||, bnorm set if requested.
-__global__ void k_normalize(int len, int j, int m1, int nblk, const double* __restrict__ w,
-                            double* __restrict__ out, const double* __restrict__ part, double* __restrict__ H,
-                            DevState* st, int set_bnorm) {
-  if (j >= 0 && st->skip) return;
+// out = w / ||w|| per system; j >= 0: H[j+1, j] = ||w||; j < 0: start of a
+// cycle, beta = ||w|| (and bnorm = ||w|| if set_bnorm).
+__global__ void k_normalize(int j, int m, const double* __restrict__ w, double* __restrict__ out,
+                            const double* __restrict__ part1, double* __restrict__ H, DevState* st,
+                            const int4* __restrict__ blk, const int4* __restrict__ sysb, int set_bnorm) {
+  const int4 B = blk[blockIdx.x];
+  if (j >= 0 ? st[B.x].skip : !st[B.x].active) return;
+  const int4 S = sysb[B.x];
   __shared__ double nrm;
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[b];
+    for (int b = S.x; b < S.y; ++b) s += part1[b];
     nrm = sqrt(s);
   }
   __syncthreads();
   const double v = nrm;
   const double inv = v > 0.0 ? 1.0 / v : 0.0;
-  for (int x = blockIdx.x * kBS + threadIdx.x; x < len; x += gridDim.x * kBS) out[x] = w[x] * inv;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  for (int x = B.y + threadIdx.x; x < B.z; x += kBS) out[x] = w[x] * inv;
+  if ((int)blockIdx.x == S.x && threadIdx.x == 0) {
     if (j >= 0) {
-      H[(size_t)j * m1 + j + 1] = v;
+      H[(size_t)B.x * (m + 1) * m + (size_t)j * (m + 1) + j + 1] = v;
     } else {
-      if (set_bnorm) st->bnorm = v;
-      st->beta = v;
+      if (set_bnorm) st[B.x].bnorm = v;
+      st[B.x].beta = v;
     }
   }
 }
 
-// Apply earlier rotations to column j, make rotation j, update g, test.
-__global__ void k_givens(int j, int m1, double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
-                         double* __restrict__ g, DevState* st) {
-  if (st->skip) return;
-  double* h = H + (size_t)j * m1;
+// Per system: apply earlier rotations to column j, make rotation j, update g, test.
+__global__ void k_givens(int j, int m, int K, double* __restrict__ H, double* __restrict__ cs,
+                         double* __restrict__ sn, double* __restrict__ g, DevState* st) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= K) return;
+  DevState& S = st[sys];
+  if (S.skip) return;
+  const int m1 = m + 1;
+  double* h = H + (size_t)sys * m1 * m + (size_t)j * m1;
+  double* c_ = cs + (size_t)sys * m;
+  double* s_ = sn + (size_t)sys * m;
+  double* g_ = g + (size_t)sys * m1;
   for (int i = 0; i < j; ++i) {
-    double t = cs[i] * h[i] + sn[i] * h[i + 1];
-    h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+    double t = c_[i] * h[i] + s_[i] * h[i + 1];
+    h[i + 1] = -s_[i] * h[i] + c_[i] * h[i + 1];
     h[i] = t;
   }
   double a = h[j], b = h[j + 1];
   double den = hypot(a, b);
   double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-  cs[j] = c;
-  sn[j] = s;
+  c_[j] = c;
+  s_[j] = s;
   h[j] = den;
   h[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  st->k = j + 1;
-  st->iters += 1;
-  st->est = st->bnorm > 0.0 ? fabs(g[j + 1]) / st->bnorm : 0.0;
-  if (st->est <= st->tol || b == 0.0) st->conv = 1;
-  if (st->iters >= st->max_iter) st->stop = 1;
-  if (st->conv || st->stop || j + 1 == st->m) st->skip = 1;
+  g_[j + 1] = -s * g_[j];
+  g_[j] = c * g_[j];
+  S.k = j + 1;
+  S.iters += 1;
+  S.est = S.bnorm > 0.0 ? fabs(g_[j + 1]) / S.bnorm : 0.0;
+  if (S.est <= S.tol || b == 0.0) S.conv = 1;
+  if (S.iters >= S.max_iter) S.stop = 1;
+  if (S.conv || S.stop || j + 1 == S.m) S.skip = 1;
 }
 
-// Least squares R y = g (k x k) and the restart coefficients z = Q^T (g_k e_k) / |g_k|.
-__global__ void k_lsq(int m1, const double* __restrict__ H, const double* __restrict__ cs,
+// Per system: least squares R y = g (k x k) and the restart coefficients
+// z = Q^T (g_k e_k) / |g_k|.
+__global__ void k_lsq(int m, int K, const double* __restrict__ H, const double* __restrict__ cs,
                       const double* __restrict__ sn, const double* __restrict__ g, double* __restrict__ y,
                       double* __restrict__ z, DevState* st) {
-  const int k = st->k;
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= K) return;
+  DevState& S = st[sys];
+  const int k = S.k;
+  if (!S.active || k == 0) return;
+  const int m1 = m + 1;
+  const double* Hs = H + (size_t)sys * m1 * m;
+  const double* c_ = cs + (size_t)sys * m;
+  const double* s_ = sn + (size_t)sys * m;
+  const double* g_ = g + (size_t)sys * m1;
+  double* y_ = y + (size_t)sys * m;
+  double* z_ = z + (size_t)sys * m1;
   for (int i = k - 1; i >= 0; --i) {
-    double s = g[i];
-    for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * m1 + i] * y[l];
-    y[i] = s / H[(size_t)i * m1 + i];
+    double s = g_[i];
+    for (int l = i + 1; l < k; ++l) s -= Hs[(size_t)l * m1 + i] * y_[l];
+    y_[i] = s / Hs[(size_t)i * m1 + i];
   }
-  double gk = g[k];
-  double beta = fabs(gk);
-  for (int i = 0; i <= k; ++i) z[i] = 0.0;
-  z[k] = beta > 0.0 ? gk / beta : 0.0;
+  const double gk = g_[k];
+  const double beta = fabs(gk);
+  for (int i = 0; i <= k; ++i) z_[i] = 0.0;
+  z_[k] = beta > 0.0 ? gk / beta : 0.0;
   for (int i = k - 1; i >= 0; --i) {
-    double a = z[i], b = z[i + 1];
-    z[i] = cs[i] * a - sn[i] * b;
-    z[i + 1] = sn[i] * a + cs[i] * b;
+    double a = z_[i], b = z_[i + 1];
+    z_[i] = c_[i] * a - s_[i] * b;
+    z_[i + 1] = s_[i] * a + c_[i] * b;
   }
-  st->beta = beta;
+  S.beta = beta;
 }
 
-// x += sum_{i<k} y_i V_i ; V_0 <- sum_{i<=k} z_i V_i ; next cycle's g, k, skip.
-__global__ void k_update(int len, int m1, double* __restrict__ V, double* __restrict__ x,
-                         const double* __restrict__ y, const double* __restrict__ z, double* __restrict__ g,
-                         DevState* st) {
-  const int k = st->k;
-  for (int e = blockIdx.x * kBS + threadIdx.x; e < len; e += gridDim.x * kBS) {
+// x += sum_{i<k} y_i V_i ; V_0 <- sum_{i<=k} z_i V_i (per system)
+__global__ void k_update(int m, int64_t len, double* __restrict__ V, double* __restrict__ x,
+                         const double* __restrict__ y, const double* __restrict__ z, const DevState* st,
+                         const int4* __restrict__ blk) {
+  const int4 B = blk[blockIdx.x];
+  const DevState& S = st[B.x];
+  const int k = S.k;
+  if (!S.active || k == 0) return;
+  const double* y_ = y + (size_t)B.x * m;
+  const double* z_ = z + (size_t)B.x * (m + 1);
+  for (int e = B.y + threadIdx.x; e < B.z; e += kBS) {
     double dx = 0.0, v0 = 0.0;
     for (int i = 0; i <= k; ++i) {
       double v = V[(size_t)i * len + e];
-      if (i < k) dx += y[i] * v;
-      v0 += z[i] * v;
+      if (i < k) dx += y_[i] * v;
+      v0 += z_[i] * v;
     }
     x[e] += dx;
     V[e] = v0;
   }
 }
 
-__global__ void k_next_cycle(int m1, double* __restrict__ g, DevState* st) {
-  g[0] = st->beta;
-  for (int i = 1; i < m1; ++i) g[i] = 0.0;
-  st->k = 0;
-  st->est = st->bnorm > 0.0 ? st->beta / st->bnorm : 0.0;
-  if (st->beta == 0.0 || st->est <= st->tol) st->conv = 1;
-  st->skip = (st->conv || st->stop) ? 1 : 0;
+__global__ void k_next_cycle(int m, int K, double* __restrict__ g, DevState* st) {
+  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sys >= K) return;
+  DevState& S = st[sys];
+  if (!S.active) return;
+  double* g_ = g + (size_t)sys * (m + 1);
+  g_[0] = S.beta;
+  for (int i = 1; i <= m; ++i) g_[i] = 0.0;
+  S.k = 0;
+  S.est = S.bnorm > 0.0 ? S.beta / S.bnorm : 0.0;
+  if (S.beta == 0.0 || S.est <= S.tol) S.conv = 1;
+  S.skip = (S.conv || S.stop) ? 1 : 0;
 }
 
-// r = rhs - y (2n), elementwise
-__global__ void k_sub(int len, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out) {
-  int i = blockIdx.x * kBS + threadIdx.x;
+__global__ void k_sub(int64_t len, const double* __restrict__ a, const double* __restrict__ b,
+                      double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * kBS + threadIdx.x;
   if (i < len) out[i] = a[i] - b[i];
 }
-__global__ void k_axpy(int len, double alpha, const double* __restrict__ a, double* __restrict__ out) {
-  int i = blockIdx.x * kBS + threadIdx.x;
-  if (i < len) out[i] += alpha * a[i];
-}
-__global__ void k_init_state(DevState* st, int m, int max_iter, double tol) {
-  st->k = 0;
-  st->skip = 0;
-  st->conv = 0;
-  st->stop = max_iter <= 0 ? 1 : 0;
-  st->iters = 0;
-  st->max_iter = max_iter;
-  st->m = m;
-  st->tol = tol;
-  st->est = 1.0;
+__global__ void k_add(int64_t len, const double* __restrict__ a, double* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * kBS + threadIdx.x;
+  if (i < len) out[i] += a[i];
 }
 
-}  // namespace
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, (n + kBS - 1) / kBS); }
 
 struct GraphTag {
   uint64_t gen;
   double eps_in, eps_out, kappa;
+  bool timed;
   bool operator==(const GraphTag& o) const {
-    return gen == o.gen && eps_in == o.eps_in && eps_out == o.eps_out && kappa == o.kappa;
+    return gen == o.gen && eps_in == o.eps_in && eps_out == o.eps_out && kappa == o.kappa && timed == o.timed;
   }
 };
 struct Recorded {
@@ -238,16 +279,22 @@ struct Recorded {
   long long kernels;              // kernel nodes in the graph
 };
 
+}  // namespace
+
 struct GmresWork {
-  int64_t n = 0;
-  int m = 0;
-  int nblk = 0;
-  DevBuf<double> V, w, H, cs, sn, g, y, z, part, r, d, t;
-  DevState* st = nullptr;     // device
-  DevState* st_host = nullptr;  // pinned
-  // recorded cycles keyed by (precision, transpose)
-  std::map<int, Recorded> graphs;
-  const std::vector<EventPair>* replayed = nullptr;  // events of the graph launched last
+  uint64_t lay_key = 0;
+  int m = 0, K = 0, nblk = 0;
+  int64_t len = 0;
+  DevBuf<double> V, w, H, cs, sn, g, y, z, part, part1, r, d, t;
+  DevBuf<int4> blk, sysb;
+  DevBuf<int> mask;  // per system: 1 = leave out of the FP64 residual
+  std::vector<int4> sysb_host;
+  DevState* st = nullptr;
+  DevState* st_host = nullptr;   // pinned
+  double* part1_host = nullptr;  // pinned
+  int* mask_host = nullptr;      // pinned
+  std::map<int, Recorded> graphs;  // recorded cycles keyed by (precision, transpose)
+  const std::vector<EventPair>* replayed = nullptr;
   ~GmresWork() {
     for (auto& kv : graphs) {
       cudaGraphExecDestroy(kv.second.exec);
@@ -255,6 +302,8 @@ struct GmresWork {
     }
     if (st) cudaFree(st);
     if (st_host) cudaFreeHost(st_host);
+    if (part1_host) cudaFreeHost(part1_host);
+    if (mask_host) cudaFreeHost(mask_host);
   }
 };
 
@@ -265,94 +314,108 @@ void gmres_free(Surface* s) {
 
 namespace {
 
-GmresWork* workspace(Surface* s, int m) {
+GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
   GmresWork* w = s->gw;
-  if (w && w->n == s->n && w->m == m) return w;
+  if (w && w->lay_key == L.key && w->m == m && w->K == L.K) return w;
   if (w) gmres_free(s);
   w = new GmresWork();
   s->gw = w;
-  const int64_t len = 2 * s->n;
-  w->n = s->n;
+  w->lay_key = L.key;
   w->m = m;
-  w->nblk = (int)std::min<int64_t>(2 * s->num_sms, (len + 4 * kBS - 1) / (4 * kBS));
-  w->nblk = std::max(w->nblk, 1);
+  w->K = L.K;
+  w->len = L.len;
+  // blocks: each covers one contiguous range (about 1024 unknowns) of one system
+  std::vector<int4> blk;
+  std::vector<int4> sysb(L.K);
+  for (int k = 0; k < L.K; ++k) {
+    const int64_t lk = 2 * (int64_t)L.n[k];
+    const int nb = (int)std::min<int64_t>(512, std::max<int64_t>(1, (lk + 1023) / 1024));
+    const int64_t chunk = (lk + nb - 1) / nb;
+    sysb[k] = make_int4((int)blk.size(), (int)blk.size() + nb, 0, 0);
+    for (int b = 0; b < nb; ++b) {
+      const int64_t a = L.vec_off[k] + b * chunk, e = std::min<int64_t>(L.vec_off[k] + lk, a + chunk);
+      blk.push_back(make_int4(k, (int)a, (int)e, sysb[k].x));
+    }
+  }
+  w->nblk = (int)blk.size();
+  w->sysb_host = sysb;
+  const int64_t len = L.len;
   w->V.ensure((size_t)(m + 1) * len);
   w->w.ensure(len);
   w->r.ensure(len);
   w->d.ensure(len);
   w->t.ensure(len);
-  w->H.ensure((size_t)(m + 1) * m);
-  w->cs.ensure(m);
-  w->sn.ensure(m);
-  w->g.ensure(m + 1);
-  w->y.ensure(m);
-  w->z.ensure(m + 1);
+  w->H.ensure((size_t)L.K * (m + 1) * m);
+  w->cs.ensure((size_t)L.K * m);
+  w->sn.ensure((size_t)L.K * m);
+  w->g.ensure((size_t)L.K * (m + 1));
+  w->y.ensure((size_t)L.K * m);
+  w->z.ensure((size_t)L.K * (m + 1));
   w->part.ensure((size_t)w->nblk * (m + 1));
-  BIPB_CUDA(cudaMalloc(reinterpret_cast<void**>(&w->st), sizeof(DevState)));
-  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->st_host), sizeof(DevState)));
+  w->part1.ensure(w->nblk);
+  w->blk.ensure(blk.size());
+  w->sysb.ensure(L.K);
+  w->mask.ensure(L.K);
+  BIPB_CUDA(cudaMalloc(reinterpret_cast<void**>(&w->st), L.K * sizeof(DevState)));
+  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->st_host), L.K * sizeof(DevState)));
+  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->part1_host), w->nblk * sizeof(double)));
+  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->mask_host), L.K * sizeof(int)));
+  BIPB_CUDA(cudaMemcpyAsync(w->blk.p, blk.data(), blk.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(w->sysb.p, sysb.data(), sysb.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));
+  ++s->alloc_gen;
   return w;
 }
 
-int blocks(int64_t n) { return (int)((n + kBS - 1) / kBS); }
-
-// Norm of vec into st->beta (and bnorm if set_bnorm), out = vec / ||vec||.
-void start_cycle(Surface* s, GmresWork* w, const double* vec, bool set_bnorm) {
-  const int len = (int)(2 * s->n);
-  k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(len, vec, w->part.p, w->st, 1);
-  BIPB_LAUNCHED(s);
-  k_normalize<<<w->nblk, kBS, 0, s->stream>>>(len, -1, w->m + 1, w->nblk, vec, w->V.p, w->part.p, w->H.p,
-                                               w->st, set_bnorm ? 1 : 0);
-  BIPB_LAUNCHED(s);
-  k_next_cycle<<<1, 1, 0, s->stream>>>(w->m + 1, w->g.p, w->st);
-  BIPB_LAUNCHED(s);
-}
-
 // One restart cycle: kernels only (no host synchronisation, no allocation).
-void issue_cycle(Surface* s, GmresWork* w, const bipb_medium& med, int precision, bool transpose) {
-  const int len = (int)(2 * s->n);
-  const int m = w->m, m1 = m + 1;
+void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& med, int precision,
+                 bool transpose) {
+  const int m = w->m, m1 = m + 1, K = w->K, nb = w->nblk;
+  const int64_t len = w->len;
+  const int kg = (K + 127) / 128;
   for (int j = 0; j < m; ++j) {
     double* vj = w->V.p + (size_t)j * len;
-    matvec(s, med, precision, transpose, vj, w->w.p, &w->st->skip);
+    matvec(s, L, med, precision, transpose, vj, w->w.p, &w->st->skip, kStateInts);
     for (int pass = 0; pass < 2; ++pass) {
-      k_dots<<<w->nblk, kBS, 0, s->stream>>>(len, j, m1, w->V.p, w->w.p, w->part.p, w->st);
+      k_dots<<<nb, kBS, 0, s->stream>>>(j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
       BIPB_LAUNCHED(s);
-      k_orth<<<w->nblk, kBS, 0, s->stream>>>(len, j, m1, w->nblk, w->V.p, w->w.p, w->part.p, w->H.p, pass,
-                                             w->st);
+      k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, pass, w->st, w->blk.p,
+                                        w->sysb.p);
       BIPB_LAUNCHED(s);
     }
-    k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(len, w->w.p, w->part.p, w->st, 0);
+    k_sumsq<<<nb, kBS, 0, s->stream>>>(w->w.p, w->part1.p, w->st, w->blk.p, 0);
     BIPB_LAUNCHED(s);
-    k_normalize<<<w->nblk, kBS, 0, s->stream>>>(len, j, m1, w->nblk, w->w.p, vj + len, w->part.p, w->H.p,
-                                                 w->st, 0);
+    k_normalize<<<nb, kBS, 0, s->stream>>>(j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
+                                           0);
     BIPB_LAUNCHED(s);
-    k_givens<<<1, 1, 0, s->stream>>>(j, m1, w->H.p, w->cs.p, w->sn.p, w->g.p, w->st);
+    k_givens<<<kg, 128, 0, s->stream>>>(j, m, K, w->H.p, w->cs.p, w->sn.p, w->g.p, w->st);
     BIPB_LAUNCHED(s);
   }
-  k_lsq<<<1, 1, 0, s->stream>>>(m1, w->H.p, w->cs.p, w->sn.p, w->g.p, w->y.p, w->z.p, w->st);
+  k_lsq<<<kg, 128, 0, s->stream>>>(m, K, w->H.p, w->cs.p, w->sn.p, w->g.p, w->y.p, w->z.p, w->st);
   BIPB_LAUNCHED(s);
-  k_update<<<w->nblk, kBS, 0, s->stream>>>(len, m1, w->V.p, w->d.p, w->y.p, w->z.p, w->g.p, w->st);
+  k_update<<<nb, kBS, 0, s->stream>>>(m, len, w->V.p, w->d.p, w->y.p, w->z.p, w->st, w->blk.p);
   BIPB_LAUNCHED(s);
-  k_next_cycle<<<1, 1, 0, s->stream>>>(m1, w->g.p, w->st);
+  k_next_cycle<<<kg, 128, 0, s->stream>>>(m, K, w->g.p, w->st);
   BIPB_LAUNCHED(s);
 }
 
-void run_cycle(Surface* s, GmresWork* w, const bipb_medium& med, int precision, bool transpose) {
+void run_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& med, int precision,
+               bool transpose) {
   // A recorded cycle bakes in the medium and every buffer address, so it is
   // tagged with both and re-recorded when either changes.
   const int key = precision * 2 + (transpose ? 1 : 0);
-  const GraphTag tag{s->alloc_gen, med.eps_in, med.eps_out, med.kappa};
+  const GraphTag tag{s->alloc_gen, med.eps_in, med.eps_out, med.kappa, s->timer.on};
   auto it = w->graphs.find(key);
-  if (it != w->graphs.end() && it->second.tag == tag && it->second.events.empty() == !s->timer.on) {
+  if (it != w->graphs.end() && it->second.tag == tag) {
     BIPB_CUDA(cudaGraphLaunch(it->second.exec, s->stream));
     s->launches += it->second.kernels;
     w->replayed = &it->second.events;
     return;
   }
   // a plain launch first: it runs this cycle and creates every scratch buffer
-  issue_cycle(s, w, med, precision, transpose);
-  const GraphTag after{s->alloc_gen, med.eps_in, med.eps_out, med.kappa};
-  // record a copy of the cycle for the next calls (the capture does not run it)
+  issue_cycle(s, L, w, med, precision, transpose);
+  const GraphTag after{s->alloc_gen, med.eps_in, med.eps_out, med.kappa, s->timer.on};
+  // record a copy of the cycle for the next calls (recording does not run it)
   cudaGraph_t graph = nullptr;
   std::vector<EventPair> evs;
   BIPB_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
@@ -360,7 +423,7 @@ void run_cycle(Surface* s, GmresWork* w, const bipb_medium& med, int precision, 
   s->recording = true;
   s->recorded_launches = 0;
   try {
-    issue_cycle(s, w, med, precision, transpose);
+    issue_cycle(s, L, w, med, precision, transpose);
   } catch (...) {
     s->recording = false;
     s->timer.capture = nullptr;
@@ -383,13 +446,13 @@ void run_cycle(Surface* s, GmresWork* w, const bipb_medium& med, int precision, 
   BIPB_CUDA(e);
   if (it != w->graphs.end()) {
     cudaGraphExecDestroy(it->second.exec);
-    for (auto& e : it->second.events) s->timer.pool.push_back(e.a), s->timer.pool.push_back(e.b);
+    for (auto& ev : it->second.events) s->timer.pool.push_back(ev.a), s->timer.pool.push_back(ev.b);
   }
   w->graphs[key] = Recorded{exec, after, std::move(evs), kernels};
 }
 
-DevState read_state(Surface* s, GmresWork* w) {
-  BIPB_CUDA(cudaMemcpyAsync(w->st_host, w->st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+void read_states(Surface* s, GmresWork* w) {
+  BIPB_CUDA(cudaMemcpyAsync(w->st_host, w->st, w->K * sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
   BIPB_CUDA(cudaStreamSynchronize(s->stream));
   if (s->timer.on) {
     s->timer.collect();
@@ -397,109 +460,157 @@ DevState read_state(Surface* s, GmresWork* w) {
       for (auto& e : *w->replayed) s->timer.add(e);
   }
   w->replayed = nullptr;
-  return *w->st_host;
 }
 
-// GMRES on op(A) d = r0 (d starts at zero).  Returns iterations used.
-// Stops at recurrence estimate <= tol (relative to ||r0||) or max_iter.
-int gmres_core(Surface* s, GmresWork* w, const bipb_medium& med, int precision, bool transpose,
-               const double* r0, double tol, int max_iter, DevState* out) {
-  const int len = (int)(2 * s->n);
-  BIPB_CUDA(cudaMemsetAsync(w->d.p, 0, (size_t)len * sizeof(double), s->stream));
-  k_init_state<<<1, 1, 0, s->stream>>>(w->st, w->m, max_iter, tol);
+// Per-system 2-norms of a batched vector (all systems, fixed summation order).
+std::vector<double> norms(Surface* s, GmresWork* w, const double* v) {
+  k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(v, w->part1.p, w->st, w->blk.p, 2);
   BIPB_LAUNCHED(s);
-  start_cycle(s, w, r0, true);
-  DevState h = read_state(s, w);
-  while (!h.conv && !h.stop) {
-    run_cycle(s, w, med, precision, transpose);
-    h = read_state(s, w);
-  }
-  *out = h;
-  return h.iters;
-}
-
-double norm2(Surface* s, GmresWork* w, const double* v) {
-  const int len = (int)(2 * s->n);
-  k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(len, v, w->part.p, w->st, 1);
-  BIPB_LAUNCHED(s);
-  std::vector<double> h(w->nblk);
-  BIPB_CUDA(cudaMemcpyAsync(h.data(), w->part.p, w->nblk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(w->part1_host, w->part1.p, w->nblk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   BIPB_CUDA(cudaStreamSynchronize(s->stream));
-  double acc = 0.0;
-  for (double v2 : h) acc += v2;
-  return std::sqrt(acc);
+  std::vector<double> out(w->K);
+  for (int k = 0; k < w->K; ++k) {
+    double acc = 0.0;
+    for (int b = w->sysb_host[k].x; b < w->sysb_host[k].y; ++b) acc += w->part1_host[b];
+    out[k] = std::sqrt(acc);
+  }
+  return out;
+}
+
+// GMRES on op(A) d = r0 for the active systems (d starts at zero; others are
+// left alone).  Per system: stop at recurrence estimate <= tol[k] (relative
+// to ||r0_k||) or after cap[k] iterations.  Returns iterations per system.
+std::vector<int> gmres_core(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& med, int precision,
+                            bool transpose, const double* r0, const std::vector<char>& active,
+                            const std::vector<double>& tol, const std::vector<int>& cap, std::vector<int>* conv) {
+  const int K = w->K;
+  BIPB_CUDA(cudaMemsetAsync(w->d.p, 0, (size_t)w->len * sizeof(double), s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));  // st_host is about to be rewritten
+  for (int k = 0; k < K; ++k) {
+    DevState& S = w->st_host[k];
+    S = DevState{};
+    S.active = active[k] ? 1 : 0;
+    S.skip = S.active ? 0 : 1;
+    S.conv = S.active ? 0 : 1;
+    S.stop = (S.active && cap[k] <= 0) ? 1 : 0;
+    S.max_iter = cap[k];
+    S.m = w->m;
+    S.tol = tol[k];
+    S.est = 1.0;
+  }
+  BIPB_CUDA(cudaMemcpyAsync(w->st, w->st_host, K * sizeof(DevState), cudaMemcpyHostToDevice, s->stream));
+  const int kg = (K + 127) / 128;
+  k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(r0, w->part1.p, w->st, w->blk.p, 1);
+  BIPB_LAUNCHED(s);
+  k_normalize<<<w->nblk, kBS, 0, s->stream>>>(-1, w->m, r0, w->V.p, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
+                                              1);
+  BIPB_LAUNCHED(s);
+  k_next_cycle<<<kg, 128, 0, s->stream>>>(w->m, K, w->g.p, w->st);
+  BIPB_LAUNCHED(s);
+  read_states(s, w);
+  auto running = [&] {
+    for (int k = 0; k < K; ++k)
+      if (w->st_host[k].active && !w->st_host[k].conv && !w->st_host[k].stop) return true;
+    return false;
+  };
+  while (running()) {
+    run_cycle(s, L, w, med, precision, transpose);
+    read_states(s, w);
+  }
+  std::vector<int> it(K);
+  conv->assign(K, 0);
+  for (int k = 0; k < K; ++k) {
+    it[k] = w->st_host[k].iters;
+    (*conv)[k] = w->st_host[k].conv;
+  }
+  return it;
 }
 
 }  // namespace
 
-SolveResult gmres_solve(Surface* s, const bipb_medium& med, const bipb_solve_params& p, bool transpose,
-                        const double* rhs, double* x, bool warm) {
-  SolveResult res;
+std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_medium& med,
+                                     const bipb_solve_params& p, bool transpose, const double* rhs, double* x,
+                                     bool warm) {
+  const int K = L.K;
+  std::vector<SolveResult> res(K);
   const int m = p.restart > 0 ? p.restart : 10;
   const int max_iter = p.max_iter > 0 ? p.max_iter : 1000;
-  GmresWork* w = workspace(s, m);
-  const int len = (int)(2 * s->n);
-  const int nb = blocks(len);
-  const double bnorm = norm2(s, w, rhs);
-  if (bnorm == 0.0) {
-    BIPB_CUDA(cudaMemsetAsync(x, 0, (size_t)len * sizeof(double), s->stream));
-    res.converged = 1;
-    return res;
-  }
+  GmresWork* w = workspace(s, L, m);
+  const int64_t len = L.len;
+  const int nb = grid_for(len);
+  const std::vector<double> bnorm = norms(s, w, rhs);
   // r = rhs - A x (or rhs when starting from zero)
   if (warm) {
-    matvec(s, med, BIPB_FP64, transpose, x, w->t.p, nullptr);
-    res.matvecs64++;
+    matvec(s, L, med, BIPB_FP64, transpose, x, w->t.p, nullptr, 0);
+    for (auto& r : res) r.matvecs64++;
     k_sub<<<nb, kBS, 0, s->stream>>>(len, rhs, w->t.p, w->r.p);
+    BIPB_LAUNCHED(s);
   } else {
     BIPB_CUDA(cudaMemsetAsync(x, 0, (size_t)len * sizeof(double), s->stream));
     BIPB_CUDA(cudaMemcpyAsync(w->r.p, rhs, (size_t)len * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
   }
-  BIPB_LAUNCHED(s);
-  double rel = warm ? norm2(s, w, w->r.p) / bnorm : 1.0;
+  std::vector<double> rel(K, 1.0);
+  if (warm) {
+    std::vector<double> rn = norms(s, w, w->r.p);
+    for (int k = 0; k < K; ++k) rel[k] = bnorm[k] > 0 ? rn[k] / bnorm[k] : 0.0;
+  }
+  for (int k = 0; k < K; ++k)
+    if (bnorm[k] == 0.0) rel[k] = 0.0;
   const bool mixed = p.precision == BIPB_MIXED;
   const double inner_floor = p.inner_tol > 0 ? p.inner_tol : 1e-6;
   const int inner_cap = p.inner_max_iter > 0 ? p.inner_max_iter : 200;
-  int iters = 0;
-  while (rel > p.tol && iters < max_iter) {
-    double tol_rel;
-    int cap = max_iter - iters;
-    if (mixed) {
-      tol_rel = std::max(inner_floor, 0.3 * p.tol / rel);
-      cap = std::min(cap, inner_cap);
-    } else {
-      tol_rel = p.tol / rel;
+  std::vector<char> active(K), done(K, 0);
+  std::vector<int> iters(K, 0);
+  for (;;) {
+    bool any = false;
+    std::vector<double> tol_rel(K, 1.0);
+    std::vector<int> cap(K, 0);
+    for (int k = 0; k < K; ++k) {
+      active[k] = !done[k] && rel[k] > p.tol && iters[k] < max_iter;
+      if (!active[k]) continue;
+      any = true;
+      cap[k] = max_iter - iters[k];
+      if (mixed) {
+        tol_rel[k] = std::max(inner_floor, 0.3 * p.tol / rel[k]);
+        cap[k] = std::min(cap[k], inner_cap);
+      } else {
+        tol_rel[k] = p.tol / rel[k];
+      }
     }
-    DevState h;
-    int used = gmres_core(s, w, med, mixed ? BIPB_FP32 : BIPB_FP64, transpose, w->r.p, tol_rel, cap, &h);
-    iters += used;
-    if (mixed) {
-      res.matvecs32 += used;
-      res.refine_steps++;
-    } else {
-      res.matvecs64 += used;
-    }
-    // x += d ; r = rhs - A x (FP64)
-    k_axpy<<<nb, kBS, 0, s->stream>>>(len, 1.0, w->d.p, x);
+    if (!any) break;
+    std::vector<int> conv;
+    std::vector<int> used = gmres_core(s, L, w, med, mixed ? BIPB_FP32 : BIPB_FP64, transpose, w->r.p, active,
+                                       tol_rel, cap, &conv);
+    // x += d (d is zero outside the active systems); r = rhs - A x in FP64 for the active systems
+    k_add<<<nb, kBS, 0, s->stream>>>(len, w->d.p, x);
     BIPB_LAUNCHED(s);
-    matvec(s, med, BIPB_FP64, transpose, x, w->t.p, nullptr);
-    res.matvecs64++;
+    for (int k = 0; k < K; ++k) w->mask_host[k] = active[k] ? 0 : 1;
+    BIPB_CUDA(cudaMemcpyAsync(w->mask.p, w->mask_host, K * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    matvec(s, L, med, BIPB_FP64, transpose, x, w->t.p, w->mask.p, 1);
     k_sub<<<nb, kBS, 0, s->stream>>>(len, rhs, w->t.p, w->r.p);
     BIPB_LAUNCHED(s);
-    double new_rel = norm2(s, w, w->r.p) / bnorm;
-    if (!mixed && !h.conv) {  // hit the iteration cap
-      rel = new_rel;
-      break;
+    std::vector<double> rn = norms(s, w, w->r.p);
+    for (int k = 0; k < K; ++k) {
+      if (!active[k]) continue;
+      iters[k] += used[k];
+      res[k].matvecs64++;
+      if (mixed) {
+        res[k].matvecs32 += used[k];
+        res[k].refine_steps++;
+      } else {
+        res[k].matvecs64 += used[k];
+      }
+      const double new_rel = bnorm[k] > 0 ? rn[k] / bnorm[k] : 0.0;
+      if (!mixed && !conv[k]) done[k] = 1;                                           // iteration cap
+      if (mixed && res[k].refine_steps >= 3 && new_rel > 0.1 * rel[k]) done[k] = 1;  // refinement stalled
+      rel[k] = new_rel;
     }
-    if (mixed && res.refine_steps >= 3 && new_rel > 0.1 * rel) {  // refinement stalled
-      rel = new_rel;
-      break;
-    }
-    rel = new_rel;
   }
-  res.iters = iters;
-  res.rel_residual = rel;
-  res.converged = rel <= p.tol ? 1 : 0;
+  for (int k = 0; k < K; ++k) {
+    res[k].iters = iters[k];
+    res[k].rel_residual = rel[k];
+    res[k].converged = rel[k] <= p.tol ? 1 : 0;
+  }
   return res;
 }
 

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <memory>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -60,11 +62,27 @@ struct DevBuf {
   ~DevBuf() { release(); }
 };
 
-// Tiling of one pair pass: targets in tiles of nt*tpt, sources in n_splits
-// equal ranges (each CTA = one tile against one range).
-struct PassTiling {
-  int n_tiles = 0;
-  int n_splits = 0;
+// K independent systems handled by one batched pass (several right-hand
+// sides of one surface, or several surfaces).  System k has n[k] elements
+// starting at geometry element geo_off[k], 2 n[k] unknowns starting at
+// vec_off[k] of a batched vector, and nc[k] charges starting at charge
+// record chg_off[k].
+struct SysLayout {
+  int K = 0;
+  std::vector<int> geo_off, n, vec_off, chg_off, nc;
+  int64_t len = 0;  // sum of 2 n[k]
+  int max_n = 0, max_nc = 0;
+  uint64_t key = 0;
+};
+SysLayout make_layout(const std::vector<int>& geo_off, const std::vector<int>& n, const std::vector<int>& chg_off,
+                      const std::vector<int>& nc);
+
+// Work list of one pass (see kernels.cu): items of two int4 each and a
+// per-system table {n_tgt, splits, partial offset, 0} for the reductions.
+struct ItemPlan {
+  DevBuf<int4> items, tab;
+  int n_items = 0;
+  int64_t part_len = 0;  // partial sums the pass writes
 };
 
 // FP32 mat-vec kernel variants (threads per CTA, targets per thread,
@@ -136,12 +154,11 @@ struct Surface {
   cudaStream_t stream = nullptr;  // private, non-blocking; joined to user_stream per call
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
 
-  int64_t n = 0;
-  double center[3] = {0, 0, 0};  // all device coordinates are relative to the mean centroid
+  int64_t n = 0;  // elements (all surfaces of a batch handle)
 
-  DevBuf<double4_32a> geo64;  // n: (x, y, z, area), centred
-  DevBuf<double4_32a> nrm64;  // n: (nx, ny, nz, 0)
-  DevBuf<double4_32a> tgt64;  // 2n: (x, y, z, area), (nx, ny, nz, 0), centred
+  // Geometry of every element, each surface relative to its own mean
+  // centroid (part_center), so that the FP32 copies keep the most digits.
+  DevBuf<double4_32a> tgt64;  // 2n: (x, y, z, area), (nx, ny, nz, 0)
   DevBuf<float4> tgt32;   // the same in FP32
 
   // per-pass scratch
@@ -150,12 +167,23 @@ struct Surface {
   DevBuf<float> part32;
   DevBuf<double> part64;
 
-  // charges
-  int64_t nc = 0;
-  int n_rhs = 0;
+  // charges: every system's charge records (y - center, q), back to back
+  int64_t nc = 0;  // charges per configuration (single surface)
+  int n_rhs = 0;   // configurations (systems)
   int n_pos_sets = 0;
-  DevBuf<double4_32a> chg;     // n_rhs * nc: (y - center, q)
-  std::vector<double> q_host;  // n_rhs * nc
+  DevBuf<double4_32a> chg;
+  SysLayout lay;   // the systems bipb_solve works on
+
+  // surfaces of the handle (one for bipb_surface_create, several for a
+  // batch handle, one system each): element offsets, sizes, centres
+  std::vector<int> part_off, part_n;
+  std::vector<double> part_center;  // 3 per surface
+  bool batch = false;
+
+  // cached work lists and device copies of layouts (keyed by content)
+  std::map<uint64_t, std::unique_ptr<ItemPlan>> plans;
+  std::map<uint64_t, std::unique_ptr<DevBuf<int4>>> layouts;
+  const int4* lay_dev(const SysLayout& L);  // {geo_off, n, vec_off, chg_off} per system
 
   // solution state
   DevBuf<double> u;  // n_rhs * 2n
@@ -206,34 +234,36 @@ struct TimedLaunch {
   }
 };
 
-// ---- kernels.cu: passes on device memory, all on s->stream ----
-// y = A u or A^T u for one vector (u, y: 2n doubles), `skip` (device int or
-// nullptr) makes every kernel return at once when it holds a nonzero value.
-void matvec(Surface* s, const bipb_medium& m, int precision, bool transpose, const double* u,
-            double* y, const int* skip);
-// Time every FP32 mat-vec variant on this surface (reps launches each) and
-// keep the fastest; returns its index and its time per mat-vec in best_ms.
-int autotune_matvec32(Surface* s, const bipb_medium& m, int reps, double* best_ms);
-// b (2n) for right-hand side r
-void source_pass(Surface* s, const bipb_medium& m, int r, double* b);
-// reaction potential (nc, internal units) and E (kcal/mol, device scalar) for rhs r
-void reaction_pass(Surface* s, const bipb_medium& m, int r, const double* u, double* phi_reac,
+// ---- kernels.cu: batched passes on device memory, all on s->stream ----
+// Vectors are batched: system k's 2 n[k] values start at L.vec_off[k].
+// y = A u or A^T u for every system; skip (device ints, stride skip_stride,
+// one per system, or nullptr) makes the kernels skip systems whose flag is set.
+void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision, bool transpose, const double* u,
+            double* y, const int* skip, int skip_stride);
+// Time every FP32 mat-vec variant on layout L (reps launches each) and keep
+// the fastest; returns its index and its time per mat-vec in best_ms.
+int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int reps, double* best_ms);
+// b = [S1; S2] of every system
+void source_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* b);
+// reaction potential at every charge (internal units, at chg_off) and E per system (kcal/mol)
+void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, double* phi_reac,
                    double* e_out);
-// energy row c (2n) for rhs r: E = 1/2 c.u
-void energy_row_pass(Surface* s, const bipb_medium& m, int r, double* c);
-// gradient passes for rhs r given u and the adjoint lam: dE/dq (nc), dE/dy (3 nc), internal units
-void grad_pass(Surface* s, const bipb_medium& m, int r, const double* u, const double* lam,
-               double* dq, double* dy);
+// energy row c of every system: E = 1/2 c.u
+void energy_row_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* c);
+// dE/dq (per charge) and dE/dy (3 per charge), internal units, from u and the adjoint lam
+void grad_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, const double* lam, double* dq,
+               double* dy);
 
 // ---- gmres.cu ----
 struct SolveResult {
   int converged = 0, iters = 0, refine_steps = 0, matvecs64 = 0, matvecs32 = 0;
   double rel_residual = 0.0;
 };
-// Solve op(A) x = rhs for one right-hand side; x holds the initial guess
-// (zero if !warm) and receives the solution.  op = A or A^T.
-SolveResult gmres_solve(Surface* s, const bipb_medium& m, const bipb_solve_params& p, bool transpose,
-                        const double* rhs, double* x, bool warm);
+// Solve op(A_k) x_k = rhs_k for every system of L (batched vectors); x holds
+// the initial guess (zero if !warm) and receives the solutions.  op = A or A^T.
+std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_medium& m,
+                                     const bipb_solve_params& p, bool transpose, const double* rhs, double* x,
+                                     bool warm);
 void gmres_free(Surface* s);
 
 }  // namespace bipb

@@ -2,14 +2,19 @@
 // and its transpose, the source term (Eq. for S1, S2), the reaction potential
 // and solvation energy (Eq. for E_sol), and the energy gradient.
 //
-// Every pass has the same shape: targets in registers (several per thread),
-// sources streamed through shared memory in chunks, each CTA covering one
-// target tile against one split of the source chunks and writing per-split
-// partial sums; a reduction kernel then adds the splits in a fixed order in
-// FP64, applies the 1/(4 pi) and the diagonal, and writes the output.  The
-// fixed order makes every pass bitwise reproducible.
+// Every pass has one shape.  A pass runs over K independent systems at once
+// (several right-hand sides of one surface, or several surfaces of uneven
+// size); its work is a list of items, each one tile of a system's targets
+// (several per thread, in registers) against one range of that system's
+// sources (streamed through shared memory CH records at a time).  One launch
+// covers the whole list; items are balanced in size and their count fills
+// whole waves of resident CTAs.  Each item writes per-split partial sums; a
+// reduction kernel adds the splits of every target in a fixed order in FP64,
+// applies 1/(4 pi) and the diagonal, and writes the output, so every pass is
+// bitwise reproducible.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -18,7 +23,6 @@ namespace bipb {
 namespace {
 
 constexpr double kInv4Pi = 1.0 / (4.0 * kPi);
-constexpr double kFar = 1.0e10;  // position of padding records
 
 template <typename T>
 struct V4T;
@@ -31,11 +35,15 @@ struct V4T<double> {
   using type = double4_32a;
 };
 
-__device__ __forceinline__ bool skipped(const int* skip) { return skip != nullptr && *skip != 0; }
+__device__ __forceinline__ bool sys_skipped(const int* skip, int stride, int sys) {
+  return skip != nullptr && skip[(size_t)sys * stride] != 0;
+}
 
 // ------------------------------------------------------------------ policies
 // A policy P describes one pass: the target state loaded into registers, the
-// source record (RW vectors of 4), the accumulator and the pair update.
+// source record (RW vectors of 4), the accumulator (NOUT values) and the pair
+// update.  load() takes a global target index; store() writes the NOUT values
+// of local target i to part[out + c * n_tgt + i].
 
 template <typename T>
 struct ElemTgt {
@@ -46,6 +54,7 @@ template <typename T, bool TRANS>
 struct MatvecPolicy {
   using V4 = typename V4T<T>::type;
   static constexpr int RW = 2;
+  static constexpr int NOUT = 2;
   static constexpr bool SELF = true;
   using Tgt = ElemTgt<T>;
   struct Acc {
@@ -53,9 +62,7 @@ struct MatvecPolicy {
   };
   struct Args {
     const V4* tgt;  // 2 per element: (x, y, z, area), (nx, ny, nz, 0)
-    const V4* rec;  // RW per source
-    T* part;        // [split][2][n]
-    int n;
+    T* part;
     PairConst<T> c;
   };
   __device__ static void load(const Args& a, int i, Tgt& t) {
@@ -73,9 +80,9 @@ struct MatvecPolicy {
       pair_forward<MASK>(t.x, t.y, t.z, t.nx, t.ny, t.nz, A.x, A.y, A.z, A.w, B.x, B.y, B.z, self, a.c,
                          acc.p, acc.q);
   }
-  __device__ static void store(const Args& a, int split, int i, const Acc& acc) {
-    a.part[(size_t)split * 2 * a.n + i] = acc.p;
-    a.part[(size_t)split * 2 * a.n + a.n + i] = acc.q;
+  __device__ static void store(const Args& a, int out, int n_tgt, int i, const Acc& acc) {
+    a.part[(size_t)out + i] = acc.p;
+    a.part[(size_t)out + n_tgt + i] = acc.q;
   }
 };
 
@@ -83,20 +90,18 @@ struct MatvecPolicy {
 //   4 pi eps_in S1 += q s,   4 pi eps_in S2 += -q (n_i.d) s^3   (d/dnu_x = +n_x.grad_x)
 struct SourcePolicy {
   static constexpr int RW = 1;
+  static constexpr int NOUT = 2;
   static constexpr bool SELF = false;
   using Tgt = ElemTgt<double>;
   struct Acc {
     double s1, s2;
   };
   struct Args {
-    const double4_32a* geo;
-    const double4_32a* nrm;
-    const double4_32a* rec;  // (y, q)
-    double* part;        // [split][2][n]
-    int n;
+    const double4_32a* tgt;  // 2 per element
+    double* part;
   };
   __device__ static void load(const Args& a, int i, Tgt& t) {
-    double4_32a g = a.geo[i], v = a.nrm[i];
+    double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
     t = Tgt{g.x, g.y, g.z, v.x, v.y, v.z};
   }
   __device__ static void zero(Acc& acc) { acc.s1 = 0.0, acc.s2 = 0.0; }
@@ -109,9 +114,9 @@ struct SourcePolicy {
     acc.s1 += qs;
     acc.s2 -= qs * (s * s) * (t.nx * dx + t.ny * dy + t.nz * dz);
   }
-  __device__ static void store(const Args& a, int split, int i, const Acc& acc) {
-    a.part[(size_t)split * 2 * a.n + i] = acc.s1;
-    a.part[(size_t)split * 2 * a.n + a.n + i] = acc.s2;
+  __device__ static void store(const Args& a, int out, int n_tgt, int i, const Acc& acc) {
+    a.part[(size_t)out + i] = acc.s1;
+    a.part[(size_t)out + n_tgt + i] = acc.s2;
   }
 };
 
@@ -124,6 +129,7 @@ struct PointTgt {
 //   4 pi phi_reac += s [ (1 - e) a_j + (eps t - 1) (m_j.d) s^2 ]  (K1 psi + K2 phi, n_j only)
 struct ReactionPolicy {
   static constexpr int RW = 2;
+  static constexpr int NOUT = 1;
   static constexpr bool SELF = false;
   using Tgt = PointTgt;
   struct Acc {
@@ -131,9 +137,7 @@ struct ReactionPolicy {
   };
   struct Args {
     const double4_32a* pts;  // (y, q)
-    const double4_32a* rec;
-    double* part;  // [split][n_pts]
-    int n;         // number of charges
+    double* part;
     PairConst<double> c;
   };
   __device__ static void load(const Args& a, int k, Tgt& t) {
@@ -154,8 +158,45 @@ struct ReactionPolicy {
     p += ((a.c.eps * t1 - 1.0) * cm) * (s * s);
     acc.p += p * s;
   }
-  __device__ static void store(const Args& a, int split, int k, const Acc& acc) {
-    a.part[(size_t)split * a.n + k] = acc.p;
+  __device__ static void store(const Args& a, int out, int, int k, const Acc& acc) {
+    a.part[(size_t)out + k] = acc.p;
+  }
+};
+
+// Energy row c: target element j, source charge k (record (y_k, q_k)), d = y_k - x_j:
+//   4 pi K2(y_k, x_j) = (eps t - 1) (n_j.d) s^3,  4 pi K1(y_k, x_j) = (1 - e) s
+struct EnergyRowPolicy {
+  static constexpr int RW = 1;
+  static constexpr int NOUT = 2;
+  static constexpr bool SELF = false;
+  using Tgt = ElemTgt<double>;
+  struct Acc {
+    double cphi, cpsi;
+  };
+  struct Args {
+    const double4_32a* tgt;
+    double* part;
+    PairConst<double> c;
+  };
+  __device__ static void load(const Args& a, int i, Tgt& t) {
+    double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
+    t = Tgt{g.x, g.y, g.z, v.x, v.y, v.z};
+  }
+  __device__ static void zero(Acc& acc) { acc.cphi = 0.0, acc.cpsi = 0.0; }
+  template <bool MASK>
+  __device__ static void pair(const Args& a, const Tgt& t, const double4_32a* r, bool, Acc& acc) {
+    const double4_32a A = r[0];
+    double dx = A.x - t.x, dy = A.y - t.y, dz = A.z - t.z;
+    double s, rr, e;
+    radial<false>(dx * dx + dy * dy + dz * dz, false, a.c, s, rr, e);
+    double t1 = e * (rr * a.c.kappa) + e;
+    double cj = t.nx * dx + t.ny * dy + t.nz * dz;
+    acc.cphi += A.w * (a.c.eps * t1 - 1.0) * cj * (s * s * s);
+    acc.cpsi += A.w * (1.0 - e) * s;
+  }
+  __device__ static void store(const Args& a, int out, int n_tgt, int i, const Acc& acc) {
+    a.part[(size_t)out + i] = acc.cphi;
+    a.part[(size_t)out + n_tgt + i] = acc.cpsi;
   }
 };
 
@@ -171,6 +212,7 @@ struct ReactionPolicy {
 // (G0(x_j, y) and dG0(x_j, y)/dnu_x) and its y-gradient.
 struct GradPolicy {
   static constexpr int RW = 3;
+  static constexpr int NOUT = 8;
   static constexpr bool SELF = false;
   using Tgt = PointTgt;
   struct Acc {
@@ -178,9 +220,7 @@ struct GradPolicy {
   };
   struct Args {
     const double4_32a* pts;
-    const double4_32a* rec;
-    double* part;  // [split][8][n_pts]
-    int n;
+    double* part;
     PairConst<double> c;
   };
   __device__ static void load(const Args& a, int k, Tgt& t) {
@@ -216,43 +256,46 @@ struct GradPolicy {
       acc.gb[m] += s3 * (pv[m] - fb * d[m]);
     }
   }
-  __device__ static void store(const Args& a, int split, int k, const Acc& acc) {
-    double* o = a.part + (size_t)split * 8 * a.n + k;
+  __device__ static void store(const Args& a, int out, int n_tgt, int k, const Acc& acc) {
+    double* o = a.part + (size_t)out + k;
     o[0] = acc.p;
-    o[(size_t)a.n] = acc.sb;
+    o[(size_t)n_tgt] = acc.sb;
     for (int m = 0; m < 3; ++m) {
-      o[(size_t)(2 + m) * a.n] = acc.ga[m];
-      o[(size_t)(5 + m) * a.n] = acc.gb[m];
+      o[(size_t)(2 + m) * n_tgt] = acc.ga[m];
+      o[(size_t)(5 + m) * n_tgt] = acc.gb[m];
     }
   }
 };
 
-// ------------------------------------------------------------------ tiled driver
-// grid = (n_tiles, n_splits).  CTA (x, y) handles targets
-// [x*NT*TPT, (x+1)*NT*TPT) (thread t owns x*NT*TPT + k*NT + t, k < TPT)
-// against sources [y*ns/S, (y+1)*ns/S) with S = n_splits, staged through
-// shared memory CH records at a time (the last chunk of a split may be short).
+// ------------------------------------------------------------------ item kernel
+// One CTA per work item (two int4):
+//   {tgt_off, n_tgt, t0, sys}  targets tgt_off + [t0, t0 + NT*TPT) of a system
+//                              with n_tgt targets (thread t owns t0 + k*NT + t)
+//   {src_off, s0, s1, out}     sources src_off + [s0, s1); partials at part[out]
+// The self pair (same local index) is masked only in source chunks that
+// overlap the item's own targets.
 template <class P, typename V4, int NT, int TPT, int CH>
-__global__ void __launch_bounds__(NT) k_tiled(typename P::Args a, int n_targets, int n_sources, int n_splits,
-                                              const V4* __restrict__ rec, const int* __restrict__ skip) {
+__global__ void __launch_bounds__(NT) k_items(typename P::Args a, const int4* __restrict__ items,
+                                              const V4* __restrict__ rec, const int* __restrict__ skip,
+                                              int skip_stride) {
   __shared__ V4 sh[CH * P::RW];
-  if (skipped(skip)) return;
-  const int t0 = blockIdx.x * NT * TPT;
+  const int4 I0 = items[2 * blockIdx.x], I1 = items[2 * blockIdx.x + 1];
+  const int tgt_off = I0.x, n_tgt = I0.y, t0 = I0.z, sys = I0.w;
+  const int src_off = I1.x, s0 = I1.y, s1 = I1.z, out = I1.w;
+  if (sys_skipped(skip, skip_stride, sys)) return;
   typename P::Tgt tg[TPT];
   typename P::Acc acc[TPT];
   int idx[TPT];
 #pragma unroll
   for (int k = 0; k < TPT; ++k) {
     idx[k] = t0 + k * NT + threadIdx.x;
-    P::load(a, min(idx[k], n_targets - 1), tg[k]);
+    P::load(a, tgt_off + min(idx[k], n_tgt - 1), tg[k]);
     P::zero(acc[k]);
   }
-  const int s0 = (int)((int64_t)blockIdx.y * n_sources / n_splits);
-  const int s1 = (int)((int64_t)(blockIdx.y + 1) * n_sources / n_splits);
   for (int j0 = s0; j0 < s1; j0 += CH) {
     const int cnt = min(CH, s1 - j0);
     __syncthreads();
-    const V4* src = rec + (size_t)j0 * P::RW;
+    const V4* src = rec + (size_t)(src_off + j0) * P::RW;
     for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
     __syncthreads();
     const bool diag = P::SELF && (j0 < t0 + NT * TPT) && (j0 + cnt > t0);
@@ -279,96 +322,209 @@ __global__ void __launch_bounds__(NT) k_tiled(typename P::Args a, int n_targets,
   }
 #pragma unroll
   for (int k = 0; k < TPT; ++k)
-    if (idx[k] < n_targets) P::store(a, blockIdx.y, idx[k], acc[k]);
+    if (idx[k] < n_tgt) P::store(a, out, n_tgt, idx[k], acc[k]);
 }
 
-// Source split count: every split gets the same number of sources (+-1), and
-// the CTA count fills whole waves of resident CTAs (slots = SMs x CTAs per SM)
-// as closely as possible, so that no SM idles while others finish a tail.
-PassTiling make_tiling(int64_t n_targets, int64_t n_sources, int targets_per_cta, int slots, int min_src) {
-  PassTiling t;
-  t.n_tiles = (int)((n_targets + targets_per_cta - 1) / targets_per_cta);
-  const int max_s = (int)std::max<int64_t>(1, std::min<int64_t>(n_sources / std::max(min_src, 1), 4096));
-  auto eff = [&](int sp) {
-    const long ctas = (long)t.n_tiles * sp;
-    const long waves = (ctas + slots - 1) / slots;
-    return (double)ctas / ((double)waves * slots);
+// ------------------------------------------------------------------ work lists
+// Per-system description of one pass: targets [tgt_off, tgt_off + n_tgt),
+// sources [src_off, src_off + n_src).
+struct PassSys {
+  int tgt_off, n_tgt, src_off, n_src;
+};
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+  return h;
+}
+
+// Build (or fetch) the work list of a pass.  Every system's sources are cut
+// into splits of about L sources; L is chosen so that the item count fills
+// whole waves of resident CTAs (slots = SMs x CTAs per SM) as closely as
+// possible, with at least min_src sources per split.  Items are ordered
+// largest system first.
+ItemPlan* plan_items(Surface* s, int pass_id, const std::vector<PassSys>& sys, int targets_per_cta, int slots,
+                     int min_src, int nout) {
+  uint64_t key = 0xcbf29ce484222325ull;
+  int hdr[4] = {pass_id, targets_per_cta, slots, min_src};
+  key = fnv(key, hdr, sizeof(hdr));
+  key = fnv(key, sys.data(), sys.size() * sizeof(PassSys));
+  auto it = s->plans.find(key);
+  if (it != s->plans.end()) return it->second.get();
+
+  const int K = (int)sys.size();
+  int n_src_max = 1;
+  for (auto& p : sys) n_src_max = std::max(n_src_max, p.n_src);
+  auto tiles_of = [&](const PassSys& p) { return (p.n_tgt + targets_per_cta - 1) / targets_per_cta; };
+  auto splits_of = [&](const PassSys& p, int L) { return std::max(1, (p.n_src + L - 1) / L); };
+  auto count = [&](int L) {
+    long c = 0;
+    for (auto& p : sys) c += (long)tiles_of(p) * splits_of(p, L);
+    return c;
   };
+  auto eff = [&](int L) {
+    const long c = count(L);
+    const long waves = (c + slots - 1) / slots;
+    return (double)c / ((double)waves * slots);
+  };
+  const int max_s = std::max(1, std::min(n_src_max / std::max(min_src, 1), 4096));
   double best = 0.0;
-  for (int sp = 1; sp <= max_s; ++sp) best = std::max(best, eff(sp));
-  int best_s = 1;
-  for (int sp = 1; sp <= max_s; ++sp)
-    if (eff(sp) >= 0.98 * best) {  // the fewest splits within 2 % of the best fill
-      best_s = sp;
+  for (int S = 1; S <= max_s; ++S) best = std::max(best, eff((n_src_max + S - 1) / S));
+  int L = n_src_max;
+  for (int S = 1; S <= max_s; ++S) {
+    const int l = (n_src_max + S - 1) / S;
+    if (eff(l) >= 0.98 * best) {  // the fewest splits within 2 % of the best fill
+      L = l;
       break;
     }
-  t.n_splits = best_s;
-  return t;
+  }
+
+  auto plan = std::make_unique<ItemPlan>();
+  std::vector<int> order(K);
+  for (int k = 0; k < K; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (long)sys[x].n_tgt * sys[x].n_src > (long)sys[y].n_tgt * sys[y].n_src;
+  });
+  std::vector<int64_t> sys_out(K);
+  std::vector<int> sys_splits(K);
+  int64_t out = 0;
+  for (int k = 0; k < K; ++k) {
+    sys_out[k] = out;
+    sys_splits[k] = splits_of(sys[k], L);
+    out += (int64_t)sys_splits[k] * nout * sys[k].n_tgt;
+  }
+  BIPB_REQUIRE(out < ((int64_t)1 << 31), "pass too large for one work list");
+  plan->part_len = out;
+  std::vector<int4> items;
+  for (int k : order) {
+    const PassSys& p = sys[k];
+    const int S = sys_splits[k];
+    for (int t = 0; t < tiles_of(p); ++t)
+      for (int sp = 0; sp < S; ++sp) {
+        const int s0 = (int)((int64_t)sp * p.n_src / S), s1 = (int)((int64_t)(sp + 1) * p.n_src / S);
+        items.push_back(make_int4(p.tgt_off, p.n_tgt, t * targets_per_cta, k));
+        items.push_back(make_int4(p.src_off, s0, s1, (int)(sys_out[k] + (int64_t)sp * nout * p.n_tgt)));
+      }
+  }
+  plan->n_items = (int)(items.size() / 2);
+  // per-system table for the reductions: {n_tgt, splits, out offset, unused}
+  std::vector<int4> tab(K);
+  for (int k = 0; k < K; ++k) tab[k] = make_int4(sys[k].n_tgt, sys_splits[k], (int)sys_out[k], 0);
+  plan->items.ensure(items.size());
+  plan->tab.ensure(K);
+  BIPB_CUDA(cudaMemcpyAsync(plan->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, tab.data(), K * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));  // the host vectors go out of scope
+  ++s->alloc_gen;
+  ItemPlan* raw = plan.get();
+  s->plans[key] = std::move(plan);
+  return raw;
+}
+
+// Resident CTAs per SM of one item-kernel instantiation (queried once).
+template <class P, typename V4, int NT, int TPT, int CH>
+int items_occupancy() {
+  static int occ = [] {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_items<P, V4, NT, TPT, CH>, NT, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      o = 1;
+    }
+    return std::max(o, 1);
+  }();
+  return occ;
+}
+
+template <class P, typename V4, int NT, int TPT, int CH>
+ItemPlan* plan_pass(Surface* s, int pass_id, const std::vector<PassSys>& sys, int min_src) {
+  return plan_items(s, pass_id, sys, NT * TPT, s->num_sms * items_occupancy<P, V4, NT, TPT, CH>(), min_src,
+                    P::NOUT);
+}
+
+template <class P, typename V4, int NT, int TPT, int CH>
+void launch_items(Surface* s, int kind, const ItemPlan* plan, const typename P::Args& a, const V4* rec,
+                  const int* skip, int skip_stride) {
+  TimedLaunch tlaunch(s, kind);
+  k_items<P, V4, NT, TPT, CH><<<plan->n_items, NT, 0, s->stream>>>(a, plan->items.p, rec, skip, skip_stride);
+  BIPB_LAUNCHED(s);
 }
 
 // ------------------------------------------------------------------ pack / reduce
+// grid = (blocks over the largest system, K).  lay[k] = {geo_off, n, vec_off, chg_off}.
 // Forward record of element j from u = [phi; psi]: (x, a = ds psi), (m = ds phi n, 0);
 // transposed record from w = [wphi; wpsi]: (x, wphi), (p = wpsi n, 0).
+// Records of system k start at vec_off / 2.
 template <typename V4, typename T>
-__global__ void k_pack(int n, int n_pad, bool transpose, const double4_32a* __restrict__ geo,
-                       const double4_32a* __restrict__ nrm, const double* __restrict__ u, V4* __restrict__ rec,
-                       const int* __restrict__ skip) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_pad || skipped(skip)) return;
+__global__ void k_pack(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
+                       const double* __restrict__ u, V4* __restrict__ rec, const int* __restrict__ skip,
+                       int skip_stride) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.y || sys_skipped(skip, skip_stride, k)) return;
+  const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
+  const double* uk = u + L.z;
+  const double phi = uk[j], psi = uk[L.y + j];
+  const double sc = transpose ? phi : g.w * psi;  // 4th slot
+  const double f = transpose ? psi : g.w * phi;   // multiplies the normal
   V4 r0, r1;
-  if (j < n) {
-    double4_32a g = geo[j], v = nrm[j];
-    double phi = u[j], psi = u[n + j];
-    double sc = transpose ? phi : g.w * psi;     // 4th slot
-    double f = transpose ? psi : g.w * phi;      // multiplies the normal
-    r0.x = (T)g.x, r0.y = (T)g.y, r0.z = (T)g.z, r0.w = (T)sc;
-    r1.x = (T)(f * v.x), r1.y = (T)(f * v.y), r1.z = (T)(f * v.z), r1.w = (T)0;
-  } else {
-    r0.x = r0.y = r0.z = (T)kFar, r0.w = (T)0;
-    r1.x = r1.y = r1.z = r1.w = (T)0;
-  }
-  rec[2 * j] = r0;
-  rec[2 * j + 1] = r1;
+  r0.x = (T)g.x, r0.y = (T)g.y, r0.z = (T)g.z, r0.w = (T)sc;
+  r1.x = (T)(f * v.x), r1.y = (T)(f * v.y), r1.z = (T)(f * v.z), r1.w = (T)0;
+  const size_t o = (size_t)(L.z / 2 + j);
+  rec[2 * o] = r0;
+  rec[2 * o + 1] = r1;
 }
 
-// y_i = diag * u_i - (1/(4 pi)) * scale_i * sum_s part[s][i], i < 2n,
+// y_i = diag * u_i - (1/(4 pi)) * scale_i * sum over splits, i < 2n of each system;
 // diag = 1/2 (1 + eps) on the phi half and 1/2 (1 + 1/eps) on the psi half;
 // scale_i = area of element (i mod n) for the transpose, 1 otherwise.
 template <typename PT>
-__global__ void k_reduce_matvec(int n, int n_splits, const PT* __restrict__ part,
-                                const double* __restrict__ u, double* __restrict__ y, double d_phi,
-                                double d_psi, const double4_32a* __restrict__ geo_for_area,
-                                const int* __restrict__ skip) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * n || skipped(skip)) return;
+__global__ void k_reduce_matvec(const int4* __restrict__ lay, const int4* __restrict__ tab,
+                                const PT* __restrict__ part, const double* __restrict__ u, double* __restrict__ y,
+                                double d_phi, double d_psi, const double4_32a* __restrict__ tgt64_for_area,
+                                const int* __restrict__ skip, int skip_stride) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k], T = tab[k];
+  const int n = L.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n || sys_skipped(skip, skip_stride, k)) return;
   double acc = 0.0;
-  for (int sp = 0; sp < n_splits; ++sp) acc += (double)part[(size_t)sp * 2 * n + i];
-  int e = i < n ? i : i - n;
-  double sc = geo_for_area ? geo_for_area[e].w : 1.0;
-  y[i] = (i < n ? d_phi : d_psi) * u[i] - kInv4Pi * sc * acc;
+  for (int sp = 0; sp < T.y; ++sp) acc += (double)part[(size_t)T.z + (size_t)sp * 2 * n + i];
+  const int e = i < n ? i : i - n;
+  const double sc = tgt64_for_area ? tgt64_for_area[2 * (L.x + e)].w : 1.0;
+  y[L.z + i] = (i < n ? d_phi : d_psi) * u[L.z + i] - kInv4Pi * sc * acc;
 }
 
-__global__ void k_reduce_source(int n, int n_splits, const double* __restrict__ part, double scale,
-                                double* __restrict__ b) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// b of every system: S1, S2 times 1/(4 pi eps_in)
+__global__ void k_reduce_source(const int4* __restrict__ lay, const int4* __restrict__ tab,
+                                const double* __restrict__ part, double scale, double* __restrict__ b) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k], T = tab[k];
+  const int n = L.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * n) return;
   double acc = 0.0;
-  for (int sp = 0; sp < n_splits; ++sp) acc += part[(size_t)sp * 2 * n + i];
-  b[i] = scale * acc;
+  for (int sp = 0; sp < T.y; ++sp) acc += part[(size_t)T.z + (size_t)sp * 2 * n + i];
+  b[L.z + i] = scale * acc;
 }
 
-// phi_reac_k = (1/(4 pi)) sum_s part; E = KCAL/2 sum_k q_k phi_reac_k (one block, fixed order).
-__global__ void k_reduce_reaction(int nc, int n_splits, const double* __restrict__ part,
-                                  const double4_32a* __restrict__ pts, double* __restrict__ phi_reac,
-                                  double* __restrict__ e_out) {
+// One block per system: phi_reac_k = (1/(4 pi)) sum over splits;
+// E = KCAL/2 sum_k q_k phi_reac_k in a fixed order.
+__global__ void k_reduce_reaction(const int4* __restrict__ tab, const int4* __restrict__ lay,
+                                  const double* __restrict__ part, const double4_32a* __restrict__ chg,
+                                  double* __restrict__ phi_reac, double* __restrict__ e_out) {
   __shared__ double red[1024];
+  const int k = blockIdx.x;
+  const int4 T = tab[k];
+  const int nc = T.x, c0 = lay[k].w;
   double local = 0.0;
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+  for (int q = threadIdx.x; q < nc; q += blockDim.x) {
     double acc = 0.0;
-    for (int sp = 0; sp < n_splits; ++sp) acc += part[(size_t)sp * nc + k];
+    for (int sp = 0; sp < T.y; ++sp) acc += part[(size_t)T.z + (size_t)sp * nc + q];
     acc *= kInv4Pi;
-    if (phi_reac) phi_reac[k] = acc;
-    local += pts[k].w * acc;
+    if (phi_reac) phi_reac[c0 + q] = acc;
+    local += chg[c0 + q].w * acc;
   }
   red[threadIdx.x] = local;
   __syncthreads();
@@ -376,92 +532,56 @@ __global__ void k_reduce_reaction(int nc, int n_splits, const double* __restrict
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0 && e_out) *e_out = 0.5 * kKcal * red[0];
+  if (threadIdx.x == 0 && e_out) e_out[k] = 0.5 * kKcal * red[0];
 }
 
-__global__ void k_energy_row_reduce(int n, int n_splits, const double* __restrict__ part,
-                                    const double4_32a* __restrict__ geo, double* __restrict__ c) {
-  // part[s][0][j] = sum_k q_k 4pi K2(y_k, x_j) with n_j, part[s][1][j] = sum_k q_k 4pi K1(y_k, x_j)
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_energy_row_reduce(const int4* __restrict__ lay, const int4* __restrict__ tab,
+                                    const double* __restrict__ part, const double4_32a* __restrict__ tgt64,
+                                    double* __restrict__ c) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k], T = tab[k];
+  const int n = L.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * n) return;
   double acc = 0.0;
-  for (int sp = 0; sp < n_splits; ++sp) acc += part[(size_t)sp * 2 * n + i];
-  int e = i < n ? i : i - n;
-  c[i] = geo[e].w * kInv4Pi * acc;
+  for (int sp = 0; sp < T.y; ++sp) acc += part[(size_t)T.z + (size_t)sp * 2 * n + i];
+  const int e = i < n ? i : i - n;
+  c[L.z + i] = tgt64[2 * (L.x + e)].w * kInv4Pi * acc;
 }
 
-// Energy row c: target element j, source charge k (record (y_k, q_k)), d = y_k - x_j:
-//   4 pi K2(y_k, x_j) = (eps t - 1) (n_j.d) s^3,  4 pi K1(y_k, x_j) = (1 - e) s
-struct EnergyRowPolicy {
-  static constexpr int RW = 1;
-  static constexpr bool SELF = false;
-  using Tgt = ElemTgt<double>;
-  struct Acc {
-    double cphi, cpsi;
-  };
-  struct Args {
-    const double4_32a* geo;
-    const double4_32a* nrm;
-    double* part;
-    int n;
-    PairConst<double> c;
-  };
-  __device__ static void load(const Args& a, int i, Tgt& t) {
-    double4_32a g = a.geo[i], v = a.nrm[i];
-    t = Tgt{g.x, g.y, g.z, v.x, v.y, v.z};
-  }
-  __device__ static void zero(Acc& acc) { acc.cphi = 0.0, acc.cpsi = 0.0; }
-  template <bool MASK>
-  __device__ static void pair(const Args& a, const Tgt& t, const double4_32a* r, bool, Acc& acc) {
-    const double4_32a A = r[0];
-    double dx = A.x - t.x, dy = A.y - t.y, dz = A.z - t.z;
-    double s, rr, e;
-    radial<false>(dx * dx + dy * dy + dz * dz, false, a.c, s, rr, e);
-    double t1 = e * (rr * a.c.kappa) + e;
-    double cj = t.nx * dx + t.ny * dy + t.nz * dz;
-    acc.cphi += A.w * (a.c.eps * t1 - 1.0) * cj * (s * s * s);
-    acc.cpsi += A.w * (1.0 - e) * s;
-  }
-  __device__ static void store(const Args& a, int split, int i, const Acc& acc) {
-    a.part[(size_t)split * 2 * a.n + i] = acc.cphi;
-    a.part[(size_t)split * 2 * a.n + a.n + i] = acc.cpsi;
-  }
-};
-
-__global__ void k_pack_grad(int n, int n_pad, const double4_32a* __restrict__ geo,
-                            const double4_32a* __restrict__ nrm, const double* __restrict__ u,
-                            const double* __restrict__ lam, double4_32a* __restrict__ rec) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n_pad) return;
-  double4_32a r0, r1, r2;
-  if (j < n) {
-    double4_32a g = geo[j], v = nrm[j];
-    double aphi = g.w * u[j];
-    r0 = make_double4_32a(g.x, g.y, g.z, g.w * u[n + j]);
-    r1 = make_double4_32a(aphi * v.x, aphi * v.y, aphi * v.z, lam[j]);
-    double lp = lam[n + j];
-    r2 = make_double4_32a(lp * v.x, lp * v.y, lp * v.z, 0.0);
-  } else {
-    r0 = make_double4_32a(kFar, kFar, kFar, 0.0);
-    r1 = make_double4_32a(0.0, 0.0, 0.0, 0.0);
-    r2 = r1;
-  }
-  rec[3 * j] = r0;
-  rec[3 * j + 1] = r1;
-  rec[3 * j + 2] = r2;
+// Gradient records of every system (3 per element, at vec_off / 2).
+__global__ void k_pack_grad(const int4* __restrict__ lay, const double4_32a* __restrict__ tgt64,
+                            const double* __restrict__ u, const double* __restrict__ lam,
+                            double4_32a* __restrict__ rec) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.y) return;
+  const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
+  const double* uk = u + L.z;
+  const double* lk = lam + L.z;
+  const double aphi = g.w * uk[j];
+  const size_t o = (size_t)(L.z / 2 + j);
+  rec[3 * o] = make_double4_32a(g.x, g.y, g.z, g.w * uk[L.y + j]);
+  rec[3 * o + 1] = make_double4_32a(aphi * v.x, aphi * v.y, aphi * v.z, lk[j]);
+  const double lp = lk[L.y + j];
+  rec[3 * o + 2] = make_double4_32a(lp * v.x, lp * v.y, lp * v.z, 0.0);
 }
 
-__global__ void k_reduce_grad(int nc, int n_splits, const double* __restrict__ part,
-                              const double4_32a* __restrict__ pts, double inv_eps_in,
-                              double* __restrict__ dq, double* __restrict__ dy) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nc) return;
+__global__ void k_reduce_grad(const int4* __restrict__ tab, const int4* __restrict__ lay,
+                              const double* __restrict__ part, const double4_32a* __restrict__ chg,
+                              double inv_eps_in, double* __restrict__ dq, double* __restrict__ dy) {
+  const int k = blockIdx.y;
+  const int4 T = tab[k];
+  const int nc = T.x, c0 = lay[k].w;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nc) return;
   double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int sp = 0; sp < n_splits; ++sp)
-    for (int c = 0; c < 8; ++c) v[c] += part[(size_t)sp * 8 * nc + (size_t)c * nc + k];
-  double q = pts[k].w;
-  dq[k] = 0.5 * kInv4Pi * (v[0] + inv_eps_in * v[1]);
-  for (int m = 0; m < 3; ++m) dy[3 * k + m] = 0.5 * q * kInv4Pi * (v[2 + m] + inv_eps_in * v[5 + m]);
+  for (int sp = 0; sp < T.y; ++sp)
+    for (int c = 0; c < 8; ++c) v[c] += part[(size_t)T.z + (size_t)sp * 8 * nc + (size_t)c * nc + q];
+  const double qq = chg[c0 + q].w;
+  dq[c0 + q] = 0.5 * kInv4Pi * (v[0] + inv_eps_in * v[1]);
+  for (int m = 0; m < 3; ++m) dy[3 * (c0 + q) + m] = 0.5 * qq * kInv4Pi * (v[2 + m] + inv_eps_in * v[5 + m]);
 }
 
 template <typename T>
@@ -475,107 +595,127 @@ PairConst<T> pair_const(const bipb_medium& m) {
   return c;
 }
 
-int blocks_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+int blocks_for(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
-__global__ void k_charge_records(int nc, int nc_pad, const double4_32a* __restrict__ chg,
-                                 double4_32a* __restrict__ rec) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nc_pad) return;
-  rec[k] = k < nc ? chg[k] : make_double4_32a(kFar, kFar, kFar, 0.0);
+enum PassId { kPassMv64 = 1, kPassMv64T, kPassMv32 = 16, kPassMv32T = 32, kPassSource = 48, kPassReaction, kPassRow,
+              kPassGrad };
+
+std::vector<PassSys> matvec_sys(const SysLayout& L) {
+  std::vector<PassSys> v(L.K);
+  for (int k = 0; k < L.K; ++k) v[k] = PassSys{L.geo_off[k], L.n[k], L.vec_off[k] / 2, L.n[k]};
+  return v;
 }
 
-// Resident CTAs per SM of one tiled-kernel instantiation (queried once).
-template <class P, typename V4, int NT, int TPT, int CH>
-int tiled_occupancy() {
-  static int occ = [] {
-    int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tiled<P, V4, NT, TPT, CH>, NT, 0) != cudaSuccess) {
-      (void)cudaGetLastError();
-      o = 1;
-    }
-    return std::max(o, 1);
-  }();
-  return occ;
-}
-
-template <class P, typename V4, int NT, int TPT, int CH>
-PassTiling plan_tiled(Surface* s, int64_t n_targets, int64_t n_sources, int min_src) {
-  return make_tiling(n_targets, n_sources, NT * TPT, s->num_sms * tiled_occupancy<P, V4, NT, TPT, CH>(), min_src);
-}
-
-// Launch of one tiled pass with a tiling from plan_tiled.
-template <class P, typename V4, int NT, int TPT, int CH>
-void launch_tiled(Surface* s, int kind, const PassTiling& tl, const typename P::Args& a, int64_t n_targets,
-                  int64_t n_sources, const V4* rec, const int* skip) {
-  dim3 grid(tl.n_tiles, tl.n_splits);
-  TimedLaunch tlaunch(s, kind);
-  k_tiled<P, V4, NT, TPT, CH><<<grid, NT, 0, s->stream>>>(a, (int)n_targets, (int)n_sources, tl.n_splits, rec,
-                                                          skip);
-  BIPB_LAUNCHED(s);
-}
-
-// FP32 forward / transpose mat-vec variants (the autotuner picks one).
+// FP32 forward / transpose mat-vec (one variant of the autotuned tiling).
 template <bool TRANS, int NT, int TPT, int CH>
-void run_matvec32(Surface* s, const PairConst<float>& c, const double* u, double* y, double dphi,
-                  double dpsi, const int* skip) {
-  const int n = (int)s->n;
+void run_matvec32(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y,
+                  double dphi, double dpsi, const int* skip, int skip_stride) {
   using P = MatvecPolicy<float, TRANS>;
-  PassTiling tl = plan_tiled<P, float4, NT, TPT, CH>(s, n, n, CH);
-  const int n_pad = n;
-  s->grow(s->rec32, (size_t)2 * n_pad);
-  s->grow(s->part32, (size_t)tl.n_splits * 2 * n);
-  k_pack<float4, float><<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(
-      n, n_pad, TRANS, s->geo64.p, s->nrm64.p, u, s->rec32.p, skip);
+  ItemPlan* plan =
+      plan_pass<P, float4, NT, TPT, CH>(s, (TRANS ? kPassMv32T : kPassMv32) + s->mv32_variant, matvec_sys(L), CH);
+  s->grow(s->rec32, (size_t)L.len);  // 2 records per element = one per unknown
+  s->grow(s->part32, (size_t)plan->part_len);
+  const int4* lay = s->lay_dev(L);
+  k_pack<float4, float><<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, TRANS, s->tgt64.p, u, s->rec32.p, skip, skip_stride);
   BIPB_LAUNCHED(s);
-  typename P::Args a{s->tgt32.p, s->rec32.p, s->part32.p, n, c};
-  launch_tiled<P, float4, NT, TPT, CH>(s, TRANS ? kTMv32T : kTMv32, tl, a, n, n, s->rec32.p, skip);
-  k_reduce_matvec<float><<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(
-      n, tl.n_splits, s->part32.p, u, y, dphi, dpsi, TRANS ? s->geo64.p : nullptr, skip);
+  typename P::Args a{s->tgt32.p, s->part32.p, c};
+  launch_items<P, float4, NT, TPT, CH>(s, TRANS ? kTMv32T : kTMv32, plan, a, s->rec32.p, skip, skip_stride);
+  k_reduce_matvec<float><<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, plan->tab.p, s->part32.p, u, y, dphi, dpsi, TRANS ? s->tgt64.p : nullptr, skip, skip_stride);
   BIPB_LAUNCHED(s);
 }
 
 template <bool TRANS>
-void run_matvec64(Surface* s, const PairConst<double>& c, const double* u, double* y, double dphi,
-                  double dpsi, const int* skip) {
+void run_matvec64(Surface* s, const SysLayout& L, const PairConst<double>& c, const double* u, double* y,
+                  double dphi, double dpsi, const int* skip, int skip_stride) {
   constexpr int NT = 128, TPT = 2, CH = 64;
-  const int n = (int)s->n;
   using P = MatvecPolicy<double, TRANS>;
-  PassTiling tl = plan_tiled<P, double4_32a, NT, TPT, CH>(s, n, n, CH);
-  const int n_pad = n;
-  s->grow(s->rec64, (size_t)2 * n_pad);
-  s->grow(s->part64, (size_t)tl.n_splits * 2 * n);
-  k_pack<double4_32a, double><<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(
-      n, n_pad, TRANS, s->geo64.p, s->nrm64.p, u, s->rec64.p, skip);
+  ItemPlan* plan = plan_pass<P, double4_32a, NT, TPT, CH>(s, TRANS ? kPassMv64T : kPassMv64, matvec_sys(L), CH);
+  s->grow(s->rec64, (size_t)L.len);
+  s->grow(s->part64, (size_t)plan->part_len);
+  const int4* lay = s->lay_dev(L);
+  k_pack<double4_32a, double><<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, TRANS, s->tgt64.p, u, s->rec64.p, skip, skip_stride);
   BIPB_LAUNCHED(s);
-  typename P::Args a{s->tgt64.p, s->rec64.p, s->part64.p, n, c};
-  launch_tiled<P, double4_32a, NT, TPT, CH>(s, TRANS ? kTMv64T : kTMv64, tl, a, n, n, s->rec64.p, skip);
-  k_reduce_matvec<double><<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(
-      n, tl.n_splits, s->part64.p, u, y, dphi, dpsi, TRANS ? s->geo64.p : nullptr, skip);
+  typename P::Args a{s->tgt64.p, s->part64.p, c};
+  launch_items<P, double4_32a, NT, TPT, CH>(s, TRANS ? kTMv64T : kTMv64, plan, a, s->rec64.p, skip, skip_stride);
+  k_reduce_matvec<double><<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, plan->tab.p, s->part64.p, u, y, dphi, dpsi, TRANS ? s->tgt64.p : nullptr, skip, skip_stride);
   BIPB_LAUNCHED(s);
+}
+
+__global__ void k_fill_test_vector(int len, double* u) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) u[i] = 0.5 + 0.25 * sin(0.37 * i) + (i & 7) * 0.01;
 }
 
 }  // namespace
 
-void matvec(Surface* s, const bipb_medium& m, int precision, bool transpose, const double* u, double* y,
-            const int* skip) {
+// ------------------------------------------------------------------ layouts
+SysLayout make_layout(const std::vector<int>& geo_off, const std::vector<int>& n, const std::vector<int>& chg_off,
+                      const std::vector<int>& nc) {
+  SysLayout L;
+  L.K = (int)n.size();
+  L.geo_off = geo_off;
+  L.n = n;
+  L.chg_off = chg_off;
+  L.nc = nc;
+  L.vec_off.resize(L.K);
+  int64_t off = 0;
+  for (int k = 0; k < L.K; ++k) {
+    L.vec_off[k] = (int)off;
+    off += 2 * (int64_t)n[k];
+    L.max_n = std::max(L.max_n, n[k]);
+    L.max_nc = std::max(L.max_nc, nc[k]);
+  }
+  BIPB_REQUIRE(off < ((int64_t)1 << 31), "too many unknowns in one batch");
+  L.len = off;
+  uint64_t h = 0xcbf29ce484222325ull;
+  h = fnv(h, L.geo_off.data(), L.K * sizeof(int));
+  h = fnv(h, L.n.data(), L.K * sizeof(int));
+  h = fnv(h, L.chg_off.data(), L.K * sizeof(int));
+  h = fnv(h, L.nc.data(), L.K * sizeof(int));
+  L.key = h;
+  return L;
+}
+
+const int4* Surface::lay_dev(const SysLayout& L) {
+  auto it = layouts.find(L.key);
+  if (it != layouts.end()) return it->second->p;
+  std::vector<int4> tab(L.K);
+  for (int k = 0; k < L.K; ++k) tab[k] = make_int4(L.geo_off[k], L.n[k], L.vec_off[k], L.chg_off[k]);
+  auto d = std::make_unique<DevBuf<int4>>();
+  d->ensure(L.K);
+  BIPB_CUDA(cudaMemcpyAsync(d->p, tab.data(), L.K * sizeof(int4), cudaMemcpyHostToDevice, stream));
+  BIPB_CUDA(cudaStreamSynchronize(stream));
+  ++alloc_gen;
+  const int4* p = d->p;
+  layouts[L.key] = std::move(d);
+  return p;
+}
+
+// ------------------------------------------------------------------ passes
+void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision, bool transpose, const double* u,
+            double* y, const int* skip, int skip_stride) {
   const double eps = m.eps_out / m.eps_in;
   const double dphi = 0.5 * (1.0 + eps), dpsi = 0.5 * (1.0 + 1.0 / eps);
   if (precision == BIPB_FP64) {
     PairConst<double> c = pair_const<double>(m);
     if (transpose)
-      run_matvec64<true>(s, c, u, y, dphi, dpsi, skip);
+      run_matvec64<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     else
-      run_matvec64<false>(s, c, u, y, dphi, dpsi, skip);
+      run_matvec64<false>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     return;
   }
   PairConst<float> c = pair_const<float>(m);
   switch (s->mv32_variant) {
-#define BIPB_MV32(I_, NT_, TPT_, CH_)                                    \
-  case I_:                                                               \
-    if (transpose)                                                       \
-      run_matvec32<true, NT_, TPT_, CH_>(s, c, u, y, dphi, dpsi, skip);  \
-    else                                                                 \
-      run_matvec32<false, NT_, TPT_, CH_>(s, c, u, y, dphi, dpsi, skip); \
+#define BIPB_MV32(I_, NT_, TPT_, CH_)                                                      \
+  case I_:                                                                                 \
+    if (transpose)                                                                         \
+      run_matvec32<true, NT_, TPT_, CH_>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);    \
+    else                                                                                   \
+      run_matvec32<false, NT_, TPT_, CH_>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);   \
     return;
     BIPB_MV32(0, 256, 2, 128)
     BIPB_MV32(1, 256, 1, 128)
@@ -590,15 +730,8 @@ void matvec(Surface* s, const bipb_medium& m, int precision, bool transpose, con
   }
 }
 
-namespace {
-__global__ void k_fill_test_vector(int len, double* u) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < len) u[i] = 0.5 + 0.25 * sin(0.37 * i) + (i & 7) * 0.01;
-}
-}  // namespace
-
-int autotune_matvec32(Surface* s, const bipb_medium& m, int reps, double* best_ms) {
-  const int len = (int)(2 * s->n);
+int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int reps, double* best_ms) {
+  const int len = (int)L.len;
   DevBuf<double> u, y;
   u.ensure(len);
   y.ensure(len);
@@ -614,9 +747,9 @@ int autotune_matvec32(Surface* s, const bipb_medium& m, int reps, double* best_m
   try {
     for (int v = 0; v < kNumMv32Variants; ++v) {
       s->mv32_variant = v;
-      matvec(s, m, BIPB_FP32, false, u.p, y.p, nullptr);  // warm-up (and buffer growth)
+      matvec(s, L, m, BIPB_FP32, false, u.p, y.p, nullptr, 0);  // warm-up (and buffer growth)
       BIPB_CUDA(cudaEventRecord(a, s->stream));
-      for (int r = 0; r < reps; ++r) matvec(s, m, BIPB_FP32, false, u.p, y.p, nullptr);
+      for (int r = 0; r < reps; ++r) matvec(s, L, m, BIPB_FP32, false, u.p, y.p, nullptr, 0);
       BIPB_CUDA(cudaEventRecord(b, s->stream));
       BIPB_CUDA(cudaEventSynchronize(b));
       float ms = 0.f;
@@ -637,74 +770,65 @@ int autotune_matvec32(Surface* s, const bipb_medium& m, int reps, double* best_m
   return best;
 }
 
-void source_pass(Surface* s, const bipb_medium& m, int r, double* b) {
+void source_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* b) {
   constexpr int NT = 128, TPT = 1, CH = 64;
-  const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<SourcePolicy, double4_32a, NT, TPT, CH>(s, n, nc, CH);
-  const int nc_pad = nc;
-  s->grow(s->rec64, (size_t)nc_pad);
-  k_charge_records<<<blocks_for(nc_pad, 256), 256, 0, s->stream>>>(nc, nc_pad, s->chg.p + (size_t)r * nc,
-                                                                   s->rec64.p);
-  BIPB_LAUNCHED(s);
-  s->grow(s->part64, (size_t)tl.n_splits * 2 * n);
-  SourcePolicy::Args a{s->geo64.p, s->nrm64.p, s->rec64.p, s->part64.p, n};
-  launch_tiled<SourcePolicy, double4_32a, NT, TPT, CH>(s, kTSource, tl, a, n, nc, s->rec64.p, nullptr);
-  k_reduce_source<<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(n, tl.n_splits, s->part64.p,
-                                                                 kInv4Pi / m.eps_in, b);
+  std::vector<PassSys> sys(L.K);
+  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.geo_off[k], L.n[k], L.chg_off[k], L.nc[k]};
+  ItemPlan* plan = plan_pass<SourcePolicy, double4_32a, NT, TPT, CH>(s, kPassSource, sys, CH);
+  s->grow(s->part64, (size_t)plan->part_len);
+  SourcePolicy::Args a{s->tgt64.p, s->part64.p};
+  launch_items<SourcePolicy, double4_32a, NT, TPT, CH>(s, kTSource, plan, a, s->chg.p, nullptr, 0);
+  k_reduce_source<<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      s->lay_dev(L), plan->tab.p, s->part64.p, kInv4Pi / m.eps_in, b);
   BIPB_LAUNCHED(s);
 }
 
-void reaction_pass(Surface* s, const bipb_medium& m, int r, const double* u, double* phi_reac,
+void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, double* phi_reac,
                    double* e_out) {
   constexpr int NT = 128, TPT = 1, CH = 64;
-  const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<ReactionPolicy, double4_32a, NT, TPT, CH>(s, nc, n, CH);
-  const int n_pad = n;
-  s->grow(s->rec64, (size_t)2 * n_pad);
-  k_pack<double4_32a, double><<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(
-      n, n_pad, false, s->geo64.p, s->nrm64.p, u, s->rec64.p, nullptr);
+  std::vector<PassSys> sys(L.K);
+  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.chg_off[k], L.nc[k], L.vec_off[k] / 2, L.n[k]};
+  ItemPlan* plan = plan_pass<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kPassReaction, sys, CH);
+  s->grow(s->rec64, (size_t)L.len);
+  s->grow(s->part64, (size_t)plan->part_len);
+  const int4* lay = s->lay_dev(L);
+  k_pack<double4_32a, double><<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, false, s->tgt64.p, u, s->rec64.p, nullptr, 0);
   BIPB_LAUNCHED(s);
-  s->grow(s->part64, (size_t)tl.n_splits * nc);
-  ReactionPolicy::Args a{s->chg.p + (size_t)r * nc, s->rec64.p, s->part64.p, nc, pair_const<double>(m)};
-  launch_tiled<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kTReaction, tl, a, nc, n, s->rec64.p, nullptr);
-  k_reduce_reaction<<<1, 1024, 0, s->stream>>>(nc, tl.n_splits, s->part64.p, s->chg.p + (size_t)r * nc,
-                                               phi_reac, e_out);
+  ReactionPolicy::Args a{s->chg.p, s->part64.p, pair_const<double>(m)};
+  launch_items<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kTReaction, plan, a, s->rec64.p, nullptr, 0);
+  k_reduce_reaction<<<L.K, 1024, 0, s->stream>>>(plan->tab.p, lay, s->part64.p, s->chg.p, phi_reac, e_out);
   BIPB_LAUNCHED(s);
 }
 
-void energy_row_pass(Surface* s, const bipb_medium& m, int r, double* c) {
+void energy_row_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* c) {
   constexpr int NT = 128, TPT = 1, CH = 64;
-  const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, n, nc, CH);
-  const int nc_pad = nc;
-  s->grow(s->rec64, (size_t)nc_pad);
-  k_charge_records<<<blocks_for(nc_pad, 256), 256, 0, s->stream>>>(nc, nc_pad, s->chg.p + (size_t)r * nc,
-                                                                   s->rec64.p);
-  BIPB_LAUNCHED(s);
-  s->grow(s->part64, (size_t)tl.n_splits * 2 * n);
-  EnergyRowPolicy::Args a{s->geo64.p, s->nrm64.p, s->part64.p, n, pair_const<double>(m)};
-  launch_tiled<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kTRow, tl, a, n, nc, s->rec64.p, nullptr);
-  k_energy_row_reduce<<<blocks_for(2 * n, 256), 256, 0, s->stream>>>(n, tl.n_splits, s->part64.p,
-                                                                      s->geo64.p, c);
+  std::vector<PassSys> sys(L.K);
+  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.geo_off[k], L.n[k], L.chg_off[k], L.nc[k]};
+  ItemPlan* plan = plan_pass<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kPassRow, sys, CH);
+  s->grow(s->part64, (size_t)plan->part_len);
+  EnergyRowPolicy::Args a{s->tgt64.p, s->part64.p, pair_const<double>(m)};
+  launch_items<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kTRow, plan, a, s->chg.p, nullptr, 0);
+  k_energy_row_reduce<<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      s->lay_dev(L), plan->tab.p, s->part64.p, s->tgt64.p, c);
   BIPB_LAUNCHED(s);
 }
 
-void grad_pass(Surface* s, const bipb_medium& m, int r, const double* u, const double* lam, double* dq,
+void grad_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, const double* lam, double* dq,
                double* dy) {
   constexpr int NT = 128, TPT = 1, CH = 32;
-  const int n = (int)s->n, nc = (int)s->nc;
-  PassTiling tl = plan_tiled<GradPolicy, double4_32a, NT, TPT, CH>(s, nc, n, CH);
-  const int n_pad = n;
-  s->grow(s->rec64, (size_t)3 * n_pad);
-  k_pack_grad<<<blocks_for(n_pad, 256), 256, 0, s->stream>>>(n, n_pad, s->geo64.p, s->nrm64.p, u, lam,
-                                                             s->rec64.p);
+  std::vector<PassSys> sys(L.K);
+  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.chg_off[k], L.nc[k], L.vec_off[k] / 2, L.n[k]};
+  ItemPlan* plan = plan_pass<GradPolicy, double4_32a, NT, TPT, CH>(s, kPassGrad, sys, CH);
+  s->grow(s->rec64, (size_t)3 * L.len / 2);
+  s->grow(s->part64, (size_t)plan->part_len);
+  const int4* lay = s->lay_dev(L);
+  k_pack_grad<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, s->tgt64.p, u, lam, s->rec64.p);
   BIPB_LAUNCHED(s);
-  s->grow(s->part64, (size_t)tl.n_splits * 8 * nc);
-  GradPolicy::Args a{s->chg.p + (size_t)r * nc, s->rec64.p, s->part64.p, nc, pair_const<double>(m)};
-  launch_tiled<GradPolicy, double4_32a, NT, TPT, CH>(s, kTGrad, tl, a, nc, n, s->rec64.p, nullptr);
-  k_reduce_grad<<<blocks_for(nc, 256), 256, 0, s->stream>>>(nc, tl.n_splits, s->part64.p,
-                                                            s->chg.p + (size_t)r * nc, 1.0 / m.eps_in,
-                                                            dq, dy);
+  GradPolicy::Args a{s->chg.p, s->part64.p, pair_const<double>(m)};
+  launch_items<GradPolicy, double4_32a, NT, TPT, CH>(s, kTGrad, plan, a, s->rec64.p, nullptr, 0);
+  k_reduce_grad<<<dim3(blocks_for(L.max_nc, 256), L.K), 256, 0, s->stream>>>(plan->tab.p, lay, s->part64.p,
+                                                                              s->chg.p, 1.0 / m.eps_in, dq, dy);
   BIPB_LAUNCHED(s);
 }
 

@@ -275,3 +275,67 @@ def test_full_size_matvec_sampled_rows(bipb, orc, cfg):
     scale = np.abs(ref).max()
     np.testing.assert_allclose(a64[rows], ref, rtol=0, atol=1e-12 * scale)
     assert np.abs(a32[rows] - ref).max() < 2e-5 * scale
+
+
+# ---------------------------------------------------------------- uneven batches
+def _uneven():
+    a = synth.born_problem(level=2, radius=4.0)
+    a.charge_pos = np.array([[0.3, -0.2, 0.5], [-1.0, 0.4, 0.1]])
+    a.q = np.array([[0.7, -0.4]])
+    b = _ragged(3)
+    c = synth.kirkwood_problem(level=3, radius=9.0, n_charges=5, charge_radius=6.0)
+    return [a, b, c]
+
+
+def test_uneven_batch_matvec_matches_oracle(bipb, orc):
+    probs = _uneven()
+    rng = np.random.default_rng(21)
+    us = [rng.standard_normal(2 * p.n) for p in probs]
+    with bipb.BatchSurface([(p.centroids, p.normals, p.areas) for p in probs]) as s:
+        u = _dev(np.concatenate(us))
+        for prec, tol in ((bipb.FP64, 1e-12), (bipb.FP32, 2e-5)):
+            for transpose in (False, True):
+                y = torch.full_like(u, float("nan"))
+                s.matvec(u, y, precision=prec, transpose=transpose)
+                parts = np.split(y.cpu().numpy(), np.cumsum([2 * p.n for p in probs])[:-1])
+                for p, uk, yk in zip(probs, us, parts):
+                    f = orc.matvec_t if transpose else orc.matvec
+                    ref = f(p.centroids, p.normals, p.areas, p.eps_out / p.eps_in, p.kappa, uk)
+                    assert np.abs(yk - ref).max() < tol * np.abs(ref).max(), (prec, transpose)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uneven_batch_solve_matches_single_solves(bipb, prec):
+    probs = _uneven()
+    P = bipb.FP64 if prec == "fp64" else bipb.MIXED
+    tol = 1e-11 if prec == "fp64" else 1e-9
+    with bipb.BatchSurface([(p.centroids, p.normals, p.areas) for p in probs]) as s:
+        s.set_charges([(p.charge_pos, p.q[0]) for p in probs])
+        info = s.solve(tol=tol, precision=P)
+        assert len(info) == 3 and all(i["converged"] for i in info)
+        e = s.energy()
+        phi, dphi = s.surface_potential()
+        dq, dy = s.energy_grad(tol=1e-10, precision=P)
+    for k, p in enumerate(probs):
+        with bipb.Surface(p.centroids, p.normals, p.areas) as s1:
+            s1.set_charges(p.charge_pos, p.q)
+            s1.solve(tol=tol, precision=P)
+            rt = 1e-9 if prec == "fp64" else 1e-7
+            assert e[k] == pytest.approx(s1.energy()[0], rel=rt)
+            ph1, dph1 = s1.surface_potential()
+            assert np.linalg.norm(phi[k] - ph1[0]) < rt * 10 * np.linalg.norm(ph1[0])
+            dq1, dy1 = s1.energy_grad(tol=1e-10, precision=P)
+            np.testing.assert_allclose(dq[k], dq1[0], rtol=1e-6, atol=1e-9 * np.abs(dq1).max())
+            np.testing.assert_allclose(dy[k], dy1[0], rtol=1e-6, atol=1e-9 * np.abs(dy1).max())
+
+
+def test_uneven_batch_one_launch_per_pass(bipb):
+    """A batched mat-vec is one pack, one pair-kernel and one reduction launch."""
+    probs = _uneven()
+    with bipb.BatchSurface([(p.centroids, p.normals, p.areas) for p in probs]) as s:
+        u = _dev(np.ones(sum(2 * p.n for p in probs)))
+        y = torch.empty_like(u)
+        s.matvec(u, y, precision=bipb.FP32)
+        n0 = bipb.launch_count(s)
+        s.matvec(u, y, precision=bipb.FP32)
+        assert bipb.launch_count(s) - n0 == 3
