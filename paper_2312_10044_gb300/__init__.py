@@ -11,6 +11,7 @@ contiguous), used only as device memory.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 
 import numpy as np
@@ -83,6 +84,7 @@ class BipbError(RuntimeError):
 
 
 _lib = None
+_charge_versions = itertools.count(1)
 
 
 def load_library():
@@ -238,6 +240,7 @@ class Surface:
         n_pos = 1 if pos.ndim == 2 else pos.shape[0]
         pos = _host(pos, (n_pos, nc, 3))
         _check(self._L.bipb_charges_set(self._h, nc, _hp(pos), n_pos, n_rhs, _hp(q)))
+        self._charge_version = next(_charge_versions)
         self.nc, self.n_rhs = nc, n_rhs
         self.n_charges_total = nc * n_rhs
 
@@ -372,6 +375,7 @@ class BatchSurface(Surface):
         nc = (ctypes.c_int64 * k)(*[v.shape[0] for v in q])
         _check(self._L.bipb_charges_set_batch(self._h, nc, (ctypes.c_void_p * k)(*[p.ctypes.data for p in pos]),
                                               (ctypes.c_void_p * k)(*[v.ctypes.data for v in q])))
+        self._charge_version = next(_charge_versions)
         self.ncs = [v.shape[0] for v in q]
         self.n_charges_total = sum(self.ncs)
         self.n_rhs = k

@@ -339,3 +339,46 @@ def test_uneven_batch_one_launch_per_pass(bipb):
         n0 = bipb.launch_count(s)
         s.matvec(u, y, precision=bipb.FP32)
         assert bipb.launch_count(s) - n0 == 3
+
+
+# ---------------------------------------------------------------- autograd
+def test_autograd_energy_matches_oracle_and_finite_differences(bipb, orc):
+    from paper_2312_10044_gb300.torch_ops import SolvationEnergy
+
+    p = synth.protein_like_problem(level=3, radius=12.0, n_charges=6, seed=8)
+    e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="direct")
+    model = SolvationEnergy(p.centroids, p.normals, p.areas, tol=1e-12, precision=bipb.FP64)
+    q = torch.tensor(p.q[0], dtype=torch.float64, requires_grad=True)
+    pos = torch.tensor(p.charge_pos, dtype=torch.float64, requires_grad=True)
+    e = model(q, pos)
+    e.backward()
+    assert e.item() == pytest.approx(e_ref, rel=1e-10)
+    np.testing.assert_allclose(q.grad.numpy(), dq_ref, rtol=1e-8)
+    np.testing.assert_allclose(pos.grad.numpy(), dy_ref, rtol=1e-7, atol=1e-9 * np.abs(dy_ref).max())
+    # central differences, h = 1e-4 A, on two atoms
+    h = 1e-4
+    for k in (0, 3):
+        for a in range(3):
+            with torch.no_grad():
+                pp = pos.detach().clone()
+                pp[k, a] += h
+                ep = model(q.detach(), pp).item()
+                pp[k, a] -= 2 * h
+                em = model(q.detach(), pp).item()
+            fd = (ep - em) / (2 * h)
+            assert pos.grad[k, a].item() == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(dy_ref).max())
+
+
+def test_autograd_batched_mixed(bipb):
+    from paper_2312_10044_gb300.torch_ops import SolvationEnergy
+
+    base = synth.protein_like_problem(level=3, n_charges=10)
+    batch = synth.batched_charges(base, n_rhs=2, n_charges=10)
+    model = SolvationEnergy(batch.centroids, batch.normals, batch.areas, tol=1e-9)
+    q = torch.tensor(batch.q, dtype=torch.float64, requires_grad=True)
+    pos = torch.tensor(batch.charge_pos, dtype=torch.float64, requires_grad=True)
+    e = model(q, pos)
+    (e * torch.tensor([1.0, -2.0], dtype=torch.float64)).sum().backward()
+    # Euler identity per configuration: sum_k q_k dE/dq_k = 2 E (weights 1 and -2)
+    assert torch.dot(q[0].detach(), q.grad[0]).item() == pytest.approx(2 * e[0].item(), rel=1e-6)
+    assert torch.dot(q[1].detach(), q.grad[1]).item() == pytest.approx(-2 * 2 * e[1].item(), rel=1e-6)
