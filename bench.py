@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--variant", type=int, default=-1, help="FP32 mat-vec variant for --mode matvec32")
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64", "matvecdf"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
@@ -196,7 +196,7 @@ def run_matvec_only(args):
     import paper_2312_10044_gb300 as bipb
 
     prob, desc = workload(args.workload)
-    prec = bipb.FP32 if args.mode == "matvec32" else bipb.FP64
+    prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64}[args.mode]
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
     with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
         if args.variant >= 0:
@@ -298,7 +298,7 @@ def main():
     cnt, tms = timers[dom]
     avg_ms = tms / max(cnt, 1)
     f_mhz = clocks["sm_mhz"] if clocks else 2070.0
-    lanes = FP32_LANES_PER_SM if dom.startswith("matvec32") else FP64_LANES_PER_SM
+    lanes = FP64_LANES_PER_SM if dom.startswith("matvec64") else FP32_LANES_PER_SM
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     pairs_launch = n * (n - 1)
     achieved = pairs_launch * PAIR_FLOPS / (avg_ms / 1e3) / 1e12
@@ -318,7 +318,8 @@ def main():
     u = torch.randn(2 * n, dtype=torch.float64, device=dev)
     y = torch.empty_like(u)
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
-    for prec, name, reps in (() if args.no_extra else ((bipb.FP32, "fp32", 20), (bipb.FP64, "fp64", 3))):
+    for prec, name, reps in (() if args.no_extra else ((bipb.FP32, "fp32", 20), (bipb.FP64, "fp64", 3),
+                                                          (bipb.DF64, "df64", 5))):
         s.matvec(u, y, precision=prec, med=med)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -338,6 +339,16 @@ def main():
         torch.cuda.synchronize()
         extra["solve_ms_fp64"] = a.elapsed_time(b)
         extra["fp64_info"] = i64
+        # the same solve with the double-float residual (FP32 Krylov + df64 refinement)
+        pdf = bipb.solve_params(prob.eps_in, prob.eps_out, prob.kappa, tol=TOL, restart=10,
+                                precision=bipb.MIXED_DF64)
+        s.solve(pdf)
+        a.record()
+        idf = s.solve(pdf)[0]
+        b.record()
+        torch.cuda.synchronize()
+        extra["solve_ms_mixed_df64"] = a.elapsed_time(b)
+        extra["mixed_df64_info"] = idf
     extra["solve_ms_mixed"] = total_ms / args.steps
     extra["mixed_info"] = info0
     extra["energy_kcal"] = infos[-1][1]

@@ -54,9 +54,12 @@ typedef enum {
 } bipb_status;
 
 typedef enum {
-  BIPB_FP64 = 0,  /* all pair arithmetic in FP64 */
-  BIPB_MIXED = 1, /* FP32 pair arithmetic inside GMRES, FP64 refinement residual */
-  BIPB_FP32 = 2   /* mat-vec only: FP32 pair arithmetic, FP64 sums across tiles */
+  BIPB_FP64 = 0,       /* all pair arithmetic in FP64 */
+  BIPB_MIXED = 1,      /* FP32 pair arithmetic inside GMRES, FP64 refinement residual */
+  BIPB_FP32 = 2,       /* mat-vec only: FP32 pair arithmetic, FP64 sums across tiles */
+  BIPB_DF64 = 3,       /* pair arithmetic in double-float (two FP32 words, ~48 bits) on the FP32
+                          pipe, FP64 sums across tiles; as a solve: GMRES on that mat-vec */
+  BIPB_MIXED_DF64 = 4  /* FP32 pair arithmetic inside GMRES, double-float refinement residual */
 } bipb_precision;
 
 /* Dielectric medium (Sec. 2.1): eps_in > 0 inside, eps_out > 0 outside, kappa >= 0 (1/A). */
@@ -71,7 +74,7 @@ typedef struct {
   double tol;          /* target ||b - A u||_2 / ||b||_2, 0 < tol < 1 */
   int restart;         /* GMRES restart length m, 1..64 (10 if 0) */
   int max_iter;        /* cap on GMRES iterations summed over restarts and refinement steps (1000 if 0) */
-  int precision;       /* bipb_precision: BIPB_FP64 or BIPB_MIXED */
+  int precision;       /* bipb_precision: BIPB_FP64, BIPB_MIXED, BIPB_DF64 or BIPB_MIXED_DF64 */
   int inner_max_iter;  /* MIXED: cap on inner iterations per refinement step (200 if 0) */
   double inner_tol;    /* MIXED: inner relative tolerance per refinement step (1e-6 if 0) */
   const double* x0;    /* optional warm start, host, n_rhs x 2N internal units, or NULL (zero) */
@@ -179,8 +182,8 @@ bipb_status bipb_energy_grad(bipb_surface s, const bipb_solve_params* p, double*
  *   u, y: device, n_vec x 2N doubles, internal units; y must not alias u.
  *   For a batch handle n_vec must be 1 and u, y are batched vectors (the
  *   block-diagonal operator of all surfaces).
- *   precision: BIPB_FP64 or BIPB_FP32 (FP32 pair arithmetic per source tile,
- *   FP64 sums across tiles and for the diagonal).
+ *   precision: BIPB_FP64, BIPB_FP32 (FP32 pair arithmetic per source tile,
+ *   FP64 sums across tiles and for the diagonal) or BIPB_DF64.
  */
 bipb_status bipb_matvec(bipb_surface s, const bipb_medium* m, int precision, int transpose,
                         int n_vec, const double* u, double* y);
@@ -214,7 +217,9 @@ typedef enum {
   BIPB_KERNEL_REACTION = 5,   /* reaction-potential / energy pair kernel */
   BIPB_KERNEL_ENERGY_ROW = 6, /* energy-row pair kernel (adjoint right-hand side) */
   BIPB_KERNEL_GRAD = 7,       /* energy-gradient pair kernel */
-  BIPB_KERNEL_KINDS = 8
+  BIPB_KERNEL_MATVECDF = 8,   /* double-float mat-vec pair kernel */
+  BIPB_KERNEL_MATVECDF_T = 9, /* double-float transposed mat-vec pair kernel */
+  BIPB_KERNEL_KINDS = 10
 } bipb_kernel_kind;
 
 /* Turn timing on (1) or off (0); turning it on clears the totals. */

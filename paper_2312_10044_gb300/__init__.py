@@ -29,6 +29,8 @@ BIPB_ERR_STATE = 5
 FP64 = 0
 MIXED = 1
 FP32 = 2
+DF64 = 3
+MIXED_DF64 = 4
 
 KCAL = 4.0 * np.pi * 332.0716  # internal units -> kcal/mol (per e)
 
@@ -41,7 +43,8 @@ EXPORTED = (
 )
 MATVEC32_VARIANTS = 7
 
-KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad")
+KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad",
+                "matvec_df", "matvec_df_t")
 
 
 class bipb_medium(ctypes.Structure):

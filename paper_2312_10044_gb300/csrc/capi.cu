@@ -89,7 +89,9 @@ void validate_params(const bipb_solve_params* p) {
   BIPB_REQUIRE(std::isfinite(p->tol) && p->tol > 0 && p->tol < 1, "tol must lie in (0, 1)");
   BIPB_REQUIRE(p->restart >= 0 && p->restart <= kMaxRestart, "restart must lie in [1, 64] (0 = 10)");
   BIPB_REQUIRE(p->max_iter >= 0, "max_iter must be >= 0 (0 = 1000)");
-  BIPB_REQUIRE(p->precision == BIPB_FP64 || p->precision == BIPB_MIXED, "precision must be FP64 or MIXED");
+  BIPB_REQUIRE(p->precision == BIPB_FP64 || p->precision == BIPB_MIXED || p->precision == BIPB_DF64 ||
+                   p->precision == BIPB_MIXED_DF64,
+               "precision must be FP64, MIXED, DF64 or MIXED_DF64");
   BIPB_REQUIRE(p->inner_max_iter >= 0, "inner_max_iter must be >= 0");
   BIPB_REQUIRE(std::isfinite(p->inner_tol) && p->inner_tol >= 0 && p->inner_tol < 1, "inner_tol must lie in [0, 1)");
 }
@@ -397,7 +399,8 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
   return guarded([&] {
     Surface* s = checked(h);
     validate_medium(m);
-    BIPB_REQUIRE(precision == BIPB_FP64 || precision == BIPB_FP32, "precision must be FP64 or FP32");
+    BIPB_REQUIRE(precision == BIPB_FP64 || precision == BIPB_FP32 || precision == BIPB_DF64,
+                 "precision must be FP64, FP32 or DF64");
     BIPB_REQUIRE(n_vec >= 1 && n_vec <= 4096, "n_vec must lie in [1, 4096]");
     BIPB_REQUIRE(!s->batch || n_vec == 1, "a batch handle takes one batched vector (n_vec = 1)");
     BIPB_REQUIRE(u && y, "NULL vector");

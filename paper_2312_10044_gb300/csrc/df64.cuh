@@ -1,0 +1,199 @@
+// Double-float ("df64") arithmetic on the FP32 pipe, and the mat-vec pair
+// in that arithmetic.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// about 48 significant bits.  The operations are built from error-free
+// transformations: Knuth's TwoSum, Dekker's FastTwoSum (|a| >= |b|) and the
+// FMA-based TwoProduct (see Dekker 1971; Shewchuk 1997; Hida, Li and Bailey
+// 2001 for the double-double analogue).  The __f*_rn intrinsics keep the
+// compiler from contracting or reassociating them.
+//
+// GB300 executes FP64 at 2 lanes per SM per cycle against 128 for FP32, so
+// a mat-vec pair in df64 (several hundred FP32 instructions) is several
+// times faster than the same pair in native FP64 while keeping a relative
+// accuracy near 1e-13; it serves as the high-precision residual of the mixed
+// solve.
+//
+// exp(-kappa r) follows Tang's table-driven method (ACM TOMS 15, 1989):
+// x = k ln2/32 + f with |f| <= ln2/64 (Cody-Waite reduction with ln2/32 split
+// in three parts so that k * L1 is exact), exp(x) = 2^(k>>5) * 2^((k&31)/32)
+// * exp(f), the 32 table values 2^(j/32) held as df64 in shared memory and
+// exp(f) - 1 = f + f^2/2 + f^3/6 + f^4/24 + f^5/120 (truncation f^6/720 <
+// 3e-15 for |f| <= ln2/64).
+// 1/sqrt(r2) is one Newton step in df64 from the MUFU estimate (error
+// squared: about 1e-14).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bipb {
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float hi, float lo) { return df{hi, lo}; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df{s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return df{s, e};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return df{p, e};
+}
+// x + y: exact TwoSum of the leading parts, the trailing parts added in FP32.
+// Absolute error about 2^-47 max(|x|, |y|).
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+// x + f for a float f
+__device__ __forceinline__ df df_add_f(df x, float f) {
+  df s = two_sum(x.hi, f);
+  s.lo = __fadd_rn(s.lo, x.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_mul(df x, df y) {
+  float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mul_f(df x, float f) {
+  float p = __fmul_rn(x.hi, f);
+  float e = __fmaf_rn(x.hi, f, -p);
+  e = __fmaf_rn(x.lo, f, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_sqr(df x) {
+  float p = __fmul_rn(x.hi, x.hi);
+  float e = __fmaf_rn(x.hi, x.hi, -p);
+  e = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ df df_scale(df x, float pow2) { return df{__fmul_rn(x.hi, pow2), __fmul_rn(x.lo, pow2)}; }
+__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ df df_from_double(double v) {
+  float hi = __double2float_rn(v);
+  return df{hi, __double2float_rn(v - (double)hi)};
+}
+// dot product of two df 3-vectors
+__device__ __forceinline__ df df_dot3(df ax, df ay, df az, df bx, df by, df bz) {
+  return df_add(df_add(df_mul(ax, bx), df_mul(ay, by)), df_mul(az, bz));
+}
+
+struct DFConst {
+  df eps, inveps, kappa;  // eps_out/eps_in, its inverse, kappa
+  float l1, l2, l3;       // ln2/32 = l1 + l2 + l3, l1 with 12 significant bits
+  float inv_l;            // 32/ln2
+};
+
+// 1/sqrt(r2) for r2 > 0: MUFU estimate, one Newton step in df64.
+__device__ __forceinline__ df df_rsqrt(df r2) {
+  float s0;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(s0) : "f"(r2.hi));
+  // h = r2 * s0^2 (close to 1); s = s0 + s0 (1 - h) / 2
+  df h = df_mul(r2, two_prod(s0, s0));
+  float d = __fadd_rn(__fsub_rn(1.0f, h.hi), -h.lo);  // 1 - h, exact leading part
+  return fast_two_sum(s0, __fmul_rn(__fmul_rn(s0, d), 0.5f));
+}
+
+// exp(x) for x <= 0 (clamped at -80), tab[j] = 2^(j/32) as df64.
+__device__ __forceinline__ df df_exp_neg(df x, const DFConst& c, const df* tab) {
+  if (x.hi < -80.0f) x = df{-80.0f, 0.0f};
+  const float kf = rintf(__fmul_rn(x.hi, c.inv_l));
+  const int k = (int)kf;
+  // f = x - k ln2/32, with k * l1 exact
+  const float f1 = __fmaf_rn(-kf, c.l1, x.hi);  // exact (Sterbenz)
+  df f = two_sum(f1, x.lo);
+  f = df_add(f, df_neg(two_prod(kf, c.l2)));
+  f.lo = __fmaf_rn(-kf, c.l3, f.lo);
+  // exp(f) - 1 = f + f^2/2 + f^3 (1/6 + f/24 + f^2/120)
+  const df h2 = df_scale(df_sqr(f), 0.5f);
+  const float fh = f.hi;
+  const float tail = __fmul_rn(__fmul_rn(__fmul_rn(fh, fh), fh),
+                               __fmaf_rn(fh, __fmaf_rn(fh, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f));
+  df em1 = df_add(f, h2);
+  em1 = fast_two_sum(em1.hi, __fadd_rn(em1.lo, tail));
+  df ef = two_sum(1.0f, em1.hi);
+  ef = fast_two_sum(ef.hi, __fadd_rn(ef.lo, em1.lo));
+  const df t = tab[k & 31];
+  df r = df_mul(ef, t);
+  const int m = k >> 5;  // floor(k / 32)
+  return df_scale(r, __int_as_float((127 + m) << 23));
+}
+
+// Forward pair (the formula of pair_forward in pair.cuh) in df64.
+// MASK/self: see pair.cuh (s = 0 for the self pair).
+template <bool MASK>
+__device__ __forceinline__ void df_pair_forward(const df* xi, const df* ni, const df* xj, df a, const df* m, bool self,
+                                                const DFConst& c, const df* tab, df& accP, df& accQ) {
+  const df dx = df_sub(xi[0], xj[0]), dy = df_sub(xi[1], xj[1]), dz = df_sub(xi[2], xj[2]);
+  const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  df s = df_rsqrt(r2);
+  if (MASK && self) s = df{0.0f, 0.0f};
+  const df r = df_mul(r2, s);
+  const df kr = df_mul(r, c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df ci = df_dot3(ni[0], ni[1], ni[2], dx, dy, dz);
+  const df cm = df_dot3(m[0], m[1], m[2], dx, dy, dz);
+  const df cim = df_dot3(ni[0], ni[1], ni[2], m[0], m[1], m[2]);
+  const df t = df_add(df_mul(e, kr), e);                           // e (1 + kr)
+  const df tm1 = df_add_f(t, -1.0f);                               // t - 1
+  const df wm3 = df_add(df_mul(df_sub(t, e), kr), df_mul_f(tm1, 3.0f));  // w - 3 = 3 (t - 1) + (t - e) kr
+  const df s2 = df_sqr(s);
+  // P = s [ (1 - e) a + (eps t - 1) cm s^2 ]
+  const df ome = df_add_f(df_neg(e), 1.0f);
+  df p = df_mul(ome, a);
+  p = df_add(p, df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cm), s2));
+  accP = df_add(accP, df_mul(p, s));
+  // Q = s^3 [ (t/eps - 1) ci a + (t - 1) cim - (w - 3) ci cm s^2 ]
+  df q = df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), ci), a);
+  q = df_add(q, df_mul(tm1, cim));
+  q = df_sub(q, df_mul(wm3, df_mul(df_mul(ci, cm), s2)));
+  accQ = df_add(accQ, df_mul(q, df_mul(s2, s)));
+}
+
+// Transposed pair (the formula of pair_transpose in pair.cuh) in df64:
+// output element j (x, n) gathers element i (xs, wphi, p = wpsi n_i).
+template <bool MASK>
+__device__ __forceinline__ void df_pair_transpose(const df* xj, const df* nj, const df* xi, df wphi, const df* pv,
+                                                  bool self, const DFConst& c, const df* tab, df& accP, df& accQ) {
+  const df dx = df_sub(xi[0], xj[0]), dy = df_sub(xi[1], xj[1]), dz = df_sub(xi[2], xj[2]);
+  const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  df s = df_rsqrt(r2);
+  if (MASK && self) s = df{0.0f, 0.0f};
+  const df r = df_mul(r2, s);
+  const df kr = df_mul(r, c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df cj = df_dot3(nj[0], nj[1], nj[2], dx, dy, dz);
+  const df cp = df_dot3(pv[0], pv[1], pv[2], dx, dy, dz);
+  const df cnp = df_dot3(nj[0], nj[1], nj[2], pv[0], pv[1], pv[2]);
+  const df t = df_add(df_mul(e, kr), e);
+  const df tm1 = df_add_f(t, -1.0f);
+  const df wm3 = df_add(df_mul(df_sub(t, e), kr), df_mul_f(tm1, 3.0f));
+  const df s2 = df_sqr(s);
+  // Zphi = s^3 [ (eps t - 1) c_j wphi + (t - 1)(n_j.p) - (w - 3)(p.d) c_j s^2 ]
+  df q = df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cj), wphi);
+  q = df_add(q, df_mul(tm1, cnp));
+  q = df_sub(q, df_mul(wm3, df_mul(df_mul(cp, cj), s2)));
+  accP = df_add(accP, df_mul(q, df_mul(s2, s)));
+  // Zpsi = s [ (1 - e) wphi + (t/eps - 1)(p.d) s^2 ]
+  df p = df_mul(df_add_f(df_neg(e), 1.0f), wphi);
+  p = df_add(p, df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), cp), s2));
+  accQ = df_add(accQ, df_mul(p, s));
+}
+
+}  // namespace bipb

@@ -541,7 +541,8 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   const std::vector<double> bnorm = norms(s, w, rhs);
   // r = rhs - A x (or rhs when starting from zero)
   if (warm) {
-    matvec(s, L, med, BIPB_FP64, transpose, x, w->t.p, nullptr, 0);
+    matvec(s, L, med, p.precision == BIPB_FP64 || p.precision == BIPB_MIXED ? BIPB_FP64 : BIPB_DF64, transpose, x,
+           w->t.p, nullptr, 0);
     for (auto& r : res) r.matvecs64++;
     k_sub<<<nb, kBS, 0, s->stream>>>(len, rhs, w->t.p, w->r.p);
     BIPB_LAUNCHED(s);
@@ -556,7 +557,10 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   }
   for (int k = 0; k < K; ++k)
     if (bnorm[k] == 0.0) rel[k] = 0.0;
-  const bool mixed = p.precision == BIPB_MIXED;
+  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64;
+  // arithmetic of the Krylov mat-vecs and of the residual r = b - A x
+  const int inner = mixed ? BIPB_FP32 : p.precision;
+  const int resid = (p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_DF64) ? BIPB_DF64 : BIPB_FP64;
   const double inner_floor = p.inner_tol > 0 ? p.inner_tol : 1e-6;
   const int inner_cap = p.inner_max_iter > 0 ? p.inner_max_iter : 200;
   std::vector<char> active(K), done(K, 0);
@@ -579,14 +583,13 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
     }
     if (!any) break;
     std::vector<int> conv;
-    std::vector<int> used = gmres_core(s, L, w, med, mixed ? BIPB_FP32 : BIPB_FP64, transpose, w->r.p, active,
-                                       tol_rel, cap, &conv);
+    std::vector<int> used = gmres_core(s, L, w, med, inner, transpose, w->r.p, active, tol_rel, cap, &conv);
     // x += d (d is zero outside the active systems); r = rhs - A x in FP64 for the active systems
     k_add<<<nb, kBS, 0, s->stream>>>(len, w->d.p, x);
     BIPB_LAUNCHED(s);
     for (int k = 0; k < K; ++k) w->mask_host[k] = active[k] ? 0 : 1;
     BIPB_CUDA(cudaMemcpyAsync(w->mask.p, w->mask_host, K * sizeof(int), cudaMemcpyHostToDevice, s->stream));
-    matvec(s, L, med, BIPB_FP64, transpose, x, w->t.p, w->mask.p, 1);
+    matvec(s, L, med, resid, transpose, x, w->t.p, w->mask.p, 1);
     k_sub<<<nb, kBS, 0, s->stream>>>(len, rhs, w->t.p, w->r.p);
     BIPB_LAUNCHED(s);
     std::vector<double> rn = norms(s, w, w->r.p);

@@ -93,7 +93,7 @@ constexpr int kNumMv32Variants = 7;
 constexpr int kMaxRestart = 64;
 
 // Per-kernel CUDA-event timing of the pair kernels (off by default).
-enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTKinds };
+enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTMvDF, kTMvDFT, kTKinds };
 
 struct EventPair {
   int kind;
@@ -163,6 +163,7 @@ struct Surface {
 
   // per-pass scratch
   DevBuf<float4> rec32;
+  DevBuf<float4> recdf;
   DevBuf<double4_32a> rec64;
   DevBuf<float> part32;
   DevBuf<double> part64;

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "df64.cuh"
 #include "internal.cuh"
 
 namespace bipb {
@@ -56,6 +57,8 @@ struct MatvecPolicy {
   static constexpr int RW = 2;
   static constexpr int NOUT = 2;
   static constexpr bool SELF = true;
+  template <class A>
+  __device__ static void prologue(const A&) {}
   using Tgt = ElemTgt<T>;
   struct Acc {
     T p, q;
@@ -86,12 +89,65 @@ struct MatvecPolicy {
   }
 };
 
+// Mat-vec in double-float arithmetic (df64.cuh).  Record per source, 4 float4:
+// (x.hi, a.hi), (x.lo, a.lo), (m.hi, 0), (m.lo, 0) with a = ds psi and
+// m = ds phi n (forward) or a = wphi, m = wpsi n (transposed).
+__device__ df* df_exp_table() {
+  __shared__ df tab[32];
+  return tab;
+}
+
+template <bool TRANS>
+struct MatvecDFPolicy {
+  static constexpr int RW = 4;
+  static constexpr int NOUT = 2;
+  static constexpr bool SELF = true;
+  struct Tgt {
+    df x[3], n[3];
+  };
+  struct Acc {
+    df p, q;
+  };
+  struct Args {
+    const double4_32a* tgt;
+    double* part;
+    DFConst c;
+  };
+  __device__ static void prologue(const Args&) {
+    df* tab = df_exp_table();
+    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  }
+  __device__ static void load(const Args& a, int i, Tgt& t) {
+    double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
+    t.x[0] = df_from_double(g.x), t.x[1] = df_from_double(g.y), t.x[2] = df_from_double(g.z);
+    t.n[0] = df_from_double(v.x), t.n[1] = df_from_double(v.y), t.n[2] = df_from_double(v.z);
+  }
+  __device__ static void zero(Acc& acc) { acc.p = df{0.f, 0.f}, acc.q = df{0.f, 0.f}; }
+  template <bool MASK>
+  __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool self, Acc& acc) {
+    const float4 A = r[0], B = r[1], C = r[2], D = r[3];
+    const df xs[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    const df m[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
+    const df w = df{A.w, B.w};
+    if (TRANS)
+      df_pair_transpose<MASK>(t.x, t.n, xs, w, m, self, a.c, df_exp_table(), acc.p, acc.q);
+    else
+      df_pair_forward<MASK>(t.x, t.n, xs, w, m, self, a.c, df_exp_table(), acc.p, acc.q);
+  }
+  __device__ static void store(const Args& a, int out, int n_tgt, int i, const Acc& acc) {
+    a.part[(size_t)out + i] = df_to_double(acc.p);
+    a.part[(size_t)out + n_tgt + i] = df_to_double(acc.q);
+  }
+};
+
 // Source term: target element i, source charge k with record (y_k, q_k), d = x_i - y_k:
 //   4 pi eps_in S1 += q s,   4 pi eps_in S2 += -q (n_i.d) s^3   (d/dnu_x = +n_x.grad_x)
 struct SourcePolicy {
   static constexpr int RW = 1;
   static constexpr int NOUT = 2;
   static constexpr bool SELF = false;
+  template <class A>
+  __device__ static void prologue(const A&) {}
   using Tgt = ElemTgt<double>;
   struct Acc {
     double s1, s2;
@@ -131,6 +187,8 @@ struct ReactionPolicy {
   static constexpr int RW = 2;
   static constexpr int NOUT = 1;
   static constexpr bool SELF = false;
+  template <class A>
+  __device__ static void prologue(const A&) {}
   using Tgt = PointTgt;
   struct Acc {
     double p;
@@ -169,6 +227,8 @@ struct EnergyRowPolicy {
   static constexpr int RW = 1;
   static constexpr int NOUT = 2;
   static constexpr bool SELF = false;
+  template <class A>
+  __device__ static void prologue(const A&) {}
   using Tgt = ElemTgt<double>;
   struct Acc {
     double cphi, cpsi;
@@ -214,6 +274,8 @@ struct GradPolicy {
   static constexpr int RW = 3;
   static constexpr int NOUT = 8;
   static constexpr bool SELF = false;
+  template <class A>
+  __device__ static void prologue(const A&) {}
   using Tgt = PointTgt;
   struct Acc {
     double p, sb, ga[3], gb[3];
@@ -283,6 +345,7 @@ __global__ void __launch_bounds__(NT) k_items(typename P::Args a, const int4* __
   const int tgt_off = I0.x, n_tgt = I0.y, t0 = I0.z, sys = I0.w;
   const int src_off = I1.x, s0 = I1.y, s1 = I1.z, out = I1.w;
   if (sys_skipped(skip, skip_stride, sys)) return;
+  P::prologue(a);  // per-CTA shared tables (made visible by the first barrier below)
   typename P::Tgt tg[TPT];
   typename P::Acc acc[TPT];
   int idx[TPT];
@@ -476,6 +539,28 @@ __global__ void k_pack(const int4* __restrict__ lay, bool transpose, const doubl
   rec[2 * o + 1] = r1;
 }
 
+// df64 records (4 float4 per element) of every system, forward or transposed.
+__global__ void k_pack_df(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
+                          const double* __restrict__ u, float4* __restrict__ rec, const int* __restrict__ skip,
+                          int skip_stride) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.y || sys_skipped(skip, skip_stride, k)) return;
+  const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
+  const double* uk = u + L.z;
+  const double phi = uk[j], psi = uk[L.y + j];
+  const double sc = transpose ? phi : g.w * psi;
+  const double f = transpose ? psi : g.w * phi;
+  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z), w = df_from_double(sc);
+  const df m0 = df_from_double(f * v.x), m1 = df_from_double(f * v.y), m2 = df_from_double(f * v.z);
+  const size_t o = 4 * (size_t)(L.z / 2 + j);
+  rec[o] = make_float4(x0.hi, x1.hi, x2.hi, w.hi);
+  rec[o + 1] = make_float4(x0.lo, x1.lo, x2.lo, w.lo);
+  rec[o + 2] = make_float4(m0.hi, m1.hi, m2.hi, 0.f);
+  rec[o + 3] = make_float4(m0.lo, m1.lo, m2.lo, 0.f);
+}
+
 // y_i = diag * u_i - (1/(4 pi)) * scale_i * sum over splits, i < 2n of each system;
 // diag = 1/2 (1 + eps) on the phi half and 1/2 (1 + 1/eps) on the psi half;
 // scale_i = area of element (i mod n) for the transpose, 1 otherwise.
@@ -597,8 +682,29 @@ PairConst<T> pair_const(const bipb_medium& m) {
 
 int blocks_for(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
-enum PassId { kPassMv64 = 1, kPassMv64T, kPassMv32 = 16, kPassMv32T = 32, kPassSource = 48, kPassReaction, kPassRow,
-              kPassGrad };
+enum PassId { kPassMv64 = 1, kPassMv64T, kPassMvDF, kPassMvDFT, kPassMv32 = 16, kPassMv32T = 32, kPassSource = 48,
+              kPassReaction, kPassRow, kPassGrad };
+
+DFConst df_const(const bipb_medium& m) {
+  auto split = [](double v) {
+    df r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+  };
+  const double eps = m.eps_out / m.eps_in;
+  DFConst c;
+  c.eps = split(eps);
+  c.inveps = split(1.0 / eps);
+  c.kappa = split(m.kappa);
+  const double L = 0.693147180559945309417232121458 / 32.0;
+  const double l1 = std::ldexp(std::nearbyint(std::ldexp(L, 17)), -17);  // 12 significant bits
+  c.l1 = (float)l1;
+  c.l2 = (float)(L - l1);
+  c.l3 = (float)(L - l1 - (double)c.l2);
+  c.inv_l = (float)(32.0 / 0.693147180559945309417232121458);
+  return c;
+}
 
 std::vector<PassSys> matvec_sys(const SysLayout& L) {
   std::vector<PassSys> v(L.K);
@@ -640,6 +746,25 @@ void run_matvec64(Surface* s, const SysLayout& L, const PairConst<double>& c, co
   BIPB_LAUNCHED(s);
   typename P::Args a{s->tgt64.p, s->part64.p, c};
   launch_items<P, double4_32a, NT, TPT, CH>(s, TRANS ? kTMv64T : kTMv64, plan, a, s->rec64.p, skip, skip_stride);
+  k_reduce_matvec<double><<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, plan->tab.p, s->part64.p, u, y, dphi, dpsi, TRANS ? s->tgt64.p : nullptr, skip, skip_stride);
+  BIPB_LAUNCHED(s);
+}
+
+template <bool TRANS>
+void run_matvec_df(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
+                   double dpsi, const int* skip, int skip_stride) {
+  constexpr int NT = 128, TPT = 1, CH = 64;
+  using P = MatvecDFPolicy<TRANS>;
+  ItemPlan* plan = plan_pass<P, float4, NT, TPT, CH>(s, TRANS ? kPassMvDFT : kPassMvDF, matvec_sys(L), CH);
+  s->grow(s->recdf, (size_t)2 * L.len);  // 4 float4 per element
+  s->grow(s->part64, (size_t)plan->part_len);
+  const int4* lay = s->lay_dev(L);
+  k_pack_df<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, TRANS, s->tgt64.p, u, s->recdf.p, skip,
+                                                                        skip_stride);
+  BIPB_LAUNCHED(s);
+  typename P::Args a{s->tgt64.p, s->part64.p, c};
+  launch_items<P, float4, NT, TPT, CH>(s, TRANS ? kTMvDFT : kTMvDF, plan, a, s->recdf.p, skip, skip_stride);
   k_reduce_matvec<double><<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
       lay, plan->tab.p, s->part64.p, u, y, dphi, dpsi, TRANS ? s->tgt64.p : nullptr, skip, skip_stride);
   BIPB_LAUNCHED(s);
@@ -700,6 +825,14 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
             double* y, const int* skip, int skip_stride) {
   const double eps = m.eps_out / m.eps_in;
   const double dphi = 0.5 * (1.0 + eps), dpsi = 0.5 * (1.0 + 1.0 / eps);
+  if (precision == BIPB_DF64) {
+    DFConst c = df_const(m);
+    if (transpose)
+      run_matvec_df<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
+    else
+      run_matvec_df<false>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
+    return;
+  }
   if (precision == BIPB_FP64) {
     PairConst<double> c = pair_const<double>(m);
     if (transpose)

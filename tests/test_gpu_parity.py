@@ -67,7 +67,7 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
     ref = np.stack([f(p.centroids, p.normals, p.areas, eps, p.kappa, u) for u in U])
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
-        cases = [(bipb.FP64, 0)] + [(bipb.FP32, v) for v in range(bipb.MATVEC32_VARIANTS)]
+        cases = [(bipb.FP64, 0), (bipb.DF64, 0)] + [(bipb.FP32, v) for v in range(bipb.MATVEC32_VARIANTS)]
         for prec, variant in cases:
             s.set_variant(variant)
             yd = torch.full_like(ud, float("nan"))
@@ -77,6 +77,8 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
             scale = np.abs(ref).max()
             if prec == bipb.FP64:
                 np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * scale)
+            elif prec == bipb.DF64:
+                np.testing.assert_allclose(y, ref, rtol=0, atol=2e-12 * scale)
             else:
                 assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 3e-6, variant
                 assert np.abs(y - ref).max() < 2e-5 * scale, variant
@@ -93,7 +95,7 @@ def test_matvec_is_deterministic(bipb):
     p = _ragged(3)
     u = _dev(np.random.default_rng(0).standard_normal(2 * p.n))
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
-        for prec in (bipb.FP64, bipb.FP32):
+        for prec in (bipb.FP64, bipb.FP32, bipb.DF64):
             a, b = torch.empty_like(u), torch.empty_like(u)
             s.matvec(u, a, precision=prec)
             s.matvec(u, b, precision=prec)
@@ -156,24 +158,24 @@ def test_born_iteration_count_matches_oracle_gmres(bipb, orc):
     assert info[0]["rel_residual"] <= 1e-8
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "df64", "mixed_df64"])
 def test_kirkwood_solve(bipb, orc, prec):
     p = synth.kirkwood_problem(level=4)
     ref = orc.solve(p, method="gmres", tol=1e-12)
     phi_ref, dphi_ref = ref.surface_potential()
-    P = bipb.FP64 if prec == "fp64" else bipb.MIXED
-    tol = 1e-12 if prec == "fp64" else 1e-8
+    P = {"fp64": bipb.FP64, "mixed": bipb.MIXED, "df64": bipb.DF64, "mixed_df64": bipb.MIXED_DF64}[prec]
+    tol = 1e-12 if prec in ("fp64", "df64") else 1e-8
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         s.set_charges(p.charge_pos, p.q)
         info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=tol, precision=P)[0]
         e = s.energy()[0]
         phi, dphi = s.surface_potential()
     assert info["converged"] and info["rel_residual"] <= tol
-    rt = 1e-10 if prec == "fp64" else 1e-7
+    rt = 1e-10 if prec in ("fp64", "df64") else 1e-7
     assert e == pytest.approx(ref.energy_kcal, rel=rt)
     assert np.linalg.norm(phi[0] - phi_ref) / np.linalg.norm(phi_ref) < rt
     assert np.linalg.norm(dphi[0] - dphi_ref) / np.linalg.norm(dphi_ref) < rt
-    if prec == "mixed":
+    if prec.startswith("mixed"):
         assert info["refine_steps"] >= 1 and info["matvecs32"] > info["matvecs64"]
 
 
@@ -268,12 +270,14 @@ def test_full_size_matvec_sampled_rows(bipb, orc, cfg):
     ref = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows)
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(u)
-        y64, y32 = torch.empty_like(ud), torch.empty_like(ud)
+        y64, y32, ydf = torch.empty_like(ud), torch.empty_like(ud), torch.empty_like(ud)
         s.matvec(ud, y64, precision=bipb.FP64, med=_med(bipb, p))
         s.matvec(ud, y32, precision=bipb.FP32, med=_med(bipb, p))
-        a64, a32 = y64.cpu().numpy(), y32.cpu().numpy()
+        s.matvec(ud, ydf, precision=bipb.DF64, med=_med(bipb, p))
+        a64, a32, adf = y64.cpu().numpy(), y32.cpu().numpy(), ydf.cpu().numpy()
     scale = np.abs(ref).max()
     np.testing.assert_allclose(a64[rows], ref, rtol=0, atol=1e-12 * scale)
+    np.testing.assert_allclose(adf[rows], ref, rtol=0, atol=2e-12 * scale)
     assert np.abs(a32[rows] - ref).max() < 2e-5 * scale
 
 
