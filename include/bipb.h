@@ -59,7 +59,11 @@ typedef enum {
   BIPB_FP32 = 2,       /* mat-vec only: FP32 pair arithmetic, FP64 sums across tiles */
   BIPB_DF64 = 3,       /* pair arithmetic in double-float (two FP32 words, ~48 bits) on the FP32
                           pipe, FP64 sums across tiles; as a solve: GMRES on that mat-vec */
-  BIPB_MIXED_DF64 = 4  /* FP32 pair arithmetic inside GMRES, double-float refinement residual */
+  BIPB_MIXED_DF64 = 4, /* FP32 pair arithmetic inside GMRES, double-float refinement residual */
+  BIPB_TF32 = 5,       /* mat-vec only, right-hand sides of one surface: kernel tiles generated in
+                          FP32 and contracted against blocks of 64 right-hand sides on the tensor
+                          cores (TF32 operands, FP32 accumulation, FP64 sums across tiles) */
+  BIPB_MIXED_TF32 = 6  /* TF32 tensor-core mat-vec inside GMRES, double-float refinement residual */
 } bipb_precision;
 
 /* Dielectric medium (Sec. 2.1): eps_in > 0 inside, eps_out > 0 outside, kappa >= 0 (1/A). */
@@ -74,7 +78,7 @@ typedef struct {
   double tol;          /* target ||b - A u||_2 / ||b||_2, 0 < tol < 1 */
   int restart;         /* GMRES restart length m, 1..64 (10 if 0) */
   int max_iter;        /* cap on GMRES iterations summed over restarts and refinement steps (1000 if 0) */
-  int precision;       /* bipb_precision: BIPB_FP64, BIPB_MIXED, BIPB_DF64 or BIPB_MIXED_DF64 */
+  int precision;       /* bipb_precision: BIPB_FP64, BIPB_MIXED, BIPB_DF64, BIPB_MIXED_DF64 or BIPB_MIXED_TF32 */
   int inner_max_iter;  /* MIXED: cap on inner iterations per refinement step (200 if 0) */
   double inner_tol;    /* MIXED: inner relative tolerance per refinement step (1e-6 if 0) */
   const double* x0;    /* optional warm start, host, n_rhs x 2N internal units, or NULL (zero) */
@@ -183,7 +187,8 @@ bipb_status bipb_energy_grad(bipb_surface s, const bipb_solve_params* p, double*
  *   For a batch handle n_vec must be 1 and u, y are batched vectors (the
  *   block-diagonal operator of all surfaces).
  *   precision: BIPB_FP64, BIPB_FP32 (FP32 pair arithmetic per source tile,
- *   FP64 sums across tiles and for the diagonal) or BIPB_DF64.
+ *   FP64 sums across tiles and for the diagonal), BIPB_DF64 or BIPB_TF32
+ *   (single-surface handles; the tensor-core path of the multi-RHS mat-vec).
  */
 bipb_status bipb_matvec(bipb_surface s, const bipb_medium* m, int precision, int transpose,
                         int n_vec, const double* u, double* y);
@@ -219,7 +224,8 @@ typedef enum {
   BIPB_KERNEL_GRAD = 7,       /* energy-gradient pair kernel */
   BIPB_KERNEL_MATVECDF = 8,   /* double-float mat-vec pair kernel */
   BIPB_KERNEL_MATVECDF_T = 9, /* double-float transposed mat-vec pair kernel */
-  BIPB_KERNEL_KINDS = 10
+  BIPB_KERNEL_MATVEC_TC = 10, /* tensor-core multi-RHS mat-vec kernel */
+  BIPB_KERNEL_KINDS = 11
 } bipb_kernel_kind;
 
 /* Turn timing on (1) or off (0); turning it on clears the totals. */

@@ -31,6 +31,8 @@ MIXED = 1
 FP32 = 2
 DF64 = 3
 MIXED_DF64 = 4
+TF32 = 5
+MIXED_TF32 = 6
 
 KCAL = 4.0 * np.pi * 332.0716  # internal units -> kcal/mol (per e)
 
@@ -44,7 +46,7 @@ EXPORTED = (
 MATVEC32_VARIANTS = 7
 
 KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad",
-                "matvec_df", "matvec_df_t")
+                "matvec_df", "matvec_df_t", "matvec_tc")
 
 
 class bipb_medium(ctypes.Structure):

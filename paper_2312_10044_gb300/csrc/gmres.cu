@@ -539,10 +539,15 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   const int64_t len = L.len;
   const int nb = grid_for(len);
   const std::vector<double> bnorm = norms(s, w, rhs);
+  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_MIXED_TF32;
+  // arithmetic of the Krylov mat-vecs and of the residual r = b - A x (the
+  // adjoint solve has no tensor-core transpose and uses FP32 there)
+  const int inner = !mixed ? p.precision
+                           : (p.precision == BIPB_MIXED_TF32 && !transpose ? BIPB_TF32 : BIPB_FP32);
+  const int resid = (p.precision == BIPB_MIXED || p.precision == BIPB_FP64) ? BIPB_FP64 : BIPB_DF64;
   // r = rhs - A x (or rhs when starting from zero)
   if (warm) {
-    matvec(s, L, med, p.precision == BIPB_FP64 || p.precision == BIPB_MIXED ? BIPB_FP64 : BIPB_DF64, transpose, x,
-           w->t.p, nullptr, 0);
+    matvec(s, L, med, resid, transpose, x, w->t.p, nullptr, 0);
     for (auto& r : res) r.matvecs64++;
     k_sub<<<nb, kBS, 0, s->stream>>>(len, rhs, w->t.p, w->r.p);
     BIPB_LAUNCHED(s);
@@ -557,10 +562,6 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   }
   for (int k = 0; k < K; ++k)
     if (bnorm[k] == 0.0) rel[k] = 0.0;
-  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64;
-  // arithmetic of the Krylov mat-vecs and of the residual r = b - A x
-  const int inner = mixed ? BIPB_FP32 : p.precision;
-  const int resid = (p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_DF64) ? BIPB_DF64 : BIPB_FP64;
   const double inner_floor = p.inner_tol > 0 ? p.inner_tol : 1e-6;
   const int inner_cap = p.inner_max_iter > 0 ? p.inner_max_iter : 200;
   std::vector<char> active(K), done(K, 0);

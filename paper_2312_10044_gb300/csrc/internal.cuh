@@ -93,7 +93,8 @@ constexpr int kNumMv32Variants = 7;
 constexpr int kMaxRestart = 64;
 
 // Per-kernel CUDA-event timing of the pair kernels (off by default).
-enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTMvDF, kTMvDFT, kTKinds };
+enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTMvDF, kTMvDFT, kTMvTC,
+                 kTKinds };
 
 struct EventPair {
   int kind;
@@ -164,6 +165,8 @@ struct Surface {
   // per-pass scratch
   DevBuf<float4> rec32;
   DevBuf<float4> recdf;
+  DevBuf<float> upk;   // TF32 right-hand-side tiles of the tensor-core mat-vec
+  DevBuf<int> tc_err;  // set by the tensor-core kernel when a bounded wait ran out
   DevBuf<double4_32a> rec64;
   DevBuf<float> part32;
   DevBuf<double> part64;
@@ -244,6 +247,14 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
 // Time every FP32 mat-vec variant on layout L (reps launches each) and keep
 // the fastest; returns its index and its time per mat-vec in best_ms.
 int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int reps, double* best_ms);
+// y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)
+void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
+               double dpsi, const int* skip, int skip_stride);
+// FP64 reduction of FP32 per-split partials (kernels.cu), tab[k] = {n, splits, offset, 0}
+void launch_reduce_matvec32(Surface* s, const SysLayout& L, const int4* tab, const float* part, const double* u,
+                            double* y, double dphi, double dpsi, const int* skip, int skip_stride);
+// throws if a tensor-core kernel reported a timed-out wait since the last check (synchronises)
+void check_tc_error(Surface* s);
 // b = [S1; S2] of every system
 void source_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* b);
 // reaction potential at every charge (internal units, at chg_off) and E per system (kcal/mol)

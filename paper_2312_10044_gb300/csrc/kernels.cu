@@ -825,6 +825,10 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
             double* y, const int* skip, int skip_stride) {
   const double eps = m.eps_out / m.eps_in;
   const double dphi = 0.5 * (1.0 + eps), dpsi = 0.5 * (1.0 + 1.0 / eps);
+  if (precision == BIPB_TF32) {
+    matvec_tc(s, L, pair_const<float>(m), u, y, dphi, dpsi, skip, skip_stride);
+    return;
+  }
   if (precision == BIPB_DF64) {
     DFConst c = df_const(m);
     if (transpose)
@@ -860,6 +864,24 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
 #undef BIPB_MV32
     default:
       throw Error(BIPB_ERR_INVALID_ARG, "unknown FP32 mat-vec variant");
+  }
+}
+
+void launch_reduce_matvec32(Surface* s, const SysLayout& L, const int4* tab, const float* part, const double* u,
+                            double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
+  k_reduce_matvec<float><<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      s->lay_dev(L), tab, part, u, y, dphi, dpsi, nullptr, skip, skip_stride);
+  BIPB_LAUNCHED(s);
+}
+
+void check_tc_error(Surface* s) {
+  if (s->tc_err.cap == 0) return;
+  int h = 0;
+  BIPB_CUDA(cudaMemcpyAsync(&h, s->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));
+  if (h) {
+    BIPB_CUDA(cudaMemsetAsync(s->tc_err.p, 0, sizeof(int), s->stream));
+    throw Error(BIPB_ERR_CUDA, "tensor-core mat-vec: a bounded wait on an mbarrier ran out");
   }
 }
 

@@ -1,0 +1,318 @@
+// Multi-right-hand-side mat-vec on the 5th-generation tensor cores.
+//
+// Y = A U for a block of up to 64 right-hand sides U (2N x B) on one
+// surface.  Per CTA: 128 targets (two MMA tiles of M = 128 rows: target
+// unknowns phi_i, psi_i interleaved) against a range of source chunks of 16
+// sources (K = 32 source unknowns phi_j, psi_j interleaved).  For every chunk
+// the CUDA cores generate the kernel tile once,
+//     [ K2 ds_j   K1 ds_j ]        (row phi_i)
+//     [ K4 ds_j   K3 ds_j ]        (row psi_i)     (Sec. 2.2.1, Eqs. 5-6)
+// round it to TF32 (round to nearest) and store it in shared memory in the
+// K-major core-matrix layout; the matching U tile (TF32, packed per chunk in
+// global memory by k_pack_u_tc) arrives by a bulk TMA copy; one thread then
+// issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) into FP32
+// accumulators in tensor memory, which runs while the next tile is being
+// generated.  The epilogue reads TMEM and writes per-split partial sums that
+// the FP64 reduction of kernels.cu adds, so the kernel tile costs the same as
+// in the single-RHS kernel while serving 64 right-hand sides.
+//
+// TF32 keeps 10 mantissa bits, but the diagonal 1/2(1+eps), 1/2(1+1/eps) is
+// applied exactly in FP64 by the reduction and the off-diagonal sum is a few
+// per cent of a row, so the operator is accurate to about 1e-5 relative --
+// enough for the inner solves of the mixed refinement.
+//
+// Every wait on an mbarrier is bounded; a wait that runs out sets an error
+// flag that the host turns into BIPB_ERR_CUDA, and the kernel still frees its
+// tensor memory.
+#include <algorithm>
+
+#include "internal.cuh"
+#include "tcgen05.cuh"
+
+namespace bipb {
+
+namespace {
+
+constexpr int kNB = 64;          // right-hand sides per launch (MMA N)
+constexpr int kTgt = 128;        // targets per CTA (two M = 128 tiles)
+constexpr int kChunk = 16;       // sources per chunk
+constexpr int kK = 2 * kChunk;   // MMA K per chunk
+constexpr int kABytes = 2 * 128 * kK * 4;   // A tile of one chunk (both M tiles): 32 KB
+constexpr int kBBytes = kNB * kK * 4;       // U tile of one chunk: 8 KB
+constexpr int kSBytes = kChunk * 32;        // source records of one chunk: 512 B
+constexpr int kOffA = 0;                    // 2 A buffers
+constexpr int kOffB = 2 * kABytes;          // 4 U buffers
+constexpr int kOffS = kOffB + 4 * kBBytes;  // 4 source buffers
+constexpr int kOffBar = kOffS + 4 * kSBytes;
+constexpr int kSmemBytes = kOffBar + 8 * 8 + 16;
+constexpr uint32_t kTmemCols = 128;
+constexpr long kSpinLimit = 1L << 24;
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, the TF32 U tile in
+// the K-major core-matrix layout (row = right-hand side, K = 2 j' + c).
+__global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __restrict__ u, float* __restrict__ upk) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one per (chunk, b, k)
+  if (e >= (int64_t)n_chunks * kNB * kK) return;
+  const int ch = (int)(e / (kNB * kK));
+  const int rem = (int)(e % (kNB * kK));
+  const int b = rem / kK, k = rem % kK;
+  const int j = ch * kChunk + (k >> 1), c = k & 1;
+  float v = 0.f;
+  if (b < n_rhs && j < n) v = to_tf32((float)u[(int64_t)b * 2 * n + (int64_t)c * n + j]);
+  upk[(int64_t)ch * (kNB * kK) + tc::kmajor_offset(b, k, kK) / 4] = v;
+}
+
+// The four kernel values of pair (target i, source j) times ds_j (times 4 pi):
+// returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3]; zero when masked.
+__device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float nxi, float nyi, float nzi, float4 g,
+                                             float4 nv, bool zero, const PairConst<float>& c, float* v) {
+  const float dx = xi - g.x, dy = yi - g.y, dz = zi - g.z;
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  float s = fminf(rsqrt_approx(r2), kSMaxF);
+  s = zero ? 0.f : s;
+  const float r = r2 * s;
+  const float e = ex2_approx(r * c.nkl2e);
+  const float kr = r * c.kappa;
+  const float ci = nxi * dx + nyi * dy + nzi * dz;
+  const float cj = nv.x * dx + nv.y * dy + nv.z * dz;
+  const float cij = nxi * nv.x + nyi * nv.y + nzi * nv.z;
+  const float t = e * kr + e;
+  const float tm1 = t - 1.f;
+  const float wm3 = (t - e) * kr + 3.f * tm1;
+  const float sa = s * g.w;
+  const float s2 = s * s;
+  const float s3a = s2 * sa;
+  v[1] = to_tf32(sa - e * sa);                                  // K1 ds = (1 - e) s ds
+  v[0] = to_tf32(((c.eps * t - 1.f) * cj) * s3a);               // K2 ds
+  v[3] = to_tf32(((t * c.inveps - 1.f) * ci) * s3a);            // K3 ds
+  v[2] = to_tf32((tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a);   // K4 ds
+}
+
+// items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
+__global__ void __launch_bounds__(128, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
+                                                    const float4* __restrict__ tgt32, const float* __restrict__ upk,
+                                                    float* __restrict__ part, PairConst<float> c,
+                                                    int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources landed
+  uint64_t* done = full + 4;                                      // 2: MMAs of an A buffer finished
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 item = items[blockIdx.x];
+  const int t0 = item.x, c0 = item.y, c1 = item.z, split = item.w;
+
+  if (tid == 0) {
+    for (int q = 0; q < 4; ++q) tc::mbar_init(&full[q], 1);
+    for (int q = 0; q < 2; ++q) tc::mbar_init(&done[q], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  auto issue_load = [&](int it) {  // chunk c0 + it into buffer it & 3 (thread 0)
+    const int ch = c0 + it, q = it & 3;
+    const int cnt = min(kChunk, n - ch * kChunk);
+    arrive_expect_tx(&full[q], kBBytes + cnt * 32);
+    bulk_load(smem + kOffB + q * kBBytes, upk + (int64_t)ch * (kNB * kK), kBBytes, &full[q]);
+    bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &full[q]);
+  };
+  const int n_it = c1 - c0;
+  if (tid == 0) {
+    if (n_it > 0) issue_load(0);
+    if (n_it > 1) issue_load(1);
+  }
+
+  // this thread's target: rows 2 lt, 2 lt + 1 of M tile mb
+  const int mb = tid >> 6, lt = tid & 63;
+  const int ti = t0 + tid;
+  const bool tvalid = ti < n;
+  const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
+  const int row0 = 128 * mb + 2 * lt;
+  const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
+  const uint32_t idesc = tc::idesc_tf32(128, kNB);
+  bool ok = true;
+
+  for (int it = 0; it < n_it; ++it) {
+    const int s = it & 1, q = it & 3;
+    if (it >= 2) ok &= tc::mbar_wait(&done[s], ((it - 2) >> 1) & 1, kSpinLimit);
+    ok &= tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
+    const int ch = c0 + it;
+    const int j0 = ch * kChunk;
+    const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
+    unsigned char* A = smem + kOffA + s * kABytes;
+    const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
+#pragma unroll 2
+    for (int kb = 0; kb < kChunk / 2; ++kb) {
+      float va[4], vb[4];
+      const int ja = j0 + 2 * kb, jb = ja + 1;
+      const bool za = edge && (!tvalid || ja >= n || ja == ti);
+      const bool zb = edge && (!tvalid || jb >= n || jb == ti);
+      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb], S[4 * kb + 1], za, c, va);
+      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb + 2], S[4 * kb + 3], zb, c, vb);
+      if (za) va[0] = va[1] = va[2] = va[3] = 0.f;
+      if (zb) vb[0] = vb[1] = vb[2] = vb[3] = 0.f;
+      const float4 rphi = make_float4(va[0], va[1], vb[0], vb[1]);
+      const float4 rpsi = make_float4(va[2], va[3], vb[2], vb[3]);
+      float4* pphi = reinterpret_cast<float4*>(A + tc::kmajor_offset(row0, 4 * kb, kK));
+      float4* ppsi = reinterpret_cast<float4*>(A + tc::kmajor_offset(row0 + 1, 4 * kb, kK));
+      if (swap) {
+        *ppsi = rpsi;
+        *pphi = rphi;
+      } else {
+        *pphi = rphi;
+        *ppsi = rpsi;
+      }
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(smem + kOffB + q * kBBytes);
+      for (int m = 0; m < 2; ++m)
+        for (int ks = 0; ks < kK / 8; ++ks) {
+          const uint64_t ad = tc::smem_desc(a0 + m * (kABytes / 2) + 256 * ks, 128, (kK / 4) * 128);
+          const uint64_t bd = tc::smem_desc(b0 + 256 * ks, 128, (kK / 4) * 128);
+          tc::mma_tf32(tmem + m * kNB, ad, bd, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+        }
+      tc::mma_commit(&done[s]);
+      if (it + 2 < n_it) issue_load(it + 2);  // its buffer's last reader (chunk it - 2) is done
+    }
+  }
+  if (n_it > 0) ok &= tc::mbar_wait(&done[(n_it - 1) & 1], ((n_it - 1) >> 1) & 1, kSpinLimit);
+  tc::fence_after_sync();
+  const bool all_ok = __syncthreads_and(ok) != 0;
+  if (!all_ok && tid == 0) atomicExch(err, 1);
+
+  // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2
+  if (all_ok && n_it > 0) {
+    for (int m = 0; m < 2; ++m) {
+      const int r = 32 * warp + lane;
+      const int i = t0 + 64 * m + (r >> 1), comp = r & 1;
+      for (int cb = 0; cb < kNB / 16; ++cb) {
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + m * kNB + 16 * cb, v);
+        if (i < n)
+          for (int x = 0; x < 16; ++x) {
+            const int b = 16 * cb + x;
+            if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = v[x];
+          }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+int matvec_tc_block() { return kNB; }
+
+void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
+               double dpsi, const int* skip, int skip_stride) {
+  const int n = L.n[0];
+  for (int k = 0; k < L.K; ++k)
+    BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == n && L.vec_off[k] == 2 * n * k,
+                 "the tensor-core mat-vec needs right-hand sides of one surface");
+  BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrhs_tc, 128, kSmemBytes) != cudaSuccess || occ < 1) {
+    (void)cudaGetLastError();
+    occ = 1;
+  }
+  const int n_chunks = (n + kChunk - 1) / kChunk;
+  const int tiles = (n + kTgt - 1) / kTgt;
+  // source splits (whole chunks) that fill whole waves of resident CTAs
+  const int slots = s->num_sms * occ;
+  int best_s = 1;
+  double best = 0.0;
+  for (int sp = 1; sp <= std::min(8, std::max(1, n_chunks / 8)); ++sp) {
+    const long ctas = (long)tiles * sp, waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / ((double)waves * slots);
+    if (eff > best * 1.02) best = eff, best_s = sp;
+  }
+  const int S = best_s;
+  // work list, cached per (n, S)
+  const uint64_t key = 0x7c0000000000ull ^ ((uint64_t)n << 8) ^ (uint64_t)S;
+  auto it = s->plans.find(key);
+  ItemPlan* plan;
+  if (it == s->plans.end()) {
+    auto p = std::make_unique<ItemPlan>();
+    std::vector<int4> items;
+    for (int t = 0; t < tiles; ++t)
+      for (int sp = 0; sp < S; ++sp)
+        items.push_back(make_int4(t * kTgt, (int)((int64_t)sp * n_chunks / S), (int)((int64_t)(sp + 1) * n_chunks / S),
+                                  sp));
+    p->n_items = (int)items.size();
+    p->items.ensure(items.size());
+    BIPB_CUDA(cudaMemcpyAsync(p->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                              s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    ++s->alloc_gen;
+    plan = p.get();
+    s->plans[key] = std::move(p);
+  } else {
+    plan = it->second.get();
+  }
+  const int K = L.K;
+  s->grow(s->upk, (size_t)n_chunks * kNB * kK);
+  s->grow(s->part32, (size_t)std::min(K, kNB) * S * 2 * n);
+  if (s->tc_err.cap == 0) {
+    s->grow(s->tc_err, 1);
+    BIPB_CUDA(cudaMemsetAsync(s->tc_err.p, 0, sizeof(int), s->stream));
+  }
+  // per block of up to 64 right-hand sides: pack, tensor-core pass, FP64 reduction
+  for (int b0 = 0; b0 < K; b0 += kNB) {
+    const int nb = std::min(kNB, K - b0);
+    std::vector<int> go(nb, 0), nn(nb, n), co(nb, 0), nc(nb, 0);
+    SysLayout Lb = make_layout(go, nn, co, nc);
+    std::vector<int4> tab(nb);
+    for (int b = 0; b < nb; ++b) tab[b] = make_int4(n, S, b * S * 2 * n, 0);
+    const uint64_t tkey = 0x7d0000000000ull ^ ((uint64_t)n << 16) ^ ((uint64_t)S << 8) ^ (uint64_t)nb;
+    auto tt = s->plans.find(tkey);
+    if (tt == s->plans.end()) {
+      auto p = std::make_unique<ItemPlan>();
+      p->tab.ensure(nb);
+      BIPB_CUDA(cudaMemcpyAsync(p->tab.p, tab.data(), nb * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
+      BIPB_CUDA(cudaStreamSynchronize(s->stream));
+      ++s->alloc_gen;
+      tt = s->plans.emplace(tkey, std::move(p)).first;
+    }
+    const double* ub = u + (int64_t)b0 * 2 * n;
+    double* yb = y + (int64_t)b0 * 2 * n;
+    const int64_t pk = (int64_t)n_chunks * kNB * kK;
+    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, s->upk.p);
+    BIPB_LAUNCHED(s);
+    {
+      TimedLaunch tl(s, kTMvTC);
+      k_mrhs_tc<<<plan->n_items, 128, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p, s->upk.p,
+                                                               s->part32.p, c, s->tc_err.p);
+      BIPB_LAUNCHED(s);
+    }
+    launch_reduce_matvec32(s, Lb, tt->second->tab.p, s->part32.p, ub, yb, dphi, dpsi,
+                           skip ? skip + (int64_t)b0 * skip_stride : nullptr, skip_stride);
+  }
+}
+
+}  // namespace bipb

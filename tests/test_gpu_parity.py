@@ -386,3 +386,36 @@ def test_autograd_batched_mixed(bipb):
     # Euler identity per configuration: sum_k q_k dE/dq_k = 2 E (weights 1 and -2)
     assert torch.dot(q[0].detach(), q.grad[0]).item() == pytest.approx(2 * e[0].item(), rel=1e-6)
     assert torch.dot(q[1].detach(), q.grad[1]).item() == pytest.approx(-2 * 2 * e[1].item(), rel=1e-6)
+
+
+# ---------------------------------------------------------------- tensor-core multi-RHS
+@pytest.mark.parametrize("n_rhs", [5, 70])
+def test_tensor_core_matvec_matches_oracle(bipb, orc, n_rhs):
+    """TF32 tensor-core mat-vec (kernel tile once per 64 right-hand sides) vs
+    the FP64 oracle; the TF32 operator is accurate to about 1e-5 relative."""
+    p = _ragged(3)
+    eps = p.eps_out / p.eps_in
+    U = np.random.default_rng(30 + n_rhs).standard_normal((n_rhs, 2 * p.n))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TF32, med=_med(bipb, p))
+        Y = yd.cpu().numpy()
+    for r in (0, n_rhs // 2, n_rhs - 1):
+        ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
+        assert np.all(np.isfinite(Y[r]))
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-5
+        assert np.abs(Y[r] - ref).max() < 3e-4 * np.abs(ref).max()
+
+
+def test_mixed_tf32_solve_matches_oracle(bipb, orc):
+    base = synth.protein_like_problem(level=4, n_charges=30)
+    batch = synth.batched_charges(base, n_rhs=3, n_charges=30)
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.set_charges(batch.charge_pos, batch.q)
+        info = s.solve(tol=1e-9, precision=bipb.MIXED_TF32)
+        e = s.energy()
+    for r in range(3):
+        assert info[r]["converged"] and info[r]["rel_residual"] <= 1e-9
+        ref = orc.solve(batch, rhs=r, method="gmres", tol=1e-12)
+        assert e[r] == pytest.approx(ref.energy_kcal, rel=1e-7)
