@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--variant", type=int, default=-1, help="FP32 mat-vec variant for --mode matvec32")
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64", "matvecdf"],
+    ap.add_argument("--configs", default="3,4a,4b,5", help="--mode configs: which larger configurations")
+    ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64", "matvecdf", "configs"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
@@ -221,10 +222,125 @@ def run_matvec_only(args):
                       "gpairs": prob.n * (prob.n - 1) / ms / 1e6}), flush=True)
 
 
+def _timed(fn, torch):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    out = fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
+
+
+def run_configs(args):
+    """One timed run of each larger configuration (after one untimed warm-up
+    of the same call): protein-like single solve, 64-RHS batched solve on the
+    tensor-core path vs CUDA cores, uneven batch of 8 surfaces, and the
+    level-7 adjoint (forward + adjoint solve + gradient).  Prints one JSON
+    line per configuration."""
+    import torch
+
+    import synth
+    from paper_2312_10044_gb300.build import build
+
+    build()
+    import paper_2312_10044_gb300 as bipb
+
+    which = args.configs.split(",")
+    out = []
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+        out.append(d)
+
+    if "3" in which:
+        p = synth.protein_like_problem()
+        med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
+        with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+            s.set_charges(p.charge_pos, p.q)
+            v, mv = s.autotune(med, reps=2)
+            res = {"config": "protein-like N=81920, 2000 charges", "matvec32_variant": v, "matvec32_ms": mv}
+            for name, prec in (("mixed_df64", bipb.MIXED_DF64), ("mixed_fp64_residual", bipb.MIXED)):
+                prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=prec)
+                s.solve(prm)
+                ms, info = _timed(lambda: s.solve(prm), torch)
+                res[f"solve_ms_{name}"] = ms
+                res[f"{name}_info"] = info[0]
+            res["energy_kcal"] = float(s.energy()[0])
+            # plain FP64 GMRES: one run (26+ FP64 mat-vecs of ~0.7 s)
+            if not args.no_fp64:
+                prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.FP64)
+                ms, info = _timed(lambda: s.solve(prm), torch)
+                res["solve_ms_fp64"] = ms
+                res["fp64_info"] = info[0]
+            emit(res)
+    if "4a" in which:
+        base = synth.protein_like_problem()
+        p = synth.batched_charges(base, n_rhs=64, n_charges=2000)
+        med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
+        with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+            s.set_charges(p.charge_pos, p.q)
+            n = p.n
+            U = torch.randn(64, 2 * n, dtype=torch.float64, device="cuda")
+            Y = torch.empty_like(U)
+            res = {"config": "batched: protein-like N=81920, 64 charge sets x 2000"}
+            for name, prec in (("tf32_tensor", bipb.TF32), ("fp32_cuda_cores", bipb.FP32)):
+                s.matvec(U, Y, precision=prec, med=med)
+                ms, _ = _timed(lambda: s.matvec(U, Y, precision=prec, med=med), torch)
+                res[f"matvec64rhs_ms_{name}"] = ms
+                res[f"pair_rhs_per_s_{name}"] = 64 * n * (n - 1) / (ms / 1e3)
+            prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.MIXED_TF32)
+            bipb.timer_enable(s, True)
+            ms, info = _timed(lambda: s.solve(prm), torch)
+            t = bipb.timer_read(s)
+            bipb.timer_enable(s, False)
+            res["solve_ms_mixed_tf32_64rhs"] = ms
+            res["kernel_ms"] = {k: v[1] for k, v in t.items() if v[0]}
+            res["iters_max"] = max(i["iters"] for i in info)
+            res["refine_steps_max"] = max(i["refine_steps"] for i in info)
+            res["rel_residual_max"] = max(i["rel_residual"] for i in info)
+            emit(res)
+    if "4b" in which:
+        probs = synth.uneven_batch_problems()
+        with bipb.BatchSurface([(q.centroids, q.normals, q.areas) for q in probs]) as s:
+            s.set_charges([(q.charge_pos, q.q[0]) for q in probs])
+            prm = bipb.solve_params(probs[0].eps_in, probs[0].eps_out, probs[0].kappa, tol=TOL,
+                                    precision=bipb.MIXED_DF64)
+            s.solve(prm)
+            ms, info = _timed(lambda: s.solve(prm), torch)
+            res = {"config": "uneven batch: 8 displaced spheres, levels 4,4,4,5,5,5,6,6",
+                   "sizes": [q.n for q in probs], "sum_n2": sum(q.n * q.n for q in probs),
+                   "solve_ms_mixed_df64": ms, "iters": [i["iters"] for i in info],
+                   "rel_residual_max": max(i["rel_residual"] for i in info)}
+            # the same surfaces one at a time
+            tot = 0.0
+            for q in probs:
+                with bipb.Surface(q.centroids, q.normals, q.areas) as s1:
+                    s1.set_charges(q.charge_pos, q.q)
+                    s1.solve(prm)
+                    m1, _ = _timed(lambda: s1.solve(prm), torch)
+                    tot += m1
+            res["solve_ms_one_at_a_time"] = tot
+            emit(res)
+    if "5" in which:
+        p = synth.adjoint_problem()
+        with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+            s.set_charges(p.charge_pos, p.q)
+            prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.MIXED_DF64)
+            ms_f, info = _timed(lambda: s.solve(prm), torch)
+            ms_g, (dq, dy) = _timed(lambda: s.energy_grad(prm), torch)
+            emit({"config": "adjoint: displaced icosphere level 7 (N=327680), R=45, 10000 charges",
+                  "solve_ms_mixed_df64": ms_f, "energy_grad_ms": ms_g, "info": info[0],
+                  "energy_kcal": float(s.energy()[0]), "max_abs_force": float(np.abs(dy).max())})
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "configs":
+        return run_configs(args)
     if args.mode != "solve":
         return run_matvec_only(args)
     import torch

@@ -419,3 +419,22 @@ def test_mixed_tf32_solve_matches_oracle(bipb, orc):
         assert info[r]["converged"] and info[r]["rel_residual"] <= 1e-9
         ref = orc.solve(batch, rhs=r, method="gmres", tol=1e-12)
         assert e[r] == pytest.approx(ref.energy_kcal, rel=1e-7)
+
+
+def test_adjoint_config_level4_copy_matches_oracle(bipb, orc):
+    """The adjoint configuration (R = 45 A, 10000 charges) on a level-4 copy of
+    its surface: dE/dq and dE/dpos of 32 seeded atoms vs the oracle's FP64 adjoint."""
+    p = synth.adjoint_problem(level=4)
+    e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="gmres", tol=1e-12)
+    atoms = np.random.default_rng(32).choice(p.nc, 32, replace=False)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        s.solve(tol=1e-12, precision=bipb.FP64)
+        assert s.energy()[0] == pytest.approx(e_ref, rel=1e-10)
+        dq, dy = s.energy_grad(tol=1e-12, precision=bipb.FP64)
+        np.testing.assert_allclose(dq[0][atoms], dq_ref[atoms], rtol=1e-8)
+        np.testing.assert_allclose(dy[0][atoms], dy_ref[atoms], rtol=1e-6, atol=1e-8 * np.abs(dy_ref).max())
+        # the mixed path (FP32 Krylov, double-float residual), forward and adjoint at 1e-10
+        s.solve(tol=1e-10, precision=bipb.MIXED_DF64)
+        dqm, dym = s.energy_grad(tol=1e-10, precision=bipb.MIXED_DF64)
+        np.testing.assert_allclose(dym[0][atoms], dy_ref[atoms], rtol=1e-5, atol=1e-7 * np.abs(dy_ref).max())
