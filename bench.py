@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--variant", type=int, default=-1, help="FP32 mat-vec variant for --mode matvec32")
     ap.add_argument("--configs", default="3,4a,4b,5", help="--mode configs: which larger configurations")
-    ap.add_argument("--mode", default="solve", choices=["solve", "matvec32", "matvec64", "matvecdf", "configs"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvectc", "configs"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
@@ -201,12 +202,13 @@ def run_matvec_only(args):
     import paper_2312_10044_gb300 as bipb
 
     prob, desc = workload(args.workload)
-    prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64}[args.mode]
+    prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64, "matvectc": bipb.TF32}[args.mode]
+    n_vec = 64 if args.mode == "matvectc" else 1
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
     with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
         if args.variant >= 0:
             s.set_variant(args.variant)
-        u = torch.randn(2 * prob.n, dtype=torch.float64, device="cuda")
+        u = torch.randn(n_vec, 2 * prob.n, dtype=torch.float64, device="cuda")
         y = torch.empty_like(u)
         for _ in range(args.warmup):
             s.matvec(u, y, precision=prec, med=med)
@@ -218,8 +220,9 @@ def run_matvec_only(args):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
-    print(json.dumps({"mode": args.mode, "workload": desc, "ms_per_matvec": ms,
-                      "gpairs": prob.n * (prob.n - 1) / ms / 1e6}), flush=True)
+    print(json.dumps({"mode": args.mode, "workload": desc, "n_vec": n_vec, "ms_per_matvec": ms,
+                      "gpairs": prob.n * (prob.n - 1) / ms / 1e6,
+                      "g_pair_rhs": n_vec * prob.n * (prob.n - 1) / ms / 1e6}), flush=True)
 
 
 def _timed(fn, torch):
