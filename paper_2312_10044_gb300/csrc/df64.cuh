@@ -197,3 +197,46 @@ __device__ __forceinline__ void df_pair_transpose(const df* xj, const df* nj, co
 }
 
 }  // namespace bipb
+
+namespace bipb {
+
+// The four kernel values of pair (target i, source j) times ds_j (times 4 pi)
+// in df64: k[0] = K2 ds, k[1] = K1 ds, k[2] = K4 ds, k[3] = K3 ds (the 2 x 2
+// block that maps (phi_j, psi_j) to the (phi_i, psi_i) rows).  s = 0 for the
+// self pair when MASK and self.
+template <bool MASK>
+__device__ __forceinline__ void df_kernel_block(const df* xi, const df* ni, const df* xj, const df* nj, df area,
+                                                bool self, const DFConst& c, const df* tab, df* k) {
+  const df dx = df_sub(xi[0], xj[0]), dy = df_sub(xi[1], xj[1]), dz = df_sub(xi[2], xj[2]);
+  const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  df s = df_rsqrt(r2);
+  if (MASK && self) s = df{0.0f, 0.0f};
+  const df r = df_mul(r2, s);
+  const df kr = df_mul(r, c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df ci = df_dot3(ni[0], ni[1], ni[2], dx, dy, dz);
+  const df cj = df_dot3(nj[0], nj[1], nj[2], dx, dy, dz);
+  const df cij = df_dot3(ni[0], ni[1], ni[2], nj[0], nj[1], nj[2]);
+  const df t = df_add(df_mul(e, kr), e);
+  const df tm1 = df_add_f(t, -1.0f);
+  const df wm3 = df_add(df_mul(df_sub(t, e), kr), df_mul_f(tm1, 3.0f));
+  const df sa = df_mul(s, area);
+  const df s2 = df_sqr(s);
+  const df s3a = df_mul(s2, sa);
+  k[1] = df_mul(df_add_f(df_neg(e), 1.0f), sa);                                     // K1 ds
+  k[0] = df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cj), s3a);                // K2 ds
+  k[3] = df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), ci), s3a);             // K3 ds
+  k[2] = df_mul(df_sub(df_mul(tm1, cij), df_mul(wm3, df_mul(df_mul(ci, cj), s2))), s3a);  // K4 ds
+}
+
+// acc += a * b with an exact leading product and an unnormalised trailing
+// part (renormalise with fast_two_sum before use).
+__device__ __forceinline__ void df_mac(df& acc, df a, df b) {
+  const df p = two_prod(a.hi, b.hi);
+  const float plo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+  const df s = two_sum(acc.hi, p.hi);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, plo));
+}
+
+}  // namespace bipb

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "bipb.h"
+#include "df64.cuh"
 #include "pair.cuh"
 
 namespace bipb {
@@ -250,6 +251,14 @@ int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int 
 // y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)
 void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
                double dpsi, const int* skip, int skip_stride);
+// y = A u for right-hand sides of one surface, double-float arithmetic, kernel
+// blocks shared by 16 right-hand sides (mrhs_df.cu)
+void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
+                    double dpsi, const int* skip, int skip_stride);
+DFConst make_df_const(const bipb_medium& m);
+// FP64 reduction of FP64 per-split partials (kernels.cu), tab[k] = {n, splits, offset, 0}
+void launch_reduce_matvec64(Surface* s, const SysLayout& L, const int4* tab, const double* part, const double* u,
+                            double* y, double dphi, double dpsi, const int* skip, int skip_stride);
 // FP64 reduction of FP32 per-split partials (kernels.cu), tab[k] = {n, splits, offset, 0}
 void launch_reduce_matvec32(Surface* s, const SysLayout& L, const int4* tab, const float* part, const double* u,
                             double* y, double dphi, double dpsi, const int* skip, int skip_stride);

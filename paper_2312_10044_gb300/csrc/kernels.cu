@@ -16,7 +16,6 @@
 #include <cmath>
 #include <cstring>
 
-#include "df64.cuh"
 #include "internal.cuh"
 
 namespace bipb {
@@ -685,7 +684,7 @@ int blocks_for(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1
 enum PassId { kPassMv64 = 1, kPassMv64T, kPassMvDF, kPassMvDFT, kPassMv32 = 16, kPassMv32T = 32, kPassSource = 48,
               kPassReaction, kPassRow, kPassGrad };
 
-DFConst df_const(const bipb_medium& m) {
+DFConst df_const_impl(const bipb_medium& m) {
   auto split = [](double v) {
     df r;
     r.hi = (float)v;
@@ -830,7 +829,14 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     return;
   }
   if (precision == BIPB_DF64) {
-    DFConst c = df_const(m);
+    DFConst c = df_const_impl(m);
+    bool shared_surface = L.K >= 4;
+    for (int k = 0; k < L.K && shared_surface; ++k)
+      shared_surface = L.geo_off[k] == 0 && L.n[k] == L.n[0] && L.vec_off[k] == 2 * L.n[0] * k;
+    if (shared_surface && !transpose) {  // kernel blocks shared by 16 right-hand sides
+      matvec_df_mrhs(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
+      return;
+    }
     if (transpose)
       run_matvec_df<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     else
@@ -865,6 +871,15 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     default:
       throw Error(BIPB_ERR_INVALID_ARG, "unknown FP32 mat-vec variant");
   }
+}
+
+DFConst make_df_const(const bipb_medium& m) { return df_const_impl(m); }
+
+void launch_reduce_matvec64(Surface* s, const SysLayout& L, const int4* tab, const double* part, const double* u,
+                            double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
+  k_reduce_matvec<double><<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      s->lay_dev(L), tab, part, u, y, dphi, dpsi, nullptr, skip, skip_stride);
+  BIPB_LAUNCHED(s);
 }
 
 void launch_reduce_matvec32(Surface* s, const SysLayout& L, const int4* tab, const float* part, const double* u,

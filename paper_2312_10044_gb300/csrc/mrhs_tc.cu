@@ -1,9 +1,10 @@
 // Multi-right-hand-side mat-vec on the 5th-generation tensor cores.
 //
 // Y = A U for a block of up to 64 right-hand sides U (2N x B) on one
-// surface.  Per CTA: 128 targets (two MMA tiles of M = 128 rows: target
-// unknowns phi_i, psi_i interleaved) against a range of source chunks of 16
-// sources (K = 32 source unknowns phi_j, psi_j interleaved).  For every chunk
+// surface.  Per CTA (256 threads, two per target, each generating half of a
+// chunk): 128 targets (two MMA tiles of M = 128 rows: target unknowns phi_i,
+// psi_i interleaved) against a range of source chunks of 16 sources (K = 32
+// source unknowns phi_j, psi_j interleaved).  For every chunk
 // the CUDA cores generate the kernel tile once,
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i)
 //     [ K4 ds_j   K3 ds_j ]        (row psi_i)     (Sec. 2.2.1, Eqs. 5-6)
@@ -106,7 +107,9 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
 }
 
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
-__global__ void __launch_bounds__(128, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads, 2) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
                                                     const float4* __restrict__ tgt32, const float* __restrict__ upk,
                                                     float* __restrict__ part, PairConst<float> c,
                                                     int* __restrict__ err) {
@@ -142,9 +145,9 @@ __global__ void __launch_bounds__(128, 1) k_mrhs_tc(int n, int n_rhs, int n_spli
     if (n_it > 1) issue_load(1);
   }
 
-  // this thread's target: rows 2 lt, 2 lt + 1 of M tile mb
-  const int mb = tid >> 6, lt = tid & 63;
-  const int ti = t0 + tid;
+  // this thread's target: rows 2 lt, 2 lt + 1 of M tile mb; half h of each chunk
+  const int mb = (tid >> 6) & 1, lt = tid & 63, h = tid >> 7;
+  const int ti = t0 + (tid & 127);
   const bool tvalid = ti < n;
   const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
   const int row0 = 128 * mb + 2 * lt;
@@ -161,8 +164,9 @@ __global__ void __launch_bounds__(128, 1) k_mrhs_tc(int n, int n_rhs, int n_spli
     const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
     unsigned char* A = smem + kOffA + s * kABytes;
     const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
-#pragma unroll 2
-    for (int kb = 0; kb < kChunk / 2; ++kb) {
+#pragma unroll
+    for (int kk = 0; kk < kChunk / 4; ++kk) {
+      const int kb = (kChunk / 4) * h + kk;
       float va[4], vb[4];
       const int ja = j0 + 2 * kb, jb = ja + 1;
       const bool za = edge && (!tvalid || ja >= n || ja == ti);
@@ -204,14 +208,16 @@ __global__ void __launch_bounds__(128, 1) k_mrhs_tc(int n, int n_rhs, int n_spli
   const bool all_ok = __syncthreads_and(ok) != 0;
   if (!all_ok && tid == 0) atomicExch(err, 1);
 
-  // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2
+  // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2;
+  // warp w reads lane quarter w % 4 of tile w / 4
   if (all_ok && n_it > 0) {
-    for (int m = 0; m < 2; ++m) {
-      const int r = 32 * warp + lane;
+    {
+      const int m = warp >> 2, quarter = warp & 3;
+      const int r = 32 * quarter + lane;
       const int i = t0 + 64 * m + (r >> 1), comp = r & 1;
       for (int cb = 0; cb < kNB / 16; ++cb) {
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + m * kNB + 16 * cb, v);
+        tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + m * kNB + 16 * cb, v);
         if (i < n)
           for (int x = 0; x < 16; ++x) {
             const int b = 16 * cb + x;
@@ -237,7 +243,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
                  "the tensor-core mat-vec needs right-hand sides of one surface");
   BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrhs_tc, 128, kSmemBytes) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrhs_tc, kThreads, kSmemBytes) != cudaSuccess || occ < 1) {
     (void)cudaGetLastError();
     occ = 1;
   }
@@ -306,7 +312,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     BIPB_LAUNCHED(s);
     {
       TimedLaunch tl(s, kTMvTC);
-      k_mrhs_tc<<<plan->n_items, 128, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p, s->upk.p,
+      k_mrhs_tc<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p, s->upk.p,
                                                                s->part32.p, c, s->tc_err.p);
       BIPB_LAUNCHED(s);
     }

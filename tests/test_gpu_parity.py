@@ -438,3 +438,19 @@ def test_adjoint_config_level4_copy_matches_oracle(bipb, orc):
         s.solve(tol=1e-10, precision=bipb.MIXED_DF64)
         dqm, dym = s.energy_grad(tol=1e-10, precision=bipb.MIXED_DF64)
         np.testing.assert_allclose(dym[0][atoms], dy_ref[atoms], rtol=1e-5, atol=1e-7 * np.abs(dy_ref).max())
+
+
+@pytest.mark.parametrize("n_rhs", [5, 70])
+def test_multi_rhs_df64_matvec_matches_oracle(bipb, orc, n_rhs):
+    """The batched double-float mat-vec (kernel block shared by 16 right-hand sides)."""
+    p = _ragged(3)
+    eps = p.eps_out / p.eps_in
+    U = np.random.default_rng(40 + n_rhs).standard_normal((n_rhs, 2 * p.n))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.DF64, med=_med(bipb, p))
+        Y = yd.cpu().numpy()
+    for r in (0, n_rhs // 2, n_rhs - 1):
+        ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
+        np.testing.assert_allclose(Y[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
