@@ -65,9 +65,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--variant", type=int, default=-1, help="FP32 mat-vec variant for --mode matvec32")
+    ap.add_argument("--ordered-pairs", action="store_true",
+                    help="FP64 / double-float mat-vecs visit every ordered pair (default: unordered pairs once)")
     ap.add_argument("--configs", default="3,4a,4b,5", help="--mode configs: which larger configurations")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvectc", "configs"],
+                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "configs"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
@@ -202,12 +204,15 @@ def run_matvec_only(args):
     import paper_2312_10044_gb300 as bipb
 
     prob, desc = workload(args.workload)
-    prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64, "matvectc": bipb.TF32}[args.mode]
-    n_vec = 64 if args.mode == "matvectc" else 1
+    prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64, "matvecdfm": bipb.DF64,
+            "matvectc": bipb.TF32}[args.mode]
+    n_vec = 64 if args.mode in ("matvectc", "matvecdfm") else 1
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
     with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
         if args.variant >= 0:
             s.set_variant(args.variant)
+        if args.ordered_pairs:
+            s.symmetric_pairs(False)
         u = torch.randn(n_vec, 2 * prob.n, dtype=torch.float64, device="cuda")
         y = torch.empty_like(u)
         for _ in range(args.warmup):

@@ -237,18 +237,30 @@ bipb_status bipb_timer_read(bipb_surface s, int kind, int64_t* launches, double*
 
 /*
  * Autotuner of the FP32 mat-vec tiling (threads per CTA, targets per thread,
- * sources per shared-memory chunk): times every compiled variant, reps
- * launches each, on this surface and medium, keeps the fastest for the
- * handle, and returns its index (host, may be NULL) and its time per mat-vec
- * in ms (host, may be NULL).  Synchronises the handle's stream.  Variants
- * differ only in summation order, not in the operator.
+ * sources per shared-memory chunk, and whether each unordered pair is
+ * visited once or twice): times every compiled variant, reps launches each,
+ * on this surface and medium, keeps the fastest for the handle, and returns
+ * its index (host, may be NULL) and its time per mat-vec in ms (host, may be
+ * NULL).  Synchronises the handle's stream.  Variants differ only in
+ * summation order, not in the operator.
  */
 bipb_status bipb_autotune(bipb_surface s, const bipb_medium* m, int reps, int* variant,
                           double* ms_per_matvec);
 
-/* Select an FP32 mat-vec variant by index, 0 <= variant < BIPB_MATVEC32_VARIANTS. */
-#define BIPB_MATVEC32_VARIANTS 7
+/* Select an FP32 mat-vec variant by index, 0 <= variant < BIPB_MATVEC32_VARIANTS.
+ * Variants 0-6 visit every ordered pair (i, j) (one target per thread
+ * gathering all sources); variants 7-9 visit every unordered pair {i, j} once
+ * and apply it to both rows, sharing 1/r, exp(-kappa r), t and w between the
+ * two directions of Eqs. 5-6. */
+#define BIPB_MATVEC32_VARIANTS 10
 bipb_status bipb_matvec_variant(bipb_surface s, int variant);
+
+/* How the FP64 and double-float mat-vecs (and their transposes) visit pairs:
+ * symmetric = 1 (the default) evaluates every unordered pair once and applies
+ * it to both rows; symmetric = 0 evaluates every ordered pair.  Both compute
+ * the operator of Eqs. 5-6 and differ only in summation order.  Surfaces too
+ * large for the symmetric work list use the ordered form either way. */
+bipb_status bipb_symmetric_pairs(bipb_surface s, int symmetric);
 
 /* Number of CUDA kernels this handle has launched since creation (kernels
  * inside replayed CUDA graphs included).  Host output; no synchronisation. */

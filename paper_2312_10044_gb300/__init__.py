@@ -42,8 +42,9 @@ EXPORTED = (
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
     "bipb_autotune", "bipb_matvec_variant", "bipb_surface_create_batch", "bipb_charges_set_batch",
+    "bipb_symmetric_pairs",
 )
-MATVEC32_VARIANTS = 7
+MATVEC32_VARIANTS = 10
 
 KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad",
                 "matvec_df", "matvec_df_t", "matvec_tc")
@@ -126,6 +127,7 @@ def load_library():
         "bipb_surface_create_batch": ([I, P, P, P, P, P, P], st),
         "bipb_charges_set_batch": ([P, P, P, P], st),
         "bipb_matvec_variant": ([P, I], st),
+        "bipb_symmetric_pairs": ([P, I], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -308,6 +310,10 @@ class Surface:
 
     def set_variant(self, variant):
         _check(self._L.bipb_matvec_variant(self._h, int(variant)))
+
+    def symmetric_pairs(self, on=True):
+        """FP64 / double-float mat-vecs: visit every unordered pair once (True) or every ordered pair."""
+        _check(self._L.bipb_symmetric_pairs(self._h, int(bool(on))))
 
     def source(self, b, med=None):
         m = med if med is not None else medium()

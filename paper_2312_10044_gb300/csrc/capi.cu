@@ -571,6 +571,14 @@ bipb_status bipb_matvec_variant(bipb_surface h, int variant) {
   });
 }
 
+bipb_status bipb_symmetric_pairs(bipb_surface h, int symmetric) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(symmetric == 0 || symmetric == 1, "symmetric must be 0 or 1");
+    s->sym_pairs = symmetric != 0;
+  });
+}
+
 bipb_status bipb_launch_count(bipb_surface h, int64_t* launches) {
   return guarded([&] {
     Surface* s = checked(h);

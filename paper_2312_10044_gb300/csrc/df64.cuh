@@ -240,3 +240,68 @@ __device__ __forceinline__ void df_mac(df& acc, df a, df b) {
 }
 
 }  // namespace bipb
+
+namespace bipb {
+
+// Symmetric pair terms in df64 (the radial part shared by both directions of
+// an unordered pair; see SymTerms in pair.cuh).
+struct DFTerms {
+  df s, s2, s3, ome, tm1, wm3, et1, te1;
+};
+
+template <bool MASK>
+__device__ __forceinline__ DFTerms df_sym_terms(df dx, df dy, df dz, bool self, const DFConst& c, const df* tab) {
+  DFTerms R;
+  const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  R.s = df_rsqrt(r2);
+  if (MASK && self) R.s = df{0.0f, 0.0f};
+  const df r = df_mul(r2, R.s);
+  const df kr = df_mul(r, c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df ekr = df_mul(e, kr);
+  const df t = df_add(ekr, e);
+  R.tm1 = df_add_f(t, -1.0f);
+  R.wm3 = df_add(df_mul(ekr, kr), df_mul_f(R.tm1, 3.0f));  // 3 (t - 1) + e (kappa r)^2
+  R.ome = df_add_f(df_neg(e), 1.0f);
+  R.s2 = df_sqr(R.s);
+  R.s3 = df_mul(R.s2, R.s);
+  R.et1 = df_add_f(df_mul(c.eps, t), -1.0f);
+  R.te1 = df_add_f(df_mul(t, c.inveps), -1.0f);
+  return R;
+}
+
+__device__ __forceinline__ df df_signed(df x, int sign) { return sign > 0 ? x : df_neg(x); }
+
+// Forward direction in df64 (sym_forward in pair.cuh).
+template <int SIGN>
+__device__ __forceinline__ void df_sym_forward(const DFTerms& R, const df* d, const df* nt, df a, const df* m,
+                                               df& accP, df& accQ) {
+  const df ci = df_dot3(nt[0], nt[1], nt[2], d[0], d[1], d[2]);
+  const df cm = df_dot3(m[0], m[1], m[2], d[0], d[1], d[2]);
+  const df cim = df_dot3(nt[0], nt[1], nt[2], m[0], m[1], m[2]);
+  df p = df_mul(R.ome, a);
+  p = df_add(p, df_mul(df_mul(df_signed(R.et1, SIGN), cm), R.s2));
+  accP = df_add(accP, df_mul(p, R.s));
+  df q = df_mul(df_mul(df_signed(R.te1, SIGN), ci), a);
+  q = df_add(q, df_mul(R.tm1, cim));
+  q = df_sub(q, df_mul(R.wm3, df_mul(df_mul(ci, cm), R.s2)));
+  accQ = df_add(accQ, df_mul(q, R.s3));
+}
+
+// Transposed direction in df64 (sym_transpose in pair.cuh).
+template <int SIGN>
+__device__ __forceinline__ void df_sym_transpose(const DFTerms& R, const df* d, const df* no, df wphi, const df* pv,
+                                                 df& accP, df& accQ) {
+  const df cj = df_dot3(no[0], no[1], no[2], d[0], d[1], d[2]);
+  const df cp = df_dot3(pv[0], pv[1], pv[2], d[0], d[1], d[2]);
+  const df cnp = df_dot3(no[0], no[1], no[2], pv[0], pv[1], pv[2]);
+  df q = df_mul(df_mul(df_signed(R.et1, SIGN), cj), wphi);
+  q = df_add(q, df_mul(R.tm1, cnp));
+  q = df_sub(q, df_mul(R.wm3, df_mul(df_mul(cp, cj), R.s2)));
+  accP = df_add(accP, df_mul(q, R.s3));
+  df p = df_mul(R.ome, wphi);
+  p = df_add(p, df_mul(df_mul(df_signed(R.te1, SIGN), cp), R.s2));
+  accQ = df_add(accQ, df_mul(p, R.s));
+}
+
+}  // namespace bipb

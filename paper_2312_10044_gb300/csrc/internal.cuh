@@ -87,9 +87,12 @@ struct ItemPlan {
 };
 
 // FP32 mat-vec kernel variants (threads per CTA, targets per thread,
-// sources per shared-memory chunk): 0 (256,2,128) 1 (256,1,128)
-// 2 (128,2,128) 3 (256,4,128) 4 (128,4,64) 5 (512,1,128) 6 (256,2,64).
-constexpr int kNumMv32Variants = 7;
+// sources per shared-memory chunk): every ordered pair: 0 (256,2,128)
+// 1 (256,1,128) 2 (128,2,128) 3 (256,4,128) 4 (128,4,64) 5 (512,1,128)
+// 6 (256,2,64); every unordered pair once (sym.cu): 7 (256,2,128)
+// 8 (128,4,128) 9 (256,4,64).
+constexpr int kNumMv32Variants = 10;
+constexpr int kFirstSymVariant = 7;
 
 constexpr int kMaxRestart = 64;
 
@@ -199,6 +202,7 @@ struct Surface {
   bipb_medium solved_medium{0, 0, 0};
 
   int mv32_variant = 0;  // index into the FP32 mat-vec variants (set by the autotuner)
+  bool sym_pairs = true;  // FP64 / double-float mat-vecs visit unordered pairs once (sym.cu)
   GmresWork* gw = nullptr;
   KernelTimer timer;
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves (recorded graphs go stale)
@@ -248,6 +252,14 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
 // Time every FP32 mat-vec variant on layout L (reps launches each) and keep
 // the fastest; returns its index and its time per mat-vec in best_ms.
 int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int reps, double* best_ms);
+// ---- sym.cu: mat-vecs visiting every unordered pair once; false when the
+// layout is too large for the symmetric work list (nothing launched then)
+bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, int variant,
+                  const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride);
+bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, bool transpose, const double* u,
+                  double* y, double dphi, double dpsi, const int* skip, int skip_stride);
+bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
+                   double dphi, double dpsi, const int* skip, int skip_stride);
 // y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)
 void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
                double dpsi, const int* skip, int skip_stride);

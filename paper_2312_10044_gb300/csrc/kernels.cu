@@ -837,6 +837,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
       matvec_df_mrhs(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
       return;
     }
+    if (s->sym_pairs && matvec_sym_df(s, L, c, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;
     if (transpose)
       run_matvec_df<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     else
@@ -845,6 +846,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
   }
   if (precision == BIPB_FP64) {
     PairConst<double> c = pair_const<double>(m);
+    if (s->sym_pairs && matvec_sym64(s, L, c, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;
     if (transpose)
       run_matvec64<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     else
@@ -852,7 +854,12 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     return;
   }
   PairConst<float> c = pair_const<float>(m);
-  switch (s->mv32_variant) {
+  int variant = s->mv32_variant;
+  if (variant >= kFirstSymVariant) {
+    if (matvec_sym32(s, L, c, transpose, variant - kFirstSymVariant, u, y, dphi, dpsi, skip, skip_stride)) return;
+    variant = 0;  // too large for the symmetric work list
+  }
+  switch (variant) {
 #define BIPB_MV32(I_, NT_, TPT_, CH_)                                                      \
   case I_:                                                                                 \
     if (transpose)                                                                         \

@@ -133,4 +133,71 @@ __device__ __forceinline__ void pair_transpose(T xj, T yj, T zj, T nxj, T nyj, T
   accQ = p * s + accQ;
 }
 
+// ------------------------------------------------------------------ symmetric pairs
+// The four kernels depend on the pair through r, e, t, w (symmetric in i and
+// j) and through c_i, c_j, c_ij and the sign of d (d_ji = -d_ij).  A kernel
+// that visits the unordered pair {i, j} once computes the radial terms once
+// and applies them in both directions: target i gathering source j
+// (sign +1, d = x_i - x_j) and target j gathering source i (sign -1).
+template <typename T>
+struct SymTerms {
+  T s, s2, s3, ome, tm1, wm3, et1, te1;  // 1/r, s^2, s^3, 1 - e, t - 1, w - 3, eps t - 1, t/eps - 1
+};
+
+template <bool MASK, typename T>
+__device__ __forceinline__ SymTerms<T> sym_terms(T dx, T dy, T dz, bool self, const PairConst<T>& c) {
+  SymTerms<T> R;
+  T r, e;
+  radial<MASK>(dx * dx + dy * dy + dz * dz, self, c, R.s, r, e);
+  const T kr = r * c.kappa;
+  const T ekr = e * kr;
+  const T t = ekr + e;
+  R.tm1 = t - T(1);
+  R.wm3 = ekr * kr + T(3) * R.tm1;  // w - 3 = 3 (t - 1) + e (kappa r)^2
+  R.ome = T(1) - e;
+  R.s2 = R.s * R.s;
+  R.s3 = R.s2 * R.s;
+  R.et1 = c.eps * t - T(1);
+  R.te1 = t * c.inveps - T(1);
+  return R;
+}
+
+// Forward direction: target (normal nt) gathers source (a = ds psi, m = ds phi n);
+// SIGN = +1 when d points from the source to the target, -1 otherwise.
+//   P += s [ (1 - e) a + (eps t - 1) (m.d) s^2 ]
+//   Q += s^3 [ (t/eps - 1) (nt.d) a + (t - 1) (nt.m) - (w - 3) (nt.d)(m.d) s^2 ]
+template <int SIGN, typename T>
+__device__ __forceinline__ void sym_forward(const SymTerms<T>& R, T dx, T dy, T dz, T ntx, T nty, T ntz, T a, T mx,
+                                            T my, T mz, T& accP, T& accQ) {
+  const T ci = ntx * dx + nty * dy + ntz * dz;
+  const T cm = mx * dx + my * dy + mz * dz;
+  const T cim = ntx * mx + nty * my + ntz * mz;
+  T p = R.ome * a;
+  p = (T(SIGN) * R.et1 * cm) * R.s2 + p;
+  accP = p * R.s + accP;
+  T q = (T(SIGN) * R.te1 * ci) * a;
+  q = R.tm1 * cim + q;
+  q = q - R.wm3 * ((ci * cm) * R.s2);
+  accQ = q * R.s3 + accQ;
+}
+
+// Transposed direction: output element (normal no) gathers element (wphi, p = wpsi n);
+// SIGN = +1 when d points from the output element to the gathered one.
+//   Zphi += s^3 [ (eps t - 1) (no.d) wphi + (t - 1)(no.p) - (w - 3)(p.d)(no.d) s^2 ]
+//   Zpsi += s [ (1 - e) wphi + (t/eps - 1)(p.d) s^2 ]
+template <int SIGN, typename T>
+__device__ __forceinline__ void sym_transpose(const SymTerms<T>& R, T dx, T dy, T dz, T nox, T noy, T noz, T wphi,
+                                              T px, T py, T pz, T& accP, T& accQ) {
+  const T cj = nox * dx + noy * dy + noz * dz;
+  const T cp = px * dx + py * dy + pz * dz;
+  const T cnp = nox * px + noy * py + noz * pz;
+  T q = (T(SIGN) * R.et1 * cj) * wphi;
+  q = R.tm1 * cnp + q;
+  q = q - R.wm3 * ((cp * cj) * R.s2);
+  accP = q * R.s3 + accP;
+  T p = R.ome * wphi;
+  p = (T(SIGN) * R.te1 * cp) * R.s2 + p;
+  accQ = p * R.s + accQ;
+}
+
 }  // namespace bipb

@@ -1,0 +1,511 @@
+// Mat-vec of Eqs. 5-6 (and its transpose) visiting every unordered pair once.
+//
+// The four kernels of a pair share r, e^{-kappa r}, t and w; only the dot
+// products with the normals and the sign of d differ between the two
+// directions.  Each work item is one tile of T targets of a system (row I)
+// against a range of sources at or after the tile's first element; every pair
+// (i, j) with j > i is evaluated once and applied both ways:
+//   target i gathers source j      -> register accumulators (i side)
+//   target j gathers source i      -> summed over the CTA's T targets (j side)
+// In the tile's own diagonal block the pairs with j <= i are masked (1/r = 0).
+// The j side of one source is reduced across the warp by a fixed butterfly
+// and across the warps in a fixed order, so results are bitwise reproducible.
+//
+// Partial sums (per system, T = targets per tile, nT tiles):
+//   i side: one block of 2 x T values per item (rows' items are numbered
+//           row by row, so a row's blocks are consecutive);
+//   j side: for row I, 2 x (n - I T) values (every element j >= I T).
+// The reduction adds, for element e of tile E, the i-side blocks of row E and
+// the j-side values of rows 0..E, in that fixed order, in FP64.
+#include <algorithm>
+#include <cmath>
+#include <queue>
+
+#include "internal.cuh"
+
+namespace bipb {
+
+namespace {
+
+constexpr double kInv4PiS = 1.0 / (4.0 * kPi);
+
+template <typename T>
+struct SymV4;
+template <>
+struct SymV4<float> {
+  using type = float4;
+};
+template <>
+struct SymV4<double> {
+  using type = double4_32a;
+};
+
+// ------------------------------------------------------------------ policies
+// Record of an element (both roles): position, a, m and the normal, where
+// (a, m) = (ds psi, ds phi n) for A u and (wphi, wpsi n) for A^T w.
+
+template <typename T, bool TRANS>
+struct SymPolicy {
+  using V4 = typename SymV4<T>::type;
+  using PT = T;  // partial sums are stored in this type
+  static constexpr int RW = 3;  // (x, a), (m, 0), (n, 0)
+  struct Elem {
+    T x[3], a, m[3], n[3];
+  };
+  struct Acc {
+    T p, q;
+  };
+  struct Args {
+    PairConst<T> c;
+  };
+  __device__ static void prologue(const Args&) {}
+  __device__ static void load(const V4* r, Elem& e) {
+    const V4 A = r[0], B = r[1], C = r[2];
+    e.x[0] = A.x, e.x[1] = A.y, e.x[2] = A.z, e.a = A.w;
+    e.m[0] = B.x, e.m[1] = B.y, e.m[2] = B.z;
+    e.n[0] = C.x, e.n[1] = C.y, e.n[2] = C.z;
+  }
+  __device__ static void zero(Acc& v) { v.p = T(0), v.q = T(0); }
+  // i-side of target t and j-side of source sj for the pair d = x_t - x_sj
+  template <bool MASK>
+  __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
+    const T dx = t.x[0] - sj.x[0], dy = t.x[1] - sj.x[1], dz = t.x[2] - sj.x[2];
+    const SymTerms<T> R = sym_terms<MASK>(dx, dy, dz, masked, g.c);
+    if (!TRANS) {
+      sym_forward<1>(R, dx, dy, dz, t.n[0], t.n[1], t.n[2], sj.a, sj.m[0], sj.m[1], sj.m[2], ti.p, ti.q);
+      sym_forward<-1>(R, dx, dy, dz, sj.n[0], sj.n[1], sj.n[2], t.a, t.m[0], t.m[1], t.m[2], tj.p, tj.q);
+    } else {
+      sym_transpose<-1>(R, dx, dy, dz, t.n[0], t.n[1], t.n[2], sj.a, sj.m[0], sj.m[1], sj.m[2], ti.p, ti.q);
+      sym_transpose<1>(R, dx, dy, dz, sj.n[0], sj.n[1], sj.n[2], t.a, t.m[0], t.m[1], t.m[2], tj.p, tj.q);
+    }
+  }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static T shfl(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ static PT out(T v) { return v; }
+};
+
+__device__ df* sym_exp_table() {
+  __shared__ df tab[32];
+  return tab;
+}
+
+// df64 record, 5 float4: (x.hi, a.hi), (x.lo, a.lo), (m.hi, n0.hi), (m.lo, n0.lo), (n1.hi, n2.hi, n1.lo, n2.lo)
+template <bool TRANS>
+struct SymDFPolicy {
+  using V4 = float4;
+  using PT = double;
+  static constexpr int RW = 5;
+  struct Elem {
+    df x[3], a, m[3], n[3];
+  };
+  struct Acc {
+    df p, q;
+  };
+  struct Args {
+    DFConst c;
+  };
+  __device__ static void prologue(const Args&) {
+    df* tab = sym_exp_table();
+    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  }
+  __device__ static void load(const float4* r, Elem& e) {
+    const float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
+    e.x[0] = df{A.x, B.x}, e.x[1] = df{A.y, B.y}, e.x[2] = df{A.z, B.z}, e.a = df{A.w, B.w};
+    e.m[0] = df{C.x, D.x}, e.m[1] = df{C.y, D.y}, e.m[2] = df{C.z, D.z};
+    e.n[0] = df{C.w, D.w}, e.n[1] = df{E.x, E.z}, e.n[2] = df{E.y, E.w};
+  }
+  __device__ static void zero(Acc& v) { v.p = df{0.f, 0.f}, v.q = df{0.f, 0.f}; }
+  template <bool MASK>
+  __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
+    const df d[3] = {df_sub(t.x[0], sj.x[0]), df_sub(t.x[1], sj.x[1]), df_sub(t.x[2], sj.x[2])};
+    const DFTerms R = df_sym_terms<MASK>(d[0], d[1], d[2], masked, g.c, sym_exp_table());
+    if (!TRANS) {
+      df_sym_forward<1>(R, d, t.n, sj.a, sj.m, ti.p, ti.q);
+      df_sym_forward<-1>(R, d, sj.n, t.a, t.m, tj.p, tj.q);
+    } else {
+      df_sym_transpose<-1>(R, d, t.n, sj.a, sj.m, ti.p, ti.q);
+      df_sym_transpose<1>(R, d, sj.n, t.a, t.m, tj.p, tj.q);
+    }
+  }
+  __device__ static df add(df a, df b) { return df_add(a, b); }
+  __device__ static df shfl(df v, int m) {
+    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+  }
+  __device__ static PT out(df v) { return df_to_double(v); }
+};
+
+// ------------------------------------------------------------------ kernel
+// Item (two int4): {rec_off, n, t0, sys}, {s0, s1, jrow, ioff}:
+//   targets t0 + [0, T) of a system with n elements whose records start at
+//   rec_off; sources [s0, s1) (s0 >= t0); i-side partials at part[ioff +
+//   c T + i - t0], j-side at part[jrow + c (n - t0) + j - t0].
+template <class P, int NT, int TPT, int CH>
+__global__ void __launch_bounds__(NT) k_sym(typename P::Args g, const int4* __restrict__ items,
+                                            const typename P::V4* __restrict__ rec, typename P::PT* __restrict__ part,
+                                            const int* __restrict__ skip, int skip_stride) {
+  using V4 = typename P::V4;
+  using Acc = typename P::Acc;
+  constexpr int NW = NT / 32, T = NT * TPT;
+  __shared__ V4 sh[CH * P::RW];
+  __shared__ Acc jred[NW][CH];
+  const int4 I0 = items[2 * blockIdx.x], I1 = items[2 * blockIdx.x + 1];
+  const int rec_off = I0.x, n = I0.y, t0 = I0.z, sys = I0.w;
+  const int s0 = I1.x, s1 = I1.y, jrow = I1.z, ioff = I1.w;
+  if (skip != nullptr && skip[(size_t)sys * skip_stride] != 0) return;
+  P::prologue(g);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  typename P::Elem tg[TPT];
+  Acc acc[TPT];
+  int idx[TPT];
+#pragma unroll
+  for (int k = 0; k < TPT; ++k) {
+    idx[k] = t0 + k * NT + threadIdx.x;
+    P::load(rec + (size_t)(rec_off + min(idx[k], n - 1)) * P::RW, tg[k]);
+    P::zero(acc[k]);
+  }
+  const int len = n - t0;  // j-side row length
+  for (int j0 = s0; j0 < s1; j0 += CH) {
+    const int cnt = min(CH, s1 - j0);
+    __syncthreads();
+    const V4* src = rec + (size_t)(rec_off + j0) * P::RW;
+    for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
+    __syncthreads();
+    const bool diag = j0 < t0 + T;  // the chunk overlaps the tile's own targets: mask j <= i
+    for (int jj = 0; jj < cnt; ++jj) {
+      typename P::Elem sj;
+      P::load(sh + jj * P::RW, sj);
+      Acc tj;
+      P::zero(tj);
+      if (diag) {
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) P::template pair<true>(g, tg[k], sj, j0 + jj <= idx[k], acc[k], tj);
+      } else {
+#pragma unroll
+        for (int k = 0; k < TPT; ++k) P::template pair<false>(g, tg[k], sj, false, acc[k], tj);
+      }
+      // fixed butterfly: lanes 0-15 end with the P total, lanes 16-31 with Q
+      const bool upper = (lane & 16) != 0;
+      auto keep = upper ? tj.q : tj.p;
+      keep = P::add(keep, P::shfl(upper ? tj.p : tj.q, 16));
+#pragma unroll
+      for (int m = 8; m >= 1; m >>= 1) keep = P::add(keep, P::shfl(keep, m));
+      if (lane == 0) jred[warp][jj].p = keep;
+      if (lane == 16) jred[warp][jj].q = keep;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += NT) {
+      Acc v = jred[0][q];
+#pragma unroll
+      for (int w = 1; w < NW; ++w) v.p = P::add(v.p, jred[w][q].p), v.q = P::add(v.q, jred[w][q].q);
+      const int o = j0 + q - t0;
+      part[(size_t)jrow + o] = P::out(v.p);
+      part[(size_t)jrow + len + o] = P::out(v.q);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TPT; ++k)
+    if (idx[k] < n) {
+      part[(size_t)ioff + idx[k] - t0] = P::out(acc[k].p);
+      part[(size_t)ioff + T + idx[k] - t0] = P::out(acc[k].q);
+    }
+}
+
+// ------------------------------------------------------------------ pack / reduce
+// Records of every system at vec_off / 2 (RW vectors each).  lay[k] = {geo_off, n, vec_off, chg_off}.
+template <typename V4, typename T>
+__global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
+                           const double* __restrict__ u, V4* __restrict__ rec, const int* __restrict__ skip,
+                           int skip_stride) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.y || (skip != nullptr && skip[(size_t)k * skip_stride] != 0)) return;
+  const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
+  const double phi = u[L.z + j], psi = u[L.z + L.y + j];
+  const double a = transpose ? phi : g.w * psi;
+  const double f = transpose ? psi : g.w * phi;
+  V4 r0, r1, r2;
+  r0.x = (T)g.x, r0.y = (T)g.y, r0.z = (T)g.z, r0.w = (T)a;
+  r1.x = (T)(f * v.x), r1.y = (T)(f * v.y), r1.z = (T)(f * v.z), r1.w = (T)0;
+  r2.x = (T)v.x, r2.y = (T)v.y, r2.z = (T)v.z, r2.w = (T)0;
+  V4* o = rec + 3 * (size_t)(L.z / 2 + j);
+  o[0] = r0, o[1] = r1, o[2] = r2;
+}
+
+__global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
+                              const double* __restrict__ u, float4* __restrict__ rec, const int* __restrict__ skip,
+                              int skip_stride) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= L.y || (skip != nullptr && skip[(size_t)k * skip_stride] != 0)) return;
+  const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
+  const double phi = u[L.z + j], psi = u[L.z + L.y + j];
+  const double a = transpose ? phi : g.w * psi;
+  const double f = transpose ? psi : g.w * phi;
+  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z), w = df_from_double(a);
+  const df m0 = df_from_double(f * v.x), m1 = df_from_double(f * v.y), m2 = df_from_double(f * v.z);
+  const df n0 = df_from_double(v.x), n1 = df_from_double(v.y), n2 = df_from_double(v.z);
+  float4* o = rec + 5 * (size_t)(L.z / 2 + j);
+  o[0] = make_float4(x0.hi, x1.hi, x2.hi, w.hi);
+  o[1] = make_float4(x0.lo, x1.lo, x2.lo, w.lo);
+  o[2] = make_float4(m0.hi, m1.hi, m2.hi, n0.hi);
+  o[3] = make_float4(m0.lo, m1.lo, m2.lo, n0.lo);
+  o[4] = make_float4(n1.hi, n2.hi, n1.lo, n2.lo);
+}
+
+// y_i = diag u_i - (1/(4 pi)) scale_i (i-side blocks of the element's row + j-side rows 0..E).
+// tab[k] = {n, first row entry, j-side base, T}; tab[row entry + E] = {first i-side block, blocks, 0, 0}.
+template <typename PT>
+__global__ void k_reduce_sym(const int4* __restrict__ lay, const int4* __restrict__ tab, const PT* __restrict__ part,
+                             const double* __restrict__ u, double* __restrict__ y, double d_phi, double d_psi,
+                             const double4_32a* __restrict__ tgt64_for_area, const int* __restrict__ skip,
+                             int skip_stride) {
+  const int k = blockIdx.y;
+  const int4 L = lay[k], S = tab[k];
+  const int n = L.y, T = S.w;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n || (skip != nullptr && skip[(size_t)k * skip_stride] != 0)) return;
+  const int c = i < n ? 0 : 1;
+  const int e = i - c * n;
+  const int E = e / T;
+  const int4 R = tab[S.y + E];
+  double acc = 0.0;
+  for (int b = 0; b < R.y; ++b) acc += (double)part[(size_t)R.x + (size_t)b * 2 * T + (size_t)c * T + (e - E * T)];
+  for (int I = 0; I <= E; ++I) {
+    const int64_t row = (int64_t)S.z + 2 * ((int64_t)I * n - (int64_t)T * I * (I - 1) / 2);
+    acc += (double)part[row + (int64_t)c * (n - I * T) + (e - I * T)];
+  }
+  const double sc = tgt64_for_area ? tgt64_for_area[2 * (L.x + e)].w : 1.0;
+  y[L.z + i] = (c == 0 ? d_phi : d_psi) * u[L.z + i] - kInv4PiS * sc * acc;
+}
+
+int blocks_of(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------ work list
+// Rows of every system are cut into pieces of about Lsrc sources; Lsrc is the
+// candidate whose greedy schedule (pieces sorted by size, each to the first
+// free CTA slot) finishes first.  A piece costs T x (sources + 32).
+ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slots, int ch) {
+  auto it = s->plans.find(key);
+  if (it != s->plans.end()) return it->second.get();
+  const int K = L.K;
+  struct Row {
+    int k, I, len;
+  };
+  std::vector<Row> rows;
+  for (int k = 0; k < K; ++k) {
+    const int nT = (L.n[k] + T - 1) / T;
+    for (int I = 0; I < nT; ++I) rows.push_back(Row{k, I, L.n[k] - I * T});
+  }
+  auto pieces_of = [&](int len, int Ls) { return std::max(1, (len + Ls - 1) / Ls); };
+  auto makespan = [&](int Ls) {
+    std::vector<double> cost;
+    for (const Row& r : rows) {
+      const int P = pieces_of(r.len, Ls);
+      for (int p = 0; p < P; ++p) cost.push_back((double)((int64_t)(p + 1) * r.len / P - (int64_t)p * r.len / P) + 32.0);
+    }
+    std::sort(cost.begin(), cost.end(), std::greater<double>());
+    std::priority_queue<double, std::vector<double>, std::greater<double>> q;
+    for (int i = 0; i < slots; ++i) q.push(0.0);
+    double end = 0.0;
+    for (double c : cost) {
+      const double t = q.top() + c;
+      q.pop();
+      q.push(t);
+      end = std::max(end, t);
+    }
+    return end;
+  };
+  int n_max = 1;
+  double total = 0.0;
+  for (int k = 0; k < K; ++k) n_max = std::max(n_max, L.n[k]);
+  for (const Row& r : rows) total += r.len;
+  int best_L = n_max;
+  double best = makespan(n_max);
+  // at most about 2e5 pieces: the candidates start where the list gets that long
+  for (double Ls = std::max((double)ch, total / 2e5); Ls < n_max; Ls *= 1.15) {
+    const double m = makespan((int)Ls);
+    if (m < best * 0.995) best = m, best_L = (int)Ls;
+  }
+
+  // pieces numbered row by row (i-side blocks), then ordered by size for the launch
+  struct Piece {
+    int k, I, s0, s1, ioff;
+  };
+  std::vector<Piece> pieces;
+  std::vector<int4> tab(K);
+  std::vector<int4> rowtab;
+  std::vector<int64_t> jbase(K);
+  int64_t off = 0;
+  int blocks = 0;
+  for (int k = 0; k < K; ++k) {
+    const int n = L.n[k], nT = (n + T - 1) / T;
+    tab[k] = make_int4(n, K + (int)rowtab.size(), 0, T);
+    for (int I = 0; I < nT; ++I) {
+      const int t0 = I * T, len = n - t0, P = pieces_of(len, best_L);
+      rowtab.push_back(make_int4(0, P, 0, 0));
+      for (int p = 0; p < P; ++p) {
+        pieces.push_back(Piece{k, I, t0 + (int)((int64_t)p * len / P), t0 + (int)((int64_t)(p + 1) * len / P),
+                               blocks});
+        ++blocks;
+      }
+    }
+  }
+  // i-side blocks first (2 T each), then the j-side rows of every system
+  {
+    int b = 0;
+    for (auto& rt : rowtab) {
+      rt.x = (int)((int64_t)b * 2 * T);
+      b += rt.y;
+    }
+  }
+  off = (int64_t)blocks * 2 * T;
+  for (int k = 0; k < K; ++k) {
+    const int n = L.n[k], nT = (n + T - 1) / T;
+    jbase[k] = off;
+    for (int I = 0; I < nT; ++I) off += 2 * (int64_t)(n - I * T);
+  }
+  BIPB_REQUIRE(off < ((int64_t)1 << 31), "mat-vec too large for one symmetric work list");
+  for (int k = 0; k < K; ++k) tab[k].z = (int)jbase[k];
+  std::stable_sort(pieces.begin(), pieces.end(),
+                   [](const Piece& a, const Piece& b) { return a.s1 - a.s0 > b.s1 - b.s0; });
+  std::vector<int4> items;
+  items.reserve(2 * pieces.size());
+  for (const Piece& p : pieces) {
+    const int n = L.n[p.k], t0 = p.I * T;
+    const int64_t jrow = jbase[p.k] + 2 * ((int64_t)p.I * n - (int64_t)T * p.I * (p.I - 1) / 2);
+    items.push_back(make_int4(L.vec_off[p.k] / 2, n, t0, p.k));
+    items.push_back(make_int4(p.s0, p.s1, (int)jrow, (int)((int64_t)p.ioff * 2 * T)));
+  }
+  tab.insert(tab.end(), rowtab.begin(), rowtab.end());
+  auto plan = std::make_unique<ItemPlan>();
+  plan->n_items = (int)pieces.size();
+  plan->part_len = off;
+  plan->items.ensure(items.size());
+  plan->tab.ensure(tab.size());
+  BIPB_CUDA(cudaMemcpyAsync(plan->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));
+  ++s->alloc_gen;
+  ItemPlan* raw = plan.get();
+  s->plans[key] = std::move(plan);
+  return raw;
+}
+
+// Plan-cache key of one symmetric pass over one layout (SplitMix64 finaliser,
+// so that distinct (pass, layout) pairs do not collide by construction).
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+uint64_t sym_key(int pass_id, uint64_t layout_key) {
+  return mix64(layout_key ^ mix64(0x5e11000000000000ull + (uint64_t)pass_id));
+}
+
+// Partial sums a symmetric pass over L needs with tiles of T targets (the
+// i-side blocks excluded), and whether they fit the 32-bit offsets.
+bool sym_fits(const SysLayout& L, int T) {
+  int64_t off = 0;
+  for (int k = 0; k < L.K; ++k) {
+    const int n = L.n[k], nT = (n + T - 1) / T;
+    off += 2 * ((int64_t)nT * n - (int64_t)T * nT * (nT - 1) / 2);
+  }
+  return off < ((int64_t)1 << 30);
+}
+
+template <class P, int NT, int TPT, int CH>
+int sym_occupancy() {
+  static int occ = [] {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sym<P, NT, TPT, CH>, NT, 0) != cudaSuccess) {
+      (void)cudaGetLastError();
+      o = 1;
+    }
+    return std::max(o, 1);
+  }();
+  return occ;
+}
+
+template <class P, int NT, int TPT, int CH>
+void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typename P::Args& g, bool transpose,
+             DevBuf<typename P::V4>& recbuf, DevBuf<typename P::PT>& partbuf, const double* u, double* y,
+             double dphi, double dpsi, const int* skip, int skip_stride) {
+  constexpr int T = NT * TPT;
+  const uint64_t key = sym_key(pass_id, L.key);
+  ItemPlan* plan = plan_sym(s, key, L, T, s->num_sms * sym_occupancy<P, NT, TPT, CH>(), CH);
+  s->grow(recbuf, (size_t)(L.len / 2) * P::RW);
+  s->grow(partbuf, (size_t)plan->part_len);
+  const int4* lay = s->lay_dev(L);
+  if constexpr (P::RW == 5) {
+    k_pack_sym_df<<<dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, transpose, s->tgt64.p, u,
+                                                                              recbuf.p, skip, skip_stride);
+  } else {
+    k_pack_sym<typename P::V4, typename P::PT><<<dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream>>>(
+        lay, transpose, s->tgt64.p, u, recbuf.p, skip, skip_stride);
+  }
+  BIPB_LAUNCHED(s);
+  {
+    TimedLaunch tl(s, kind);
+    k_sym<P, NT, TPT, CH><<<plan->n_items, NT, 0, s->stream>>>(g, plan->items.p, recbuf.p, partbuf.p, skip,
+                                                                skip_stride);
+    BIPB_LAUNCHED(s);
+  }
+  k_reduce_sym<typename P::PT><<<dim3(blocks_of(2 * (int64_t)L.max_n, 256), L.K), 256, 0, s->stream>>>(
+      lay, plan->tab.p, partbuf.p, u, y, dphi, dpsi, transpose ? s->tgt64.p : nullptr, skip, skip_stride);
+  BIPB_LAUNCHED(s);
+}
+
+}  // namespace
+
+bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, int variant,
+                  const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
+  static const int kT[3] = {512, 512, 1024};
+  if (variant < 0 || variant > 2) throw Error(BIPB_ERR_INVALID_ARG, "unknown symmetric FP32 mat-vec variant");
+  if (!sym_fits(L, kT[variant])) return false;
+  const int kind = transpose ? kTMv32T : kTMv32;
+#define BIPB_SYM32(V_, NT_, TPT_, CH_)                                                                       \
+  case V_:                                                                                                   \
+    if (transpose)                                                                                           \
+      run_sym<SymPolicy<float, true>, NT_, TPT_, CH_>(s, 0x100 + V_, kind, L, {c}, true, s->rec32, s->part32, \
+                                                      u, y, dphi, dpsi, skip, skip_stride);                  \
+    else                                                                                                     \
+      run_sym<SymPolicy<float, false>, NT_, TPT_, CH_>(s, 0x200 + V_, kind, L, {c}, false, s->rec32,         \
+                                                       s->part32, u, y, dphi, dpsi, skip, skip_stride);      \
+    return true;
+  switch (variant) {
+    BIPB_SYM32(0, 256, 2, 128)
+    BIPB_SYM32(1, 128, 4, 128)
+    BIPB_SYM32(2, 256, 4, 64)
+  }
+#undef BIPB_SYM32
+  return false;
+}
+
+bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, bool transpose, const double* u,
+                  double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
+  if (!sym_fits(L, 256)) return false;
+  if (transpose)
+    run_sym<SymPolicy<double, true>, 128, 2, 64>(s, 0x300, kTMv64T, L, {c}, true, s->rec64, s->part64, u, y, dphi,
+                                                 dpsi, skip, skip_stride);
+  else
+    run_sym<SymPolicy<double, false>, 128, 2, 64>(s, 0x400, kTMv64, L, {c}, false, s->rec64, s->part64, u, y, dphi,
+                                                  dpsi, skip, skip_stride);
+  return true;
+}
+
+bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
+                   double dphi, double dpsi, const int* skip, int skip_stride) {
+  if (!sym_fits(L, 128)) return false;
+  if (transpose)
+    run_sym<SymDFPolicy<true>, 128, 1, 32>(s, 0x500, kTMvDFT, L, {c}, true, s->recdf, s->part64, u, y, dphi, dpsi,
+                                           skip, skip_stride);
+  else
+    run_sym<SymDFPolicy<false>, 128, 1, 32>(s, 0x600, kTMvDF, L, {c}, false, s->recdf, s->part64, u, y, dphi, dpsi,
+                                            skip, skip_stride);
+  return true;
+}
+
+}  // namespace bipb

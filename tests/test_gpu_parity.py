@@ -67,9 +67,11 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
     ref = np.stack([f(p.centroids, p.normals, p.areas, eps, p.kappa, u) for u in U])
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
-        cases = [(bipb.FP64, 0), (bipb.DF64, 0)] + [(bipb.FP32, v) for v in range(bipb.MATVEC32_VARIANTS)]
-        for prec, variant in cases:
+        cases = [(bipb.FP64, 0, sym) for sym in (True, False)] + [(bipb.DF64, 0, sym) for sym in (True, False)]
+        cases += [(bipb.FP32, v, True) for v in range(bipb.MATVEC32_VARIANTS)]
+        for prec, variant, sym in cases:
             s.set_variant(variant)
+            s.symmetric_pairs(sym)
             yd = torch.full_like(ud, float("nan"))
             s.matvec(ud, yd, precision=prec, transpose=transpose, med=_med(bipb, p))
             y = yd.cpu().numpy()
@@ -297,7 +299,11 @@ def test_uneven_batch_matvec_matches_oracle(bipb, orc):
     us = [rng.standard_normal(2 * p.n) for p in probs]
     with bipb.BatchSurface([(p.centroids, p.normals, p.areas) for p in probs]) as s:
         u = _dev(np.concatenate(us))
-        for prec, tol in ((bipb.FP64, 1e-12), (bipb.FP32, 2e-5)):
+        cases = [(bipb.FP64, 1e-12, 0, True), (bipb.FP64, 1e-12, 0, False), (bipb.DF64, 2e-12, 0, True)]
+        cases += [(bipb.FP32, 2e-5, v, True) for v in (0, 7, 8, 9)]
+        for prec, tol, variant, sym in cases:
+            s.set_variant(variant)
+            s.symmetric_pairs(sym)
             for transpose in (False, True):
                 y = torch.full_like(u, float("nan"))
                 s.matvec(u, y, precision=prec, transpose=transpose)
@@ -305,7 +311,7 @@ def test_uneven_batch_matvec_matches_oracle(bipb, orc):
                 for p, uk, yk in zip(probs, us, parts):
                     f = orc.matvec_t if transpose else orc.matvec
                     ref = f(p.centroids, p.normals, p.areas, p.eps_out / p.eps_in, p.kappa, uk)
-                    assert np.abs(yk - ref).max() < tol * np.abs(ref).max(), (prec, transpose)
+                    assert np.abs(yk - ref).max() < tol * np.abs(ref).max(), (prec, variant, sym, transpose)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
