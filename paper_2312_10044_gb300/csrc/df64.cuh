@@ -89,9 +89,30 @@ __device__ __forceinline__ df df_from_double(double v) {
   float hi = __double2float_rn(v);
   return df{hi, __double2float_rn(v - (double)hi)};
 }
-// dot product of two df 3-vectors
+// Dot product of two df 3-vectors: the three leading products are exact
+// (TwoProduct), their sum is formed by two TwoSums, every trailing part
+// (product errors, cross terms, TwoSum errors) is added in FP32, and one
+// FastTwoSum renormalises.  Absolute error about 2^-46 of the largest product.
 __device__ __forceinline__ df df_dot3(df ax, df ay, df az, df bx, df by, df bz) {
-  return df_add(df_add(df_mul(ax, bx), df_mul(ay, by)), df_mul(az, bz));
+  const float p0 = __fmul_rn(ax.hi, bx.hi), p1 = __fmul_rn(ay.hi, by.hi), p2 = __fmul_rn(az.hi, bz.hi);
+  const float e0 = __fmaf_rn(ax.lo, bx.hi, __fmaf_rn(ax.hi, bx.lo, __fmaf_rn(ax.hi, bx.hi, -p0)));
+  const float e1 = __fmaf_rn(ay.lo, by.hi, __fmaf_rn(ay.hi, by.lo, __fmaf_rn(ay.hi, by.hi, -p1)));
+  const float e2 = __fmaf_rn(az.lo, bz.hi, __fmaf_rn(az.hi, bz.lo, __fmaf_rn(az.hi, bz.hi, -p2)));
+  const df s = two_sum(p0, p1);
+  const df t = two_sum(s.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, s.lo)), t.lo);
+  return fast_two_sum(t.hi, lo);
+}
+// x^2 + y^2 + z^2 for df components, in the same way as df_dot3.
+__device__ __forceinline__ df df_sumsq3(df x, df y, df z) {
+  const float p0 = __fmul_rn(x.hi, x.hi), p1 = __fmul_rn(y.hi, y.hi), p2 = __fmul_rn(z.hi, z.hi);
+  const float e0 = __fmaf_rn(__fadd_rn(x.hi, x.hi), x.lo, __fmaf_rn(x.hi, x.hi, -p0));
+  const float e1 = __fmaf_rn(__fadd_rn(y.hi, y.hi), y.lo, __fmaf_rn(y.hi, y.hi, -p1));
+  const float e2 = __fmaf_rn(__fadd_rn(z.hi, z.hi), z.lo, __fmaf_rn(z.hi, z.hi, -p2));
+  const df s = two_sum(p0, p1);
+  const df t = two_sum(s.hi, p2);
+  const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, s.lo)), t.lo);
+  return fast_two_sum(t.hi, lo);
 }
 
 struct DFConst {
@@ -245,14 +266,16 @@ namespace bipb {
 
 // Symmetric pair terms in df64 (the radial part shared by both directions of
 // an unordered pair; see SymTerms in pair.cuh).
+// ka = (eps t - 1) s^2 and kb = t/eps - 1 for A u; ka = eps t - 1 and
+// kb = (t/eps - 1) s^2 for A^T w (the factor s^2 goes where the formula has it).
 struct DFTerms {
-  df s, s2, s3, ome, tm1, wm3, et1, te1;
+  df s, s3, ome, tm1, ka, kb, wm3s2;  // wm3s2 = (w - 3) s^2
 };
 
-template <bool MASK>
+template <bool MASK, bool TRANS>
 __device__ __forceinline__ DFTerms df_sym_terms(df dx, df dy, df dz, bool self, const DFConst& c, const df* tab) {
   DFTerms R;
-  const df r2 = df_add(df_add(df_sqr(dx), df_sqr(dy)), df_sqr(dz));
+  const df r2 = df_sumsq3(dx, dy, dz);
   R.s = df_rsqrt(r2);
   if (MASK && self) R.s = df{0.0f, 0.0f};
   const df r = df_mul(r2, R.s);
@@ -261,18 +284,21 @@ __device__ __forceinline__ DFTerms df_sym_terms(df dx, df dy, df dz, bool self, 
   const df ekr = df_mul(e, kr);
   const df t = df_add(ekr, e);
   R.tm1 = df_add_f(t, -1.0f);
-  R.wm3 = df_add(df_mul(ekr, kr), df_mul_f(R.tm1, 3.0f));  // 3 (t - 1) + e (kappa r)^2
+  const df wm3 = df_add(df_mul(ekr, kr), df_mul_f(R.tm1, 3.0f));  // 3 (t - 1) + e (kappa r)^2
   R.ome = df_add_f(df_neg(e), 1.0f);
-  R.s2 = df_sqr(R.s);
-  R.s3 = df_mul(R.s2, R.s);
-  R.et1 = df_add_f(df_mul(c.eps, t), -1.0f);
-  R.te1 = df_add_f(df_mul(t, c.inveps), -1.0f);
+  const df s2 = df_sqr(R.s);
+  R.s3 = df_mul(s2, R.s);
+  const df et1 = df_add_f(df_mul(c.eps, t), -1.0f), te1 = df_add_f(df_mul(t, c.inveps), -1.0f);
+  R.ka = TRANS ? et1 : df_mul(et1, s2);
+  R.kb = TRANS ? df_mul(te1, s2) : te1;
+  R.wm3s2 = df_mul(wm3, s2);
   return R;
 }
 
 __device__ __forceinline__ df df_signed(df x, int sign) { return sign > 0 ? x : df_neg(x); }
 
-// Forward direction in df64 (sym_forward in pair.cuh).
+// Forward direction in df64 (sym_forward in pair.cuh); R from df_sym_terms<MASK, false>.
+// The accumulators are updated lazily (df_mac): renormalise them before use.
 template <int SIGN>
 __device__ __forceinline__ void df_sym_forward(const DFTerms& R, const df* d, const df* nt, df a, const df* m,
                                                df& accP, df& accQ) {
@@ -280,28 +306,28 @@ __device__ __forceinline__ void df_sym_forward(const DFTerms& R, const df* d, co
   const df cm = df_dot3(m[0], m[1], m[2], d[0], d[1], d[2]);
   const df cim = df_dot3(nt[0], nt[1], nt[2], m[0], m[1], m[2]);
   df p = df_mul(R.ome, a);
-  p = df_add(p, df_mul(df_mul(df_signed(R.et1, SIGN), cm), R.s2));
-  accP = df_add(accP, df_mul(p, R.s));
-  df q = df_mul(df_mul(df_signed(R.te1, SIGN), ci), a);
+  p = df_add(p, df_mul(df_signed(R.ka, SIGN), cm));
+  df_mac(accP, p, R.s);
+  df q = df_mul(df_mul(df_signed(R.kb, SIGN), ci), a);
   q = df_add(q, df_mul(R.tm1, cim));
-  q = df_sub(q, df_mul(R.wm3, df_mul(df_mul(ci, cm), R.s2)));
-  accQ = df_add(accQ, df_mul(q, R.s3));
+  q = df_sub(q, df_mul(R.wm3s2, df_mul(ci, cm)));
+  df_mac(accQ, q, R.s3);
 }
 
-// Transposed direction in df64 (sym_transpose in pair.cuh).
+// Transposed direction in df64 (sym_transpose in pair.cuh); R from df_sym_terms<MASK, true>.
 template <int SIGN>
 __device__ __forceinline__ void df_sym_transpose(const DFTerms& R, const df* d, const df* no, df wphi, const df* pv,
                                                  df& accP, df& accQ) {
   const df cj = df_dot3(no[0], no[1], no[2], d[0], d[1], d[2]);
   const df cp = df_dot3(pv[0], pv[1], pv[2], d[0], d[1], d[2]);
   const df cnp = df_dot3(no[0], no[1], no[2], pv[0], pv[1], pv[2]);
-  df q = df_mul(df_mul(df_signed(R.et1, SIGN), cj), wphi);
+  df q = df_mul(df_mul(df_signed(R.ka, SIGN), cj), wphi);
   q = df_add(q, df_mul(R.tm1, cnp));
-  q = df_sub(q, df_mul(R.wm3, df_mul(df_mul(cp, cj), R.s2)));
-  accP = df_add(accP, df_mul(q, R.s3));
+  q = df_sub(q, df_mul(R.wm3s2, df_mul(cp, cj)));
+  df_mac(accP, q, R.s3);
   df p = df_mul(R.ome, wphi);
-  p = df_add(p, df_mul(df_mul(df_signed(R.te1, SIGN), cp), R.s2));
-  accQ = df_add(accQ, df_mul(p, R.s));
+  p = df_add(p, df_mul(df_signed(R.kb, SIGN), cp));
+  df_mac(accQ, p, R.s);
 }
 
 }  // namespace bipb

@@ -89,8 +89,8 @@ struct ItemPlan {
 // FP32 mat-vec kernel variants (threads per CTA, targets per thread,
 // sources per shared-memory chunk): every ordered pair: 0 (256,2,128)
 // 1 (256,1,128) 2 (128,2,128) 3 (256,4,128) 4 (128,4,64) 5 (512,1,128)
-// 6 (256,2,64); every unordered pair once (sym.cu): 7 (256,2,128)
-// 8 (128,4,128) 9 (256,4,64).
+// 6 (256,2,64); every unordered pair once (sym.cu): 7 (256,2,64)
+// 8 (128,4,64) 9 (256,4,64).
 constexpr int kNumMv32Variants = 10;
 constexpr int kFirstSymVariant = 7;
 

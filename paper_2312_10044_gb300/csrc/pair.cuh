@@ -139,12 +139,15 @@ __device__ __forceinline__ void pair_transpose(T xj, T yj, T zj, T nxj, T nyj, T
 // that visits the unordered pair {i, j} once computes the radial terms once
 // and applies them in both directions: target i gathering source j
 // (sign +1, d = x_i - x_j) and target j gathering source i (sign -1).
+// s = 1/r, s3 = s^3, ome = 1 - e, tm1 = t - 1, wm3s2 = (w - 3) s^2, and
+// ka = (eps t - 1) s^2, kb = t/eps - 1 for A u (TRANS = false), or
+// ka = eps t - 1, kb = (t/eps - 1) s^2 for A^T w (TRANS = true).
 template <typename T>
 struct SymTerms {
-  T s, s2, s3, ome, tm1, wm3, et1, te1;  // 1/r, s^2, s^3, 1 - e, t - 1, w - 3, eps t - 1, t/eps - 1
+  T s, s3, ome, tm1, ka, kb, wm3s2;
 };
 
-template <bool MASK, typename T>
+template <bool MASK, bool TRANS, typename T>
 __device__ __forceinline__ SymTerms<T> sym_terms(T dx, T dy, T dz, bool self, const PairConst<T>& c) {
   SymTerms<T> R;
   T r, e;
@@ -153,16 +156,18 @@ __device__ __forceinline__ SymTerms<T> sym_terms(T dx, T dy, T dz, bool self, co
   const T ekr = e * kr;
   const T t = ekr + e;
   R.tm1 = t - T(1);
-  R.wm3 = ekr * kr + T(3) * R.tm1;  // w - 3 = 3 (t - 1) + e (kappa r)^2
+  const T s2 = R.s * R.s;
+  R.wm3s2 = (ekr * kr + T(3) * R.tm1) * s2;  // w - 3 = 3 (t - 1) + e (kappa r)^2
   R.ome = T(1) - e;
-  R.s2 = R.s * R.s;
-  R.s3 = R.s2 * R.s;
-  R.et1 = c.eps * t - T(1);
-  R.te1 = t * c.inveps - T(1);
+  R.s3 = s2 * R.s;
+  const T et1 = c.eps * t - T(1), te1 = t * c.inveps - T(1);
+  R.ka = TRANS ? et1 : et1 * s2;
+  R.kb = TRANS ? te1 * s2 : te1;
   return R;
 }
 
-// Forward direction: target (normal nt) gathers source (a = ds psi, m = ds phi n);
+// Forward direction (R from sym_terms<MASK, false>): target (normal nt) gathers
+// source (a = ds psi, m = ds phi n);
 // SIGN = +1 when d points from the source to the target, -1 otherwise.
 //   P += s [ (1 - e) a + (eps t - 1) (m.d) s^2 ]
 //   Q += s^3 [ (t/eps - 1) (nt.d) a + (t - 1) (nt.m) - (w - 3) (nt.d)(m.d) s^2 ]
@@ -173,15 +178,16 @@ __device__ __forceinline__ void sym_forward(const SymTerms<T>& R, T dx, T dy, T 
   const T cm = mx * dx + my * dy + mz * dz;
   const T cim = ntx * mx + nty * my + ntz * mz;
   T p = R.ome * a;
-  p = (T(SIGN) * R.et1 * cm) * R.s2 + p;
+  p = (T(SIGN) * R.ka) * cm + p;
   accP = p * R.s + accP;
-  T q = (T(SIGN) * R.te1 * ci) * a;
+  T q = (T(SIGN) * R.kb * ci) * a;
   q = R.tm1 * cim + q;
-  q = q - R.wm3 * ((ci * cm) * R.s2);
+  q = q - R.wm3s2 * (ci * cm);
   accQ = q * R.s3 + accQ;
 }
 
-// Transposed direction: output element (normal no) gathers element (wphi, p = wpsi n);
+// Transposed direction (R from sym_terms<MASK, true>): output element (normal no)
+// gathers element (wphi, p = wpsi n);
 // SIGN = +1 when d points from the output element to the gathered one.
 //   Zphi += s^3 [ (eps t - 1) (no.d) wphi + (t - 1)(no.p) - (w - 3)(p.d)(no.d) s^2 ]
 //   Zpsi += s [ (1 - e) wphi + (t/eps - 1)(p.d) s^2 ]
@@ -191,12 +197,12 @@ __device__ __forceinline__ void sym_transpose(const SymTerms<T>& R, T dx, T dy, 
   const T cj = nox * dx + noy * dy + noz * dz;
   const T cp = px * dx + py * dy + pz * dz;
   const T cnp = nox * px + noy * py + noz * pz;
-  T q = (T(SIGN) * R.et1 * cj) * wphi;
+  T q = (T(SIGN) * R.ka * cj) * wphi;
   q = R.tm1 * cnp + q;
-  q = q - R.wm3 * ((cp * cj) * R.s2);
+  q = q - R.wm3s2 * (cp * cj);
   accP = q * R.s3 + accP;
   T p = R.ome * wphi;
-  p = (T(SIGN) * R.te1 * cp) * R.s2 + p;
+  p = (T(SIGN) * R.kb) * cp + p;
   accQ = p * R.s + accQ;
 }
 

@@ -11,9 +11,16 @@
 // The j side of one source is reduced across the warp by a fixed butterfly
 // and across the warps in a fixed order, so results are bitwise reproducible.
 //
+// Row I of a system has n - I T sources, so rows shrink down the system.
+// Rows I and nT - 1 - I are folded together (about n + T sources between
+// them) and the folded rows are cut into pieces of equal length; a piece is
+// one work item and covers one or two segments (tile, source range).  All
+// items thus carry the same work, and their number is chosen to fill whole
+// waves of resident CTAs.
+//
 // Partial sums (per system, T = targets per tile, nT tiles):
-//   i side: one block of 2 x T values per item (rows' items are numbered
-//           row by row, so a row's blocks are consecutive);
+//   i side: one block of 2 x T values per segment (a row's segments are
+//           numbered consecutively, in source order);
 //   j side: for row I, 2 x (n - I T) values (every element j >= I T).
 // The reduction adds, for element e of tile E, the i-side blocks of row E and
 // the j-side values of rows 0..E, in that fixed order, in FP64.
@@ -49,6 +56,7 @@ struct SymPolicy {
   using V4 = typename SymV4<T>::type;
   using PT = T;  // partial sums are stored in this type
   static constexpr int RW = 3;  // (x, a), (m, 0), (n, 0)
+  static constexpr int UNROLL = sizeof(T) == 4 ? 2 : 1;  // sources in flight per thread
   struct Elem {
     T x[3], a, m[3], n[3];
   };
@@ -70,7 +78,7 @@ struct SymPolicy {
   template <bool MASK>
   __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
     const T dx = t.x[0] - sj.x[0], dy = t.x[1] - sj.x[1], dz = t.x[2] - sj.x[2];
-    const SymTerms<T> R = sym_terms<MASK>(dx, dy, dz, masked, g.c);
+    const SymTerms<T> R = sym_terms<MASK, TRANS>(dx, dy, dz, masked, g.c);
     if (!TRANS) {
       sym_forward<1>(R, dx, dy, dz, t.n[0], t.n[1], t.n[2], sj.a, sj.m[0], sj.m[1], sj.m[2], ti.p, ti.q);
       sym_forward<-1>(R, dx, dy, dz, sj.n[0], sj.n[1], sj.n[2], t.a, t.m[0], t.m[1], t.m[2], tj.p, tj.q);
@@ -79,6 +87,7 @@ struct SymPolicy {
       sym_transpose<1>(R, dx, dy, dz, sj.n[0], sj.n[1], sj.n[2], t.a, t.m[0], t.m[1], t.m[2], tj.p, tj.q);
     }
   }
+  __device__ static void renorm(Acc&) {}
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static T shfl(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
   __device__ static PT out(T v) { return v; }
@@ -95,6 +104,7 @@ struct SymDFPolicy {
   using V4 = float4;
   using PT = double;
   static constexpr int RW = 5;
+  static constexpr int UNROLL = 1;
   struct Elem {
     df x[3], a, m[3], n[3];
   };
@@ -118,7 +128,7 @@ struct SymDFPolicy {
   template <bool MASK>
   __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
     const df d[3] = {df_sub(t.x[0], sj.x[0]), df_sub(t.x[1], sj.x[1]), df_sub(t.x[2], sj.x[2])};
-    const DFTerms R = df_sym_terms<MASK>(d[0], d[1], d[2], masked, g.c, sym_exp_table());
+    const DFTerms R = df_sym_terms<MASK, TRANS>(d[0], d[1], d[2], masked, g.c, sym_exp_table());
     if (!TRANS) {
       df_sym_forward<1>(R, d, t.n, sj.a, sj.m, ti.p, ti.q);
       df_sym_forward<-1>(R, d, sj.n, t.a, t.m, tj.p, tj.q);
@@ -126,6 +136,11 @@ struct SymDFPolicy {
       df_sym_transpose<-1>(R, d, t.n, sj.a, sj.m, ti.p, ti.q);
       df_sym_transpose<1>(R, d, sj.n, t.a, t.m, tj.p, tj.q);
     }
+  }
+  // the accumulators are updated lazily (df_mac): bring them back to normal form
+  __device__ static void renorm(Acc& v) {
+    v.p = two_sum(v.p.hi, v.p.lo);
+    v.q = two_sum(v.q.hi, v.q.lo);
   }
   __device__ static df add(df a, df b) { return df_add(a, b); }
   __device__ static df shfl(df v, int m) {
@@ -135,12 +150,42 @@ struct SymDFPolicy {
 };
 
 // ------------------------------------------------------------------ kernel
-// Item (two int4): {rec_off, n, t0, sys}, {s0, s1, jrow, ioff}:
-//   targets t0 + [0, T) of a system with n elements whose records start at
-//   rec_off; sources [s0, s1) (s0 >= t0); i-side partials at part[ioff +
-//   c T + i - t0], j-side at part[jrow + c (n - t0) + j - t0].
-template <class P, int NT, int TPT, int CH>
-__global__ void __launch_bounds__(NT) k_sym(typename P::Args g, const int4* __restrict__ items,
+// One shared-memory chunk of cnt sources (starting at j0) against the
+// thread's TPT targets.  MASK: the chunk overlaps the tile's own targets, and
+// pairs with j <= i are masked.  The j side of every source is reduced over
+// the warp by a fixed butterfly (lanes 0-15 end with P, lanes 16-31 with Q)
+// and left in jred[warp][source].
+template <class P, int TPT, int CH, bool MASK>
+__device__ __forceinline__ void sym_chunk(const typename P::Args& g, const typename P::Elem* tg, const int* idx,
+                                          typename P::Acc* acc, const typename P::V4* sh, int cnt, int j0,
+                                          typename P::Acc (*jred)[CH]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool upper = (lane & 16) != 0;
+#pragma unroll P::UNROLL
+  for (int jj = 0; jj < cnt; ++jj) {
+    typename P::Elem sj;
+    P::load(sh + jj * P::RW, sj);
+    typename P::Acc tj;
+    P::zero(tj);
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) P::template pair<MASK>(g, tg[k], sj, MASK && j0 + jj <= idx[k], acc[k], tj);
+    P::renorm(tj);
+    auto keep = upper ? tj.q : tj.p;
+    keep = P::add(keep, P::shfl(upper ? tj.p : tj.q, 16));
+#pragma unroll
+    for (int m = 8; m >= 1; m >>= 1) keep = P::add(keep, P::shfl(keep, m));
+    if (lane == 0) jred[warp][jj].p = keep;
+    if (lane == 16) jred[warp][jj].q = keep;
+  }
+}
+
+// Item (three int4): {rec_off, n, sys, jbase}, then two segments
+// {t0, s0, s1, ioff} (s0 == s1: empty): targets t0 + [0, T) of a system with n
+// elements whose records start at rec_off, against sources [s0, s1) (s0 >=
+// t0); i-side partials at part[ioff + c T + i - t0], j-side at part[jrow +
+// c (n - t0) + j - t0] with jrow the start of row t0 / T after jbase.
+template <class P, int NT, int TPT, int CH, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4* __restrict__ items,
                                             const typename P::V4* __restrict__ rec, typename P::PT* __restrict__ part,
                                             const int* __restrict__ skip, int skip_stride) {
   using V4 = typename P::V4;
@@ -148,66 +193,55 @@ __global__ void __launch_bounds__(NT) k_sym(typename P::Args g, const int4* __re
   constexpr int NW = NT / 32, T = NT * TPT;
   __shared__ V4 sh[CH * P::RW];
   __shared__ Acc jred[NW][CH];
-  const int4 I0 = items[2 * blockIdx.x], I1 = items[2 * blockIdx.x + 1];
-  const int rec_off = I0.x, n = I0.y, t0 = I0.z, sys = I0.w;
-  const int s0 = I1.x, s1 = I1.y, jrow = I1.z, ioff = I1.w;
+  const int4 H = items[3 * blockIdx.x];
+  const int rec_off = H.x, n = H.y, sys = H.z, jbase = H.w;
   if (skip != nullptr && skip[(size_t)sys * skip_stride] != 0) return;
-  P::prologue(g);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  typename P::Elem tg[TPT];
-  Acc acc[TPT];
-  int idx[TPT];
+  P::prologue(g);  // per-CTA shared tables (made visible by the first barrier below)
+  for (int seg = 0; seg < 2; ++seg) {
+    const int4 S = items[3 * blockIdx.x + 1 + seg];
+    const int t0 = S.x, s0 = S.y, s1 = S.z, ioff = S.w;
+    if (s0 >= s1) continue;
+    const int I = t0 / T;
+    const int64_t jrow = jbase + 2 * ((int64_t)I * n - (int64_t)T * I * (I - 1) / 2);
+    const int len = n - t0;  // j-side row length
+    typename P::Elem tg[TPT];
+    Acc acc[TPT];
+    int idx[TPT];
 #pragma unroll
-  for (int k = 0; k < TPT; ++k) {
-    idx[k] = t0 + k * NT + threadIdx.x;
-    P::load(rec + (size_t)(rec_off + min(idx[k], n - 1)) * P::RW, tg[k]);
-    P::zero(acc[k]);
-  }
-  const int len = n - t0;  // j-side row length
-  for (int j0 = s0; j0 < s1; j0 += CH) {
-    const int cnt = min(CH, s1 - j0);
-    __syncthreads();
-    const V4* src = rec + (size_t)(rec_off + j0) * P::RW;
-    for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
-    __syncthreads();
-    const bool diag = j0 < t0 + T;  // the chunk overlaps the tile's own targets: mask j <= i
-    for (int jj = 0; jj < cnt; ++jj) {
-      typename P::Elem sj;
-      P::load(sh + jj * P::RW, sj);
-      Acc tj;
-      P::zero(tj);
-      if (diag) {
+    for (int k = 0; k < TPT; ++k) {
+      idx[k] = t0 + k * NT + threadIdx.x;
+      P::load(rec + (size_t)(rec_off + min(idx[k], n - 1)) * P::RW, tg[k]);
+      P::zero(acc[k]);
+    }
+    for (int j0 = s0; j0 < s1; j0 += CH) {
+      const int cnt = min(CH, s1 - j0);
+      __syncthreads();
+      const V4* src = rec + (size_t)(rec_off + j0) * P::RW;
+      for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
+      __syncthreads();
+      if (j0 < t0 + T)
+        sym_chunk<P, TPT, CH, true>(g, tg, idx, acc, sh, cnt, j0, jred);
+      else
+        sym_chunk<P, TPT, CH, false>(g, tg, idx, acc, sh, cnt, j0, jred);
 #pragma unroll
-        for (int k = 0; k < TPT; ++k) P::template pair<true>(g, tg[k], sj, j0 + jj <= idx[k], acc[k], tj);
-      } else {
+      for (int k = 0; k < TPT; ++k) P::renorm(acc[k]);
+      __syncthreads();
+      for (int q = threadIdx.x; q < cnt; q += NT) {
+        Acc v = jred[0][q];
 #pragma unroll
-        for (int k = 0; k < TPT; ++k) P::template pair<false>(g, tg[k], sj, false, acc[k], tj);
+        for (int w = 1; w < NW; ++w) v.p = P::add(v.p, jred[w][q].p), v.q = P::add(v.q, jred[w][q].q);
+        const int o = j0 + q - t0;
+        part[jrow + o] = P::out(v.p);
+        part[jrow + len + o] = P::out(v.q);
       }
-      // fixed butterfly: lanes 0-15 end with the P total, lanes 16-31 with Q
-      const bool upper = (lane & 16) != 0;
-      auto keep = upper ? tj.q : tj.p;
-      keep = P::add(keep, P::shfl(upper ? tj.p : tj.q, 16));
-#pragma unroll
-      for (int m = 8; m >= 1; m >>= 1) keep = P::add(keep, P::shfl(keep, m));
-      if (lane == 0) jred[warp][jj].p = keep;
-      if (lane == 16) jred[warp][jj].q = keep;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < cnt; q += NT) {
-      Acc v = jred[0][q];
 #pragma unroll
-      for (int w = 1; w < NW; ++w) v.p = P::add(v.p, jred[w][q].p), v.q = P::add(v.q, jred[w][q].q);
-      const int o = j0 + q - t0;
-      part[(size_t)jrow + o] = P::out(v.p);
-      part[(size_t)jrow + len + o] = P::out(v.q);
-    }
+    for (int k = 0; k < TPT; ++k)
+      if (idx[k] < n) {
+        part[(size_t)ioff + idx[k] - t0] = P::out(acc[k].p);
+        part[(size_t)ioff + T + idx[k] - t0] = P::out(acc[k].q);
+      }
   }
-#pragma unroll
-  for (int k = 0; k < TPT; ++k)
-    if (idx[k] < n) {
-      part[(size_t)ioff + idx[k] - t0] = P::out(acc[k].p);
-      part[(size_t)ioff + T + idx[k] - t0] = P::out(acc[k].q);
-    }
 }
 
 // ------------------------------------------------------------------ pack / reduce
@@ -283,27 +317,42 @@ __global__ void k_reduce_sym(const int4* __restrict__ lay, const int4* __restric
 int blocks_of(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
 // ------------------------------------------------------------------ work list
-// Rows of every system are cut into pieces of about Lsrc sources; Lsrc is the
-// candidate whose greedy schedule (pieces sorted by size, each to the first
-// free CTA slot) finishes first.  A piece costs T x (sources + 32).
+// Folded rows (I, nT - 1 - I) of every system are cut into pieces of about
+// Lsrc sources; Lsrc is the candidate whose greedy schedule (pieces sorted by
+// size, each to the first free CTA slot) finishes first.  A piece costs its
+// sources plus 32 per segment (loading a tile, storing its partials).
 ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slots, int ch) {
   auto it = s->plans.find(key);
   if (it != s->plans.end()) return it->second.get();
   const int K = L.K;
-  struct Row {
-    int k, I, len;
+  struct Fold {
+    int k, Ia, Ib, la, lb;  // rows Ia and Ib (-1: none) with la and lb sources
   };
-  std::vector<Row> rows;
+  std::vector<Fold> folds;
+  int64_t total = 0;
+  int n_max = 1;
   for (int k = 0; k < K; ++k) {
-    const int nT = (L.n[k] + T - 1) / T;
-    for (int I = 0; I < nT; ++I) rows.push_back(Row{k, I, L.n[k] - I * T});
+    const int n = L.n[k], nT = (n + T - 1) / T;
+    n_max = std::max(n_max, n);
+    for (int I = 0; I < nT / 2; ++I) {
+      const int Ib = nT - 1 - I;
+      folds.push_back(Fold{k, I, Ib, n - I * T, n - Ib * T});
+    }
+    if (nT % 2) folds.push_back(Fold{k, nT / 2, -1, n - (nT / 2) * T, 0});
   }
-  auto pieces_of = [&](int len, int Ls) { return std::max(1, (len + Ls - 1) / Ls); };
-  auto makespan = [&](int Ls) {
+  for (const Fold& f : folds) total += f.la + f.lb;
+  auto pieces_of = [&](const Fold& f, double Ls) {
+    return std::max(1, (int)std::lround((f.la + f.lb) / Ls));
+  };
+  auto makespan = [&](double Ls) {
     std::vector<double> cost;
-    for (const Row& r : rows) {
-      const int P = pieces_of(r.len, Ls);
-      for (int p = 0; p < P; ++p) cost.push_back((double)((int64_t)(p + 1) * r.len / P - (int64_t)p * r.len / P) + 32.0);
+    for (const Fold& f : folds) {
+      const int P = pieces_of(f, Ls), len = f.la + f.lb;
+      for (int p = 0; p < P; ++p) {
+        const int a = (int)((int64_t)p * len / P), b = (int)((int64_t)(p + 1) * len / P);
+        const int segs = (a < f.la ? 1 : 0) + (b > f.la ? 1 : 0);
+        cost.push_back((double)(b - a) + 32.0 * segs);
+      }
     }
     std::sort(cost.begin(), cost.end(), std::greater<double>());
     std::priority_queue<double, std::vector<double>, std::greater<double>> q;
@@ -317,74 +366,91 @@ ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slot
     }
     return end;
   };
-  int n_max = 1;
-  double total = 0.0;
-  for (int k = 0; k < K; ++k) n_max = std::max(n_max, L.n[k]);
-  for (const Row& r : rows) total += r.len;
-  int best_L = n_max;
-  double best = makespan(n_max);
   // at most about 2e5 pieces: the candidates start where the list gets that long
-  for (double Ls = std::max((double)ch, total / 2e5); Ls < n_max; Ls *= 1.15) {
-    const double m = makespan((int)Ls);
-    if (m < best * 0.995) best = m, best_L = (int)Ls;
+  double best_L = 2.0 * n_max, best = makespan(best_L);
+  for (double Ls = std::max((double)ch, (double)total / 2e5); Ls < 2.0 * n_max; Ls *= 1.05) {
+    const double m = makespan(Ls);
+    if (m < best * 0.995) best = m, best_L = Ls;
   }
 
-  // pieces numbered row by row (i-side blocks), then ordered by size for the launch
-  struct Piece {
-    int k, I, s0, s1, ioff;
+  // segments: {k, row, s0, s1, piece}; a piece has one or two
+  struct Seg {
+    int k, I, s0, s1, piece;
   };
-  std::vector<Piece> pieces;
-  std::vector<int4> tab(K);
-  std::vector<int4> rowtab;
-  std::vector<int64_t> jbase(K);
-  int64_t off = 0;
-  int blocks = 0;
-  for (int k = 0; k < K; ++k) {
-    const int n = L.n[k], nT = (n + T - 1) / T;
-    tab[k] = make_int4(n, K + (int)rowtab.size(), 0, T);
-    for (int I = 0; I < nT; ++I) {
-      const int t0 = I * T, len = n - t0, P = pieces_of(len, best_L);
-      rowtab.push_back(make_int4(0, P, 0, 0));
-      for (int p = 0; p < P; ++p) {
-        pieces.push_back(Piece{k, I, t0 + (int)((int64_t)p * len / P), t0 + (int)((int64_t)(p + 1) * len / P),
-                               blocks});
-        ++blocks;
+  std::vector<Seg> segs;
+  std::vector<int> piece_cost;
+  for (const Fold& f : folds) {
+    const int P = pieces_of(f, best_L), len = f.la + f.lb;
+    for (int p = 0; p < P; ++p) {
+      const int a = (int)((int64_t)p * len / P), b = (int)((int64_t)(p + 1) * len / P);
+      const int id = (int)piece_cost.size();
+      piece_cost.push_back(b - a);
+      const int ta = f.Ia * T;
+      if (a < f.la) segs.push_back(Seg{f.k, f.Ia, ta + a, ta + std::min(b, f.la), id});
+      if (b > f.la) {
+        const int tb = f.Ib * T;
+        segs.push_back(Seg{f.k, f.Ib, tb + std::max(a - f.la, 0), tb + (b - f.la), id});
       }
     }
   }
-  // i-side blocks first (2 T each), then the j-side rows of every system
-  {
-    int b = 0;
-    for (auto& rt : rowtab) {
-      rt.x = (int)((int64_t)b * 2 * T);
-      b += rt.y;
-    }
+  // i-side blocks numbered row by row (system, row, first source)
+  std::vector<int> order(segs.size());
+  for (size_t i = 0; i < segs.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    const Seg &a = segs[x], &b = segs[y];
+    if (a.k != b.k) return a.k < b.k;
+    if (a.I != b.I) return a.I < b.I;
+    return a.s0 < b.s0;
+  });
+  std::vector<int> block(segs.size());
+  std::vector<int4> tab(K);
+  std::vector<int> rowbase(K);
+  int nrows = 0;
+  for (int k = 0; k < K; ++k) {
+    rowbase[k] = K + nrows;
+    nrows += (L.n[k] + T - 1) / T;
   }
-  off = (int64_t)blocks * 2 * T;
+  std::vector<int4> rowtab(nrows, make_int4(0, 0, 0, 0));
+  for (size_t r = 0; r < order.size(); ++r) {
+    const Seg& g = segs[order[r]];
+    block[order[r]] = (int)r;
+    int4& e = rowtab[rowbase[g.k] - K + g.I];
+    if (e.y == 0) e.x = (int)((int64_t)r * 2 * T);
+    e.y += 1;
+  }
+  int64_t off = (int64_t)segs.size() * 2 * T;
+  std::vector<int64_t> jbase(K);
   for (int k = 0; k < K; ++k) {
     const int n = L.n[k], nT = (n + T - 1) / T;
     jbase[k] = off;
-    for (int I = 0; I < nT; ++I) off += 2 * (int64_t)(n - I * T);
+    off += 2 * ((int64_t)nT * n - (int64_t)T * nT * (nT - 1) / 2);
+    tab[k] = make_int4(n, rowbase[k], (int)jbase[k], T);
   }
   BIPB_REQUIRE(off < ((int64_t)1 << 31), "mat-vec too large for one symmetric work list");
-  for (int k = 0; k < K; ++k) tab[k].z = (int)jbase[k];
-  std::stable_sort(pieces.begin(), pieces.end(),
-                   [](const Piece& a, const Piece& b) { return a.s1 - a.s0 > b.s1 - b.s0; });
-  std::vector<int4> items;
-  items.reserve(2 * pieces.size());
-  for (const Piece& p : pieces) {
-    const int n = L.n[p.k], t0 = p.I * T;
-    const int64_t jrow = jbase[p.k] + 2 * ((int64_t)p.I * n - (int64_t)T * p.I * (p.I - 1) / 2);
-    items.push_back(make_int4(L.vec_off[p.k] / 2, n, t0, p.k));
-    items.push_back(make_int4(p.s0, p.s1, (int)jrow, (int)((int64_t)p.ioff * 2 * T)));
+
+  // items: three int4 per piece, largest piece first
+  const int n_pieces = (int)piece_cost.size();
+  std::vector<int4> items((size_t)3 * n_pieces, make_int4(0, 0, 0, 0));
+  std::vector<int> nseg(n_pieces, 0);
+  for (size_t i = 0; i < segs.size(); ++i) {
+    const Seg& g = segs[i];
+    const int p = g.piece;
+    items[3 * p] = make_int4(L.vec_off[g.k] / 2, L.n[g.k], g.k, (int)jbase[g.k]);
+    items[3 * p + 1 + nseg[p]++] = make_int4(g.I * T, g.s0, g.s1, (int)((int64_t)block[i] * 2 * T));
   }
+  std::vector<int> porder(n_pieces);
+  for (int p = 0; p < n_pieces; ++p) porder[p] = p;
+  std::stable_sort(porder.begin(), porder.end(), [&](int x, int y) { return piece_cost[x] > piece_cost[y]; });
+  std::vector<int4> sorted((size_t)3 * n_pieces);
+  for (int p = 0; p < n_pieces; ++p)
+    for (int c = 0; c < 3; ++c) sorted[(size_t)3 * p + c] = items[(size_t)3 * porder[p] + c];
   tab.insert(tab.end(), rowtab.begin(), rowtab.end());
   auto plan = std::make_unique<ItemPlan>();
-  plan->n_items = (int)pieces.size();
+  plan->n_items = n_pieces;
   plan->part_len = off;
-  plan->items.ensure(items.size());
+  plan->items.ensure(sorted.size());
   plan->tab.ensure(tab.size());
-  BIPB_CUDA(cudaMemcpyAsync(plan->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+  BIPB_CUDA(cudaMemcpyAsync(plan->items.p, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             s->stream));
   BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
   BIPB_CUDA(cudaStreamSynchronize(s->stream));
@@ -416,11 +482,11 @@ bool sym_fits(const SysLayout& L, int T) {
   return off < ((int64_t)1 << 30);
 }
 
-template <class P, int NT, int TPT, int CH>
+template <class P, int NT, int TPT, int CH, int MINB>
 int sym_occupancy() {
   static int occ = [] {
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sym<P, NT, TPT, CH>, NT, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_sym<P, NT, TPT, CH, MINB>, NT, 0) != cudaSuccess) {
       (void)cudaGetLastError();
       o = 1;
     }
@@ -429,13 +495,13 @@ int sym_occupancy() {
   return occ;
 }
 
-template <class P, int NT, int TPT, int CH>
+template <class P, int NT, int TPT, int CH, int MINB>
 void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typename P::Args& g, bool transpose,
              DevBuf<typename P::V4>& recbuf, DevBuf<typename P::PT>& partbuf, const double* u, double* y,
              double dphi, double dpsi, const int* skip, int skip_stride) {
   constexpr int T = NT * TPT;
   const uint64_t key = sym_key(pass_id, L.key);
-  ItemPlan* plan = plan_sym(s, key, L, T, s->num_sms * sym_occupancy<P, NT, TPT, CH>(), CH);
+  ItemPlan* plan = plan_sym(s, key, L, T, s->num_sms * sym_occupancy<P, NT, TPT, CH, MINB>(), CH);
   s->grow(recbuf, (size_t)(L.len / 2) * P::RW);
   s->grow(partbuf, (size_t)plan->part_len);
   const int4* lay = s->lay_dev(L);
@@ -449,8 +515,8 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
   BIPB_LAUNCHED(s);
   {
     TimedLaunch tl(s, kind);
-    k_sym<P, NT, TPT, CH><<<plan->n_items, NT, 0, s->stream>>>(g, plan->items.p, recbuf.p, partbuf.p, skip,
-                                                                skip_stride);
+    k_sym<P, NT, TPT, CH, MINB><<<plan->n_items, NT, 0, s->stream>>>(g, plan->items.p, recbuf.p, partbuf.p, skip,
+                                                                      skip_stride);
     BIPB_LAUNCHED(s);
   }
   k_reduce_sym<typename P::PT><<<dim3(blocks_of(2 * (int64_t)L.max_n, 256), L.K), 256, 0, s->stream>>>(
@@ -462,23 +528,23 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
 
 bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, int variant,
                   const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
-  static const int kT[3] = {512, 512, 1024};
+  static const int kT[3] = {512, 512, 1024};  // NT x TPT of the variants below
   if (variant < 0 || variant > 2) throw Error(BIPB_ERR_INVALID_ARG, "unknown symmetric FP32 mat-vec variant");
   if (!sym_fits(L, kT[variant])) return false;
   const int kind = transpose ? kTMv32T : kTMv32;
-#define BIPB_SYM32(V_, NT_, TPT_, CH_)                                                                       \
+#define BIPB_SYM32(V_, NT_, TPT_, CH_, MINB_)                                                               \
   case V_:                                                                                                   \
     if (transpose)                                                                                           \
-      run_sym<SymPolicy<float, true>, NT_, TPT_, CH_>(s, 0x100 + V_, kind, L, {c}, true, s->rec32, s->part32, \
-                                                      u, y, dphi, dpsi, skip, skip_stride);                  \
+      run_sym<SymPolicy<float, true>, NT_, TPT_, CH_, MINB_>(s, 0x100 + V_, kind, L, {c}, true, s->rec32,    \
+                                                             s->part32, u, y, dphi, dpsi, skip, skip_stride); \
     else                                                                                                     \
-      run_sym<SymPolicy<float, false>, NT_, TPT_, CH_>(s, 0x200 + V_, kind, L, {c}, false, s->rec32,         \
-                                                       s->part32, u, y, dphi, dpsi, skip, skip_stride);      \
+      run_sym<SymPolicy<float, false>, NT_, TPT_, CH_, MINB_>(s, 0x200 + V_, kind, L, {c}, false, s->rec32,  \
+                                                              s->part32, u, y, dphi, dpsi, skip, skip_stride); \
     return true;
   switch (variant) {
-    BIPB_SYM32(0, 256, 2, 128)
-    BIPB_SYM32(1, 128, 4, 128)
-    BIPB_SYM32(2, 256, 4, 64)
+    BIPB_SYM32(0, 256, 2, 64, 4)
+    BIPB_SYM32(1, 128, 4, 64, 5)
+    BIPB_SYM32(2, 256, 4, 64, 3)
   }
 #undef BIPB_SYM32
   return false;
@@ -488,10 +554,10 @@ bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, bo
                   double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
   if (!sym_fits(L, 256)) return false;
   if (transpose)
-    run_sym<SymPolicy<double, true>, 128, 2, 64>(s, 0x300, kTMv64T, L, {c}, true, s->rec64, s->part64, u, y, dphi,
+    run_sym<SymPolicy<double, true>, 128, 2, 64, 1>(s, 0x300, kTMv64T, L, {c}, true, s->rec64, s->part64, u, y, dphi,
                                                  dpsi, skip, skip_stride);
   else
-    run_sym<SymPolicy<double, false>, 128, 2, 64>(s, 0x400, kTMv64, L, {c}, false, s->rec64, s->part64, u, y, dphi,
+    run_sym<SymPolicy<double, false>, 128, 2, 64, 1>(s, 0x400, kTMv64, L, {c}, false, s->rec64, s->part64, u, y, dphi,
                                                   dpsi, skip, skip_stride);
   return true;
 }
@@ -500,10 +566,10 @@ bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, bool transp
                    double dphi, double dpsi, const int* skip, int skip_stride) {
   if (!sym_fits(L, 128)) return false;
   if (transpose)
-    run_sym<SymDFPolicy<true>, 128, 1, 32>(s, 0x500, kTMvDFT, L, {c}, true, s->recdf, s->part64, u, y, dphi, dpsi,
+    run_sym<SymDFPolicy<true>, 128, 1, 32, 1>(s, 0x500, kTMvDFT, L, {c}, true, s->recdf, s->part64, u, y, dphi, dpsi,
                                            skip, skip_stride);
   else
-    run_sym<SymDFPolicy<false>, 128, 1, 32>(s, 0x600, kTMvDF, L, {c}, false, s->recdf, s->part64, u, y, dphi, dpsi,
+    run_sym<SymDFPolicy<false>, 128, 1, 32, 1>(s, 0x600, kTMvDF, L, {c}, false, s->recdf, s->part64, u, y, dphi, dpsi,
                                             skip, skip_stride);
   return true;
 }
