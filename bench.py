@@ -30,6 +30,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -41,10 +42,15 @@ METRIC = "BIE matvec Gpairs/s; GMRES solve time at 1e-8 rel. residual, mixed vs 
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Algorithmic work per pair of the mat-vec ("Roofline"): flops
-# of the pair formula (an FMA counts 2) and FP32/FP64 pipe instructions.
+# Algorithmic work per ordered pair of the mat-vec: flops of the pair formula
+# with the source's area and values folded into its record (an FMA counts 2)
+# and the FP32/FP64-pipe instructions of that formula.
 PAIR_FLOPS = 56
 PAIR_PIPE_INSTR = 39
+# DRAM bytes (read + write) per launch of the FP32 mat-vec kernel on the Kirkwood
+# workload, by variant, from one ncu capture of that variant's kernel (the
+# records and partial sums stay in L2); variants without a capture report null
+DRAM_BYTES_FP32_KIRKWOOD = {9: 1.083648e6, 5: 1.369088e6}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM per clock
 FP64_LANES_PER_SM = 2    # FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
 
@@ -64,7 +70,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
-    ap.add_argument("--variant", type=int, default=-1, help="FP32 mat-vec variant for --mode matvec32")
+    ap.add_argument("--clocks-csv", default="", help="also keep the raw nvidia-smi clock samples in this file")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="FP32 mat-vec variant (default: autotuned; --mode matvec32: the handle's default)")
     ap.add_argument("--ordered-pairs", action="store_true",
                     help="FP64 / double-float mat-vecs visit every ordered pair (default: unordered pairs once)")
     ap.add_argument("--configs", default="3,4a,4b,5", help="--mode configs: which larger configurations")
@@ -93,14 +101,16 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, path=None):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.keep = bool(path)  # keep the raw samples only where asked
+        self.path = path or os.path.join(tempfile.gettempdir(), f"bipb_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            if os.path.dirname(self.path):
+                os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -120,7 +130,11 @@ class ClockSampler:
         self.f.close()
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as f:
+            lines = f.readlines()
+        if not self.keep:
+            os.remove(self.path)
+        for line in lines:
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -383,14 +397,19 @@ def main():
         e = s.energy()
         return info[0], e[0]
 
-    variant, mv_ms = s.autotune(bipb.medium(prob.eps_in, prob.eps_out, prob.kappa), reps=3)
-    log(f"autotune: FP32 mat-vec variant {variant}, {mv_ms:.4f} ms")
+    if args.variant >= 0:  # fixed variant (profiling runs: the autotuner's timings under a profiler differ)
+        s.set_variant(args.variant)
+        variant = args.variant
+        log(f"FP32 mat-vec variant {variant} (fixed)")
+    else:
+        variant, mv_ms = s.autotune(bipb.medium(prob.eps_in, prob.eps_out, prob.kappa), reps=3)
+        log(f"autotune: FP32 mat-vec variant {variant}, {mv_ms:.4f} ms")
     for _ in range(args.warmup):
         info, e = step()
     log(f"warm-up: {info} E={e:.6f} kcal/mol")
 
     # ---- timed region: K steps, events per step, L2 flushed between steps
-    cs = ClockSampler(local)
+    cs = ClockSampler(local, args.clocks_csv)
     bipb.timer_enable(s, True)
     launches0 = bipb.launch_count(s)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -435,8 +454,11 @@ def main():
     achieved = pairs_launch * PAIR_FLOPS / (avg_ms / 1e3) / 1e12
     peak = nsm * lanes * 2 * f_mhz * 1e6 / 1e12
     pipe_frac = pairs_launch * PAIR_PIPE_INSTR / (avg_ms / 1e3) / (nsm * lanes * f_mhz * 1e6)
+    traffic = None
+    if dom == "matvec32" and args.workload == "kirkwood":
+        traffic = DRAM_BYTES_FP32_KIRKWOOD.get(variant)
     roofline = {"bound": "alu", "kernel": f"{dom} pair kernel", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "pipe": "fp32" if lanes == FP32_LANES_PER_SM else "fp64", "pipe_frac": pipe_frac,
                 "peak_basis": f"{nsm} SMs x {lanes} {('FP32' if lanes == 128 else 'FP64')} FMA lanes x 2 flop x "
                               f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",

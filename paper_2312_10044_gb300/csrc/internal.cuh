@@ -201,7 +201,7 @@ struct Surface {
   bool have_solution = false;
   bipb_medium solved_medium{0, 0, 0};
 
-  int mv32_variant = 0;  // index into the FP32 mat-vec variants (set by the autotuner)
+  int mv32_variant = kFirstSymVariant + 2;  // FP32 mat-vec variant (the autotuner may change it)
   bool sym_pairs = true;  // FP64 / double-float mat-vecs visit unordered pairs once (sym.cu)
   GmresWork* gw = nullptr;
   KernelTimer timer;

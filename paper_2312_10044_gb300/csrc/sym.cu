@@ -318,8 +318,9 @@ int blocks_of(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1)
 
 // ------------------------------------------------------------------ work list
 // Folded rows (I, nT - 1 - I) of every system are cut into pieces of about
-// Lsrc sources; Lsrc is the candidate whose greedy schedule (pieces sorted by
-// size, each to the first free CTA slot) finishes first.  A piece costs its
+// Lsrc sources; Lsrc is the candidate (the length giving 1 .. 8 waves of
+// equal pieces) whose greedy schedule (pieces sorted by size, each to the
+// first free CTA slot) finishes first.  A piece costs its
 // sources plus 32 per segment (loading a tile, storing its partials).
 ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slots, int ch) {
   auto it = s->plans.find(key);
@@ -366,9 +367,10 @@ ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slot
     }
     return end;
   };
-  // at most about 2e5 pieces: the candidates start where the list gets that long
+  // candidates: the piece length that gives w waves of equal pieces, w = 1 .. 8
   double best_L = 2.0 * n_max, best = makespan(best_L);
-  for (double Ls = std::max((double)ch, (double)total / 2e5); Ls < 2.0 * n_max; Ls *= 1.05) {
+  for (int w = 1; w <= 8; ++w) {
+    const double Ls = std::max((double)ch, (double)total / ((double)w * slots));
     const double m = makespan(Ls);
     if (m < best * 0.995) best = m, best_L = Ls;
   }

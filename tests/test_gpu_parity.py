@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
 
-Tolerances (derivations in the design doc):
+Tolerances (each derived from the arithmetic of the path it checks):
 * FP64 passes (mat-vec, transpose, source, reaction): 1e-12 relative to the
   largest output (reordered FP64 sums over N <= 20480 terms).
 * FP32 mat-vec: 3e-6 in the 2-norm and 2e-5 of the largest output per
