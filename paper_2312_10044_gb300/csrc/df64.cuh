@@ -331,3 +331,35 @@ __device__ __forceinline__ void df_sym_transpose(const DFTerms& R, const df* d, 
 }
 
 }  // namespace bipb
+
+namespace bipb {
+
+// Source term of one (element, charge) pair in df64: target element (x, n),
+// charge (y, q), d = x - y:  S1 += q s,  S2 += -q (n.d) s^3  (times 4 pi eps_in).
+__device__ __forceinline__ void df_source_pair(const df* x, const df* nv, const df* y, df q, df& s1, df& s2) {
+  const df d0 = df_sub(x[0], y[0]), d1 = df_sub(x[1], y[1]), d2 = df_sub(x[2], y[2]);
+  const df s = df_rsqrt(df_sumsq3(d0, d1, d2));
+  const df qs = df_mul(q, s);
+  s1 = df_add(s1, qs);
+  const df cn = df_dot3(nv[0], nv[1], nv[2], d0, d1, d2);
+  s2 = df_sub(s2, df_mul(df_mul(qs, df_sqr(s)), cn));
+}
+
+// Reaction potential at a point y from one element (forward record: x, a =
+// ds psi, m = ds phi n), d = y - x (the K1, K2 terms with n_j only):
+//   4 pi phi += s [ (1 - e) a + (eps t - 1) (m.d) s^2 ]
+__device__ __forceinline__ void df_reaction_pair(const df* y, const df* x, df a, const df* m, const DFConst& c,
+                                                 const df* tab, df& acc) {
+  const df d0 = df_sub(y[0], x[0]), d1 = df_sub(y[1], x[1]), d2 = df_sub(y[2], x[2]);
+  const df r2 = df_sumsq3(d0, d1, d2);
+  const df s = df_rsqrt(r2);
+  const df kr = df_mul(df_mul(r2, s), c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df t = df_add(df_mul(e, kr), e);
+  const df cm = df_dot3(m[0], m[1], m[2], d0, d1, d2);
+  df p = df_mul(df_add_f(df_neg(e), 1.0f), a);
+  p = df_add(p, df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cm), df_sqr(s)));
+  acc = df_add(acc, df_mul(p, s));
+}
+
+}  // namespace bipb

@@ -174,12 +174,14 @@ struct Surface {
   DevBuf<double4_32a> rec64;
   DevBuf<float> part32;
   DevBuf<double> part64;
+  DevBuf<int> rhs_idx;  // right-hand-side indices of a compacted multi-RHS pass
 
   // charges: every system's charge records (y - center, q), back to back
   int64_t nc = 0;  // charges per configuration (single surface)
   int n_rhs = 0;   // configurations (systems)
   int n_pos_sets = 0;
   DevBuf<double4_32a> chg;
+  DevBuf<float4> chgdf;  // the charges as df64 records (2 float4 each), packed by the source pass
   SysLayout lay;   // the systems bipb_solve works on
 
   // surfaces of the handle (one for bipb_surface_create, several for a

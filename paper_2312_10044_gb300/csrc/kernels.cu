@@ -139,17 +139,22 @@ struct MatvecDFPolicy {
   }
 };
 
-// Source term: target element i, source charge k with record (y_k, q_k), d = x_i - y_k:
+// Source term in df64: target element i, source charge k with df record
+// (y_k.hi, q_k.hi), (y_k.lo, q_k.lo), d = x_i - y_k:
 //   4 pi eps_in S1 += q s,   4 pi eps_in S2 += -q (n_i.d) s^3   (d/dnu_x = +n_x.grad_x)
+// GB300 executes FP64 at 1/64 of the FP32 rate; df64 keeps b accurate to
+// about 1e-14 relative at a fraction of the FP64 cost.
 struct SourcePolicy {
-  static constexpr int RW = 1;
+  static constexpr int RW = 2;
   static constexpr int NOUT = 2;
   static constexpr bool SELF = false;
   template <class A>
   __device__ static void prologue(const A&) {}
-  using Tgt = ElemTgt<double>;
+  struct Tgt {
+    df x[3], n[3];
+  };
   struct Acc {
-    double s1, s2;
+    df s1, s2;
   };
   struct Args {
     const double4_32a* tgt;  // 2 per element
@@ -157,21 +162,19 @@ struct SourcePolicy {
   };
   __device__ static void load(const Args& a, int i, Tgt& t) {
     double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
-    t = Tgt{g.x, g.y, g.z, v.x, v.y, v.z};
+    t.x[0] = df_from_double(g.x), t.x[1] = df_from_double(g.y), t.x[2] = df_from_double(g.z);
+    t.n[0] = df_from_double(v.x), t.n[1] = df_from_double(v.y), t.n[2] = df_from_double(v.z);
   }
-  __device__ static void zero(Acc& acc) { acc.s1 = 0.0, acc.s2 = 0.0; }
+  __device__ static void zero(Acc& acc) { acc.s1 = df{0.f, 0.f}, acc.s2 = df{0.f, 0.f}; }
   template <bool MASK>
-  __device__ static void pair(const Args&, const Tgt& t, const double4_32a* r, bool, Acc& acc) {
-    const double4_32a A = r[0];
-    double dx = t.x - A.x, dy = t.y - A.y, dz = t.z - A.z;
-    double s = fmin(rsqrt(dx * dx + dy * dy + dz * dz), kSMaxD);
-    double qs = A.w * s;
-    acc.s1 += qs;
-    acc.s2 -= qs * (s * s) * (t.nx * dx + t.ny * dy + t.nz * dz);
+  __device__ static void pair(const Args&, const Tgt& t, const float4* r, bool, Acc& acc) {
+    const float4 A = r[0], B = r[1];
+    const df y[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    df_source_pair(t.x, t.n, y, df{A.w, B.w}, acc.s1, acc.s2);
   }
   __device__ static void store(const Args& a, int out, int n_tgt, int i, const Acc& acc) {
-    a.part[(size_t)out + i] = acc.s1;
-    a.part[(size_t)out + n_tgt + i] = acc.s2;
+    a.part[(size_t)out + i] = df_to_double(acc.s1);
+    a.part[(size_t)out + n_tgt + i] = df_to_double(acc.s2);
   }
 };
 
@@ -179,44 +182,43 @@ struct PointTgt {
   double x, y, z;
 };
 
-// Reaction potential at a charge y_k from the surface (forward FP64 record
-// (x_j, a_j = ds psi_j), m_j = ds phi_j n_j), d = y_k - x_j:
+// Reaction potential at a charge y_k from the surface in df64 (forward df
+// record (x_j, a_j = ds psi_j), m_j = ds phi_j n_j), d = y_k - x_j:
 //   4 pi phi_reac += s [ (1 - e) a_j + (eps t - 1) (m_j.d) s^2 ]  (K1 psi + K2 phi, n_j only)
 struct ReactionPolicy {
-  static constexpr int RW = 2;
+  static constexpr int RW = 4;
   static constexpr int NOUT = 1;
   static constexpr bool SELF = false;
-  template <class A>
-  __device__ static void prologue(const A&) {}
-  using Tgt = PointTgt;
+  struct Tgt {
+    df y[3];
+  };
   struct Acc {
-    double p;
+    df p;
   };
   struct Args {
     const double4_32a* pts;  // (y, q)
     double* part;
-    PairConst<double> c;
+    DFConst c;
   };
+  template <class A>
+  __device__ static void prologue(const A&) {
+    df* tab = df_exp_table();
+    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  }
   __device__ static void load(const Args& a, int k, Tgt& t) {
     double4_32a g = a.pts[k];
-    t = Tgt{g.x, g.y, g.z};
+    t.y[0] = df_from_double(g.x), t.y[1] = df_from_double(g.y), t.y[2] = df_from_double(g.z);
   }
-  __device__ static void zero(Acc& acc) { acc.p = 0.0; }
+  __device__ static void zero(Acc& acc) { acc.p = df{0.f, 0.f}; }
   template <bool MASK>
-  __device__ static void pair(const Args& a, const Tgt& t, const double4_32a* r, bool, Acc& acc) {
-    const double4_32a A = r[0], B = r[1];
-    double dx = t.x - A.x, dy = t.y - A.y, dz = t.z - A.z;
-    double r2 = dx * dx + dy * dy + dz * dz;
-    double s, rr, e;
-    radial<false>(r2, false, a.c, s, rr, e);
-    double t1 = e * (rr * a.c.kappa) + e;
-    double cm = B.x * dx + B.y * dy + B.z * dz;
-    double p = A.w - e * A.w;
-    p += ((a.c.eps * t1 - 1.0) * cm) * (s * s);
-    acc.p += p * s;
+  __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool, Acc& acc) {
+    const float4 A = r[0], B = r[1], C = r[2], D = r[3];
+    const df xs[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    const df m[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
+    df_reaction_pair(t.y, xs, df{A.w, B.w}, m, a.c, df_exp_table(), acc.p);
   }
   __device__ static void store(const Args& a, int out, int, int k, const Acc& acc) {
-    a.part[(size_t)out + k] = acc.p;
+    a.part[(size_t)out + k] = df_to_double(acc.p);
   }
 };
 
@@ -947,14 +949,31 @@ int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int 
   return best;
 }
 
+// df64 records of every charge: (y.hi, q.hi), (y.lo, q.lo)
+__global__ void k_pack_chg_df(int n_chg, const double4_32a* __restrict__ chg, float4* __restrict__ rec) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_chg) return;
+  const double4_32a c = chg[k];
+  const df x = df_from_double(c.x), y = df_from_double(c.y), z = df_from_double(c.z), q = df_from_double(c.w);
+  rec[2 * k] = make_float4(x.hi, y.hi, z.hi, q.hi);
+  rec[2 * k + 1] = make_float4(x.lo, y.lo, z.lo, q.lo);
+}
+
 void source_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* b) {
   constexpr int NT = 128, TPT = 1, CH = 64;
   std::vector<PassSys> sys(L.K);
-  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.geo_off[k], L.n[k], L.chg_off[k], L.nc[k]};
-  ItemPlan* plan = plan_pass<SourcePolicy, double4_32a, NT, TPT, CH>(s, kPassSource, sys, CH);
+  int n_chg = 0;
+  for (int k = 0; k < L.K; ++k) {
+    sys[k] = PassSys{L.geo_off[k], L.n[k], L.chg_off[k], L.nc[k]};
+    n_chg = std::max(n_chg, L.chg_off[k] + L.nc[k]);
+  }
+  ItemPlan* plan = plan_pass<SourcePolicy, float4, NT, TPT, CH>(s, kPassSource, sys, CH);
+  s->grow(s->chgdf, (size_t)2 * n_chg);
   s->grow(s->part64, (size_t)plan->part_len);
+  k_pack_chg_df<<<blocks_for(n_chg, 256), 256, 0, s->stream>>>(n_chg, s->chg.p, s->chgdf.p);
+  BIPB_LAUNCHED(s);
   SourcePolicy::Args a{s->tgt64.p, s->part64.p};
-  launch_items<SourcePolicy, double4_32a, NT, TPT, CH>(s, kTSource, plan, a, s->chg.p, nullptr, 0);
+  launch_items<SourcePolicy, float4, NT, TPT, CH>(s, kTSource, plan, a, s->chgdf.p, nullptr, 0);
   k_reduce_source<<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
       s->lay_dev(L), plan->tab.p, s->part64.p, kInv4Pi / m.eps_in, b);
   BIPB_LAUNCHED(s);
@@ -965,15 +984,15 @@ void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const d
   constexpr int NT = 128, TPT = 1, CH = 64;
   std::vector<PassSys> sys(L.K);
   for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.chg_off[k], L.nc[k], L.vec_off[k] / 2, L.n[k]};
-  ItemPlan* plan = plan_pass<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kPassReaction, sys, CH);
-  s->grow(s->rec64, (size_t)L.len);
+  ItemPlan* plan = plan_pass<ReactionPolicy, float4, NT, TPT, CH>(s, kPassReaction, sys, CH);
+  s->grow(s->recdf, (size_t)2 * L.len);  // 4 float4 per element
   s->grow(s->part64, (size_t)plan->part_len);
   const int4* lay = s->lay_dev(L);
-  k_pack<double4_32a, double><<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(
-      lay, false, s->tgt64.p, u, s->rec64.p, nullptr, 0);
+  k_pack_df<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, false, s->tgt64.p, u, s->recdf.p,
+                                                                          nullptr, 0);
   BIPB_LAUNCHED(s);
-  ReactionPolicy::Args a{s->chg.p, s->part64.p, pair_const<double>(m)};
-  launch_items<ReactionPolicy, double4_32a, NT, TPT, CH>(s, kTReaction, plan, a, s->rec64.p, nullptr, 0);
+  ReactionPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(m)};
+  launch_items<ReactionPolicy, float4, NT, TPT, CH>(s, kTReaction, plan, a, s->recdf.p, nullptr, 0);
   k_reduce_reaction<<<L.K, 1024, 0, s->stream>>>(plan->tab.p, lay, s->part64.p, s->chg.p, phi_reac, e_out);
   BIPB_LAUNCHED(s);
 }

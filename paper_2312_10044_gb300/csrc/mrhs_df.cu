@@ -1,16 +1,18 @@
 // Multi-right-hand-side mat-vec in double-float arithmetic (the refinement
 // residual of batched solves).
 //
-// Y = A U for up to 64 right-hand sides of one surface.  A CTA of 256
-// threads covers 64 targets x 4 groups of 16 right-hand sides (warp w: group
-// w % 4, targets 32 (w / 4) + lane) against one range of sources, staged 16
-// at a time in shared memory together with their 64 right-hand-side values.
-// Every thread generates the 2 x 2 kernel block of each pair in df64 (the
-// K1..K4 of Sec. 2.2.1 times ds_j, df64.cuh) once and applies it to its 16
-// right-hand sides with df64 multiply-adds, so the costly generation is
-// shared by 16 right-hand sides instead of repeated for each.  Partial sums
-// per source split are written in FP64 and added by the FP64 reduction of
-// kernels.cu.
+// Y = A U for up to 64 right-hand sides of one surface.  A CTA covers 64
+// targets and G groups of 16 right-hand sides (G = 1, 2 or 4, 64 G threads)
+// against one range of sources, staged 16 at a time in shared memory with
+// their right-hand-side values.  For every chunk the CTA first generates the
+// 2 x 2 kernel block of each (target, source) pair in df64 once (the K1..K4
+// of Sec. 2.2.1 times ds_j, df64.cuh; 16 / G pairs per thread) into shared
+// memory; then thread (group g, target t) applies the 16 blocks of its target
+// to the group's 16 right-hand sides with df64 multiply-adds.  The costly
+// generation is thus shared by all right-hand sides of the CTA, and a pass
+// over fewer right-hand sides (a refinement step in which most systems have
+// converged) uses fewer groups.  Partial sums per source split are written in
+// FP64 and added by the FP64 reduction of kernels.cu.
 #include <algorithm>
 
 #include "df64.cuh"
@@ -20,22 +22,34 @@ namespace bipb {
 
 namespace {
 
-constexpr int kNB = 64;     // right-hand sides per launch
-constexpr int kGB = 16;     // right-hand sides per thread
+constexpr int kNB = 64;     // right-hand sides per launch (at most)
+constexpr int kGB = 16;     // right-hand sides per group (per thread)
 constexpr int kTgt = 64;    // targets per CTA
-constexpr int kNT = 256;    // threads per CTA
 constexpr int kCh = 16;     // sources per shared-memory chunk
 
-// items: {t0, s0, s1, split}; u: system b at (b0 + b) * 2n; part: [b][split][2n]
-__global__ void __launch_bounds__(kNT, 1) k_mrhs_df(int n, int nb, int n_splits, const int4* __restrict__ items,
-                                                    const double4_32a* __restrict__ tgt64, const double* __restrict__ u,
-                                                    double* __restrict__ part, DFConst c) {
-  __shared__ float4 srec[kCh][4];        // (x.hi, n.hi), (x.lo, n.lo) split as below
-  __shared__ float4 ush[kCh][kNB];       // (phi.hi, phi.lo, psi.hi, psi.lo)
-  __shared__ df tab[32];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = warp & 3;
-  const int tl = 32 * (warp >> 2) + lane;
+// Dynamic shared memory of one CTA with G groups: kernel blocks (hi, lo),
+// right-hand-side values, source records, exp table.
+template <int G>
+constexpr int smem_bytes() {
+  return 2 * kCh * kTgt * 16 + kGB * G * kCh * 16 + kCh * 4 * 16 + 32 * 8;
+}
+
+// items: {t0, s0, s1, split}; u: right-hand side b at rhs[b] * 2n (b * 2n when
+// rhs is null); part: [b][split][2n]
+template <int G>
+__global__ void __launch_bounds__(kTgt * G, 1) k_mrhs_df(int n, int nb, int n_splits, const int4* __restrict__ items,
+                                                         const double4_32a* __restrict__ tgt64,
+                                                         const double* __restrict__ u, const int* __restrict__ rhs,
+                                                         double* __restrict__ part, DFConst c) {
+  constexpr int NT = kTgt * G;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* kbh = reinterpret_cast<float4*>(smem);           // [kCh][kTgt]: (K2, K1, K4, K3) ds, hi parts
+  float4* kbl = kbh + kCh * kTgt;                           // lo parts
+  float4* ush = kbl + kCh * kTgt;                           // [16 G][kCh]: (phi.hi, phi.lo, psi.hi, psi.lo)
+  float4* srec = ush + kGB * G * kCh;                       // [kCh][4]: x, n split as below
+  df* tab = reinterpret_cast<df*>(srec + kCh * 4);          // 2^(j/32)
+  const int tid = threadIdx.x;
+  const int g = tid / kTgt, tl = tid % kTgt;  // MAC phase: group g (warp-uniform), target tl
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, s0 = item.y, s1 = item.z, split = item.w;
   if (tid < 32) tab[tid] = df_from_double(exp2((double)tid / 32.0));
@@ -53,47 +67,56 @@ __global__ void __launch_bounds__(kNT, 1) k_mrhs_df(int n, int nb, int n_splits,
 
   for (int j0 = s0; j0 < s1; j0 += kCh) {
     const int cnt = min(kCh, s1 - j0);
-    __syncthreads();
+    __syncthreads();  // the previous chunk's blocks and values have been used
     if (tid < cnt) {
       const double4_32a gj = tgt64[2 * (j0 + tid)], vj = tgt64[2 * (j0 + tid) + 1];
       const df x0 = df_from_double(gj.x), x1 = df_from_double(gj.y), x2 = df_from_double(gj.z);
       const df n0 = df_from_double(vj.x), n1 = df_from_double(vj.y), n2 = df_from_double(vj.z);
       const df a = df_from_double(gj.w);
-      srec[tid][0] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
-      srec[tid][1] = make_float4(x0.lo, x1.lo, x2.lo, a.lo);
-      srec[tid][2] = make_float4(n0.hi, n1.hi, n2.hi, 0.f);
-      srec[tid][3] = make_float4(n0.lo, n1.lo, n2.lo, 0.f);
+      srec[4 * tid] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
+      srec[4 * tid + 1] = make_float4(x0.lo, x1.lo, x2.lo, a.lo);
+      srec[4 * tid + 2] = make_float4(n0.hi, n1.hi, n2.hi, 0.f);
+      srec[4 * tid + 3] = make_float4(n0.lo, n1.lo, n2.lo, 0.f);
     }
-    // right-hand-side values: e = (b * 2 + comp) * cnt + q (q fastest: coalesced reads)
-    for (int e = tid; e < kNB * 2 * cnt; e += kNT) {
+    // right-hand-side values, e = (b * 2 + comp) * cnt + q (q fastest: coalesced reads,
+    // consecutive shared-memory words)
+    for (int e = tid; e < kGB * G * 2 * cnt; e += NT) {
       const int q = e % cnt, bc = e / cnt, b = bc >> 1, comp = bc & 1;
-      const double v = b < nb ? u[(int64_t)b * 2 * n + (int64_t)comp * n + j0 + q] : 0.0;
+      const double v = b < nb ? u[(int64_t)(rhs ? rhs[b] : b) * 2 * n + (int64_t)comp * n + j0 + q] : 0.0;
       const df d = df_from_double(v);
-      float* dst = reinterpret_cast<float*>(&ush[q][b]) + 2 * comp;
+      float* dst = reinterpret_cast<float*>(&ush[b * kCh + q]) + 2 * comp;
       dst[0] = d.hi;
       dst[1] = d.lo;
     }
     __syncthreads();
-    for (int q = 0; q < cnt; ++q) {
-      const float4 A = srec[q][0], B = srec[q][1], C = srec[q][2], D = srec[q][3];
+    // kernel blocks of (target tl, source q) for q = g, g + G, ...
+    for (int q = g; q < cnt; q += G) {
+      const float4 A = srec[4 * q], B = srec[4 * q + 1], C = srec[4 * q + 2], D = srec[4 * q + 3];
       const df xj[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
       const df nj[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
       df k[4];
       df_kernel_block<true>(xi, ni, xj, nj, df{A.w, B.w}, !tvalid || j0 + q == ti, c, tab, k);
+      kbh[q * kTgt + tl] = make_float4(k[0].hi, k[1].hi, k[2].hi, k[3].hi);
+      kbl[q * kTgt + tl] = make_float4(k[0].lo, k[1].lo, k[2].lo, k[3].lo);
+    }
+    __syncthreads();
+    for (int q = 0; q < cnt; ++q) {
+      const float4 H = kbh[q * kTgt + tl], Lo = kbl[q * kTgt + tl];
+      const df k0 = df{H.x, Lo.x}, k1 = df{H.y, Lo.y}, k2 = df{H.z, Lo.z}, k3 = df{H.w, Lo.w};
 #pragma unroll
       for (int b = 0; b < kGB; ++b) {
-        const float4 uv = ush[q][kGB * g + b];
+        const float4 uv = ush[(kGB * g + b) * kCh + q];
         const df up = df{uv.x, uv.y}, uq = df{uv.z, uv.w};
-        df_mac(accp[b], k[0], up);
-        df_mac(accp[b], k[1], uq);
-        df_mac(accq[b], k[2], up);
-        df_mac(accq[b], k[3], uq);
+        df_mac(accp[b], k0, up);
+        df_mac(accp[b], k1, uq);
+        df_mac(accq[b], k2, up);
+        df_mac(accq[b], k3, uq);
       }
     }
 #pragma unroll
     for (int b = 0; b < kGB; ++b) {
-      accp[b] = fast_two_sum(accp[b].hi, accp[b].lo);
-      accq[b] = fast_two_sum(accq[b].hi, accq[b].lo);
+      accp[b] = two_sum(accp[b].hi, accp[b].lo);
+      accq[b] = two_sum(accq[b].hi, accq[b].lo);
     }
   }
   if (!tvalid) return;
@@ -107,16 +130,24 @@ __global__ void __launch_bounds__(kNT, 1) k_mrhs_df(int n, int nb, int n_splits,
   }
 }
 
-}  // namespace
+template <int G>
+int mrhs_df_occupancy() {
+  static int occ = [] {
+    int o = 0;
+    if (cudaFuncSetAttribute(k_mrhs_df<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<G>()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_mrhs_df<G>, kTgt * G, smem_bytes<G>()) != cudaSuccess) {
+      (void)cudaGetLastError();
+      o = 1;
+    }
+    return std::max(o, 1);
+  }();
+  return occ;
+}
 
-void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
-                    double dpsi, const int* skip, int skip_stride) {
-  const int n = L.n[0];
-  for (int k = 0; k < L.K; ++k)
-    BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == n && L.vec_off[k] == 2 * n * k,
-                 "the multi-RHS double-float mat-vec needs right-hand sides of one surface");
+// Work list of one group count: target tiles x source splits filling whole waves.
+ItemPlan* mrhs_df_plan(Surface* s, int n, int G, int slots, int* S_out) {
   const int tiles = (n + kTgt - 1) / kTgt;
-  const int slots = s->num_sms;  // one CTA per SM (register bound)
   int S = 1;
   double best = 0.0;
   for (int sp = 1; sp <= std::min(12, std::max(1, n / (4 * kCh))); ++sp) {
@@ -124,7 +155,8 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
     const double eff = (double)ctas / ((double)waves * slots);
     if (eff > best * 1.02) best = eff, S = sp;
   }
-  const uint64_t key = 0x7e0000000000ull ^ ((uint64_t)n << 8) ^ (uint64_t)S;
+  *S_out = S;
+  const uint64_t key = 0x7e0000000000ull ^ ((uint64_t)n << 12) ^ ((uint64_t)G << 8) ^ (uint64_t)S;
   auto it = s->plans.find(key);
   if (it == s->plans.end()) {
     auto p = std::make_unique<ItemPlan>();
@@ -140,12 +172,54 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
     ++s->alloc_gen;
     it = s->plans.emplace(key, std::move(p)).first;
   }
-  ItemPlan* plan = it->second.get();
-  s->grow(s->part64, (size_t)std::min(L.K, kNB) * S * 2 * n);
-  for (int b0 = 0; b0 < L.K; b0 += kNB) {
-    const int nb = std::min(kNB, L.K - b0);
-    std::vector<int> go(nb, 0), nn(nb, n), co(nb, 0), nc(nb, 0);
-    SysLayout Lb = make_layout(go, nn, co, nc);
+  return it->second.get();
+}
+
+}  // namespace
+
+void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
+                    double dpsi, const int* skip, int skip_stride) {
+  const int n = L.n[0];
+  for (int k = 0; k < L.K; ++k)
+    BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == n && L.vec_off[k] == 2 * n * k,
+                 "the multi-RHS double-float mat-vec needs right-hand sides of one surface");
+  // right-hand sides to compute: all, or those whose skip flag is clear (the
+  // refinement residual of a batch in which some systems have converged)
+  std::vector<int> act;
+  if (skip != nullptr) {
+    std::vector<int> flags((size_t)(L.K - 1) * skip_stride + 1);
+    BIPB_CUDA(cudaMemcpyAsync(flags.data(), skip, flags.size() * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < L.K; ++k)
+      if (flags[(size_t)k * skip_stride] == 0) act.push_back(k);
+  } else {
+    for (int k = 0; k < L.K; ++k) act.push_back(k);
+  }
+  const int n_act = (int)act.size();
+  for (int g0 = 0; g0 < n_act; g0 += kNB) {
+    const int nb = std::min(kNB, n_act - g0);
+    const int G = nb <= kGB ? 1 : (nb <= 2 * kGB ? 2 : 4);
+    const int slots = s->num_sms * (G == 1 ? mrhs_df_occupancy<1>() : G == 2 ? mrhs_df_occupancy<2>()
+                                                                             : mrhs_df_occupancy<4>());
+    int S = 1;
+    ItemPlan* plan = mrhs_df_plan(s, n, G, slots, &S);
+    s->grow(s->part64, (size_t)nb * S * 2 * n);
+    // reduction layout: right-hand side b of this group at vec_off = act[g0 + b] * 2n of u and y
+    SysLayout Lb;
+    Lb.K = nb;
+    Lb.geo_off.assign(nb, 0);
+    Lb.n.assign(nb, n);
+    Lb.chg_off.assign(nb, 0);
+    Lb.nc.assign(nb, 0);
+    Lb.vec_off.resize(nb);
+    uint64_t h = 0x6d72687364660000ull ^ (uint64_t)n;
+    for (int b = 0; b < nb; ++b) {
+      Lb.vec_off[b] = act[g0 + b] * 2 * n;
+      h = (h ^ (uint64_t)Lb.vec_off[b]) * 0x100000001b3ull;
+    }
+    Lb.len = (int64_t)nb * 2 * n;
+    Lb.max_n = n;
+    Lb.key = h;
     const uint64_t tkey = 0x7f0000000000ull ^ ((uint64_t)n << 16) ^ ((uint64_t)S << 8) ^ (uint64_t)nb;
     auto tt = s->plans.find(tkey);
     if (tt == s->plans.end()) {
@@ -158,15 +232,36 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
       ++s->alloc_gen;
       tt = s->plans.emplace(tkey, std::move(p)).first;
     }
-    const double* ub = u + (int64_t)b0 * 2 * n;
-    double* yb = y + (int64_t)b0 * 2 * n;
+    const int* rhs = nullptr;
+    const double* ub = u + (int64_t)act[g0] * 2 * n;
+    if (act[g0 + nb - 1] - act[g0] != nb - 1) {  // not contiguous: pass the indices
+      s->grow(s->rhs_idx, (size_t)nb);
+      BIPB_CUDA(cudaMemcpyAsync(s->rhs_idx.p, act.data() + g0, nb * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+      BIPB_CUDA(cudaStreamSynchronize(s->stream));
+      rhs = s->rhs_idx.p;
+      ub = u;
+    }
+    // the 4-group kernel needs more than the default 48 KB of dynamic shared memory
+    if (G == 1)
+      BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>()));
+    else if (G == 2)
+      BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>()));
+    else
+      BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<4>()));
     {
       TimedLaunch tl(s, kTMvDF);
-      k_mrhs_df<<<plan->n_items, kNT, 0, s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p, ub, s->part64.p, c);
+      if (G == 1)
+        k_mrhs_df<1><<<plan->n_items, kTgt, smem_bytes<1>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p, ub,
+                                                                          rhs, s->part64.p, c);
+      else if (G == 2)
+        k_mrhs_df<2><<<plan->n_items, 2 * kTgt, smem_bytes<2>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p,
+                                                                              ub, rhs, s->part64.p, c);
+      else
+        k_mrhs_df<4><<<plan->n_items, 4 * kTgt, smem_bytes<4>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p,
+                                                                              ub, rhs, s->part64.p, c);
       BIPB_LAUNCHED(s);
     }
-    launch_reduce_matvec64(s, Lb, tt->second->tab.p, s->part64.p, ub, yb, dphi, dpsi,
-                           skip ? skip + (int64_t)b0 * skip_stride : nullptr, skip_stride);
+    launch_reduce_matvec64(s, Lb, tt->second->tab.p, s->part64.p, u, y, dphi, dpsi, nullptr, 0);
   }
 }
 

@@ -196,6 +196,30 @@ def test_multiple_charge_sets_match_single_solves(bipb):
             np.testing.assert_allclose(s.surface_potential()[0][0], phi_all[r], rtol=1e-8, atol=1e-9)
 
 
+def test_batched_mixed_df64_with_idle_systems(bipb):
+    """20 charge sets solved together in MIXED_DF64; sets 3 and 7 carry no
+    charge, so they are idle from the start and the batched double-float
+    residual runs over a non-contiguous subset of the right-hand sides."""
+    base = synth.protein_like_problem(level=3, n_charges=20)
+    batch = synth.batched_charges(base, n_rhs=20, n_charges=20)
+    q = batch.q.copy()
+    q[3] = 0.0
+    q[7] = 0.0
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.set_charges(batch.charge_pos, q)
+        info = s.solve(tol=1e-10, precision=bipb.MIXED_DF64)
+        assert all(i["converged"] for i in info)
+        e_all = s.energy()
+        phi_all, _ = s.surface_potential()
+        assert e_all[3] == 0.0 and e_all[7] == 0.0
+        assert not phi_all[3].any() and not phi_all[7].any()
+        for r in (0, 8, 19):
+            s.set_charges(batch.charge_pos[r], q[r])
+            s.solve(tol=1e-10, precision=bipb.MIXED_DF64)
+            assert s.energy()[0] == pytest.approx(e_all[r], rel=1e-8)
+            np.testing.assert_allclose(s.surface_potential()[0][0], phi_all[r], rtol=1e-7, atol=1e-8)
+
+
 def test_gradient_matches_oracle_adjoint(bipb, orc):
     p = synth.kirkwood_problem(level=3, radius=10.0, n_charges=6, charge_radius=7.0)
     e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="direct")
