@@ -75,7 +75,8 @@ def parse():
                     help="FP32 mat-vec variant (default: autotuned; --mode matvec32: the handle's default)")
     ap.add_argument("--ordered-pairs", action="store_true",
                     help="FP64 / double-float mat-vecs visit every ordered pair (default: unordered pairs once)")
-    ap.add_argument("--configs", default="3,4a,4b,5", help="--mode configs: which larger configurations")
+    ap.add_argument("--configs", default="3,4a,4b,5",
+                    help="--mode configs: which larger configurations (5fd: the full-size central-difference check)")
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "configs"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
@@ -354,7 +355,79 @@ def run_configs(args):
             emit({"config": "adjoint: displaced icosphere level 7 (N=327680), R=45, 10000 charges",
                   "solve_ms_mixed_df64": ms_f, "energy_grad_ms": ms_g, "info": info[0],
                   "energy_kcal": float(s.energy()[0]), "max_abs_force": float(np.abs(dy).max())})
+    if "5fd" in which:
+        emit(config5_central_differences(bipb, torch))
     return out
+
+
+def config5_central_differences(bipb, torch):
+    """Full-size check of the adjoint gradient on 32 seeded atoms (level 7).
+
+    Moving charge k by +-h e_d changes only its own term of the source b and
+    of the energy row c, so E(y +- h e_d) - E(y) = 1/2 [dc.u + c.du + dc.du]
+    with A du = db, where db and dc are the source and energy row of the
+    charge pair {(y_k +- h e_d, q_k), (y_k, -q_k)}.  The 192 pair systems are
+    solved together (TF32 Krylov + double-float residual, tol 1e-9), and each
+    term is a reaction-energy pass: no difference of two large energies is
+    taken.  dE/dq_k (E is quadratic in q, so central differences are exact)
+    = 1/2 (c_k.u + c.u_k) with u_k the solution for a unit charge at y_k.
+    """
+    import synth
+
+    p = synth.adjoint_problem()
+    n, y, q = p.n, p.charge_pos, p.q[0]
+    med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
+    atoms = np.sort(np.random.default_rng(7).choice(p.nc, 32, replace=False))
+    h = 1e-4
+    res = {"config": "adjoint gradient vs central differences: level 7 (N=327680), 10000 charges, 32 seeded "
+                      "atoms, h=1e-4 A (solution differences)"}
+    t0 = time.perf_counter()
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(y, q)
+        base = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=1e-10, precision=bipb.MIXED_DF64)
+        s.solve(base)
+        phi, dphi = s.surface_potential()
+        u0 = np.concatenate([phi[0], dphi[0]]) / bipb.KCAL
+        dq, dy = s.energy_grad(base)
+        pos_sets, q_sets = [], []
+        for k in atoms:
+            for d in range(3):
+                for sg in (1.0, -1.0):
+                    yp = y[k].copy()
+                    yp[d] += sg * h
+                    pos_sets.append([yp, y[k]])
+                    q_sets.append([q[k], -q[k]])
+        for k in atoms:  # unit charge at y_k (the second charge is empty)
+            pos_sets.append([y[k], y[k]])
+            q_sets.append([1.0, 0.0])
+        B = len(q_sets)
+        s.set_charges(np.array(pos_sets), np.array(q_sets))
+        prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=1e-9, precision=bipb.MIXED_TF32)
+        ms, info = _timed(lambda: s.solve(prm), torch)
+        res["pair_solves"] = {"systems": B, "ms": ms, "converged": int(sum(i["converged"] for i in info)),
+                              "rel_residual_max": max(i["rel_residual"] for i in info)}
+        phi, dphi = s.surface_potential()
+        du = torch.tensor(np.concatenate([phi, dphi], axis=1) / bipb.KCAL, dtype=torch.float64, device="cuda")
+        del phi, dphi
+        e_b = torch.empty(B, dtype=torch.float64, device="cuda")
+        s.reaction(du, None, e_b, med)  # 1/2 dc.du
+        e_a = torch.empty_like(e_b)
+        s.reaction(torch.tensor(u0, device="cuda").repeat(B, 1), None, e_a, med)  # 1/2 dc.u
+        s.set_charges(y[None], np.repeat(q[None], B, axis=0))
+        e_c = torch.empty_like(e_b)
+        s.reaction(du, None, e_c, med)  # 1/2 c.du
+    D = (e_a + e_b + e_c).cpu().numpy()
+    g_fd = ((D[0:192:2] - D[1:192:2]) / (2 * h)).reshape(32, 3)
+    g_adj = dy[0][atoms]
+    dq_fd = (e_a + e_c).cpu().numpy()[192:]
+    dq_adj = dq[0][atoms]
+    res["dE_dy_max_rel_err"] = float(np.abs(g_fd - g_adj).max() / np.abs(g_adj).max())
+    res["dE_dy_per_atom_rel_err_max"] = float(
+        (np.linalg.norm(g_fd - g_adj, axis=1) / np.linalg.norm(g_adj, axis=1)).max())
+    res["dE_dq_max_rel_err"] = float(np.abs(dq_fd - dq_adj).max() / np.abs(dq_adj).max())
+    res["max_abs_force"] = float(np.abs(g_adj).max())
+    res["seconds_total"] = time.perf_counter() - t0
+    return res
 
 
 def main():

@@ -470,6 +470,58 @@ def test_adjoint_config_level4_copy_matches_oracle(bipb, orc):
         np.testing.assert_allclose(dym[0][atoms], dy_ref[atoms], rtol=1e-5, atol=1e-7 * np.abs(dy_ref).max())
 
 
+def test_central_differences_by_solution_differences(bipb, orc):
+    """Central differences (h = 1e-4 A) of E in the positions and charges of 6
+    atoms, formed from solution differences: moving charge k changes only its
+    own source and energy-row terms, so E(y_k +- h e_d) - E = 1/2 [dc.u +
+    c.du + dc.du] with A du = db for the charge pair {(y_k +- h e_d, q_k),
+    (y_k, -q_k)}, each term a reaction-energy pass on the GPU.  The result is
+    compared with the GPU adjoint gradient and with the oracle's."""
+    p = synth.adjoint_problem(level=3, n_charges=200)
+    e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="direct")
+    n, y, q = p.n, p.charge_pos, p.q[0]
+    med = _med(bipb, p)
+    atoms = np.sort(np.random.default_rng(9).choice(p.nc, 6, replace=False))
+    h = 1e-4
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(y, q)
+        s.solve(tol=1e-12, precision=bipb.FP64)
+        phi, dphi = s.surface_potential()
+        u0 = np.concatenate([phi[0], dphi[0]]) / bipb.KCAL
+        dq, dy = s.energy_grad(tol=1e-12, precision=bipb.FP64)
+        pos_sets, q_sets = [], []
+        for k in atoms:
+            for d in range(3):
+                for sg in (1.0, -1.0):
+                    yp = y[k].copy()
+                    yp[d] += sg * h
+                    pos_sets.append([yp, y[k]])
+                    q_sets.append([q[k], -q[k]])
+        for k in atoms:
+            pos_sets.append([y[k], y[k]])
+            q_sets.append([1.0, 0.0])
+        B = len(q_sets)
+        s.set_charges(np.array(pos_sets), np.array(q_sets))
+        info = s.solve(tol=1e-12, precision=bipb.MIXED_DF64)
+        assert all(i["converged"] for i in info)
+        phi, dphi = s.surface_potential()
+        du = _dev(np.concatenate([phi, dphi], axis=1) / bipb.KCAL)
+        e_a, e_b, e_c = (torch.empty(B, dtype=torch.float64, device="cuda") for _ in range(3))
+        s.reaction(_dev(np.tile(u0, (B, 1))), None, e_a, med)
+        s.reaction(du, None, e_b, med)
+        s.set_charges(y[None], np.repeat(q[None], B, axis=0))
+        s.reaction(du, None, e_c, med)
+    m = len(atoms) * 6
+    D = (e_a + e_b + e_c).cpu().numpy()
+    g_fd = ((D[0:m:2] - D[1:m:2]) / (2 * h)).reshape(len(atoms), 3)
+    dq_fd = (e_a + e_c).cpu().numpy()[m:]
+    scale = np.abs(dy_ref[atoms]).max()
+    np.testing.assert_allclose(g_fd, dy[0][atoms], rtol=0, atol=1e-5 * scale)
+    np.testing.assert_allclose(g_fd, dy_ref[atoms], rtol=0, atol=1e-5 * scale)
+    np.testing.assert_allclose(dq_fd, dq[0][atoms], rtol=1e-9)
+    np.testing.assert_allclose(dq_fd, dq_ref[atoms], rtol=1e-9)
+
+
 @pytest.mark.parametrize("n_rhs", [5, 70])
 def test_multi_rhs_df64_matvec_matches_oracle(bipb, orc, n_rhs):
     """The batched double-float mat-vec (kernel block shared by 16 right-hand sides)."""
