@@ -68,43 +68,67 @@ __device__ double block_sum(double v) {
 // sysb[k] = {first block, end block, 0, 0}.  Every block covers one
 // contiguous range of one system's unknowns.
 
-// part[b * m1 + i] = V_i . w over block b's range, i <= j
+// Sum of v over a warp in a fixed order (tree of shuffles down), then
+// broadcast from lane 0, so every lane holds the same, reproducible value.
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// sum over blocks b in [b0, b1) of part[b * stride + i], by one warp, fixed order
+__device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part, int stride, int i, int b0, int b1) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b = b0 + lane; b < b1; b += 32) s += part[(size_t)b * stride + i];
+  return warp_sum(s);
+}
+
+// part[b * m1 + i] = V_i . w over block b's range, i <= j (warp i % 8 takes vector i)
 __global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V, const double* __restrict__ w,
                        double* __restrict__ part, const DevState* st, const int4* __restrict__ blk) {
   const int4 B = blk[blockIdx.x];
   if (st[B.x].skip) return;
-  for (int i = 0; i <= j; ++i) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j; i += kBS / 32) {
     const double* v = V + (size_t)i * len;
     double acc = 0.0;
-    for (int x = B.y + threadIdx.x; x < B.z; x += kBS) acc += v[x] * w[x];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * m1 + i] = acc;
+    for (int x = B.y + lane; x < B.z; x += 32) acc += v[x] * w[x];
+    acc = warp_sum(acc);
+    if (lane == 0) part[(size_t)blockIdx.x * m1 + i] = acc;
   }
 }
 
-// h_i = sum over the system's blocks of part[.][i]; w -= sum_i h_i V_i; H[:, j] (+)= h
+// h_i = sum over the system's blocks of part[.][i]; w -= sum_i h_i V_i; H[:, j] (+)= h;
+// with want_norm, also part1[b] = sum of the updated w^2 over block b's range.
 __global__ void k_orth(int j, int m, int64_t len, const double* __restrict__ V, double* __restrict__ w,
                        const double* __restrict__ part, double* __restrict__ H, int accumulate, const DevState* st,
-                       const int4* __restrict__ blk, const int4* __restrict__ sysb) {
+                       const int4* __restrict__ blk, const int4* __restrict__ sysb, double* __restrict__ part1,
+                       int want_norm) {
   const int4 B = blk[blockIdx.x];
   if (st[B.x].skip) return;
   const int m1 = m + 1;
   const int4 S = sysb[B.x];
   __shared__ double h[kMaxRestart + 1];
-  for (int i = threadIdx.x; i <= j; i += kBS) {
-    double s = 0.0;
-    for (int b = S.x; b < S.y; ++b) s += part[(size_t)b * m1 + i];
-    h[i] = s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j; i += kBS / 32) {
+    const double v = warp_sum_parts(part, m1, i, S.x, S.y);
+    if (lane == 0) h[i] = v;
   }
   __syncthreads();
   if ((int)blockIdx.x == S.x) {
     double* Hs = H + (size_t)B.x * m1 * m + (size_t)j * m1;
     for (int i = threadIdx.x; i <= j; i += kBS) Hs[i] = accumulate ? Hs[i] + h[i] : h[i];
   }
+  double ss = 0.0;
   for (int x = B.y + threadIdx.x; x < B.z; x += kBS) {
     double acc = w[x];
     for (int i = 0; i <= j; ++i) acc -= h[i] * V[(size_t)i * len + x];
     w[x] = acc;
+    ss += acc * acc;
+  }
+  if (want_norm) {
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) part1[blockIdx.x] = ss;
   }
 }
 
@@ -129,10 +153,9 @@ __global__ void k_normalize(int j, int m, const double* __restrict__ w, double* 
   if (j >= 0 ? st[B.x].skip : !st[B.x].active) return;
   const int4 S = sysb[B.x];
   __shared__ double nrm;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int b = S.x; b < S.y; ++b) s += part1[b];
-    nrm = sqrt(s);
+  if (threadIdx.x < 32) {
+    const double s = warp_sum_parts(part1, 1, 0, S.x, S.y);
+    if (threadIdx.x == 0) nrm = sqrt(s);
   }
   __syncthreads();
   const double v = nrm;
@@ -324,12 +347,13 @@ GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
   w->m = m;
   w->K = L.K;
   w->len = L.len;
-  // blocks: each covers one contiguous range (about 1024 unknowns) of one system
+  // blocks: each covers one contiguous range (about 256 unknowns, at most
+  // 1024 blocks per system) of one system
   std::vector<int4> blk;
   std::vector<int4> sysb(L.K);
   for (int k = 0; k < L.K; ++k) {
     const int64_t lk = 2 * (int64_t)L.n[k];
-    const int nb = (int)std::min<int64_t>(512, std::max<int64_t>(1, (lk + 1023) / 1024));
+    const int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (lk + 255) / 256));
     const int64_t chunk = (lk + nb - 1) / nb;
     sysb[k] = make_int4((int)blk.size(), (int)blk.size() + nb, 0, 0);
     for (int b = 0; b < nb; ++b) {
@@ -376,15 +400,13 @@ void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium
   for (int j = 0; j < m; ++j) {
     double* vj = w->V.p + (size_t)j * len;
     matvec(s, L, med, precision, transpose, vj, w->w.p, &w->st->skip, kStateInts);
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 2; ++pass) {  // CGS2; the second pass also forms the block norms
       k_dots<<<nb, kBS, 0, s->stream>>>(j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
       BIPB_LAUNCHED(s);
       k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, pass, w->st, w->blk.p,
-                                        w->sysb.p);
+                                        w->sysb.p, w->part1.p, pass);
       BIPB_LAUNCHED(s);
     }
-    k_sumsq<<<nb, kBS, 0, s->stream>>>(w->w.p, w->part1.p, w->st, w->blk.p, 0);
-    BIPB_LAUNCHED(s);
     k_normalize<<<nb, kBS, 0, s->stream>>>(j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
                                            0);
     BIPB_LAUNCHED(s);
