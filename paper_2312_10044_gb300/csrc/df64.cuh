@@ -264,70 +264,42 @@ __device__ __forceinline__ void df_mac(df& acc, df a, df b) {
 
 namespace bipb {
 
-// Symmetric pair terms in df64 (the radial part shared by both directions of
-// an unordered pair; see SymTerms in pair.cuh).
-// ka = (eps t - 1) s^2 and kb = t/eps - 1 for A u; ka = eps t - 1 and
-// kb = (t/eps - 1) s^2 for A^T w (the factor s^2 goes where the formula has it).
-struct DFTerms {
-  df s, s3, ome, tm1, ka, kb, wm3s2;  // wm3s2 = (w - 3) s^2
-};
-
+// The symmetric pair of pair.cuh (sym_pair) in df64.  The four accumulators
+// are updated lazily (df_mac): renormalise them before use.
 template <bool MASK, bool TRANS>
-__device__ __forceinline__ DFTerms df_sym_terms(df dx, df dy, df dz, bool self, const DFConst& c, const df* tab) {
-  DFTerms R;
-  const df r2 = df_sumsq3(dx, dy, dz);
-  R.s = df_rsqrt(r2);
-  if (MASK && self) R.s = df{0.0f, 0.0f};
-  const df r = df_mul(r2, R.s);
-  const df kr = df_mul(r, c.kappa);
+__device__ __forceinline__ void df_sym_pair(const df* d, const df* nt, df at, df alt, const df* ns, df as, df als,
+                                            bool self, const DFConst& c, const df* tab, df& Pt, df& Qt, df& Ps,
+                                            df& Qs) {
+  const df r2 = df_sumsq3(d[0], d[1], d[2]);
+  df s = df_rsqrt(r2);
+  if (MASK && self) s = df{0.0f, 0.0f};
+  const df kr = df_mul(df_mul(r2, s), c.kappa);
   const df e = df_exp_neg(df_neg(kr), c, tab);
   const df ekr = df_mul(e, kr);
   const df t = df_add(ekr, e);
-  R.tm1 = df_add_f(t, -1.0f);
-  const df wm3 = df_add(df_mul(ekr, kr), df_mul_f(R.tm1, 3.0f));  // 3 (t - 1) + e (kappa r)^2
-  R.ome = df_add_f(df_neg(e), 1.0f);
-  const df s2 = df_sqr(R.s);
-  R.s3 = df_mul(s2, R.s);
+  const df tm1 = df_add_f(t, -1.0f);
+  const df s2 = df_sqr(s);
+  const df s3 = df_mul(s2, s);
+  const df wm3s2 = df_mul(df_add(df_mul(ekr, kr), df_mul_f(tm1, 3.0f)), s2);
+  const df ome = df_add_f(df_neg(e), 1.0f);
   const df et1 = df_add_f(df_mul(c.eps, t), -1.0f), te1 = df_add_f(df_mul(t, c.inveps), -1.0f);
-  R.ka = TRANS ? et1 : df_mul(et1, s2);
-  R.kb = TRANS ? df_mul(te1, s2) : te1;
-  R.wm3s2 = df_mul(wm3, s2);
-  return R;
-}
-
-__device__ __forceinline__ df df_signed(df x, int sign) { return sign > 0 ? x : df_neg(x); }
-
-// Forward direction in df64 (sym_forward in pair.cuh); R from df_sym_terms<MASK, false>.
-// The accumulators are updated lazily (df_mac): renormalise them before use.
-template <int SIGN>
-__device__ __forceinline__ void df_sym_forward(const DFTerms& R, const df* d, const df* nt, df a, const df* m,
-                                               df& accP, df& accQ) {
   const df ci = df_dot3(nt[0], nt[1], nt[2], d[0], d[1], d[2]);
-  const df cm = df_dot3(m[0], m[1], m[2], d[0], d[1], d[2]);
-  const df cim = df_dot3(nt[0], nt[1], nt[2], m[0], m[1], m[2]);
-  df p = df_mul(R.ome, a);
-  p = df_add(p, df_mul(df_signed(R.ka, SIGN), cm));
-  df_mac(accP, p, R.s);
-  df q = df_mul(df_mul(df_signed(R.kb, SIGN), ci), a);
-  q = df_add(q, df_mul(R.tm1, cim));
-  q = df_sub(q, df_mul(R.wm3s2, df_mul(ci, cm)));
-  df_mac(accQ, q, R.s3);
-}
-
-// Transposed direction in df64 (sym_transpose in pair.cuh); R from df_sym_terms<MASK, true>.
-template <int SIGN>
-__device__ __forceinline__ void df_sym_transpose(const DFTerms& R, const df* d, const df* no, df wphi, const df* pv,
-                                                 df& accP, df& accQ) {
-  const df cj = df_dot3(no[0], no[1], no[2], d[0], d[1], d[2]);
-  const df cp = df_dot3(pv[0], pv[1], pv[2], d[0], d[1], d[2]);
-  const df cnp = df_dot3(no[0], no[1], no[2], pv[0], pv[1], pv[2]);
-  df q = df_mul(df_mul(df_signed(R.ka, SIGN), cj), wphi);
-  q = df_add(q, df_mul(R.tm1, cnp));
-  q = df_sub(q, df_mul(R.wm3s2, df_mul(cp, cj)));
-  df_mac(accP, q, R.s3);
-  df p = df_mul(R.ome, wphi);
-  p = df_add(p, df_mul(df_signed(R.kb, SIGN), cp));
-  df_mac(accQ, p, R.s);
+  const df cj = df_dot3(ns[0], ns[1], ns[2], d[0], d[1], d[2]);
+  const df cij = df_dot3(nt[0], nt[1], nt[2], ns[0], ns[1], ns[2]);
+  const df U = df_sub(df_mul(tm1, cij), df_mul(wm3s2, df_mul(ci, cj)));
+  if (!TRANS) {
+    const df ka = df_mul(et1, s2);
+    df_mac(Pt, df_add(df_mul(df_mul(ka, cj), als), df_mul(ome, as)), s);
+    df_mac(Qt, df_add(df_mul(als, U), df_mul(df_mul(te1, ci), as)), s3);
+    df_mac(Ps, df_sub(df_mul(ome, at), df_mul(df_mul(ka, ci), alt)), s);
+    df_mac(Qs, df_sub(df_mul(alt, U), df_mul(df_mul(te1, cj), at)), s3);
+  } else {
+    const df kb = df_mul(te1, s2);
+    df_mac(Pt, df_sub(df_mul(als, U), df_mul(df_mul(et1, ci), as)), s3);
+    df_mac(Qt, df_sub(df_mul(ome, as), df_mul(df_mul(kb, cj), als)), s);
+    df_mac(Ps, df_add(df_mul(alt, U), df_mul(df_mul(et1, cj), at)), s3);
+    df_mac(Qs, df_add(df_mul(ome, at), df_mul(df_mul(kb, ci), alt)), s);
+  }
 }
 
 }  // namespace bipb

@@ -90,7 +90,7 @@ struct ItemPlan {
 // sources per shared-memory chunk): every ordered pair: 0 (256,2,128)
 // 1 (256,1,128) 2 (128,2,128) 3 (256,4,128) 4 (128,4,64) 5 (512,1,128)
 // 6 (256,2,64); every unordered pair once (sym.cu): 7 (256,2,64)
-// 8 (128,4,64) 9 (256,4,64).
+// 8 (128,4,64) 9 (256,4,64, two CTAs per SM).
 constexpr int kNumMv32Variants = 10;
 constexpr int kFirstSymVariant = 7;
 
@@ -203,7 +203,7 @@ struct Surface {
   bool have_solution = false;
   bipb_medium solved_medium{0, 0, 0};
 
-  int mv32_variant = kFirstSymVariant + 2;  // FP32 mat-vec variant (the autotuner may change it)
+  int mv32_variant = kFirstSymVariant;  // FP32 mat-vec variant (the autotuner may change it)
   bool sym_pairs = true;  // FP64 / double-float mat-vecs visit unordered pairs once (sym.cu)
   GmresWork* gw = nullptr;
   KernelTimer timer;

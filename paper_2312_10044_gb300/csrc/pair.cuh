@@ -135,75 +135,55 @@ __device__ __forceinline__ void pair_transpose(T xj, T yj, T zj, T nxj, T nyj, T
 
 // ------------------------------------------------------------------ symmetric pairs
 // The four kernels depend on the pair through r, e, t, w (symmetric in i and
-// j) and through c_i, c_j, c_ij and the sign of d (d_ji = -d_ij).  A kernel
-// that visits the unordered pair {i, j} once computes the radial terms once
-// and applies them in both directions: target i gathering source j
-// (sign +1, d = x_i - x_j) and target j gathering source i (sign -1).
-// s = 1/r, s3 = s^3, ome = 1 - e, tm1 = t - 1, wm3s2 = (w - 3) s^2, and
-// ka = (eps t - 1) s^2, kb = t/eps - 1 for A u (TRANS = false), or
-// ka = eps t - 1, kb = (t/eps - 1) s^2 for A^T w (TRANS = true).
-template <typename T>
-struct SymTerms {
-  T s, s3, ome, tm1, ka, kb, wm3s2;
-};
-
+// j) and through c_i = n_i.d, c_j = n_j.d, c_ij = n_i.n_j (d = x_i - x_j, so
+// d_ji = -d).  A kernel that visits the unordered pair {i, j} once computes
+// them once and applies them in both directions.  With each element's record
+// holding its normal, write m = alpha n (alpha = ds phi for A u; for A^T w
+// the record's second field p = beta n with beta = wpsi): then m_j.d =
+// alpha_j c_j, n_i.m_j = alpha_j c_ij, and both directions share
+//   U = (t - 1) c_ij - (w - 3) s^2 c_i c_j.
+// A u (a = ds psi):
+//   P_i += s [ (1 - e) a_j + (eps t - 1) s^2 alpha_j c_j ]
+//   Q_i += s^3 [ (t/eps - 1) c_i a_j + alpha_j U ]
+//   P_j += s [ (1 - e) a_i - (eps t - 1) s^2 alpha_i c_i ]
+//   Q_j += s^3 [ -(t/eps - 1) c_j a_i + alpha_i U ]
+// A^T w (a = wphi; the phi output gathers K2, K4, the psi output K1, K3):
+//   Zphi_i += s^3 [ -(eps t - 1) c_i a_j + beta_j U ]
+//   Zpsi_i += s [ (1 - e) a_j - (t/eps - 1) s^2 beta_j c_j ]
+//   Zphi_j += s^3 [ (eps t - 1) c_j a_i + beta_i U ]
+//   Zpsi_j += s [ (1 - e) a_i + (t/eps - 1) s^2 beta_i c_i ]
+// (t = target i of the thread, s = source j; P/Q the two outputs of each.)
 template <bool MASK, bool TRANS, typename T>
-__device__ __forceinline__ SymTerms<T> sym_terms(T dx, T dy, T dz, bool self, const PairConst<T>& c) {
-  SymTerms<T> R;
-  T r, e;
-  radial<MASK>(dx * dx + dy * dy + dz * dz, self, c, R.s, r, e);
+__device__ __forceinline__ void sym_pair(T dx, T dy, T dz, const T* nt, T at, T alt, const T* ns, T as, T als,
+                                         bool self, const PairConst<T>& c, T& Pt, T& Qt, T& Ps, T& Qs) {
+  T s, r, e;
+  radial<MASK>(dx * dx + dy * dy + dz * dz, self, c, s, r, e);
   const T kr = r * c.kappa;
   const T ekr = e * kr;
   const T t = ekr + e;
-  R.tm1 = t - T(1);
-  const T s2 = R.s * R.s;
-  R.wm3s2 = (ekr * kr + T(3) * R.tm1) * s2;  // w - 3 = 3 (t - 1) + e (kappa r)^2
-  R.ome = T(1) - e;
-  R.s3 = s2 * R.s;
+  const T tm1 = t - T(1);
+  const T s2 = s * s;
+  const T s3 = s2 * s;
+  const T wm3s2 = (ekr * kr + T(3) * tm1) * s2;  // (w - 3) s^2, w - 3 = 3 (t - 1) + e (kappa r)^2
+  const T ome = T(1) - e;
   const T et1 = c.eps * t - T(1), te1 = t * c.inveps - T(1);
-  R.ka = TRANS ? et1 : et1 * s2;
-  R.kb = TRANS ? te1 * s2 : te1;
-  return R;
-}
-
-// Forward direction (R from sym_terms<MASK, false>): target (normal nt) gathers
-// source (a = ds psi, m = ds phi n);
-// SIGN = +1 when d points from the source to the target, -1 otherwise.
-//   P += s [ (1 - e) a + (eps t - 1) (m.d) s^2 ]
-//   Q += s^3 [ (t/eps - 1) (nt.d) a + (t - 1) (nt.m) - (w - 3) (nt.d)(m.d) s^2 ]
-template <int SIGN, typename T>
-__device__ __forceinline__ void sym_forward(const SymTerms<T>& R, T dx, T dy, T dz, T ntx, T nty, T ntz, T a, T mx,
-                                            T my, T mz, T& accP, T& accQ) {
-  const T ci = ntx * dx + nty * dy + ntz * dz;
-  const T cm = mx * dx + my * dy + mz * dz;
-  const T cim = ntx * mx + nty * my + ntz * mz;
-  T p = R.ome * a;
-  p = (T(SIGN) * R.ka) * cm + p;
-  accP = p * R.s + accP;
-  T q = (T(SIGN) * R.kb * ci) * a;
-  q = R.tm1 * cim + q;
-  q = q - R.wm3s2 * (ci * cm);
-  accQ = q * R.s3 + accQ;
-}
-
-// Transposed direction (R from sym_terms<MASK, true>): output element (normal no)
-// gathers element (wphi, p = wpsi n);
-// SIGN = +1 when d points from the output element to the gathered one.
-//   Zphi += s^3 [ (eps t - 1) (no.d) wphi + (t - 1)(no.p) - (w - 3)(p.d)(no.d) s^2 ]
-//   Zpsi += s [ (1 - e) wphi + (t/eps - 1)(p.d) s^2 ]
-template <int SIGN, typename T>
-__device__ __forceinline__ void sym_transpose(const SymTerms<T>& R, T dx, T dy, T dz, T nox, T noy, T noz, T wphi,
-                                              T px, T py, T pz, T& accP, T& accQ) {
-  const T cj = nox * dx + noy * dy + noz * dz;
-  const T cp = px * dx + py * dy + pz * dz;
-  const T cnp = nox * px + noy * py + noz * pz;
-  T q = (T(SIGN) * R.ka * cj) * wphi;
-  q = R.tm1 * cnp + q;
-  q = q - R.wm3s2 * (cp * cj);
-  accP = q * R.s3 + accP;
-  T p = R.ome * wphi;
-  p = (T(SIGN) * R.kb) * cp + p;
-  accQ = p * R.s + accQ;
+  const T ci = nt[0] * dx + nt[1] * dy + nt[2] * dz;
+  const T cj = ns[0] * dx + ns[1] * dy + ns[2] * dz;
+  const T cij = nt[0] * ns[0] + nt[1] * ns[1] + nt[2] * ns[2];
+  const T U = tm1 * cij - wm3s2 * (ci * cj);
+  if (!TRANS) {
+    const T ka = et1 * s2;
+    Pt = ((ka * cj) * als + ome * as) * s + Pt;
+    Qt = (als * U + (te1 * ci) * as) * s3 + Qt;
+    Ps = (ome * at - (ka * ci) * alt) * s + Ps;
+    Qs = (alt * U - (te1 * cj) * at) * s3 + Qs;
+  } else {
+    const T kb = te1 * s2;
+    Pt = (als * U - (et1 * ci) * as) * s3 + Pt;
+    Qt = (ome * as - (kb * cj) * als) * s + Qt;
+    Ps = (alt * U + (et1 * cj) * at) * s3 + Ps;
+    Qs = (ome * at + (kb * ci) * alt) * s + Qs;
+  }
 }
 
 }  // namespace bipb

@@ -8,8 +8,9 @@
 //   target i gathers source j      -> register accumulators (i side)
 //   target j gathers source i      -> summed over the CTA's T targets (j side)
 // In the tile's own diagonal block the pairs with j <= i are masked (1/r = 0).
-// The j side of one source is reduced across the warp by a fixed butterfly
-// and across the warps in a fixed order, so results are bitwise reproducible.
+// The j side of a source is summed over a warp by accumulators that rotate
+// through the lanes, and over the warps in a fixed order, so results are
+// bitwise reproducible.
 //
 // Row I of a system has n - I T sources, so rows shrink down the system.
 // Rows I and nT - 1 - I are folded together (about n + T sources between
@@ -27,6 +28,7 @@
 #include <algorithm>
 #include <cmath>
 #include <queue>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -48,17 +50,17 @@ struct SymV4<double> {
 };
 
 // ------------------------------------------------------------------ policies
-// Record of an element (both roles): position, a, m and the normal, where
-// (a, m) = (ds psi, ds phi n) for A u and (wphi, wpsi n) for A^T w.
+// Record of an element (both roles): position, a, normal, alpha, where
+// (a, alpha) = (ds psi, ds phi) for A u and (wphi, wpsi) for A^T w.
 
 template <typename T, bool TRANS>
 struct SymPolicy {
   using V4 = typename SymV4<T>::type;
   using PT = T;  // partial sums are stored in this type
-  static constexpr int RW = 3;  // (x, a), (m, 0), (n, 0)
+  static constexpr int RW = 2;  // (x, a), (n, alpha)
   static constexpr int UNROLL = sizeof(T) == 4 ? 2 : 1;  // sources in flight per thread
   struct Elem {
-    T x[3], a, m[3], n[3];
+    T x[3], a, n[3], al;
   };
   struct Acc {
     T p, q;
@@ -68,28 +70,28 @@ struct SymPolicy {
   };
   __device__ static void prologue(const Args&) {}
   __device__ static void load(const V4* r, Elem& e) {
-    const V4 A = r[0], B = r[1], C = r[2];
+    const V4 A = r[0], B = r[1];
     e.x[0] = A.x, e.x[1] = A.y, e.x[2] = A.z, e.a = A.w;
-    e.m[0] = B.x, e.m[1] = B.y, e.m[2] = B.z;
-    e.n[0] = C.x, e.n[1] = C.y, e.n[2] = C.z;
+    e.n[0] = B.x, e.n[1] = B.y, e.n[2] = B.z, e.al = B.w;
   }
   __device__ static void zero(Acc& v) { v.p = T(0), v.q = T(0); }
   // i-side of target t and j-side of source sj for the pair d = x_t - x_sj
   template <bool MASK>
   __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
-    const T dx = t.x[0] - sj.x[0], dy = t.x[1] - sj.x[1], dz = t.x[2] - sj.x[2];
-    const SymTerms<T> R = sym_terms<MASK, TRANS>(dx, dy, dz, masked, g.c);
-    if (!TRANS) {
-      sym_forward<1>(R, dx, dy, dz, t.n[0], t.n[1], t.n[2], sj.a, sj.m[0], sj.m[1], sj.m[2], ti.p, ti.q);
-      sym_forward<-1>(R, dx, dy, dz, sj.n[0], sj.n[1], sj.n[2], t.a, t.m[0], t.m[1], t.m[2], tj.p, tj.q);
-    } else {
-      sym_transpose<-1>(R, dx, dy, dz, t.n[0], t.n[1], t.n[2], sj.a, sj.m[0], sj.m[1], sj.m[2], ti.p, ti.q);
-      sym_transpose<1>(R, dx, dy, dz, sj.n[0], sj.n[1], sj.n[2], t.a, t.m[0], t.m[1], t.m[2], tj.p, tj.q);
-    }
+    sym_pair<MASK, TRANS>(t.x[0] - sj.x[0], t.x[1] - sj.x[1], t.x[2] - sj.x[2], t.n, t.a, t.al, sj.n, sj.a, sj.al,
+                          masked, g.c, ti.p, ti.q, tj.p, tj.q);
   }
   __device__ static void renorm(Acc&) {}
   __device__ static T add(T a, T b) { return a + b; }
-  __device__ static T shfl(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  __device__ static T shfl_from(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  // a source slot past the end of a chunk: far away, no field, no normal (adds exact zeros)
+  __device__ static void pad(V4* r) {
+    V4 z;
+    z.x = T(1e4), z.y = T(1e4), z.z = T(1e4), z.w = T(0);
+    r[0] = z;
+    z.x = z.y = z.z = T(0);
+    r[1] = z;
+  }
   __device__ static PT out(T v) { return v; }
 };
 
@@ -98,15 +100,15 @@ __device__ df* sym_exp_table() {
   return tab;
 }
 
-// df64 record, 5 float4: (x.hi, a.hi), (x.lo, a.lo), (m.hi, n0.hi), (m.lo, n0.lo), (n1.hi, n2.hi, n1.lo, n2.lo)
+// df64 record, 4 float4: (x.hi, a.hi), (x.lo, a.lo), (n.hi, alpha.hi), (n.lo, alpha.lo)
 template <bool TRANS>
 struct SymDFPolicy {
   using V4 = float4;
   using PT = double;
-  static constexpr int RW = 5;
+  static constexpr int RW = 4;
   static constexpr int UNROLL = 1;
   struct Elem {
-    df x[3], a, m[3], n[3];
+    df x[3], a, n[3], al;
   };
   struct Acc {
     df p, q;
@@ -119,23 +121,16 @@ struct SymDFPolicy {
     if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
   }
   __device__ static void load(const float4* r, Elem& e) {
-    const float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
+    const float4 A = r[0], B = r[1], C = r[2], D = r[3];
     e.x[0] = df{A.x, B.x}, e.x[1] = df{A.y, B.y}, e.x[2] = df{A.z, B.z}, e.a = df{A.w, B.w};
-    e.m[0] = df{C.x, D.x}, e.m[1] = df{C.y, D.y}, e.m[2] = df{C.z, D.z};
-    e.n[0] = df{C.w, D.w}, e.n[1] = df{E.x, E.z}, e.n[2] = df{E.y, E.w};
+    e.n[0] = df{C.x, D.x}, e.n[1] = df{C.y, D.y}, e.n[2] = df{C.z, D.z}, e.al = df{C.w, D.w};
   }
   __device__ static void zero(Acc& v) { v.p = df{0.f, 0.f}, v.q = df{0.f, 0.f}; }
   template <bool MASK>
   __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
     const df d[3] = {df_sub(t.x[0], sj.x[0]), df_sub(t.x[1], sj.x[1]), df_sub(t.x[2], sj.x[2])};
-    const DFTerms R = df_sym_terms<MASK, TRANS>(d[0], d[1], d[2], masked, g.c, sym_exp_table());
-    if (!TRANS) {
-      df_sym_forward<1>(R, d, t.n, sj.a, sj.m, ti.p, ti.q);
-      df_sym_forward<-1>(R, d, sj.n, t.a, t.m, tj.p, tj.q);
-    } else {
-      df_sym_transpose<-1>(R, d, t.n, sj.a, sj.m, ti.p, ti.q);
-      df_sym_transpose<1>(R, d, sj.n, t.a, t.m, tj.p, tj.q);
-    }
+    df_sym_pair<MASK, TRANS>(d, t.n, t.a, t.al, sj.n, sj.a, sj.al, masked, g.c, sym_exp_table(), ti.p, ti.q, tj.p,
+                             tj.q);
   }
   // the accumulators are updated lazily (df_mac): bring them back to normal form
   __device__ static void renorm(Acc& v) {
@@ -143,8 +138,12 @@ struct SymDFPolicy {
     v.q = two_sum(v.q.hi, v.q.lo);
   }
   __device__ static df add(df a, df b) { return df_add(a, b); }
-  __device__ static df shfl(df v, int m) {
-    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+  __device__ static df shfl_from(df v, int src) {
+    return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+  }
+  __device__ static void pad(float4* r) {
+    r[0] = make_float4(1e4f, 1e4f, 1e4f, 0.f);
+    r[1] = r[2] = r[3] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __device__ static PT out(df v) { return df_to_double(v); }
 };
@@ -152,30 +151,37 @@ struct SymDFPolicy {
 // ------------------------------------------------------------------ kernel
 // One shared-memory chunk of cnt sources (starting at j0) against the
 // thread's TPT targets.  MASK: the chunk overlaps the tile's own targets, and
-// pairs with j <= i are masked.  The j side of every source is reduced over
-// the warp by a fixed butterfly (lanes 0-15 end with P, lanes 16-31 with Q)
-// and left in jred[warp][source].
+// pairs with j <= i are masked.  The j side rotates through the warp: the
+// chunk is taken in blocks of 32 sources (the slots past cnt padded with
+// records that add exact zeros); at step k of a block, lane l evaluates
+// source (l + k) mod 32 against its targets, then takes over the accumulator
+// of the next source from lane l + 1.  After 32 steps lane l holds the
+// complete j-side sum of source (l + 31) mod 32 over the warp's targets,
+// accumulated in a fixed order; it leaves it in jred[warp][source].
 template <class P, int TPT, int CH, bool MASK>
 __device__ __forceinline__ void sym_chunk(const typename P::Args& g, const typename P::Elem* tg, const int* idx,
-                                          typename P::Acc* acc, const typename P::V4* sh, int cnt, int j0,
-                                          typename P::Acc (*jred)[CH]) {
+                                              typename P::Acc* acc, const typename P::V4* sh, int cnt, int j0,
+                                              typename P::Acc (*jred)[CH]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool upper = (lane & 16) != 0;
-#pragma unroll P::UNROLL
-  for (int jj = 0; jj < cnt; ++jj) {
-    typename P::Elem sj;
-    P::load(sh + jj * P::RW, sj);
+  const int next = (lane + 1) & 31;
+  for (int r0 = 0; r0 < cnt; r0 += 32) {
     typename P::Acc tj;
     P::zero(tj);
+#pragma unroll P::UNROLL
+    for (int k = 0; k < 32; ++k) {
+      const int jj = r0 + ((lane + k) & 31);
+      typename P::Elem sj;
+      P::load(sh + jj * P::RW, sj);
 #pragma unroll
-    for (int k = 0; k < TPT; ++k) P::template pair<MASK>(g, tg[k], sj, MASK && j0 + jj <= idx[k], acc[k], tj);
+      for (int t = 0; t < TPT; ++t) P::template pair<MASK>(g, tg[t], sj, MASK && j0 + jj <= idx[t], acc[t], tj);
+      if (k < 31) {
+        tj.p = P::shfl_from(tj.p, next);
+        tj.q = P::shfl_from(tj.q, next);
+      }
+    }
     P::renorm(tj);
-    auto keep = upper ? tj.q : tj.p;
-    keep = P::add(keep, P::shfl(upper ? tj.p : tj.q, 16));
-#pragma unroll
-    for (int m = 8; m >= 1; m >>= 1) keep = P::add(keep, P::shfl(keep, m));
-    if (lane == 0) jred[warp][jj].p = keep;
-    if (lane == 16) jred[warp][jj].q = keep;
+    const int mine = r0 + ((lane + 31) & 31);
+    if (mine < cnt) jred[warp][mine] = tj;
   }
 }
 
@@ -218,6 +224,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4
       __syncthreads();
       const V4* src = rec + (size_t)(rec_off + j0) * P::RW;
       for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
+      for (int q = cnt + threadIdx.x; q < ((cnt + 31) & ~31); q += NT) P::pad(sh + q * P::RW);
       __syncthreads();
       if (j0 < t0 + T)
         sym_chunk<P, TPT, CH, true>(g, tg, idx, acc, sh, cnt, j0, jred);
@@ -246,6 +253,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4
 
 // ------------------------------------------------------------------ pack / reduce
 // Records of every system at vec_off / 2 (RW vectors each).  lay[k] = {geo_off, n, vec_off, chg_off}.
+// A u: a = ds psi, alpha = ds phi; A^T w: a = wphi, alpha = wpsi.
 template <typename V4, typename T>
 __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
                            const double* __restrict__ u, V4* __restrict__ rec, const int* __restrict__ skip,
@@ -257,13 +265,12 @@ __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const d
   const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
   const double phi = u[L.z + j], psi = u[L.z + L.y + j];
   const double a = transpose ? phi : g.w * psi;
-  const double f = transpose ? psi : g.w * phi;
-  V4 r0, r1, r2;
+  const double al = transpose ? psi : g.w * phi;
+  V4 r0, r1;
   r0.x = (T)g.x, r0.y = (T)g.y, r0.z = (T)g.z, r0.w = (T)a;
-  r1.x = (T)(f * v.x), r1.y = (T)(f * v.y), r1.z = (T)(f * v.z), r1.w = (T)0;
-  r2.x = (T)v.x, r2.y = (T)v.y, r2.z = (T)v.z, r2.w = (T)0;
-  V4* o = rec + 3 * (size_t)(L.z / 2 + j);
-  o[0] = r0, o[1] = r1, o[2] = r2;
+  r1.x = (T)v.x, r1.y = (T)v.y, r1.z = (T)v.z, r1.w = (T)al;
+  V4* o = rec + 2 * (size_t)(L.z / 2 + j);
+  o[0] = r0, o[1] = r1;
 }
 
 __global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
@@ -275,17 +282,15 @@ __global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, cons
   if (j >= L.y || (skip != nullptr && skip[(size_t)k * skip_stride] != 0)) return;
   const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
   const double phi = u[L.z + j], psi = u[L.z + L.y + j];
-  const double a = transpose ? phi : g.w * psi;
-  const double f = transpose ? psi : g.w * phi;
-  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z), w = df_from_double(a);
-  const df m0 = df_from_double(f * v.x), m1 = df_from_double(f * v.y), m2 = df_from_double(f * v.z);
+  const df a = df_from_double(transpose ? phi : g.w * psi);
+  const df al = df_from_double(transpose ? psi : g.w * phi);
+  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z);
   const df n0 = df_from_double(v.x), n1 = df_from_double(v.y), n2 = df_from_double(v.z);
-  float4* o = rec + 5 * (size_t)(L.z / 2 + j);
-  o[0] = make_float4(x0.hi, x1.hi, x2.hi, w.hi);
-  o[1] = make_float4(x0.lo, x1.lo, x2.lo, w.lo);
-  o[2] = make_float4(m0.hi, m1.hi, m2.hi, n0.hi);
-  o[3] = make_float4(m0.lo, m1.lo, m2.lo, n0.lo);
-  o[4] = make_float4(n1.hi, n2.hi, n1.lo, n2.lo);
+  float4* o = rec + 4 * (size_t)(L.z / 2 + j);
+  o[0] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
+  o[1] = make_float4(x0.lo, x1.lo, x2.lo, a.lo);
+  o[2] = make_float4(n0.hi, n1.hi, n2.hi, al.hi);
+  o[3] = make_float4(n0.lo, n1.lo, n2.lo, al.lo);
 }
 
 // y_i = diag u_i - (1/(4 pi)) scale_i (i-side blocks of the element's row + j-side rows 0..E).
@@ -306,10 +311,20 @@ __global__ void k_reduce_sym(const int4* __restrict__ lay, const int4* __restric
   const int4 R = tab[S.y + E];
   double acc = 0.0;
   for (int b = 0; b < R.y; ++b) acc += (double)part[(size_t)R.x + (size_t)b * 2 * T + (size_t)c * T + (e - E * T)];
-  for (int I = 0; I <= E; ++I) {
+  // rows 0..E in order; four loads in flight at a time
+  auto at = [&](int I) {
     const int64_t row = (int64_t)S.z + 2 * ((int64_t)I * n - (int64_t)T * I * (I - 1) / 2);
-    acc += (double)part[row + (int64_t)c * (n - I * T) + (e - I * T)];
+    return (double)part[row + (int64_t)c * (n - I * T) + (e - I * T)];
+  };
+  int I = 0;
+  for (; I + 4 <= E + 1; I += 4) {
+    const double v0 = at(I), v1 = at(I + 1), v2 = at(I + 2), v3 = at(I + 3);
+    acc += v0;
+    acc += v1;
+    acc += v2;
+    acc += v3;
   }
+  for (; I <= E; ++I) acc += at(I);
   const double sc = tgt64_for_area ? tgt64_for_area[2 * (L.x + e)].w : 1.0;
   y[L.z + i] = (c == 0 ? d_phi : d_psi) * u[L.z + i] - kInv4PiS * sc * acc;
 }
@@ -507,7 +522,7 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
   s->grow(recbuf, (size_t)(L.len / 2) * P::RW);
   s->grow(partbuf, (size_t)plan->part_len);
   const int4* lay = s->lay_dev(L);
-  if constexpr (P::RW == 5) {
+  if constexpr (std::is_same<typename P::PT, double>::value && std::is_same<typename P::V4, float4>::value) {
     k_pack_sym_df<<<dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, transpose, s->tgt64.p, u,
                                                                               recbuf.p, skip, skip_stride);
   } else {
@@ -546,7 +561,7 @@ bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, boo
   switch (variant) {
     BIPB_SYM32(0, 256, 2, 64, 4)
     BIPB_SYM32(1, 128, 4, 64, 5)
-    BIPB_SYM32(2, 256, 4, 64, 3)
+    BIPB_SYM32(2, 256, 4, 64, 2)
   }
 #undef BIPB_SYM32
   return false;
