@@ -62,11 +62,6 @@ bipb_status guarded(F&& f) {
 
 bool finite3(const double* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
-struct KeyHash {
-  size_t operator()(const std::array<uint64_t, 3>& k) const {
-    return (size_t)(k[0] * 0x9E3779B97F4A7C15ull ^ (k[1] + 0x632BE59BD9B4E019ull) * 31 ^ k[2] * 0x94D049BB133111EBull);
-  }
-};
 std::array<uint64_t, 3> key_of(const double* p) {
   std::array<uint64_t, 3> k;
   for (int i = 0; i < 3; ++i) {
@@ -129,6 +124,26 @@ Surface* checked(bipb_surface h) {
 
 using namespace bipb;
 
+// The stream-ordered pool of a device keeps up to 4 GiB of freed memory for
+// reuse (this process only; the driver default returns it at every
+// synchronisation).
+namespace bipb {
+void keep_pool_memory(int device) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (std::find(done.begin(), done.end(), device) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = 4ull << 30;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) (void)cudaGetLastError();
+  } else {
+    (void)cudaGetLastError();
+  }
+  done.push_back(device);
+}
+}  // namespace bipb
+
 extern "C" {
 
 const char* bipb_version(void) { return "bipb 0.1 (sm_103a)"; }
@@ -175,16 +190,24 @@ void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::v
     for (int k = 0; k < 3; ++k) c[k] += P.c[3 * i + k];
   }
   for (int k = 0; k < 3; ++k) c[k] /= (double)P.n;
-  // duplicates: exact in FP64, and after centring and rounding to FP32
-  std::unordered_set<std::array<uint64_t, 3>, KeyHash> seen64, seen32;
-  seen64.reserve(2 * P.n);
-  seen32.reserve(2 * P.n);
+  // duplicates of the centred centroids, in FP64 and after rounding to FP32
+  // (sorted keys; the FP64 ones are kept to reject charges on a centroid)
+  std::vector<std::array<uint64_t, 3>> k64((size_t)P.n), k32((size_t)P.n);
   for (int64_t i = 0; i < P.n; ++i) {
-    BIPB_REQUIRE(seen64.insert(key_of(P.c + 3 * i)).second, "two centroids coincide");
-    double f[3];
-    for (int k = 0; k < 3; ++k) f[k] = (double)(float)(P.c[3 * i + k] - c[k]);
-    BIPB_REQUIRE(seen32.insert(key_of(f)).second, "two centroids coincide after rounding to FP32");
+    double d[3], f[3];
+    for (int k = 0; k < 3; ++k) {
+      d[k] = P.c[3 * i + k] - c[k];
+      f[k] = (double)(float)d[k];
+    }
+    k64[i] = key_of(d);
+    k32[i] = key_of(f);
   }
+  std::sort(k64.begin(), k64.end());
+  std::sort(k32.begin(), k32.end());
+  BIPB_REQUIRE(std::adjacent_find(k64.begin(), k64.end()) == k64.end(), "two centroids coincide");
+  BIPB_REQUIRE(std::adjacent_find(k32.begin(), k32.end()) == k32.end(),
+               "two centroids coincide after rounding to FP32");
+  s->part_keys.push_back(std::move(k64));
   s->part_off.push_back((int)s->n);
   s->part_n.push_back((int)P.n);
   for (int k = 0; k < 3; ++k) s->part_center.push_back(c[k]);
@@ -222,53 +245,50 @@ bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream,
     BIPB_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming));
     BIPB_CUDA(cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming));
-    s->tgt64.ensure(tgt.size());
-    s->tgt32.ensure(tgt32.size());
-    BIPB_CUDA(cudaMemcpy(s->tgt64.p, tgt.data(), tgt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
-    BIPB_CUDA(cudaMemcpy(s->tgt32.p, tgt32.data(), tgt32.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    keep_pool_memory(dev);
+    s->tgt64.ensure(tgt.size(), s->stream);
+    s->tgt32.ensure(tgt32.size(), s->stream);
+    BIPB_CUDA(cudaMemcpyAsync(s->tgt64.p, tgt.data(), tgt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice,
+                              s->stream));
+    BIPB_CUDA(cudaMemcpyAsync(s->tgt32.p, tgt32.data(), tgt32.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                              s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
     s->magic = kMagic;
   } catch (...) {
-    if (s->stream) cudaStreamDestroy(s->stream);
+    cudaStream_t st = s->stream;
     if (s->ev_in) cudaEventDestroy(s->ev_in);
     if (s->ev_out) cudaEventDestroy(s->ev_out);
-    delete s;
+    delete s;  // its buffers go back to the pool on its stream
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
     throw;
   }
   register_handle(s);
   return reinterpret_cast<bipb_surface>(s);
 }
 
-// Charge records of one system, centred like its surface; rejects charges on a centroid.
+// Charge records of one system, centred like its surface; rejects charges on
+// a centroid (binary search in the surface's sorted centred centroid keys).
 void append_charges(Surface* s, int part, int64_t nc, const double* pos, const double* q,
-                    const std::unordered_set<std::array<uint64_t, 3>, KeyHash>& cent, std::vector<double4_32a>& rec) {
+                    std::vector<double4_32a>& rec) {
   const double* c = &s->part_center[3 * part];
+  const auto& keys = s->part_keys[part];
   for (int64_t k = 0; k < nc; ++k) {
     BIPB_REQUIRE(finite3(pos + 3 * k), "non-finite charge position");
     BIPB_REQUIRE(std::isfinite(q[k]), "non-finite charge");
     double p[3] = {pos[3 * k] - c[0], pos[3 * k + 1] - c[1], pos[3 * k + 2] - c[2]};
-    BIPB_REQUIRE(cent.find(key_of(p)) == cent.end(), "a charge sits on a centroid");
+    BIPB_REQUIRE(!std::binary_search(keys.begin(), keys.end(), key_of(p)), "a charge sits on a centroid");
     rec.push_back(make_double4_32a(p[0], p[1], p[2], q[k]));
   }
 }
 
-// Centred centroid keys of one surface (to reject charges that sit on a centroid).
-std::unordered_set<std::array<uint64_t, 3>, KeyHash> centroid_keys(Surface* s, int part) {
-  const int n = s->part_n[part];
-  std::vector<double4_32a> g(2 * (size_t)n);
-  BIPB_CUDA(cudaMemcpy(g.data(), s->tgt64.p + 2 * (size_t)s->part_off[part], g.size() * sizeof(double4_32a),
-                       cudaMemcpyDeviceToHost));
-  std::unordered_set<std::array<uint64_t, 3>, KeyHash> cent;
-  cent.reserve(2 * n);
-  for (int i = 0; i < n; ++i) {
-    double p[3] = {g[2 * i].x, g[2 * i].y, g[2 * i].z};
-    cent.insert(key_of(p));
-  }
-  return cent;
-}
-
 void store_charges(Surface* s, const std::vector<double4_32a>& rec, SysLayout lay) {
   s->grow(s->chg, rec.size());
-  BIPB_CUDA(cudaMemcpy(s->chg.p, rec.data(), rec.size() * sizeof(double4_32a), cudaMemcpyHostToDevice));
+  BIPB_CUDA(cudaMemcpyAsync(s->chg.p, rec.data(), rec.size() * sizeof(double4_32a), cudaMemcpyHostToDevice,
+                            s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));
   s->lay = std::move(lay);
   s->n_rhs = s->lay.K;
   s->have_solution = false;
@@ -317,6 +337,7 @@ bipb_status bipb_surface_create_batch(int n_surf, const int64_t* n_tri, const do
   });
 }
 
+
 bipb_status bipb_surface_destroy(bipb_surface h) {
   return guarded([&] {
     Surface* s = checked(h);
@@ -325,10 +346,12 @@ bipb_status bipb_surface_destroy(bipb_surface h) {
     cudaStreamSynchronize(s->stream);
     gmres_free(s);
     s->magic = 0;
-    cudaStreamDestroy(s->stream);
     cudaEventDestroy(s->ev_in);
     cudaEventDestroy(s->ev_out);
-    delete s;
+    cudaStream_t st = s->stream;
+    delete s;  // its buffers go back to the pool on its stream
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
   });
 }
 
@@ -343,13 +366,12 @@ bipb_status bipb_charges_set(bipb_surface h, int64_t nc, const double* pos, int 
     BIPB_REQUIRE(pos && q, "NULL input array");
     BIPB_REQUIRE((int64_t)n_rhs * nc <= (int64_t)1 << 28, "too many charges in total");
     DeviceGuard dg(s->device);
-    auto cent = centroid_keys(s, 0);
     std::vector<double4_32a> rec;
     rec.reserve((size_t)n_rhs * nc);
     std::vector<int> go(n_rhs, 0), n(n_rhs, (int)s->n), co(n_rhs), ncv(n_rhs, (int)nc);
     for (int r = 0; r < n_rhs; ++r) {
       co[r] = (int)(r * nc);
-      append_charges(s, 0, nc, pos + (size_t)(n_pos_sets == 1 ? 0 : r) * nc * 3, q + (size_t)r * nc, cent, rec);
+      append_charges(s, 0, nc, pos + (size_t)(n_pos_sets == 1 ? 0 : r) * nc * 3, q + (size_t)r * nc, rec);
     }
     s->nc = nc;
     s->n_pos_sets = n_pos_sets;
@@ -372,8 +394,7 @@ bipb_status bipb_charges_set_batch(bipb_surface h, const int64_t* nc, const doub
       BIPB_REQUIRE(pos[k] && q[k], "NULL charge array");
       co[k] = (int)rec.size();
       ncv[k] = (int)nc[k];
-      auto cent = centroid_keys(s, k);
-      append_charges(s, k, nc[k], pos[k], q[k], cent, rec);
+      append_charges(s, k, nc[k], pos[k], q[k], rec);
       BIPB_REQUIRE(rec.size() <= ((size_t)1 << 28), "too many charges in total");
     }
     s->nc = 0;
@@ -524,10 +545,10 @@ bipb_status bipb_energy_grad(bipb_surface h, const bipb_solve_params* p, double*
     size_t n_chg = 0;
     for (int k = 0; k < L.K; ++k) n_chg += L.nc[k];
     DevBuf<double> c, lam, dq, dy;
-    c.ensure(L.len);
-    lam.ensure(L.len);
-    dq.ensure(n_chg);
-    dy.ensure(3 * n_chg);
+    c.ensure(L.len, s->stream);
+    lam.ensure(L.len, s->stream);
+    dq.ensure(n_chg, s->stream);
+    dy.ensure(3 * n_chg, s->stream);
     bipb_solve_params pa = *p;
     pa.x0 = nullptr;
     energy_row_pass(s, L, m, c.p);

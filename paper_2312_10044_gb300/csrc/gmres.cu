@@ -312,10 +312,12 @@ struct GmresWork {
   DevBuf<int4> blk, sysb;
   DevBuf<int> mask;  // per system: 1 = leave out of the FP64 residual
   std::vector<int4> sysb_host;
-  DevState* st = nullptr;
-  DevState* st_host = nullptr;   // pinned
-  double* part1_host = nullptr;  // pinned
-  int* mask_host = nullptr;      // pinned
+  DevBuf<DevState> st_buf;
+  DevState* st = nullptr;  // st_buf.p
+  // host copies (pageable: every transfer of them is followed by a synchronisation)
+  std::vector<DevState> st_host;
+  std::vector<double> part1_host;
+  std::vector<int> mask_host;
   std::map<int, Recorded> graphs;  // recorded cycles keyed by (precision, transpose)
   const std::vector<EventPair>* replayed = nullptr;
   ~GmresWork() {
@@ -323,10 +325,6 @@ struct GmresWork {
       cudaGraphExecDestroy(kv.second.exec);
       for (auto& e : kv.second.events) cudaEventDestroy(e.a), cudaEventDestroy(e.b);
     }
-    if (st) cudaFree(st);
-    if (st_host) cudaFreeHost(st_host);
-    if (part1_host) cudaFreeHost(part1_host);
-    if (mask_host) cudaFreeHost(mask_host);
   }
 };
 
@@ -364,26 +362,27 @@ GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
   w->nblk = (int)blk.size();
   w->sysb_host = sysb;
   const int64_t len = L.len;
-  w->V.ensure((size_t)(m + 1) * len);
-  w->w.ensure(len);
-  w->r.ensure(len);
-  w->d.ensure(len);
-  w->t.ensure(len);
-  w->H.ensure((size_t)L.K * (m + 1) * m);
-  w->cs.ensure((size_t)L.K * m);
-  w->sn.ensure((size_t)L.K * m);
-  w->g.ensure((size_t)L.K * (m + 1));
-  w->y.ensure((size_t)L.K * m);
-  w->z.ensure((size_t)L.K * (m + 1));
-  w->part.ensure((size_t)w->nblk * (m + 1));
-  w->part1.ensure(w->nblk);
-  w->blk.ensure(blk.size());
-  w->sysb.ensure(L.K);
-  w->mask.ensure(L.K);
-  BIPB_CUDA(cudaMalloc(reinterpret_cast<void**>(&w->st), L.K * sizeof(DevState)));
-  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->st_host), L.K * sizeof(DevState)));
-  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->part1_host), w->nblk * sizeof(double)));
-  BIPB_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w->mask_host), L.K * sizeof(int)));
+  w->V.ensure((size_t)(m + 1) * len, s->stream);
+  w->w.ensure(len, s->stream);
+  w->r.ensure(len, s->stream);
+  w->d.ensure(len, s->stream);
+  w->t.ensure(len, s->stream);
+  w->H.ensure((size_t)L.K * (m + 1) * m, s->stream);
+  w->cs.ensure((size_t)L.K * m, s->stream);
+  w->sn.ensure((size_t)L.K * m, s->stream);
+  w->g.ensure((size_t)L.K * (m + 1), s->stream);
+  w->y.ensure((size_t)L.K * m, s->stream);
+  w->z.ensure((size_t)L.K * (m + 1), s->stream);
+  w->part.ensure((size_t)w->nblk * (m + 1), s->stream);
+  w->part1.ensure(w->nblk, s->stream);
+  w->blk.ensure(blk.size(), s->stream);
+  w->sysb.ensure(L.K, s->stream);
+  w->mask.ensure(L.K, s->stream);
+  w->st_buf.ensure(L.K, s->stream);
+  w->st = w->st_buf.p;
+  w->st_host.resize(L.K);
+  w->part1_host.resize(w->nblk);
+  w->mask_host.resize(L.K);
   BIPB_CUDA(cudaMemcpyAsync(w->blk.p, blk.data(), blk.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
   BIPB_CUDA(cudaMemcpyAsync(w->sysb.p, sysb.data(), sysb.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
   BIPB_CUDA(cudaStreamSynchronize(s->stream));
@@ -474,7 +473,7 @@ void run_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& 
 }
 
 void read_states(Surface* s, GmresWork* w) {
-  BIPB_CUDA(cudaMemcpyAsync(w->st_host, w->st, w->K * sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(w->st_host.data(), w->st, w->K * sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
   BIPB_CUDA(cudaStreamSynchronize(s->stream));
   if (s->timer.on) {
     s->timer.collect();
@@ -488,7 +487,7 @@ void read_states(Surface* s, GmresWork* w) {
 std::vector<double> norms(Surface* s, GmresWork* w, const double* v) {
   k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(v, w->part1.p, w->st, w->blk.p, 2);
   BIPB_LAUNCHED(s);
-  BIPB_CUDA(cudaMemcpyAsync(w->part1_host, w->part1.p, w->nblk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(w->part1_host.data(), w->part1.p, w->nblk * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   BIPB_CUDA(cudaStreamSynchronize(s->stream));
   std::vector<double> out(w->K);
   for (int k = 0; k < w->K; ++k) {
@@ -520,7 +519,7 @@ std::vector<int> gmres_core(Surface* s, const SysLayout& L, GmresWork* w, const 
     S.tol = tol[k];
     S.est = 1.0;
   }
-  BIPB_CUDA(cudaMemcpyAsync(w->st, w->st_host, K * sizeof(DevState), cudaMemcpyHostToDevice, s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(w->st, w->st_host.data(), K * sizeof(DevState), cudaMemcpyHostToDevice, s->stream));
   const int kg = (K + 127) / 128;
   k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(r0, w->part1.p, w->st, w->blk.p, 1);
   BIPB_LAUNCHED(s);
@@ -614,7 +613,7 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
     k_add<<<nb, kBS, 0, s->stream>>>(len, w->d.p, x);
     BIPB_LAUNCHED(s);
     for (int k = 0; k < K; ++k) w->mask_host[k] = active[k] ? 0 : 1;
-    BIPB_CUDA(cudaMemcpyAsync(w->mask.p, w->mask_host, K * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    BIPB_CUDA(cudaMemcpyAsync(w->mask.p, w->mask_host.data(), K * sizeof(int), cudaMemcpyHostToDevice, s->stream));
     matvec(s, L, med, resid, transpose, x, w->t.p, w->mask.p, 1);
     k_sub<<<nb, kBS, 0, s->stream>>>(len, rhs, w->t.p, w->r.p);
     BIPB_LAUNCHED(s);

@@ -7,6 +7,7 @@
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "bipb.h"
@@ -42,21 +43,34 @@ struct Error : std::runtime_error {
     if (!(cond)) throw ::bipb::Error(BIPB_ERR_INVALID_ARG, (msg));  \
   } while (0)
 
-// Owning device buffer that only grows.
+// Keep freed device memory in the device's stream-ordered pool (up to this
+// many bytes) so that new handles and growing buffers reuse it instead of
+// going back to the driver.  Set once per device, for this process only.
+void keep_pool_memory(int device);
+
+// Owning device buffer that only grows.  Memory comes from the device's
+// stream-ordered pool on the stream that uses the buffer (the handle's), and
+// goes back to it on the same stream, ordered after every earlier use.
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
   size_t cap = 0;
+  cudaStream_t stream = nullptr;
   // returns true when the buffer moved
-  bool ensure(size_t count) {
+  bool ensure(size_t count, cudaStream_t st = nullptr) {
     if (count <= cap) return false;
+    // buffers are created before a CUDA graph is recorded, never inside one
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BIPB_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) throw Error(BIPB_ERR_CUDA, "device buffer allocation while recording a graph");
     release();
-    BIPB_CUDA(cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T)));
+    stream = st;
+    BIPB_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), stream));
     cap = count;
     return true;
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, stream);
     p = nullptr;
     cap = 0;
   }
@@ -188,6 +202,7 @@ struct Surface {
   // batch handle, one system each): element offsets, sizes, centres
   std::vector<int> part_off, part_n;
   std::vector<double> part_center;  // 3 per surface
+  std::vector<std::vector<std::array<uint64_t, 3>>> part_keys;  // sorted bit patterns of the centred centroids
   bool batch = false;
 
   // cached work lists and device copies of layouts (keyed by content)
@@ -214,7 +229,7 @@ struct Surface {
 
   template <typename T>
   void grow(DevBuf<T>& buf, size_t count) {
-    if (buf.ensure(count)) ++alloc_gen;
+    if (buf.ensure(count, stream)) ++alloc_gen;
   }
 };
 

@@ -474,8 +474,8 @@ ItemPlan* plan_items(Surface* s, int pass_id, const std::vector<PassSys>& sys, i
   // per-system table for the reductions: {n_tgt, splits, out offset, unused}
   std::vector<int4> tab(K);
   for (int k = 0; k < K; ++k) tab[k] = make_int4(sys[k].n_tgt, sys_splits[k], (int)sys_out[k], 0);
-  plan->items.ensure(items.size());
-  plan->tab.ensure(K);
+  plan->items.ensure(items.size(), s->stream);
+  plan->tab.ensure(K, s->stream);
   BIPB_CUDA(cudaMemcpyAsync(plan->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             s->stream));
   BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, tab.data(), K * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
@@ -812,7 +812,7 @@ const int4* Surface::lay_dev(const SysLayout& L) {
   std::vector<int4> tab(L.K);
   for (int k = 0; k < L.K; ++k) tab[k] = make_int4(L.geo_off[k], L.n[k], L.vec_off[k], L.chg_off[k]);
   auto d = std::make_unique<DevBuf<int4>>();
-  d->ensure(L.K);
+  d->ensure(L.K, stream);
   BIPB_CUDA(cudaMemcpyAsync(d->p, tab.data(), L.K * sizeof(int4), cudaMemcpyHostToDevice, stream));
   BIPB_CUDA(cudaStreamSynchronize(stream));
   ++alloc_gen;
@@ -912,8 +912,8 @@ void check_tc_error(Surface* s) {
 int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int reps, double* best_ms) {
   const int len = (int)L.len;
   DevBuf<double> u, y;
-  u.ensure(len);
-  y.ensure(len);
+  u.ensure(len, s->stream);
+  y.ensure(len, s->stream);
   k_fill_test_vector<<<blocks_for(len, 256), 256, 0, s->stream>>>(len, u.p);
   BIPB_LAUNCHED(s);
   cudaEvent_t a, b;

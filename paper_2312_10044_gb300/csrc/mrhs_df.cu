@@ -165,7 +165,7 @@ ItemPlan* mrhs_df_plan(Surface* s, int n, int G, int slots, int* S_out) {
       for (int sp = 0; sp < S; ++sp)
         items.push_back(make_int4(t * kTgt, (int)((int64_t)sp * n / S), (int)((int64_t)(sp + 1) * n / S), sp));
     p->n_items = (int)items.size();
-    p->items.ensure(items.size());
+    p->items.ensure(items.size(), s->stream);
     BIPB_CUDA(cudaMemcpyAsync(p->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
                               s->stream));
     BIPB_CUDA(cudaStreamSynchronize(s->stream));
@@ -226,7 +226,7 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
       auto p = std::make_unique<ItemPlan>();
       std::vector<int4> tab(nb);
       for (int b = 0; b < nb; ++b) tab[b] = make_int4(n, S, b * S * 2 * n, 0);
-      p->tab.ensure(nb);
+      p->tab.ensure(nb, s->stream);
       BIPB_CUDA(cudaMemcpyAsync(p->tab.p, tab.data(), nb * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
       BIPB_CUDA(cudaStreamSynchronize(s->stream));
       ++s->alloc_gen;

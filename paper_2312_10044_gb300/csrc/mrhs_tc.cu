@@ -271,7 +271,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
         items.push_back(make_int4(t * kTgt, (int)((int64_t)sp * n_chunks / S), (int)((int64_t)(sp + 1) * n_chunks / S),
                                   sp));
     p->n_items = (int)items.size();
-    p->items.ensure(items.size());
+    p->items.ensure(items.size(), s->stream);
     BIPB_CUDA(cudaMemcpyAsync(p->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
                               s->stream));
     BIPB_CUDA(cudaStreamSynchronize(s->stream));
@@ -299,7 +299,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     auto tt = s->plans.find(tkey);
     if (tt == s->plans.end()) {
       auto p = std::make_unique<ItemPlan>();
-      p->tab.ensure(nb);
+      p->tab.ensure(nb, s->stream);
       BIPB_CUDA(cudaMemcpyAsync(p->tab.p, tab.data(), nb * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
       BIPB_CUDA(cudaStreamSynchronize(s->stream));
       ++s->alloc_gen;

@@ -69,8 +69,11 @@ struct SymPolicy {
     PairConst<T> c;
   };
   __device__ static void prologue(const Args&) {}
-  __device__ static void load(const V4* r, Elem& e) {
-    const V4 A = r[0], B = r[1];
+  __device__ static void load(const V4* r, Elem& e) { unpack(r[0], r[1], e); }
+  // record q of a chunk staged as planes (vector r of record q at sh[r * CH + q])
+  template <int CH>
+  __device__ static void load_plane(const V4* sh, int q, Elem& e) { unpack(sh[q], sh[CH + q], e); }
+  __device__ static void unpack(const V4& A, const V4& B, Elem& e) {
     e.x[0] = A.x, e.x[1] = A.y, e.x[2] = A.z, e.a = A.w;
     e.n[0] = B.x, e.n[1] = B.y, e.n[2] = B.z, e.al = B.w;
   }
@@ -84,13 +87,14 @@ struct SymPolicy {
   __device__ static void renorm(Acc&) {}
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static T shfl_from(T v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-  // a source slot past the end of a chunk: far away, no field, no normal (adds exact zeros)
-  __device__ static void pad(V4* r) {
+  // a source slot q past the end of a chunk: far away, no field, no normal (adds exact zeros)
+  template <int CH>
+  __device__ static void pad(V4* sh, int q) {
     V4 z;
     z.x = T(1e4), z.y = T(1e4), z.z = T(1e4), z.w = T(0);
-    r[0] = z;
+    sh[q] = z;
     z.x = z.y = z.z = T(0);
-    r[1] = z;
+    sh[CH + q] = z;
   }
   __device__ static PT out(T v) { return v; }
 };
@@ -120,8 +124,12 @@ struct SymDFPolicy {
     df* tab = sym_exp_table();
     if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
   }
-  __device__ static void load(const float4* r, Elem& e) {
-    const float4 A = r[0], B = r[1], C = r[2], D = r[3];
+  __device__ static void load(const float4* r, Elem& e) { unpack(r[0], r[1], r[2], r[3], e); }
+  template <int CH>
+  __device__ static void load_plane(const float4* sh, int q, Elem& e) {
+    unpack(sh[q], sh[CH + q], sh[2 * CH + q], sh[3 * CH + q], e);
+  }
+  __device__ static void unpack(const float4& A, const float4& B, const float4& C, const float4& D, Elem& e) {
     e.x[0] = df{A.x, B.x}, e.x[1] = df{A.y, B.y}, e.x[2] = df{A.z, B.z}, e.a = df{A.w, B.w};
     e.n[0] = df{C.x, D.x}, e.n[1] = df{C.y, D.y}, e.n[2] = df{C.z, D.z}, e.al = df{C.w, D.w};
   }
@@ -141,9 +149,10 @@ struct SymDFPolicy {
   __device__ static df shfl_from(df v, int src) {
     return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
   }
-  __device__ static void pad(float4* r) {
-    r[0] = make_float4(1e4f, 1e4f, 1e4f, 0.f);
-    r[1] = r[2] = r[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+  template <int CH>
+  __device__ static void pad(float4* sh, int q) {
+    sh[q] = make_float4(1e4f, 1e4f, 1e4f, 0.f);
+    sh[CH + q] = sh[2 * CH + q] = sh[3 * CH + q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __device__ static PT out(df v) { return df_to_double(v); }
 };
@@ -171,7 +180,7 @@ __device__ __forceinline__ void sym_chunk(const typename P::Args& g, const typen
     for (int k = 0; k < 32; ++k) {
       const int jj = r0 + ((lane + k) & 31);
       typename P::Elem sj;
-      P::load(sh + jj * P::RW, sj);
+      P::template load_plane<CH>(sh, jj, sj);
 #pragma unroll
       for (int t = 0; t < TPT; ++t) P::template pair<MASK>(g, tg[t], sj, MASK && j0 + jj <= idx[t], acc[t], tj);
       if (k < 31) {
@@ -222,9 +231,11 @@ __global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4
     for (int j0 = s0; j0 < s1; j0 += CH) {
       const int cnt = min(CH, s1 - j0);
       __syncthreads();
+      // stage the chunk as planes: vector r of record q at sh[r * CH + q] (the
+      // lanes of a warp read consecutive records: no bank conflicts)
       const V4* src = rec + (size_t)(rec_off + j0) * P::RW;
-      for (int q = threadIdx.x; q < cnt * P::RW; q += NT) sh[q] = src[q];
-      for (int q = cnt + threadIdx.x; q < ((cnt + 31) & ~31); q += NT) P::pad(sh + q * P::RW);
+      for (int e = threadIdx.x; e < cnt * P::RW; e += NT) sh[(e % P::RW) * CH + e / P::RW] = src[e];
+      for (int q = cnt + threadIdx.x; q < ((cnt + 31) & ~31); q += NT) P::template pad<CH>(sh, q);
       __syncthreads();
       if (j0 < t0 + T)
         sym_chunk<P, TPT, CH, true>(g, tg, idx, acc, sh, cnt, j0, jred);
@@ -465,8 +476,8 @@ ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slot
   auto plan = std::make_unique<ItemPlan>();
   plan->n_items = n_pieces;
   plan->part_len = off;
-  plan->items.ensure(sorted.size());
-  plan->tab.ensure(tab.size());
+  plan->items.ensure(sorted.size(), s->stream);
+  plan->tab.ensure(tab.size(), s->stream);
   BIPB_CUDA(cudaMemcpyAsync(plan->items.p, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice,
                             s->stream));
   BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
