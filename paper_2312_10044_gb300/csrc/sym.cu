@@ -27,6 +27,9 @@
 // the j-side values of rows 0..E, in that fixed order, in FP64.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <queue>
 #include <type_traits>
 
@@ -348,9 +351,55 @@ int blocks_of(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1)
 // equal pieces) whose greedy schedule (pieces sorted by size, each to the
 // first free CTA slot) finishes first.  A piece costs its
 // sources plus 32 per segment (loading a tile, storing its partials).
+struct HostPlan {
+  std::vector<int4> items, tab;
+  int n_items = 0;
+  int64_t part_len = 0;
+};
+
+HostPlan compute_sym_plan(const SysLayout& L, int T, int slots, int ch);
+
+// The work list depends only on the layout, the tile and the CTA slots:
+// handles of the same sizes share its host copy (a process-wide memo of at
+// most 64 entries), and each uploads it once.
 ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slots, int ch) {
   auto it = s->plans.find(key);
   if (it != s->plans.end()) return it->second.get();
+  uint64_t mk = 0xcbf29ce484222325ull;
+  auto mix = [&](uint64_t v) { mk = (mk ^ v) * 0x100000001b3ull; };
+  mix((uint64_t)T), mix((uint64_t)slots), mix((uint64_t)ch), mix((uint64_t)L.K);
+  for (int k = 0; k < L.K; ++k) mix((uint64_t)L.n[k]), mix((uint64_t)L.vec_off[k]);
+  static std::mutex mu;
+  static std::map<uint64_t, std::shared_ptr<const HostPlan>> memo;
+  std::shared_ptr<const HostPlan> hp;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto m = memo.find(mk);
+    if (m != memo.end()) hp = m->second;
+  }
+  if (!hp) {
+    hp = std::make_shared<const HostPlan>(compute_sym_plan(L, T, slots, ch));
+    std::lock_guard<std::mutex> lock(mu);
+    if (memo.size() >= 64) memo.erase(memo.begin());
+    memo[mk] = hp;
+  }
+  auto plan = std::make_unique<ItemPlan>();
+  plan->n_items = hp->n_items;
+  plan->part_len = hp->part_len;
+  plan->items.ensure(hp->items.size(), s->stream);
+  plan->tab.ensure(hp->tab.size(), s->stream);
+  BIPB_CUDA(cudaMemcpyAsync(plan->items.p, hp->items.data(), hp->items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            s->stream));
+  BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, hp->tab.data(), hp->tab.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));
+  ++s->alloc_gen;
+  ItemPlan* raw = plan.get();
+  s->plans[key] = std::move(plan);
+  return raw;
+}
+
+HostPlan compute_sym_plan(const SysLayout& L, int T, int slots, int ch) {
   const int K = L.K;
   struct Fold {
     int k, Ia, Ib, la, lb;  // rows Ia and Ib (-1: none) with la and lb sources
@@ -473,19 +522,12 @@ ItemPlan* plan_sym(Surface* s, uint64_t key, const SysLayout& L, int T, int slot
   for (int p = 0; p < n_pieces; ++p)
     for (int c = 0; c < 3; ++c) sorted[(size_t)3 * p + c] = items[(size_t)3 * porder[p] + c];
   tab.insert(tab.end(), rowtab.begin(), rowtab.end());
-  auto plan = std::make_unique<ItemPlan>();
-  plan->n_items = n_pieces;
-  plan->part_len = off;
-  plan->items.ensure(sorted.size(), s->stream);
-  plan->tab.ensure(tab.size(), s->stream);
-  BIPB_CUDA(cudaMemcpyAsync(plan->items.p, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice,
-                            s->stream));
-  BIPB_CUDA(cudaMemcpyAsync(plan->tab.p, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice, s->stream));
-  BIPB_CUDA(cudaStreamSynchronize(s->stream));
-  ++s->alloc_gen;
-  ItemPlan* raw = plan.get();
-  s->plans[key] = std::move(plan);
-  return raw;
+  HostPlan hp;
+  hp.items = std::move(sorted);
+  hp.tab = std::move(tab);
+  hp.n_items = n_pieces;
+  hp.part_len = off;
+  return hp;
 }
 
 // Plan-cache key of one symmetric pass over one layout (SplitMix64 finaliser,
