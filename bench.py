@@ -439,22 +439,17 @@ def main():
     if args.mode != "solve":
         return run_matvec_only(args)
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
+    from paper_2312_10044_gb300 import replicas
+    from paper_2312_10044_gb300.build import build
+
+    world, rank, local = replicas.init("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from paper_2312_10044_gb300.build import build
-
     if rank == 0:
         build()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     import paper_2312_10044_gb300 as bipb
 
     prob, desc = workload(args.workload)
@@ -486,8 +481,7 @@ def main():
     bipb.timer_enable(s, True)
     launches0 = bipb.launch_count(s)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     torch.cuda.synchronize()
     cs.start()
     infos = []
@@ -498,21 +492,16 @@ def main():
         evs[k][1].record()
     torch.cuda.synchronize()
     clocks = cs.stop()
-    if world > 1:
-        dist.barrier()
+    replicas.barrier(world)
     launches = bipb.launch_count(s) - launches0
     timers = bipb.timer_read(s)
     bipb.timer_enable(s, False)
     ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = float(sum(ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = replicas.max_over_ranks(float(sum(ms)), world, dev)
     info0 = infos[-1][0]
     mv = info0["matvecs32"] + info0["matvecs64"]
     pairs_step = mv * n * (n - 1) + 2 * n * nc
-    value = world * args.steps * pairs_step / (total_ms / 1e3) / 1e9
+    value = replicas.whole_job_rate(args.steps * pairs_step, world, total_ms / 1e3) / 1e9
 
     # ---- dominant kernel and its roofline (from the events around each launch)
     dom = max(timers, key=lambda k: timers[k][1])
@@ -587,6 +576,7 @@ def main():
     qq = torch.from_numpy(np.ascontiguousarray(prob.q)).pin_memory()
     e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
     torch.cuda.synchronize()
+    replicas.barrier(world)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         with bipb.Surface(cen.numpy(), nrm.numpy(), area.numpy()) as s2:
@@ -594,10 +584,11 @@ def main():
             s2.solve(params)
             s2.energy()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / max(e2e_steps, 1)
+    e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / max(e2e_steps, 1), world, dev)
     h2d = cen.numel() * 8 + nrm.numel() * 8 + area.numel() * 8 + pos.numel() * 8 + qq.numel() * 8
     e2e = None if not e2e_steps else {
-        "value": world * pairs_step / e2e_s / 1e9, "unit": "Gpairs/s", "h2d_bytes_per_step": int(h2d),
+        "value": replicas.whole_job_rate(pairs_step, world, e2e_s) / 1e9, "unit": "Gpairs/s",
+        "h2d_bytes_per_step": int(h2d),
         "d2h_bytes_per_step": 8, "ms_per_step": e2e_s * 1e3,
         "api": "bipb_surface_create + bipb_charges_set + bipb_solve + bipb_energy + bipb_surface_destroy"}
 
@@ -617,8 +608,7 @@ def main():
         line.update(extra)
         print(json.dumps(line), flush=True)
     s.close()
-    if world > 1:
-        dist.destroy_process_group()
+    replicas.finish(world)
 
 
 if __name__ == "__main__":

@@ -86,6 +86,34 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
                 assert np.abs(y - ref).max() < 2e-5 * scale, variant
 
 
+def test_degenerate_media(bipb, orc):
+    """kappa = 0 (pure Coulomb kernels) against the oracle in every precision,
+    and no dielectric contrast with kappa = 0, where every kernel vanishes
+    exactly: A = I and the solve returns b after one iteration."""
+    p = _ragged(3)
+    rng = np.random.default_rng(8)
+    U = rng.standard_normal((2, 2 * p.n))
+    med0 = bipb.medium(1.0, 80.0, 0.0)
+    ref = np.stack([orc.matvec(p.centroids, p.normals, p.areas, 80.0, 0.0, u) for u in U])
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        for prec, variant, tol in ((bipb.FP64, 0, 1e-12), (bipb.DF64, 0, 2e-12), (bipb.FP32, 0, 2e-5),
+                                   (bipb.FP32, 7, 2e-5)):
+            s.set_variant(variant)
+            yd = torch.full_like(ud, float("nan"))
+            s.matvec(ud, yd, precision=prec, med=med0)
+            assert np.abs(yd.cpu().numpy() - ref).max() < tol * np.abs(ref).max(), (prec, variant)
+        unit = bipb.medium(1.0, 1.0, 0.0)
+        for prec in (bipb.FP64, bipb.DF64, bipb.FP32):
+            yd = torch.full_like(ud, float("nan"))
+            s.matvec(ud, yd, precision=prec, med=unit)
+            assert torch.equal(yd, ud), prec
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(eps_in=1.0, eps_out=1.0, kappa=0.0, tol=1e-12, precision=bipb.MIXED_DF64)[0]
+        assert info["converged"] and info["iters"] <= 1
+        assert s.energy()[0] == 0.0
+
+
 def test_autotune_picks_a_variant(bipb):
     p = synth.kirkwood_problem(level=3)
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
