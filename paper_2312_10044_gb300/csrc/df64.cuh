@@ -287,18 +287,26 @@ __device__ __forceinline__ void df_sym_pair(const df* d, const df* nt, df at, df
   const df cj = df_dot3(ns[0], ns[1], ns[2], d[0], d[1], d[2]);
   const df cij = df_dot3(nt[0], nt[1], nt[2], ns[0], ns[1], ns[2]);
   const df U = df_sub(df_mul(tm1, cij), df_mul(wm3s2, df_mul(ci, cj)));
+  // s and s^3 folded into the four coefficients every update uses
+  const df ome_s = df_mul(ome, s), et1_s3 = df_mul(et1, s3), te1_s3 = df_mul(te1, s3), U_s3 = df_mul(U, s3);
   if (!TRANS) {
-    const df ka = df_mul(et1, s2);
-    df_mac(Pt, df_add(df_mul(df_mul(ka, cj), als), df_mul(ome, as)), s);
-    df_mac(Qt, df_add(df_mul(als, U), df_mul(df_mul(te1, ci), as)), s3);
-    df_mac(Ps, df_sub(df_mul(ome, at), df_mul(df_mul(ka, ci), alt)), s);
-    df_mac(Qs, df_sub(df_mul(alt, U), df_mul(df_mul(te1, cj), at)), s3);
+    df_mac(Pt, ome_s, as);
+    df_mac(Pt, df_mul(et1_s3, cj), als);
+    df_mac(Qt, df_mul(te1_s3, ci), as);
+    df_mac(Qt, U_s3, als);
+    df_mac(Ps, ome_s, at);
+    df_mac(Ps, df_neg(df_mul(et1_s3, ci)), alt);
+    df_mac(Qs, df_neg(df_mul(te1_s3, cj)), at);
+    df_mac(Qs, U_s3, alt);
   } else {
-    const df kb = df_mul(te1, s2);
-    df_mac(Pt, df_sub(df_mul(als, U), df_mul(df_mul(et1, ci), as)), s3);
-    df_mac(Qt, df_sub(df_mul(ome, as), df_mul(df_mul(kb, cj), als)), s);
-    df_mac(Ps, df_add(df_mul(alt, U), df_mul(df_mul(et1, cj), at)), s3);
-    df_mac(Qs, df_add(df_mul(ome, at), df_mul(df_mul(kb, ci), alt)), s);
+    df_mac(Pt, U_s3, als);
+    df_mac(Pt, df_neg(df_mul(et1_s3, ci)), as);
+    df_mac(Qt, ome_s, as);
+    df_mac(Qt, df_neg(df_mul(te1_s3, cj)), als);
+    df_mac(Ps, U_s3, alt);
+    df_mac(Ps, df_mul(et1_s3, cj), at);
+    df_mac(Qs, ome_s, at);
+    df_mac(Qs, df_mul(te1_s3, ci), alt);
   }
 }
 

@@ -171,18 +171,18 @@ __device__ __forceinline__ void sym_pair(T dx, T dy, T dz, const T* nt, T at, T 
   const T cj = ns[0] * dx + ns[1] * dy + ns[2] * dz;
   const T cij = nt[0] * ns[0] + nt[1] * ns[1] + nt[2] * ns[2];
   const T U = tm1 * cij - wm3s2 * (ci * cj);
+  // s and s^3 folded into the four coefficients every update uses
+  const T ome_s = ome * s, et1_s3 = et1 * s3, te1_s3 = te1 * s3, U_s3 = U * s3;
   if (!TRANS) {
-    const T ka = et1 * s2;
-    Pt = ((ka * cj) * als + ome * as) * s + Pt;
-    Qt = (als * U + (te1 * ci) * as) * s3 + Qt;
-    Ps = (ome * at - (ka * ci) * alt) * s + Ps;
-    Qs = (alt * U - (te1 * cj) * at) * s3 + Qs;
+    Pt = (et1_s3 * cj) * als + (ome_s * as + Pt);
+    Qt = U_s3 * als + ((te1_s3 * ci) * as + Qt);
+    Ps = ome_s * at - ((et1_s3 * ci) * alt - Ps);
+    Qs = U_s3 * alt - ((te1_s3 * cj) * at - Qs);
   } else {
-    const T kb = te1 * s2;
-    Pt = (als * U - (et1 * ci) * as) * s3 + Pt;
-    Qt = (ome * as - (kb * cj) * als) * s + Qt;
-    Ps = (alt * U + (et1 * cj) * at) * s3 + Ps;
-    Qs = (ome * at + (kb * ci) * alt) * s + Qs;
+    Pt = U_s3 * als - ((et1_s3 * ci) * as - Pt);
+    Qt = ome_s * as - ((te1_s3 * cj) * als - Qt);
+    Ps = U_s3 * alt + ((et1_s3 * cj) * at + Ps);
+    Qs = ome_s * at + ((te1_s3 * ci) * alt + Qs);
   }
 }
 

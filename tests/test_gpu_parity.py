@@ -313,9 +313,10 @@ def test_warm_start_from_solution_needs_no_iterations(bipb):
 
 
 # ---------------------------------------------------------------- full-size sampled checks
-@pytest.mark.parametrize("cfg", ["kirkwood", "protein_like"])
+@pytest.mark.parametrize("cfg", ["kirkwood", "protein_like", "adjoint"])
 def test_full_size_matvec_sampled_rows(bipb, orc, cfg):
-    """The benchmark's mat-vec launch at full size, checked on sampled rows."""
+    """The benchmark's mat-vec launch at full size (up to level 7, N = 327680,
+    where the symmetric work list spans 640 tile rows), checked on sampled rows."""
     p = synth.problem_by_name(cfg)
     eps = p.eps_out / p.eps_in
     u = np.random.default_rng(9).standard_normal(2 * p.n)
