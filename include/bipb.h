@@ -251,7 +251,7 @@ bipb_status bipb_autotune(bipb_surface s, const bipb_medium* m, int reps, int* v
  * Variants 0-6 visit every ordered pair (i, j) (one target per thread
  * gathering all sources); variants 7-9 visit every unordered pair {i, j} once
  * and apply it to both rows, sharing 1/r, exp(-kappa r), t and w between the
- * two directions of Eqs. 5-6.  A new handle starts with variant 7. */
+ * two directions of Eqs. 5-6.  A new handle starts with variant 9. */
 #define BIPB_MATVEC32_VARIANTS 10
 bipb_status bipb_matvec_variant(bipb_surface s, int variant);
 

@@ -218,7 +218,7 @@ struct Surface {
   bool have_solution = false;
   bipb_medium solved_medium{0, 0, 0};
 
-  int mv32_variant = kFirstSymVariant;  // FP32 mat-vec variant (the autotuner may change it)
+  int mv32_variant = kFirstSymVariant + 2;  // FP32 mat-vec variant (the autotuner may change it)
   bool sym_pairs = true;  // FP64 / double-float mat-vecs visit unordered pairs once (sym.cu)
   GmresWork* gw = nullptr;
   KernelTimer timer;
