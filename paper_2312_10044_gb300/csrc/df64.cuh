@@ -343,3 +343,62 @@ __device__ __forceinline__ void df_reaction_pair(const df* y, const df* x, df a,
 }
 
 }  // namespace bipb
+
+namespace bipb {
+
+// Energy row of one (element, charge) pair in df64: element j (x, n), charge
+// (y, q), d = y - x (times 4 pi):  cphi += q (eps t - 1)(n.d) s^3,  cpsi += q (1 - e) s.
+__device__ __forceinline__ void df_energy_row_pair(const df* x, const df* nv, const df* y, df q, const DFConst& c,
+                                                   const df* tab, df& cphi, df& cpsi) {
+  const df d0 = df_sub(y[0], x[0]), d1 = df_sub(y[1], x[1]), d2 = df_sub(y[2], x[2]);
+  const df r2 = df_sumsq3(d0, d1, d2);
+  const df s = df_rsqrt(r2);
+  const df kr = df_mul(df_mul(r2, s), c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df t = df_add(df_mul(e, kr), e);
+  const df cj = df_dot3(nv[0], nv[1], nv[2], d0, d1, d2);
+  const df s3 = df_mul(df_sqr(s), s);
+  df_mac(cphi, df_mul(df_mul(q, df_add_f(df_mul(c.eps, t), -1.0f)), cj), s3);
+  df_mac(cpsi, df_mul(q, df_add_f(df_neg(e), 1.0f)), s);
+}
+
+// Energy gradient at a charge y from one element in df64.  Element record:
+// x, a = ds psi, normal n, alpha = ds phi (m = alpha n), lphi, beta = lpsi
+// (p = beta n) from the adjoint lam = [lphi; lpsi]; d = y - x, cn = n.d.
+// With inv = 1 / eps_in (times 4 pi):
+//   v   += s [ (1 - e) a + (eps t - 1) alpha cn s^2 ] + inv s [ lphi + beta cn s^2 ]
+//   g_m += Cn n_m + Cd d_m, where
+//   Cn = s^3 [ (eps t - 1) alpha + inv beta ]
+//   Cd = s^3 [ (t - 1) a - (eps w - 3) alpha cn s^2 - inv (lphi + 3 beta cn s^2) ]
+// (the y-gradients of the energy row and of the adjoint-weighted source).
+__device__ __forceinline__ void df_grad_pair(const df* y, const df* x, df a, const df* nv, df al, df lphi, df beta,
+                                             const DFConst& c, df inv, const df* tab, df& v, df* g) {
+  const df d[3] = {df_sub(y[0], x[0]), df_sub(y[1], x[1]), df_sub(y[2], x[2])};
+  const df r2 = df_sumsq3(d[0], d[1], d[2]);
+  const df s = df_rsqrt(r2);
+  const df kr = df_mul(df_mul(r2, s), c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df ekr = df_mul(e, kr);
+  const df t = df_add(ekr, e);
+  const df w = df_mul(e, df_add_f(df_mul(kr, df_add_f(kr, 3.0f)), 3.0f));  // e (3 + 3 kr + kr^2)
+  const df s2 = df_sqr(s);
+  const df s3 = df_mul(s2, s);
+  const df cn = df_dot3(nv[0], nv[1], nv[2], d[0], d[1], d[2]);
+  const df et1 = df_add_f(df_mul(c.eps, t), -1.0f);
+  const df acn_s2 = df_mul(df_mul(al, cn), s2);
+  const df bcn_s2 = df_mul(df_mul(beta, cn), s2);
+  // potential at y and the adjoint-weighted source
+  df_mac(v, df_add(df_mul(df_add_f(df_neg(e), 1.0f), a), df_mul(et1, acn_s2)), s);
+  df_mac(v, df_mul(inv, df_add(lphi, bcn_s2)), s);
+  const df Cn = df_mul(df_add(df_mul(et1, al), df_mul(inv, beta)), s3);
+  const df Cd = df_mul(df_sub(df_sub(df_mul(df_add_f(t, -1.0f), a),
+                                     df_mul(df_add_f(df_mul(c.eps, w), -3.0f), acn_s2)),
+                              df_mul(inv, df_add(lphi, df_mul_f(bcn_s2, 3.0f)))),
+                       s3);
+  for (int m = 0; m < 3; ++m) {
+    df_mac(g[m], Cn, nv[m]);
+    df_mac(g[m], Cd, d[m]);
+  }
+}
+
+}  // namespace bipb

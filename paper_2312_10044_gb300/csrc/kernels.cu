@@ -72,6 +72,7 @@ struct MatvecPolicy {
     t = Tgt{g.x, g.y, g.z, v.x, v.y, v.z};
   }
   __device__ static void zero(Acc& acc) { acc.p = T(0), acc.q = T(0); }
+  __device__ static void renorm(Acc&) {}
   template <bool MASK>
   __device__ static void pair(const Args& a, const Tgt& t, const V4* r, bool self, Acc& acc) {
     const V4 A = r[0], B = r[1];
@@ -122,6 +123,7 @@ struct MatvecDFPolicy {
     t.n[0] = df_from_double(v.x), t.n[1] = df_from_double(v.y), t.n[2] = df_from_double(v.z);
   }
   __device__ static void zero(Acc& acc) { acc.p = df{0.f, 0.f}, acc.q = df{0.f, 0.f}; }
+  __device__ static void renorm(Acc&) {}
   template <bool MASK>
   __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool self, Acc& acc) {
     const float4 A = r[0], B = r[1], C = r[2], D = r[3];
@@ -166,6 +168,7 @@ struct SourcePolicy {
     t.n[0] = df_from_double(v.x), t.n[1] = df_from_double(v.y), t.n[2] = df_from_double(v.z);
   }
   __device__ static void zero(Acc& acc) { acc.s1 = df{0.f, 0.f}, acc.s2 = df{0.f, 0.f}; }
+  __device__ static void renorm(Acc&) {}
   template <bool MASK>
   __device__ static void pair(const Args&, const Tgt& t, const float4* r, bool, Acc& acc) {
     const float4 A = r[0], B = r[1];
@@ -176,10 +179,6 @@ struct SourcePolicy {
     a.part[(size_t)out + i] = df_to_double(acc.s1);
     a.part[(size_t)out + n_tgt + i] = df_to_double(acc.s2);
   }
-};
-
-struct PointTgt {
-  double x, y, z;
 };
 
 // Reaction potential at a charge y_k from the surface in df64 (forward df
@@ -210,6 +209,7 @@ struct ReactionPolicy {
     t.y[0] = df_from_double(g.x), t.y[1] = df_from_double(g.y), t.y[2] = df_from_double(g.z);
   }
   __device__ static void zero(Acc& acc) { acc.p = df{0.f, 0.f}; }
+  __device__ static void renorm(Acc&) {}
   template <bool MASK>
   __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool, Acc& acc) {
     const float4 A = r[0], B = r[1], C = r[2], D = r[3];
@@ -222,111 +222,101 @@ struct ReactionPolicy {
   }
 };
 
-// Energy row c: target element j, source charge k (record (y_k, q_k)), d = y_k - x_j:
+// Energy row c in df64: target element j, source charge k (df record
+// (y_k, q_k)), d = y_k - x_j:
 //   4 pi K2(y_k, x_j) = (eps t - 1) (n_j.d) s^3,  4 pi K1(y_k, x_j) = (1 - e) s
 struct EnergyRowPolicy {
-  static constexpr int RW = 1;
+  static constexpr int RW = 2;
   static constexpr int NOUT = 2;
   static constexpr bool SELF = false;
-  template <class A>
-  __device__ static void prologue(const A&) {}
-  using Tgt = ElemTgt<double>;
+  struct Tgt {
+    df x[3], n[3];
+  };
   struct Acc {
-    double cphi, cpsi;
+    df cphi, cpsi;
   };
   struct Args {
     const double4_32a* tgt;
     double* part;
-    PairConst<double> c;
+    DFConst c;
   };
+  template <class A>
+  __device__ static void prologue(const A&) {
+    df* tab = df_exp_table();
+    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  }
   __device__ static void load(const Args& a, int i, Tgt& t) {
     double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
-    t = Tgt{g.x, g.y, g.z, v.x, v.y, v.z};
+    t.x[0] = df_from_double(g.x), t.x[1] = df_from_double(g.y), t.x[2] = df_from_double(g.z);
+    t.n[0] = df_from_double(v.x), t.n[1] = df_from_double(v.y), t.n[2] = df_from_double(v.z);
   }
-  __device__ static void zero(Acc& acc) { acc.cphi = 0.0, acc.cpsi = 0.0; }
+  __device__ static void zero(Acc& acc) { acc.cphi = df{0.f, 0.f}, acc.cpsi = df{0.f, 0.f}; }
+  __device__ static void renorm(Acc& acc) {
+    acc.cphi = two_sum(acc.cphi.hi, acc.cphi.lo);
+    acc.cpsi = two_sum(acc.cpsi.hi, acc.cpsi.lo);
+  }
   template <bool MASK>
-  __device__ static void pair(const Args& a, const Tgt& t, const double4_32a* r, bool, Acc& acc) {
-    const double4_32a A = r[0];
-    double dx = A.x - t.x, dy = A.y - t.y, dz = A.z - t.z;
-    double s, rr, e;
-    radial<false>(dx * dx + dy * dy + dz * dz, false, a.c, s, rr, e);
-    double t1 = e * (rr * a.c.kappa) + e;
-    double cj = t.nx * dx + t.ny * dy + t.nz * dz;
-    acc.cphi += A.w * (a.c.eps * t1 - 1.0) * cj * (s * s * s);
-    acc.cpsi += A.w * (1.0 - e) * s;
+  __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool, Acc& acc) {
+    const float4 A = r[0], B = r[1];
+    const df y[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    df_energy_row_pair(t.x, t.n, y, df{A.w, B.w}, a.c, df_exp_table(), acc.cphi, acc.cpsi);
   }
   __device__ static void store(const Args& a, int out, int n_tgt, int i, const Acc& acc) {
-    a.part[(size_t)out + i] = acc.cphi;
-    a.part[(size_t)out + n_tgt + i] = acc.cpsi;
+    a.part[(size_t)out + i] = df_to_double(acc.cphi);
+    a.part[(size_t)out + n_tgt + i] = df_to_double(acc.cpsi);
   }
 };
 
-// Energy gradient at charge y_k.  Records per element j: (x_j, a_j),
-// (m_j, lphi_j), (p_j = lpsi_j n_j, 0) with u = [phi; psi] and the adjoint
-// lam = [lphi; lpsi].  With d = y_k - x_j (times 4 pi):
-//   phi_reac  += s [ (1-e) a + (eps t - 1)(m.d) s^2 ]
-//   grad_A    += s^3 [ (eps t - 1) m + ((t - 1) a - (eps w - 3)(m.d) s^2) d ]
-//   src_B     += s [ lphi + (p.d) s^2 ]
-//   grad_B    += s^3 [ p - (lphi + 3 (p.d) s^2) d ]
-// grad_A is the y-gradient of the energy row (d/dy of K1(y, x_j) and
-// K2(y, x_j)); src_B and grad_B are the adjoint-weighted source column
-// (G0(x_j, y) and dG0(x_j, y)/dnu_x) and its y-gradient.
+// Energy gradient at charge y_k in df64 (df_grad_pair in df64.cuh).  Record
+// per element j, 5 float4: (x.hi, a.hi), (x.lo, a.lo), (n.hi, alpha.hi),
+// (n.lo, alpha.lo), (lphi.hi, lphi.lo, beta.hi, beta.lo) with a = ds psi,
+// alpha = ds phi and the adjoint lam = [lphi; beta].  Outputs per charge: v
+// (dE/dq up to 1/2 and 1/(4 pi)) and the three components of the gradient g.
 struct GradPolicy {
-  static constexpr int RW = 3;
-  static constexpr int NOUT = 8;
+  static constexpr int RW = 5;
+  static constexpr int NOUT = 4;
   static constexpr bool SELF = false;
-  template <class A>
-  __device__ static void prologue(const A&) {}
-  using Tgt = PointTgt;
+  struct Tgt {
+    df y[3];
+  };
   struct Acc {
-    double p, sb, ga[3], gb[3];
+    df v, g[3];
   };
   struct Args {
     const double4_32a* pts;
     double* part;
-    PairConst<double> c;
+    DFConst c;
+    df inv_eps_in;
   };
+  template <class A>
+  __device__ static void prologue(const A&) {
+    df* tab = df_exp_table();
+    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  }
   __device__ static void load(const Args& a, int k, Tgt& t) {
     double4_32a g = a.pts[k];
-    t = Tgt{g.x, g.y, g.z};
+    t.y[0] = df_from_double(g.x), t.y[1] = df_from_double(g.y), t.y[2] = df_from_double(g.z);
   }
   __device__ static void zero(Acc& acc) {
-    acc.p = acc.sb = 0.0;
-    for (int m = 0; m < 3; ++m) acc.ga[m] = acc.gb[m] = 0.0;
+    acc.v = df{0.f, 0.f};
+    for (int m = 0; m < 3; ++m) acc.g[m] = df{0.f, 0.f};
+  }
+  __device__ static void renorm(Acc& acc) {
+    acc.v = two_sum(acc.v.hi, acc.v.lo);
+    for (int m = 0; m < 3; ++m) acc.g[m] = two_sum(acc.g[m].hi, acc.g[m].lo);
   }
   template <bool MASK>
-  __device__ static void pair(const Args& a, const Tgt& t, const double4_32a* r, bool, Acc& acc) {
-    const double4_32a A = r[0], B = r[1], C = r[2];
-    double d[3] = {t.x - A.x, t.y - A.y, t.z - A.z};
-    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    double s, rr, e;
-    radial<false>(r2, false, a.c, s, rr, e);
-    double kr = rr * a.c.kappa;
-    double t1 = e * kr + e;
-    double w = e * (3.0 + kr * (3.0 + kr));
-    double s2 = s * s, s3 = s2 * s;
-    double cm = B.x * d[0] + B.y * d[1] + B.z * d[2];
-    double cp = C.x * d[0] + C.y * d[1] + C.z * d[2];
-    double et1 = a.c.eps * t1 - 1.0;
-    acc.p += s * ((A.w - e * A.w) + et1 * cm * s2);
-    double fa = (t1 - 1.0) * A.w - (a.c.eps * w - 3.0) * cm * s2;
-    double mv[3] = {B.x, B.y, B.z}, pv[3] = {C.x, C.y, C.z};
-    double lphi = B.w;
-    acc.sb += s * (lphi + cp * s2);
-    double fb = lphi + 3.0 * cp * s2;
-    for (int m = 0; m < 3; ++m) {
-      acc.ga[m] += s3 * (et1 * mv[m] + fa * d[m]);
-      acc.gb[m] += s3 * (pv[m] - fb * d[m]);
-    }
+  __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool, Acc& acc) {
+    const float4 A = r[0], B = r[1], C = r[2], D = r[3], E = r[4];
+    const df x[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    const df nv[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
+    df_grad_pair(t.y, x, df{A.w, B.w}, nv, df{C.w, D.w}, df{E.x, E.y}, df{E.z, E.w}, a.c, a.inv_eps_in,
+                 df_exp_table(), acc.v, acc.g);
   }
   __device__ static void store(const Args& a, int out, int n_tgt, int k, const Acc& acc) {
     double* o = a.part + (size_t)out + k;
-    o[0] = acc.p;
-    o[(size_t)n_tgt] = acc.sb;
-    for (int m = 0; m < 3; ++m) {
-      o[(size_t)(2 + m) * n_tgt] = acc.ga[m];
-      o[(size_t)(5 + m) * n_tgt] = acc.gb[m];
-    }
+    o[0] = df_to_double(acc.v);
+    for (int m = 0; m < 3; ++m) o[(size_t)(1 + m) * n_tgt] = df_to_double(acc.g[m]);
   }
 };
 
@@ -383,6 +373,8 @@ __global__ void __launch_bounds__(NT) k_items(typename P::Args a, const int4* __
           P::template pair<true>(a, tg[k], sh + jj * P::RW, j0 + jj == idx[k], acc[k]);
       }
     }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) P::renorm(acc[k]);  // lazily updated accumulators back to normal form
   }
 #pragma unroll
   for (int k = 0; k < TPT; ++k)
@@ -635,10 +627,11 @@ __global__ void k_energy_row_reduce(const int4* __restrict__ lay, const int4* __
   c[L.z + i] = tgt64[2 * (L.x + e)].w * kInv4Pi * acc;
 }
 
-// Gradient records of every system (3 per element, at vec_off / 2).
+// Gradient records of every system in df64 (5 float4 per element, at
+// vec_off / 2): (x, a = ds psi), (n, alpha = ds phi), (lphi, beta = lpsi).
 __global__ void k_pack_grad(const int4* __restrict__ lay, const double4_32a* __restrict__ tgt64,
                             const double* __restrict__ u, const double* __restrict__ lam,
-                            double4_32a* __restrict__ rec) {
+                            float4* __restrict__ rec) {
   const int k = blockIdx.y;
   const int4 L = lay[k];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -646,28 +639,33 @@ __global__ void k_pack_grad(const int4* __restrict__ lay, const double4_32a* __r
   const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
   const double* uk = u + L.z;
   const double* lk = lam + L.z;
-  const double aphi = g.w * uk[j];
-  const size_t o = (size_t)(L.z / 2 + j);
-  rec[3 * o] = make_double4_32a(g.x, g.y, g.z, g.w * uk[L.y + j]);
-  rec[3 * o + 1] = make_double4_32a(aphi * v.x, aphi * v.y, aphi * v.z, lk[j]);
-  const double lp = lk[L.y + j];
-  rec[3 * o + 2] = make_double4_32a(lp * v.x, lp * v.y, lp * v.z, 0.0);
+  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z);
+  const df n0 = df_from_double(v.x), n1 = df_from_double(v.y), n2 = df_from_double(v.z);
+  const df a = df_from_double(g.w * uk[L.y + j]), al = df_from_double(g.w * uk[j]);
+  const df lphi = df_from_double(lk[j]), beta = df_from_double(lk[L.y + j]);
+  float4* o = rec + 5 * (size_t)(L.z / 2 + j);
+  o[0] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
+  o[1] = make_float4(x0.lo, x1.lo, x2.lo, a.lo);
+  o[2] = make_float4(n0.hi, n1.hi, n2.hi, al.hi);
+  o[3] = make_float4(n0.lo, n1.lo, n2.lo, al.lo);
+  o[4] = make_float4(lphi.hi, lphi.lo, beta.hi, beta.lo);
 }
 
+// dE/dq = 1/2 (1/(4 pi)) v and dE/dy = 1/2 q (1/(4 pi)) g per charge (sums over splits in a fixed order)
 __global__ void k_reduce_grad(const int4* __restrict__ tab, const int4* __restrict__ lay,
                               const double* __restrict__ part, const double4_32a* __restrict__ chg,
-                              double inv_eps_in, double* __restrict__ dq, double* __restrict__ dy) {
+                              double* __restrict__ dq, double* __restrict__ dy) {
   const int k = blockIdx.y;
   const int4 T = tab[k];
   const int nc = T.x, c0 = lay[k].w;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= nc) return;
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double v[4] = {0, 0, 0, 0};
   for (int sp = 0; sp < T.y; ++sp)
-    for (int c = 0; c < 8; ++c) v[c] += part[(size_t)T.z + (size_t)sp * 8 * nc + (size_t)c * nc + q];
+    for (int c = 0; c < 4; ++c) v[c] += part[(size_t)T.z + (size_t)sp * 4 * nc + (size_t)c * nc + q];
   const double qq = chg[c0 + q].w;
-  dq[c0 + q] = 0.5 * kInv4Pi * (v[0] + inv_eps_in * v[1]);
-  for (int m = 0; m < 3; ++m) dy[3 * (c0 + q) + m] = 0.5 * qq * kInv4Pi * (v[2 + m] + inv_eps_in * v[5 + m]);
+  dq[c0 + q] = 0.5 * kInv4Pi * v[0];
+  for (int m = 0; m < 3; ++m) dy[3 * (c0 + q) + m] = 0.5 * qq * kInv4Pi * v[1 + m];
 }
 
 template <typename T>
@@ -1000,11 +998,18 @@ void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const d
 void energy_row_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* c) {
   constexpr int NT = 128, TPT = 1, CH = 64;
   std::vector<PassSys> sys(L.K);
-  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.geo_off[k], L.n[k], L.chg_off[k], L.nc[k]};
-  ItemPlan* plan = plan_pass<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kPassRow, sys, CH);
+  int n_chg = 0;
+  for (int k = 0; k < L.K; ++k) {
+    sys[k] = PassSys{L.geo_off[k], L.n[k], L.chg_off[k], L.nc[k]};
+    n_chg = std::max(n_chg, L.chg_off[k] + L.nc[k]);
+  }
+  ItemPlan* plan = plan_pass<EnergyRowPolicy, float4, NT, TPT, CH>(s, kPassRow, sys, CH);
+  s->grow(s->chgdf, (size_t)2 * n_chg);
   s->grow(s->part64, (size_t)plan->part_len);
-  EnergyRowPolicy::Args a{s->tgt64.p, s->part64.p, pair_const<double>(m)};
-  launch_items<EnergyRowPolicy, double4_32a, NT, TPT, CH>(s, kTRow, plan, a, s->chg.p, nullptr, 0);
+  k_pack_chg_df<<<blocks_for(n_chg, 256), 256, 0, s->stream>>>(n_chg, s->chg.p, s->chgdf.p);
+  BIPB_LAUNCHED(s);
+  EnergyRowPolicy::Args a{s->tgt64.p, s->part64.p, df_const_impl(m)};
+  launch_items<EnergyRowPolicy, float4, NT, TPT, CH>(s, kTRow, plan, a, s->chgdf.p, nullptr, 0);
   k_energy_row_reduce<<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
       s->lay_dev(L), plan->tab.p, s->part64.p, s->tgt64.p, c);
   BIPB_LAUNCHED(s);
@@ -1015,16 +1020,18 @@ void grad_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const doubl
   constexpr int NT = 128, TPT = 1, CH = 32;
   std::vector<PassSys> sys(L.K);
   for (int k = 0; k < L.K; ++k) sys[k] = PassSys{L.chg_off[k], L.nc[k], L.vec_off[k] / 2, L.n[k]};
-  ItemPlan* plan = plan_pass<GradPolicy, double4_32a, NT, TPT, CH>(s, kPassGrad, sys, CH);
-  s->grow(s->rec64, (size_t)3 * L.len / 2);
+  ItemPlan* plan = plan_pass<GradPolicy, float4, NT, TPT, CH>(s, kPassGrad, sys, CH);
+  s->grow(s->recdf, (size_t)5 * L.len / 2);  // 5 float4 per element
   s->grow(s->part64, (size_t)plan->part_len);
   const int4* lay = s->lay_dev(L);
-  k_pack_grad<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, s->tgt64.p, u, lam, s->rec64.p);
+  k_pack_grad<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, s->tgt64.p, u, lam, s->recdf.p);
   BIPB_LAUNCHED(s);
-  GradPolicy::Args a{s->chg.p, s->part64.p, pair_const<double>(m)};
-  launch_items<GradPolicy, double4_32a, NT, TPT, CH>(s, kTGrad, plan, a, s->rec64.p, nullptr, 0);
+  const double inv = 1.0 / m.eps_in;
+  const float inv_hi = (float)inv;
+  GradPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(m), df{inv_hi, (float)(inv - (double)inv_hi)}};
+  launch_items<GradPolicy, float4, NT, TPT, CH>(s, kTGrad, plan, a, s->recdf.p, nullptr, 0);
   k_reduce_grad<<<dim3(blocks_for(L.max_nc, 256), L.K), 256, 0, s->stream>>>(plan->tab.p, lay, s->part64.p,
-                                                                              s->chg.p, 1.0 / m.eps_in, dq, dy);
+                                                                              s->chg.p, dq, dy);
   BIPB_LAUNCHED(s);
 }
 
