@@ -321,6 +321,8 @@ def run_configs(args):
             res["kernel_ms"] = {k: v[1] for k, v in t.items() if v[0]}
             res["iters_max"] = max(i["iters"] for i in info)
             res["refine_steps_max"] = max(i["refine_steps"] for i in info)
+            res["refine_steps_hist"] = {str(k): sum(1 for i in info if i["refine_steps"] == k)
+                                        for k in sorted({i["refine_steps"] for i in info})}
             res["rel_residual_max"] = max(i["rel_residual"] for i in info)
             emit(res)
     if "4b" in which:
