@@ -87,11 +87,12 @@ typedef struct {
 typedef struct {
   int converged;       /* 1 if rel_residual <= tol */
   int iters;           /* GMRES iterations (inner iterations for MIXED) */
-  int refine_steps;    /* MIXED: refinement steps taken (0 for FP64) */
-  int matvecs64;       /* FP64 mat-vecs applied to this right-hand side */
-  int matvecs32;       /* FP32 mat-vecs applied to this right-hand side */
+  int refine_steps;    /* mixed modes: refinement steps taken (0 for FP64 and DF64) */
+  int matvecs64;       /* FP64 or double-float mat-vecs applied to this right-hand side */
+  int matvecs32;       /* FP32 (or TF32) mat-vecs applied to this right-hand side */
   int reserved;
-  double rel_residual; /* final ||b - A u|| / ||b||, FP64 true residual */
+  double rel_residual; /* final ||b - A u|| / ||b||: the true residual, formed with the FP64 or
+                          double-float mat-vec and FP64 vector arithmetic */
   double seconds;      /* wall time of the whole bipb_solve call */
 } bipb_solve_info;
 
@@ -193,7 +194,8 @@ bipb_status bipb_energy_grad(bipb_surface s, const bipb_solve_params* p, double*
 bipb_status bipb_matvec(bipb_surface s, const bipb_medium* m, int precision, int transpose,
                         int n_vec, const double* u, double* y);
 
-/* b = [S1; S2] for every configuration: device, n_rhs x 2N doubles (FP64). */
+/* b = [S1; S2] for every configuration: device, n_rhs x 2N doubles (pair
+ * arithmetic in double-float, about 1e-14 relative; FP64 sums). */
 bipb_status bipb_source(bipb_surface s, const bipb_medium* m, double* b);
 
 /*
@@ -202,7 +204,8 @@ bipb_status bipb_source(bipb_surface s, const bipb_medium* m, double* b);
  *   phi_reac(y_k) = sum_j ds_j [K1(y_k, x_j) psi_j + K2(y_k, x_j) phi_j]
  * written to phi_reac (device, n_rhs x nc, internal units), and
  * e_sol (device, n_rhs, kcal/mol) = 4 pi 332.0716 * 1/2 sum_k q_k phi_reac(y_k).
- * Either output may be NULL.  FP64.
+ * Either output may be NULL.  Pair arithmetic in double-float (about 1e-14
+ * relative), FP64 sums in a fixed order.
  */
 bipb_status bipb_reaction(bipb_surface s, const bipb_medium* m, const double* u,
                           double* phi_reac, double* e_sol);
