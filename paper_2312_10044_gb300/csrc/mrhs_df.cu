@@ -1,14 +1,14 @@
 // Multi-right-hand-side mat-vec in double-float arithmetic (the refinement
 // residual of batched solves).
 //
-// Y = A U for up to 64 right-hand sides of one surface.  A CTA covers 64
-// targets and G groups of 16 right-hand sides (G = 1, 2 or 4, 64 G threads)
-// against one range of sources, staged 16 at a time in shared memory with
-// their right-hand-side values.  For every chunk the CTA first generates the
-// 2 x 2 kernel block of each (target, source) pair in df64 once (the K1..K4
-// of Sec. 2.2.1 times ds_j, df64.cuh; 16 / G pairs per thread) into shared
-// memory; then thread (group g, target t) applies the 16 blocks of its target
-// to the group's 16 right-hand sides with df64 multiply-adds.  The costly
+// Y = A U for up to 64 right-hand sides of one surface.  A CTA covers 32
+// targets and G groups of 8 right-hand sides (G = 1, 2, 4 or 8, 32 G
+// threads) against one range of sources, staged 16 at a time in shared
+// memory with their right-hand-side values.  For every chunk the CTA first
+// generates the 2 x 2 kernel block of each (target, source) pair in df64 once
+// (the K1..K4 of Sec. 2.2.1 times ds_j, df64.cuh; 16 / G pairs per thread)
+// into shared memory; then thread (group g, target t) applies the 16 blocks
+// of its target to the group's 8 right-hand sides with df64 multiply-adds.  The costly
 // generation is thus shared by all right-hand sides of the CTA, and a pass
 // over fewer right-hand sides (a refinement step in which most systems have
 // converged) uses fewer groups.  Partial sums per source split are written in
@@ -23,8 +23,8 @@ namespace bipb {
 namespace {
 
 constexpr int kNB = 64;     // right-hand sides per launch (at most)
-constexpr int kGB = 16;     // right-hand sides per group (per thread)
-constexpr int kTgt = 64;    // targets per CTA
+constexpr int kGB = 8;      // right-hand sides per group (per thread)
+constexpr int kTgt = 32;    // targets per CTA
 constexpr int kCh = 16;     // sources per shared-memory chunk
 
 // Dynamic shared memory of one CTA with G groups: kernel blocks (hi, lo),
@@ -37,7 +37,7 @@ constexpr int smem_bytes() {
 // items: {t0, s0, s1, split}; u: right-hand side b at rhs[b] * 2n (b * 2n when
 // rhs is null); part: [b][split][2n]
 template <int G>
-__global__ void __launch_bounds__(kTgt * G, 1) k_mrhs_df(int n, int nb, int n_splits, const int4* __restrict__ items,
+__global__ void __launch_bounds__(kTgt * G, 512 / (kTgt * G)) k_mrhs_df(int n, int nb, int n_splits, const int4* __restrict__ items,
                                                          const double4_32a* __restrict__ tgt64,
                                                          const double* __restrict__ u, const int* __restrict__ rhs,
                                                          double* __restrict__ part, DFConst c) {
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kTgt * G, 1) k_mrhs_df(int n, int nb, int n_sp
   extern __shared__ __align__(16) unsigned char smem[];
   float4* kbh = reinterpret_cast<float4*>(smem);           // [kCh][kTgt]: (K2, K1, K4, K3) ds, hi parts
   float4* kbl = kbh + kCh * kTgt;                           // lo parts
-  float4* ush = kbl + kCh * kTgt;                           // [16 G][kCh]: (phi.hi, phi.lo, psi.hi, psi.lo)
+  float4* ush = kbl + kCh * kTgt;                           // [8 G][kCh]: (phi.hi, phi.lo, psi.hi, psi.lo)
   float4* srec = ush + kGB * G * kCh;                       // [kCh][4]: x, n split as below
   df* tab = reinterpret_cast<df*>(srec + kCh * 4);          // 2^(j/32)
   const int tid = threadIdx.x;
@@ -145,6 +145,15 @@ int mrhs_df_occupancy() {
   return occ;
 }
 
+template <int G>
+void launch_mrhs_df(Surface* s, const ItemPlan* plan, int n, int nb, int S, const double* ub, const int* rhs,
+                    const DFConst& c) {
+  BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<G>()));
+  k_mrhs_df<G><<<plan->n_items, kTgt * G, smem_bytes<G>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p, ub, rhs,
+                                                                       s->part64.p, c);
+  BIPB_LAUNCHED(s);
+}
+
 // Work list of one group count: target tiles x source splits filling whole waves.
 ItemPlan* mrhs_df_plan(Surface* s, int n, int G, int slots, int* S_out) {
   const int tiles = (n + kTgt - 1) / kTgt;
@@ -198,9 +207,11 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
   const int n_act = (int)act.size();
   for (int g0 = 0; g0 < n_act; g0 += kNB) {
     const int nb = std::min(kNB, n_act - g0);
-    const int G = nb <= kGB ? 1 : (nb <= 2 * kGB ? 2 : 4);
-    const int slots = s->num_sms * (G == 1 ? mrhs_df_occupancy<1>() : G == 2 ? mrhs_df_occupancy<2>()
-                                                                             : mrhs_df_occupancy<4>());
+    const int G = nb <= kGB ? 1 : nb <= 2 * kGB ? 2 : nb <= 4 * kGB ? 4 : 8;
+    const int slots = s->num_sms * (G == 1   ? mrhs_df_occupancy<1>()
+                                    : G == 2 ? mrhs_df_occupancy<2>()
+                                    : G == 4 ? mrhs_df_occupancy<4>()
+                                             : mrhs_df_occupancy<8>());
     int S = 1;
     ItemPlan* plan = mrhs_df_plan(s, n, G, slots, &S);
     s->grow(s->part64, (size_t)nb * S * 2 * n);
@@ -241,25 +252,16 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
       rhs = s->rhs_idx.p;
       ub = u;
     }
-    // the 4-group kernel needs more than the default 48 KB of dynamic shared memory
-    if (G == 1)
-      BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>()));
-    else if (G == 2)
-      BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>()));
-    else
-      BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<4>()));
     {
       TimedLaunch tl(s, kTMvDF);
       if (G == 1)
-        k_mrhs_df<1><<<plan->n_items, kTgt, smem_bytes<1>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p, ub,
-                                                                          rhs, s->part64.p, c);
+        launch_mrhs_df<1>(s, plan, n, nb, S, ub, rhs, c);
       else if (G == 2)
-        k_mrhs_df<2><<<plan->n_items, 2 * kTgt, smem_bytes<2>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p,
-                                                                              ub, rhs, s->part64.p, c);
+        launch_mrhs_df<2>(s, plan, n, nb, S, ub, rhs, c);
+      else if (G == 4)
+        launch_mrhs_df<4>(s, plan, n, nb, S, ub, rhs, c);
       else
-        k_mrhs_df<4><<<plan->n_items, 4 * kTgt, smem_bytes<4>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p,
-                                                                              ub, rhs, s->part64.p, c);
-      BIPB_LAUNCHED(s);
+        launch_mrhs_df<8>(s, plan, n, nb, S, ub, rhs, c);
     }
     launch_reduce_matvec64(s, Lb, tt->second->tab.p, s->part64.p, u, y, dphi, dpsi, nullptr, 0);
   }
