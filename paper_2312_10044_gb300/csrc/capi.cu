@@ -191,22 +191,19 @@ void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::v
   }
   for (int k = 0; k < 3; ++k) c[k] /= (double)P.n;
   // duplicates of the centred centroids, in FP64 and after rounding to FP32
-  // (sorted keys; the FP64 ones are kept to reject charges on a centroid)
-  std::vector<std::array<uint64_t, 3>> k64((size_t)P.n), k32((size_t)P.n);
+  // (the FP64 set is kept to reject charges on a centroid)
+  KeySet k64, k32;
+  k64.reserve((size_t)P.n);
+  k32.reserve((size_t)P.n);
   for (int64_t i = 0; i < P.n; ++i) {
     double d[3], f[3];
     for (int k = 0; k < 3; ++k) {
       d[k] = P.c[3 * i + k] - c[k];
       f[k] = (double)(float)d[k];
     }
-    k64[i] = key_of(d);
-    k32[i] = key_of(f);
+    BIPB_REQUIRE(k64.insert(key_of(d)), "two centroids coincide");
+    BIPB_REQUIRE(k32.insert(key_of(f)), "two centroids coincide after rounding to FP32");
   }
-  std::sort(k64.begin(), k64.end());
-  std::sort(k32.begin(), k32.end());
-  BIPB_REQUIRE(std::adjacent_find(k64.begin(), k64.end()) == k64.end(), "two centroids coincide");
-  BIPB_REQUIRE(std::adjacent_find(k32.begin(), k32.end()) == k32.end(),
-               "two centroids coincide after rounding to FP32");
   s->part_keys.push_back(std::move(k64));
   s->part_off.push_back((int)s->n);
   s->part_n.push_back((int)P.n);
@@ -270,7 +267,7 @@ bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream,
 }
 
 // Charge records of one system, centred like its surface; rejects charges on
-// a centroid (binary search in the surface's sorted centred centroid keys).
+// a centroid (lookup in the surface's set of centred centroid keys).
 void append_charges(Surface* s, int part, int64_t nc, const double* pos, const double* q,
                     std::vector<double4_32a>& rec) {
   const double* c = &s->part_center[3 * part];
@@ -279,7 +276,7 @@ void append_charges(Surface* s, int part, int64_t nc, const double* pos, const d
     BIPB_REQUIRE(finite3(pos + 3 * k), "non-finite charge position");
     BIPB_REQUIRE(std::isfinite(q[k]), "non-finite charge");
     double p[3] = {pos[3 * k] - c[0], pos[3 * k + 1] - c[1], pos[3 * k + 2] - c[2]};
-    BIPB_REQUIRE(!std::binary_search(keys.begin(), keys.end(), key_of(p)), "a charge sits on a centroid");
+    BIPB_REQUIRE(!keys.contains(key_of(p)), "a charge sits on a centroid");
     rec.push_back(make_double4_32a(p[0], p[1], p[2], q[k]));
   }
 }

@@ -77,6 +77,47 @@ struct DevBuf {
   ~DevBuf() { release(); }
 };
 
+// Set of 3-component bit patterns (centroid coordinates) with open addressing:
+// one flat table of indices, linear probing, no per-key allocation.
+struct KeySet {
+  std::vector<std::array<uint64_t, 3>> keys;
+  std::vector<int32_t> slot;  // index into keys, or -1
+  uint64_t mask = 0;
+  static uint64_t mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+  }
+  static uint64_t hash(const std::array<uint64_t, 3>& k) { return mix(k[0] ^ mix(k[1] ^ mix(k[2]))); }
+  void reserve(size_t n) {
+    size_t sz = 16;
+    while (sz < 2 * n) sz <<= 1;
+    slot.assign(sz, -1);
+    mask = sz - 1;
+    keys.reserve(n);
+  }
+  // false if k is already present
+  bool insert(const std::array<uint64_t, 3>& k) {
+    for (uint64_t h = hash(k) & mask;; h = (h + 1) & mask) {
+      const int32_t i = slot[h];
+      if (i < 0) {
+        slot[h] = (int32_t)keys.size();
+        keys.push_back(k);
+        return true;
+      }
+      if (keys[i] == k) return false;
+    }
+  }
+  bool contains(const std::array<uint64_t, 3>& k) const {
+    if (slot.empty()) return false;
+    for (uint64_t h = hash(k) & mask;; h = (h + 1) & mask) {
+      const int32_t i = slot[h];
+      if (i < 0) return false;
+      if (keys[i] == k) return true;
+    }
+  }
+};
+
 // K independent systems handled by one batched pass (several right-hand
 // sides of one surface, or several surfaces).  System k has n[k] elements
 // starting at geometry element geo_off[k], 2 n[k] unknowns starting at
@@ -202,7 +243,7 @@ struct Surface {
   // batch handle, one system each): element offsets, sizes, centres
   std::vector<int> part_off, part_n;
   std::vector<double> part_center;  // 3 per surface
-  std::vector<std::vector<std::array<uint64_t, 3>>> part_keys;  // sorted bit patterns of the centred centroids
+  std::vector<KeySet> part_keys;  // bit patterns of the centred centroids, per surface
   bool batch = false;
 
   // cached work lists and device copies of layouts (keyed by content)

@@ -65,7 +65,7 @@ def geom():
 
 
 @pytest.mark.parametrize("case", ["nan_centroid", "zero_area", "neg_area", "bad_normal", "duplicate", "too_small",
-                                  "inf_normal"])
+                                  "inf_normal", "duplicate_fp32"])
 def test_create_rejects_bad_geometry(bipb, geom, case):
     c, n, a = (v.copy() for v in geom)
     if case == "nan_centroid":
@@ -82,10 +82,15 @@ def test_create_rejects_bad_geometry(bipb, geom, case):
         c, n, a = c[:1], n[:1], a[:1]
     elif case == "inf_normal":
         n[4, 0] = np.inf
+    elif case == "duplicate_fp32":
+        # distinct in FP64, equal once rounded to the FP32 working copy
+        c[5] = c[9] + 1e-9
     st, h, msg = _create(bipb, c, n, a)
     assert st == bipb.BIPB_ERR_INVALID_ARG, msg
     assert h.value is None
     assert msg
+    if case == "duplicate_fp32":
+        assert "FP32" in msg
 
 
 def test_null_and_stale_handles_are_rejected(bipb):
