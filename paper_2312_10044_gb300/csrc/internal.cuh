@@ -230,6 +230,8 @@ struct Surface {
   DevBuf<float> part32;
   DevBuf<double> part64;
   DevBuf<int> rhs_idx;  // right-hand-side indices of a compacted multi-RHS pass
+  DevBuf<float4> geodf;  // multi-RHS df64 pass: geometry as df64 records (4 float4 each)
+  DevBuf<float4> udf;    // multi-RHS df64 pass: right-hand sides as df64 (phi, psi) pairs
 
   // charges: every system's charge records (y - center, q), back to back
   int64_t nc = 0;  // charges per configuration (single surface)

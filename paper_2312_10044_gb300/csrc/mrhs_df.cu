@@ -27,6 +27,34 @@ constexpr int kGB = 8;      // right-hand sides per group (per thread)
 constexpr int kTgt = 32;    // targets per CTA
 constexpr int kCh = 16;     // sources per shared-memory chunk
 
+// Double-float copies made once per pass, so that the hot loop stages plain
+// float4 records and never converts from FP64 (GB300 runs FP64 and its
+// conversions at a small fraction of the FP32 rate):
+//   geo[4 j .. 4 j + 3] = (x.hi, a.hi), (x.lo, a.lo), (n.hi, 0), (n.lo, 0) of element j
+//     (x the centred centroid as a 3-vector, a = ds_j, n the normal);
+//   u4[b n + j] = (phi.hi, phi.lo, psi.hi, psi.lo) of right-hand side b (the
+//     rhs[b]-th of u when rhs is given), element j.
+// blockIdx.y < nb packs right-hand side blockIdx.y, blockIdx.y == nb the geometry.
+__global__ void k_pack_mrhs_df(int n, int nb, const double4_32a* __restrict__ tgt64, const double* __restrict__ u,
+                               const int* __restrict__ rhs, float4* __restrict__ geo, float4* __restrict__ u4) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int b = blockIdx.y;
+  if (b < nb) {
+    const double* ub = u + (int64_t)(rhs ? rhs[b] : b) * 2 * n;
+    const df p = df_from_double(ub[j]), q = df_from_double(ub[n + j]);
+    u4[(int64_t)b * n + j] = make_float4(p.hi, p.lo, q.hi, q.lo);
+    return;
+  }
+  const double4_32a g = tgt64[2 * j], v = tgt64[2 * j + 1];
+  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z), a = df_from_double(g.w);
+  const df n0 = df_from_double(v.x), n1 = df_from_double(v.y), n2 = df_from_double(v.z);
+  geo[4 * j] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
+  geo[4 * j + 1] = make_float4(x0.lo, x1.lo, x2.lo, a.lo);
+  geo[4 * j + 2] = make_float4(n0.hi, n1.hi, n2.hi, 0.f);
+  geo[4 * j + 3] = make_float4(n0.lo, n1.lo, n2.lo, 0.f);
+}
+
 // Dynamic shared memory of one CTA with G groups: kernel blocks (hi, lo),
 // right-hand-side values, source records, exp table.
 template <int G>
@@ -34,13 +62,12 @@ constexpr int smem_bytes() {
   return 2 * kCh * kTgt * 16 + kGB * G * kCh * 16 + kCh * 4 * 16 + 32 * 8;
 }
 
-// items: {t0, s0, s1, split}; u: right-hand side b at rhs[b] * 2n (b * 2n when
-// rhs is null); part: [b][split][2n]
+// items: {t0, s0, s1, split}; geo, u4: the packed records of k_pack_mrhs_df;
+// part: [b][split][2n]
 template <int G>
-__global__ void __launch_bounds__(kTgt * G, 512 / (kTgt * G)) k_mrhs_df(int n, int nb, int n_splits, const int4* __restrict__ items,
-                                                         const double4_32a* __restrict__ tgt64,
-                                                         const double* __restrict__ u, const int* __restrict__ rhs,
-                                                         double* __restrict__ part, DFConst c) {
+__global__ void __launch_bounds__(kTgt * G, 512 / (kTgt * G))
+    k_mrhs_df(int n, int nb, int n_splits, const int4* __restrict__ items, const float4* __restrict__ geo,
+              const float4* __restrict__ u4, double* __restrict__ part, DFConst c) {
   constexpr int NT = kTgt * G;
   extern __shared__ __align__(16) unsigned char smem[];
   float4* kbh = reinterpret_cast<float4*>(smem);           // [kCh][kTgt]: (K2, K1, K4, K3) ds, hi parts
@@ -57,9 +84,10 @@ __global__ void __launch_bounds__(kTgt * G, 512 / (kTgt * G)) k_mrhs_df(int n, i
   const bool tvalid = ti < n;
   df xi[3], ni[3];
   {
-    const double4_32a gi = tgt64[2 * min(ti, n - 1)], vi = tgt64[2 * min(ti, n - 1) + 1];
-    xi[0] = df_from_double(gi.x), xi[1] = df_from_double(gi.y), xi[2] = df_from_double(gi.z);
-    ni[0] = df_from_double(vi.x), ni[1] = df_from_double(vi.y), ni[2] = df_from_double(vi.z);
+    const int64_t r = 4 * (int64_t)min(ti, n - 1);
+    const float4 A = geo[r], B = geo[r + 1], C = geo[r + 2], D = geo[r + 3];
+    xi[0] = df{A.x, B.x}, xi[1] = df{A.y, B.y}, xi[2] = df{A.z, B.z};
+    ni[0] = df{C.x, D.x}, ni[1] = df{C.y, D.y}, ni[2] = df{C.z, D.z};
   }
   df accp[kGB], accq[kGB];
 #pragma unroll
@@ -68,25 +96,11 @@ __global__ void __launch_bounds__(kTgt * G, 512 / (kTgt * G)) k_mrhs_df(int n, i
   for (int j0 = s0; j0 < s1; j0 += kCh) {
     const int cnt = min(kCh, s1 - j0);
     __syncthreads();  // the previous chunk's blocks and values have been used
-    if (tid < cnt) {
-      const double4_32a gj = tgt64[2 * (j0 + tid)], vj = tgt64[2 * (j0 + tid) + 1];
-      const df x0 = df_from_double(gj.x), x1 = df_from_double(gj.y), x2 = df_from_double(gj.z);
-      const df n0 = df_from_double(vj.x), n1 = df_from_double(vj.y), n2 = df_from_double(vj.z);
-      const df a = df_from_double(gj.w);
-      srec[4 * tid] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
-      srec[4 * tid + 1] = make_float4(x0.lo, x1.lo, x2.lo, a.lo);
-      srec[4 * tid + 2] = make_float4(n0.hi, n1.hi, n2.hi, 0.f);
-      srec[4 * tid + 3] = make_float4(n0.lo, n1.lo, n2.lo, 0.f);
-    }
-    // right-hand-side values, e = (b * 2 + comp) * cnt + q (q fastest: coalesced reads,
-    // consecutive shared-memory words)
-    for (int e = tid; e < kGB * G * 2 * cnt; e += NT) {
-      const int q = e % cnt, bc = e / cnt, b = bc >> 1, comp = bc & 1;
-      const double v = b < nb ? u[(int64_t)(rhs ? rhs[b] : b) * 2 * n + (int64_t)comp * n + j0 + q] : 0.0;
-      const df d = df_from_double(v);
-      float* dst = reinterpret_cast<float*>(&ush[b * kCh + q]) + 2 * comp;
-      dst[0] = d.hi;
-      dst[1] = d.lo;
+    for (int e = tid; e < 4 * cnt; e += NT) srec[e] = geo[4 * (int64_t)j0 + e];
+    // right-hand-side values, e = b * cnt + q (q fastest: coalesced reads)
+    for (int e = tid; e < kGB * G * cnt; e += NT) {
+      const int q = e % cnt, b = e / cnt;
+      ush[b * kCh + q] = b < nb ? u4[(int64_t)b * n + j0 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     // kernel blocks of (target tl, source q) for q = g, g + G, ...
@@ -146,11 +160,10 @@ int mrhs_df_occupancy() {
 }
 
 template <int G>
-void launch_mrhs_df(Surface* s, const ItemPlan* plan, int n, int nb, int S, const double* ub, const int* rhs,
-                    const DFConst& c) {
+void launch_mrhs_df(Surface* s, const ItemPlan* plan, int n, int nb, int S, const DFConst& c) {
   BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_df<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<G>()));
-  k_mrhs_df<G><<<plan->n_items, kTgt * G, smem_bytes<G>(), s->stream>>>(n, nb, S, plan->items.p, s->tgt64.p, ub, rhs,
-                                                                       s->part64.p, c);
+  k_mrhs_df<G><<<plan->n_items, kTgt * G, smem_bytes<G>(), s->stream>>>(n, nb, S, plan->items.p, s->geodf.p,
+                                                                       s->udf.p, s->part64.p, c);
   BIPB_LAUNCHED(s);
 }
 
@@ -252,16 +265,21 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
       rhs = s->rhs_idx.p;
       ub = u;
     }
+    s->grow(s->geodf, (size_t)4 * n);
+    s->grow(s->udf, (size_t)nb * n);
+    k_pack_mrhs_df<<<dim3((n + 255) / 256, nb + 1), 256, 0, s->stream>>>(n, nb, s->tgt64.p, ub, rhs, s->geodf.p,
+                                                                          s->udf.p);
+    BIPB_LAUNCHED(s);
     {
       TimedLaunch tl(s, kTMvDF);
       if (G == 1)
-        launch_mrhs_df<1>(s, plan, n, nb, S, ub, rhs, c);
+        launch_mrhs_df<1>(s, plan, n, nb, S, c);
       else if (G == 2)
-        launch_mrhs_df<2>(s, plan, n, nb, S, ub, rhs, c);
+        launch_mrhs_df<2>(s, plan, n, nb, S, c);
       else if (G == 4)
-        launch_mrhs_df<4>(s, plan, n, nb, S, ub, rhs, c);
+        launch_mrhs_df<4>(s, plan, n, nb, S, c);
       else
-        launch_mrhs_df<8>(s, plan, n, nb, S, ub, rhs, c);
+        launch_mrhs_df<8>(s, plan, n, nb, S, c);
     }
     launch_reduce_matvec64(s, Lb, tt->second->tab.p, s->part64.p, u, y, dphi, dpsi, nullptr, 0);
   }
