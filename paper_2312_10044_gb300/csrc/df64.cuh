@@ -56,7 +56,18 @@ __device__ __forceinline__ df df_add(df x, df y) {
   s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
   return fast_two_sum(s.hi, s.lo);
 }
+// x + y when the exponent of x.hi is at least that of y.hi (FastTwoSum of
+// the leading parts is then exact), e.g. 1 - e for 0 < e <= 1.
+__device__ __forceinline__ df df_add_ordered(df x, df y) {
+  df s = fast_two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ df df_neg(df x) { return df{-x.hi, -x.lo}; }
+// 1 - e for 0 <= e <= 1 (e = exp(-kappa r)), and t - 1 for 0 <= t <= 1
+// (t = e (1 + kappa r)): the exponent of 1 is the larger one.
+__device__ __forceinline__ df df_one_minus(df e) { return df_add_ordered(df{1.0f, 0.0f}, df_neg(e)); }
+__device__ __forceinline__ df df_minus_one(df t) { return df_add_ordered(df{-1.0f, 0.0f}, t); }
 __device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
 // x + f for a float f
 __device__ __forceinline__ df df_add_f(df x, float f) {
@@ -152,9 +163,9 @@ __device__ __forceinline__ df df_exp_neg(df x, const DFConst& c, const df* tab) 
   const float fh = f.hi;
   const float tail = __fmul_rn(__fmul_rn(__fmul_rn(fh, fh), fh),
                                __fmaf_rn(fh, __fmaf_rn(fh, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f));
-  df em1 = df_add(f, h2);
+  df em1 = df_add_ordered(f, h2);  // |f^2 / 2| < |f|
   em1 = fast_two_sum(em1.hi, __fadd_rn(em1.lo, tail));
-  df ef = two_sum(1.0f, em1.hi);
+  df ef = fast_two_sum(1.0f, em1.hi);  // |exp(f) - 1| < 1
   ef = fast_two_sum(ef.hi, __fadd_rn(ef.lo, em1.lo));
   const df t = tab[k & 31];
   df r = df_mul(ef, t);
@@ -178,11 +189,11 @@ __device__ __forceinline__ void df_pair_forward(const df* xi, const df* ni, cons
   const df cm = df_dot3(m[0], m[1], m[2], dx, dy, dz);
   const df cim = df_dot3(ni[0], ni[1], ni[2], m[0], m[1], m[2]);
   const df t = df_add(df_mul(e, kr), e);                           // e (1 + kr)
-  const df tm1 = df_add_f(t, -1.0f);                               // t - 1
+  const df tm1 = df_minus_one(t);                               // t - 1
   const df wm3 = df_add(df_mul(df_sub(t, e), kr), df_mul_f(tm1, 3.0f));  // w - 3 = 3 (t - 1) + (t - e) kr
   const df s2 = df_sqr(s);
   // P = s [ (1 - e) a + (eps t - 1) cm s^2 ]
-  const df ome = df_add_f(df_neg(e), 1.0f);
+  const df ome = df_one_minus(e);
   df p = df_mul(ome, a);
   p = df_add(p, df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cm), s2));
   accP = df_add(accP, df_mul(p, s));
@@ -209,7 +220,7 @@ __device__ __forceinline__ void df_pair_transpose(const df* xj, const df* nj, co
   const df cp = df_dot3(pv[0], pv[1], pv[2], dx, dy, dz);
   const df cnp = df_dot3(nj[0], nj[1], nj[2], pv[0], pv[1], pv[2]);
   const df t = df_add(df_mul(e, kr), e);
-  const df tm1 = df_add_f(t, -1.0f);
+  const df tm1 = df_minus_one(t);
   const df wm3 = df_add(df_mul(df_sub(t, e), kr), df_mul_f(tm1, 3.0f));
   const df s2 = df_sqr(s);
   // Zphi = s^3 [ (eps t - 1) c_j wphi + (t - 1)(n_j.p) - (w - 3)(p.d) c_j s^2 ]
@@ -218,7 +229,7 @@ __device__ __forceinline__ void df_pair_transpose(const df* xj, const df* nj, co
   q = df_sub(q, df_mul(wm3, df_mul(df_mul(cp, cj), s2)));
   accP = df_add(accP, df_mul(q, df_mul(s2, s)));
   // Zpsi = s [ (1 - e) wphi + (t/eps - 1)(p.d) s^2 ]
-  df p = df_mul(df_add_f(df_neg(e), 1.0f), wphi);
+  df p = df_mul(df_one_minus(e), wphi);
   p = df_add(p, df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), cp), s2));
   accQ = df_add(accQ, df_mul(p, s));
 }
@@ -245,12 +256,12 @@ __device__ __forceinline__ void df_kernel_block(const df* xi, const df* ni, cons
   const df cj = df_dot3(nj[0], nj[1], nj[2], dx, dy, dz);
   const df cij = df_dot3(ni[0], ni[1], ni[2], nj[0], nj[1], nj[2]);
   const df t = df_add(df_mul(e, kr), e);
-  const df tm1 = df_add_f(t, -1.0f);
+  const df tm1 = df_minus_one(t);
   const df wm3 = df_add(df_mul(df_sub(t, e), kr), df_mul_f(tm1, 3.0f));
   const df sa = df_mul(s, area);
   const df s2 = df_sqr(s);
   const df s3a = df_mul(s2, sa);
-  k[1] = df_mul(df_add_f(df_neg(e), 1.0f), sa);                                     // K1 ds
+  k[1] = df_mul(df_one_minus(e), sa);                                     // K1 ds
   k[0] = df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cj), s3a);                // K2 ds
   k[3] = df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), ci), s3a);             // K3 ds
   k[2] = df_mul(df_sub(df_mul(tm1, cij), df_mul(wm3, df_mul(df_mul(ci, cj), s2))), s3a);  // K4 ds
@@ -283,11 +294,11 @@ __device__ __forceinline__ void df_sym_pair(const df* d, const df* nt, df at, df
   const df e = df_exp_neg(df_neg(kr), c, tab);
   const df ekr = df_mul(e, kr);
   const df t = df_add(ekr, e);
-  const df tm1 = df_add_f(t, -1.0f);
+  const df tm1 = df_minus_one(t);
   const df s2 = df_sqr(s);
   const df s3 = df_mul(s2, s);
   const df wm3s2 = df_mul(df_add(df_mul(ekr, kr), df_mul_f(tm1, 3.0f)), s2);
-  const df ome = df_add_f(df_neg(e), 1.0f);
+  const df ome = df_one_minus(e);
   const df et1 = df_add_f(df_mul(c.eps, t), -1.0f), te1 = df_add_f(df_mul(t, c.inveps), -1.0f);
   const df ci = df_dot3(nt[0], nt[1], nt[2], d[0], d[1], d[2]);
   const df cj = df_dot3(ns[0], ns[1], ns[2], d[0], d[1], d[2]);
@@ -343,7 +354,7 @@ __device__ __forceinline__ void df_reaction_pair(const df* y, const df* x, df a,
   const df e = df_exp_neg(df_neg(kr), c, tab);
   const df t = df_add(df_mul(e, kr), e);
   const df cm = df_dot3(m[0], m[1], m[2], d0, d1, d2);
-  df p = df_mul(df_add_f(df_neg(e), 1.0f), a);
+  df p = df_mul(df_one_minus(e), a);
   p = df_add(p, df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cm), df_sqr(s)));
   acc = df_add(acc, df_mul(p, s));
 }
@@ -365,7 +376,7 @@ __device__ __forceinline__ void df_energy_row_pair(const df* x, const df* nv, co
   const df cj = df_dot3(nv[0], nv[1], nv[2], d0, d1, d2);
   const df s3 = df_mul(df_sqr(s), s);
   df_mac(cphi, df_mul(df_mul(q, df_add_f(df_mul(c.eps, t), -1.0f)), cj), s3);
-  df_mac(cpsi, df_mul(q, df_add_f(df_neg(e), 1.0f)), s);
+  df_mac(cpsi, df_mul(q, df_one_minus(e)), s);
 }
 
 // Energy gradient at a charge y from one element in df64.  Element record:
@@ -394,10 +405,10 @@ __device__ __forceinline__ void df_grad_pair(const df* y, const df* x, df a, con
   const df acn_s2 = df_mul(df_mul(al, cn), s2);
   const df bcn_s2 = df_mul(df_mul(beta, cn), s2);
   // potential at y and the adjoint-weighted source
-  df_mac(v, df_add(df_mul(df_add_f(df_neg(e), 1.0f), a), df_mul(et1, acn_s2)), s);
+  df_mac(v, df_add(df_mul(df_one_minus(e), a), df_mul(et1, acn_s2)), s);
   df_mac(v, df_mul(inv, df_add(lphi, bcn_s2)), s);
   const df Cn = df_mul(df_add(df_mul(et1, al), df_mul(inv, beta)), s3);
-  const df Cd = df_mul(df_sub(df_sub(df_mul(df_add_f(t, -1.0f), a),
+  const df Cd = df_mul(df_sub(df_sub(df_mul(df_minus_one(t), a),
                                      df_mul(df_add_f(df_mul(c.eps, w), -3.0f), acn_s2)),
                               df_mul(inv, df_add(lphi, df_mul_f(bcn_s2, 3.0f)))),
                        s3);

@@ -45,6 +45,8 @@ struct DevState {
   double bnorm;  // norm of the right-hand side of this call
   double beta;   // norm of the current cycle's start residual
   double est;    // latest |g_k| / bnorm
+  int arrive;    // blocks of this system done with the current normalisation step
+  int pad_;
 };
 constexpr int kStateInts = (int)(sizeof(DevState) / sizeof(int));
 static_assert(offsetof(DevState, skip) == sizeof(int), "skip must be the second int");
@@ -84,10 +86,8 @@ __device__ __forceinline__ double warp_sum_parts(const double* __restrict__ part
 }
 
 // part[b * m1 + i] = V_i . w over block b's range, i <= j (warp i % 8 takes vector i)
-__global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V, const double* __restrict__ w,
-                       double* __restrict__ part, const DevState* st, const int4* __restrict__ blk) {
-  const int4 B = blk[blockIdx.x];
-  if (st[B.x].skip) return;
+__device__ __forceinline__ void block_dots(int j, int m1, int64_t len, const double* __restrict__ V,
+                                           const double* w, double* __restrict__ part, int4 B) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i <= j; i += kBS / 32) {
     const double* v = V + (size_t)i * len;
@@ -98,12 +98,21 @@ __global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V,
   }
 }
 
+__global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V, const double* __restrict__ w,
+                       double* __restrict__ part, const DevState* st, const int4* __restrict__ blk) {
+  const int4 B = blk[blockIdx.x];
+  if (st[B.x].skip) return;
+  block_dots(j, m1, len, V, w, part, B);
+}
+
 // h_i = sum over the system's blocks of part[.][i]; w -= sum_i h_i V_i; H[:, j] (+)= h;
-// with want_norm, also part1[b] = sum of the updated w^2 over block b's range.
+// with want_norm, also part1[b] = sum of the updated w^2 over block b's range;
+// with part_next, also the block's dot products of the updated w for the
+// second Gram-Schmidt pass (block-local, so they need no extra launch).
 __global__ void k_orth(int j, int m, int64_t len, const double* __restrict__ V, double* __restrict__ w,
                        const double* __restrict__ part, double* __restrict__ H, int accumulate, const DevState* st,
                        const int4* __restrict__ blk, const int4* __restrict__ sysb, double* __restrict__ part1,
-                       int want_norm) {
+                       int want_norm, double* __restrict__ part_next) {
   const int4 B = blk[blockIdx.x];
   if (st[B.x].skip) return;
   const int m1 = m + 1;
@@ -130,6 +139,10 @@ __global__ void k_orth(int j, int m, int64_t len, const double* __restrict__ V, 
     ss = block_sum(ss);
     if (threadIdx.x == 0) part1[blockIdx.x] = ss;
   }
+  if (part_next != nullptr) {
+    __syncthreads();  // the block's updated w is visible to all its threads
+    block_dots(j, m1, len, V, w, part_next, B);
+  }
 }
 
 // part1[b] = sum of w^2 over block b's range (mode 0: systems not skipped,
@@ -144,40 +157,10 @@ __global__ void k_sumsq(const double* __restrict__ w, double* __restrict__ part1
   if (threadIdx.x == 0) part1[blockIdx.x] = acc;
 }
 
-// out = w / ||w|| per system; j >= 0: H[j+1, j] = ||w||; j < 0: start of a
-// cycle, beta = ||w|| (and bnorm = ||w|| if set_bnorm).
-__global__ void k_normalize(int j, int m, const double* __restrict__ w, double* __restrict__ out,
-                            const double* __restrict__ part1, double* __restrict__ H, DevState* st,
-                            const int4* __restrict__ blk, const int4* __restrict__ sysb, int set_bnorm) {
-  const int4 B = blk[blockIdx.x];
-  if (j >= 0 ? st[B.x].skip : !st[B.x].active) return;
-  const int4 S = sysb[B.x];
-  __shared__ double nrm;
-  if (threadIdx.x < 32) {
-    const double s = warp_sum_parts(part1, 1, 0, S.x, S.y);
-    if (threadIdx.x == 0) nrm = sqrt(s);
-  }
-  __syncthreads();
-  const double v = nrm;
-  const double inv = v > 0.0 ? 1.0 / v : 0.0;
-  for (int x = B.y + threadIdx.x; x < B.z; x += kBS) out[x] = w[x] * inv;
-  if ((int)blockIdx.x == S.x && threadIdx.x == 0) {
-    if (j >= 0) {
-      H[(size_t)B.x * (m + 1) * m + (size_t)j * (m + 1) + j + 1] = v;
-    } else {
-      if (set_bnorm) st[B.x].bnorm = v;
-      st[B.x].beta = v;
-    }
-  }
-}
-
 // Per system: apply earlier rotations to column j, make rotation j, update g, test.
-__global__ void k_givens(int j, int m, int K, double* __restrict__ H, double* __restrict__ cs,
-                         double* __restrict__ sn, double* __restrict__ g, DevState* st) {
-  const int sys = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sys >= K) return;
+__device__ void givens_step(int j, int m, int sys, double* __restrict__ H, double* __restrict__ cs,
+                            double* __restrict__ sn, double* __restrict__ g, DevState* st) {
   DevState& S = st[sys];
-  if (S.skip) return;
   const int m1 = m + 1;
   double* h = H + (size_t)sys * m1 * m + (size_t)j * m1;
   double* c_ = cs + (size_t)sys * m;
@@ -203,6 +186,43 @@ __global__ void k_givens(int j, int m, int K, double* __restrict__ H, double* __
   if (S.est <= S.tol || b == 0.0) S.conv = 1;
   if (S.iters >= S.max_iter) S.stop = 1;
   if (S.conv || S.stop || j + 1 == S.m) S.skip = 1;
+}
+
+// out = w / ||w|| per system; j >= 0: H[j+1, j] = ||w|| and the Givens step of
+// column j, both by the last block of the system to finish (every block has
+// then passed its skip test, so the step may set skip; the blocks' arrival
+// is counted with an atomic after a fence, no block waits); j < 0: start of
+// a cycle, beta = ||w|| (and bnorm = ||w|| if set_bnorm).
+__global__ void k_normalize(int j, int m, const double* __restrict__ w, double* __restrict__ out,
+                            const double* __restrict__ part1, double* __restrict__ H, DevState* st,
+                            const int4* __restrict__ blk, const int4* __restrict__ sysb, int set_bnorm,
+                            double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g) {
+  const int4 B = blk[blockIdx.x];
+  if (j >= 0 ? st[B.x].skip : !st[B.x].active) return;
+  const int4 S = sysb[B.x];
+  __shared__ double nrm;
+  if (threadIdx.x < 32) {
+    const double s = warp_sum_parts(part1, 1, 0, S.x, S.y);
+    if (threadIdx.x == 0) nrm = sqrt(s);
+  }
+  __syncthreads();
+  const double v = nrm;
+  const double inv = v > 0.0 ? 1.0 / v : 0.0;
+  for (int x = B.y + threadIdx.x; x < B.z; x += kBS) out[x] = w[x] * inv;
+  if (threadIdx.x != 0) return;
+  if (j < 0) {
+    if ((int)blockIdx.x == S.x) {
+      if (set_bnorm) st[B.x].bnorm = v;
+      st[B.x].beta = v;
+    }
+    return;
+  }
+  __threadfence();
+  if (atomicAdd(&st[B.x].arrive, 1) != S.y - S.x - 1) return;
+  __threadfence();
+  st[B.x].arrive = 0;
+  H[(size_t)B.x * (m + 1) * m + (size_t)j * (m + 1) + j + 1] = v;
+  givens_step(j, m, B.x, H, cs, sn, g, st);
 }
 
 // Per system: least squares R y = g (k x k) and the restart coefficients
@@ -308,7 +328,7 @@ struct GmresWork {
   uint64_t lay_key = 0;
   int m = 0, K = 0, nblk = 0;
   int64_t len = 0;
-  DevBuf<double> V, w, H, cs, sn, g, y, z, part, part1, r, d, t;
+  DevBuf<double> V, w, H, cs, sn, g, y, z, part, part2, part1, r, d, t;
   DevBuf<int4> blk, sysb;
   DevBuf<int> mask;  // per system: 1 = leave out of the FP64 residual
   std::vector<int4> sysb_host;
@@ -374,6 +394,7 @@ GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
   w->y.ensure((size_t)L.K * m, s->stream);
   w->z.ensure((size_t)L.K * (m + 1), s->stream);
   w->part.ensure((size_t)w->nblk * (m + 1), s->stream);
+  w->part2.ensure((size_t)w->nblk * (m + 1), s->stream);
   w->part1.ensure(w->nblk, s->stream);
   w->blk.ensure(blk.size(), s->stream);
   w->sysb.ensure(L.K, s->stream);
@@ -399,17 +420,18 @@ void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium
   for (int j = 0; j < m; ++j) {
     double* vj = w->V.p + (size_t)j * len;
     matvec(s, L, med, precision, transpose, vj, w->w.p, &w->st->skip, kStateInts);
-    for (int pass = 0; pass < 2; ++pass) {  // CGS2; the second pass also forms the block norms
-      k_dots<<<nb, kBS, 0, s->stream>>>(j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
-      BIPB_LAUNCHED(s);
-      k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, pass, w->st, w->blk.p,
-                                        w->sysb.p, w->part1.p, pass);
-      BIPB_LAUNCHED(s);
-    }
-    k_normalize<<<nb, kBS, 0, s->stream>>>(j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
-                                           0);
+    // CGS2: the first pass also takes the dot products of the second, the
+    // second also forms the block norms
+    k_dots<<<nb, kBS, 0, s->stream>>>(j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
     BIPB_LAUNCHED(s);
-    k_givens<<<kg, 128, 0, s->stream>>>(j, m, K, w->H.p, w->cs.p, w->sn.p, w->g.p, w->st);
+    k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, 0, w->st, w->blk.p, w->sysb.p,
+                                      w->part1.p, 0, w->part2.p);
+    BIPB_LAUNCHED(s);
+    k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part2.p, w->H.p, 1, w->st, w->blk.p, w->sysb.p,
+                                      w->part1.p, 1, nullptr);
+    BIPB_LAUNCHED(s);
+    k_normalize<<<nb, kBS, 0, s->stream>>>(j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
+                                           0, w->cs.p, w->sn.p, w->g.p);
     BIPB_LAUNCHED(s);
   }
   k_lsq<<<kg, 128, 0, s->stream>>>(m, K, w->H.p, w->cs.p, w->sn.p, w->g.p, w->y.p, w->z.p, w->st);
@@ -524,7 +546,7 @@ std::vector<int> gmres_core(Surface* s, const SysLayout& L, GmresWork* w, const 
   k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(r0, w->part1.p, w->st, w->blk.p, 1);
   BIPB_LAUNCHED(s);
   k_normalize<<<w->nblk, kBS, 0, s->stream>>>(-1, w->m, r0, w->V.p, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
-                                              1);
+                                              1, w->cs.p, w->sn.p, w->g.p);
   BIPB_LAUNCHED(s);
   k_next_cycle<<<kg, 128, 0, s->stream>>>(w->m, K, w->g.p, w->st);
   BIPB_LAUNCHED(s);
