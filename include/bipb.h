@@ -62,7 +62,8 @@ typedef enum {
   BIPB_MIXED_DF64 = 4, /* FP32 pair arithmetic inside GMRES, double-float refinement residual */
   BIPB_TF32 = 5,       /* mat-vec only, right-hand sides of one surface: kernel tiles generated in
                           FP32 and contracted against blocks of 64 right-hand sides on the tensor
-                          cores (TF32 operands, FP32 accumulation, FP64 sums across tiles) */
+                          cores (each FP32 operand split into two TF32 parts, three TF32 products
+                          per tile, FP32 accumulation, FP64 sums across tiles: about FP32 accuracy) */
   BIPB_MIXED_TF32 = 6  /* TF32 tensor-core mat-vec inside GMRES, double-float refinement residual */
 } bipb_precision;
 

@@ -606,9 +606,9 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   for (int k = 0; k < K; ++k)
     if (bnorm[k] == 0.0) rel[k] = 0.0;
   // inner solves stop near the inner operator's own accuracy (about 1e-7 for
-  // FP32 pairs, 1e-5 for TF32 kernel blocks): iterating further does not
-  // reduce the true residual
-  const double inner_floor = p.inner_tol > 0 ? p.inner_tol : (inner == BIPB_TF32 ? 1e-5 : 1e-6);
+  // FP32 pairs and for the split-TF32 tensor-core tiles): iterating further
+  // does not reduce the true residual
+  const double inner_floor = p.inner_tol > 0 ? p.inner_tol : 1e-6;
   const int inner_cap = p.inner_max_iter > 0 ? p.inner_max_iter : 200;
   std::vector<char> active(K), done(K, 0);
   std::vector<int> iters(K, 0);

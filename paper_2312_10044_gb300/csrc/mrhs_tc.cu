@@ -1,26 +1,35 @@
 // Multi-right-hand-side mat-vec on the 5th-generation tensor cores.
 //
 // Y = A U for a block of up to 64 right-hand sides U (2N x B) on one
-// surface.  Per CTA (256 threads, two per target, each generating half of a
-// chunk): 128 targets (two MMA tiles of M = 128 rows: target unknowns phi_i,
-// psi_i interleaved) against a range of source chunks of 16 sources (K = 32
-// source unknowns phi_j, psi_j interleaved).  For every chunk
-// the CUDA cores generate the kernel tile once,
+// surface.  Per CTA (512 threads, four per target, each generating a quarter
+// of a chunk): 128 targets (two MMA tiles of M = 128 rows: target unknowns
+// phi_i, psi_i interleaved) against a range of source chunks of 16 sources
+// (K = 32 source unknowns phi_j, psi_j interleaved).  For every chunk the
+// CUDA cores generate the kernel tile once,
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i)
 //     [ K4 ds_j   K3 ds_j ]        (row psi_i)     (Sec. 2.2.1, Eqs. 5-6)
-// round it to TF32 (round to nearest) and store it in shared memory in the
-// K-major core-matrix layout; the matching U tile (TF32, packed per chunk in
-// global memory by k_pack_u_tc) arrives by a bulk TMA copy; one thread then
-// issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) into FP32
-// accumulators in tensor memory, which runs while the next tile is being
-// generated.  The epilogue reads TMEM and writes per-split partial sums that
-// the FP64 reduction of kernels.cu adds, so the kernel tile costs the same as
-// in the single-RHS kernel while serving 64 right-hand sides.
+// split every FP32 value a into TF32 parts a_hi = tf32(a), a_lo = tf32(a -
+// a_hi) and store both tiles in shared memory in the K-major core-matrix
+// layout; the matching U tiles (U_hi, U_lo, packed per chunk in global
+// memory by k_pack_u_tc) arrive by a bulk TMA copy; one thread then issues
+// tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) for A_hi U_hi + A_hi U_lo +
+// A_lo U_hi into FP32 accumulators in tensor memory, which runs while the
+// next tile is being generated.
 //
-// TF32 keeps 10 mantissa bits, but the diagonal 1/2(1+eps), 1/2(1+1/eps) is
-// applied exactly in FP64 by the reduction and the off-diagonal sum is a few
-// per cent of a row, so the operator is accurate to about 1e-5 relative --
-// enough for the inner solves of the mixed refinement.
+// Accuracy.  Three TF32 products ("3xTF32") drop only A_lo U_lo and the TF32
+// rounding of the low parts, both about 2^-22 of a product.  The tensor
+// core's FP32 accumulation, however, is not to be run over a whole source
+// range: summed over thousands of chunks its error grows with the length of
+// the sum and does not average out for smooth vectors (measured on the
+// protein-like surface at N = 81920: 1.7e-4 of the off-diagonal part for
+// phi = 1, against 1.2e-5 for the FP32 CUDA-core mat-vec).  So every chunk
+// starts a fresh accumulator (two TMEM accumulator sets, alternating), and
+// while the tensor core works on chunk c the threads read the result of
+// chunk c - 1 from TMEM and add it to FP32 registers.  The operator is then
+// accurate to FP32 level and the mixed refinement reaches 1e-8 in two steps.
+// The epilogue writes per-split partial sums that the FP64 reduction of
+// kernels.cu adds, so the kernel tile costs about the same as in the
+// single-RHS kernel while serving 64 right-hand sides.
 //
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
 // flag that the host turns into BIPB_ERR_CUDA, and the kernel still frees its
@@ -38,15 +47,15 @@ constexpr int kNB = 64;          // right-hand sides per launch (MMA N)
 constexpr int kTgt = 128;        // targets per CTA (two M = 128 tiles)
 constexpr int kChunk = 16;       // sources per chunk
 constexpr int kK = 2 * kChunk;   // MMA K per chunk
-constexpr int kABytes = 2 * 128 * kK * 4;   // A tile of one chunk (both M tiles): 32 KB
-constexpr int kBBytes = kNB * kK * 4;       // U tile of one chunk: 8 KB
+constexpr int kABytes = 2 * 128 * kK * 4;   // one TF32 part of the A tile of a chunk (both M tiles): 32 KB
+constexpr int kBBytes = kNB * kK * 4;       // one TF32 part of the U tile of a chunk: 8 KB
 constexpr int kSBytes = kChunk * 32;        // source records of one chunk: 512 B
-constexpr int kOffA = 0;                    // 2 A buffers
-constexpr int kOffB = 2 * kABytes;          // 4 U buffers
-constexpr int kOffS = kOffB + 4 * kBBytes;  // 4 source buffers
+constexpr int kOffA = 0;                    // 2 A buffers, each [hi | lo]
+constexpr int kOffB = 4 * kABytes;          // 4 U buffers, each [hi | lo]
+constexpr int kOffS = kOffB + 8 * kBBytes;  // 4 source buffers
 constexpr int kOffBar = kOffS + 4 * kSBytes;
 constexpr int kSmemBytes = kOffBar + 8 * 8 + 16;
-constexpr uint32_t kTmemCols = 128;
+constexpr uint32_t kTmemCols = 256;         // two accumulator sets of 2 tiles x 64 columns
 constexpr long kSpinLimit = 1L << 24;
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -66,8 +75,9 @@ __device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) 
                : "memory");
 }
 
-// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, the TF32 U tile in
-// the K-major core-matrix layout (row = right-hand side, K = 2 j' + c).
+// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, the TF32 tiles U_hi
+// and U_lo (one after the other) in the K-major core-matrix layout (row =
+// right-hand side, K = 2 j' + c).
 __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __restrict__ u, float* __restrict__ upk) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one per (chunk, b, k)
   if (e >= (int64_t)n_chunks * kNB * kK) return;
@@ -75,13 +85,19 @@ __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __rest
   const int rem = (int)(e % (kNB * kK));
   const int b = rem / kK, k = rem % kK;
   const int j = ch * kChunk + (k >> 1), c = k & 1;
-  float v = 0.f;
-  if (b < n_rhs && j < n) v = to_tf32((float)u[(int64_t)b * 2 * n + (int64_t)c * n + j]);
-  upk[(int64_t)ch * (kNB * kK) + tc::kmajor_offset(b, k, kK) / 4] = v;
+  float hi = 0.f, lo = 0.f;
+  if (b < n_rhs && j < n) {
+    const double v = u[(int64_t)b * 2 * n + (int64_t)c * n + j];
+    hi = to_tf32((float)v);
+    lo = to_tf32((float)(v - (double)hi));
+  }
+  float* tile = upk + (int64_t)ch * (2 * kNB * kK);
+  tile[tc::kmajor_offset(b, k, kK) / 4] = hi;
+  tile[kNB * kK + tc::kmajor_offset(b, k, kK) / 4] = lo;
 }
 
-// The four kernel values of pair (target i, source j) times ds_j (times 4 pi):
-// returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3]; zero when masked.
+// The four kernel values of pair (target i, source j) times ds_j (times 4 pi),
+// in FP32: returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3].
 __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float nxi, float nyi, float nzi, float4 g,
                                              float4 nv, bool zero, const PairConst<float>& c, float* v) {
   const float dx = xi - g.x, dy = yi - g.y, dz = zi - g.z;
@@ -100,22 +116,28 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   const float sa = s * g.w;
   const float s2 = s * s;
   const float s3a = s2 * sa;
-  v[1] = to_tf32(sa - e * sa);                                  // K1 ds = (1 - e) s ds
-  v[0] = to_tf32(((c.eps * t - 1.f) * cj) * s3a);               // K2 ds
-  v[3] = to_tf32(((t * c.inveps - 1.f) * ci) * s3a);            // K3 ds
-  v[2] = to_tf32((tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a);   // K4 ds
+  v[1] = sa - e * sa;                                  // K1 ds = (1 - e) s ds
+  v[0] = ((c.eps * t - 1.f) * cj) * s3a;               // K2 ds
+  v[3] = ((t * c.inveps - 1.f) * ci) * s3a;            // K3 ds
+  v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
+}
+
+// a -> (tf32(a), tf32(a - tf32(a))); a - tf32(a) is exact in FP32
+__device__ __forceinline__ void split_tf32(float4 a, float4& hi, float4& lo) {
+  hi = make_float4(to_tf32(a.x), to_tf32(a.y), to_tf32(a.z), to_tf32(a.w));
+  lo = make_float4(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y), to_tf32(a.z - hi.z), to_tf32(a.w - hi.w));
 }
 
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 
-__global__ void __launch_bounds__(kThreads, 2) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
+__global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
                                                     const float4* __restrict__ tgt32, const float* __restrict__ upk,
                                                     float* __restrict__ part, PairConst<float> c,
                                                     int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources landed
-  uint64_t* done = full + 4;                                      // 2: MMAs of an A buffer finished
+  uint64_t* done = full + 4;                                      // 2: MMAs of a chunk finished (per parity)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 item = items[blockIdx.x];
@@ -135,8 +157,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_mrhs_tc(int n, int n_rhs, int n
   auto issue_load = [&](int it) {  // chunk c0 + it into buffer it & 3 (thread 0)
     const int ch = c0 + it, q = it & 3;
     const int cnt = min(kChunk, n - ch * kChunk);
-    arrive_expect_tx(&full[q], kBBytes + cnt * 32);
-    bulk_load(smem + kOffB + q * kBBytes, upk + (int64_t)ch * (kNB * kK), kBBytes, &full[q]);
+    arrive_expect_tx(&full[q], 2 * kBBytes + cnt * 32);
+    bulk_load(smem + kOffB + q * 2 * kBBytes, upk + (int64_t)ch * (2 * kNB * kK), 2 * kBBytes, &full[q]);
     bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &full[q]);
   };
   const int n_it = c1 - c0;
@@ -145,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_mrhs_tc(int n, int n_rhs, int n
     if (n_it > 1) issue_load(1);
   }
 
-  // this thread's target: rows 2 lt, 2 lt + 1 of M tile mb; half h of each chunk
+  // generation: this thread's target, rows 2 lt, 2 lt + 1 of M tile mb; quarter h of each chunk
   const int mb = (tid >> 6) & 1, lt = tid & 63, h = tid >> 7;
   const int ti = t0 + (tid & 127);
   const bool tvalid = ti < n;
@@ -153,20 +175,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_mrhs_tc(int n, int n_rhs, int n
   const int row0 = 128 * mb + 2 * lt;
   const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
   const uint32_t idesc = tc::idesc_tf32(128, kNB);
+  // accumulation: TMEM lane quarter wq (the warp's own), tile wm, columns [32 wh, 32 wh + 32)
+  const int wq = warp & 3, wm = (warp >> 2) & 1, wh = warp >> 3;
+  const uint32_t tcol = ((uint32_t)(32 * wq) << 16) + wm * kNB + 32 * wh;
+  float acc[32];
+#pragma unroll
+  for (int x = 0; x < 32; ++x) acc[x] = 0.f;
   bool ok = true;
+  // add the result of chunk it (accumulator set it & 1) to the registers
+  auto drain = [&](int it) {
+    ok &= tc::mbar_wait(&done[it & 1], (it >> 1) & 1, kSpinLimit);
+    tc::fence_after_sync();
+    float v[16];
+    const uint32_t base = tmem + tcol + (it & 1) * (2 * kNB);
+    tc::tmem_ld16(base, v);
+#pragma unroll
+    for (int x = 0; x < 16; ++x) acc[x] += v[x];
+    tc::tmem_ld16(base + 16, v);
+#pragma unroll
+    for (int x = 0; x < 16; ++x) acc[16 + x] += v[x];
+    tc::fence_before_sync();
+  };
 
   for (int it = 0; it < n_it; ++it) {
     const int s = it & 1, q = it & 3;
-    if (it >= 2) ok &= tc::mbar_wait(&done[s], ((it - 2) >> 1) & 1, kSpinLimit);
+    // buffer s was last read by the MMAs of chunk it - 2, drained in the previous iteration
     ok &= tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
     const int ch = c0 + it;
     const int j0 = ch * kChunk;
     const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
-    unsigned char* A = smem + kOffA + s * kABytes;
+    unsigned char* A = smem + kOffA + s * 2 * kABytes;  // hi part; the lo part kABytes further
     const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
 #pragma unroll
-    for (int kk = 0; kk < kChunk / 4; ++kk) {
-      const int kb = (kChunk / 4) * h + kk;
+    for (int kk = 0; kk < kChunk / 8; ++kk) {
+      const int kb = (kChunk / 8) * h + kk;
       float va[4], vb[4];
       const int ja = j0 + 2 * kb, jb = ja + 1;
       const bool za = edge && (!tvalid || ja >= n || ja == ti);
@@ -175,56 +217,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_mrhs_tc(int n, int n_rhs, int n
       kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb + 2], S[4 * kb + 3], zb, c, vb);
       if (za) va[0] = va[1] = va[2] = va[3] = 0.f;
       if (zb) vb[0] = vb[1] = vb[2] = vb[3] = 0.f;
-      const float4 rphi = make_float4(va[0], va[1], vb[0], vb[1]);
-      const float4 rpsi = make_float4(va[2], va[3], vb[2], vb[3]);
-      float4* pphi = reinterpret_cast<float4*>(A + tc::kmajor_offset(row0, 4 * kb, kK));
-      float4* ppsi = reinterpret_cast<float4*>(A + tc::kmajor_offset(row0 + 1, 4 * kb, kK));
+      float4 phi_hi, phi_lo, psi_hi, psi_lo;
+      split_tf32(make_float4(va[0], va[1], vb[0], vb[1]), phi_hi, phi_lo);
+      split_tf32(make_float4(va[2], va[3], vb[2], vb[3]), psi_hi, psi_lo);
+      const uint32_t ophi = tc::kmajor_offset(row0, 4 * kb, kK), opsi = tc::kmajor_offset(row0 + 1, 4 * kb, kK);
       if (swap) {
-        *ppsi = rpsi;
-        *pphi = rphi;
+        *reinterpret_cast<float4*>(A + opsi) = psi_hi;
+        *reinterpret_cast<float4*>(A + ophi) = phi_hi;
+        *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
+        *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
       } else {
-        *pphi = rphi;
-        *ppsi = rpsi;
+        *reinterpret_cast<float4*>(A + ophi) = phi_hi;
+        *reinterpret_cast<float4*>(A + opsi) = psi_hi;
+        *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
+        *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
       }
     }
     tc::fence_proxy_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    __syncthreads();  // tile it complete; every thread has drained chunk it - 2 (set s is free)
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(smem + kOffB + q * kBBytes);
+      const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(smem + kOffB + q * 2 * kBBytes);
+      const uint32_t dcol = tmem + s * (2 * kNB);
       for (int m = 0; m < 2; ++m)
         for (int ks = 0; ks < kK / 8; ++ks) {
-          const uint64_t ad = tc::smem_desc(a0 + m * (kABytes / 2) + 256 * ks, 128, (kK / 4) * 128);
-          const uint64_t bd = tc::smem_desc(b0 + 256 * ks, 128, (kK / 4) * 128);
-          tc::mma_tf32(tmem + m * kNB, ad, bd, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+          const uint32_t ah = a0 + m * (kABytes / 2) + 256 * ks, bh = b0 + 256 * ks;
+          const uint64_t a_hi = tc::smem_desc(ah, 128, (kK / 4) * 128);
+          const uint64_t a_lo = tc::smem_desc(ah + kABytes, 128, (kK / 4) * 128);
+          const uint64_t b_hi = tc::smem_desc(bh, 128, (kK / 4) * 128);
+          const uint64_t b_lo = tc::smem_desc(bh + kBBytes, 128, (kK / 4) * 128);
+          tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
+          tc::mma_tf32(dcol + m * kNB, a_hi, b_lo, idesc, 1u);
+          tc::mma_tf32(dcol + m * kNB, a_lo, b_hi, idesc, 1u);
         }
       tc::mma_commit(&done[s]);
-      if (it + 2 < n_it) issue_load(it + 2);  // its buffer's last reader (chunk it - 2) is done
+      // U / source buffer (it + 2) & 3 was last read by chunk it - 2, whose MMAs are done
+      if (it + 2 < n_it) issue_load(it + 2);
     }
+    if (it > 0) drain(it - 1);
   }
-  if (n_it > 0) ok &= tc::mbar_wait(&done[(n_it - 1) & 1], ((n_it - 1) >> 1) & 1, kSpinLimit);
-  tc::fence_after_sync();
+  if (n_it > 0) drain(n_it - 1);
   const bool all_ok = __syncthreads_and(ok) != 0;
   if (!all_ok && tid == 0) atomicExch(err, 1);
 
-  // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2;
-  // warp w reads lane quarter w % 4 of tile w / 4
+  // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2
   if (all_ok && n_it > 0) {
-    {
-      const int m = warp >> 2, quarter = warp & 3;
-      const int r = 32 * quarter + lane;
-      const int i = t0 + 64 * m + (r >> 1), comp = r & 1;
-      for (int cb = 0; cb < kNB / 16; ++cb) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + m * kNB + 16 * cb, v);
-        if (i < n)
-          for (int x = 0; x < 16; ++x) {
-            const int b = 16 * cb + x;
-            if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = v[x];
-          }
+    const int r = 32 * wq + lane;
+    const int i = t0 + 64 * wm + (r >> 1), comp = r & 1;
+    if (i < n)
+#pragma unroll
+      for (int x = 0; x < 32; ++x) {
+        const int b = 32 * wh + x;
+        if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x];
       }
-    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -282,7 +328,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     plan = it->second.get();
   }
   const int K = L.K;
-  s->grow(s->upk, (size_t)n_chunks * kNB * kK);
+  s->grow(s->upk, (size_t)n_chunks * 2 * kNB * kK);
   s->grow(s->part32, (size_t)std::min(K, kNB) * S * 2 * n);
   if (s->tc_err.cap == 0) {
     s->grow(s->tc_err, 1);

@@ -450,8 +450,10 @@ def test_autograd_batched_mixed(bipb):
 # ---------------------------------------------------------------- tensor-core multi-RHS
 @pytest.mark.parametrize("n_rhs", [5, 70])
 def test_tensor_core_matvec_matches_oracle(bipb, orc, n_rhs):
-    """TF32 tensor-core mat-vec (kernel tile once per 64 right-hand sides) vs
-    the FP64 oracle; the TF32 operator is accurate to about 1e-5 relative."""
+    """Tensor-core mat-vec (kernel tile once per 64 right-hand sides, FP32
+    operands split into two TF32 parts, three TF32 products) vs the FP64
+    oracle: held to the FP32 mat-vec's bounds, 3e-6 in the 2-norm and 2e-5
+    of the largest output."""
     p = _ragged(3)
     eps = p.eps_out / p.eps_in
     U = np.random.default_rng(30 + n_rhs).standard_normal((n_rhs, 2 * p.n))
@@ -463,8 +465,8 @@ def test_tensor_core_matvec_matches_oracle(bipb, orc, n_rhs):
     for r in (0, n_rhs // 2, n_rhs - 1):
         ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
         assert np.all(np.isfinite(Y[r]))
-        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-5
-        assert np.abs(Y[r] - ref).max() < 3e-4 * np.abs(ref).max()
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6
+        assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
 
 
 def test_mixed_tf32_solve_matches_oracle(bipb, orc):
