@@ -54,7 +54,7 @@ constexpr int kOffA = 0;                    // 2 A buffers, each [hi | lo]
 constexpr int kOffB = 4 * kABytes;          // 4 U buffers, each [hi | lo]
 constexpr int kOffS = kOffB + 8 * kBBytes;  // 4 source buffers
 constexpr int kOffBar = kOffS + 4 * kSBytes;
-constexpr int kSmemBytes = kOffBar + 8 * 8 + 16;
+constexpr int kSmemBytes = kOffBar + 10 * 8 + 16;
 constexpr uint32_t kTmemCols = 256;         // two accumulator sets of 2 tiles x 64 columns
 constexpr long kSpinLimit = 1L << 24;
 
@@ -129,23 +129,36 @@ __device__ __forceinline__ void split_tf32(float4 a, float4& hi, float4& lo) {
 }
 
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
-constexpr int kThreads = 512;
+// Warps 0-15 generate tiles and accumulate; warp 16 (one lane) issues the
+// bulk copies and the MMAs, so no generating warp waits for the issue.
+constexpr int kGenThreads = 512;
+constexpr int kThreads = kGenThreads + 32;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
 
 __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
                                                     const float4* __restrict__ tgt32, const float* __restrict__ upk,
                                                     float* __restrict__ part, PairConst<float> c,
                                                     int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources landed
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources of a chunk landed
   uint64_t* done = full + 4;                                      // 2: MMAs of a chunk finished (per parity)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 8);
+  uint64_t* ready = done + 2;                                     // 2: A tile of a chunk written (512 arrivals)
+  uint64_t* drained = ready + 2;                                  // 2: accumulator set read back (512 arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, c0 = item.y, c1 = item.z, split = item.w;
 
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) tc::mbar_init(&full[q], 1);
-    for (int q = 0; q < 2; ++q) tc::mbar_init(&done[q], 1);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&done[q], 1);
+      tc::mbar_init(&ready[q], kGenThreads);
+      tc::mbar_init(&drained[q], kGenThreads);
+    }
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
@@ -153,116 +166,129 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-
-  auto issue_load = [&](int it) {  // chunk c0 + it into buffer it & 3 (thread 0)
-    const int ch = c0 + it, q = it & 3;
-    const int cnt = min(kChunk, n - ch * kChunk);
-    arrive_expect_tx(&full[q], 2 * kBBytes + cnt * 32);
-    bulk_load(smem + kOffB + q * 2 * kBBytes, upk + (int64_t)ch * (2 * kNB * kK), 2 * kBBytes, &full[q]);
-    bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &full[q]);
-  };
   const int n_it = c1 - c0;
-  if (tid == 0) {
-    if (n_it > 0) issue_load(0);
-    if (n_it > 1) issue_load(1);
-  }
-
-  // generation: this thread's target, rows 2 lt, 2 lt + 1 of M tile mb; quarter h of each chunk
-  const int mb = (tid >> 6) & 1, lt = tid & 63, h = tid >> 7;
-  const int ti = t0 + (tid & 127);
-  const bool tvalid = ti < n;
-  const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
-  const int row0 = 128 * mb + 2 * lt;
-  const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
-  const uint32_t idesc = tc::idesc_tf32(128, kNB);
+  bool ok = true;
   // accumulation: TMEM lane quarter wq (the warp's own), tile wm, columns [32 wh, 32 wh + 32)
-  const int wq = warp & 3, wm = (warp >> 2) & 1, wh = warp >> 3;
-  const uint32_t tcol = ((uint32_t)(32 * wq) << 16) + wm * kNB + 32 * wh;
+  const int wq = warp & 3, wm = (warp >> 2) & 1, wh = (warp >> 3) & 1;
   float acc[32];
 #pragma unroll
   for (int x = 0; x < 32; ++x) acc[x] = 0.f;
-  bool ok = true;
-  // add the result of chunk it (accumulator set it & 1) to the registers
-  auto drain = [&](int it) {
-    ok &= tc::mbar_wait(&done[it & 1], (it >> 1) & 1, kSpinLimit);
-    tc::fence_after_sync();
-    float v[16];
-    const uint32_t base = tmem + tcol + (it & 1) * (2 * kNB);
-    tc::tmem_ld16(base, v);
-#pragma unroll
-    for (int x = 0; x < 16; ++x) acc[x] += v[x];
-    tc::tmem_ld16(base + 16, v);
-#pragma unroll
-    for (int x = 0; x < 16; ++x) acc[16 + x] += v[x];
-    tc::fence_before_sync();
-  };
 
-  for (int it = 0; it < n_it; ++it) {
-    const int s = it & 1, q = it & 3;
-    // buffer s was last read by the MMAs of chunk it - 2, drained in the previous iteration
-    ok &= tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
-    const int ch = c0 + it;
-    const int j0 = ch * kChunk;
-    const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
-    unsigned char* A = smem + kOffA + s * 2 * kABytes;  // hi part; the lo part kABytes further
-    const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
-#pragma unroll
-    for (int kk = 0; kk < kChunk / 8; ++kk) {
-      const int kb = (kChunk / 8) * h + kk;
-      float va[4], vb[4];
-      const int ja = j0 + 2 * kb, jb = ja + 1;
-      const bool za = edge && (!tvalid || ja >= n || ja == ti);
-      const bool zb = edge && (!tvalid || jb >= n || jb == ti);
-      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb], S[4 * kb + 1], za, c, va);
-      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb + 2], S[4 * kb + 3], zb, c, vb);
-      if (za) va[0] = va[1] = va[2] = va[3] = 0.f;
-      if (zb) vb[0] = vb[1] = vb[2] = vb[3] = 0.f;
-      float4 phi_hi, phi_lo, psi_hi, psi_lo;
-      split_tf32(make_float4(va[0], va[1], vb[0], vb[1]), phi_hi, phi_lo);
-      split_tf32(make_float4(va[2], va[3], vb[2], vb[3]), psi_hi, psi_lo);
-      const uint32_t ophi = tc::kmajor_offset(row0, 4 * kb, kK), opsi = tc::kmajor_offset(row0 + 1, 4 * kb, kK);
-      if (swap) {
-        *reinterpret_cast<float4*>(A + opsi) = psi_hi;
-        *reinterpret_cast<float4*>(A + ophi) = phi_hi;
-        *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
-        *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
-      } else {
-        *reinterpret_cast<float4*>(A + ophi) = phi_hi;
-        *reinterpret_cast<float4*>(A + opsi) = psi_hi;
-        *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
-        *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
+  if (warp == kGenThreads / 32) {
+    // ---------------------------------------------------------- issue warp
+    if (lane == 0) {
+      auto issue_load = [&](int it) {  // chunk c0 + it into buffer it & 3
+        const int ch = c0 + it, q = it & 3;
+        const int cnt = min(kChunk, n - ch * kChunk);
+        arrive_expect_tx(&full[q], 2 * kBBytes + cnt * 32);
+        bulk_load(smem + kOffB + q * 2 * kBBytes, upk + (int64_t)ch * (2 * kNB * kK), 2 * kBBytes, &full[q]);
+        bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &full[q]);
+      };
+      if (n_it > 0) issue_load(0);
+      if (n_it > 1) issue_load(1);
+      const uint32_t idesc = tc::idesc_tf32(128, kNB);
+      for (int it = 0; it < n_it; ++it) {
+        const int s = it & 1, q = it & 3;
+        // accumulator set s: chunk it - 2 read back; tile it written; U of chunk it landed
+        if (it >= 2) ok = ok && tc::mbar_wait(&drained[s], ((it - 2) >> 1) & 1, kSpinLimit);
+        ok = ok && tc::mbar_wait(&ready[s], (it >> 1) & 1, kSpinLimit);
+        ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t a0 = tc::smem_u32(smem + kOffA + s * 2 * kABytes), b0 = tc::smem_u32(smem + kOffB + q * 2 * kBBytes);
+        const uint32_t dcol = tmem + s * (2 * kNB);
+        for (int m = 0; m < 2; ++m)
+          for (int ks = 0; ks < kK / 8; ++ks) {
+            const uint32_t ah = a0 + m * (kABytes / 2) + 256 * ks, bh = b0 + 256 * ks;
+            const uint64_t a_hi = tc::smem_desc(ah, 128, (kK / 4) * 128);
+            const uint64_t a_lo = tc::smem_desc(ah + kABytes, 128, (kK / 4) * 128);
+            const uint64_t b_hi = tc::smem_desc(bh, 128, (kK / 4) * 128);
+            const uint64_t b_lo = tc::smem_desc(bh + kBBytes, 128, (kK / 4) * 128);
+            tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
+            tc::mma_tf32(dcol + m * kNB, a_hi, b_lo, idesc, 1u);
+            tc::mma_tf32(dcol + m * kNB, a_lo, b_hi, idesc, 1u);
+          }
+        tc::mma_commit(&done[s]);
+        // U / source buffer (it + 2) & 3 was last read by chunk it - 2: its MMAs are done
+        // (drained) and its tile was generated (ready)
+        if (it + 2 < n_it) issue_load(it + 2);
       }
     }
-    tc::fence_proxy_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();  // tile it complete; every thread has drained chunk it - 2 (set s is free)
-    if (tid == 0) {
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------- generating warps
+    // this thread's target: rows 2 lt, 2 lt + 1 of M tile mb; quarter h of each chunk
+    const int mb = (tid >> 6) & 1, lt = tid & 63, h = tid >> 7;
+    const int ti = t0 + (tid & 127);
+    const bool tvalid = ti < n;
+    const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
+    const int row0 = 128 * mb + 2 * lt;
+    const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
+    const uint32_t tcol = ((uint32_t)(32 * wq) << 16) + wm * kNB + 32 * wh;
+    // add the result of chunk it (accumulator set it & 1) to the registers, then release the set
+    auto drain = [&](int it) {
+      ok = ok && tc::mbar_wait(&done[it & 1], (it >> 1) & 1, kSpinLimit);
+      if (!ok) return;
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(smem + kOffB + q * 2 * kBBytes);
-      const uint32_t dcol = tmem + s * (2 * kNB);
-      for (int m = 0; m < 2; ++m)
-        for (int ks = 0; ks < kK / 8; ++ks) {
-          const uint32_t ah = a0 + m * (kABytes / 2) + 256 * ks, bh = b0 + 256 * ks;
-          const uint64_t a_hi = tc::smem_desc(ah, 128, (kK / 4) * 128);
-          const uint64_t a_lo = tc::smem_desc(ah + kABytes, 128, (kK / 4) * 128);
-          const uint64_t b_hi = tc::smem_desc(bh, 128, (kK / 4) * 128);
-          const uint64_t b_lo = tc::smem_desc(bh + kBBytes, 128, (kK / 4) * 128);
-          tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
-          tc::mma_tf32(dcol + m * kNB, a_hi, b_lo, idesc, 1u);
-          tc::mma_tf32(dcol + m * kNB, a_lo, b_hi, idesc, 1u);
+      float v[16];
+      const uint32_t base = tmem + tcol + (it & 1) * (2 * kNB);
+      tc::tmem_ld16(base, v);
+#pragma unroll
+      for (int x = 0; x < 16; ++x) acc[x] += v[x];
+      tc::tmem_ld16(base + 16, v);
+#pragma unroll
+      for (int x = 0; x < 16; ++x) acc[16 + x] += v[x];
+      tc::fence_before_sync();
+      mbar_arrive(&drained[it & 1]);
+    };
+    for (int it = 0; it < n_it; ++it) {
+      const int s = it & 1, q = it & 3;
+      // A buffer s was last read by the MMAs of chunk it - 2, drained in the previous iteration
+      ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
+      if (!ok) break;
+      const int j0 = (c0 + it) * kChunk;
+      const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
+      unsigned char* A = smem + kOffA + s * 2 * kABytes;  // hi part; the lo part kABytes further
+      const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
+#pragma unroll
+      for (int kk = 0; kk < kChunk / 8; ++kk) {
+        const int kb = (kChunk / 8) * h + kk;
+        float va[4], vb[4];
+        const int ja = j0 + 2 * kb, jb = ja + 1;
+        const bool za = edge && (!tvalid || ja >= n || ja == ti);
+        const bool zb = edge && (!tvalid || jb >= n || jb == ti);
+        kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb], S[4 * kb + 1], za, c, va);
+        kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb + 2], S[4 * kb + 3], zb, c, vb);
+        if (za) va[0] = va[1] = va[2] = va[3] = 0.f;
+        if (zb) vb[0] = vb[1] = vb[2] = vb[3] = 0.f;
+        float4 phi_hi, phi_lo, psi_hi, psi_lo;
+        split_tf32(make_float4(va[0], va[1], vb[0], vb[1]), phi_hi, phi_lo);
+        split_tf32(make_float4(va[2], va[3], vb[2], vb[3]), psi_hi, psi_lo);
+        const uint32_t ophi = tc::kmajor_offset(row0, 4 * kb, kK), opsi = tc::kmajor_offset(row0 + 1, 4 * kb, kK);
+        if (swap) {
+          *reinterpret_cast<float4*>(A + opsi) = psi_hi;
+          *reinterpret_cast<float4*>(A + ophi) = phi_hi;
+          *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
+          *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
+        } else {
+          *reinterpret_cast<float4*>(A + ophi) = phi_hi;
+          *reinterpret_cast<float4*>(A + opsi) = psi_hi;
+          *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
+          *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
         }
-      tc::mma_commit(&done[s]);
-      // U / source buffer (it + 2) & 3 was last read by chunk it - 2, whose MMAs are done
-      if (it + 2 < n_it) issue_load(it + 2);
+      }
+      tc::fence_proxy_async_smem();  // this thread's tile stores, visible to the tensor core
+      mbar_arrive(&ready[s]);
+      if (it > 0) drain(it - 1);
+      if (!ok) break;
     }
-    if (it > 0) drain(it - 1);
+    if (ok && n_it > 0) drain(n_it - 1);
   }
-  if (n_it > 0) drain(n_it - 1);
   const bool all_ok = __syncthreads_and(ok) != 0;
   if (!all_ok && tid == 0) atomicExch(err, 1);
 
   // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2
-  if (all_ok && n_it > 0) {
+  if (all_ok && n_it > 0 && warp < kGenThreads / 32) {
     const int r = 32 * wq + lane;
     const int i = t0 + 64 * wm + (r >> 1), comp = r & 1;
     if (i < n)
