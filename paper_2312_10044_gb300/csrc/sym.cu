@@ -347,7 +347,7 @@ int blocks_of(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1)
 
 // ------------------------------------------------------------------ work list
 // Folded rows (I, nT - 1 - I) of every system are cut into pieces of about
-// Lsrc sources; Lsrc is the candidate (the length giving 1 .. 8 waves of
+// Lsrc sources; Lsrc is the candidate (the length giving 1 .. 32 waves of
 // equal pieces) whose greedy schedule (pieces sorted by size, each to the
 // first free CTA slot) finishes first.  A piece costs its
 // sources plus 32 per segment (loading a tile, storing its partials).
@@ -442,10 +442,15 @@ HostPlan compute_sym_plan(const SysLayout& L, int T, int slots, int ch) {
     }
     return end;
   };
-  // candidates: the piece length that gives w waves of equal pieces, w = 1 .. 8
+  // candidates: the piece length that gives w waves of equal pieces, w from 1
+  // to 32 (uneven batches need many short pieces to balance); stop once the
+  // schedule is within 1 % of the ideal total / slots
+  const double ideal = (double)total / (double)slots;
   double best_L = 2.0 * n_max, best = makespan(best_L);
-  for (int w = 1; w <= 8; ++w) {
-    const double Ls = std::max((double)ch, (double)total / ((double)w * slots));
+  static const double kWaves[] = {1, 1.5, 2, 3, 4, 6, 8, 12, 16, 24, 32};
+  for (double w : kWaves) {
+    if (best <= 1.01 * ideal) break;
+    const double Ls = std::max((double)ch, (double)total / (w * slots));
     const double m = makespan(Ls);
     if (m < best * 0.995) best = m, best_L = Ls;
   }
