@@ -23,9 +23,10 @@
 // the sum and does not average out for smooth vectors (measured on the
 // protein-like surface at N = 81920: 1.7e-4 of the off-diagonal part for
 // phi = 1, against 1.2e-5 for the FP32 CUDA-core mat-vec).  So every chunk
-// starts a fresh accumulator (two TMEM accumulator sets, alternating), and
-// while the tensor core works on chunk c the threads read the result of
-// chunk c - 1 from TMEM and add it to FP32 registers.  The operator is then
+// starts a fresh accumulator (three TMEM accumulator sets in turn), and while
+// the threads generate chunk c they read the result of chunk c - 2 from TMEM
+// (long finished, the loads overlapping the generation) and add it to FP32
+// registers.  The operator is then
 // accurate to FP32 level and the mixed refinement reaches 1e-8 in two steps.
 // The epilogue writes per-split partial sums that the FP64 reduction of
 // kernels.cu adds, so the kernel tile costs about the same as in the
@@ -54,8 +55,9 @@ constexpr int kOffA = 0;                    // 2 A buffers, each [hi | lo]
 constexpr int kOffB = 4 * kABytes;          // 4 U buffers, each [hi | lo]
 constexpr int kOffS = kOffB + 8 * kBBytes;  // 4 source buffers
 constexpr int kOffBar = kOffS + 4 * kSBytes;
-constexpr int kSmemBytes = kOffBar + 10 * 8 + 16;
-constexpr uint32_t kTmemCols = 256;         // two accumulator sets of 2 tiles x 64 columns
+constexpr int kSmemBytes = kOffBar + 12 * 8 + 16;
+constexpr int kSets = 3;                    // TMEM accumulator sets (chunk c uses set c % 3)
+constexpr uint32_t kTmemCols = 512;         // three sets of 2 tiles x 64 columns, rounded to a power of 2
 constexpr long kSpinLimit = 1L << 24;
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -144,19 +146,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
                                                     int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources of a chunk landed
-  uint64_t* done = full + 4;                                      // 2: MMAs of a chunk finished (per parity)
-  uint64_t* ready = done + 2;                                     // 2: A tile of a chunk written (512 arrivals)
-  uint64_t* drained = ready + 2;                                  // 2: accumulator set read back (512 arrivals)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 2);
+  uint64_t* ready = full + 4;                                     // 2: A tile of a chunk written (512 arrivals)
+  uint64_t* done = ready + 2;                                     // 3: MMAs of a chunk finished (per set)
+  uint64_t* drained = done + kSets;                               // 3: accumulator set read back (512 arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + kSets);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, c0 = item.y, c1 = item.z, split = item.w;
 
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) tc::mbar_init(&full[q], 1);
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < 2; ++q) tc::mbar_init(&ready[q], kGenThreads);
+    for (int q = 0; q < kSets; ++q) {
       tc::mbar_init(&done[q], 1);
-      tc::mbar_init(&ready[q], kGenThreads);
       tc::mbar_init(&drained[q], kGenThreads);
     }
     tc::fence_mbar_init();
@@ -188,29 +190,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       if (n_it > 1) issue_load(1);
       const uint32_t idesc = tc::idesc_tf32(128, kNB);
       for (int it = 0; it < n_it; ++it) {
-        const int s = it & 1, q = it & 3;
-        // accumulator set s: chunk it - 2 read back; tile it written; U of chunk it landed
-        if (it >= 2) ok = ok && tc::mbar_wait(&drained[s], ((it - 2) >> 1) & 1, kSpinLimit);
+        const int s = it & 1, q = it & 3, set = it % kSets;
+        // accumulator set: chunk it - 3 read back; tile it written; U of chunk it landed
+        if (it >= kSets) ok = ok && tc::mbar_wait(&drained[set], ((it - kSets) / kSets) & 1, kSpinLimit);
         ok = ok && tc::mbar_wait(&ready[s], (it >> 1) & 1, kSpinLimit);
         ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
         if (!ok) break;
         tc::fence_after_sync();
-        const uint32_t a0 = tc::smem_u32(smem + kOffA + s * 2 * kABytes), b0 = tc::smem_u32(smem + kOffB + q * 2 * kBBytes);
-        const uint32_t dcol = tmem + s * (2 * kNB);
+        // descriptors of the chunk's first core matrices; the others differ only in
+        // the start-address field (bits 0-13, in 16-byte units, no carry: smem < 256 KB)
+        const uint64_t da = tc::smem_desc(tc::smem_u32(smem + kOffA + s * 2 * kABytes), 128, (kK / 4) * 128);
+        const uint64_t db = tc::smem_desc(tc::smem_u32(smem + kOffB + q * 2 * kBBytes), 128, (kK / 4) * 128);
+        const uint32_t dcol = tmem + set * (2 * kNB);
+#pragma unroll
         for (int m = 0; m < 2; ++m)
+#pragma unroll
           for (int ks = 0; ks < kK / 8; ++ks) {
-            const uint32_t ah = a0 + m * (kABytes / 2) + 256 * ks, bh = b0 + 256 * ks;
-            const uint64_t a_hi = tc::smem_desc(ah, 128, (kK / 4) * 128);
-            const uint64_t a_lo = tc::smem_desc(ah + kABytes, 128, (kK / 4) * 128);
-            const uint64_t b_hi = tc::smem_desc(bh, 128, (kK / 4) * 128);
-            const uint64_t b_lo = tc::smem_desc(bh + kBBytes, 128, (kK / 4) * 128);
+            const uint64_t a_hi = da + (uint64_t)((m * (kABytes / 2) + 256 * ks) >> 4);
+            const uint64_t a_lo = a_hi + (uint64_t)(kABytes >> 4);
+            const uint64_t b_hi = db + (uint64_t)((256 * ks) >> 4);
+            const uint64_t b_lo = b_hi + (uint64_t)(kBBytes >> 4);
             tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
             tc::mma_tf32(dcol + m * kNB, a_hi, b_lo, idesc, 1u);
             tc::mma_tf32(dcol + m * kNB, a_lo, b_hi, idesc, 1u);
           }
-        tc::mma_commit(&done[s]);
-        // U / source buffer (it + 2) & 3 was last read by chunk it - 2: its MMAs are done
-        // (drained) and its tile was generated (ready)
+        tc::mma_commit(&done[set]);
+        // U / source buffer (it + 2) & 3 was last read by chunk it - 2: the tile of
+        // chunk it is ready only after every generating thread saw chunk it - 2 done
         if (it + 2 < n_it) issue_load(it + 2);
       }
     }
@@ -225,33 +231,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     const int row0 = 128 * mb + 2 * lt;
     const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
     const uint32_t tcol = ((uint32_t)(32 * wq) << 16) + wm * kNB + 32 * wh;
-    // add the result of chunk it (accumulator set it & 1) to the registers, then release the set
-    auto drain = [&](int it) {
-      ok = ok && tc::mbar_wait(&done[it & 1], (it >> 1) & 1, kSpinLimit);
+    // synchronous read-back of chunk d (after the loop)
+    auto drain = [&](int d) {
+      ok = ok && tc::mbar_wait(&done[d % kSets], (d / kSets) & 1, kSpinLimit);
       if (!ok) return;
       tc::fence_after_sync();
       float v[16];
-      const uint32_t base = tmem + tcol + (it & 1) * (2 * kNB);
+      const uint32_t base = tmem + tcol + (d % kSets) * (2 * kNB);
       tc::tmem_ld16(base, v);
 #pragma unroll
       for (int x = 0; x < 16; ++x) acc[x] += v[x];
       tc::tmem_ld16(base + 16, v);
 #pragma unroll
       for (int x = 0; x < 16; ++x) acc[16 + x] += v[x];
-      tc::fence_before_sync();
-      mbar_arrive(&drained[it & 1]);
     };
     for (int it = 0; it < n_it; ++it) {
       const int s = it & 1, q = it & 3;
-      // A buffer s was last read by the MMAs of chunk it - 2, drained in the previous iteration
       ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
+      // chunk it - 2: its MMAs read A buffer s, and its accumulators are read back below
+      const int d = it - 2;
+      if (d >= 0) ok = ok && tc::mbar_wait(&done[d % kSets], (d / kSets) & 1, kSpinLimit);
       if (!ok) break;
+      if (d >= 0) tc::fence_after_sync();
+      const uint32_t dbase = tmem + tcol + ((d + kSets) % kSets) * (2 * kNB);
       const int j0 = (c0 + it) * kChunk;
       const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
       unsigned char* A = smem + kOffA + s * 2 * kABytes;  // hi part; the lo part kABytes further
       const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
 #pragma unroll
       for (int kk = 0; kk < kChunk / 8; ++kk) {
+        uint32_t v[16];
+        if (d >= 0) tc::tmem_ld16_async(dbase + 16 * kk, v);  // lands while this part is generated
         const int kb = (kChunk / 8) * h + kk;
         float va[4], vb[4];
         const int ja = j0 + 2 * kb, jb = ja + 1;
@@ -276,13 +286,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
           *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
           *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
         }
+        if (d >= 0) {
+          tc::tmem_wait_ld16(v);
+#pragma unroll
+          for (int x = 0; x < 16; ++x) acc[16 * kk + x] += __uint_as_float(v[x]);
+        }
+      }
+      if (d >= 0) {
+        tc::fence_before_sync();
+        mbar_arrive(&drained[d % kSets]);
       }
       tc::fence_proxy_async_smem();  // this thread's tile stores, visible to the tensor core
       mbar_arrive(&ready[s]);
-      if (it > 0) drain(it - 1);
-      if (!ok) break;
     }
-    if (ok && n_it > 0) drain(n_it - 1);
+    for (int d = max(0, n_it - 2); ok && d < n_it; ++d) drain(d);
   }
   const bool all_ok = __syncthreads_and(ok) != 0;
   if (!all_ok && tid == 0) atomicExch(err, 1);
