@@ -167,13 +167,14 @@ __device__ __forceinline__ void sym_pair(T dx, T dy, T dz, const T* nt, T at, T 
   // (w - 3) s^2 with w - 3 = 3 (t - 1) + e (kappa r)^2 and r s = 1: 3 (t - 1) s^2 + e kappa^2
   // (the self pair, s = 0, gets e kappa^2 instead of 0, but there c_i = c_j = t - 1 = 0)
   const T wm3s2 = tm1 * (T(3) * s2) + e * c.kappa2;
-  const T et1 = c.eps * t - T(1), te1 = t * c.inveps - T(1);
+  const T ts3 = t * s3;
   const T ci = nt[0] * dx + nt[1] * dy + nt[2] * dz;
   const T cj = ns[0] * dx + ns[1] * dy + ns[2] * dz;
   const T cij = nt[0] * ns[0] + nt[1] * ns[1] + nt[2] * ns[2];
   const T U = tm1 * cij - wm3s2 * (ci * cj);
   // s and s^3 folded into the four coefficients every update uses
-  const T ome_s = s - e * s, et1_s3 = et1 * s3, te1_s3 = te1 * s3, U_s3 = U * s3;
+  const T ome_s = s - e * s, U_s3 = U * s3;
+  const T et1_s3 = c.eps * ts3 - s3, te1_s3 = c.inveps * ts3 - s3;  // (eps t - 1) s^3, (t/eps - 1) s^3
   if (!TRANS) {
     Pt = (et1_s3 * cj) * als + (ome_s * as + Pt);
     Qt = U_s3 * als + ((te1_s3 * ci) * as + Qt);
