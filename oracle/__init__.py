@@ -68,6 +68,9 @@ def lib():
         L.orc_energy.argtypes = [I, P, P, P, D, D, I, P, P, P, P]
         L.orc_energy.restype = D
         L.orc_grad.argtypes = [I, P, P, P, D, D, D, I, P, P, P, P, P, P]
+        L.orc_potential.argtypes = [I, P, P, P, D, D, P, I, P, ctypes.c_int, I, P, P, D, P]
+        L.orc_coulomb.argtypes = [I, P, P, D]
+        L.orc_coulomb.restype = D
         _lib = L
     return _lib
 
@@ -181,6 +184,26 @@ def energy(x, nrm, area, eps, kappa, y, q, u):
     pr = np.zeros(nc)
     e = lib().orc_energy(n, _p(x), _p(nrm), _p(area), eps, kappa, nc, _p(y), _p(q), _p(u), _p(pr))
     return e, pr
+
+
+def potential(x, nrm, area, eps, kappa, u, pts, inside, y=None, q=None, eps_in=1.0):
+    """Potential at points ``pts`` (internal units) from surface values u:
+    Eq. eq_inside (with S1 of the charges y, q) when ``inside``, else the
+    exterior representation Eq. eqbim_2 with dphi2/dnu = psi / eps."""
+    x, nrm, area, u, pts = _c(x), _c(nrm), _c(area), _c(u), _c(pts, (-1, 3))
+    if y is None:
+        y, q = np.zeros((0, 3)), np.zeros(0)
+    y, q = _c(y, (-1, 3)), _c(q)
+    out = np.zeros(pts.shape[0])
+    lib().orc_potential(x.shape[0], _p(x), _p(nrm), _p(area), eps, kappa, _p(u), pts.shape[0], _p(pts),
+                        1 if inside else 0, q.shape[0], _p(y), _p(q), eps_in, _p(out))
+    return out
+
+
+def coulomb(y, q, eps_in):
+    """1/2 (1/eps_in) sum over ordered pairs k != l of q_k q_l G0 (internal units)."""
+    y, q = _c(y, (-1, 3)), _c(q)
+    return lib().orc_coulomb(q.shape[0], _p(y), _p(q), eps_in)
 
 
 def grad(x, nrm, area, eps, kappa, eps_in, y, q, u, lam):

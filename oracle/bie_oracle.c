@@ -29,6 +29,13 @@
  *   S2 = (1/eps_in) sum_k q_k dG0(x_i, y_k)/dnu_x.
  * Solvation energy (Eq. for E_sol), in the units of the unknowns:
  *   E = 1/2 sum_k q_k sum_j ds_j [K1(y_k, x_j) psi_j + K2(y_k, x_j) phi_j].
+ * Potential at a point p off the surface (Sec. 2.2.1):
+ *   p inside (Eq. eq_inside):  phi(p) = sum_j ds_j [K1(p, x_j) psi_j + K2(p, x_j) phi_j] + S1(p);
+ *   p outside (Eq. eqbim_2):   phi(p) = sum_j ds_j [-Gk(p, x_j) dphi2/dnu_j + dGk(p, x_j)/dnu_y phi_j]
+ *   with dphi2/dnu = (eps_in / eps_out) psi (flux continuity across the surface).
+ * Coulomb energy of the charges in the solute dielectric (the Coulomb part of
+ * E_free, Eq. free_energy, without the infinite self terms):
+ *   E_coul = 1/2 (1/eps_in) sum_{k != l} q_k q_l G0(y_k, y_l).
  */
 #include <math.h>
 #include <stdint.h>
@@ -372,4 +379,47 @@ void orc_grad(int64_t n, const double* x, const double* nrm, const double* area,
     dE_dq[k] = 0.5 * (sq + sl / eps_in);
     for (int m = 0; m < 3; ++m) dE_dy[3 * k + m] = 0.5 * q[k] * (gy[m] + gl[m] / eps_in);
   }
+}
+
+/* Potential at np points p (units of the unknowns), Eq. eq_inside for
+ * inside != 0 (then the nc charges y, q enter through S1) and Eq. eqbim_2
+ * otherwise.  u = [phi ; psi] on the n elements. */
+void orc_potential(int64_t n, const double* x, const double* nrm, const double* area, double eps,
+                   double kappa, const double* u, int64_t np, const double* p, int inside, int64_t nc,
+                   const double* y, const double* q, double eps_in, double* out) {
+  const double* phi = u;
+  const double* psi = u + n;
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < np; ++i) {
+    double s = 0.0, g[8];
+    for (int64_t j = 0; j < n; ++j) {
+      pair_derivs(p + 3 * i, NULL, x + 3 * j, nrm + 3 * j, kappa, g);
+      if (inside)
+        s += area[j] * ((g[0] - g[1]) * psi[j] + (eps * g[3] - g[2]) * phi[j]);
+      else
+        s += area[j] * (-g[1] * psi[j] / eps + g[3] * phi[j]);
+    }
+    if (inside) {
+      double s1 = 0.0;
+      for (int64_t k = 0; k < nc; ++k) {
+        pair_derivs(p + 3 * i, NULL, y + 3 * k, NULL, 0.0, g);
+        s1 += q[k] * g[0];
+      }
+      s += s1 / eps_in;
+    }
+    out[i] = s;
+  }
+}
+
+/* E_coul = 1/2 (1/eps_in) sum_{k != l} q_k q_l G0(y_k, y_l), units of the unknowns. */
+double orc_coulomb(int64_t nc, const double* y, const double* q, double eps_in) {
+  double e = 0.0;
+  for (int64_t k = 0; k < nc; ++k)
+    for (int64_t l = 0; l < nc; ++l) {
+      if (l == k) continue;
+      double d[3] = {y[3 * k] - y[3 * l], y[3 * k + 1] - y[3 * l + 1], y[3 * k + 2] - y[3 * l + 2]};
+      e += q[k] * q[l] * g0(sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    }
+  return 0.5 * e / eps_in;
 }

@@ -41,6 +41,17 @@ def born_surface(q, a, eps_in, eps_out, kappa):
     return phi, dphi
 
 
+def born_potential(r, q, a, eps_in, eps_out, kappa):
+    """Potential (kcal/mol/e) at distance r from a charge q at the centre of
+    the sphere: inside, the charge's Coulomb potential plus the constant
+    reaction potential of born_energy; outside, the screened field whose
+    surface value born_surface gives."""
+    r = np.asarray(r, dtype=np.float64)
+    inside = q / (eps_in * r) + q * (1.0 / (eps_out * a * (1.0 + kappa * a)) - 1.0 / (eps_in * a))
+    outside = q * np.exp(-kappa * (r - a)) / (eps_out * (1.0 + kappa * a) * r)
+    return COULOMB * np.where(r < a, inside, outside)
+
+
 def _log_deriv_k(nmax, z):
     """lambda_n = z k_n'(z) / k_n(z) for the modified spherical Bessel k_n.
 
@@ -104,3 +115,30 @@ def kirkwood_denergy_dr(r_k, a, eps_in, eps_out, kappa, nmax=60, q=1.0):
         fac = (eps_in * (n + 1.0) + eps_out * lam[n]) / (eps_in * n - eps_out * lam[n])
         s += fac * 2 * n * r_k ** (2 * n - 1) / a ** (2 * n + 1)
     return 0.5 * COULOMB * q * q * s / eps_in
+
+
+def kirkwood_reaction_potential(pos, q, pts, a, eps_in, eps_out, kappa, nmax=60):
+    """Reaction potential (kcal/mol/e) at points inside the sphere: the field
+    sum_k sum_n B_n(k) r^n P_n(cos gamma) of kirkwood_energy evaluated at
+    each point (gamma the angle between the point and charge k)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    q = np.asarray(q, dtype=np.float64).reshape(-1)
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, 3)
+    rk = np.linalg.norm(pos, axis=1)
+    rp = np.linalg.norm(pts, axis=1)
+    lam = _log_deriv_k(nmax, kappa * a)
+    fac = (eps_in * (np.arange(nmax + 1) + 1.0) + eps_out * lam) / (eps_in * np.arange(nmax + 1) - eps_out * lam)
+    rr = np.outer(rp, rk)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cosg = np.where(rr > 0, (pts @ pos.T) / np.where(rr > 0, rr, 1.0), 1.0)
+    cosg = np.clip(cosg, -1.0, 1.0)
+    x = rr / (a * a)
+    total = np.zeros_like(x)
+    p_prev, p_n = None, np.ones_like(cosg)
+    xn = np.ones_like(x)
+    for n in range(nmax + 1):
+        total += xn * (fac[n] / (eps_in * a)) * p_n
+        xn = xn * x
+        p_next = cosg.copy() if n == 0 else ((2 * n + 1) * cosg * p_n - n * p_prev) / (n + 1)
+        p_prev, p_n = p_n, p_next
+    return COULOMB * (total @ q)

@@ -356,3 +356,91 @@ def test_kirkwood_radial_force(orc):
         _, _, dy = orc.energy_gradient(p, method="direct")
         errs.append(abs(np.dot(dy[0], d) / exact - 1))
     assert errs[1] < errs[0] < 0.3
+
+
+# ------------------------------------------------------------------ potential off the surface, Coulomb energy
+def _born_points(scale_in, scale_out):
+    dirs = np.array([[1.0, 0.0, 0.0], [0.3, 0.5, 0.8], [-0.6, 0.2, -0.7]])
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    return np.concatenate([s * dirs for s in scale_in]), np.concatenate([s * dirs for s in scale_out])
+
+
+def test_point_potential_born_exact_surface_data(orc):
+    """With the exact Born surface values, Eq. eq_inside (inside, with the
+    centre charge's S1) and the exterior representation reproduce the closed
+    form up to the centroid-rule quadrature error, which falls 4x per level."""
+    pin, pout = _born_points((0.5, 1.2), (3.0, 6.0))
+    ein, eout = [], []
+    for lev in (2, 3, 4):
+        p = synth.born_problem(level=lev, eps_in=2.0)  # eps_in != 1 so that S1's 1/eps_in counts
+        n = p.centroids.shape[0]
+        phi, dphi = cf.born_surface(1.0, 2.0, p.eps_in, p.eps_out, p.kappa)
+        u = np.concatenate([np.full(n, phi / orc.KCAL), np.full(n, dphi / orc.KCAL)])
+        eps = p.eps_out / p.eps_in
+        vi = orc.KCAL * orc.potential(p.centroids, p.normals, p.areas, eps, p.kappa, u, pin, True,
+                                      np.zeros((1, 3)), np.array([1.0]), p.eps_in)
+        vo = orc.KCAL * orc.potential(p.centroids, p.normals, p.areas, eps, p.kappa, u, pout, False)
+        ri, ro = np.linalg.norm(pin, axis=1), np.linalg.norm(pout, axis=1)
+        ein.append(np.abs(vi / cf.born_potential(ri, 1.0, 2.0, p.eps_in, p.eps_out, p.kappa) - 1).max())
+        eout.append(np.abs(vo / cf.born_potential(ro, 1.0, 2.0, p.eps_in, p.eps_out, p.kappa) - 1).max())
+    for e in (ein, eout):
+        assert e[0] > 3.5 * e[1] > 3.5 * 3.5 * e[2]
+    assert ein[2] < 1e-3 and eout[2] < 2e-3
+
+
+def test_point_potential_kirkwood_reaction_field(orc):
+    """The surface integral of Eq. eq_inside alone (no charges passed) is the
+    reaction potential; from the oracle's own solve it converges to the
+    Kirkwood series at interior points as the sphere is refined."""
+    pts = np.array([[3.0, 1.0, -2.0], [-8.0, 4.0, 5.0], [0.0, -10.0, 2.0]])
+    errs = []
+    for lev in (2, 3, 4):
+        p = synth.kirkwood_problem(level=lev, n_charges=5)
+        y = p.charge_pos if p.charge_pos.ndim == 2 else p.charge_pos[0]
+        s = orc.solve(p, method="gmres", tol=1e-11, max_iter=400)
+        v = orc.KCAL * orc.potential(p.centroids, p.normals, p.areas, p.eps_out / p.eps_in, p.kappa, s.u, pts,
+                                     True)
+        ex = cf.kirkwood_reaction_potential(y, p.q[0], pts, 20.0, p.eps_in, p.eps_out, p.kappa)
+        errs.append(np.abs(v - ex).max() / np.abs(ex).max())
+    assert errs[0] > 2.0 * errs[1] > 2.0 * 2.0 * errs[2]
+    assert errs[2] < 0.02
+
+
+def test_exterior_potential_far_field_is_total_charge(orc):
+    """Without salt the exterior potential far away is that of the total
+    charge in the solvent dielectric, Q / (eps_out R) (Gauss's law), for
+    the oracle's discrete solution of an off-centre charge set."""
+    p = synth.kirkwood_problem(level=3, n_charges=4)
+    p.kappa = 0.0
+    s = orc.solve(p, method="gmres", tol=1e-11, max_iter=400)
+    dirs = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [-0.5, 0.5, -0.7]])
+    dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+    R = 20000.0
+    v = orc.KCAL * orc.potential(p.centroids, p.normals, p.areas, p.eps_out / p.eps_in, 0.0, s.u, R * dirs, False)
+    Q = float(np.sum(p.q[0]))
+    # the discrete solution's flux is off by its discretisation error (1.7 % at
+    # level 3, 0.9 % at level 4); a dropped or flipped term is off by O(1)
+    np.testing.assert_allclose(v, 332.0716 * Q / (p.eps_out * R), rtol=0.03)
+
+
+def test_coulomb_energy_textbook_values(orc):
+    """Two unit charges 1 A apart in vacuum: 332.0716 kcal/mol; charges
+    (1, 1, -1) on an equilateral triangle of side 2 in eps_in = 4: the three
+    pair terms sum to -1, so E = -332.0716 / (4 * 2).  Rigid motions and a
+    permutation leave it unchanged; scaling the lengths by s scales it by 1/s."""
+    e2 = orc.KCAL * orc.coulomb(np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]]), np.array([1.0, 1.0]), 1.0)
+    assert e2 == pytest.approx(332.0716, rel=1e-14)
+    tri = 2.0 * np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.5, math.sqrt(3) / 2, 0.0]])
+    q = np.array([1.0, 1.0, -1.0])
+    e3 = orc.KCAL * orc.coulomb(tri, q, 4.0)
+    assert e3 == pytest.approx(-332.0716 / 8.0, rel=1e-13)
+    rng = np.random.default_rng(9)
+    y = rng.standard_normal((7, 3))
+    qq = rng.standard_normal(7)
+    e = orc.coulomb(y, qq, 2.0)
+    c, sn = math.cos(0.7), math.sin(0.7)
+    Rm = np.array([[c, -sn, 0.0], [sn, c, 0.0], [0.0, 0.0, 1.0]])
+    perm = rng.permutation(7)
+    assert orc.coulomb(y @ Rm.T + [3.0, -1.0, 2.0], qq, 2.0) == pytest.approx(e, rel=1e-12)
+    assert orc.coulomb(y[perm], qq[perm], 2.0) == pytest.approx(e, rel=1e-12)
+    assert orc.coulomb(2.5 * y, qq, 2.0) == pytest.approx(e / 2.5, rel=1e-12)
