@@ -168,6 +168,36 @@ bipb_status bipb_energy(bipb_surface s, double* e_sol);
 bipb_status bipb_surface_potential(bipb_surface s, double* phi, double* dphi_dn);
 
 /*
+ * Potential (kcal/mol/e) at points off the surface, from the last solve, for
+ * every configuration: host arrays pts (n_pts x 3, A, the frame of the
+ * surface's centroids) and phi (n_rhs x n_pts).  The caller states where the
+ * points lie (no inside test is made):
+ *   BIPB_REGION_INSIDE  (the molecule, Omega_1): Eq. eq_inside,
+ *     phi(p) = sum_j ds_j [K1(p, x_j) dphi/dnu_j + K2(p, x_j) phi_j] + S1(p);
+ *   BIPB_REGION_OUTSIDE (the solvent, Omega_2): the exterior representation
+ *     Eq. eqbim_2, phi(p) = sum_j ds_j [-Gk(p, x_j) (eps_in/eps_out) dphi/dnu_j
+ *     + dGk(p, x_j)/dnu_y phi_j] (flux continuity gives the exterior
+ *     normal derivative).
+ * Pair arithmetic in double-float (about 1e-14 relative), FP64 sums in a
+ * fixed order.  Single-surface handles; at most 2^24 points per call.
+ * Points on or very near the surface (closer than the element size) get
+ * the quadrature error of the centroid rule there.
+ */
+typedef enum { BIPB_REGION_INSIDE = 0, BIPB_REGION_OUTSIDE = 1 } bipb_region;
+bipb_status bipb_potential_at(bipb_surface s, int region, int64_t n_pts, const double* pts, double* phi);
+
+/*
+ * Electrostatic free energy (Eq. free_energy) per configuration, kcal/mol,
+ * host arrays (either may be NULL):
+ *   e_coul = 332.0716 / eps_in * 1/2 sum_{k != l} q_k q_l / |y_k - y_l|
+ *            (the charges' Coulomb energy in the solute dielectric; the
+ *            infinite self terms k = l of S1(y_k) are left out);
+ *   e_free = E_sol + e_coul.
+ * Requires a successful bipb_solve.  FP64, O(Nc^2) pairs, fixed order.
+ */
+bipb_status bipb_energy_free(bipb_surface s, double* e_free, double* e_coul);
+
+/*
  * Gradient of the solvation energy (kcal/mol) of every configuration with
  * respect to its charges (host, n_rhs x nc, kcal/mol/e) and charge positions
  * (host, n_rhs x nc x 3, kcal/mol/A), at fixed surface, from one adjoint
@@ -229,7 +259,8 @@ typedef enum {
   BIPB_KERNEL_MATVECDF = 8,   /* double-float mat-vec pair kernel */
   BIPB_KERNEL_MATVECDF_T = 9, /* double-float transposed mat-vec pair kernel */
   BIPB_KERNEL_MATVEC_TC = 10, /* tensor-core multi-RHS mat-vec kernel */
-  BIPB_KERNEL_KINDS = 11
+  BIPB_KERNEL_POTENTIAL = 11, /* potential-at-points pair kernels */
+  BIPB_KERNEL_KINDS = 12
 } bipb_kernel_kind;
 
 /* Turn timing on (1) or off (0); turning it on clears the totals. */

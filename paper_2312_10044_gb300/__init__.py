@@ -42,12 +42,14 @@ EXPORTED = (
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
     "bipb_autotune", "bipb_matvec_variant", "bipb_surface_create_batch", "bipb_charges_set_batch",
-    "bipb_symmetric_pairs",
+    "bipb_symmetric_pairs", "bipb_potential_at", "bipb_energy_free",
 )
 MATVEC32_VARIANTS = 10
 
 KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad",
-                "matvec_df", "matvec_df_t", "matvec_tc")
+                "matvec_df", "matvec_df_t", "matvec_tc", "potential")
+REGION_INSIDE = 0
+REGION_OUTSIDE = 1
 
 
 class bipb_medium(ctypes.Structure):
@@ -128,6 +130,8 @@ def load_library():
         "bipb_charges_set_batch": ([P, P, P, P], st),
         "bipb_matvec_variant": ([P, I], st),
         "bipb_symmetric_pairs": ([P, I], st),
+        "bipb_potential_at": ([P, I, I64, P, P], st),
+        "bipb_energy_free": ([P, P, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -269,6 +273,22 @@ class Surface:
         e = np.zeros(self.n_systems)
         _check(self._L.bipb_energy(self._h, _hp(e)))
         return e
+
+    def potential_at(self, pts, inside=True):
+        """Potential (kcal/mol/e) at points (n, 3) A of the solute (inside) or
+        the solvent (outside), shape (n_systems, n)."""
+        p = _host(pts, (-1, 3))
+        out = np.zeros((self.n_systems, p.shape[0]))
+        region = REGION_INSIDE if inside else REGION_OUTSIDE
+        _check(self._L.bipb_potential_at(self._h, region, p.shape[0], _hp(p), _hp(out)))
+        return out
+
+    def energy_free(self):
+        """(E_free, E_coul) per system, kcal/mol: E_free = E_sol + E_coul."""
+        ef = np.zeros(self.n_systems)
+        ec = np.zeros(self.n_systems)
+        _check(self._L.bipb_energy_free(self._h, _hp(ef), _hp(ec)))
+        return ef, ec
 
     def surface_potential(self):
         """(phi, dphi/dnu): (n_rhs, N) arrays, or lists per surface for a batch handle."""

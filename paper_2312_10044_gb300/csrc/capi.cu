@@ -526,6 +526,81 @@ bipb_status bipb_surface_potential(bipb_surface h, double* phi, double* dphi_dn)
   });
 }
 
+bipb_status bipb_potential_at(bipb_surface h, int region, int64_t n_pts, const double* pts, double* phi) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(region == BIPB_REGION_INSIDE || region == BIPB_REGION_OUTSIDE, "unknown region");
+    BIPB_REQUIRE(n_pts >= 0 && n_pts <= ((int64_t)1 << 24), "n_pts must be in [0, 2^24]");
+    BIPB_REQUIRE(n_pts == 0 || (pts != nullptr && phi != nullptr), "pts or phi is NULL");
+    BIPB_REQUIRE(!s->batch, "bipb_potential_at takes single-surface handles");
+    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+    if (n_pts == 0) return;
+    const SysLayout& L = s->lay;
+    // the points in the frame of the surface's centred copies
+    const double* c = &s->part_center[0];
+    std::vector<double4_32a> p1((size_t)n_pts), p2((size_t)2 * n_pts);
+    for (int64_t i = 0; i < n_pts; ++i) {
+      double d[3];
+      for (int k = 0; k < 3; ++k) {
+        BIPB_REQUIRE(std::isfinite(pts[3 * i + k]), "non-finite point");
+        d[k] = pts[3 * i + k] - c[k];
+      }
+      p1[i] = double4_32a{d[0], d[1], d[2], 0.0};
+      p2[2 * i] = p1[i];
+      p2[2 * i + 1] = double4_32a{0.0, 0.0, 0.0, 0.0};
+    }
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    s->grow(s->pts, (size_t)n_pts);
+    s->grow(s->pts2, (size_t)2 * n_pts);
+    s->grow(s->pot, (size_t)L.K * n_pts);
+    BIPB_CUDA(cudaMemcpyAsync(s->pts.p, p1.data(), p1.size() * sizeof(double4_32a), cudaMemcpyHostToDevice,
+                              s->stream));
+    BIPB_CUDA(cudaMemcpyAsync(s->pts2.p, p2.data(), p2.size() * sizeof(double4_32a), cudaMemcpyHostToDevice,
+                              s->stream));
+    potential_pass(s, L, s->solved_medium, s->u.p, region == BIPB_REGION_INSIDE, (int)n_pts, s->pts.p, s->pts2.p,
+                   s->pot.p);
+    BIPB_CUDA(cudaMemcpyAsync(phi, s->pot.p, (size_t)L.K * n_pts * sizeof(double), cudaMemcpyDeviceToHost,
+                              s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    for (int64_t i = 0; i < (int64_t)L.K * n_pts; ++i) phi[i] *= kKcal;
+  });
+}
+
+bipb_status bipb_energy_free(bipb_surface h, double* e_free, double* e_coul) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(e_free || e_coul, "both outputs are NULL");
+    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+    const SysLayout& L = s->lay;
+    std::vector<int4> tab(L.K);
+    for (int k = 0; k < L.K; ++k) tab[k] = make_int4(0, 0, L.nc[k], L.chg_off[k]);
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    s->grow(s->coul_tab, (size_t)L.K);
+    BIPB_CUDA(cudaMemcpyAsync(s->coul_tab.p, tab.data(), tab.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                              s->stream));
+    int nc_max = 1;
+    for (int k = 0; k < L.K; ++k) nc_max = std::max(nc_max, L.nc[k]);
+    s->grow(s->coul, (size_t)L.K * ((nc_max + 255) / 256));
+    int blocks = 0;
+    coulomb_pass(s, L, s->coul_tab.p, s->coul.p, &blocks);
+    std::vector<double> part((size_t)L.K * blocks), es(L.K);
+    BIPB_CUDA(cudaMemcpyAsync(part.data(), s->coul.p, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                              s->stream));
+    BIPB_CUDA(cudaMemcpyAsync(es.data(), s->e_dev.p, es.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    for (int k = 0; k < L.K; ++k) {
+      double acc = 0.0;
+      for (int b = 0; b < blocks; ++b) acc += part[(size_t)k * blocks + b];
+      // 1/2 (1/eps_in) sum_{c != l} q_c q_l / (4 pi r) in internal units, times 4 pi 332.0716
+      const double ec = 0.5 * 332.0716 / s->solved_medium.eps_in * acc;
+      if (e_coul) e_coul[k] = ec;
+      if (e_free) e_free[k] = es[k] + ec;
+    }
+  });
+}
+
 bipb_status bipb_energy_grad(bipb_surface h, const bipb_solve_params* p, double* dE_dq, double* dE_dpos) {
   bipb_status st = BIPB_OK;
   bipb_status rc = guarded([&] {

@@ -359,6 +359,23 @@ __device__ __forceinline__ void df_reaction_pair(const df* y, const df* x, df a,
   acc = df_add(acc, df_mul(p, s));
 }
 
+// Potential at a point y in the solvent from one element (forward record: x,
+// a = ds psi, m = ds phi n), d = y - x: the exterior representation (Eq.
+// eqbim_2) with dphi2/dnu = psi / eps (flux continuity), times 4 pi:
+//   4 pi phi += s [ t (m.d) s^2 - (1/eps) e a ]   (-Gk dphi2/dnu + dGk/dnu_y phi)
+__device__ __forceinline__ void df_exterior_pair(const df* y, const df* x, df a, const df* m, const DFConst& c,
+                                                 const df* tab, df& acc) {
+  const df d0 = df_sub(y[0], x[0]), d1 = df_sub(y[1], x[1]), d2 = df_sub(y[2], x[2]);
+  const df r2 = df_sumsq3(d0, d1, d2);
+  const df s = df_rsqrt(r2);
+  const df kr = df_mul(df_mul(r2, s), c.kappa);
+  const df e = df_exp_neg(df_neg(kr), c, tab);
+  const df t = df_add(df_mul(e, kr), e);
+  const df cm = df_dot3(m[0], m[1], m[2], d0, d1, d2);
+  const df p = df_sub(df_mul(df_mul(t, cm), df_sqr(s)), df_mul(df_mul(c.inveps, e), a));
+  acc = df_add(acc, df_mul(p, s));
+}
+
 }  // namespace bipb
 
 namespace bipb {

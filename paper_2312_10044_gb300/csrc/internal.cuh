@@ -153,7 +153,7 @@ constexpr int kMaxRestart = 64;
 
 // Per-kernel CUDA-event timing of the pair kernels (off by default).
 enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTMvDF, kTMvDFT, kTMvTC,
-                 kTKinds };
+                 kTPotential, kTKinds };
 
 struct EventPair {
   int kind;
@@ -232,6 +232,10 @@ struct Surface {
   DevBuf<int> rhs_idx;  // right-hand-side indices of a compacted multi-RHS pass
   DevBuf<float4> geodf;  // multi-RHS df64 pass: geometry as df64 records (4 float4 each)
   DevBuf<float4> udf;    // multi-RHS df64 pass: right-hand sides as df64 (phi, psi) pairs
+  DevBuf<double4_32a> pts, pts2;  // points of bipb_potential_at: (p, 0); (p, 0), (0, 0)
+  DevBuf<double> pot;             // their potentials, n_rhs x n_pts
+  DevBuf<double> coul;            // Coulomb block sums
+  DevBuf<int4> coul_tab;          // {0, 0, nc, chg_off} per system
 
   // charges: every system's charge records (y - center, q), back to back
   int64_t nc = 0;  // charges per configuration (single surface)
@@ -342,6 +346,15 @@ void source_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* b
 void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, double* phi_reac,
                    double* e_out);
 // energy row c of every system: E = 1/2 c.u
+// Potential at n_pts points (device records: pts one (p, 0) per point, pts2 two,
+// (p, 0) and a zero normal) for every system, internal units, into out[k n_pts + q]:
+// Eq. eq_inside when inside (with S1 of the system's charges), else the
+// exterior representation (Eq. eqbim_2).
+void potential_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, bool inside,
+                    int n_pts, const double4_32a* pts, const double4_32a* pts2, double* out);
+// part[k * blocks + b]: block sums of sum_{c != l} q_c q_l / |y_c - y_l| of system k;
+// tab[k] = {0, 0, nc, chg_off}.
+void coulomb_pass(Surface* s, const SysLayout& L, const int4* tab, double* part, int* blocks);
 void energy_row_pass(Surface* s, const SysLayout& L, const bipb_medium& m, double* c);
 // dE/dq (per charge) and dE/dy (3 per charge), internal units, from u and the adjoint lam
 void grad_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, const double* lam, double* dq,

@@ -222,6 +222,19 @@ struct ReactionPolicy {
   }
 };
 
+// Potential at a point y in the solvent from the surface in df64 (the same
+// forward df record as the reaction pass), the exterior representation:
+//   4 pi phi(y) += s [ t (m_j.d) s^2 - (1/eps) e a_j ],  d = y - x_j
+struct ExteriorPolicy : ReactionPolicy {
+  template <bool MASK>
+  __device__ static void pair(const Args& a, const Tgt& t, const float4* r, bool, Acc& acc) {
+    const float4 A = r[0], B = r[1], C = r[2], D = r[3];
+    const df xs[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    const df m[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
+    df_exterior_pair(t.y, xs, df{A.w, B.w}, m, a.c, df_exp_table(), acc.p);
+  }
+};
+
 // Energy row c in df64: target element j, source charge k (df record
 // (y_k, q_k)), d = y_k - x_j:
 //   4 pi K2(y_k, x_j) = (eps t - 1) (n_j.d) s^3,  4 pi K1(y_k, x_j) = (1 - e) s
@@ -613,6 +626,51 @@ __global__ void k_reduce_reaction(const int4* __restrict__ tab, const int4* __re
   if (threadIdx.x == 0 && e_out) e_out[k] = 0.5 * kKcal * red[0];
 }
 
+// Potential at points: out[k n_pts + q] (+)= scale * sum over splits of
+// part[tab[k].z + sp * stride * n_pts + q], splits added in order.
+__global__ void k_reduce_points(const int4* __restrict__ tab, const double* __restrict__ part, int n_pts,
+                                int stride, double scale, int accumulate, double* __restrict__ out) {
+  const int k = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_pts) return;
+  const int4 T = tab[k];
+  double acc = 0.0;
+  for (int sp = 0; sp < T.y; ++sp) acc += part[(size_t)T.z + (size_t)sp * stride * n_pts + q];
+  double* o = out + (size_t)k * n_pts + q;
+  *o = (accumulate ? *o : 0.0) + scale * acc;
+}
+
+// Coulomb energy of the charges of system k in the solute, Eq. free_energy
+// without the self terms: part[k * gridDim.x + b] = sum over the block's
+// charges c of q_c sum_{l != c} q_l / |y_c - y_l| (FP64, l in order, then a
+// fixed-order tree over the block).
+__global__ void k_coulomb(const int4* __restrict__ lay, const double4_32a* __restrict__ chg,
+                          double* __restrict__ part) {  // lay[k] = {0, 0, nc, chg_off}
+  __shared__ double red[256];
+  const int k = blockIdx.y;
+  const int c0 = lay[k].w, nc = lay[k].z;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (c < nc) {
+    const double4_32a a = chg[c0 + c];
+    double row = 0.0;
+    for (int l = 0; l < nc; ++l) {
+      if (l == c) continue;
+      const double4_32a b = chg[c0 + l];
+      const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+      row += b.w * rsqrt(dx * dx + dy * dy + dz * dz);
+    }
+    v = a.w * row;
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = red[0];
+}
+
 __global__ void k_energy_row_reduce(const int4* __restrict__ lay, const int4* __restrict__ tab,
                                     const double* __restrict__ part, const double4_32a* __restrict__ tgt64,
                                     double* __restrict__ c) {
@@ -683,7 +741,7 @@ PairConst<T> pair_const(const bipb_medium& m) {
 int blocks_for(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1) / bs); }
 
 enum PassId { kPassMv64 = 1, kPassMv64T, kPassMvDF, kPassMvDFT, kPassMv32 = 16, kPassMv32T = 32, kPassSource = 48,
-              kPassReaction, kPassRow, kPassGrad };
+              kPassReaction, kPassRow, kPassGrad, kPassPotIn, kPassPotOut, kPassPotSrc };
 
 DFConst df_const_impl(const bipb_medium& m) {
   auto split = [](double v) {
@@ -993,6 +1051,61 @@ void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const d
   ReactionPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(m)};
   launch_items<ReactionPolicy, float4, NT, TPT, CH>(s, kTReaction, plan, a, s->recdf.p, nullptr, 0);
   k_reduce_reaction<<<L.K, 1024, 0, s->stream>>>(plan->tab.p, lay, s->part64.p, s->chg.p, phi_reac, e_out);
+  BIPB_LAUNCHED(s);
+}
+
+void potential_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const double* u, bool inside,
+                    int n_pts, const double4_32a* pts, const double4_32a* pts2, double* out) {
+  constexpr int NT = 128, TPT = 1, CH = 64;
+  // surface integral: targets are the points (shared by every system), sources the elements
+  std::vector<PassSys> sys(L.K);
+  for (int k = 0; k < L.K; ++k) sys[k] = PassSys{0, n_pts, L.vec_off[k] / 2, L.n[k]};
+  s->grow(s->recdf, (size_t)2 * L.len);  // 4 float4 per element
+  const int4* lay = s->lay_dev(L);
+  k_pack_df<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, false, s->tgt64.p, u, s->recdf.p,
+                                                                          nullptr, 0);
+  BIPB_LAUNCHED(s);
+  ReactionPolicy::Args a{pts, nullptr, df_const_impl(m)};
+  ItemPlan* plan;
+  if (inside) {
+    plan = plan_pass<ReactionPolicy, float4, NT, TPT, CH>(s, kPassPotIn, sys, CH);
+    s->grow(s->part64, (size_t)plan->part_len);
+    a.part = s->part64.p;
+    launch_items<ReactionPolicy, float4, NT, TPT, CH>(s, kTPotential, plan, a, s->recdf.p, nullptr, 0);
+  } else {
+    plan = plan_pass<ExteriorPolicy, float4, NT, TPT, CH>(s, kPassPotOut, sys, CH);
+    s->grow(s->part64, (size_t)plan->part_len);
+    a.part = s->part64.p;
+    launch_items<ExteriorPolicy, float4, NT, TPT, CH>(s, kTPotential, plan, a, s->recdf.p, nullptr, 0);
+  }
+  k_reduce_points<<<dim3(blocks_for(n_pts, 256), L.K), 256, 0, s->stream>>>(plan->tab.p, s->part64.p, n_pts, 1,
+                                                                           kInv4Pi, 0, out);
+  BIPB_LAUNCHED(s);
+  if (!inside) return;
+  // S1 at the points (Eq. eq_inside): targets the points with a zero normal, sources the charges
+  int n_chg = 0;
+  for (int k = 0; k < L.K; ++k) {
+    sys[k] = PassSys{0, n_pts, L.chg_off[k], L.nc[k]};
+    n_chg = std::max(n_chg, L.chg_off[k] + L.nc[k]);
+  }
+  if (n_chg == 0) return;
+  ItemPlan* sp = plan_pass<SourcePolicy, float4, NT, TPT, CH>(s, kPassPotSrc, sys, CH);
+  s->grow(s->chgdf, (size_t)2 * n_chg);
+  s->grow(s->part64, (size_t)sp->part_len);
+  k_pack_chg_df<<<blocks_for(n_chg, 256), 256, 0, s->stream>>>(n_chg, s->chg.p, s->chgdf.p);
+  BIPB_LAUNCHED(s);
+  SourcePolicy::Args b{pts2, s->part64.p};
+  launch_items<SourcePolicy, float4, NT, TPT, CH>(s, kTPotential, sp, b, s->chgdf.p, nullptr, 0);
+  k_reduce_points<<<dim3(blocks_for(n_pts, 256), L.K), 256, 0, s->stream>>>(sp->tab.p, s->part64.p, n_pts, 2,
+                                                                           kInv4Pi / m.eps_in, 1, out);
+  BIPB_LAUNCHED(s);
+}
+
+void coulomb_pass(Surface* s, const SysLayout& L, const int4* tab, double* part, int* blocks) {
+  int nc_max = 1;
+  for (int k = 0; k < L.K; ++k) nc_max = std::max(nc_max, L.nc[k]);
+  *blocks = blocks_for(nc_max, 256);
+  k_coulomb<<<dim3(*blocks, L.K), 256, 0, s->stream>>>(tab, s->chg.p, part);
   BIPB_LAUNCHED(s);
 }
 

@@ -567,3 +567,71 @@ def test_multi_rhs_df64_matvec_matches_oracle(bipb, orc, n_rhs):
     for r in (0, n_rhs // 2, n_rhs - 1):
         ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
         np.testing.assert_allclose(Y[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- potential at points, free energy
+def _ball(rng, n, r0, r1):
+    """n points with radii uniform in [r0, r1) and uniform directions."""
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    return d * rng.uniform(r0, r1, n)[:, None]
+
+
+def test_potential_at_points_matches_oracle(bipb, orc):
+    """Potential at 300 points inside the molecule (Eq. eq_inside, with S1 of
+    the charges) and 257 points in the solvent (the exterior
+    representation), for two charge sets, against the oracle's potential of
+    its own solve (both FP64 to 1e-12): 1e-9 of the largest value."""
+    base = synth.protein_like_problem(level=3, n_charges=12)
+    batch = synth.batched_charges(base, n_rhs=2, n_charges=12)
+    eps = batch.eps_out / batch.eps_in
+    rng = np.random.default_rng(40)
+    pin = _ball(rng, 300, 0.0, 20.0)   # the surface lies at r >= 25.5
+    pout = _ball(rng, 257, 31.0, 80.0)  # ... and at r <= 29.3
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.set_charges(batch.charge_pos, batch.q)
+        with pytest.raises(bipb.BipbError):
+            s.potential_at(pin, inside=True)  # no solve yet
+        s.solve(tol=1e-12, precision=bipb.FP64)
+        vin = s.potential_at(pin, inside=True)
+        vout = s.potential_at(pout, inside=False)
+        assert s.potential_at(np.zeros((0, 3))).shape == (2, 0)
+    for r in range(2):
+        ref = orc.solve(batch, rhs=r, method="gmres", tol=1e-12)
+        y, q = batch.charge_pos[r], batch.q[r]
+        rin = orc.KCAL * orc.potential(batch.centroids, batch.normals, batch.areas, eps, batch.kappa, ref.u, pin,
+                                       True, y, q, batch.eps_in)
+        rout = orc.KCAL * orc.potential(batch.centroids, batch.normals, batch.areas, eps, batch.kappa, ref.u, pout,
+                                        False)
+        np.testing.assert_allclose(vin[r], rin, rtol=0, atol=1e-9 * np.abs(rin).max())
+        np.testing.assert_allclose(vout[r], rout, rtol=0, atol=1e-9 * np.abs(rout).max())
+
+
+def test_energy_free_matches_oracle(bipb, orc):
+    """E_free = E_sol + E_coul per charge set (Eq. free_energy without the
+    self terms) against the oracle; E_coul alone to 1e-12."""
+    base = synth.protein_like_problem(level=3, n_charges=300)
+    batch = synth.batched_charges(base, n_rhs=3, n_charges=300)
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.set_charges(batch.charge_pos, batch.q)
+        s.solve(tol=1e-12, precision=bipb.FP64)
+        e_sol = s.energy()
+        e_free, e_coul = s.energy_free()
+    for r in range(3):
+        ec = orc.KCAL * orc.coulomb(batch.charge_pos[r], batch.q[r], batch.eps_in)
+        assert e_coul[r] == pytest.approx(ec, rel=1e-12)
+        ref = orc.solve(batch, rhs=r, method="gmres", tol=1e-12)
+        assert e_free[r] == pytest.approx(ref.energy_kcal + ec, rel=1e-10)
+        assert e_free[r] - e_sol[r] == pytest.approx(e_coul[r], rel=1e-12)
+
+
+def test_potential_at_rejects_batch_handles(bipb):
+    probs = [synth.born_problem(level=1), synth.born_problem(level=2)]
+    with bipb.BatchSurface([(q.centroids, q.normals, q.areas) for q in probs]) as s:
+        s.set_charges([(q.charge_pos, q.q[0]) for q in probs])
+        s.solve(tol=1e-10, precision=bipb.FP64)
+        with pytest.raises(bipb.BipbError):
+            s.potential_at(np.zeros((3, 3)))
+        ef, ec = s.energy_free()  # the free energy works per surface
+        np.testing.assert_allclose(ec, 0.0)  # one charge per surface: no pairs
+        np.testing.assert_allclose(ef, s.energy(), rtol=1e-14)
