@@ -290,6 +290,21 @@ def run_configs(args):
                 res[f"solve_ms_{name}"] = ms
                 res[f"{name}_info"] = info[0]
             res["energy_kcal"] = float(s.energy()[0])
+            # potential maps (10^4 points in the molecule, 10^4 in the solvent) and the free energy
+            rng = np.random.default_rng(11)
+            dirs = rng.standard_normal((20000, 3))
+            dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+            radii = np.concatenate([rng.uniform(0.0, 20.0, 10000), rng.uniform(31.0, 80.0, 10000)])
+            pts = dirs * radii[:, None]
+            s.potential_at(pts[:10000], inside=True)
+            ms_in, _ = _timed(lambda: s.potential_at(pts[:10000], inside=True), torch)
+            ms_out, _ = _timed(lambda: s.potential_at(pts[10000:], inside=False), torch)
+            ms_free, (ef, ec) = _timed(lambda: s.energy_free(), torch)
+            res["potential_ms_10k_inside"] = ms_in
+            res["potential_ms_10k_outside"] = ms_out
+            res["energy_free_ms"] = ms_free
+            res["energy_free_kcal"] = float(ef[0])
+            res["energy_coulomb_kcal"] = float(ec[0])
             # plain FP64 GMRES: one run (26+ FP64 mat-vecs of ~0.7 s)
             if not args.no_fp64:
                 prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.FP64)
