@@ -50,6 +50,8 @@ KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "r
                 "matvec_df", "matvec_df_t", "matvec_tc", "potential")
 REGION_INSIDE = 0
 REGION_OUTSIDE = 1
+PRECOND_NONE = 0
+PRECOND_SELF = 1
 
 
 class bipb_medium(ctypes.Structure):
@@ -66,6 +68,8 @@ class bipb_solve_params(ctypes.Structure):
         ("inner_max_iter", ctypes.c_int),
         ("inner_tol", ctypes.c_double),
         ("x0", ctypes.c_void_p),
+        ("precond", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -183,9 +187,9 @@ def medium(eps_in=1.0, eps_out=80.0, kappa=0.1257):
 
 
 def solve_params(eps_in=1.0, eps_out=80.0, kappa=0.1257, tol=1e-8, restart=10, max_iter=1000,
-                 precision=MIXED, inner_max_iter=0, inner_tol=0.0, x0=None):
+                 precision=MIXED, inner_max_iter=0, inner_tol=0.0, x0=None, precond=PRECOND_NONE):
     p = bipb_solve_params(bipb_medium(eps_in, eps_out, kappa), tol, restart, max_iter, precision,
-                          inner_max_iter, inner_tol, None)
+                          inner_max_iter, inner_tol, None, precond, 0)
     return p
 
 

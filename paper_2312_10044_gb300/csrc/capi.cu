@@ -89,6 +89,8 @@ void validate_params(const bipb_solve_params* p) {
                "precision must be FP64, MIXED, DF64, MIXED_DF64 or MIXED_TF32");
   BIPB_REQUIRE(p->inner_max_iter >= 0, "inner_max_iter must be >= 0");
   BIPB_REQUIRE(std::isfinite(p->inner_tol) && p->inner_tol >= 0 && p->inner_tol < 1, "inner_tol must lie in [0, 1)");
+  BIPB_REQUIRE(p->precond == BIPB_PRECOND_NONE || p->precond == BIPB_PRECOND_SELF, "unknown precond");
+  BIPB_REQUIRE(p->reserved == 0, "reserved must be 0");
 }
 
 }  // namespace

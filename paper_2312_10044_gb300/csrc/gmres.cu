@@ -98,6 +98,17 @@ __device__ __forceinline__ void block_dots(int j, int m1, int64_t len, const dou
   }
 }
 
+// Preconditioning by the element self blocks (Sec. 2.2.4 with one element per
+// leaf): with the self pair omitted, element i's 2 x 2 block of A is
+// diag(1/2 (1 + eps), 1/2 (1 + 1/eps)), so M^-1 scales the phi rows by pre.x
+// and the psi rows by pre.y.  It is applied on the right, A M^-1 y = r,
+// d = M^-1 y: GMRES then minimises the true residual, which is what the
+// stopping tests and the refinement read.  lay[k] = {geo_off, n, vec_off,
+// chg_off} of system k.
+__device__ __forceinline__ double precond_factor(int x, int4 Lk, double2 pre) {
+  return (x - Lk.z < Lk.y) ? pre.x : pre.y;
+}
+
 __global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V, const double* __restrict__ w,
                        double* __restrict__ part, const DevState* st, const int4* __restrict__ blk) {
   const int4 B = blk[blockIdx.x];
@@ -188,7 +199,8 @@ __device__ void givens_step(int j, int m, int sys, double* __restrict__ H, doubl
   if (S.conv || S.stop || j + 1 == S.m) S.skip = 1;
 }
 
-// out = w / ||w|| per system; j >= 0: H[j+1, j] = ||w|| and the Givens step of
+// out = w / ||w|| per system (and tz = M^-1 out when preconditioned); j >= 0:
+// H[j+1, j] = ||w|| and the Givens step of
 // column j, both by the last block of the system to finish (every block has
 // then passed its skip test, so the step may set skip; the blocks' arrival
 // is counted with an atomic after a fence, no block waits); j < 0: start of
@@ -196,7 +208,8 @@ __device__ void givens_step(int j, int m, int sys, double* __restrict__ H, doubl
 __global__ void k_normalize(int j, int m, const double* __restrict__ w, double* __restrict__ out,
                             const double* __restrict__ part1, double* __restrict__ H, DevState* st,
                             const int4* __restrict__ blk, const int4* __restrict__ sysb, int set_bnorm,
-                            double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g) {
+                            double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                            double* __restrict__ tz, const int4* __restrict__ lay, double2 pre) {
   const int4 B = blk[blockIdx.x];
   if (j >= 0 ? st[B.x].skip : !st[B.x].active) return;
   const int4 S = sysb[B.x];
@@ -209,6 +222,10 @@ __global__ void k_normalize(int j, int m, const double* __restrict__ w, double* 
   const double v = nrm;
   const double inv = v > 0.0 ? 1.0 / v : 0.0;
   for (int x = B.y + threadIdx.x; x < B.z; x += kBS) out[x] = w[x] * inv;
+  if (tz != nullptr) {  // the next mat-vec's input M^-1 out
+    const int4 Lk = lay[B.x];
+    for (int x = B.y + threadIdx.x; x < B.z; x += kBS) tz[x] = precond_factor(x, Lk, pre) * (w[x] * inv);
+  }
   if (threadIdx.x != 0) return;
   if (j < 0) {
     if ((int)blockIdx.x == S.x) {
@@ -259,10 +276,12 @@ __global__ void k_lsq(int m, int K, const double* __restrict__ H, const double* 
   S.beta = beta;
 }
 
-// x += sum_{i<k} y_i V_i ; V_0 <- sum_{i<=k} z_i V_i (per system)
+// x += M^-1 sum_{i<k} y_i V_i ; V_0 <- sum_{i<=k} z_i V_i (per system); when
+// preconditioned (tz != nullptr) also tz = M^-1 V_0, the next cycle's first input
 __global__ void k_update(int m, int64_t len, double* __restrict__ V, double* __restrict__ x,
                          const double* __restrict__ y, const double* __restrict__ z, const DevState* st,
-                         const int4* __restrict__ blk) {
+                         const int4* __restrict__ blk, double* __restrict__ tz, const int4* __restrict__ lay,
+                         double2 pre) {
   const int4 B = blk[blockIdx.x];
   const DevState& S = st[B.x];
   const int k = S.k;
@@ -276,7 +295,13 @@ __global__ void k_update(int m, int64_t len, double* __restrict__ V, double* __r
       if (i < k) dx += y_[i] * v;
       v0 += z_[i] * v;
     }
-    x[e] += dx;
+    if (tz != nullptr) {
+      const double f = precond_factor(e, lay[B.x], pre);
+      x[e] += f * dx;
+      tz[e] = f * v0;
+    } else {
+      x[e] += dx;
+    }
     V[e] = v0;
   }
 }
@@ -327,8 +352,9 @@ struct Recorded {
 struct GmresWork {
   uint64_t lay_key = 0;
   int m = 0, K = 0, nblk = 0;
+  int precond = 0;  // bipb_precond of the current call
   int64_t len = 0;
-  DevBuf<double> V, w, H, cs, sn, g, y, z, part, part2, part1, r, d, t;
+  DevBuf<double> V, w, H, cs, sn, g, y, z, part, part2, part1, r, d, t, tz;
   DevBuf<int4> blk, sysb;
   DevBuf<int> mask;  // per system: 1 = leave out of the FP64 residual
   std::vector<int4> sysb_host;
@@ -386,6 +412,7 @@ GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
   w->w.ensure(len, s->stream);
   w->r.ensure(len, s->stream);
   w->d.ensure(len, s->stream);
+  w->tz.ensure(len, s->stream);
   w->t.ensure(len, s->stream);
   w->H.ensure((size_t)L.K * (m + 1) * m, s->stream);
   w->cs.ensure((size_t)L.K * m, s->stream);
@@ -412,14 +439,23 @@ GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
 }
 
 // One restart cycle: kernels only (no host synchronisation, no allocation).
+// M^-1 of the self-block preconditioner: 1 / (1/2 (1 + eps)), 1 / (1/2 (1 + 1/eps))
+double2 precond_factors(const bipb_medium& m) {
+  const double eps = m.eps_out / m.eps_in;
+  return make_double2(2.0 / (1.0 + eps), 2.0 / (1.0 + 1.0 / eps));
+}
+
 void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& med, int precision,
                  bool transpose) {
+  const int4* lay = w->precond ? s->lay_dev(L) : nullptr;
+  double* tz = w->precond ? w->tz.p : nullptr;
+  const double2 pre = precond_factors(med);
   const int m = w->m, m1 = m + 1, K = w->K, nb = w->nblk;
   const int64_t len = w->len;
   const int kg = (K + 127) / 128;
   for (int j = 0; j < m; ++j) {
     double* vj = w->V.p + (size_t)j * len;
-    matvec(s, L, med, precision, transpose, vj, w->w.p, &w->st->skip, kStateInts);
+    matvec(s, L, med, precision, transpose, tz ? tz : vj, w->w.p, &w->st->skip, kStateInts);
     // CGS2: the first pass also takes the dot products of the second, the
     // second also forms the block norms
     k_dots<<<nb, kBS, 0, s->stream>>>(j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
@@ -431,12 +467,12 @@ void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium
                                       w->part1.p, 1, nullptr);
     BIPB_LAUNCHED(s);
     k_normalize<<<nb, kBS, 0, s->stream>>>(j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
-                                           0, w->cs.p, w->sn.p, w->g.p);
+                                           0, w->cs.p, w->sn.p, w->g.p, tz, lay, pre);
     BIPB_LAUNCHED(s);
   }
   k_lsq<<<kg, 128, 0, s->stream>>>(m, K, w->H.p, w->cs.p, w->sn.p, w->g.p, w->y.p, w->z.p, w->st);
   BIPB_LAUNCHED(s);
-  k_update<<<nb, kBS, 0, s->stream>>>(m, len, w->V.p, w->d.p, w->y.p, w->z.p, w->st, w->blk.p);
+  k_update<<<nb, kBS, 0, s->stream>>>(m, len, w->V.p, w->d.p, w->y.p, w->z.p, w->st, w->blk.p, tz, lay, pre);
   BIPB_LAUNCHED(s);
   k_next_cycle<<<kg, 128, 0, s->stream>>>(m, K, w->g.p, w->st);
   BIPB_LAUNCHED(s);
@@ -446,7 +482,7 @@ void run_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& 
                bool transpose) {
   // A recorded cycle bakes in the medium and every buffer address, so it is
   // tagged with both and re-recorded when either changes.
-  const int key = precision * 2 + (transpose ? 1 : 0);
+  const int key = (precision * 2 + (transpose ? 1 : 0)) * 2 + (w->precond ? 1 : 0);
   const GraphTag tag{s->alloc_gen, med.eps_in, med.eps_out, med.kappa, s->timer.on};
   auto it = w->graphs.find(key);
   if (it != w->graphs.end() && it->second.tag == tag) {
@@ -546,7 +582,8 @@ std::vector<int> gmres_core(Surface* s, const SysLayout& L, GmresWork* w, const 
   k_sumsq<<<w->nblk, kBS, 0, s->stream>>>(r0, w->part1.p, w->st, w->blk.p, 1);
   BIPB_LAUNCHED(s);
   k_normalize<<<w->nblk, kBS, 0, s->stream>>>(-1, w->m, r0, w->V.p, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
-                                              1, w->cs.p, w->sn.p, w->g.p);
+                                              1, w->cs.p, w->sn.p, w->g.p, w->precond ? w->tz.p : nullptr,
+                                              w->precond ? s->lay_dev(L) : nullptr, precond_factors(med));
   BIPB_LAUNCHED(s);
   k_next_cycle<<<kg, 128, 0, s->stream>>>(w->m, K, w->g.p, w->st);
   BIPB_LAUNCHED(s);
@@ -579,6 +616,7 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   const int m = p.restart > 0 ? p.restart : 10;
   const int max_iter = p.max_iter > 0 ? p.max_iter : 1000;
   GmresWork* w = workspace(s, L, m);
+  w->precond = p.precond;
   const int64_t len = L.len;
   const int nb = grid_for(len);
   const std::vector<double> bnorm = norms(s, w, rhs);

@@ -105,6 +105,6 @@ def test_null_and_stale_handles_are_rejected(bipb):
 
 
 def test_solve_params_layout_matches_header(bipb):
-    # medium (3 doubles) + tol + 4 ints + inner_tol + pointer
-    assert ctypes.sizeof(bipb.bipb_solve_params) == 3 * 8 + 8 + 4 * 4 + 8 + 8
+    # medium (3 doubles) + tol + 4 ints + inner_tol + pointer + precond + reserved
+    assert ctypes.sizeof(bipb.bipb_solve_params) == 3 * 8 + 8 + 4 * 4 + 8 + 8 + 4 + 4
     assert ctypes.sizeof(bipb.bipb_solve_info) == 6 * 4 + 2 * 8
