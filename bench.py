@@ -8,7 +8,10 @@ refinement residual b - A x in double-float arithmetic -- two FP32 words,
 ~48 bits, verified against FP64 to 2e-12 -- FP64 Krylov recurrences and
 sums), solvation energy (read back to the host).  The same solve with a
 native-FP64 refinement residual and the plain FP64 GMRES solve are timed
-beside it (solve_ms_mixed_fp64_residual, solve_ms_fp64).
+beside it (solve_ms_mixed_fp64_residual, solve_ms_fp64), and so are the
+mixed and FP64 solves with the element self-block preconditioner of Sec.
+2.2.4 (solve_ms_mixed_precond_self, solve_ms_fp64_precond_self), which the
+paper's GPU pipeline leaves out and the step therefore leaves out too.
 
 Default workload: the Kirkwood sphere (icosphere level 5, N = 20480
 triangles, 2N = 40960 unknowns, radius 20 A, 50 charges, eps 1/80,
@@ -283,8 +286,10 @@ def run_configs(args):
             s.set_charges(p.charge_pos, p.q)
             v, mv = s.autotune(med, reps=2)
             res = {"config": "protein-like N=81920, 2000 charges", "matvec32_variant": v, "matvec32_ms": mv}
-            for name, prec in (("mixed_df64", bipb.MIXED_DF64), ("mixed_fp64_residual", bipb.MIXED)):
-                prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=prec)
+            for name, prec, pc in (("mixed_df64", bipb.MIXED_DF64, bipb.PRECOND_NONE),
+                                   ("mixed_fp64_residual", bipb.MIXED, bipb.PRECOND_NONE),
+                                   ("mixed_df64_precond_self", bipb.MIXED_DF64, bipb.PRECOND_SELF)):
+                prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=prec, precond=pc)
                 s.solve(prm)
                 ms, info = _timed(lambda: s.solve(prm), torch)
                 res[f"solve_ms_{name}"] = ms
@@ -339,6 +344,12 @@ def run_configs(args):
             res["refine_steps_hist"] = {str(k): sum(1 for i in info if i["refine_steps"] == k)
                                         for k in sorted({i["refine_steps"] for i in info})}
             res["rel_residual_max"] = max(i["rel_residual"] for i in info)
+            # the same with the element self-block preconditioner (Sec. 2.2.4)
+            prm.precond = bipb.PRECOND_SELF
+            ms, info = _timed(lambda: s.solve(prm), torch)
+            res["solve_ms_mixed_tf32_64rhs_precond_self"] = ms
+            res["iters_max_precond_self"] = max(i["iters"] for i in info)
+            res["rel_residual_max_precond_self"] = max(i["rel_residual"] for i in info)
             emit(res)
     if "4b" in which:
         probs = synth.uneven_batch_problems()
@@ -369,9 +380,17 @@ def run_configs(args):
             prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.MIXED_DF64)
             ms_f, info = _timed(lambda: s.solve(prm), torch)
             ms_g, (dq, dy) = _timed(lambda: s.energy_grad(prm), torch)
-            emit({"config": "adjoint: displaced icosphere level 7 (N=327680), R=45, 10000 charges",
-                  "solve_ms_mixed_df64": ms_f, "energy_grad_ms": ms_g, "info": info[0],
-                  "energy_kcal": float(s.energy()[0]), "max_abs_force": float(np.abs(dy).max())})
+            res = {"config": "adjoint: displaced icosphere level 7 (N=327680), R=45, 10000 charges",
+                   "solve_ms_mixed_df64": ms_f, "energy_grad_ms": ms_g, "info": info[0],
+                   "energy_kcal": float(s.energy()[0]), "max_abs_force": float(np.abs(dy).max())}
+            # the same with the element self-block preconditioner (Sec. 2.2.4)
+            prm.precond = bipb.PRECOND_SELF
+            ms_fp, info_p = _timed(lambda: s.solve(prm), torch)
+            ms_gp, (dqp, dyp) = _timed(lambda: s.energy_grad(prm), torch)
+            res.update({"solve_ms_mixed_df64_precond_self": ms_fp, "energy_grad_ms_precond_self": ms_gp,
+                        "info_precond_self": info_p[0],
+                        "max_rel_force_difference_precond": float(np.abs(dyp - dy).max() / np.abs(dy).max())})
+            emit(res)
     if "5fd" in which:
         emit(config5_central_differences(bipb, torch))
     return out
@@ -582,6 +601,28 @@ def main():
         torch.cuda.synchronize()
         extra["solve_ms_mixed_fp64_residual"] = a.elapsed_time(b)
         extra["mixed_fp64_residual_info"] = im
+        # plain FP64 GMRES with the element self-block preconditioner (Sec. 2.2.4)
+        p64.precond = bipb.PRECOND_SELF
+        s.solve(p64)
+        a.record()
+        ip = s.solve(p64)[0]
+        b.record()
+        torch.cuda.synchronize()
+        extra["solve_ms_fp64_precond_self"] = a.elapsed_time(b)
+        extra["fp64_precond_self_info"] = ip
+    # the step's mixed solve with the element self-block preconditioner (Sec.
+    # 2.2.4, applied on the right): same true-residual target, fewer FP32 mat-vecs
+    pp = bipb.solve_params(prob.eps_in, prob.eps_out, prob.kappa, tol=TOL, restart=10,
+                           precision=bipb.MIXED_DF64, precond=bipb.PRECOND_SELF)
+    s.solve(pp)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        ipp = s.solve(pp)[0]
+    b.record()
+    torch.cuda.synchronize()
+    extra["solve_ms_mixed_precond_self"] = a.elapsed_time(b) / 5
+    extra["mixed_precond_self_info"] = ipp
     extra["solve_ms_mixed"] = total_ms / args.steps
     extra["mixed_info"] = info0
     extra["energy_kcal"] = infos[-1][1]
