@@ -18,7 +18,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import MIXED, Surface, solve_params
+from . import MIXED, PRECOND_NONE, Surface, solve_params
 
 
 class BipbEnergy(torch.autograd.Function):
@@ -71,10 +71,11 @@ class SolvationEnergy(torch.nn.Module):
     """
 
     def __init__(self, centroids, normals, areas, eps_in=1.0, eps_out=80.0, kappa=0.1257, tol=1e-8,
-                 precision=MIXED, restart=10):
+                 precision=MIXED, restart=10, precond=PRECOND_NONE):
         super().__init__()
         self.surface = Surface(np.asarray(centroids), np.asarray(normals), np.asarray(areas))
-        self.params = solve_params(eps_in, eps_out, kappa, tol=tol, restart=restart, precision=precision)
+        self.params = solve_params(eps_in, eps_out, kappa, tol=tol, restart=restart, precision=precision,
+                                   precond=precond)
 
     def forward(self, q, pos):
         return BipbEnergy.apply(q, pos, self.surface, self.params)

@@ -681,3 +681,29 @@ def test_self_block_preconditioned_batch_and_adjoint(bipb, orc):
     np.testing.assert_allclose(e1, e0, rtol=1e-8)
     np.testing.assert_allclose(dq1, dq0, rtol=0, atol=1e-7 * np.abs(dq0).max())
     np.testing.assert_allclose(dy1, dy0, rtol=0, atol=1e-7 * np.abs(dy0).max())
+
+
+def test_new_entry_points_reject_bad_arguments(bipb):
+    p = synth.born_problem(level=2)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=1e-8, precision=bipb.FP64)
+        prm.precond = 7
+        with pytest.raises(bipb.BipbError):
+            s.solve(prm)
+        prm.precond, prm.reserved = bipb.PRECOND_SELF, 1
+        with pytest.raises(bipb.BipbError):
+            s.solve(prm)
+        prm.reserved = 0
+        assert s.solve(prm)[0]["converged"]
+        L = bipb.load_library()
+        pts = np.array([[0.1, 0.2, 0.3]])
+        out = np.zeros(1)
+        st = L.bipb_potential_at(s.handle, 5, 1, pts.ctypes.data, out.ctypes.data)
+        assert st == bipb.BIPB_ERR_INVALID_ARG
+        with pytest.raises(bipb.BipbError):
+            s.potential_at(np.array([[np.nan, 0.0, 0.0]]))
+        # the inside potential at the centre's neighbourhood is finite and the outside one decays
+        v_in = s.potential_at(np.array([[0.3, 0.0, 0.0]]), inside=True)
+        v_out = s.potential_at(np.array([[10.0, 0.0, 0.0], [20.0, 0.0, 0.0]]), inside=False)
+        assert np.isfinite(v_in).all() and v_out[0, 0] > v_out[0, 1] > 0
