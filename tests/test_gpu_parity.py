@@ -6,8 +6,13 @@ Tolerances (each derived from the arithmetic of the path it checks):
 * FP32 mat-vec: 3e-6 in the 2-norm and 2e-5 of the largest output per
   element (FP32 pair arithmetic with 2^-22 MUFU approximations, FP32 sums
   over one source split, FP64 across splits).
+* Double-float mat-vec: 2e-12 of the largest output (pairs in ~48-bit
+  arithmetic; measured 4e-14).
+* Split-TF32 tensor-core mat-vec: the FP32 bounds.
 * Solves: energies and potentials within 1e-10 (FP64, both sides solved to
-  1e-12) and within 1e-7 (mixed, refined to 1e-8 ... 1e-10).
+  1e-12) and within 1e-7 (mixed, refined to 1e-8 ... 1e-10); potentials at
+  points off the surface within 1e-9 of the largest value (the difference
+  of two solves to 1e-12, carried through a kernel sum).
 """
 import numpy as np
 import pytest
