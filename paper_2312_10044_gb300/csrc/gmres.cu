@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstddef>
 #include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -364,15 +365,74 @@ struct GmresWork {
   std::vector<DevState> st_host;
   std::vector<double> part1_host;
   std::vector<int> mask_host;
-  std::map<int, Recorded> graphs;  // recorded cycles keyed by (precision, transpose)
+  std::map<int, Recorded> graphs;  // recorded cycles keyed by (precision, transpose, precond)
   const std::vector<EventPair>* replayed = nullptr;
-  ~GmresWork() {
-    for (auto& kv : graphs) {
+  int device = 0;
+  ~GmresWork();
+};
+
+namespace {
+
+// Executable restart-cycle graphs of destroyed handles, kept for reuse: a new
+// handle records its own cycle and, when a kept executable of the same kind
+// accepts that graph (cudaGraphExecUpdate checks that the topology matches),
+// updates it in place instead of instantiating a new one.  At most kPoolMax
+// are kept; they are released with the process (the pool is never destroyed,
+// so no CUDA call runs during static destruction).
+struct PooledExec {
+  int device, key;
+  cudaGraphExec_t exec;
+};
+constexpr size_t kPoolMax = 16;
+std::mutex& pool_mutex() {
+  static auto* m = new std::mutex;
+  return *m;
+}
+std::vector<PooledExec>& exec_pool() {
+  static auto* v = new std::vector<PooledExec>;
+  return *v;
+}
+
+void pool_put(int device, int key, cudaGraphExec_t exec) {
+  std::lock_guard<std::mutex> lock(pool_mutex());
+  if (exec_pool().size() < kPoolMax) {
+    exec_pool().push_back(PooledExec{device, key, exec});
+  } else {
+    cudaGraphExecDestroy(exec);
+  }
+}
+
+// An executable updated to run graph g, or nullptr.
+cudaGraphExec_t pool_take(int device, int key, cudaGraph_t g) {
+  std::lock_guard<std::mutex> lock(pool_mutex());
+  auto& v = exec_pool();
+  int tries = 0;
+  for (size_t i = 0; i < v.size() && tries < 4; ++i) {
+    if (v[i].device != device || v[i].key != key) continue;
+    ++tries;
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(v[i].exec, g, &info) == cudaSuccess) {
+      cudaGraphExec_t e = v[i].exec;
+      v.erase(v.begin() + (std::ptrdiff_t)i);
+      return e;
+    }
+    (void)cudaGetLastError();  // a topology mismatch is not an error here
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+GmresWork::~GmresWork() {
+  for (auto& kv : graphs) {
+    if (kv.second.events.empty()) {
+      pool_put(device, kv.first, kv.second.exec);  // untimed cycles only: no event nodes to carry over
+    } else {
       cudaGraphExecDestroy(kv.second.exec);
       for (auto& e : kv.second.events) cudaEventDestroy(e.a), cudaEventDestroy(e.b);
     }
   }
-};
+}
 
 void gmres_free(Surface* s) {
   delete s->gw;
@@ -386,6 +446,7 @@ GmresWork* workspace(Surface* s, const SysLayout& L, int m) {
   if (w && w->lay_key == L.key && w->m == m && w->K == L.K) return w;
   if (w) gmres_free(s);
   w = new GmresWork();
+  w->device = s->device;
   s->gw = w;
   w->lay_key = L.key;
   w->m = m;
@@ -519,8 +580,8 @@ void run_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium& 
     for (auto& e : evs) s->timer.pool.push_back(e.a), s->timer.pool.push_back(e.b);
     return;
   }
-  cudaGraphExec_t exec;
-  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphExec_t exec = evs.empty() ? pool_take(s->device, key, graph) : nullptr;
+  cudaError_t e = exec ? cudaSuccess : cudaGraphInstantiate(&exec, graph, 0);
   cudaGraphDestroy(graph);
   BIPB_CUDA(e);
   if (it != w->graphs.end()) {
