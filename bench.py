@@ -346,8 +346,13 @@ def run_configs(args):
             res["rel_residual_max"] = max(i["rel_residual"] for i in info)
             # the same with the element self-block preconditioner (Sec. 2.2.4)
             prm.precond = bipb.PRECOND_SELF
+            bipb.timer_enable(s, True)
             ms, info = _timed(lambda: s.solve(prm), torch)
+            t = bipb.timer_read(s)
+            bipb.timer_enable(s, False)
             res["solve_ms_mixed_tf32_64rhs_precond_self"] = ms
+            res["kernel_ms_precond_self"] = {k: v[1] for k, v in t.items() if v[0]}
+            res["kernel_launches_precond_self"] = {k: v[0] for k, v in t.items() if v[0]}
             res["iters_max_precond_self"] = max(i["iters"] for i in info)
             res["rel_residual_max_precond_self"] = max(i["rel_residual"] for i in info)
             emit(res)
