@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
+    ap.add_argument("--precond", default="none", choices=["none", "self"],
+                    help="preconditioner of the step's solve (none: the paper's GPU pipeline; self: element "
+                         "self blocks of Sec. 2.2.4)")
     ap.add_argument("--clocks-csv", default="", help="also keep the raw nvidia-smi clock samples in this file")
     ap.add_argument("--variant", type=int, default=-1,
                     help="FP32 mat-vec variant (default: autotuned; --mode matvec32: the handle's default)")
@@ -496,7 +499,8 @@ def main():
     prob, desc = workload(args.workload)
     n, nc = prob.n, prob.nc
     params = bipb.solve_params(prob.eps_in, prob.eps_out, prob.kappa, tol=TOL, restart=10,
-                               precision=bipb.MIXED_DF64)
+                               precision=bipb.MIXED_DF64,
+                               precond=bipb.PRECOND_SELF if args.precond == "self" else bipb.PRECOND_NONE)
     s = bipb.Surface(prob.centroids, prob.normals, prob.areas)
     s.set_charges(prob.charge_pos, prob.q)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -667,7 +671,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 (Krylov mat-vecs) + df64 (residual) + f64",
                 "data": "synthetic",
                 "config": {"workload": desc, "n": n, "nc": nc, "tol": TOL, "restart": 10, "l2": "flushed",
-                           "parallelism": f"replicas{world}", "matvec32_variant": variant},
+                           "parallelism": f"replicas{world}", "matvec32_variant": variant,
+                           "precond": args.precond},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         line.update(extra)
