@@ -62,14 +62,6 @@ bipb_status guarded(F&& f) {
 
 bool finite3(const double* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
 
-std::array<uint64_t, 3> key_of(const double* p) {
-  std::array<uint64_t, 3> k;
-  for (int i = 0; i < 3; ++i) {
-    double v = p[i] == 0.0 ? 0.0 : p[i];  // -0 == +0
-    std::memcpy(&k[i], &v, 8);
-  }
-  return k;
-}
 
 void validate_medium(const bipb_medium* m) {
   BIPB_REQUIRE(m != nullptr, "medium is NULL");
@@ -192,35 +184,44 @@ void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::v
     for (int k = 0; k < 3; ++k) c[k] += P.c[3 * i + k];
   }
   for (int k = 0; k < 3; ++k) c[k] /= (double)P.n;
-  // duplicates of the centred centroids, in FP64 and after rounding to FP32
-  // (the FP64 set is kept to reject charges on a centroid)
-  KeySet k64, k32;
-  k64.reserve((size_t)P.n);
-  k32.reserve((size_t)P.n);
+  // centred copies, and the check for duplicates (in FP32, then FP64 on a hit);
+  // the set is kept to reject charges on a centroid
+  CentroidSet cs;
+  cs.d.resize(3 * (size_t)P.n);
+  cs.f.resize(3 * (size_t)P.n);
+  cs.reserve((size_t)P.n);
   for (int64_t i = 0; i < P.n; ++i) {
-    double d[3], f[3];
     for (int k = 0; k < 3; ++k) {
-      d[k] = P.c[3 * i + k] - c[k];
-      f[k] = (double)(float)d[k];
+      const double d = P.c[3 * i + k] - c[k];
+      cs.d[3 * i + k] = d;
+      cs.f[3 * i + k] = (float)d;
     }
-    BIPB_REQUIRE(k64.insert(key_of(d)), "two centroids coincide");
-    BIPB_REQUIRE(k32.insert(key_of(f)), "two centroids coincide after rounding to FP32");
+    const int32_t j = cs.insert((int32_t)i);
+    if (j >= 0) {
+      const bool same64 = cs.d[3 * j] == cs.d[3 * i] && cs.d[3 * j + 1] == cs.d[3 * i + 1] &&
+                          cs.d[3 * j + 2] == cs.d[3 * i + 2];
+      throw Error(BIPB_ERR_INVALID_ARG,
+                  same64 ? "two centroids coincide" : "two centroids coincide after rounding to FP32");
+    }
   }
-  s->part_keys.push_back(std::move(k64));
   s->part_off.push_back((int)s->n);
   s->part_n.push_back((int)P.n);
   for (int k = 0; k < 3; ++k) s->part_center.push_back(c[k]);
+  const size_t base = tgt.size();
+  tgt.resize(base + 2 * (size_t)P.n);
+  tgt32.resize(base + 2 * (size_t)P.n);
   for (int64_t i = 0; i < P.n; ++i) {
-    const double* p = P.c + 3 * i;
     const double* v = P.nrm + 3 * i;
-    double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    double4_32a g = make_double4_32a(p[0] - c[0], p[1] - c[1], p[2] - c[2], P.area[i]);
-    double4_32a nv = make_double4_32a(v[0] / len, v[1] / len, v[2] / len, 0.0);
-    tgt.push_back(g);
-    tgt.push_back(nv);
-    tgt32.push_back(make_float4((float)g.x, (float)g.y, (float)g.z, (float)g.w));
-    tgt32.push_back(make_float4((float)nv.x, (float)nv.y, (float)nv.z, 0.f));
+    const double inv = 1.0 / std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double* d = &cs.d[3 * i];
+    const float* f = &cs.f[3 * i];
+    const double nx = v[0] * inv, ny = v[1] * inv, nz = v[2] * inv;
+    tgt[base + 2 * i] = make_double4_32a(d[0], d[1], d[2], P.area[i]);
+    tgt[base + 2 * i + 1] = make_double4_32a(nx, ny, nz, 0.0);
+    tgt32[base + 2 * i] = make_float4(f[0], f[1], f[2], (float)P.area[i]);
+    tgt32[base + 2 * i + 1] = make_float4((float)nx, (float)ny, (float)nz, 0.f);
   }
+  s->part_keys.push_back(std::move(cs));
   s->n += P.n;
 }
 
@@ -269,7 +270,7 @@ bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream,
 }
 
 // Charge records of one system, centred like its surface; rejects charges on
-// a centroid (lookup in the surface's set of centred centroid keys).
+// a centroid (lookup in the surface's set of centred centroids).
 void append_charges(Surface* s, int part, int64_t nc, const double* pos, const double* q,
                     std::vector<double4_32a>& rec) {
   const double* c = &s->part_center[3 * part];
@@ -278,7 +279,10 @@ void append_charges(Surface* s, int part, int64_t nc, const double* pos, const d
     BIPB_REQUIRE(finite3(pos + 3 * k), "non-finite charge position");
     BIPB_REQUIRE(std::isfinite(q[k]), "non-finite charge");
     double p[3] = {pos[3 * k] - c[0], pos[3 * k + 1] - c[1], pos[3 * k + 2] - c[2]};
-    BIPB_REQUIRE(!keys.contains(key_of(p)), "a charge sits on a centroid");
+    const float pf[3] = {(float)p[0], (float)p[1], (float)p[2]};
+    const int32_t j = keys.find(pf);  // the only centroid that can equal p in FP64
+    BIPB_REQUIRE(j < 0 || !(keys.d[3 * j] == p[0] && keys.d[3 * j + 1] == p[1] && keys.d[3 * j + 2] == p[2]),
+                 "a charge sits on a centroid");
     rec.push_back(make_double4_32a(p[0], p[1], p[2], q[k]));
   }
 }

@@ -8,6 +8,7 @@
 #include <stdexcept>
 #include <string>
 #include <array>
+#include <cstring>
 #include <vector>
 
 #include "bipb.h"
@@ -77,46 +78,61 @@ struct DevBuf {
   ~DevBuf() { release(); }
 };
 
-// Set of 3-component bit patterns (centroid coordinates) with open addressing:
-// one flat table of indices, linear probing, no per-key allocation.
-struct KeySet {
-  std::vector<std::array<uint64_t, 3>> keys;
-  std::vector<int32_t> slot;  // index into keys, or -1
+// The centred centroids of one surface, in FP64 and rounded to FP32, with a
+// hash set (open addressing, one flat table of element indices) keyed by the
+// bit patterns of the FP32 triple.  FP32 duplicates are found on insertion;
+// an FP64 comparison is made only on a key hit.
+struct CentroidSet {
+  std::vector<double> d;      // 3 per element, FP64
+  std::vector<float> f;       // 3 per element, the same rounded to FP32
+  std::vector<int32_t> slot;  // element index, or -1
   uint64_t mask = 0;
   static uint64_t mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
     return z ^ (z >> 31);
   }
-  static uint64_t hash(const std::array<uint64_t, 3>& k) { return mix(k[0] ^ mix(k[1] ^ mix(k[2]))); }
+  static uint32_t bits(float v) {  // -0 and +0 alike
+    uint32_t u;
+    const float w = v == 0.0f ? 0.0f : v;
+    std::memcpy(&u, &w, 4);
+    return u;
+  }
+  static uint64_t hash(const float* p) {
+    return mix(((uint64_t)bits(p[0]) << 32 | bits(p[1])) ^ mix(bits(p[2])));
+  }
+  static bool same(const float* a, const float* b) {
+    return bits(a[0]) == bits(b[0]) && bits(a[1]) == bits(b[1]) && bits(a[2]) == bits(b[2]);
+  }
   void reserve(size_t n) {
     size_t sz = 16;
     while (sz < 2 * n) sz <<= 1;
     slot.assign(sz, -1);
     mask = sz - 1;
-    keys.reserve(n);
   }
-  // false if k is already present
-  bool insert(const std::array<uint64_t, 3>& k) {
-    for (uint64_t h = hash(k) & mask;; h = (h + 1) & mask) {
-      const int32_t i = slot[h];
-      if (i < 0) {
-        slot[h] = (int32_t)keys.size();
-        keys.push_back(k);
-        return true;
+  // element i (whose f is set) into the table; -1, or the element with the same FP32 point
+  int32_t insert(int32_t i) {
+    const float* p = &f[3 * (size_t)i];
+    for (uint64_t h = hash(p) & mask;; h = (h + 1) & mask) {
+      const int32_t j = slot[h];
+      if (j < 0) {
+        slot[h] = i;
+        return -1;
       }
-      if (keys[i] == k) return false;
+      if (same(&f[3 * (size_t)j], p)) return j;
     }
   }
-  bool contains(const std::array<uint64_t, 3>& k) const {
-    if (slot.empty()) return false;
-    for (uint64_t h = hash(k) & mask;; h = (h + 1) & mask) {
-      const int32_t i = slot[h];
-      if (i < 0) return false;
-      if (keys[i] == k) return true;
+  // the element at FP32 point p, or -1
+  int32_t find(const float* p) const {
+    if (slot.empty()) return -1;
+    for (uint64_t h = hash(p) & mask;; h = (h + 1) & mask) {
+      const int32_t j = slot[h];
+      if (j < 0) return -1;
+      if (same(&f[3 * (size_t)j], p)) return j;
     }
   }
 };
+
 
 // K independent systems handled by one batched pass (several right-hand
 // sides of one surface, or several surfaces).  System k has n[k] elements
@@ -249,7 +265,7 @@ struct Surface {
   // batch handle, one system each): element offsets, sizes, centres
   std::vector<int> part_off, part_n;
   std::vector<double> part_center;  // 3 per surface
-  std::vector<KeySet> part_keys;  // bit patterns of the centred centroids, per surface
+  std::vector<CentroidSet> part_keys;  // the centred centroids of every surface
   bool batch = false;
 
   // cached work lists and device copies of layouts (keyed by content)

@@ -712,3 +712,15 @@ def test_new_entry_points_reject_bad_arguments(bipb):
         v_in = s.potential_at(np.array([[0.3, 0.0, 0.0]]), inside=True)
         v_out = s.potential_at(np.array([[10.0, 0.0, 0.0], [20.0, 0.0, 0.0]]), inside=False)
         assert np.isfinite(v_in).all() and v_out[0, 0] > v_out[0, 1] > 0
+
+
+def test_charge_on_a_centroid_is_rejected(bipb):
+    """A charge exactly on a centroid (FP64) is rejected; one that only rounds
+    to the same FP32 point is accepted."""
+    p = synth.born_problem(level=2)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        on = p.centroids[17].copy()
+        with pytest.raises(bipb.BipbError, match="centroid"):
+            s.set_charges(np.array([[0.0, 0.0, 0.0], on]), np.array([[1.0, -1.0]]))
+        near = on + np.array([1e-12, 0.0, 0.0])
+        s.set_charges(np.array([[0.0, 0.0, 0.0], near]), np.array([[1.0, -1.0]]))
