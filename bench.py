@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--configs", default="3,4a,4b,5",
                     help="--mode configs: which larger configurations (5fd: the full-size central-difference check)")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "configs"],
+                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "configs", "peaks"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
@@ -474,12 +474,43 @@ def config5_central_differences(bipb, torch):
     return res
 
 
+def run_peaks(args):
+    """Measured throughput of the FP32 FFMA, FP64 DFMA and MUFU pipes (the
+    microbenchmark microbench/alu_peaks.cu, built here with nvcc), against the
+    nominal unit counts at the SM clock sampled meanwhile."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    src = os.path.join(here, "paper_2312_10044_gb300", "microbench", "alu_peaks.cu")
+    exe = os.path.join(here, "_build", "alu_peaks")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src])
+    clocks = ClockSampler(0, args.clocks_csv or None)
+    clocks.start()
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    clk = clocks.stop()
+    vals = dict(line.split(None, 1) for line in out.splitlines() if line.strip())
+    if vals.get("status", "").strip() != "ok":
+        raise RuntimeError(out)
+    sms = int(vals["sms"])
+    f = (clk["sm_mhz"] if clk else 2070.0) * 1e6
+    res = {"mode": "peaks", "sms": sms, "clocks": clk}
+    for name, lanes in (("ffma", FP32_LANES_PER_SM), ("dfma", FP64_LANES_PER_SM), ("mufu", 16)):
+        v = float(vals[f"{name}_per_s"])
+        nominal = sms * lanes * f
+        res[f"{name}_per_s"] = v
+        res[f"{name}_nominal_per_s"] = nominal
+        res[f"{name}_frac_of_nominal"] = v / nominal
+    print(json.dumps(res), flush=True)
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "configs":
         return run_configs(args)
+    if args.mode == "peaks":
+        return run_peaks(args)
     if args.mode != "solve":
         return run_matvec_only(args)
     import torch
