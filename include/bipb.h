@@ -212,6 +212,7 @@ bipb_status bipb_potential_at(bipb_surface s, int region, int64_t n_pts, const d
  *            infinite self terms k = l of S1(y_k) are left out);
  *   e_free = E_sol + e_coul.
  * Requires a successful bipb_solve.  FP64, O(Nc^2) pairs, fixed order.
+ * BIPB_ERR_INVALID_ARG if two charges of a configuration coincide.
  */
 bipb_status bipb_energy_free(bipb_surface s, double* e_free, double* e_coul);
 

@@ -601,6 +601,7 @@ bipb_status bipb_energy_free(bipb_surface h, double* e_free, double* e_coul) {
       for (int b = 0; b < blocks; ++b) acc += part[(size_t)k * blocks + b];
       // 1/2 (1/eps_in) sum_{c != l} q_c q_l / (4 pi r) in internal units, times 4 pi 332.0716
       const double ec = 0.5 * 332.0716 / s->solved_medium.eps_in * acc;
+      BIPB_REQUIRE(std::isfinite(ec), "two charges coincide: their Coulomb energy is infinite");
       if (e_coul) e_coul[k] = ec;
       if (e_free) e_free[k] = es[k] + ec;
     }
