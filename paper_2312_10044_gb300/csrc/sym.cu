@@ -61,7 +61,7 @@ struct SymPolicy {
   using V4 = typename SymV4<T>::type;
   using PT = T;  // partial sums are stored in this type
   static constexpr int RW = 2;  // (x, a), (n, alpha)
-  static constexpr int UNROLL = sizeof(T) == 4 ? 2 : 1;  // sources in flight per thread
+  static constexpr int UNROLL = sizeof(T) == 4 ? 4 : 1;  // sources in flight per thread
   struct Elem {
     T x[3], a, n[3], al;
   };
