@@ -225,6 +225,22 @@ void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::v
   s->n += P.n;
 }
 
+// 2^(j/1024) for j < 1024 as df64 (hi, lo) pairs, two per float4: the table
+// of the df64 exp (df64.cuh)
+const std::vector<float4>& exp_table() {
+  static const std::vector<float4> t = [] {
+    std::vector<float4> v(kExpTab / 2);
+    auto hi = [](int j) { return (float)std::exp2(j / (double)kExpTab); };
+    auto lo = [](int j) {
+      const double x = std::exp2(j / (double)kExpTab);
+      return (float)(x - (double)(float)x);
+    };
+    for (int i = 0; i < kExpTab / 2; ++i) v[i] = make_float4(hi(2 * i), lo(2 * i), hi(2 * i + 1), lo(2 * i + 1));
+    return v;
+  }();
+  return t;
+}
+
 bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream, bool batch) {
   auto* s = new Surface();
   try {
@@ -248,6 +264,10 @@ bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream,
     keep_pool_memory(dev);
     s->tgt64.ensure(tgt.size(), s->stream);
     s->tgt32.ensure(tgt32.size(), s->stream);
+    const std::vector<float4>& et = exp_table();
+    s->exptab.ensure(et.size(), s->stream);
+    BIPB_CUDA(cudaMemcpyAsync(s->exptab.p, et.data(), et.size() * sizeof(float4), cudaMemcpyHostToDevice,
+                              s->stream));
     BIPB_CUDA(cudaMemcpyAsync(s->tgt64.p, tgt.data(), tgt.size() * sizeof(double4_32a), cudaMemcpyHostToDevice,
                               s->stream));
     BIPB_CUDA(cudaMemcpyAsync(s->tgt32.p, tgt32.data(), tgt32.size() * sizeof(float4), cudaMemcpyHostToDevice,

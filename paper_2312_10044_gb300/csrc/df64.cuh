@@ -14,12 +14,15 @@
 // accuracy near 1e-13; it serves as the high-precision residual of the mixed
 // solve.
 //
-// exp(-kappa r) follows Tang's table-driven method (ACM TOMS 15, 1989):
-// x = k ln2/32 + f with |f| <= ln2/64 (Cody-Waite reduction with ln2/32 split
-// in three parts so that k * L1 is exact), exp(x) = 2^(k>>5) * 2^((k&31)/32)
-// * exp(f), the 32 table values 2^(j/32) held as df64 in shared memory and
-// exp(f) - 1 = f + f^2/2 + f^3/6 + f^4/24 + f^5/120 (truncation f^6/720 <
-// 3e-15 for |f| <= ln2/64).
+// exp(-kappa r) follows Tang's table-driven method (ACM TOMS 15, 1989) with
+// a table of 1024 values: x = k L + f, L = ln2/1024, |f| <= L/2 (Cody-Waite
+// reduction with L split in three parts, the first of 7 significant bits so
+// that k L1 is exact for |k| < 2^17), exp(x) = 2^(k>>10) 2^((k&1023)/1024)
+// exp(f).  The table values 2^(j/1024) are df64 (computed on the host,
+// copied into shared memory by every CTA).  With |f| <= 3.4e-4 the
+// polynomial is short: exp(f) = 1 + f + (f^2/2 + f^3/6), the bracket in
+// FP32 (it is below 5.8e-8, so its FP32 rounding is below 2^-46), and the
+// truncation f^4/24 is below 6e-16.
 // 1/sqrt(r2) is one Newton step in df64 from the MUFU estimate (error
 // squared: about 1e-14).
 #pragma once
@@ -132,11 +135,21 @@ __device__ __forceinline__ df df_sumsq3(df x, df y, df z) {
   return fast_two_sum(t.hi, lo);
 }
 
+constexpr int kExpTab = 1024;  // entries of the exp table, 2^(j/1024) for j < 1024 (k >> 10 below)
+
 struct DFConst {
   df eps, inveps, kappa;  // eps_out/eps_in, its inverse, kappa
-  float l1, l2, l3;       // ln2/32 = l1 + l2 + l3, l1 with 12 significant bits
-  float inv_l;            // 32/ln2
+  float l1, l2, l3;       // ln2/1024 = l1 + l2 + l3, l1 with 7 significant bits
+  float inv_l;            // 1024/ln2
+  const float4* tab;      // device copy of the exp table, two df64 entries per float4
 };
+
+// Every thread of the CTA copies its share of the exp table into sh (16-byte
+// aligned, kExpTab entries); the caller's next barrier makes it visible.
+__device__ __forceinline__ void df_load_exp_table(df* sh, const DFConst& c) {
+  float4* s4 = reinterpret_cast<float4*>(sh);
+  for (int i = threadIdx.x; i < kExpTab / 2; i += blockDim.x) s4[i] = c.tab[i];
+}
 
 // 1/sqrt(r2) for r2 > 0: MUFU estimate, one Newton step in df64.
 __device__ __forceinline__ df df_rsqrt(df r2) {
@@ -148,29 +161,25 @@ __device__ __forceinline__ df df_rsqrt(df r2) {
   return fast_two_sum(s0, __fmul_rn(__fmul_rn(s0, d), 0.5f));
 }
 
-// exp(x) for x <= 0 (clamped at -80), tab[j] = 2^(j/32) as df64.
+// exp(x) for x <= 0 (x.hi clamped at -80), tab[j] = 2^(j/1024) as df64.
 __device__ __forceinline__ df df_exp_neg(df x, const DFConst& c, const df* tab) {
-  if (x.hi < -80.0f) x = df{-80.0f, 0.0f};
-  const float kf = rintf(__fmul_rn(x.hi, c.inv_l));
-  const int k = (int)kf;
-  // f = x - k ln2/32, with k * l1 exact
-  const float f1 = __fmaf_rn(-kf, c.l1, x.hi);  // exact (Sterbenz)
+  const float xh = fmaxf(x.hi, -80.0f);
+  // k = rint(x / L): adding 1.5 * 2^23 leaves the integer in the low mantissa bits
+  const float km = __fmaf_rn(xh, c.inv_l, 12582912.0f);
+  const int k = __float_as_int(km) - 0x4B400000;
+  const float kf = __fsub_rn(km, 12582912.0f);
+  // f = x - k L, with k * l1 exact
+  const float f1 = __fmaf_rn(-kf, c.l1, xh);  // exact: |f1| < 0.32 on the grid of ulp(min(|x|, 64))
   df f = two_sum(f1, x.lo);
   f = df_add(f, df_neg(two_prod(kf, c.l2)));
   f.lo = __fmaf_rn(-kf, c.l3, f.lo);
-  // exp(f) - 1 = f + f^2/2 + f^3 (1/6 + f/24 + f^2/120)
-  const df h2 = df_scale(df_sqr(f), 0.5f);
+  // exp(f) = 1 + f + q, q = f^2/2 + f^3/6 (+ f f.lo, the trailing part's share of f^2/2)
   const float fh = f.hi;
-  const float tail = __fmul_rn(__fmul_rn(__fmul_rn(fh, fh), fh),
-                               __fmaf_rn(fh, __fmaf_rn(fh, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f));
-  df em1 = df_add_ordered(f, h2);  // |f^2 / 2| < |f|
-  em1 = fast_two_sum(em1.hi, __fadd_rn(em1.lo, tail));
-  df ef = fast_two_sum(1.0f, em1.hi);  // |exp(f) - 1| < 1
-  ef = fast_two_sum(ef.hi, __fadd_rn(ef.lo, em1.lo));
-  const df t = tab[k & 31];
-  df r = df_mul(ef, t);
-  const int m = k >> 5;  // floor(k / 32)
-  return df_scale(r, __int_as_float((127 + m) << 23));
+  const float q = __fmaf_rn(fh, f.lo, __fmul_rn(__fmul_rn(fh, fh), __fmaf_rn(fh, 1.0f / 6.0f, 0.5f)));
+  df ef = fast_two_sum(1.0f, fh);  // |f| < 1
+  ef = fast_two_sum(ef.hi, __fadd_rn(ef.lo, __fadd_rn(f.lo, q)));
+  const df r = df_mul(ef, tab[k & (kExpTab - 1)]);
+  return df_scale(r, __int_as_float((127 + (k >> 10)) << 23));  // 2^floor(k / 1024)
 }
 
 // Forward pair (the formula of pair_forward in pair.cuh) in df64.

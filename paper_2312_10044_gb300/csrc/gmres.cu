@@ -169,35 +169,44 @@ __global__ void k_sumsq(const double* __restrict__ w, double* __restrict__ part1
   if (threadIdx.x == 0) part1[blockIdx.x] = acc;
 }
 
-// Per system: apply earlier rotations to column j, make rotation j, update g, test.
-__device__ void givens_step(int j, int m, int sys, double* __restrict__ H, double* __restrict__ cs,
-                            double* __restrict__ sn, double* __restrict__ g, DevState* st) {
+// Per system: apply earlier rotations to column j, make rotation j, update g,
+// test.  The column (j + 2 entries, h[j + 1] = ||w||) and the earlier
+// rotations are in shared memory (ch, csh, snh), staged by the caller's
+// block in parallel, so the serial recurrence waits on no global load.
+__device__ void givens_step(int j, int m, int sys, double* ch, const double* csh, const double* snh,
+                            double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                            double* __restrict__ g, DevState* __restrict__ st) {
   DevState& S = st[sys];
   const int m1 = m + 1;
   double* h = H + (size_t)sys * m1 * m + (size_t)j * m1;
-  double* c_ = cs + (size_t)sys * m;
-  double* s_ = sn + (size_t)sys * m;
   double* g_ = g + (size_t)sys * m1;
+  const double gj = g_[j], bnorm = S.bnorm, tol = S.tol;
+  const int iters = S.iters + 1, max_iter = S.max_iter, Sm = S.m;
   for (int i = 0; i < j; ++i) {
-    double t = c_[i] * h[i] + s_[i] * h[i + 1];
-    h[i + 1] = -s_[i] * h[i] + c_[i] * h[i + 1];
-    h[i] = t;
+    const double t = csh[i] * ch[i] + snh[i] * ch[i + 1];
+    ch[i + 1] = -snh[i] * ch[i] + csh[i] * ch[i + 1];
+    ch[i] = t;
   }
-  double a = h[j], b = h[j + 1];
-  double den = hypot(a, b);
-  double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-  c_[j] = c;
-  s_[j] = s;
+  const double a = ch[j], b = ch[j + 1];
+  const double den = hypot(a, b);
+  const double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
+  for (int i = 0; i < j; ++i) h[i] = ch[i];
   h[j] = den;
   h[j + 1] = 0.0;
-  g_[j + 1] = -s * g_[j];
-  g_[j] = c * g_[j];
+  cs[(size_t)sys * m + j] = c;
+  sn[(size_t)sys * m + j] = s;
+  const double gj1 = -s * gj;
+  g_[j + 1] = gj1;
+  g_[j] = c * gj;
   S.k = j + 1;
-  S.iters += 1;
-  S.est = S.bnorm > 0.0 ? fabs(g_[j + 1]) / S.bnorm : 0.0;
-  if (S.est <= S.tol || b == 0.0) S.conv = 1;
-  if (S.iters >= S.max_iter) S.stop = 1;
-  if (S.conv || S.stop || j + 1 == S.m) S.skip = 1;
+  S.iters = iters;
+  const double est = bnorm > 0.0 ? fabs(gj1) / bnorm : 0.0;
+  S.est = est;
+  const int conv = est <= tol || b == 0.0;
+  const int stop = iters >= max_iter;
+  if (conv) S.conv = 1;
+  if (stop) S.stop = 1;
+  if (conv || stop || j + 1 == Sm) S.skip = 1;
 }
 
 // out = w / ||w|| per system (and tz = M^-1 out when preconditioned); j >= 0:
@@ -227,20 +236,30 @@ __global__ void k_normalize(int j, int m, const double* __restrict__ w, double* 
     const int4 Lk = lay[B.x];
     for (int x = B.y + threadIdx.x; x < B.z; x += kBS) tz[x] = precond_factor(x, Lk, pre) * (w[x] * inv);
   }
-  if (threadIdx.x != 0) return;
   if (j < 0) {
-    if ((int)blockIdx.x == S.x) {
+    if (threadIdx.x == 0 && (int)blockIdx.x == S.x) {
       if (set_bnorm) st[B.x].bnorm = v;
       st[B.x].beta = v;
     }
     return;
   }
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&st[B.x].arrive, 1) == S.y - S.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
   __threadfence();
-  if (atomicAdd(&st[B.x].arrive, 1) != S.y - S.x - 1) return;
-  __threadfence();
+  __shared__ double ch[kMaxRestart + 1], csh[kMaxRestart], snh[kMaxRestart];
+  const double* Hc = H + (size_t)B.x * (m + 1) * m + (size_t)j * (m + 1);
+  for (int i = threadIdx.x; i <= j; i += kBS) ch[i] = Hc[i];
+  for (int i = threadIdx.x; i < j; i += kBS) csh[i] = cs[(size_t)B.x * m + i], snh[i] = sn[(size_t)B.x * m + i];
+  if (threadIdx.x == 0) ch[j + 1] = v;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   st[B.x].arrive = 0;
-  H[(size_t)B.x * (m + 1) * m + (size_t)j * (m + 1) + j + 1] = v;
-  givens_step(j, m, B.x, H, cs, sn, g, st);
+  givens_step(j, m, B.x, ch, csh, snh, H, cs, sn, g, st);
 }
 
 // Per system: least squares R y = g (k x k) and the restart coefficients

@@ -236,6 +236,7 @@ struct Surface {
   // centroid (part_center), so that the FP32 copies keep the most digits.
   DevBuf<double4_32a> tgt64;  // 2n: (x, y, z, area), (nx, ny, nz, 0)
   DevBuf<float4> tgt32;   // the same in FP32
+  DevBuf<float4> exptab;  // 2^(j/1024), j < 1024, as df64 (hi, lo) pairs: the df64 exp table
 
   // per-pass scratch
   DevBuf<float4> rec32;
@@ -347,7 +348,6 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
 // blocks shared by 16 right-hand sides (mrhs_df.cu)
 void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
                     double dpsi, const int* skip, int skip_stride);
-DFConst make_df_const(const bipb_medium& m);
 // FP64 reduction of FP64 per-split partials (kernels.cu), tab[k] = {n, splits, offset, 0}
 void launch_reduce_matvec64(Surface* s, const SysLayout& L, const int4* tab, const double* part, const double* u,
                             double* y, double dphi, double dpsi, const int* skip, int skip_stride);

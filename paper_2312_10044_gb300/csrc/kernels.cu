@@ -93,7 +93,7 @@ struct MatvecPolicy {
 // (x.hi, a.hi), (x.lo, a.lo), (m.hi, 0), (m.lo, 0) with a = ds psi and
 // m = ds phi n (forward) or a = wphi, m = wpsi n (transposed).
 __device__ df* df_exp_table() {
-  __shared__ df tab[32];
+  __shared__ __align__(16) df tab[kExpTab];
   return tab;
 }
 
@@ -113,9 +113,8 @@ struct MatvecDFPolicy {
     double* part;
     DFConst c;
   };
-  __device__ static void prologue(const Args&) {
-    df* tab = df_exp_table();
-    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  __device__ static void prologue(const Args& a) {
+    df_load_exp_table(df_exp_table(), a.c);
   }
   __device__ static void load(const Args& a, int i, Tgt& t) {
     double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
@@ -200,9 +199,8 @@ struct ReactionPolicy {
     DFConst c;
   };
   template <class A>
-  __device__ static void prologue(const A&) {
-    df* tab = df_exp_table();
-    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  __device__ static void prologue(const A& a) {
+    df_load_exp_table(df_exp_table(), a.c);
   }
   __device__ static void load(const Args& a, int k, Tgt& t) {
     double4_32a g = a.pts[k];
@@ -254,9 +252,8 @@ struct EnergyRowPolicy {
     DFConst c;
   };
   template <class A>
-  __device__ static void prologue(const A&) {
-    df* tab = df_exp_table();
-    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  __device__ static void prologue(const A& a) {
+    df_load_exp_table(df_exp_table(), a.c);
   }
   __device__ static void load(const Args& a, int i, Tgt& t) {
     double4_32a g = a.tgt[2 * i], v = a.tgt[2 * i + 1];
@@ -302,9 +299,8 @@ struct GradPolicy {
     df inv_eps_in;
   };
   template <class A>
-  __device__ static void prologue(const A&) {
-    df* tab = df_exp_table();
-    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
+  __device__ static void prologue(const A& a) {
+    df_load_exp_table(df_exp_table(), a.c);
   }
   __device__ static void load(const Args& a, int k, Tgt& t) {
     double4_32a g = a.pts[k];
@@ -743,7 +739,7 @@ int blocks_for(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1
 enum PassId { kPassMv64 = 1, kPassMv64T, kPassMvDF, kPassMvDFT, kPassMv32 = 16, kPassMv32T = 32, kPassSource = 48,
               kPassReaction, kPassRow, kPassGrad, kPassPotIn, kPassPotOut, kPassPotSrc };
 
-DFConst df_const_impl(const bipb_medium& m) {
+DFConst df_const_impl(const Surface* s, const bipb_medium& m) {
   auto split = [](double v) {
     df r;
     r.hi = (float)v;
@@ -755,12 +751,13 @@ DFConst df_const_impl(const bipb_medium& m) {
   c.eps = split(eps);
   c.inveps = split(1.0 / eps);
   c.kappa = split(m.kappa);
-  const double L = 0.693147180559945309417232121458 / 32.0;
-  const double l1 = std::ldexp(std::nearbyint(std::ldexp(L, 17)), -17);  // 12 significant bits
+  const double L = 0.693147180559945309417232121458 / kExpTab;
+  const double l1 = std::ldexp(std::nearbyint(std::ldexp(L, 17)), -17);  // 7 significant bits
   c.l1 = (float)l1;
   c.l2 = (float)(L - l1);
   c.l3 = (float)(L - l1 - (double)c.l2);
-  c.inv_l = (float)(32.0 / 0.693147180559945309417232121458);
+  c.inv_l = (float)(kExpTab / 0.693147180559945309417232121458);
+  c.tab = s->exptab.p;
   return c;
 }
 
@@ -888,7 +885,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     return;
   }
   if (precision == BIPB_DF64) {
-    DFConst c = df_const_impl(m);
+    DFConst c = df_const_impl(s, m);
     bool shared_surface = L.K >= 4;
     for (int k = 0; k < L.K && shared_surface; ++k)
       shared_surface = L.geo_off[k] == 0 && L.n[k] == L.n[0] && L.vec_off[k] == 2 * L.n[0] * k;
@@ -939,7 +936,6 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
   }
 }
 
-DFConst make_df_const(const bipb_medium& m) { return df_const_impl(m); }
 
 void launch_reduce_matvec64(Surface* s, const SysLayout& L, const int4* tab, const double* part, const double* u,
                             double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
@@ -1048,7 +1044,7 @@ void reaction_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const d
   k_pack_df<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, false, s->tgt64.p, u, s->recdf.p,
                                                                           nullptr, 0);
   BIPB_LAUNCHED(s);
-  ReactionPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(m)};
+  ReactionPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(s, m)};
   launch_items<ReactionPolicy, float4, NT, TPT, CH>(s, kTReaction, plan, a, s->recdf.p, nullptr, 0);
   k_reduce_reaction<<<L.K, 1024, 0, s->stream>>>(plan->tab.p, lay, s->part64.p, s->chg.p, phi_reac, e_out);
   BIPB_LAUNCHED(s);
@@ -1065,7 +1061,7 @@ void potential_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const 
   k_pack_df<<<dim3(blocks_for(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, false, s->tgt64.p, u, s->recdf.p,
                                                                           nullptr, 0);
   BIPB_LAUNCHED(s);
-  ReactionPolicy::Args a{pts, nullptr, df_const_impl(m)};
+  ReactionPolicy::Args a{pts, nullptr, df_const_impl(s, m)};
   ItemPlan* plan;
   if (inside) {
     plan = plan_pass<ReactionPolicy, float4, NT, TPT, CH>(s, kPassPotIn, sys, CH);
@@ -1122,7 +1118,7 @@ void energy_row_pass(Surface* s, const SysLayout& L, const bipb_medium& m, doubl
   s->grow(s->part64, (size_t)plan->part_len);
   k_pack_chg_df<<<blocks_for(n_chg, 256), 256, 0, s->stream>>>(n_chg, s->chg.p, s->chgdf.p);
   BIPB_LAUNCHED(s);
-  EnergyRowPolicy::Args a{s->tgt64.p, s->part64.p, df_const_impl(m)};
+  EnergyRowPolicy::Args a{s->tgt64.p, s->part64.p, df_const_impl(s, m)};
   launch_items<EnergyRowPolicy, float4, NT, TPT, CH>(s, kTRow, plan, a, s->chgdf.p, nullptr, 0);
   k_energy_row_reduce<<<dim3(blocks_for(2 * L.max_n, 256), L.K), 256, 0, s->stream>>>(
       s->lay_dev(L), plan->tab.p, s->part64.p, s->tgt64.p, c);
@@ -1142,7 +1138,7 @@ void grad_pass(Surface* s, const SysLayout& L, const bipb_medium& m, const doubl
   BIPB_LAUNCHED(s);
   const double inv = 1.0 / m.eps_in;
   const float inv_hi = (float)inv;
-  GradPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(m), df{inv_hi, (float)(inv - (double)inv_hi)}};
+  GradPolicy::Args a{s->chg.p, s->part64.p, df_const_impl(s, m), df{inv_hi, (float)(inv - (double)inv_hi)}};
   launch_items<GradPolicy, float4, NT, TPT, CH>(s, kTGrad, plan, a, s->recdf.p, nullptr, 0);
   k_reduce_grad<<<dim3(blocks_for(L.max_nc, 256), L.K), 256, 0, s->stream>>>(plan->tab.p, lay, s->part64.p,
                                                                               s->chg.p, dq, dy);

@@ -59,7 +59,7 @@ __global__ void k_pack_mrhs_df(int n, int nb, const double4_32a* __restrict__ tg
 // right-hand-side values, source records, exp table.
 template <int G>
 constexpr int smem_bytes() {
-  return 2 * kCh * kTgt * 16 + kGB * G * kCh * 16 + kCh * 4 * 16 + 32 * 8;
+  return 2 * kCh * kTgt * 16 + kGB * G * kCh * 16 + kCh * 4 * 16 + kExpTab * 8;
 }
 
 // items: {t0, s0, s1, split}; geo, u4: the packed records of k_pack_mrhs_df;
@@ -74,12 +74,12 @@ __global__ void __launch_bounds__(kTgt * G, 512 / (kTgt * G))
   float4* kbl = kbh + kCh * kTgt;                           // lo parts
   float4* ush = kbl + kCh * kTgt;                           // [8 G][kCh]: (phi.hi, phi.lo, psi.hi, psi.lo)
   float4* srec = ush + kGB * G * kCh;                       // [kCh][4]: x, n split as below
-  df* tab = reinterpret_cast<df*>(srec + kCh * 4);          // 2^(j/32)
+  df* tab = reinterpret_cast<df*>(srec + kCh * 4);          // 2^(j/1024)
   const int tid = threadIdx.x;
   const int g = tid / kTgt, tl = tid % kTgt;  // MAC phase: group g (warp-uniform), target tl
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, s0 = item.y, s1 = item.z, split = item.w;
-  if (tid < 32) tab[tid] = df_from_double(exp2((double)tid / 32.0));
+  df_load_exp_table(tab, c);
   const int ti = t0 + tl;
   const bool tvalid = ti < n;
   df xi[3], ni[3];

@@ -103,7 +103,7 @@ struct SymPolicy {
 };
 
 __device__ df* sym_exp_table() {
-  __shared__ df tab[32];
+  __shared__ __align__(16) df tab[kExpTab];
   return tab;
 }
 
@@ -123,10 +123,7 @@ struct SymDFPolicy {
   struct Args {
     DFConst c;
   };
-  __device__ static void prologue(const Args&) {
-    df* tab = sym_exp_table();
-    if (threadIdx.x < 32) tab[threadIdx.x] = df_from_double(exp2((double)threadIdx.x / 32.0));
-  }
+  __device__ static void prologue(const Args& g) { df_load_exp_table(sym_exp_table(), g.c); }
   __device__ static void load(const float4* r, Elem& e) { unpack(r[0], r[1], r[2], r[3], e); }
   template <int CH>
   __device__ static void load_plane(const float4* sh, int q, Elem& e) {
