@@ -334,11 +334,13 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
 // the fastest; returns its index and its time per mat-vec in best_ms.
 int autotune_matvec32(Surface* s, const SysLayout& L, const bipb_medium& m, int reps, double* best_ms);
 // ---- sym.cu: mat-vecs visiting every unordered pair once; false when the
-// layout is too large for the symmetric work list (nothing launched then)
-bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, int variant,
+// layout is too large for the symmetric work list, or 0 < kappa < 1e-6
+// (nothing launched then)
+bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, double kappa, bool transpose,
+                  int variant, const double* u, double* y, double dphi, double dpsi, const int* skip,
+                  int skip_stride);
+bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, double kappa, bool transpose,
                   const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride);
-bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, bool transpose, const double* u,
-                  double* y, double dphi, double dpsi, const int* skip, int skip_stride);
 bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
                    double dphi, double dpsi, const int* skip, int skip_stride);
 // y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)

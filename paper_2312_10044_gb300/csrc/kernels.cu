@@ -731,6 +731,7 @@ PairConst<T> pair_const(const bipb_medium& m) {
   c.kappa = (T)m.kappa;
   c.nkl2e = (T)(-m.kappa * 1.4426950408889634);
   c.kappa2 = (T)(m.kappa * m.kappa);
+  c.smax = (T)kSMaxD;
   return c;
 }
 
@@ -902,7 +903,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
   }
   if (precision == BIPB_FP64) {
     PairConst<double> c = pair_const<double>(m);
-    if (s->sym_pairs && matvec_sym64(s, L, c, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;
+    if (s->sym_pairs && matvec_sym64(s, L, c, m.kappa, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;
     if (transpose)
       run_matvec64<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     else
@@ -912,7 +913,8 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
   PairConst<float> c = pair_const<float>(m);
   int variant = s->mv32_variant;
   if (variant >= kFirstSymVariant) {
-    if (matvec_sym32(s, L, c, transpose, variant - kFirstSymVariant, u, y, dphi, dpsi, skip, skip_stride)) return;
+    if (matvec_sym32(s, L, c, m.kappa, transpose, variant - kFirstSymVariant, u, y, dphi, dpsi, skip, skip_stride))
+      return;
     variant = 0;  // too large for the symmetric work list
   }
   switch (variant) {

@@ -44,6 +44,7 @@ struct PairConst {
   T kappa;   // inverse Debye length
   T nkl2e;   // -kappa * log2(e), the ex2 argument scale (FP32 path)
   T kappa2;  // kappa^2
+  T smax;    // clamp of 1/r in the units of the symmetric pair (1e6 / kappa when scaled by kappa)
 };
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
@@ -56,6 +57,15 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+
+// Precision-generic pieces of the symmetric pair: 1/sqrt (MUFU estimate in
+// FP32), min, and exp(-x) for x >= 0 (MUFU ex2 in FP32).
+__device__ __forceinline__ float rsqrt_of(float x) { return rsqrt_approx(x); }
+__device__ __forceinline__ double rsqrt_of(double x) { return rsqrt(x); }
+__device__ __forceinline__ float min_of(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double min_of(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float exp_neg_of(float x) { return ex2_approx(x * -1.4426950408889634f); }
+__device__ __forceinline__ double exp_neg_of(double x) { return exp(-x); }
 
 // 1/r (clamped; 0 for the self pair) and exp(-kappa r) for both precisions.
 template <bool MASK>
@@ -154,38 +164,63 @@ __device__ __forceinline__ void pair_transpose(T xj, T yj, T zj, T nxj, T nyj, T
 //   Zphi_j += s^3 [ (eps t - 1) c_j a_i + beta_i U ]
 //   Zpsi_j += s [ (1 - e) a_i + (t/eps - 1) s^2 beta_i c_i ]
 // (t = target i of the thread, s = source j; P/Q the two outputs of each.)
-template <bool MASK, bool TRANS, typename T>
+// Two forms, chosen per launch:
+// - SCALED (kappa > 0): positions are multiplied by kappa when the records
+//   are packed, so d, r and s are in units of the Debye length; then
+//   kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e (with r s = 1).  The
+//   kernels scale as K1 ~ kappa, K2, K3 ~ kappa^2, K4 ~ kappa^3, a product of
+//   a row factor and a column factor: the records' alpha is multiplied by
+//   kappa as well, and the caller multiplies the sums (A u: P by kappa, Q by
+//   kappa^2; A^T w: P by kappa^2, Q by kappa).
+// - LAPLACE (kappa = 0, unscaled): e = t = 1, w = 3, so K1 = K4 = 0 and only
+//   the double-layer terms (eps - 1) c_j s^3 and (1/eps - 1) c_i s^3 remain.
+template <bool MASK, bool TRANS, bool LAPLACE, typename T>
 __device__ __forceinline__ void sym_pair(T dx, T dy, T dz, const T* nt, T at, T alt, const T* ns, T as, T als,
                                          bool self, const PairConst<T>& c, T& Pt, T& Qt, T& Ps, T& Qs) {
-  T s, r, e;
-  radial<MASK>(dx * dx + dy * dy + dz * dz, self, c, s, r, e);
-  const T kr = r * c.kappa;
-  const T t = e * kr + e;
-  const T tm1 = t - T(1);
-  const T s2 = s * s;
-  const T s3 = s2 * s;
-  // (w - 3) s^2 with w - 3 = 3 (t - 1) + e (kappa r)^2 and r s = 1: 3 (t - 1) s^2 + e kappa^2
-  // (the self pair, s = 0, gets e kappa^2 instead of 0, but there c_i = c_j = t - 1 = 0)
-  const T wm3s2 = tm1 * (T(3) * s2) + e * c.kappa2;
-  const T ts3 = t * s3;
+  const T r2 = dx * dx + dy * dy + dz * dz;
+  T s = min_of(rsqrt_of(r2), c.smax);
+  if (MASK) s = self ? T(0) : s;
   const T ci = nt[0] * dx + nt[1] * dy + nt[2] * dz;
   const T cj = ns[0] * dx + ns[1] * dy + ns[2] * dz;
-  const T cij = nt[0] * ns[0] + nt[1] * ns[1] + nt[2] * ns[2];
-  const T U = tm1 * cij - wm3s2 * (ci * cj);
-  // s and s^3 folded into the four coefficients every update uses
-  const T ome_s = s - e * s, U_s3 = U * s3;
-  const T et1_s3 = c.eps * ts3 - s3, te1_s3 = c.inveps * ts3 - s3;  // (eps t - 1) s^3, (t/eps - 1) s^3
-  if (!TRANS) {
-    Pt = (et1_s3 * cj) * als + (ome_s * as + Pt);
-    Qt = U_s3 * als + ((te1_s3 * ci) * as + Qt);
-    Ps = ome_s * at - ((et1_s3 * ci) * alt - Ps);
-    Qs = U_s3 * alt - ((te1_s3 * cj) * at - Qs);
+  const T s3 = s * s * s;
+  if constexpr (LAPLACE) {
+    const T et1_s3 = c.eps * s3 - s3, te1_s3 = c.inveps * s3 - s3;  // (eps - 1) s^3, (1/eps - 1) s^3
+    if (!TRANS) {
+      Pt = (et1_s3 * cj) * als + Pt;
+      Qt = (te1_s3 * ci) * as + Qt;
+      Ps = Ps - (et1_s3 * ci) * alt;
+      Qs = Qs - (te1_s3 * cj) * at;
+    } else {
+      Pt = Pt - (et1_s3 * ci) * as;
+      Qt = Qt - (te1_s3 * cj) * als;
+      Ps = (et1_s3 * cj) * at + Ps;
+      Qs = (te1_s3 * ci) * alt + Qs;
+    }
   } else {
-    Pt = U_s3 * als - ((et1_s3 * ci) * as - Pt);
-    Qt = ome_s * as - ((te1_s3 * cj) * als - Qt);
-    Ps = U_s3 * alt + ((et1_s3 * cj) * at + Ps);
-    Qs = ome_s * at + ((te1_s3 * ci) * alt + Qs);
+    const T kr = r2 * s;  // kappa r (0 for a masked pair)
+    const T e = exp_neg_of(kr);
+    const T t = e * kr + e;
+    const T tm1 = t - T(1);
+    const T s2 = s * s;
+    // (w - 3) s^2 = 3 (t - 1) s^2 + e (a masked pair gets e = 1, but its every coefficient carries s = 0)
+    const T wm3s2 = tm1 * (T(3) * s2) + e;
+    const T ts3 = t * s3;
+    const T cij = nt[0] * ns[0] + nt[1] * ns[1] + nt[2] * ns[2];
+    const T U = tm1 * cij - wm3s2 * (ci * cj);
+    // s and s^3 folded into the four coefficients every update uses
+    const T ome_s = s - e * s, U_s3 = U * s3;
+    const T et1_s3 = c.eps * ts3 - s3, te1_s3 = c.inveps * ts3 - s3;  // (eps t - 1) s^3, (t/eps - 1) s^3
+    if (!TRANS) {
+      Pt = (et1_s3 * cj) * als + (ome_s * as + Pt);
+      Qt = U_s3 * als + ((te1_s3 * ci) * as + Qt);
+      Ps = ome_s * at - ((et1_s3 * ci) * alt - Ps);
+      Qs = U_s3 * alt - ((te1_s3 * cj) * at - Qs);
+    } else {
+      Pt = U_s3 * als - ((et1_s3 * ci) * as - Pt);
+      Qt = ome_s * as - ((te1_s3 * cj) * als - Qt);
+      Ps = U_s3 * alt + ((et1_s3 * cj) * at + Ps);
+      Qs = ome_s * at + ((te1_s3 * ci) * alt + Qs);
+    }
   }
 }
-
 }  // namespace bipb

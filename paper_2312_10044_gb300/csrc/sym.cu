@@ -56,10 +56,13 @@ struct SymV4<double> {
 // Record of an element (both roles): position, a, normal, alpha, where
 // (a, alpha) = (ds psi, ds phi) for A u and (wphi, wpsi) for A^T w.
 
-template <typename T, bool TRANS>
+// LAPLACE: the kappa = 0 form of sym_pair (pair.cuh); otherwise the records
+// are in kappa-scaled units (SCALED).
+template <typename T, bool TRANS, bool LAPLACE>
 struct SymPolicy {
   using V4 = typename SymV4<T>::type;
   using PT = T;  // partial sums are stored in this type
+  static constexpr bool SCALED = !LAPLACE;
   static constexpr int RW = 2;  // (x, a), (n, alpha)
   static constexpr int UNROLL = sizeof(T) == 4 ? 4 : 1;  // sources in flight per thread
   struct Elem {
@@ -84,7 +87,7 @@ struct SymPolicy {
   // i-side of target t and j-side of source sj for the pair d = x_t - x_sj
   template <bool MASK>
   __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
-    sym_pair<MASK, TRANS>(t.x[0] - sj.x[0], t.x[1] - sj.x[1], t.x[2] - sj.x[2], t.n, t.a, t.al, sj.n, sj.a, sj.al,
+    sym_pair<MASK, TRANS, LAPLACE>(t.x[0] - sj.x[0], t.x[1] - sj.x[1], t.x[2] - sj.x[2], t.n, t.a, t.al, sj.n, sj.a, sj.al,
                           masked, g.c, ti.p, ti.q, tj.p, tj.q);
   }
   __device__ static void renorm(Acc&) {}
@@ -112,6 +115,7 @@ template <bool TRANS>
 struct SymDFPolicy {
   using V4 = float4;
   using PT = double;
+  static constexpr bool SCALED = false;
   static constexpr int RW = 4;
   static constexpr int UNROLL = 1;
   struct Elem {
@@ -266,9 +270,10 @@ __global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4
 // Records of every system at vec_off / 2 (RW vectors each).  lay[k] = {geo_off, n, vec_off, chg_off}.
 // A u: a = ds psi, alpha = ds phi; A^T w: a = wphi, alpha = wpsi.
 template <typename V4, typename T>
+// sigma: the positions and alpha are multiplied by it (kappa-scaled records; 1 otherwise)
 __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
                            const double* __restrict__ u, V4* __restrict__ rec, const int* __restrict__ skip,
-                           int skip_stride) {
+                           int skip_stride, double sigma) {
   const int k = blockIdx.y;
   const int4 L = lay[k];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,9 +281,9 @@ __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const d
   const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
   const double phi = u[L.z + j], psi = u[L.z + L.y + j];
   const double a = transpose ? phi : g.w * psi;
-  const double al = transpose ? psi : g.w * phi;
+  const double al = sigma * (transpose ? psi : g.w * phi);
   V4 r0, r1;
-  r0.x = (T)g.x, r0.y = (T)g.y, r0.z = (T)g.z, r0.w = (T)a;
+  r0.x = (T)(sigma * g.x), r0.y = (T)(sigma * g.y), r0.z = (T)(sigma * g.z), r0.w = (T)a;
   r1.x = (T)v.x, r1.y = (T)v.y, r1.z = (T)v.z, r1.w = (T)al;
   V4* o = rec + 2 * (size_t)(L.z / 2 + j);
   o[0] = r0, o[1] = r1;
@@ -304,13 +309,14 @@ __global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, cons
   o[3] = make_float4(n0.lo, n1.lo, n2.lo, al.lo);
 }
 
-// y_i = diag u_i - (1/(4 pi)) scale_i (i-side blocks of the element's row + j-side rows 0..E).
+// y_i = diag u_i - (1/(4 pi)) scale_i f_c (i-side blocks of the element's row + j-side rows 0..E),
+// f_c = f.x for the phi rows and f.y for the psi rows (the factors of kappa-scaled records).
 // tab[k] = {n, first row entry, j-side base, T}; tab[row entry + E] = {first i-side block, blocks, 0, 0}.
 template <typename PT>
 __global__ void k_reduce_sym(const int4* __restrict__ lay, const int4* __restrict__ tab, const PT* __restrict__ part,
                              const double* __restrict__ u, double* __restrict__ y, double d_phi, double d_psi,
                              const double4_32a* __restrict__ tgt64_for_area, const int* __restrict__ skip,
-                             int skip_stride) {
+                             int skip_stride, double2 f) {
   const int k = blockIdx.y;
   const int4 L = lay[k], S = tab[k];
   const int n = L.y, T = S.w;
@@ -337,7 +343,7 @@ __global__ void k_reduce_sym(const int4* __restrict__ lay, const int4* __restric
   }
   for (; I <= E; ++I) acc += at(I);
   const double sc = tgt64_for_area ? tgt64_for_area[2 * (L.x + e)].w : 1.0;
-  y[L.z + i] = (c == 0 ? d_phi : d_psi) * u[L.z + i] - kInv4PiS * sc * acc;
+  y[L.z + i] = (c == 0 ? d_phi : d_psi) * u[L.z + i] - kInv4PiS * sc * (c == 0 ? f.x : f.y) * acc;
 }
 
 int blocks_of(int64_t n, int bs) { return (int)std::max<int64_t>(1, (n + bs - 1) / bs); }
@@ -570,8 +576,11 @@ int sym_occupancy() {
 template <class P, int NT, int TPT, int CH, int MINB>
 void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typename P::Args& g, bool transpose,
              DevBuf<typename P::V4>& recbuf, DevBuf<typename P::PT>& partbuf, const double* u, double* y,
-             double dphi, double dpsi, const int* skip, int skip_stride) {
+             double dphi, double dpsi, const int* skip, int skip_stride, double sigma = 1.0) {
   constexpr int T = NT * TPT;
+  if (!P::SCALED) sigma = 1.0;
+  // A u: P ~ sigma, Q ~ sigma^2; A^T w: P ~ sigma^2, Q ~ sigma (pair.cuh)
+  const double2 f = transpose ? make_double2(sigma * sigma, sigma) : make_double2(sigma, sigma * sigma);
   const uint64_t key = sym_key(pass_id, L.key);
   ItemPlan* plan = plan_sym(s, key, L, T, s->num_sms * sym_occupancy<P, NT, TPT, CH, MINB>(), CH);
   s->grow(recbuf, (size_t)(L.len / 2) * P::RW);
@@ -582,7 +591,7 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
                                                                               recbuf.p, skip, skip_stride);
   } else {
     k_pack_sym<typename P::V4, typename P::PT><<<dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream>>>(
-        lay, transpose, s->tgt64.p, u, recbuf.p, skip, skip_stride);
+        lay, transpose, s->tgt64.p, u, recbuf.p, skip, skip_stride, sigma);
   }
   BIPB_LAUNCHED(s);
   {
@@ -592,26 +601,52 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
     BIPB_LAUNCHED(s);
   }
   k_reduce_sym<typename P::PT><<<dim3(blocks_of(2 * (int64_t)L.max_n, 256), L.K), 256, 0, s->stream>>>(
-      lay, plan->tab.p, partbuf.p, u, y, dphi, dpsi, transpose ? s->tgt64.p : nullptr, skip, skip_stride);
+      lay, plan->tab.p, partbuf.p, u, y, dphi, dpsi, transpose ? s->tgt64.p : nullptr, skip, skip_stride, f);
   BIPB_LAUNCHED(s);
 }
 
 }  // namespace
 
-bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, int variant,
-                  const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
+// The symmetric FP32 / FP64 forms: LAPLACE for kappa = 0, kappa-scaled
+// records for kappa >= kSymKappaMin; in between (a Debye length above 1e6 A)
+// the scaled 1/r^3 could leave the FP32 range, and the caller takes the
+// ordered kernels.
+constexpr double kSymKappaMin = 1e-6;
+
+template <typename T>
+bool sym_form(double kappa, PairConst<T>& c, bool& laplace) {
+  laplace = kappa == 0.0;
+  if (!laplace && kappa < kSymKappaMin) return false;
+  c.smax = (T)(laplace ? kSMaxD : kSMaxD / kappa);  // pairs closer than 1e-6 A act as self pairs
+  return true;
+}
+
+bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c0, double kappa, bool transpose,
+                  int variant, const double* u, double* y, double dphi, double dpsi, const int* skip,
+                  int skip_stride) {
   static const int kT[3] = {512, 512, 1024};  // NT x TPT of the variants below
   if (variant < 0 || variant > 2) throw Error(BIPB_ERR_INVALID_ARG, "unknown symmetric FP32 mat-vec variant");
-  if (!sym_fits(L, kT[variant])) return false;
+  PairConst<float> c = c0;
+  bool lap = false;
+  if (!sym_fits(L, kT[variant]) || !sym_form(kappa, c, lap)) return false;
   const int kind = transpose ? kTMv32T : kTMv32;
-#define BIPB_SYM32(V_, NT_, TPT_, CH_, MINB_)                                                               \
-  case V_:                                                                                                   \
-    if (transpose)                                                                                           \
-      run_sym<SymPolicy<float, true>, NT_, TPT_, CH_, MINB_>(s, 0x100 + V_, kind, L, {c}, true, s->rec32,    \
-                                                             s->part32, u, y, dphi, dpsi, skip, skip_stride); \
-    else                                                                                                     \
-      run_sym<SymPolicy<float, false>, NT_, TPT_, CH_, MINB_>(s, 0x200 + V_, kind, L, {c}, false, s->rec32,  \
-                                                              s->part32, u, y, dphi, dpsi, skip, skip_stride); \
+#define BIPB_SYM32_RUN(TR_, LAP_, V_, NT_, TPT_, CH_, MINB_)                                                    \
+  run_sym<SymPolicy<float, TR_, LAP_>, NT_, TPT_, CH_, MINB_>(s, (TR_ ? 0x100 : 0x200) + V_, kind, L, {c}, TR_, \
+                                                               s->rec32, s->part32, u, y, dphi, dpsi, skip,      \
+                                                               skip_stride, kappa)
+#define BIPB_SYM32(V_, NT_, TPT_, CH_, MINB_)                     \
+  case V_:                                                         \
+    if (transpose) {                                               \
+      if (lap)                                                     \
+        BIPB_SYM32_RUN(true, true, V_, NT_, TPT_, CH_, MINB_);     \
+      else                                                         \
+        BIPB_SYM32_RUN(true, false, V_, NT_, TPT_, CH_, MINB_);    \
+    } else {                                                       \
+      if (lap)                                                     \
+        BIPB_SYM32_RUN(false, true, V_, NT_, TPT_, CH_, MINB_);    \
+      else                                                         \
+        BIPB_SYM32_RUN(false, false, V_, NT_, TPT_, CH_, MINB_);   \
+    }                                                              \
     return true;
   switch (variant) {
     BIPB_SYM32(0, 256, 2, 64, 4)
@@ -619,18 +654,31 @@ bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, boo
     BIPB_SYM32(2, 256, 4, 64, 2)
   }
 #undef BIPB_SYM32
+#undef BIPB_SYM32_RUN
   return false;
 }
 
-bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, bool transpose, const double* u,
-                  double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
-  if (!sym_fits(L, 256)) return false;
-  if (transpose)
-    run_sym<SymPolicy<double, true>, 128, 2, 64, 1>(s, 0x300, kTMv64T, L, {c}, true, s->rec64, s->part64, u, y, dphi,
-                                                 dpsi, skip, skip_stride);
-  else
-    run_sym<SymPolicy<double, false>, 128, 2, 64, 1>(s, 0x400, kTMv64, L, {c}, false, s->rec64, s->part64, u, y, dphi,
-                                                  dpsi, skip, skip_stride);
+bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c0, double kappa, bool transpose,
+                  const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
+  PairConst<double> c = c0;
+  bool lap = false;
+  if (!sym_fits(L, 256) || !sym_form(kappa, c, lap)) return false;
+#define BIPB_SYM64_RUN(TR_, LAP_)                                                                                \
+  run_sym<SymPolicy<double, TR_, LAP_>, 128, 2, 64, 1>(s, TR_ ? 0x300 : 0x400, TR_ ? kTMv64T : kTMv64, L, {c}, TR_, \
+                                                      s->rec64, s->part64, u, y, dphi, dpsi, skip, skip_stride,     \
+                                                      kappa)
+  if (transpose) {
+    if (lap)
+      BIPB_SYM64_RUN(true, true);
+    else
+      BIPB_SYM64_RUN(true, false);
+  } else {
+    if (lap)
+      BIPB_SYM64_RUN(false, true);
+    else
+      BIPB_SYM64_RUN(false, false);
+  }
+#undef BIPB_SYM64_RUN
   return true;
 }
 

@@ -119,6 +119,31 @@ def test_degenerate_media(bipb, orc):
         assert s.energy()[0] == 0.0
 
 
+@pytest.mark.parametrize("kappa", [1e-7, 2.5])
+def test_matvec_kappa_range(bipb, orc, kappa):
+    """The symmetric kernels work in kappa-scaled units; a Debye length
+    above 1e6 A (kappa = 1e-7) takes the ordered kernels instead, and strong
+    screening (kappa = 2.5 / A) makes e^{-kappa r} underflow for most pairs.
+    Both directions against the oracle in every precision."""
+    p = _ragged(3)
+    rng = np.random.default_rng(12)
+    U = rng.standard_normal((2, 2 * p.n))
+    med = bipb.medium(1.0, 80.0, kappa)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        for transpose in (False, True):
+            f = orc.matvec_t if transpose else orc.matvec
+            ref = np.stack([f(p.centroids, p.normals, p.areas, 80.0, kappa, u) for u in U])
+            scale = np.abs(ref).max()
+            for prec, variant, tol in ((bipb.FP64, 0, 1e-12), (bipb.DF64, 0, 2e-12), (bipb.FP32, 9, 2e-5),
+                                       (bipb.FP32, 7, 2e-5)):
+                s.set_variant(variant)
+                yd = torch.full_like(ud, float("nan"))
+                s.matvec(ud, yd, precision=prec, transpose=transpose, med=med)
+                err = np.abs(yd.cpu().numpy() - ref).max()
+                assert err < tol * scale, (prec, variant, transpose, err / scale)
+
+
 def test_autotune_picks_a_variant(bipb):
     p = synth.kirkwood_problem(level=3)
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
