@@ -174,6 +174,7 @@ void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::v
   BIPB_REQUIRE(P.n >= 2, "need at least 2 triangles per surface");
   BIPB_REQUIRE(P.c && P.nrm && P.area, "NULL input array");
   double c[3] = {0, 0, 0};
+  std::vector<double> inv_len((size_t)P.n);
   for (int64_t i = 0; i < P.n; ++i) {
     BIPB_REQUIRE(finite3(P.c + 3 * i), "non-finite centroid");
     BIPB_REQUIRE(finite3(P.nrm + 3 * i), "non-finite normal");
@@ -181,46 +182,42 @@ void add_part(Surface* s, const PartIn& P, std::vector<double4_32a>& tgt, std::v
     const double* v = P.nrm + 3 * i;
     double len = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     BIPB_REQUIRE(std::fabs(len - 1.0) <= 1e-6, "normals must have unit length (within 1e-6)");
+    inv_len[i] = 1.0 / len;
     for (int k = 0; k < 3; ++k) c[k] += P.c[3 * i + k];
   }
   for (int k = 0; k < 3; ++k) c[k] /= (double)P.n;
-  // centred copies, and the check for duplicates (in FP32, then FP64 on a hit);
-  // the set is kept to reject charges on a centroid
+  // centred copies (FP64 and FP32 records), and the check for duplicates (in
+  // FP32, then FP64 on a hit); the set is kept to reject charges on a centroid
   CentroidSet cs;
   cs.d.resize(3 * (size_t)P.n);
   cs.f.resize(3 * (size_t)P.n);
   cs.reserve((size_t)P.n);
-  for (int64_t i = 0; i < P.n; ++i) {
-    for (int k = 0; k < 3; ++k) {
-      const double d = P.c[3 * i + k] - c[k];
-      cs.d[3 * i + k] = d;
-      cs.f[3 * i + k] = (float)d;
-    }
-    const int32_t j = cs.insert((int32_t)i);
-    if (j >= 0) {
-      const bool same64 = cs.d[3 * j] == cs.d[3 * i] && cs.d[3 * j + 1] == cs.d[3 * i + 1] &&
-                          cs.d[3 * j + 2] == cs.d[3 * i + 2];
-      throw Error(BIPB_ERR_INVALID_ARG,
-                  same64 ? "two centroids coincide" : "two centroids coincide after rounding to FP32");
-    }
-  }
-  s->part_off.push_back((int)s->n);
-  s->part_n.push_back((int)P.n);
-  for (int k = 0; k < 3; ++k) s->part_center.push_back(c[k]);
   const size_t base = tgt.size();
   tgt.resize(base + 2 * (size_t)P.n);
   tgt32.resize(base + 2 * (size_t)P.n);
   for (int64_t i = 0; i < P.n; ++i) {
+    double* d = &cs.d[3 * i];
+    float* f = &cs.f[3 * i];
+    for (int k = 0; k < 3; ++k) {
+      d[k] = P.c[3 * i + k] - c[k];
+      f[k] = (float)d[k];
+    }
+    const int32_t j = cs.insert((int32_t)i);
+    if (j >= 0) {
+      const bool same64 = cs.d[3 * j] == d[0] && cs.d[3 * j + 1] == d[1] && cs.d[3 * j + 2] == d[2];
+      throw Error(BIPB_ERR_INVALID_ARG,
+                  same64 ? "two centroids coincide" : "two centroids coincide after rounding to FP32");
+    }
     const double* v = P.nrm + 3 * i;
-    const double inv = 1.0 / std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    const double* d = &cs.d[3 * i];
-    const float* f = &cs.f[3 * i];
-    const double nx = v[0] * inv, ny = v[1] * inv, nz = v[2] * inv;
+    const double nx = v[0] * inv_len[i], ny = v[1] * inv_len[i], nz = v[2] * inv_len[i];
     tgt[base + 2 * i] = make_double4_32a(d[0], d[1], d[2], P.area[i]);
     tgt[base + 2 * i + 1] = make_double4_32a(nx, ny, nz, 0.0);
     tgt32[base + 2 * i] = make_float4(f[0], f[1], f[2], (float)P.area[i]);
     tgt32[base + 2 * i + 1] = make_float4((float)nx, (float)ny, (float)nz, 0.f);
   }
+  s->part_off.push_back((int)s->n);
+  s->part_n.push_back((int)P.n);
+  for (int k = 0; k < 3; ++k) s->part_center.push_back(c[k]);
   s->part_keys.push_back(std::move(cs));
   s->n += P.n;
 }
