@@ -112,6 +112,8 @@ __device__ __forceinline__ double precond_factor(int x, int4 Lk, double2 pre) {
 
 __global__ void k_dots(int j, int m1, int64_t len, const double* __restrict__ V, const double* __restrict__ w,
                        double* __restrict__ part, const DevState* st, const int4* __restrict__ blk) {
+  chain_wait();
+  chain_release();
   const int4 B = blk[blockIdx.x];
   if (st[B.x].skip) return;
   block_dots(j, m1, len, V, w, part, B);
@@ -125,6 +127,8 @@ __global__ void k_orth(int j, int m, int64_t len, const double* __restrict__ V, 
                        const double* __restrict__ part, double* __restrict__ H, int accumulate, const DevState* st,
                        const int4* __restrict__ blk, const int4* __restrict__ sysb, double* __restrict__ part1,
                        int want_norm, double* __restrict__ part_next) {
+  chain_wait();
+  chain_release();
   const int4 B = blk[blockIdx.x];
   if (st[B.x].skip) return;
   const int m1 = m + 1;
@@ -220,6 +224,8 @@ __global__ void k_normalize(int j, int m, const double* __restrict__ w, double* 
                             const int4* __restrict__ blk, const int4* __restrict__ sysb, int set_bnorm,
                             double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
                             double* __restrict__ tz, const int4* __restrict__ lay, double2 pre) {
+  chain_wait();
+  chain_release();
   const int4 B = blk[blockIdx.x];
   if (j >= 0 ? st[B.x].skip : !st[B.x].active) return;
   const int4 S = sysb[B.x];
@@ -538,16 +544,16 @@ void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium
     matvec(s, L, med, precision, transpose, tz ? tz : vj, w->w.p, &w->st->skip, kStateInts);
     // CGS2: the first pass also takes the dot products of the second, the
     // second also forms the block norms
-    k_dots<<<nb, kBS, 0, s->stream>>>(j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
+    launch_chained(k_dots, nb, kBS, 0, s->stream, j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
     BIPB_LAUNCHED(s);
-    k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, 0, w->st, w->blk.p, w->sysb.p,
-                                      w->part1.p, 0, w->part2.p);
+    launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, 0, w->st, w->blk.p,
+                   w->sysb.p, w->part1.p, 0, w->part2.p);
     BIPB_LAUNCHED(s);
-    k_orth<<<nb, kBS, 0, s->stream>>>(j, m, len, w->V.p, w->w.p, w->part2.p, w->H.p, 1, w->st, w->blk.p, w->sysb.p,
-                                      w->part1.p, 1, nullptr);
+    launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part2.p, w->H.p, 1, w->st, w->blk.p,
+                   w->sysb.p, w->part1.p, 1, nullptr);
     BIPB_LAUNCHED(s);
-    k_normalize<<<nb, kBS, 0, s->stream>>>(j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p, w->sysb.p,
-                                           0, w->cs.p, w->sn.p, w->g.p, tz, lay, pre);
+    launch_chained(k_normalize, nb, kBS, 0, s->stream, j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p,
+                   w->sysb.p, 0, w->cs.p, w->sn.p, w->g.p, tz, lay, pre);
     BIPB_LAUNCHED(s);
   }
   k_lsq<<<kg, 128, 0, s->stream>>>(m, K, w->H.p, w->cs.p, w->sn.p, w->g.p, w->y.p, w->z.p, w->st);

@@ -1,5 +1,6 @@
 // Internal declarations of libbipb (not part of the C ABI).
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,6 +40,35 @@ struct Error : std::runtime_error {
     else                                      \
       ++(sf)->launches;                       \
   } while (0)
+// Programmatic dependent launch along the chain of one Krylov step (record
+// pack, pair kernel, reduction, Gram-Schmidt passes, normalisation): each of
+// these kernels is launched with launch_chained and begins with
+// chain_wait(), which returns once the previous kernel in the stream has
+// completed and its writes are visible (at once when there is none or it
+// was launched without the attribute); only then does it call
+// chain_release(), which lets the next kernel of the chain be scheduled.
+// The next kernel's launch and block placement thus overlap this kernel's
+// run, while at most two grids of the chain are in flight (a grid is
+// released only once every block of its predecessor has passed the wait).
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                    Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  BIPB_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 #define BIPB_REQUIRE(cond, msg)                                     \
   do {                                                              \
     if (!(cond)) throw ::bipb::Error(BIPB_ERR_INVALID_ARG, (msg));  \

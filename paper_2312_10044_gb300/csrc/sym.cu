@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4
   constexpr int NW = NT / 32, T = NT * TPT;
   __shared__ V4 sh[CH * P::RW];
   __shared__ Acc jred[NW][CH];
+  chain_wait();  // the records of the pack kernel (no early release: this kernel is long)
   const int4 H = items[3 * blockIdx.x];
   const int rec_off = H.x, n = H.y, sys = H.z, jbase = H.w;
   if (skip != nullptr && skip[(size_t)sys * skip_stride] != 0) return;
@@ -269,11 +270,13 @@ __global__ void __launch_bounds__(NT, MINB) k_sym(typename P::Args g, const int4
 // ------------------------------------------------------------------ pack / reduce
 // Records of every system at vec_off / 2 (RW vectors each).  lay[k] = {geo_off, n, vec_off, chg_off}.
 // A u: a = ds psi, alpha = ds phi; A^T w: a = wphi, alpha = wpsi.
-template <typename V4, typename T>
 // sigma: the positions and alpha are multiplied by it (kappa-scaled records; 1 otherwise)
+template <typename V4, typename T>
 __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
                            const double* __restrict__ u, V4* __restrict__ rec, const int* __restrict__ skip,
                            int skip_stride, double sigma) {
+  chain_wait();
+  chain_release();
   const int k = blockIdx.y;
   const int4 L = lay[k];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,6 +295,8 @@ __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const d
 __global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
                               const double* __restrict__ u, float4* __restrict__ rec, const int* __restrict__ skip,
                               int skip_stride) {
+  chain_wait();
+  chain_release();
   const int k = blockIdx.y;
   const int4 L = lay[k];
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -317,6 +322,8 @@ __global__ void k_reduce_sym(const int4* __restrict__ lay, const int4* __restric
                              const double* __restrict__ u, double* __restrict__ y, double d_phi, double d_psi,
                              const double4_32a* __restrict__ tgt64_for_area, const int* __restrict__ skip,
                              int skip_stride, double2 f) {
+  chain_wait();
+  chain_release();
   const int k = blockIdx.y;
   const int4 L = lay[k], S = tab[k];
   const int n = L.y, T = S.w;
@@ -587,21 +594,21 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
   s->grow(partbuf, (size_t)plan->part_len);
   const int4* lay = s->lay_dev(L);
   if constexpr (std::is_same<typename P::PT, double>::value && std::is_same<typename P::V4, float4>::value) {
-    k_pack_sym_df<<<dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream>>>(lay, transpose, s->tgt64.p, u,
-                                                                              recbuf.p, skip, skip_stride);
+    launch_chained(k_pack_sym_df, dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream, lay, transpose, s->tgt64.p, u,
+                   recbuf.p, skip, skip_stride);
   } else {
-    k_pack_sym<typename P::V4, typename P::PT><<<dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream>>>(
-        lay, transpose, s->tgt64.p, u, recbuf.p, skip, skip_stride, sigma);
+    launch_chained(k_pack_sym<typename P::V4, typename P::PT>, dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream,
+                   lay, transpose, s->tgt64.p, u, recbuf.p, skip, skip_stride, sigma);
   }
   BIPB_LAUNCHED(s);
   {
     TimedLaunch tl(s, kind);
-    k_sym<P, NT, TPT, CH, MINB><<<plan->n_items, NT, 0, s->stream>>>(g, plan->items.p, recbuf.p, partbuf.p, skip,
-                                                                      skip_stride);
+    launch_chained(k_sym<P, NT, TPT, CH, MINB>, plan->n_items, NT, 0, s->stream, g, plan->items.p, recbuf.p,
+                   partbuf.p, skip, skip_stride);
     BIPB_LAUNCHED(s);
   }
-  k_reduce_sym<typename P::PT><<<dim3(blocks_of(2 * (int64_t)L.max_n, 256), L.K), 256, 0, s->stream>>>(
-      lay, plan->tab.p, partbuf.p, u, y, dphi, dpsi, transpose ? s->tgt64.p : nullptr, skip, skip_stride, f);
+  launch_chained(k_reduce_sym<typename P::PT>, dim3(blocks_of(2 * (int64_t)L.max_n, 256), L.K), 256, 0, s->stream, lay,
+                 plan->tab.p, partbuf.p, u, y, dphi, dpsi, transpose ? s->tgt64.p : nullptr, skip, skip_stride, f);
   BIPB_LAUNCHED(s);
 }
 
