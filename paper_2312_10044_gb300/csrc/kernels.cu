@@ -730,7 +730,6 @@ PairConst<T> pair_const(const bipb_medium& m) {
   c.inveps = (T)(1.0 / eps);
   c.kappa = (T)m.kappa;
   c.nkl2e = (T)(-m.kappa * 1.4426950408889634);
-  c.kappa2 = (T)(m.kappa * m.kappa);
   c.smax = (T)kSMaxD;
   return c;
 }

@@ -43,7 +43,6 @@ struct PairConst {
   T inveps;  // 1 / eps
   T kappa;   // inverse Debye length
   T nkl2e;   // -kappa * log2(e), the ex2 argument scale (FP32 path)
-  T kappa2;  // kappa^2
   T smax;    // clamp of 1/r in the units of the symmetric pair (1e6 / kappa when scaled by kappa)
 };
 

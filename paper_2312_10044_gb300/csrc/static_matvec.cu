@@ -202,7 +202,7 @@ extern "C" bipb_status bipb_matvec32_static(int64_t n, const double* centroids, 
     c.inveps = (float)(1.0 / eps);
     c.kappa = (float)m->kappa;
     c.nkl2e = (float)(-m->kappa * 1.4426950408889634);
-    c.kappa2 = (float)(m->kappa * m->kappa);
+    c.smax = kSMaxF;
     k_static_center<<<1, 256, 0, st>>>(nn, centroids, scratch);
     BIPB_CUDA(cudaGetLastError());
     const int n_pad = n_chunks * kSCH;
