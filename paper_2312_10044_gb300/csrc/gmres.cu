@@ -6,8 +6,9 @@
 // PCIe and runs the Arnoldi process on the host every iteration, every step
 // here stays on the device: mat-vec, classical Gram-Schmidt with one
 // re-orthogonalisation (CGS2, the same Krylov basis as modified Gram-Schmidt
-// in exact arithmetic, but as matrix-vector shaped passes), Givens rotations
-// and the convergence test.  K systems (right-hand sides of one surface, or
+// in exact arithmetic, but as matrix-vector shaped passes; one pass for the
+// FP32 Krylov solve inside the mixed modes), Givens rotations and the
+// convergence test.  K systems (right-hand sides of one surface, or
 // surfaces of uneven size) advance together: one Krylov vector is the
 // concatenation of the K systems' vectors, every kernel covers all of them,
 // and a system that has converged skips its share.  The host reads one small
@@ -539,18 +540,29 @@ void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium
   const int m = w->m, m1 = m + 1, K = w->K, nb = w->nblk;
   const int64_t len = w->len;
   const int kg = (K + 127) / 128;
+  const bool cgs2 = precision == BIPB_FP64 || precision == BIPB_DF64;
   for (int j = 0; j < m; ++j) {
     double* vj = w->V.p + (size_t)j * len;
     matvec(s, L, med, precision, transpose, tz ? tz : vj, w->w.p, &w->st->skip, kStateInts);
-    // CGS2: the first pass also takes the dot products of the second, the
-    // second also forms the block norms
+    // CGS2 for FP64 and df64 Krylov mat-vecs: the first pass also takes the
+    // dot products of the second, the second also forms the block norms.
+    // The FP32 / split-TF32 Krylov solve of the mixed modes stops at a
+    // relative 1e-6 (its true residual is measured in higher precision by
+    // the refinement), and its FP64 basis of at most m vectors loses
+    // orthogonality in one classical pass only at about eps_64 cond(A)^2:
+    // one pass, which also forms the block norms.
     launch_chained(k_dots, nb, kBS, 0, s->stream, j, m1, len, w->V.p, w->w.p, w->part.p, w->st, w->blk.p);
     BIPB_LAUNCHED(s);
-    launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, 0, w->st, w->blk.p,
-                   w->sysb.p, w->part1.p, 0, w->part2.p);
-    BIPB_LAUNCHED(s);
-    launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part2.p, w->H.p, 1, w->st, w->blk.p,
-                   w->sysb.p, w->part1.p, 1, nullptr);
+    if (cgs2) {
+      launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, 0, w->st, w->blk.p,
+                     w->sysb.p, w->part1.p, 0, w->part2.p);
+      BIPB_LAUNCHED(s);
+      launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part2.p, w->H.p, 1, w->st,
+                     w->blk.p, w->sysb.p, w->part1.p, 1, nullptr);
+    } else {
+      launch_chained(k_orth, nb, kBS, 0, s->stream, j, m, len, w->V.p, w->w.p, w->part.p, w->H.p, 0, w->st, w->blk.p,
+                     w->sysb.p, w->part1.p, 1, nullptr);
+    }
     BIPB_LAUNCHED(s);
     launch_chained(k_normalize, nb, kBS, 0, s->stream, j, m, w->w.p, vj + len, w->part1.p, w->H.p, w->st, w->blk.p,
                    w->sysb.p, 0, w->cs.p, w->sn.p, w->g.p, tz, lay, pre);
