@@ -92,22 +92,26 @@ def test_matvec_fp64_and_fp32(bipb, orc, name, transpose):
 
 
 def test_degenerate_media(bipb, orc):
-    """kappa = 0 (pure Coulomb kernels) against the oracle in every precision,
-    and no dielectric contrast with kappa = 0, where every kernel vanishes
+    """kappa = 0 (pure Coulomb kernels, the symmetric kernels' own form)
+    against the oracle in every precision, both directions, and no
+    dielectric contrast with kappa = 0, where every kernel vanishes
     exactly: A = I and the solve returns b after one iteration."""
     p = _ragged(3)
     rng = np.random.default_rng(8)
     U = rng.standard_normal((2, 2 * p.n))
     med0 = bipb.medium(1.0, 80.0, 0.0)
-    ref = np.stack([orc.matvec(p.centroids, p.normals, p.areas, 80.0, 0.0, u) for u in U])
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
-        for prec, variant, tol in ((bipb.FP64, 0, 1e-12), (bipb.DF64, 0, 2e-12), (bipb.FP32, 0, 2e-5),
-                                   (bipb.FP32, 7, 2e-5)):
-            s.set_variant(variant)
-            yd = torch.full_like(ud, float("nan"))
-            s.matvec(ud, yd, precision=prec, med=med0)
-            assert np.abs(yd.cpu().numpy() - ref).max() < tol * np.abs(ref).max(), (prec, variant)
+        for transpose in (False, True):
+            f = orc.matvec_t if transpose else orc.matvec
+            ref = np.stack([f(p.centroids, p.normals, p.areas, 80.0, 0.0, u) for u in U])
+            for prec, variant, tol in ((bipb.FP64, 0, 1e-12), (bipb.DF64, 0, 2e-12), (bipb.FP32, 0, 2e-5),
+                                       (bipb.FP32, 7, 2e-5), (bipb.FP32, 9, 2e-5)):
+                s.set_variant(variant)
+                yd = torch.full_like(ud, float("nan"))
+                s.matvec(ud, yd, precision=prec, transpose=transpose, med=med0)
+                err = np.abs(yd.cpu().numpy() - ref).max()
+                assert err < tol * np.abs(ref).max(), (prec, variant, transpose)
         unit = bipb.medium(1.0, 1.0, 0.0)
         for prec in (bipb.FP64, bipb.DF64, bipb.FP32):
             yd = torch.full_like(ud, float("nan"))
