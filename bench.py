@@ -53,7 +53,7 @@ PAIR_PIPE_INSTR = 39
 # DRAM bytes (read + write) per launch of the FP32 mat-vec kernel on the Kirkwood
 # workload, by variant, from one ncu capture of that variant's kernel (the
 # records and partial sums stay in L2); variants without a capture report null
-DRAM_BYTES_FP32_KIRKWOOD = {5: 1.369088e6, 9: 0.703488e6}
+DRAM_BYTES_FP32_KIRKWOOD = {5: 1.369088e6, 9: 0.702976e6}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM per clock
 FP64_LANES_PER_SM = 2    # FP64 FMA lanes per SM per clock (1.25 TFLOP/s nominal at 2.07 GHz, 152 SMs)
 
