@@ -290,23 +290,35 @@ __device__ __forceinline__ void df_mac(df& acc, df a, df b) {
 
 namespace bipb {
 
+// x + y for x, y >= 0, left unnormalised: the trailing part stays within a
+// few ulp of the leading one (no cancellation), which products and a
+// following exponent-ordered sum take as it is.
+__device__ __forceinline__ df df_add_pos_lazy(df x, df y) {
+  const df s = two_sum(x.hi, y.hi);
+  return df{s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo))};
+}
+
 // The symmetric pair of pair.cuh (sym_pair) in df64.  The four accumulators
-// are updated lazily (df_mac): renormalise them before use.
-template <bool MASK, bool TRANS>
+// are updated lazily (df_mac): renormalise them before use.  SCALED: the
+// records are in kappa-scaled units as in sym_pair (kappa r = r2 s, (w - 3)
+// s^2 = 3 (t - 1) s^2 + e; the caller rescales the sums); otherwise
+// unscaled, for any kappa >= 0.
+template <bool MASK, bool TRANS, bool SCALED>
 __device__ __forceinline__ void df_sym_pair(const df* d, const df* nt, df at, df alt, const df* ns, df as, df als,
                                             bool self, const DFConst& c, const df* tab, df& Pt, df& Qt, df& Ps,
                                             df& Qs) {
   const df r2 = df_sumsq3(d[0], d[1], d[2]);
   df s = df_rsqrt(r2);
   if (MASK && self) s = df{0.0f, 0.0f};
-  const df kr = df_mul(df_mul(r2, s), c.kappa);
+  const df kr = SCALED ? df_mul(r2, s) : df_mul(df_mul(r2, s), c.kappa);
   const df e = df_exp_neg(df_neg(kr), c, tab);
   const df ekr = df_mul(e, kr);
-  const df t = df_add(ekr, e);
+  const df t = df_add_pos_lazy(ekr, e);  // <= 1: the sum with -1 below is exponent-ordered
   const df tm1 = df_minus_one(t);
   const df s2 = df_sqr(s);
   const df s3 = df_mul(s2, s);
-  const df wm3s2 = df_mul(df_add(df_mul(ekr, kr), df_mul_f(tm1, 3.0f)), s2);
+  const df wm3s2 = SCALED ? df_add(df_mul_f(df_mul(tm1, s2), 3.0f), e)
+                          : df_mul(df_add(df_mul(ekr, kr), df_mul_f(tm1, 3.0f)), s2);
   const df ome = df_one_minus(e);
   const df et1 = df_add_f(df_mul(c.eps, t), -1.0f), te1 = df_add_f(df_mul(t, c.inveps), -1.0f);
   const df ci = df_dot3(nt[0], nt[1], nt[2], d[0], d[1], d[2]);

@@ -371,8 +371,8 @@ bool matvec_sym32(Surface* s, const SysLayout& L, const PairConst<float>& c, dou
                   int skip_stride);
 bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, double kappa, bool transpose,
                   const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride);
-bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
-                   double dphi, double dpsi, const int* skip, int skip_stride);
+bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, double kappa, bool transpose, const double* u,
+                   double* y, double dphi, double dpsi, const int* skip, int skip_stride);
 // y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)
 void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
                double dpsi, const int* skip, int skip_stride);

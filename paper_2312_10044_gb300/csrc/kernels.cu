@@ -893,7 +893,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
       matvec_df_mrhs(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
       return;
     }
-    if (s->sym_pairs && matvec_sym_df(s, L, c, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;
+    if (s->sym_pairs && matvec_sym_df(s, L, c, m.kappa, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;
     if (transpose)
       run_matvec_df<true>(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
     else

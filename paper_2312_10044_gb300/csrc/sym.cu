@@ -110,12 +110,13 @@ __device__ df* sym_exp_table() {
   return tab;
 }
 
-// df64 record, 4 float4: (x.hi, a.hi), (x.lo, a.lo), (n.hi, alpha.hi), (n.lo, alpha.lo)
-template <bool TRANS>
+// df64 record, 4 float4: (x.hi, a.hi), (x.lo, a.lo), (n.hi, alpha.hi), (n.lo, alpha.lo);
+// SCALED: positions and alpha in kappa-scaled units (df_sym_pair)
+template <bool TRANS, bool SCALED_>
 struct SymDFPolicy {
   using V4 = float4;
   using PT = double;
-  static constexpr bool SCALED = false;
+  static constexpr bool SCALED = SCALED_;
   static constexpr int RW = 4;
   static constexpr int UNROLL = 1;
   struct Elem {
@@ -141,8 +142,8 @@ struct SymDFPolicy {
   template <bool MASK>
   __device__ static void pair(const Args& g, const Elem& t, const Elem& sj, bool masked, Acc& ti, Acc& tj) {
     const df d[3] = {df_sub(t.x[0], sj.x[0]), df_sub(t.x[1], sj.x[1]), df_sub(t.x[2], sj.x[2])};
-    df_sym_pair<MASK, TRANS>(d, t.n, t.a, t.al, sj.n, sj.a, sj.al, masked, g.c, sym_exp_table(), ti.p, ti.q, tj.p,
-                             tj.q);
+    df_sym_pair<MASK, TRANS, SCALED>(d, t.n, t.a, t.al, sj.n, sj.a, sj.al, masked, g.c, sym_exp_table(), ti.p, ti.q,
+                                     tj.p, tj.q);
   }
   // the accumulators are updated lazily (df_mac): bring them back to normal form
   __device__ static void renorm(Acc& v) {
@@ -294,7 +295,7 @@ __global__ void k_pack_sym(const int4* __restrict__ lay, bool transpose, const d
 
 __global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, const double4_32a* __restrict__ tgt64,
                               const double* __restrict__ u, float4* __restrict__ rec, const int* __restrict__ skip,
-                              int skip_stride) {
+                              int skip_stride, double sigma) {
   chain_wait();
   chain_release();
   const int k = blockIdx.y;
@@ -304,8 +305,8 @@ __global__ void k_pack_sym_df(const int4* __restrict__ lay, bool transpose, cons
   const double4_32a g = tgt64[2 * (L.x + j)], v = tgt64[2 * (L.x + j) + 1];
   const double phi = u[L.z + j], psi = u[L.z + L.y + j];
   const df a = df_from_double(transpose ? phi : g.w * psi);
-  const df al = df_from_double(transpose ? psi : g.w * phi);
-  const df x0 = df_from_double(g.x), x1 = df_from_double(g.y), x2 = df_from_double(g.z);
+  const df al = df_from_double(sigma * (transpose ? psi : g.w * phi));
+  const df x0 = df_from_double(sigma * g.x), x1 = df_from_double(sigma * g.y), x2 = df_from_double(sigma * g.z);
   const df n0 = df_from_double(v.x), n1 = df_from_double(v.y), n2 = df_from_double(v.z);
   float4* o = rec + 4 * (size_t)(L.z / 2 + j);
   o[0] = make_float4(x0.hi, x1.hi, x2.hi, a.hi);
@@ -595,7 +596,7 @@ void run_sym(Surface* s, int pass_id, int kind, const SysLayout& L, const typena
   const int4* lay = s->lay_dev(L);
   if constexpr (std::is_same<typename P::PT, double>::value && std::is_same<typename P::V4, float4>::value) {
     launch_chained(k_pack_sym_df, dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream, lay, transpose, s->tgt64.p, u,
-                   recbuf.p, skip, skip_stride);
+                   recbuf.p, skip, skip_stride, sigma);
   } else {
     launch_chained(k_pack_sym<typename P::V4, typename P::PT>, dim3(blocks_of(L.max_n, 256), L.K), 256, 0, s->stream,
                    lay, transpose, s->tgt64.p, u, recbuf.p, skip, skip_stride, sigma);
@@ -689,15 +690,26 @@ bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c0, d
   return true;
 }
 
-bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
-                   double dphi, double dpsi, const int* skip, int skip_stride) {
+bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, double kappa, bool transpose, const double* u,
+                   double* y, double dphi, double dpsi, const int* skip, int skip_stride) {
   if (!sym_fits(L, 128)) return false;
-  if (transpose)
-    run_sym<SymDFPolicy<true>, 128, 1, 32, 1>(s, 0x500, kTMvDFT, L, {c}, true, s->recdf, s->part64, u, y, dphi, dpsi,
-                                           skip, skip_stride);
-  else
-    run_sym<SymDFPolicy<false>, 128, 1, 32, 1>(s, 0x600, kTMvDF, L, {c}, false, s->recdf, s->part64, u, y, dphi, dpsi,
-                                            skip, skip_stride);
+  // kappa-scaled records for kappa >= kSymKappaMin (the FP32 rule), unscaled otherwise
+  const bool scaled = kappa >= kSymKappaMin;
+#define BIPB_SYMDF_RUN(TR_, SC_)                                                                                 \
+  run_sym<SymDFPolicy<TR_, SC_>, 128, 1, 32, 1>(s, TR_ ? 0x500 : 0x600, TR_ ? kTMvDFT : kTMvDF, L, {c}, TR_,     \
+                                               s->recdf, s->part64, u, y, dphi, dpsi, skip, skip_stride, kappa)
+  if (transpose) {
+    if (scaled)
+      BIPB_SYMDF_RUN(true, true);
+    else
+      BIPB_SYMDF_RUN(true, false);
+  } else {
+    if (scaled)
+      BIPB_SYMDF_RUN(false, true);
+    else
+      BIPB_SYMDF_RUN(false, false);
+  }
+#undef BIPB_SYMDF_RUN
   return true;
 }
 
