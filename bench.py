@@ -214,6 +214,67 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_reference_configs(args):
+    """The CPU oracle on every configuration, on this host: one FP64 mat-vec
+    on all cores and on one core (rows sampled where a full one would take
+    long, scaled to N(N-1) pairs), and the oracle's GMRES(10) solve to 1e-8
+    for the Born and Kirkwood systems; the larger solves are extrapolated
+    from the mat-vec time (stated in each line)."""
+    import platform
+
+    import oracle
+    import synth
+
+    oracle.build()
+    cores = oracle.num_threads()
+    host = {"machine": platform.machine(), "cpus": os.cpu_count(), "oracle_threads": cores}
+    rng = np.random.default_rng(7)
+
+    def matvec_s(prob, threads, max_pairs):
+        """Seconds per full mat-vec, from the rows that make up about max_pairs pairs."""
+        n = prob.n
+        eps = prob.eps_out / prob.eps_in
+        u = rng.standard_normal(2 * n)
+        rows = int(min(2 * n, max(threads * 8, max_pairs // (n - 1))))
+        sel = np.sort(rng.choice(2 * n, rows, replace=False))
+        oracle.set_threads(threads)
+        try:
+            t0 = time.perf_counter()
+            oracle.matvec_rows(prob.centroids, prob.normals, prob.areas, eps, prob.kappa, u, sel)
+            el = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(cores)
+        return el * (n * (n - 1)) / (rows * (n - 1)), rows
+
+    cfgs = (("1: Born ion, level 3", synth.born_problem(level=3), True),
+            ("2: Kirkwood sphere, level 5", synth.kirkwood_problem(level=5), True),
+            ("3: protein-like, level 6", synth.protein_like_problem(), False),
+            ("5: displaced sphere, level 7", synth.adjoint_problem(), False))
+    per_solve_mv = None
+    for name, prob, full in cfgs:
+        n = prob.n
+        t_all, r_all = matvec_s(prob, cores, 2.0e9 * cores / 16)
+        t_one, r_one = matvec_s(prob, 1, 1.2e8)
+        line = {"impl": "reference", "mode": "configs", "config": name, "n": n, "host": host,
+                "matvec_s_all_cores": t_all, "matvec_s_one_core": t_one,
+                "matvec_sample_rows": {"all_cores": r_all, "one_core": r_one, "of": 2 * n},
+                "gpairs_all_cores": n * (n - 1) / t_all / 1e9,
+                "pairs_per_s_per_core": n * (n - 1) / t_one}
+        if full:
+            t0 = time.perf_counter()
+            sol = oracle.solve(prob, method="gmres", tol=1e-8, restart=10)
+            line["solve_s"] = time.perf_counter() - t0
+            line["solve"] = f"measured: oracle GMRES(10) to 1e-8, {sol.info.get('iters')} iterations"
+            per_solve_mv = sol.info.get("iters", 0) + 1
+        else:
+            mv = per_solve_mv or 29
+            line["solve_s"] = mv * t_all
+            line["solve"] = f"extrapolated: {mv} mat-vecs (the Kirkwood solve's count) x the all-core mat-vec"
+            if name.startswith("3"):
+                line["solve_s_64_rhs"] = 64 * mv * t_all
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_matvec_only(args):
     """W + K single mat-vecs of one precision on the workload (a small, fixed launch sequence)."""
@@ -506,7 +567,7 @@ def run_peaks(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference_configs(args) if args.mode == "configs" else run_reference(args)
     if args.mode == "configs":
         return run_configs(args)
     if args.mode == "peaks":
