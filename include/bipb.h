@@ -88,18 +88,23 @@ typedef struct {
 } bipb_solve_params;
 
 /*
- * Left preconditioning of the Krylov solves (Sec. 2.2.4: GMRES on
- * M^-1 A x = M^-1 b with M the block diagonal of A over leaves of elements).
+ * Preconditioning of the Krylov solves by the block diagonal M of A over
+ * leaves of elements (Sec. 2.2.4), applied on the right: GMRES on
+ * A M^-1 y = b, u = M^-1 y, so that it minimises the true residual.
+ * (The paper writes the left form M^-1 A u = M^-1 b; both have the same
+ * preconditioned spectrum, and the right form keeps the residual that the
+ * stopping tests and the refinement read unscaled.)
  * BIPB_PRECOND_SELF takes each element as its own leaf: with the self pair
  * omitted its 2 x 2 block is diag(1/2 (1 + eps), 1/2 (1 + 1/eps)), so M^-1
- * rescales the phi and psi rows and costs nothing per iteration (it is
- * applied inside the first Gram-Schmidt kernel).  On smooth molecular
- * surfaces it cuts GMRES(10) to 1e-8 from about 27 to about 9 iterations,
- * as many as leaves of 16 to 64 elements do.  The solve still stops on the
- * true residual ||b - A u|| / ||b|| (mixed modes: the high-precision
- * refinement residual; BIPB_FP64 / BIPB_DF64: a restart on the true
- * residual until it meets tol).  The paper's GPU pipeline runs without
- * preconditioning (BIPB_PRECOND_NONE).
+ * rescales the phi and psi rows and costs nothing per iteration (the
+ * normalisation and restart kernels write the scaled input of the next
+ * mat-vec, and the solution update applies it to the correction).  On
+ * smooth molecular surfaces it cuts GMRES(10) to 1e-8 from about 27 to
+ * about 10 iterations.  The solve still stops on the true residual
+ * ||b - A u|| / ||b|| (mixed modes: the high-precision refinement
+ * residual; BIPB_FP64 / BIPB_DF64: a restart on the true residual until it
+ * meets tol).  The paper's GPU pipeline runs without preconditioning
+ * (BIPB_PRECOND_NONE).
  */
 typedef enum { BIPB_PRECOND_NONE = 0, BIPB_PRECOND_SELF = 1 } bipb_precond;
 
