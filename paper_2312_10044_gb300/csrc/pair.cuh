@@ -31,7 +31,7 @@
 
 namespace bipb {
 
-constexpr float kSMaxF = 1.0e6f;   // 1/r clamp: pairs closer than 1e-6 A act as self pairs
+constexpr float kSMaxF = 1.0e6f;   // 1/r is capped at its value at 1e-6 A (an overflow guard, not a model)
 constexpr double kSMaxD = 1.0e6;
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kCoulomb = 332.0716;           // Sec. 2.1: phi * 332.0716 -> kcal/mol/e

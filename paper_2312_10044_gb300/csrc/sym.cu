@@ -625,7 +625,7 @@ template <typename T>
 bool sym_form(double kappa, PairConst<T>& c, bool& laplace) {
   laplace = kappa == 0.0;
   if (!laplace && kappa < kSymKappaMin) return false;
-  c.smax = (T)(laplace ? kSMaxD : kSMaxD / kappa);  // pairs closer than 1e-6 A act as self pairs
+  c.smax = (T)(laplace ? kSMaxD : kSMaxD / kappa);  // the 1/r cap at 1e-6 A, in the units of the records
   return true;
 }
 
