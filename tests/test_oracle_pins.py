@@ -259,6 +259,74 @@ def test_kirkwood_convergence_across_levels(orc):
     assert errs[2] < 0.02
 
 
+# ------------------------------------------------------------------ solute dielectric eps_in != 1
+# S1 and S2 carry 1/eps_in (Sec. 2.2.1), and so do the source-column terms of
+# the gradient.  With eps_in = 1 that factor is invisible; these pins fix it:
+# without it b, and with it u and E, come out eps_in times too large.
+@pytest.mark.parametrize("eps_in", [2.0, 4.0])
+def test_born_convergence_with_solute_dielectric(orc, eps_in):
+    """Born energy and surface values at eps_in = 2 and 4 converge to the
+    closed form, whose reaction term carries 1/eps_in and whose inner normal
+    derivative is -q / (eps_in a^2) (Gauss's law in the solute)."""
+    exact = cf.born_energy(1.0, 2.0, eps_in, EPS_OUT, KAPPA)
+    phi_ex, dphi_ex = cf.born_surface(1.0, 2.0, eps_in, EPS_OUT, KAPPA)
+    errs, perr, derr = [], [], []
+    for lev in (1, 2, 3):
+        s = orc.solve(synth.born_problem(level=lev, eps_in=eps_in), method="direct")
+        errs.append(abs(s.energy_kcal / exact - 1))
+        phi, dphi = s.surface_potential()
+        perr.append(np.abs(phi / phi_ex - 1).max())
+        derr.append(np.abs(dphi / dphi_ex - 1).max())
+    assert errs[2] < 0.03 and perr[2] < 0.03 and derr[2] < 0.03
+    for e in (errs, perr, derr):
+        assert e[0] > 2.5 * e[1] > 2.5 * 2.5 * e[2] * 0.9
+
+
+def test_kirkwood_convergence_with_solute_dielectric(orc):
+    """Kirkwood sphere with eps_in = 2: the series (every order carries
+    1/eps_in) is approached level by level."""
+    p0 = synth.kirkwood_problem(level=2)
+    exact = cf.kirkwood_energy(p0.charge_pos, p0.q[0], 20.0, 2.0, EPS_OUT, KAPPA)
+    errs = []
+    for lev in (2, 3, 4):
+        p = synth.kirkwood_problem(level=lev)
+        p.eps_in = 2.0
+        s = orc.solve(p, method="gmres", tol=1e-10, max_iter=300)
+        assert s.info["converged"]
+        errs.append(abs(s.energy_kcal / exact - 1))
+    assert errs[0] > 2.5 * errs[1] and errs[1] > 2.5 * errs[2]
+    assert errs[2] < 0.02
+
+
+def test_gradient_matches_finite_differences_with_solute_dielectric(orc):
+    """dE/dq and dE/dy at eps_in = 2 against central differences of solved
+    energies: the adjoint's source-column term must carry 1/eps_in."""
+    def prob():
+        p = synth.kirkwood_problem(level=2, radius=8.0, n_charges=3, charge_radius=5.0)
+        p.eps_in = 2.0
+        return p
+
+    p = prob()
+    e, dq, dy = orc.energy_gradient(p, method="direct")
+    h = 1e-4
+    for k in range(3):
+        for m in range(3):
+            pp = prob()
+            pp.charge_pos = p.charge_pos.copy()
+            pp.charge_pos[k, m] += h
+            ep = orc.solve(pp, method="direct").energy_kcal
+            pp.charge_pos[k, m] -= 2 * h
+            em = orc.solve(pp, method="direct").energy_kcal
+            assert dy[k, m] == pytest.approx((ep - em) / (2 * h), rel=2e-6, abs=1e-7 * abs(e))
+        pq = prob()
+        pq.q = p.q.copy()
+        pq.q[0, k] += 0.01
+        ep = orc.solve(pq, method="direct").energy_kcal
+        pq.q[0, k] -= 0.02
+        em = orc.solve(pq, method="direct").energy_kcal
+        assert dq[k] == pytest.approx((ep - em) / 0.02, rel=1e-9)
+
+
 # ------------------------------------------------------------------ invariants of E
 def test_energy_quadratic_in_charges(orc):
     p = synth.kirkwood_problem(level=2, n_charges=6)
