@@ -45,11 +45,25 @@ METRIC = "BIE matvec Gpairs/s; GMRES solve time at 1e-8 rel. residual, mixed vs 
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# Algorithmic work per ordered pair of the mat-vec: flops of the pair formula
-# with the source's area and values folded into its record (an FMA counts 2)
-# and the FP32/FP64-pipe instructions of that formula.
-PAIR_FLOPS = 56
-PAIR_PIPE_INSTR = 39
+# Algorithmic work per ordered pair of the mat-vec (the unit of the roofline):
+# the pair of Eqs. 5-6 written out term by term (d, r^2, r, s^2 and s^3, the
+# exponent argument, c_i, c_j, c_ij, t and w, K1..K4, four accumulations) is
+# about 43 FP32-pipe instructions, about 20 of them FMAs, i.e. 63 flops,
+# plus 2 MUFU operations.  The kernels execute fewer (the symmetric kernel
+# about 23 FP32-pipe instructions per ordered pair, since it evaluates each
+# unordered pair once for both rows), so achieved / peak can exceed the pipe's
+# busy fraction; the ncu FMA-pipe fraction is reported beside it.
+PAIR_FLOPS = 63
+PAIR_PIPE_INSTR = 43
+# Measured FP32 FFMA throughput (bench.py --mode peaks, the microbenchmark
+# microbench/alu_peaks.cu): 3.65e13 lane-ops/s on 152 SMs at a median SM clock
+# of 1987 MHz, i.e. 120.9 FMA lanes per SM per clock of the nominal 128.  The
+# roofline's peak is this per-clock rate at the SM clock sampled in the timed
+# region (2 flop per FMA).
+FFMA_LANES_PER_SM_MEASURED = 3.65e13 / (152 * 1987e6)
+# ncu FMA-pipe busy fraction of the FP32 mat-vec pair kernel (symmetric variant
+# 9) on the Kirkwood workload, from profiles/k_sym_fp32_kirkwood.md
+NCU_FMA_PIPE_FRAC_FP32_KIRKWOOD = {9: 0.691}
 # DRAM bytes (read + write) per launch of the FP32 mat-vec kernel on the Kirkwood
 # workload, by variant, from one ncu capture of that variant's kernel (the
 # records and partial sums stay in L2); variants without a capture report null
@@ -73,6 +87,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
+    ap.add_argument("--no-config3", action="store_true", help="skip the protein-like (N = 81920) solves")
     ap.add_argument("--precond", default="none", choices=["none", "self"],
                     help="preconditioner of the step's solve (none: the paper's GPU pipeline; self: element "
                          "self blocks of Sec. 2.2.4)")
@@ -535,6 +550,34 @@ def config5_central_differences(bipb, torch):
     return res
 
 
+def config3_solves(bipb, torch):
+    """The largest single-RHS configuration beside the headline: the
+    protein-like surface (displaced icosphere level 6, N = 81920, 2000
+    charges), source + solve to 1e-8 + energy, each solve timed once after an
+    untimed run of the same call: mixed (FP32 Krylov, double-float residual),
+    mixed with an FP64 residual, plain FP64 GMRES, and the mixed solve with
+    the element self-block preconditioner."""
+    import synth
+
+    p = synth.protein_like_problem()
+    out = {"config3_workload": "protein-like surface: displaced icosphere level 6 (N=81920), R=25 A, 2000 charges, "
+                               "eps 1/80, kappa 0.1257/A, tol 1e-8"}
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        for key, prec, pre in (("mixed", bipb.MIXED_DF64, bipb.PRECOND_NONE),
+                               ("mixed_fp64_residual", bipb.MIXED, bipb.PRECOND_NONE),
+                               ("fp64", bipb.FP64, bipb.PRECOND_NONE),
+                               ("mixed_precond_self", bipb.MIXED_DF64, bipb.PRECOND_SELF)):
+            prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, restart=10, precision=prec,
+                                    precond=pre)
+            if key != "fp64":  # the FP64 solve takes seconds: one run, no warm-up
+                s.solve(prm)
+            ms, info = _timed(lambda: (s.solve(prm)[0], s.energy()[0]), torch)
+            out[f"config3_solve_ms_{key}"] = ms
+            out[f"config3_{key}_info"] = dict(info[0], energy_kcal=info[1])
+    return out
+
+
 def run_peaks(args):
     """Measured throughput of the FP32 FFMA, FP64 DFMA and MUFU pipes (the
     microbenchmark microbench/alu_peaks.cu, built here with nvcc), against the
@@ -650,19 +693,33 @@ def main():
     lanes = FP64_LANES_PER_SM if dom.startswith("matvec64") else FP32_LANES_PER_SM
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     pairs_launch = n * (n - 1)
+    fp32 = lanes == FP32_LANES_PER_SM
+    lanes_meas = FFMA_LANES_PER_SM_MEASURED if fp32 else lanes
     achieved = pairs_launch * PAIR_FLOPS / (avg_ms / 1e3) / 1e12
-    peak = nsm * lanes * 2 * f_mhz * 1e6 / 1e12
-    pipe_frac = pairs_launch * PAIR_PIPE_INSTR / (avg_ms / 1e3) / (nsm * lanes * f_mhz * 1e6)
+    peak = nsm * lanes_meas * 2 * f_mhz * 1e6 / 1e12
+    peak_nominal = nsm * lanes * 2 * f_mhz * 1e6 / 1e12
+    instr_frac = pairs_launch * PAIR_PIPE_INSTR / (avg_ms / 1e3) / (nsm * lanes_meas * f_mhz * 1e6)
     traffic = None
     if dom == "matvec32" and args.workload == "kirkwood":
         traffic = DRAM_BYTES_FP32_KIRKWOOD.get(variant)
+    ncu_pipe = NCU_FMA_PIPE_FRAC_FP32_KIRKWOOD.get(variant) if dom == "matvec32" and args.workload == "kirkwood" \
+        else None
     roofline = {"bound": "alu", "kernel": f"{dom} pair kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "pipe": "fp32" if lanes == FP32_LANES_PER_SM else "fp64", "ordered_form_pipe_frac": pipe_frac,
-                "pipe_note": f"{PAIR_PIPE_INSTR} pipe instructions per ordered pair (the ordered formula) over the "
-                             "pipe's issue peak; the symmetric kernel issues fewer per pair, so this can exceed 1",
-                "peak_basis": f"{nsm} SMs x {lanes} {('FP32' if lanes == 128 else 'FP64')} FMA lanes x 2 flop x "
-                              f"{f_mhz:.0f} MHz (median SM clock sampled in the timed region)",
+                "pipe": "fp32" if fp32 else "fp64",
+                "definition": f"achieved = {PAIR_FLOPS} flops x N(N-1) ordered pairs per launch / mean launch time; "
+                              f"peak = {nsm} SMs x {lanes_meas:.1f} measured {'FFMA' if fp32 else 'DFMA'} lanes per "
+                              f"SM per clock x 2 flop x {f_mhz:.0f} MHz (median SM clock sampled in the timed "
+                              "region); the symmetric kernel evaluates each unordered pair once for both rows, so "
+                              "it executes fewer instructions than the algorithmic count and frac can exceed 1",
+                "peak_nominal": peak_nominal, "frac_of_nominal": achieved / peak_nominal,
+                "instr_frac": instr_frac,
+                "instr_note": f"{PAIR_PIPE_INSTR} FP32-pipe instructions per ordered pair over the measured issue "
+                              "peak (can exceed 1 for the same reason)",
+                "ncu_fma_pipe_frac": ncu_pipe,
+                "ncu_note": "FMA-pipe busy fraction of this kernel from one ncu capture "
+                            "(profiles/k_sym_fp32_kirkwood.md): how busy the pipe actually is",
+                "pairs_per_launch": pairs_launch, "sms": nsm, "sm_mhz": f_mhz,
                 "avg_launch_ms": avg_ms, "launches": cnt, "effective_launches": min(cnt, eff),
                 "kernel_ms": {k: v[1] for k, v in timers.items() if v[0]},
                 "kernel_launches": {k: v[0] for k, v in timers.items() if v[0]}}
@@ -727,6 +784,8 @@ def main():
     extra["solve_ms_mixed"] = total_ms / args.steps
     extra["mixed_info"] = info0
     extra["energy_kcal"] = infos[-1][1]
+    if args.workload == "kirkwood" and not args.no_config3:
+        extra.update(config3_solves(bipb, torch))
 
     # ---- end to end through the host API: geometry + charges from pinned host
     # memory, create, solve, energy back to the host, destroy

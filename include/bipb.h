@@ -77,7 +77,7 @@ typedef struct {
 typedef struct {
   bipb_medium medium;
   double tol;          /* target ||b - A u||_2 / ||b||_2, 0 < tol < 1 */
-  int restart;         /* GMRES restart length m, 1..64 (10 if 0) */
+  int restart;         /* GMRES restart length m, 1..200 (10 if 0) */
   int max_iter;        /* cap on GMRES iterations summed over restarts and refinement steps (1000 if 0) */
   int precision;       /* bipb_precision: BIPB_FP64, BIPB_MIXED, BIPB_DF64, BIPB_MIXED_DF64 or BIPB_MIXED_TF32 */
   int inner_max_iter;  /* MIXED: cap on inner iterations per refinement step (200 if 0) */
@@ -343,8 +343,10 @@ bipb_status bipb_launch_count(bipb_surface s, int64_t* launches);
  * cudaFree or other allocating routine: its scratch (about 10 MiB) is one
  * statically sized device array that every GPU loading the library holds
  * until the process exits.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  Every call shares the one
+ * array's device address (cudaGetSymbolAddress) with the device current and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture.  A cudaDeviceReset after the first call on a device is not
+ * supported: the kept address would then be stale.  Every call shares the one
  * array, so calls that overlap on the GPU (concurrent streams, or several
  * host threads) race and corrupt each other's results: serialise them.
  * Errors are reported through the status and bipb_last_error().

@@ -61,6 +61,7 @@ def lib():
         L.orc_matvec.argtypes = [I, P, P, P, D, D, P, P]
         L.orc_matvec_t.argtypes = [I, P, P, P, D, D, P, P]
         L.orc_matvec_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
+        L.orc_matvec_t_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
         L.orc_assemble.argtypes = [I, P, P, P, D, D, P]
         L.orc_gesv.argtypes = [I, P, I, P]
         L.orc_gesv.restype = ctypes.c_int
@@ -136,6 +137,16 @@ def matvec_rows(x, nrm, area, eps, kappa, u, rows):
     out = np.zeros(rows.shape[0])
     lib().orc_matvec_rows(x.shape[0], _p(x), _p(nrm), _p(area), eps, kappa, _p(u), rows.shape[0],
                           rows.ctypes.data_as(ctypes.c_void_p), _p(out))
+    return out
+
+
+def matvec_t_rows(x, nrm, area, eps, kappa, w, rows):
+    """Rows ``rows`` (indices into [0, 2N)) of A^T w, each summed on its own."""
+    x, nrm, area, w = _c(x), _c(nrm), _c(area), _c(w)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(rows.shape[0])
+    lib().orc_matvec_t_rows(x.shape[0], _p(x), _p(nrm), _p(area), eps, kappa, _p(w), rows.shape[0],
+                            rows.ctypes.data_as(ctypes.c_void_p), _p(out))
     return out
 
 

@@ -199,6 +199,26 @@ void orc_matvec_t(int64_t n, const double* x, const double* nrm, const double* a
   }
 }
 
+/* Selected rows of A^T w: out[r] = row rows[r] of orc_matvec_t (0 <= rows[r] < 2n). */
+void orc_matvec_t_rows(int64_t n, const double* x, const double* nrm, const double* area, double eps,
+                       double kappa, const double* w, int64_t nrows, const int64_t* rows, double* out) {
+  const double* wp = w;
+  const double* ws = w + n;
+  int64_t r;
+#pragma omp parallel for schedule(static)
+  for (r = 0; r < nrows; ++r) {
+    int64_t row = rows[r];
+    int64_t j = row < n ? row : row - n;
+    double z = 0.0, K[4];
+    for (int64_t i = 0; i < n; ++i) {
+      if (i == j) continue;
+      orc_kernels(x + 3 * i, nrm + 3 * i, x + 3 * j, nrm + 3 * j, eps, kappa, K);
+      z += row < n ? K[1] * wp[i] + K[3] * ws[i] : K[0] * wp[i] + K[2] * ws[i];
+    }
+    out[r] = row < n ? 0.5 * (1.0 + eps) * wp[j] - area[j] * z : 0.5 * (1.0 + 1.0 / eps) * ws[j] - area[j] * z;
+  }
+}
+
 /* Dense A (2n x 2n, row-major), same entries as orc_matvec. */
 void orc_assemble(int64_t n, const double* x, const double* nrm, const double* area, double eps,
                   double kappa, double* A) {

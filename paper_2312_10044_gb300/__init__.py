@@ -432,14 +432,27 @@ def matvec32_static(centroids, normals, areas, u, y, med=None, stream=None):
     static device array, so no cudaMalloc happens.  Calls that overlap on the
     GPU share that array and race; serialise them.
     """
-    m = med if med is not None else medium()
-    n = centroids.numel() // 3
-    if stream is None:
-        import torch
+    import torch
 
+    m = med if med is not None else medium()
+    # sizes first: the kernels trust them and would read or write past the end
+    n, rem = divmod(centroids.numel(), 3)
+    if rem or normals.numel() != 3 * n or areas.numel() != n or u.numel() != 2 * n or y.numel() != 2 * n:
+        raise ValueError(f"matvec32_static: expected centroids and normals of 3n, areas of n, u and y of 2n "
+                         f"values; got {centroids.numel()}, {normals.numel()}, {areas.numel()}, {u.numel()}, "
+                         f"{y.numel()}")
+    tensors = (centroids, normals, areas, u, y)
+    if not all(isinstance(t, torch.Tensor) and t.is_cuda for t in tensors):
+        raise ValueError("matvec32_static: every argument must be a CUDA tensor")
+    dev = torch.cuda.current_device()
+    if any(t.device.index != dev for t in tensors):
+        raise ValueError(f"matvec32_static: every tensor must be on the current device cuda:{dev} "
+                         "(the scratch array used is that device's)")
+    if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    _check(load_library().bipb_matvec32_static(n, _dp(centroids), _dp(normals), _dp(areas), ctypes.byref(m),
-                                               _dp(u), _dp(y), ctypes.c_void_p(stream)))
+    ptrs = [_dp(t) for t in tensors]
+    _check(load_library().bipb_matvec32_static(n, ptrs[0], ptrs[1], ptrs[2], ctypes.byref(m), ptrs[3], ptrs[4],
+                                               ctypes.c_void_p(stream)))
     return y
 
 

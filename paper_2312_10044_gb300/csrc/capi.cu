@@ -74,7 +74,7 @@ void validate_params(const bipb_solve_params* p) {
   BIPB_REQUIRE(p != nullptr, "params is NULL");
   validate_medium(&p->medium);
   BIPB_REQUIRE(std::isfinite(p->tol) && p->tol > 0 && p->tol < 1, "tol must lie in (0, 1)");
-  BIPB_REQUIRE(p->restart >= 0 && p->restart <= kMaxRestart, "restart must lie in [1, 64] (0 = 10)");
+  BIPB_REQUIRE(p->restart >= 0 && p->restart <= kMaxRestart, "restart must lie in [1, 200] (0 = 10)");
   BIPB_REQUIRE(p->max_iter >= 0, "max_iter must be >= 0 (0 = 1000)");
   BIPB_REQUIRE(p->precision == BIPB_FP64 || p->precision == BIPB_MIXED || p->precision == BIPB_DF64 ||
                    p->precision == BIPB_MIXED_DF64 || p->precision == BIPB_MIXED_TF32,

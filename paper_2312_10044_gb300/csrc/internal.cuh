@@ -195,7 +195,7 @@ struct ItemPlan {
 constexpr int kNumMv32Variants = 10;
 constexpr int kFirstSymVariant = 7;
 
-constexpr int kMaxRestart = 64;
+constexpr int kMaxRestart = 200;
 
 // Per-kernel CUDA-event timing of the pair kernels (off by default).
 enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTMvDF, kTMvDFT, kTMvTC,

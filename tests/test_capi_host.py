@@ -108,3 +108,21 @@ def test_solve_params_layout_matches_header(bipb):
     # medium (3 doubles) + tol + 4 ints + inner_tol + pointer + precond + reserved
     assert ctypes.sizeof(bipb.bipb_solve_params) == 3 * 8 + 8 + 4 * 4 + 8 + 8 + 4 + 4
     assert ctypes.sizeof(bipb.bipb_solve_info) == 6 * 4 + 2 * 8
+
+
+def test_static_matvec_binding_rejects_mismatched_sizes(bipb):
+    """The allocation-free mat-vec trusts its sizes on the device, so the
+    binding checks them (and the device) before any call into the library:
+    CPU tensors stand in here, and every mismatch raises ValueError first."""
+    torch = pytest.importorskip("torch")
+    n = 10
+    z = lambda k: torch.zeros(k, dtype=torch.float64)  # noqa: E731
+    good = dict(centroids=z(3 * n), normals=z(3 * n), areas=z(n), u=z(2 * n), y=z(2 * n))
+    bad = [dict(good, centroids=z(3 * n + 1)), dict(good, normals=z(3 * n - 3)), dict(good, areas=z(n + 1)),
+           dict(good, u=z(2 * n - 1)), dict(good, y=z(4 * n))]
+    for kw in bad:
+        with pytest.raises(ValueError, match="expected centroids"):
+            bipb.matvec32_static(**kw)
+    # right sizes but not on a CUDA device: rejected before the library call as well
+    with pytest.raises(ValueError, match="CUDA"):
+        bipb.matvec32_static(**good)

@@ -1,0 +1,136 @@
+"""The benchmarked configurations checked against the oracle at their own sizes.
+
+* Kirkwood sphere, icosphere level 5 (N = 20480, the benchmark step): the
+  oracle's GMRES solved to 1e-12 against the FP64 solve (1e-10) and the two
+  mixed solves (1e-7), element by element; the energy also against the
+  Kirkwood series (discretisation error).
+* Protein-like surface, level 6 (N = 81920): after the mixed solve to 1e-8,
+  the true residual b - A u recomputed by the oracle in FP64 on 256 sampled
+  rows agrees with the residual the library reports.
+* The same surface with the split-TF32 tensor-core mat-vec (the batched
+  configuration's Krylov operator) against the oracle on sampled rows, for
+  random and smooth right-hand sides.
+
+The oracle's level-5 solve takes about half a minute on 16 cores; these
+tests are GPU tests because the library side needs the device.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import closed_forms as cf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def bipb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_10044_gb300.build import build
+
+    build()
+    import paper_2312_10044_gb300 as b
+
+    b.load_library()
+    return b
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def kirkwood5(orc):
+    p = synth.kirkwood_problem()  # level 5, R = 20 A, 50 charges
+    assert p.n == 20480
+    ref = orc.solve(p, method="gmres", tol=1e-12, max_iter=600)
+    assert ref.info["converged"]
+    return p, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_df64"])
+def test_kirkwood_level5_solve_matches_oracle(bipb, kirkwood5, prec):
+    """Reading P1(ii)/(iii): FP64 to 1e-12 within 1e-10, mixed to 1e-8 within
+    1e-7, in the energy and in phi and dphi/dnu on every element."""
+    p, ref = kirkwood5
+    phi_ref, dphi_ref = ref.surface_potential()
+    P = {"fp64": bipb.FP64, "mixed": bipb.MIXED, "mixed_df64": bipb.MIXED_DF64}[prec]
+    tol = 1e-12 if prec == "fp64" else 1e-8
+    rt = 1e-10 if prec == "fp64" else 1e-7
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=tol, precision=P)[0]
+        e = s.energy()[0]
+        phi, dphi = s.surface_potential()
+    assert info["converged"] and info["rel_residual"] <= tol
+    assert e == pytest.approx(ref.energy_kcal, rel=rt)
+    for a, r in ((phi[0], phi_ref), (dphi[0], dphi_ref)):
+        err = np.abs(a - r).max() / np.abs(r).max()
+        assert err < rt, err
+
+
+def test_kirkwood_level5_energy_vs_series(kirkwood5):
+    """The discretisation error of the level-5 system against the Kirkwood
+    series (l <= 60): below the 0.69 % of level 4."""
+    p, ref = kirkwood5
+    exact = cf.kirkwood_energy(p.charge_pos, p.q[0], 20.0, p.eps_in, p.eps_out, p.kappa)
+    err = abs(ref.energy_kcal / exact - 1)
+    assert err < 0.004, err
+
+
+def test_protein_like_mixed_solve_true_residual_on_sampled_rows(bipb, orc):
+    """Level 6 (N = 81920, 2000 charges): the mixed double-float solve to 1e-8.
+    The oracle recomputes b - A u in FP64 on 256 sampled rows; their RMS must
+    not exceed twice the RMS that a residual of 1e-8 ||b|| would have."""
+    p = synth.protein_like_problem()
+    assert p.n == 81920
+    eps = p.eps_out / p.eps_in
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-8,
+                       precision=bipb.MIXED_DF64)[0]
+        phi, dphi = s.surface_potential()
+    assert info["converged"] and info["rel_residual"] <= 1e-8
+    u = np.concatenate([phi[0], dphi[0]]) / bipb.KCAL
+    b = orc.source(p.centroids, p.normals, p.charge_pos, p.q[0], p.eps_in)
+    rows = np.sort(np.random.default_rng(60).choice(2 * p.n, 256, replace=False))
+    r = b[rows] - orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows)
+    rms = np.sqrt(np.mean(r * r))
+    bound = 2e-8 * np.linalg.norm(b) / np.sqrt(2 * p.n)
+    assert rms <= bound, (rms, bound, info["rel_residual"])
+
+
+def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
+    """Split-TF32 tensor-core mat-vec at N = 81920 (about 5000 source chunks per
+    target tile), two random and two smooth right-hand sides, on 64 sampled
+    rows: the FP32 mat-vec's bound on the whole output (2e-5 of the largest
+    value), and on the off-diagonal sum alone no worse than twice the
+    CUDA-core FP32 mat-vec's error on the same rows."""
+    p = synth.protein_like_problem()
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(61)
+    x = p.centroids / 25.0
+    smooth = [np.concatenate([1.0 + 0.3 * x[:, 2], 0.5 - 0.2 * x[:, 0]]),
+              np.concatenate([np.cos(2.0 * x[:, 0]) * x[:, 1], 1.0 + x[:, 2] ** 2])]
+    U = np.stack([rng.standard_normal(2 * p.n), rng.standard_normal(2 * p.n)] + smooth)
+    rows = np.sort(rng.choice(2 * p.n, 64, replace=False))
+    diag = np.where(rows < p.n, 0.5 * (1 + eps), 0.5 * (1 + 1 / eps))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        ytc, y32 = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
+        s.matvec(ud, ytc, precision=bipb.TF32, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
+        s.matvec(ud, y32, precision=bipb.FP32, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
+        Ytc, Y32 = ytc.cpu().numpy(), y32.cpu().numpy()
+    for v in range(U.shape[0]):
+        ref = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
+        assert np.all(np.isfinite(Ytc[v]))
+        err = np.abs(Ytc[v][rows] - ref).max() / np.abs(ref).max()
+        assert err < 2e-5, (v, err)
+        off_ref = ref - diag * U[v][rows]
+        e_tc = np.sqrt(np.mean((Ytc[v][rows] - ref) ** 2))
+        e_32 = np.sqrt(np.mean((Y32[v][rows] - ref) ** 2))
+        scale = np.sqrt(np.mean(off_ref ** 2))
+        assert e_tc <= 2 * e_32 + 1e-7 * scale, (v, e_tc / scale, e_32 / scale)

@@ -348,26 +348,117 @@ def test_warm_start_from_solution_needs_no_iterations(bipb):
 
 # ---------------------------------------------------------------- full-size sampled checks
 @pytest.mark.parametrize("cfg", ["kirkwood", "protein_like", "adjoint"])
-def test_full_size_matvec_sampled_rows(bipb, orc, cfg):
+@pytest.mark.parametrize("transpose", [False, True])
+def test_full_size_matvec_sampled_rows(bipb, orc, cfg, transpose):
     """The benchmark's mat-vec launch at full size (up to level 7, N = 327680,
-    where the symmetric work list spans 640 tile rows), checked on sampled rows."""
+    where the symmetric work list spans 640 tile rows), forward and
+    transposed, checked on sampled rows."""
     p = synth.problem_by_name(cfg)
     eps = p.eps_out / p.eps_in
     u = np.random.default_rng(9).standard_normal(2 * p.n)
     rows = np.sort(np.random.default_rng(10).choice(2 * p.n, 48, replace=False))
     rows = np.concatenate([rows, [0, p.n - 1, p.n, 2 * p.n - 1]])
-    ref = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows)
+    f = orc.matvec_t_rows if transpose else orc.matvec_rows
+    ref = f(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows)
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(u)
         y64, y32, ydf = torch.empty_like(ud), torch.empty_like(ud), torch.empty_like(ud)
-        s.matvec(ud, y64, precision=bipb.FP64, med=_med(bipb, p))
-        s.matvec(ud, y32, precision=bipb.FP32, med=_med(bipb, p))
-        s.matvec(ud, ydf, precision=bipb.DF64, med=_med(bipb, p))
+        s.matvec(ud, y64, precision=bipb.FP64, transpose=transpose, med=_med(bipb, p))
+        s.matvec(ud, y32, precision=bipb.FP32, transpose=transpose, med=_med(bipb, p))
+        s.matvec(ud, ydf, precision=bipb.DF64, transpose=transpose, med=_med(bipb, p))
         a64, a32, adf = y64.cpu().numpy(), y32.cpu().numpy(), ydf.cpu().numpy()
     scale = np.abs(ref).max()
     np.testing.assert_allclose(a64[rows], ref, rtol=0, atol=1e-12 * scale)
     np.testing.assert_allclose(adf[rows], ref, rtol=0, atol=2e-12 * scale)
     assert np.abs(a32[rows] - ref).max() < 2e-5 * scale
+
+
+# ---------------------------------------------------------------- GMRES iterates (reading P1(i))
+@pytest.mark.parametrize("name", ["born_l3", "kirkwood_l4"])
+def test_gmres_iterates_match_oracle_at_equal_iteration_count(bipb, orc, name):
+    """At equal iteration count k the FP64 GMRES(10) iterate is the same Krylov
+    minimiser on both sides (CGS2 here, modified Gram-Schmidt in the oracle;
+    Sec. 2.2.2): stopped after k = 5, 10 and 17 iterations (inside the first
+    cycle, at the restart, inside the second), the iterates agree to 1e-10
+    and so do the true residuals they leave."""
+    p = synth.born_problem(level=3) if name == "born_l3" else synth.kirkwood_problem(level=4)
+    eps = p.eps_out / p.eps_in
+    b = orc.source(p.centroids, p.normals, p.charge_pos, p.q[0], p.eps_in)
+    A = lambda v: orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, v)  # noqa: E731
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        for k in (5, 10, 17):
+            x_ref, info_ref = orc.gmres(A, b, tol=1e-15, restart=10, max_iter=k)
+            assert info_ref["iters"] == k and not info_ref["converged"]
+            info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-15, max_iter=k,
+                           precision=bipb.FP64, raise_on_not_converged=False)[0]
+            assert info["iters"] == k and not info["converged"]
+            phi, dphi = s.surface_potential()
+            x = np.concatenate([phi[0], dphi[0]]) / bipb.KCAL
+            assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-10, k
+            # the residual left is small; x differs from x_ref by rounding only
+            assert info["rel_residual"] == pytest.approx(info_ref["rel_residual"], rel=1e-6, abs=1e-12), k
+
+
+def test_long_restart_matches_oracle(bipb, orc):
+    """GMRES(m) with m = 150 (the restart length may lie in [1, 200]): inside
+    one long cycle, the iterates after k = 25 and 40 steps agree with the
+    oracle's GMRES(150) to 1e-10 (tol 1e-300: neither side stops early)."""
+    p = synth.kirkwood_problem(level=3)
+    eps = p.eps_out / p.eps_in
+    b = orc.source(p.centroids, p.normals, p.charge_pos, p.q[0], p.eps_in)
+    A = lambda v: orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, v)  # noqa: E731
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        for k in (25, 40):
+            x_ref, _ = orc.gmres(A, b, tol=1e-300, restart=150, max_iter=k)
+            info = s.solve(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-300, max_iter=k, restart=150,
+                           precision=bipb.FP64, raise_on_not_converged=False)[0]
+            assert info["iters"] == k
+            phi, dphi = s.surface_potential()
+            x = np.concatenate([phi[0], dphi[0]]) / bipb.KCAL
+            assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-10, k
+        with pytest.raises(bipb.BipbError):
+            s.solve(tol=1e-8, restart=201, precision=bipb.FP64)
+
+
+# ---------------------------------------------------------------- solute dielectric eps_in != 1
+def test_solute_dielectric_parity(bipb, orc):
+    """eps_in = 2, eps_out = 80 (S1, S2 and the gradient's source column carry
+    1/eps_in, Sec. 2.2.1): the source term, FP64 and mixed double-float
+    solves, energy, surface potential, gradient and the potential at points
+    inside and outside against the oracle."""
+    p = synth.kirkwood_problem(level=3, radius=10.0, n_charges=6, charge_radius=7.0)
+    p.eps_in = 2.0
+    eps = p.eps_out / p.eps_in
+    y, q = p.charge_pos, p.q[0]
+    b_ref = orc.source(p.centroids, p.normals, y, q, p.eps_in)
+    ref = orc.solve(p, method="direct")
+    phi_ref, dphi_ref = ref.surface_potential()
+    e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="direct")
+    rng = np.random.default_rng(41)
+    pin, pout = _ball(rng, 64, 0.0, 8.0), _ball(rng, 64, 12.0, 30.0)
+    rin = orc.KCAL * orc.potential(p.centroids, p.normals, p.areas, eps, p.kappa, ref.u, pin, True, y, q, p.eps_in)
+    rout = orc.KCAL * orc.potential(p.centroids, p.normals, p.areas, eps, p.kappa, ref.u, pout, False)
+    kw = dict(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(y, p.q)
+        bd = torch.full((2 * p.n,), float("nan"), dtype=torch.float64, device="cuda")
+        s.source(bd, med=_med(bipb, p))
+        np.testing.assert_allclose(bd.cpu().numpy(), b_ref, rtol=0, atol=1e-12 * np.abs(b_ref).max())
+        for prec, tol, rt in ((bipb.FP64, 1e-12, 1e-10), (bipb.MIXED_DF64, 1e-10, 1e-7)):
+            info = s.solve(tol=tol, precision=prec, **kw)[0]
+            assert info["converged"]
+            assert s.energy()[0] == pytest.approx(ref.energy_kcal, rel=rt)
+            phi, dphi = s.surface_potential()
+            assert np.linalg.norm(phi[0] - phi_ref) / np.linalg.norm(phi_ref) < rt
+            assert np.linalg.norm(dphi[0] - dphi_ref) / np.linalg.norm(dphi_ref) < rt
+            dq, dy = s.energy_grad(tol=tol, precision=prec, **kw)
+            np.testing.assert_allclose(dq[0], dq_ref, rtol=100 * rt)
+            np.testing.assert_allclose(dy[0], dy_ref, rtol=0, atol=100 * rt * np.abs(dy_ref).max())
+            vin, vout = s.potential_at(pin, inside=True), s.potential_at(pout, inside=False)
+            np.testing.assert_allclose(vin[0], rin, rtol=0, atol=10 * rt * np.abs(rin).max())
+            np.testing.assert_allclose(vout[0], rout, rtol=0, atol=10 * rt * np.abs(rout).max())
 
 
 # ---------------------------------------------------------------- uneven batches

@@ -108,6 +108,17 @@ def test_sampled_rows_match_full_matvec(orc, small):
     np.testing.assert_array_equal(orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows), full[rows])
 
 
+def test_sampled_transpose_rows_match_dense_transpose(orc, small):
+    """Rows of A^T w summed one by one equal the rows of the dense A^T w."""
+    p = small
+    eps = p.eps_out / p.eps_in
+    A = orc.assemble(p.centroids, p.normals, p.areas, eps, p.kappa)
+    w = np.random.default_rng(18).standard_normal(2 * p.n)
+    rows = np.array([0, 7, p.n - 1, p.n, p.n + 3, 2 * p.n - 1])
+    got = orc.matvec_t_rows(p.centroids, p.normals, p.areas, eps, p.kappa, w, rows)
+    np.testing.assert_allclose(got, (A.T @ w)[rows], rtol=1e-13, atol=1e-13 * np.abs(A.T @ w).max())
+
+
 def test_dense_entries_brute_force(orc, small):
     """Every entry of A rebuilt pair by pair from the kernels (Eqs. 5-6)."""
     p = small

@@ -1,6 +1,8 @@
 """The allocation-free FP32 mat-vec (bipb_matvec32_static) agrees with the
-handle-based FP32 mat-vec (bipb_matvec), through the C ABI, on two calls in a
-row.
+handle-based FP32 mat-vec (bipb_matvec) and with the FP64 oracle, through
+the C ABI, on two calls in a row, with and without salt (kappa = 0 takes the
+pair formula without the screened terms), on the current stream and on a
+stream of its own.
 
 bipb_matvec32_static serves callers that cannot call cudaMalloc (a host
 framework that already owns nearly all device memory, or a loop that must
@@ -36,30 +38,53 @@ def _dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-def _compare(bipb, p, seed):
-    med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
-    u = _dev(np.random.default_rng(seed).standard_normal(2 * p.n))
+def _compare(bipb, orc, p, seed, kappa, stream=None):
+    med = bipb.medium(p.eps_in, p.eps_out, kappa)
+    u_host = np.random.default_rng(seed).standard_normal(2 * p.n)
+    u = _dev(u_host)
     y_ref = torch.empty_like(u)
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         s.matvec(u, y_ref, precision=bipb.FP32, med=med)
         torch.cuda.synchronize()
     y = torch.full_like(u, float("nan"))
-    bipb.matvec32_static(_dev(p.centroids), _dev(p.normals), _dev(p.areas), u, y, med=med)
-    torch.cuda.synchronize()
+    geo = (_dev(p.centroids), _dev(p.normals), _dev(p.areas))
+    if stream is None:
+        bipb.matvec32_static(*geo, u, y, med=med)
+        torch.cuda.synchronize()
+    else:
+        stream.wait_stream(torch.cuda.current_stream())  # the inputs were written on the current stream
+        with torch.cuda.stream(stream):
+            bipb.matvec32_static(*geo, u, y, med=med, stream=stream.cuda_stream)
+        stream.synchronize()
     a, r = y.cpu().numpy(), y_ref.cpu().numpy()
+    exact = orc.matvec(p.centroids, p.normals, p.areas, p.eps_out / p.eps_in, kappa, u_host)
     assert np.all(np.isfinite(a))
-    # the FP32 mat-vec tolerance used by the parity tests
-    assert np.linalg.norm(a - r) / np.linalg.norm(r) < 3e-6
-    assert np.abs(a - r).max() < 2e-5 * np.abs(r).max()
+    # the FP32 mat-vec tolerance used by the parity tests, against the handle
+    # path and against the oracle
+    for ref in (r, exact):
+        assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < 3e-6
+        assert np.abs(a - ref).max() < 2e-5 * np.abs(ref).max()
 
 
-def test_static_matvec_matches_handle_matvec_twice(bipb):
-    # first call: 20480 triangles; second call: a ragged smaller surface
-    _compare(bipb, synth.kirkwood_problem(level=5), seed=1)
+def _ragged():
     p = synth.protein_like_problem(level=3, n_charges=5)
     keep = np.arange(p.n) % 7 != 3
     p.centroids, p.normals, p.areas = p.centroids[keep], p.normals[keep], p.areas[keep]
-    _compare(bipb, p, seed=2)
+    return p
+
+
+@pytest.mark.parametrize("kappa", [0.1257, 0.0])
+def test_static_matvec_matches_handle_matvec_twice(bipb, orc, kappa):
+    # first call: 20480 triangles; second call: a ragged smaller surface,
+    # so leftovers of the first call sit in the shared scratch array
+    _compare(bipb, orc, synth.kirkwood_problem(level=5), seed=1, kappa=kappa)
+    _compare(bipb, orc, _ragged(), seed=2, kappa=kappa)
+
+
+def test_static_matvec_on_its_own_stream(bipb, orc):
+    s = torch.cuda.Stream()
+    _compare(bipb, orc, _ragged(), seed=3, kappa=0.1257, stream=s)
+    _compare(bipb, orc, synth.born_problem(level=3), seed=4, kappa=0.1257, stream=s)
 
 
 def test_static_matvec_rejects_oversized_surface(bipb):
