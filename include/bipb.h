@@ -64,7 +64,13 @@ typedef enum {
                           FP32 and contracted against blocks of 64 right-hand sides on the tensor
                           cores (each FP32 operand split into two TF32 parts, three TF32 products
                           per tile, FP32 accumulation, FP64 sums across tiles: about FP32 accuracy) */
-  BIPB_MIXED_TF32 = 6  /* TF32 tensor-core mat-vec inside GMRES, double-float refinement residual */
+  BIPB_MIXED_TF32 = 6, /* TF32 tensor-core mat-vec inside GMRES, double-float refinement residual */
+  BIPB_TREE32 = 7,     /* mat-vec only, forward, single-surface handles: the far-field (treecode) operator
+                          of Sec. 2.2.3 in FP32 pair arithmetic, FP64 sums across work items
+                          (bipb_treecode sets its parameters) */
+  BIPB_MIXED_TREE = 8  /* far-field FP32 mat-vec inside GMRES, double-float refinement residual (the
+                          residual stays the direct sum, so the solve still reaches tol on the exact
+                          discrete system); adjoint solves use the direct FP32 transpose inside */
 } bipb_precision;
 
 /* Dielectric medium (Sec. 2.1): eps_in > 0 inside, eps_out > 0 outside, kappa >= 0 (1/A). */
@@ -284,7 +290,8 @@ typedef enum {
   BIPB_KERNEL_MATVECDF_T = 9, /* double-float transposed mat-vec pair kernel */
   BIPB_KERNEL_MATVEC_TC = 10, /* tensor-core multi-RHS mat-vec kernel */
   BIPB_KERNEL_POTENTIAL = 11, /* potential-at-points pair kernels */
-  BIPB_KERNEL_KINDS = 12
+  BIPB_KERNEL_MATVEC_TREE = 12, /* far-field (treecode) mat-vec kernel */
+  BIPB_KERNEL_KINDS = 13
 } bipb_kernel_kind;
 
 /* Turn timing on (1) or off (0); turning it on clears the totals. */
@@ -320,6 +327,33 @@ bipb_status bipb_matvec_variant(bipb_surface s, int variant);
  * the operator of Eqs. 5-6 and differ only in summation order.  Surfaces too
  * large for the symmetric work list use the ordered form either way. */
 bipb_status bipb_symmetric_pairs(bipb_surface s, int symmetric);
+
+/*
+ * Parameters of the far-field (treecode) mat-vec, Sec. 2.2.3 (BIPB_TREE32,
+ * BIPB_MIXED_TREE).  The elements form a binary tree of clusters: a cluster
+ * (a box of centroids) holding more than leaf_size elements is split in two
+ * at the median of its longest side.  Targets are taken leaf by leaf; for a
+ * target leaf B (centre x_B, radius r_B = half its box diagonal) a cluster c
+ * (x_c, r_c) is far when r_c + theta r_B <= theta |x_B - x_c|, which gives
+ * the paper's acceptance criterion r_c / |x - x_c| <= theta for every target
+ * x of B.  A far cluster with more elements than (degree + 1)^3 acts through
+ * (degree + 1)^3 proxy sources at the Chebyshev points of its box, weighted
+ * by the Lagrange interpolant of its elements' values (a polynomial of the
+ * given degree per coordinate in the source position, where the paper writes
+ * a Taylor series about the cluster centre); every other pair is summed
+ * directly.  theta in [0, 1) (0: every pair direct), degree 4, 6 or 8,
+ * leaf_size in [32, 512].  Defaults: 0.5, 6, 256 (about 1e-7 of the largest
+ * output on a 81920-element molecular surface, below the FP32 mat-vec's own
+ * error).  Single-surface handles only.  The tree is built on the host at the
+ * first far-field mat-vec after a change (it synchronises the stream then).
+ */
+bipb_status bipb_treecode(bipb_surface s, double theta, int degree, int leaf_size);
+
+/* Size of the far-field operator of the current parameters (builds it if
+ * needed): pairs = (target, source or proxy) pairs one mat-vec evaluates for
+ * one right-hand side, far_clusters = clusters acting through proxies,
+ * leaves = target leaves.  Host outputs, each may be NULL. */
+bipb_status bipb_treecode_stats(bipb_surface s, int64_t* pairs, int* far_clusters, int* leaves);
 
 /* Number of CUDA kernels this handle has launched since creation (kernels
  * inside replayed CUDA graphs included).  Host output; no synchronisation. */

@@ -62,6 +62,7 @@ def lib():
         L.orc_matvec_t.argtypes = [I, P, P, P, D, D, P, P]
         L.orc_matvec_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
         L.orc_matvec_t_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
+        L.orc_record_sums.argtypes = [I, P, P, P, I, P, P, P, P, D, D, P]
         L.orc_assemble.argtypes = [I, P, P, P, D, D, P]
         L.orc_gesv.argtypes = [I, P, I, P]
         L.orc_gesv.restype = ctypes.c_int
@@ -230,4 +231,5 @@ def grad(x, nrm, area, eps, kappa, eps_in, y, q, u, lam):
 
 from .gmres import gmres  # noqa: E402,F401
 from . import closed_forms  # noqa: E402,F401
+from . import treecode  # noqa: E402,F401
 from .solve import Solution, energy_gradient, solve, solve_adjoint  # noqa: E402,F401

@@ -219,6 +219,35 @@ void orc_matvec_t_rows(int64_t n, const double* x, const double* nrm, const doub
   }
 }
 
+/*
+ * Mat-vec sums of targets over a list of source records (the far-field
+ * treecode of Sec. 2.2.3 sums each target over its near elements and the
+ * proxy sources of its far clusters).  Record j has a position y_j, a_j
+ * (ds psi for an element) and a vector m_j (ds phi n_j for an element).  K2
+ * and K4 are linear in the source normal, so they are taken with m_j in its
+ * place:
+ *   out[2t]     = sum_j [K1(x_t, y_j) a_j + K2(x_t, y_j; m_j)]
+ *   out[2t + 1] = sum_j [K3(x_t, y_j) a_j + K4(x_t, y_j; m_j)]
+ * A record whose id equals the target's id (the self pair) is skipped.
+ */
+void orc_record_sums(int64_t nt, const double* xt, const double* nrm_t, const int64_t* tid, int64_t ns,
+                     const double* ys, const double* a, const double* m, const int64_t* sid, double eps,
+                     double kappa, double* out) {
+  int64_t t;
+#pragma omp parallel for schedule(static)
+  for (t = 0; t < nt; ++t) {
+    double sp = 0.0, ss = 0.0, K[4];
+    for (int64_t j = 0; j < ns; ++j) {
+      if (sid[j] == tid[t]) continue;
+      orc_kernels(xt + 3 * t, nrm_t + 3 * t, ys + 3 * j, m + 3 * j, eps, kappa, K);
+      sp += K[0] * a[j] + K[1];
+      ss += K[2] * a[j] + K[3];
+    }
+    out[2 * t] = sp;
+    out[2 * t + 1] = ss;
+  }
+}
+
 /* Dense A (2n x 2n, row-major), same entries as orc_matvec. */
 void orc_assemble(int64_t n, const double* x, const double* nrm, const double* area, double eps,
                   double kappa, double* A) {

@@ -33,6 +33,8 @@ DF64 = 3
 MIXED_DF64 = 4
 TF32 = 5
 MIXED_TF32 = 6
+TREE32 = 7
+MIXED_TREE = 8
 
 KCAL = 4.0 * np.pi * 332.0716  # internal units -> kcal/mol (per e)
 
@@ -42,12 +44,12 @@ EXPORTED = (
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
     "bipb_autotune", "bipb_matvec_variant", "bipb_surface_create_batch", "bipb_charges_set_batch",
-    "bipb_symmetric_pairs", "bipb_potential_at", "bipb_energy_free",
+    "bipb_symmetric_pairs", "bipb_potential_at", "bipb_energy_free", "bipb_treecode", "bipb_treecode_stats",
 )
 MATVEC32_VARIANTS = 10
 
 KERNEL_KINDS = ("matvec64", "matvec32", "matvec64_t", "matvec32_t", "source", "reaction", "energy_row", "grad",
-                "matvec_df", "matvec_df_t", "matvec_tc", "potential")
+                "matvec_df", "matvec_df_t", "matvec_tc", "potential", "matvec_tree")
 REGION_INSIDE = 0
 REGION_OUTSIDE = 1
 PRECOND_NONE = 0
@@ -136,6 +138,8 @@ def load_library():
         "bipb_symmetric_pairs": ([P, I], st),
         "bipb_potential_at": ([P, I, I64, P, P], st),
         "bipb_energy_free": ([P, P, P], st),
+        "bipb_treecode": ([P, D, I, I], st),
+        "bipb_treecode_stats": ([P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -334,6 +338,17 @@ class Surface:
 
     def set_variant(self, variant):
         _check(self._L.bipb_matvec_variant(self._h, int(variant)))
+
+    def treecode(self, theta=0.5, degree=6, leaf_size=256):
+        """Parameters of the far-field mat-vec (TREE32, MIXED_TREE): MAC theta,
+        interpolation degree per coordinate, largest leaf."""
+        _check(self._L.bipb_treecode(self._h, float(theta), int(degree), int(leaf_size)))
+
+    def treecode_stats(self):
+        """(pairs per mat-vec and right-hand side, far clusters, leaves) of the far-field operator."""
+        pairs, far, leaves = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        _check(self._L.bipb_treecode_stats(self._h, ctypes.byref(pairs), ctypes.byref(far), ctypes.byref(leaves)))
+        return pairs.value, far.value, leaves.value
 
     def symmetric_pairs(self, on=True):
         """FP64 / double-float mat-vecs: visit every unordered pair once (True) or every ordered pair."""

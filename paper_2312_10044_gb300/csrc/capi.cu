@@ -77,8 +77,9 @@ void validate_params(const bipb_solve_params* p) {
   BIPB_REQUIRE(p->restart >= 0 && p->restart <= kMaxRestart, "restart must lie in [1, 200] (0 = 10)");
   BIPB_REQUIRE(p->max_iter >= 0, "max_iter must be >= 0 (0 = 1000)");
   BIPB_REQUIRE(p->precision == BIPB_FP64 || p->precision == BIPB_MIXED || p->precision == BIPB_DF64 ||
-                   p->precision == BIPB_MIXED_DF64 || p->precision == BIPB_MIXED_TF32,
-               "precision must be FP64, MIXED, DF64, MIXED_DF64 or MIXED_TF32");
+                   p->precision == BIPB_MIXED_DF64 || p->precision == BIPB_MIXED_TF32 ||
+                   p->precision == BIPB_MIXED_TREE,
+               "precision must be FP64, MIXED, DF64, MIXED_DF64, MIXED_TF32 or MIXED_TREE");
   BIPB_REQUIRE(p->inner_max_iter >= 0, "inner_max_iter must be >= 0");
   BIPB_REQUIRE(std::isfinite(p->inner_tol) && p->inner_tol >= 0 && p->inner_tol < 1, "inner_tol must lie in [0, 1)");
   BIPB_REQUIRE(p->precond == BIPB_PRECOND_NONE || p->precond == BIPB_PRECOND_SELF, "unknown precond");
@@ -250,6 +251,7 @@ bipb_surface create_surface(const std::vector<PartIn>& parts, void* cuda_stream,
     tgt32.reserve(2 * total);
     for (auto& P : parts) add_part(s, P, tgt, tgt32);
     s->batch = batch;
+    if (!batch) s->raw_centroids.assign(parts[0].c, parts[0].c + 3 * parts[0].n);
     int dev = 0;
     BIPB_CUDA(cudaGetDevice(&dev));
     s->device = dev;
@@ -441,9 +443,11 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
     Surface* s = checked(h);
     validate_medium(m);
     BIPB_REQUIRE(precision == BIPB_FP64 || precision == BIPB_FP32 || precision == BIPB_DF64 ||
-                     precision == BIPB_TF32,
-                 "precision must be FP64, FP32, DF64 or TF32");
+                     precision == BIPB_TF32 || precision == BIPB_TREE32,
+                 "precision must be FP64, FP32, DF64, TF32 or TREE32");
     BIPB_REQUIRE(precision != BIPB_TF32 || !s->batch, "the tensor-core mat-vec needs a single-surface handle");
+    BIPB_REQUIRE(precision != BIPB_TREE32 || !s->batch, "the far-field mat-vec needs a single-surface handle");
+    BIPB_REQUIRE(precision != BIPB_TREE32 || !transpose, "the far-field mat-vec has no transpose");
     BIPB_REQUIRE(n_vec >= 1 && n_vec <= 4096, "n_vec must lie in [1, 4096]");
     BIPB_REQUIRE(!s->batch || n_vec == 1, "a batch handle takes one batched vector (n_vec = 1)");
     BIPB_REQUIRE(u && y, "NULL vector");
@@ -489,6 +493,7 @@ bipb_status bipb_solve(bipb_surface h, const bipb_solve_params* p, bipb_solve_in
     s->have_solution = false;
     source_pass(s, L, p->medium, s->b.p);
     BIPB_REQUIRE(p->precision != BIPB_MIXED_TF32 || !s->batch, "MIXED_TF32 needs a single-surface handle");
+    BIPB_REQUIRE(p->precision != BIPB_MIXED_TREE || !s->batch, "MIXED_TREE needs a single-surface handle");
     std::vector<SolveResult> res = gmres_solve(s, L, p->medium, *p, false, s->b.p, s->u.p, p->x0 != nullptr);
     if (p->precision == BIPB_MIXED_TF32) check_tc_error(s);
     reaction_pass(s, L, p->medium, s->u.p, nullptr, s->e_dev.p);
@@ -693,6 +698,30 @@ bipb_status bipb_symmetric_pairs(bipb_surface h, int symmetric) {
     Surface* s = checked(h);
     BIPB_REQUIRE(symmetric == 0 || symmetric == 1, "symmetric must be 0 or 1");
     s->sym_pairs = symmetric != 0;
+  });
+}
+
+bipb_status bipb_treecode(bipb_surface h, double theta, int degree, int leaf_size) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(!s->batch, "the far-field mat-vec needs a single-surface handle");
+    BIPB_REQUIRE(std::isfinite(theta) && theta >= 0.0 && theta < 1.0, "theta must lie in [0, 1)");
+    BIPB_REQUIRE(degree == 4 || degree == 6 || degree == 8, "degree must be 4, 6 or 8");
+    BIPB_REQUIRE(leaf_size >= 32 && leaf_size <= 512, "leaf_size must lie in [32, 512]");
+    s->far_theta = theta;
+    s->far_degree = degree;
+    s->far_leaf = leaf_size;
+  });
+}
+
+bipb_status bipb_treecode_stats(bipb_surface h, int64_t* pairs, int* far_clusters, int* leaves) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    DeviceGuard dg(s->device);
+    FarField* f = far_field(s);
+    if (pairs) *pairs = f->pair_evals;
+    if (far_clusters) *far_clusters = f->n_slots;
+    if (leaves) *leaves = f->n_leaves;
   });
 }
 

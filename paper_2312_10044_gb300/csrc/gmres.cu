@@ -718,11 +718,14 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   const int64_t len = L.len;
   const int nb = grid_for(len);
   const std::vector<double> bnorm = norms(s, w, rhs);
-  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_MIXED_TF32;
+  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_MIXED_TF32 ||
+                     p.precision == BIPB_MIXED_TREE;
   // arithmetic of the Krylov mat-vecs and of the residual r = b - A x (the
-  // adjoint solve has no tensor-core transpose and uses FP32 there)
-  const int inner = !mixed ? p.precision
-                           : (p.precision == BIPB_MIXED_TF32 && !transpose ? BIPB_TF32 : BIPB_FP32);
+  // adjoint solve has neither a tensor-core nor a far-field transpose and
+  // uses the direct FP32 mat-vec there)
+  int inner = !mixed ? p.precision : BIPB_FP32;
+  if (p.precision == BIPB_MIXED_TF32 && !transpose) inner = BIPB_TF32;
+  if (p.precision == BIPB_MIXED_TREE && !transpose) inner = BIPB_TREE32;
   const int resid = (p.precision == BIPB_MIXED || p.precision == BIPB_FP64) ? BIPB_FP64 : BIPB_DF64;
   // r = rhs - A x (or rhs when starting from zero)
   if (warm) {

@@ -199,7 +199,7 @@ constexpr int kMaxRestart = 200;
 
 // Per-kernel CUDA-event timing of the pair kernels (off by default).
 enum TimedKind { kTMv64 = 0, kTMv32, kTMv64T, kTMv32T, kTSource, kTReaction, kTRow, kTGrad, kTMvDF, kTMvDFT, kTMvTC,
-                 kTPotential, kTKinds };
+                 kTPotential, kTMvTree, kTKinds };
 
 struct EventPair {
   int kind;
@@ -252,6 +252,34 @@ struct KernelTimer {
 
 struct GmresWork;  // gmres.cu
 
+// Far-field (treecode) FP32 mat-vec of one surface (tree.cu): the tree, the
+// interaction lists cut into balanced work items, and the per-pass scratch.
+// Built on first use for the handle's parameters and kept until they change.
+struct FarField {
+  double theta = 0.0;
+  int degree = 0, leaf = 0;
+  int n = 0;           // elements
+  int n_leaves = 0;    // target batches
+  int lmax = 0;        // largest leaf
+  int nt = 0;          // threads per CTA of the far-field kernel (lmax rounded up to a warp)
+  int n_slots = 0;     // clusters that carry proxy sources
+  int n_items = 0;     // work items of the far-field kernel
+  int n_up = 0;        // pieces of the upward (proxy weight) pass
+  int rec_stride = 0;  // records per system: n elements + n_slots (degree+1)^3 proxies
+  int64_t pair_evals = 0;  // (target, record) pairs one mat-vec evaluates per system
+  DevBuf<int> perm;        // tree position -> element
+  DevBuf<int> leaf_of;     // tree position -> leaf
+  DevBuf<int4> leaf_tab;   // per leaf {first position, count, first item, items}
+  DevBuf<int4> items;      // per item {leaf, first segment, end segment, 0}
+  DevBuf<int2> segs;       // per segment {first record, count}
+  DevBuf<int4> up_pieces;  // per upward piece {slot, first position, count, 0}
+  DevBuf<int2> up_tab;     // per slot {first piece, pieces}
+  DevBuf<float> nodes;     // per slot 3 x (degree+1) Chebyshev nodes, centred FP32
+  DevBuf<float4> rec;      // records, 2 float4 each, rec_stride per system
+  DevBuf<float> part;      // partial sums, 2 lmax per item and system
+  DevBuf<double> upart;    // partial proxy weights, 4 (degree+1)^3 per piece and system
+};
+
 struct Surface {
   uint64_t magic = 0;
   int device = 0;
@@ -297,6 +325,7 @@ struct Surface {
   std::vector<int> part_off, part_n;
   std::vector<double> part_center;  // 3 per surface
   std::vector<CentroidSet> part_keys;  // the centred centroids of every surface
+  std::vector<double> raw_centroids;   // single-surface handles: the centroids as given (tree of the far field)
   bool batch = false;
 
   // cached work lists and device copies of layouts (keyed by content)
@@ -315,6 +344,10 @@ struct Surface {
   int mv32_variant = kFirstSymVariant + 2;  // FP32 mat-vec variant (the autotuner may change it)
   bool sym_pairs = true;  // FP64 / double-float mat-vecs visit unordered pairs once (sym.cu)
   GmresWork* gw = nullptr;
+  // far-field mat-vec: parameters (bipb_treecode) and the built operator
+  double far_theta = 0.5;
+  int far_degree = 6, far_leaf = 256;
+  std::unique_ptr<FarField> far;
   KernelTimer timer;
   uint64_t alloc_gen = 0;  // bumped whenever a scratch buffer moves (recorded graphs go stale)
   long long launches = 0;           // kernels launched on this handle (graph replays included)
@@ -373,6 +406,11 @@ bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, do
                   const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride);
 bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, double kappa, bool transpose, const double* u,
                    double* y, double dphi, double dpsi, const int* skip, int skip_stride);
+// y = A u for right-hand sides of one surface by the far-field treecode (tree.cu)
+void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
+                 double dpsi, const int* skip, int skip_stride);
+// the far-field operator of the handle's parameters (built on first use; synchronises then)
+FarField* far_field(Surface* s);
 // y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)
 void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
                double dpsi, const int* skip, int skip_stride);

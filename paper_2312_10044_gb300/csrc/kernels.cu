@@ -884,6 +884,11 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     matvec_tc(s, L, pair_const<float>(m), u, y, dphi, dpsi, skip, skip_stride);
     return;
   }
+  if (precision == BIPB_TREE32) {
+    BIPB_REQUIRE(!transpose, "the far-field mat-vec has no transpose");
+    matvec_tree(s, L, pair_const<float>(m), u, y, dphi, dpsi, skip, skip_stride);
+    return;
+  }
   if (precision == BIPB_DF64) {
     DFConst c = df_const_impl(s, m);
     bool shared_surface = L.K >= 4;

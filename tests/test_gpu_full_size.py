@@ -134,3 +134,52 @@ def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
         e_32 = np.sqrt(np.mean((Y32[v][rows] - ref) ** 2))
         scale = np.sqrt(np.mean(off_ref ** 2))
         assert e_tc <= 2 * e_32 + 1e-7 * scale, (v, e_tc / scale, e_32 / scale)
+
+
+def test_treecode_matvec_level6_sampled_rows(bipb, orc):
+    """The far-field mat-vec with its default parameters (theta 0.5, degree 6,
+    leaves of 256) on the protein-like surface (N = 81920): within 1e-6 of the
+    largest output of the exact (direct) mat-vec on 64 sampled rows, for random
+    and smooth right-hand sides, within the FP32 bounds of the oracle's own
+    treecode, and at under 30 % of the direct pairs."""
+    p = synth.protein_like_problem()
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(62)
+    x = p.centroids / 25.0
+    U = np.stack([rng.standard_normal(2 * p.n), np.concatenate([1.0 + 0.3 * x[:, 2], 0.5 - 0.2 * x[:, 0]])])
+    rows = np.sort(rng.choice(2 * p.n, 64, replace=False))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TREE32, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
+        Y = yd.cpu().numpy()
+        pairs, far, leaves = s.treecode_stats()
+    assert far > 0 and pairs < 0.3 * p.n * p.n
+    tree = orc.treecode.build_tree(p.centroids, 256)
+    lists = orc.treecode.interaction_lists(tree, 0.5, 6)
+    for v in range(U.shape[0]):
+        exact = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
+        ref_tc = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], 0.5, 6, 256, rows=rows,
+                                     tree=tree, lists=lists)
+        scale = np.abs(exact).max()
+        assert np.abs(Y[v][rows] - exact).max() < 1e-6 * scale, (v, np.abs(Y[v][rows] - exact).max() / scale)
+        assert np.abs(Y[v][rows] - ref_tc).max() < 2e-5 * scale
+
+
+def test_mixed_tree_solve_level7_matches_direct_mixed_solve(bipb):
+    """Level 7 (N = 327680, 10000 charges): the mixed solve with far-field
+    Krylov mat-vecs reaches 1e-8 on the exact system (its residual is the
+    direct double-float sum) and agrees with the direct mixed solve."""
+    p = synth.adjoint_problem()
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        kw = dict(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, tol=1e-8)
+        it = s.solve(precision=bipb.MIXED_TREE, **kw)[0]
+        e_tree = s.energy()[0]
+        phi_tree, _ = s.surface_potential()
+        idr = s.solve(precision=bipb.MIXED_DF64, **kw)[0]
+        e_dir = s.energy()[0]
+        phi_dir, _ = s.surface_potential()
+    assert it["converged"] and it["rel_residual"] <= 1e-8 and idr["converged"]
+    assert e_tree == pytest.approx(e_dir, rel=1e-7)
+    assert np.linalg.norm(phi_tree[0] - phi_dir[0]) / np.linalg.norm(phi_dir[0]) < 1e-7

@@ -845,3 +845,80 @@ def test_charge_on_a_centroid_is_rejected(bipb):
             s.set_charges(np.array([[0.0, 0.0, 0.0], on]), np.array([[1.0, -1.0]]))
         near = on + np.array([1e-12, 0.0, 0.0])
         s.set_charges(np.array([[0.0, 0.0, 0.0], near]), np.array([[1.0, -1.0]]))
+
+
+# ---------------------------------------------------------------- far-field (treecode) mat-vec, Sec. 2.2.3
+def _tc_vectors(p, seed):
+    x = p.centroids / np.abs(p.centroids).max()
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.standard_normal(2 * p.n), rng.standard_normal(2 * p.n),
+                     np.concatenate([1.0 + 0.3 * x[:, 2], 0.5 - 0.2 * x[:, 0]])])
+
+
+@pytest.mark.parametrize("params", [(0.7, 4, 64), (0.8, 6, 64), (0.9, 8, 64), (0.8, 4, 256), (0.0, 6, 256)])
+def test_treecode_matvec_matches_oracle_treecode(bipb, orc, params):
+    """The far-field FP32 mat-vec against the oracle's treecode on the same
+    tree (FP64, every row): the FP32 mat-vec's bounds, 3e-6 in the 2-norm and
+    2e-5 of the largest output; theta = 0 is the direct mat-vec."""
+    theta, deg, leaf = params
+    p = _ragged(4)
+    eps = p.eps_out / p.eps_in
+    U = _tc_vectors(p, 70)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.treecode(theta, deg, leaf)
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TREE32, med=_med(bipb, p))
+        Y = yd.cpu().numpy()
+        pairs, far, leaves = s.treecode_stats()
+    assert (far > 0) == (theta > 0)
+    assert leaves >= p.n // leaf and pairs <= p.n * p.n
+    for r in range(U.shape[0]):
+        ref = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r], theta, deg, leaf)
+        assert np.all(np.isfinite(Y[r]))
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6, (params, r)
+        assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max(), (params, r)
+
+
+def test_treecode_rejects_bad_use(bipb):
+    p = synth.born_problem(level=2)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        for bad in ((1.0, 6, 256), (-0.1, 6, 256), (0.5, 5, 256), (0.5, 6, 16), (0.5, 6, 1024)):
+            with pytest.raises(bipb.BipbError):
+                s.treecode(*bad)
+        u = _dev(np.ones(2 * p.n))
+        with pytest.raises(bipb.BipbError):
+            s.matvec(u, torch.empty_like(u), precision=bipb.TREE32, transpose=True)
+    probs = [synth.born_problem(level=1), synth.born_problem(level=2)]
+    with bipb.BatchSurface([(q.centroids, q.normals, q.areas) for q in probs]) as s:
+        u = _dev(np.ones(sum(2 * q.n for q in probs)))
+        with pytest.raises(bipb.BipbError):
+            s.matvec(u, torch.empty_like(u), precision=bipb.TREE32)
+
+
+def test_mixed_tree_solve_matches_oracle(bipb, orc):
+    """MIXED_TREE (far-field FP32 Krylov mat-vecs, direct double-float
+    residual) reaches the exact discrete solution: energy and potentials of
+    three charge sets against the oracle's GMRES to 1e-12 within 1e-7, and the
+    adjoint gradient (direct FP32 transpose inside) within 1e-5."""
+    base = synth.protein_like_problem(level=4, n_charges=30)
+    batch = synth.batched_charges(base, n_rhs=3, n_charges=30)
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.treecode(0.7, 4, 64)
+        s.set_charges(batch.charge_pos, batch.q)
+        prm = bipb.solve_params(batch.eps_in, batch.eps_out, batch.kappa, tol=1e-9, precision=bipb.MIXED_TREE)
+        info = s.solve(prm)
+        e = s.energy()
+        phi, _ = s.surface_potential()
+        dq, dy = s.energy_grad(prm)
+        assert s.treecode_stats()[1] > 0  # some clusters act through proxies
+    for r in range(3):
+        assert info[r]["converged"] and info[r]["rel_residual"] <= 1e-9
+        assert info[r]["refine_steps"] <= 3 and info[r]["matvecs32"] > 0
+        ref = orc.solve(batch, rhs=r, method="gmres", tol=1e-12)
+        assert e[r] == pytest.approx(ref.energy_kcal, rel=1e-7)
+        phi_ref, _ = ref.surface_potential()
+        assert np.linalg.norm(phi[r] - phi_ref) / np.linalg.norm(phi_ref) < 1e-7
+    e_ref, dq_ref, dy_ref = orc.energy_gradient(batch, rhs=1, method="gmres", tol=1e-12)
+    np.testing.assert_allclose(dq[1], dq_ref, rtol=1e-5)
+    np.testing.assert_allclose(dy[1], dy_ref, rtol=0, atol=1e-5 * np.abs(dy_ref).max())

@@ -523,3 +523,105 @@ def test_coulomb_energy_textbook_values(orc):
     assert orc.coulomb(y @ Rm.T + [3.0, -1.0, 2.0], qq, 2.0) == pytest.approx(e, rel=1e-12)
     assert orc.coulomb(y[perm], qq[perm], 2.0) == pytest.approx(e, rel=1e-12)
     assert orc.coulomb(2.5 * y, qq, 2.0) == pytest.approx(e / 2.5, rel=1e-12)
+
+
+# ------------------------------------------------------------------ far-field treecode (Sec. 2.2.3)
+@pytest.fixture(scope="module")
+def tc_surface():
+    return synth.protein_like_problem(level=4, n_charges=5)
+
+
+def test_treecode_tree_and_lists_partition_every_pair(orc, tc_surface):
+    """The tree splits at the median of the longest side, leaves hold at most
+    N0 elements, and every leaf's list covers every source element exactly
+    once (directly or inside one far cluster); every far cluster meets the
+    particle-cluster MAC r_c / |x - x_c| <= theta for each target of the leaf."""
+    tc = orc.treecode
+    p = tc_surface
+    theta, deg, leaf = 0.6, 4, 64
+    t = tc.build_tree(p.centroids, leaf)
+    n = p.n
+    assert sorted(t.perm.tolist()) == list(range(n))
+    for k, ch in enumerate(t.child):
+        if ch is None:
+            assert t.end[k] - t.start[k] <= leaf
+            continue
+        l, r = ch
+        assert t.start[l] == t.start[k] and t.end[l] == t.start[r] and t.end[r] == t.end[k]
+        assert t.end[l] - t.start[l] == (t.end[k] - t.start[k]) // 2
+        d = int(np.argmax(t.hi[k] - t.lo[k]))
+        assert p.centroids[t.perm[t.start[l]:t.end[l]], d].max() <= p.centroids[t.perm[t.start[r]:t.end[r]], d].min()
+    lists = tc.interaction_lists(t, theta, deg)
+    n_far = 0
+    for li, b in enumerate(t.leaves):
+        cover = np.zeros(n, dtype=int)
+        tgt = p.centroids[t.perm[t.start[b]:t.end[b]]]
+        for e in lists[li]:
+            if e[0] == "direct":
+                cover[e[1]:e[2]] += 1
+            else:
+                k = e[1]
+                n_far += 1
+                cover[t.start[k]:t.end[k]] += 1
+                xc, rc = tc.geometry(t, k)
+                assert t.end[k] - t.start[k] > (deg + 1) ** 3
+                assert np.all(rc / np.linalg.norm(tgt - xc, axis=1) <= theta)
+        assert np.all(cover == 1)
+    assert n_far > 0
+
+
+def test_treecode_proxies_reproduce_polynomial_moments(orc, tc_surface):
+    """The proxy weights of a cluster are Lagrange interpolation at the
+    Chebyshev points of its box: every moment sum_j a_j x^i y^j z^k with
+    i, j, k <= p is reproduced exactly by the proxies (up to rounding)."""
+    tc = orc.treecode
+    p = tc_surface
+    t = tc.build_tree(p.centroids, 64)
+    k = t.child[t.child[0][0]][1]  # a cluster of a quarter of the surface
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(p.n)
+    m = rng.standard_normal((p.n, 3))
+    deg = 4
+    pos, pa, pm = tc.proxies(t, k, p.centroids, a, m, deg)
+    idx = t.perm[t.start[k]:t.end[k]]
+    c = 0.5 * (t.lo[k] + t.hi[k])
+    x, s = p.centroids[idx] - c, pos - c
+    for i in range(deg + 1):
+        for j in range(deg + 1):
+            for l in (0, deg):
+                mono_x = x[:, 0] ** i * x[:, 1] ** j * x[:, 2] ** l
+                mono_s = s[:, 0] ** i * s[:, 1] ** j * s[:, 2] ** l
+                ref = np.dot(mono_x, a[idx])
+                assert np.dot(mono_s, pa) == pytest.approx(ref, rel=1e-9, abs=1e-9 * np.abs(mono_x * a[idx]).sum())
+                refm = mono_x @ m[idx]
+                np.testing.assert_allclose(mono_s @ pm, refm, rtol=1e-9, atol=1e-9 * np.abs(mono_x).sum())
+    # a source on a node: its basis value is exactly 1 there and 0 at the other nodes
+    nodes, w = tc.cheb_box(t.lo[k], t.hi[k], deg)
+    assert tc.lagrange_1d(np.array([nodes[0][2]]), nodes[0], w)[0].tolist() == [0.0, 0.0, 1.0, 0.0, 0.0]
+
+
+def test_treecode_theta_zero_is_the_direct_matvec(orc, tc_surface):
+    """theta = 0: no cluster is far, every pair is summed directly."""
+    p = tc_surface
+    eps = p.eps_out / p.eps_in
+    u = np.random.default_rng(5).standard_normal(2 * p.n)
+    ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u)
+    got = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u, 0.0, 6, 64)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_treecode_error_falls_with_degree(orc, tc_surface):
+    """The far-field approximation error against the direct mat-vec falls
+    geometrically with the interpolation degree (2, 4, 6) at fixed theta, on
+    a smooth field and a random one."""
+    p = tc_surface
+    eps = p.eps_out / p.eps_in
+    x = p.centroids / 25.0
+    for u in (np.concatenate([1.0 + 0.3 * x[:, 2], 0.5 - 0.2 * x[:, 0]]),
+              np.random.default_rng(6).standard_normal(2 * p.n)):
+        ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u)
+        errs = []
+        for deg in (2, 4, 6):
+            got = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u, 0.7, deg, 32)
+            errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        assert errs[0] > 5 * errs[1] > 25 * errs[2] > 0, errs
