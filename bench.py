@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein_like"])
+    ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein_like", "adjoint"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
@@ -99,7 +99,8 @@ def parse():
     ap.add_argument("--configs", default="3,4a,4b,5",
                     help="--mode configs: which larger configurations (5fd: the full-size central-difference check)")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "configs", "peaks"],
+                    choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "matvectree",
+                             "configs", "peaks"],
                     help="matvec32/matvec64: only W+K single mat-vecs of the workload (for profilers)")
     return ap.parse_args()
 
@@ -113,6 +114,8 @@ def workload(name):
                     "in r<16 A, eps 1/80, kappa 0.1257/A; source + mixed-precision GMRES(10) to 1e-8 + energy",
         "protein_like": "protein-like surface: displaced icosphere level 6 (N=81920), R=25 A, 2000 charges, "
                         "eps 1/80, kappa 0.1257/A; source + mixed-precision GMRES(10) to 1e-8 + energy",
+        "adjoint": "displaced icosphere level 7 (N=327680), R=45 A, 10000 charges, eps 1/80, kappa 0.1257/A; "
+                   "source + mixed-precision GMRES(10) to 1e-8 + energy",
     }[name]
     return p, desc
 
@@ -302,7 +305,7 @@ def run_matvec_only(args):
 
     prob, desc = workload(args.workload)
     prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64, "matvecdfm": bipb.DF64,
-            "matvectc": bipb.TF32}[args.mode]
+            "matvectc": bipb.TF32, "matvectree": bipb.TREE32}[args.mode]
     n_vec = 64 if args.mode in ("matvectc", "matvecdfm") else 1
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
     with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
@@ -389,6 +392,7 @@ def run_configs(args):
             res["energy_free_ms"] = ms_free
             res["energy_free_kcal"] = float(ef[0])
             res["energy_coulomb_kcal"] = float(ec[0])
+            res.update(far_field_timings(bipb, torch, s, p))
             # plain FP64 GMRES: one run (26+ FP64 mat-vecs of ~0.7 s)
             if not args.no_fp64:
                 prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.FP64)
@@ -474,9 +478,44 @@ def run_configs(args):
             res.update({"solve_ms_mixed_df64_precond_self": ms_fp, "energy_grad_ms_precond_self": ms_gp,
                         "info_precond_self": info_p[0],
                         "max_rel_force_difference_precond": float(np.abs(dyp - dy).max() / np.abs(dy).max())})
+            res.update(far_field_timings(bipb, torch, s, p))
             emit(res)
     if "5fd" in which:
         emit(config5_central_differences(bipb, torch))
+    return out
+
+
+def far_field_timings(bipb, torch, s, p):
+    """The far-field (treecode) FP32 mat-vec of Sec. 2.2.3 with its default
+    parameters against the direct FP32 mat-vec, and the mixed solve with it
+    (MIXED_TREE, plain and with the self-block preconditioner) against the
+    direct mixed solve; s is a handle of problem p with its charges set."""
+    n = p.n
+    med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
+    u = torch.randn(2 * n, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(u)
+    out = {}
+    pairs, far, leaves = s.treecode_stats()
+    out["tree_pairs_per_matvec"] = pairs
+    out["tree_pairs_frac_of_direct"] = pairs / (n * (n - 1))
+    out["tree_far_clusters"], out["tree_leaves"] = far, leaves
+    for name, prec, reps in (("tree32", bipb.TREE32, 10), ("fp32_direct", bipb.FP32, 5)):
+        s.matvec(u, y, precision=prec, med=med)
+        ms, _ = _timed(lambda: [s.matvec(u, y, precision=prec, med=med) for _ in range(reps)], torch)
+        out[f"matvec_ms_{name}"] = ms / reps
+    bipb.timer_enable(s, True)
+    s.matvec(u, y, precision=bipb.TREE32, med=med)
+    t = bipb.timer_read(s)
+    bipb.timer_enable(s, False)
+    out["tree_kernel_ms"] = t["matvec_tree"][1]
+    out["tree_kernel_gpairs"] = pairs / (t["matvec_tree"][1] / 1e3) / 1e9 if t["matvec_tree"][1] > 0 else None
+    for name, prec, pc in (("mixed_tree", bipb.MIXED_TREE, bipb.PRECOND_NONE),
+                           ("mixed_tree_precond_self", bipb.MIXED_TREE, bipb.PRECOND_SELF)):
+        prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=prec, precond=pc)
+        s.solve(prm)
+        ms, info = _timed(lambda: s.solve(prm), torch)
+        out[f"solve_ms_{name}"] = ms
+        out[f"{name}_info"] = dict(info[0], energy_kcal=float(s.energy()[0]))
     return out
 
 
@@ -556,7 +595,8 @@ def config3_solves(bipb, torch):
     charges), source + solve to 1e-8 + energy, each solve timed once after an
     untimed run of the same call: mixed (FP32 Krylov, double-float residual),
     mixed with an FP64 residual, plain FP64 GMRES, and the mixed solve with
-    the element self-block preconditioner."""
+    the element self-block preconditioner; then the far-field mat-vec and the
+    mixed solves on it (far_field_timings)."""
     import synth
 
     p = synth.protein_like_problem()
@@ -575,6 +615,7 @@ def config3_solves(bipb, torch):
             ms, info = _timed(lambda: (s.solve(prm)[0], s.energy()[0]), torch)
             out[f"config3_solve_ms_{key}"] = ms
             out[f"config3_{key}_info"] = dict(info[0], energy_kcal=info[1])
+        out.update({f"config3_{k}": v for k, v in far_field_timings(bipb, torch, s, p).items()})
     return out
 
 
