@@ -232,4 +232,5 @@ def grad(x, nrm, area, eps, kappa, eps_in, y, q, u, lam):
 from .gmres import gmres  # noqa: E402,F401
 from . import closed_forms  # noqa: E402,F401
 from . import treecode  # noqa: E402,F401
+from . import precond  # noqa: E402,F401
 from .solve import Solution, energy_gradient, solve, solve_adjoint  # noqa: E402,F401

@@ -25,6 +25,8 @@ from .surfaces import (  # noqa: F401
     batched_charges,
     uneven_batch_problems,
     adjoint_problem,
+    two_spheres_problem,
+    strongly_displaced_problem,
     problem_by_name,
     PROBLEM_NAMES,
 )

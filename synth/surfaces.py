@@ -305,6 +305,27 @@ def adjoint_problem(level=7, radius=45.0, n_charges=10000, seed=5):
     return Problem("adjoint", c, n, a, pos, q[None, :], meta=dict(level=level, radius=radius, seed=seed))
 
 
+def two_spheres_problem(level=3, radius=5.0, gap=0.5):
+    """Two icospheres of ``radius`` whose surfaces are ``gap`` apart along x,
+    a +1 charge at the centre of one and a -1 charge at the centre of the
+    other (near-touching surfaces, where the Krylov solve slows down)."""
+    v, f = icosphere(level, radius)
+    c, n, a = triangle_geometry(v, f)
+    off = np.array([radius + 0.5 * gap, 0.0, 0.0])
+    return Problem("two_spheres", np.concatenate([c - off, c + off]), np.concatenate([n, n]),
+                   np.concatenate([a, a]), np.stack([-off, off]), np.array([[1.0, -1.0]]),
+                   meta=dict(level=level, radius=radius, gap=gap))
+
+
+def strongly_displaced_problem(level=3, radius=10.0, amp=0.3, seed=3, n_charges=20):
+    """A displaced icosphere as in protein_like_problem with displacement
+    amplitude ``amp`` (0.3 to 0.45: 30 to 45 % of the radius)."""
+    v, f, rfn, rng = displaced_icosphere(level, radius, seed, amp=amp)
+    c, n, a = triangle_geometry(v, f)
+    pos, q = charges_inside_surface(rng, n_charges, rfn)
+    return Problem("strongly_displaced", c, n, a, pos, q[None, :], meta=dict(level=level, radius=radius, amp=amp))
+
+
 PROBLEM_NAMES = ("born", "kirkwood", "protein_like", "adjoint")
 
 
