@@ -170,6 +170,19 @@ bipb_status bipb_charges_set(bipb_surface s, int64_t nc, const double* pos, int 
                              int n_rhs, const double* q);
 
 /*
+ * bipb_charges_set with device inputs (for callers whose charges live on the
+ * GPU, e.g. the autograd path): pos and q are device arrays of the current
+ * device with the layouts of bipb_charges_set, read asynchronously on the
+ * handle's stream (ordered after the work the creation stream has queued).
+ * The checks of bipb_charges_set (finite values, no charge on a centroid)
+ * run on the device; a failure is reported, as BIPB_ERR_INVALID_ARG, by the
+ * next call that uses the charges (bipb_solve, bipb_source, bipb_reaction),
+ * which then forgets them.  Single-surface handles.
+ */
+bipb_status bipb_charges_set_dev(bipb_surface s, int64_t nc, const double* pos, int n_pos_sets, int n_rhs,
+                                 const double* q);
+
+/*
  * Charges of a batch handle: surface k gets nc[k] charges at pos[k]
  * (host, nc[k] x 3, Angstrom) with values q[k] (host, nc[k], e).
  * Charge-indexed outputs (bipb_reaction, bipb_energy_grad) list them surface
@@ -189,6 +202,10 @@ bipb_status bipb_solve(bipb_surface s, const bipb_solve_params* p, bipb_solve_in
 /* Solvation energy per configuration (or per surface of a batch handle),
  * kcal/mol, host array (Eq. for E_sol). */
 bipb_status bipb_energy(bipb_surface s, double* e_sol);
+
+/* bipb_energy into device memory (n_rhs doubles, kcal/mol), asynchronous on
+ * the handle's stream. */
+bipb_status bipb_energy_dev(bipb_surface s, double* e_sol);
 
 /*
  * Surface potential phi (kcal/mol/e) and its inner normal derivative
@@ -236,6 +253,12 @@ bipb_status bipb_energy_free(bipb_surface s, double* e_free, double* e_coul);
  */
 bipb_status bipb_energy_grad(bipb_surface s, const bipb_solve_params* p, double* dE_dq,
                              double* dE_dpos);
+
+/* bipb_energy_grad with device outputs (same layouts, kcal/mol/e and
+ * kcal/mol/A), written on the handle's stream; the adjoint GMRES still
+ * synchronises the stream once per restart cycle to read its convergence
+ * state, but no array passes through the host. */
+bipb_status bipb_energy_grad_dev(bipb_surface s, const bipb_solve_params* p, double* dE_dq, double* dE_dpos);
 
 /* ---------------------------------------------------------------------------
  * Hot-path building blocks on device memory (asynchronous on the handle's

@@ -45,6 +45,7 @@ EXPORTED = (
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
     "bipb_autotune", "bipb_matvec_variant", "bipb_surface_create_batch", "bipb_charges_set_batch",
     "bipb_symmetric_pairs", "bipb_potential_at", "bipb_energy_free", "bipb_treecode", "bipb_treecode_stats",
+    "bipb_charges_set_dev", "bipb_energy_dev", "bipb_energy_grad_dev",
 )
 MATVEC32_VARIANTS = 10
 
@@ -139,6 +140,9 @@ def load_library():
         "bipb_potential_at": ([P, I, I64, P, P], st),
         "bipb_energy_free": ([P, P, P], st),
         "bipb_treecode": ([P, D, I, I], st),
+        "bipb_charges_set_dev": ([P, I64, P, I, I, P], st),
+        "bipb_energy_dev": ([P, P], st),
+        "bipb_energy_grad_dev": ([P, P, P, P], st),
         "bipb_treecode_stats": ([P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
@@ -262,6 +266,40 @@ class Surface:
         self._charge_version = next(_charge_versions)
         self.nc, self.n_rhs = nc, n_rhs
         self.n_charges_total = nc * n_rhs
+
+    def set_charges_dev(self, pos, q):
+        """Charges from CUDA float64 tensors: pos (Nc, 3) or (B, Nc, 3), q (Nc,) or (B, Nc).
+        Checked on the device; a bad charge is reported by the next solve."""
+        if q.dim() == 1:
+            q = q.reshape(1, -1)
+        n_rhs, nc = q.shape
+        n_pos = 1 if pos.dim() == 2 else pos.shape[0]
+        if pos.numel() != n_pos * nc * 3 or n_pos not in (1, n_rhs):
+            raise ValueError("pos must be (Nc, 3) or (B, Nc, 3) matching q")
+        q, pos = q.contiguous(), pos.contiguous()
+        _check(self._L.bipb_charges_set_dev(self._h, nc, _dp(pos), n_pos, n_rhs, _dp(q)))
+        self._charge_version = next(_charge_versions)
+        self._dev_charges = (pos, q)  # kept alive until the device has read them
+        self.nc, self.n_rhs = nc, n_rhs
+        self.n_charges_total = nc * n_rhs
+
+    def energy_dev(self, out=None):
+        """E_sol per configuration (kcal/mol) into a CUDA float64 tensor."""
+        import torch
+
+        out = out if out is not None else torch.empty(self.n_systems, dtype=torch.float64, device="cuda")
+        _check(self._L.bipb_energy_dev(self._h, _dp(out)))
+        return out
+
+    def energy_grad_dev(self, params=None, **kw):
+        """(dE/dq (B, Nc), dE/dpos (B, Nc, 3)) as CUDA float64 tensors."""
+        import torch
+
+        p = params if params is not None else solve_params(**kw)
+        dq = torch.empty(self.n_charges_total, dtype=torch.float64, device="cuda")
+        dy = torch.empty(self.n_charges_total, 3, dtype=torch.float64, device="cuda")
+        _check(self._L.bipb_energy_grad_dev(self._h, ctypes.byref(p), _dp(dq), _dp(dy)))
+        return dq.reshape(self.n_rhs, self.nc), dy.reshape(self.n_rhs, self.nc, 3)
 
     # -------------------------------------------------------------- solve / outputs
     def solve(self, params=None, x0=None, raise_on_not_converged=True, **kw):

@@ -86,6 +86,51 @@ void validate_params(const bipb_solve_params* p) {
   BIPB_REQUIRE(p->reserved == 0, "reserved must be 0");
 }
 
+__device__ __forceinline__ uint64_t dev_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint32_t dev_bits(float v) { return __float_as_uint(v == 0.0f ? 0.0f : v); }
+
+// Charge records (y - centre, q) of n_rhs configurations from device arrays,
+// with the checks bipb_charges_set makes on the host: every value finite, and
+// no charge on a centroid (the centroid with the same FP32 point, found in the
+// surface's hash table, compared in FP64).  A failed check sets *err.
+__global__ void k_charges_dev(int64_t nc, int n_rhs, int n_pos_sets, const double* __restrict__ pos,
+                              const double* __restrict__ q, double cx, double cy, double cz,
+                              const int32_t* __restrict__ slot, uint64_t mask, const double4_32a* __restrict__ tgt64,
+                              double4_32a* __restrict__ rec, int* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc * n_rhs) return;
+  const int64_t r = i / nc, k = i % nc;
+  const double* P = pos + 3 * ((n_pos_sets == 1 ? 0 : r) * nc + k);
+  const double p0 = P[0] - cx, p1 = P[1] - cy, p2 = P[2] - cz, qq = q[i];
+  bool ok = isfinite(P[0]) && isfinite(P[1]) && isfinite(P[2]) && isfinite(qq);
+  if (ok) {
+    const float f0 = (float)p0, f1 = (float)p1, f2 = (float)p2;
+    const uint64_t key = ((uint64_t)dev_bits(f0) << 32 | dev_bits(f1)) ^ dev_mix(dev_bits(f2));
+    uint64_t h = dev_mix(key) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+      const int32_t j = slot[h];
+      if (j < 0) break;
+      const double4_32a g = tgt64[2 * (size_t)j];
+      if (dev_bits((float)g.x) == dev_bits(f0) && dev_bits((float)g.y) == dev_bits(f1) &&
+          dev_bits((float)g.z) == dev_bits(f2)) {
+        ok = !(g.x == p0 && g.y == p1 && g.z == p2);
+        break;
+      }
+    }
+  }
+  if (!ok) atomicOr(err, 1);
+  rec[i] = make_double4_32a(p0, p1, p2, qq);
+}
+
+__global__ void k_scale(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i];
+}
+
 }  // namespace
 
 // Live handles: a handle is dereferenced only after it is found here, so a
@@ -330,7 +375,27 @@ SysLayout matvec_layout(Surface* s, int n_vec) {
   return make_layout(go, n, co, nc);
 }
 
-void require_charges(Surface* s) { BIPB_REQUIRE(s->n_rhs > 0, "no charges set"); }
+// Charges passed on the device are checked on the device; the first call that
+// uses them reads the result (and forgets the charges if a check failed).
+void check_device_charges(Surface* s) {
+  if (!s->chg_check_pending) return;
+  int h = 0;
+  BIPB_CUDA(cudaMemcpyAsync(&h, s->chg_err.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  BIPB_CUDA(cudaStreamSynchronize(s->stream));
+  s->chg_check_pending = false;
+  if (h) {
+    s->n_rhs = 0;
+    throw Error(BIPB_ERR_INVALID_ARG, "bipb_charges_set_dev: a charge position or value is not finite, or a "
+                                      "charge sits on a centroid");
+  }
+}
+
+void require_charges(Surface* s) {
+  BIPB_REQUIRE(s->n_rhs > 0, "no charges set");
+  check_device_charges(s);
+}
+
+
 
 }  // namespace
 
@@ -398,6 +463,45 @@ bipb_status bipb_charges_set(bipb_surface h, int64_t nc, const double* pos, int 
     s->nc = nc;
     s->n_pos_sets = n_pos_sets;
     store_charges(s, rec, make_layout(go, n, co, ncv));
+  });
+}
+
+bipb_status bipb_charges_set_dev(bipb_surface h, int64_t nc, const double* pos, int n_pos_sets, int n_rhs,
+                                 const double* q) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(!s->batch, "a batch handle takes its charges through bipb_charges_set_batch");
+    BIPB_REQUIRE(nc >= 1 && nc <= (int64_t)1 << 26, "nc must lie in [1, 2^26]");
+    BIPB_REQUIRE(n_rhs >= 1 && n_rhs <= 4096, "n_rhs must lie in [1, 4096]");
+    BIPB_REQUIRE(n_pos_sets == 1 || n_pos_sets == n_rhs, "n_pos_sets must be 1 or n_rhs");
+    BIPB_REQUIRE(pos && q, "NULL input array");
+    BIPB_REQUIRE((int64_t)n_rhs * nc <= (int64_t)1 << 28, "too many charges in total");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    const CentroidSet& keys = s->part_keys[0];
+    if (s->key_slots.cap == 0) {
+      s->key_slots.ensure(keys.slot.size(), s->stream);
+      BIPB_CUDA(cudaMemcpyAsync(s->key_slots.p, keys.slot.data(), keys.slot.size() * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, s->stream));
+      s->chg_err.ensure(1, s->stream);
+      ++s->alloc_gen;
+    }
+    const int64_t total = (int64_t)n_rhs * nc;
+    s->grow(s->chg, (size_t)total);
+    BIPB_CUDA(cudaMemsetAsync(s->chg_err.p, 0, sizeof(int), s->stream));
+    const double* c = &s->part_center[0];
+    k_charges_dev<<<(unsigned)((total + 255) / 256), 256, 0, s->stream>>>(
+        nc, n_rhs, n_pos_sets, pos, q, c[0], c[1], c[2], s->key_slots.p, keys.mask, s->tgt64.p, s->chg.p,
+        s->chg_err.p);
+    BIPB_LAUNCHED(s);
+    std::vector<int> go(n_rhs, 0), n(n_rhs, (int)s->n), co(n_rhs), ncv(n_rhs, (int)nc);
+    for (int r = 0; r < n_rhs; ++r) co[r] = (int)(r * nc);
+    s->nc = nc;
+    s->n_pos_sets = n_pos_sets;
+    s->lay = make_layout(go, n, co, ncv);
+    s->n_rhs = s->lay.K;
+    s->have_solution = false;
+    s->chg_check_pending = true;
   });
 }
 
@@ -532,6 +636,17 @@ bipb_status bipb_energy(bipb_surface h, double* e_sol) {
   });
 }
 
+bipb_status bipb_energy_dev(bipb_surface h, double* e_sol) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(e_sol != nullptr, "e_sol is NULL");
+    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    BIPB_CUDA(cudaMemcpyAsync(e_sol, s->e_dev.p, s->lay.K * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  });
+}
+
 bipb_status bipb_surface_potential(bipb_surface h, double* phi, double* dphi_dn) {
   return guarded([&] {
     Surface* s = checked(h);
@@ -630,33 +745,72 @@ bipb_status bipb_energy_free(bipb_surface h, double* e_free, double* e_coul) {
   });
 }
 
+namespace {
+// Adjoint solve and gradient pass into device buffers dq (per charge) and dy
+// (3 per charge), internal units; returns BIPB_ERR_NOT_CONVERGED if an
+// adjoint solve missed tol.
+bipb_status energy_grad_device(Surface* s, const bipb_solve_params* p, DevBuf<double>& dq, DevBuf<double>& dy,
+                               size_t* n_chg_out) {
+  validate_params(p);
+  if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
+  const bipb_medium& m = s->solved_medium;
+  BIPB_REQUIRE(p->medium.eps_in == m.eps_in && p->medium.eps_out == m.eps_out && p->medium.kappa == m.kappa,
+               "params.medium differs from the medium of the last solve");
+  const SysLayout& L = s->lay;
+  size_t n_chg = 0;
+  for (int k = 0; k < L.K; ++k) n_chg += L.nc[k];
+  DevBuf<double> c, lam;
+  c.ensure(L.len, s->stream);
+  lam.ensure(L.len, s->stream);
+  dq.ensure(n_chg, s->stream);
+  dy.ensure(3 * n_chg, s->stream);
+  bipb_solve_params pa = *p;
+  pa.x0 = nullptr;
+  energy_row_pass(s, L, m, c.p);
+  std::vector<SolveResult> res = gmres_solve(s, L, m, pa, true, c.p, lam.p, false);
+  bipb_status st = BIPB_OK;
+  for (auto& r : res)
+    if (!r.converged) st = BIPB_ERR_NOT_CONVERGED;
+  grad_pass(s, L, m, s->u.p, lam.p, dq.p, dy.p);
+  *n_chg_out = n_chg;
+  return st;
+}
+}  // namespace
+
+bipb_status bipb_energy_grad_dev(bipb_surface h, const bipb_solve_params* p, double* dE_dq, double* dE_dpos) {
+  bipb_status st = BIPB_OK;
+  bipb_status rc = guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(dE_dq || dE_dpos, "both outputs are NULL");
+    DeviceGuard dg(s->device);
+    StreamJoin sj(s);
+    DevBuf<double> dq, dy;
+    size_t n_chg = 0;
+    st = energy_grad_device(s, p, dq, dy, &n_chg);
+    if (dE_dq) {
+      k_scale<<<(unsigned)((n_chg + 255) / 256), 256, 0, s->stream>>>((int64_t)n_chg, kKcal, dq.p, dE_dq);
+      BIPB_LAUNCHED(s);
+    }
+    if (dE_dpos) {
+      k_scale<<<(unsigned)((3 * n_chg + 255) / 256), 256, 0, s->stream>>>((int64_t)(3 * n_chg), kKcal, dy.p, dE_dpos);
+      BIPB_LAUNCHED(s);
+    }
+  });
+  if (rc != BIPB_OK) return rc;
+  if (st != BIPB_OK) g_last_error = "an adjoint solve did not reach tol within max_iter";
+  return st;
+}
+
 bipb_status bipb_energy_grad(bipb_surface h, const bipb_solve_params* p, double* dE_dq, double* dE_dpos) {
   bipb_status st = BIPB_OK;
   bipb_status rc = guarded([&] {
     Surface* s = checked(h);
-    validate_params(p);
     BIPB_REQUIRE(dE_dq || dE_dpos, "both outputs are NULL");
-    if (!s->have_solution) throw Error(BIPB_ERR_STATE, "bipb_solve has not run since the charges were set");
-    const bipb_medium& m = s->solved_medium;
-    BIPB_REQUIRE(p->medium.eps_in == m.eps_in && p->medium.eps_out == m.eps_out && p->medium.kappa == m.kappa,
-                 "params.medium differs from the medium of the last solve");
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    const SysLayout& L = s->lay;
+    DevBuf<double> dq, dy;
     size_t n_chg = 0;
-    for (int k = 0; k < L.K; ++k) n_chg += L.nc[k];
-    DevBuf<double> c, lam, dq, dy;
-    c.ensure(L.len, s->stream);
-    lam.ensure(L.len, s->stream);
-    dq.ensure(n_chg, s->stream);
-    dy.ensure(3 * n_chg, s->stream);
-    bipb_solve_params pa = *p;
-    pa.x0 = nullptr;
-    energy_row_pass(s, L, m, c.p);
-    std::vector<SolveResult> res = gmres_solve(s, L, m, pa, true, c.p, lam.p, false);
-    for (auto& r : res)
-      if (!r.converged) st = BIPB_ERR_NOT_CONVERGED;
-    grad_pass(s, L, m, s->u.p, lam.p, dq.p, dy.p);
+    st = energy_grad_device(s, p, dq, dy, &n_chg);
     std::vector<double> hq(n_chg), hy(3 * n_chg);
     BIPB_CUDA(cudaMemcpyAsync(hq.data(), dq.p, n_chg * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     BIPB_CUDA(cudaMemcpyAsync(hy.data(), dy.p, 3 * n_chg * sizeof(double), cudaMemcpyDeviceToHost, s->stream));

@@ -318,6 +318,12 @@ struct Surface {
   int n_pos_sets = 0;
   DevBuf<double4_32a> chg;
   DevBuf<float4> chgdf;  // the charges as df64 records (2 float4 each), packed by the source pass
+  // charges passed on the device (bipb_charges_set_dev): the centroid hash
+  // table on the device for the on-centroid check, and the check's flag,
+  // read by the next call that uses the charges
+  DevBuf<int32_t> key_slots;
+  DevBuf<int> chg_err;
+  bool chg_check_pending = false;
   SysLayout lay;   // the systems bipb_solve works on
 
   // surfaces of the handle (one for bipb_surface_create, several for a

@@ -10,8 +10,10 @@ Eq. for E_sol, differentiated at fixed surface):
     dE/dtheta = 1/2 [ (dc/dtheta) . u + lam . (db/dtheta) ],   A u = b,  E = 1/2 c . u
 
 Torch tensors are only the carriers of the inputs and outputs; every step
-runs in libbipb.  ``q`` is (B, Nc) or (Nc,), ``pos`` is (Nc, 3) or
-(B, Nc, 3).
+runs in libbipb.  CUDA tensors go to the library's device entry points
+(bipb_charges_set_dev, bipb_energy_dev, bipb_energy_grad_dev) and never pass
+through the host; CPU tensors go through the host entry points.  ``q`` is
+(B, Nc) or (Nc,), ``pos`` is (Nc, 3) or (B, Nc, 3).
 """
 from __future__ import annotations
 
@@ -21,22 +23,29 @@ import torch
 from . import MIXED, PRECOND_NONE, Surface, solve_params
 
 
+def _set(surface: Surface, q, pos):
+    if q.is_cuda:
+        surface.set_charges_dev(pos.detach().to(torch.float64), q.detach().to(torch.float64))
+    else:
+        surface.set_charges(pos.detach().to(torch.float64).numpy(), q.detach().to(torch.float64).numpy())
+
+
 class BipbEnergy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, q, pos, surface: Surface, params):
         squeeze = q.dim() == 1
-        qn = q.detach().to("cpu", torch.float64).numpy()
-        pn = pos.detach().to("cpu", torch.float64).numpy()
-        surface.set_charges(pn, qn)
+        _set(surface, q, pos)
         surface.solve(params)
-        e = surface.energy()
+        if q.is_cuda:
+            out = surface.energy_dev().to(q.dtype)
+        else:
+            out = torch.as_tensor(surface.energy(), dtype=q.dtype)
         ctx.surface = surface
         ctx.params = params
         ctx.squeeze = squeeze
         ctx.pos_batched = pos.dim() == 3
         ctx.version = surface_version(surface)
         ctx.save_for_backward(q, pos)
-        out = torch.as_tensor(e, dtype=q.dtype, device=q.device)
         return out[0] if squeeze else out
 
     @staticmethod
@@ -44,17 +53,19 @@ class BipbEnergy(torch.autograd.Function):
         q, pos = ctx.saved_tensors
         s = ctx.surface
         if surface_version(s) != ctx.version:  # the handle was used for other charges since forward
-            s.set_charges(pos.detach().to("cpu", torch.float64).numpy(), q.detach().to("cpu", torch.float64).numpy())
+            _set(s, q, pos)
             s.solve(ctx.params)
-        dq, dy = s.energy_grad(ctx.params)
-        g = grad_e.detach().to("cpu", torch.float64).numpy().reshape(-1)
+        if q.is_cuda:
+            dq, dy = s.energy_grad_dev(ctx.params)
+        else:
+            dq, dy = (torch.as_tensor(a) for a in s.energy_grad(ctx.params))
+        g = grad_e.detach().to(torch.float64).reshape(-1)
         gq = dq * g[:, None]
         gy = dy * g[:, None, None]
         if not ctx.pos_batched:
-            gy = gy.sum(axis=0)
-        grad_q = torch.as_tensor(gq[0] if ctx.squeeze else gq, dtype=q.dtype, device=q.device)
-        grad_pos = torch.as_tensor(gy, dtype=pos.dtype, device=pos.device)
-        return grad_q, grad_pos, None, None
+            gy = gy.sum(dim=0)
+        grad_q = (gq[0] if ctx.squeeze else gq).to(q.dtype)
+        return grad_q, gy.to(pos.dtype), None, None
 
 
 def surface_version(surface: Surface):
