@@ -8,8 +8,8 @@
 // CUDA cores generate the kernel tile once,
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i)
 //     [ K4 ds_j   K3 ds_j ]        (row psi_i)     (Sec. 2.2.1, Eqs. 5-6)
-// split every FP32 value a into TF32 parts a_hi = tf32(a), a_lo = tf32(a -
-// a_hi) and store both tiles in shared memory in the K-major core-matrix
+// split every FP32 value a into TF32 parts a_hi = tf32(a), a_lo = a - a_hi
+// and store both tiles in shared memory in the K-major core-matrix
 // layout; the matching U tiles (U_hi, U_lo, packed per chunk in global
 // memory by k_pack_u_tc) arrive by a bulk TMA copy; one thread then issues
 // tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) for A_hi U_hi + A_hi U_lo +
@@ -22,11 +22,12 @@
 // range: summed over thousands of chunks its error grows with the length of
 // the sum and does not average out for smooth vectors (measured on the
 // protein-like surface at N = 81920: 1.7e-4 of the off-diagonal part for
-// phi = 1, against 1.2e-5 for the FP32 CUDA-core mat-vec).  So every chunk
-// starts a fresh accumulator (three TMEM accumulator sets in turn), and while
-// the threads generate chunk c they read the result of chunk c - 2 from TMEM
-// (long finished, the loads overlapping the generation) and add it to FP32
-// registers.  The operator is then
+// phi = 1, against 1.2e-5 for the FP32 CUDA-core mat-vec).  So every group
+// of four chunks (K = 128) starts a fresh accumulator (three TMEM
+// accumulator sets in turn), and while the threads generate the first chunk
+// of group g they read the result of group g - 2 from TMEM (long finished,
+// the loads overlapping the generation) and add it to FP32 registers.  The
+// operator is then
 // accurate to FP32 level and the mixed refinement reaches 1e-8 in two steps.
 // The epilogue writes per-split partial sums that the FP64 reduction of
 // kernels.cu adds, so the kernel tile costs about the same as in the
@@ -55,8 +56,9 @@ constexpr int kOffA = 0;                    // 2 A buffers, each [hi | lo]
 constexpr int kOffB = 4 * kABytes;          // 4 U buffers, each [hi | lo]
 constexpr int kOffS = kOffB + 8 * kBBytes;  // 4 source buffers
 constexpr int kOffBar = kOffS + 4 * kSBytes;
-constexpr int kSmemBytes = kOffBar + 12 * 8 + 16;
-constexpr int kSets = 3;                    // TMEM accumulator sets (chunk c uses set c % 3)
+constexpr int kSmemBytes = kOffBar + 16 * 8 + 16;
+constexpr int kGroup = 4;                   // chunks accumulated in one TMEM set before it is read back
+constexpr int kSets = 3;                    // TMEM accumulator sets (group g uses set g % 3)
 constexpr uint32_t kTmemCols = 512;         // three sets of 2 tiles x 64 columns, rounded to a power of 2
 constexpr long kSpinLimit = 1L << 24;
 
@@ -124,10 +126,12 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
 }
 
-// a -> (tf32(a), tf32(a - tf32(a))); a - tf32(a) is exact in FP32
+// a -> (tf32(a), a - tf32(a)); a - tf32(a) is exact in FP32, and the tensor
+// core reads it as TF32 by dropping its low 13 mantissa bits (an error below
+// 2^-11 of the low part, i.e. about 2^-22 of a)
 __device__ __forceinline__ void split_tf32(float4 a, float4& hi, float4& lo) {
   hi = make_float4(to_tf32(a.x), to_tf32(a.y), to_tf32(a.z), to_tf32(a.w));
-  lo = make_float4(to_tf32(a.x - hi.x), to_tf32(a.y - hi.y), to_tf32(a.z - hi.z), to_tf32(a.w - hi.w));
+  lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
 }
 
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
@@ -147,7 +151,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources of a chunk landed
   uint64_t* ready = full + 4;                                     // 2: A tile of a chunk written (512 arrivals)
-  uint64_t* done = ready + 2;                                     // 3: MMAs of a chunk finished (per set)
+  uint64_t* afree = ready + 2;                                    // 2: MMAs of a chunk finished (per A buffer)
+  uint64_t* done = afree + 2;                                     // 3: MMAs of a group finished (per set)
   uint64_t* drained = done + kSets;                               // 3: accumulator set read back (512 arrivals)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + kSets);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -156,7 +161,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
 
   if (tid == 0) {
     for (int q = 0; q < 4; ++q) tc::mbar_init(&full[q], 1);
-    for (int q = 0; q < 2; ++q) tc::mbar_init(&ready[q], kGenThreads);
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&ready[q], kGenThreads);
+      tc::mbar_init(&afree[q], 1);
+    }
     for (int q = 0; q < kSets; ++q) {
       tc::mbar_init(&done[q], 1);
       tc::mbar_init(&drained[q], kGenThreads);
@@ -190,9 +198,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       if (n_it > 1) issue_load(1);
       const uint32_t idesc = tc::idesc_tf32(128, kNB);
       for (int it = 0; it < n_it; ++it) {
-        const int s = it & 1, q = it & 3, set = it % kSets;
-        // accumulator set: chunk it - 3 read back; tile it written; U of chunk it landed
-        if (it >= kSets) ok = ok && tc::mbar_wait(&drained[set], ((it - kSets) / kSets) & 1, kSpinLimit);
+        const int s = it & 1, q = it & 3, g = it / kGroup, set = g % kSets;
+        const bool first = it % kGroup == 0, last = it % kGroup == kGroup - 1 || it == n_it - 1;
+        // accumulator set: group g - 3 read back; tile it written; U of chunk it landed
+        if (first && g >= kSets) ok = ok && tc::mbar_wait(&drained[set], ((g - kSets) / kSets) & 1, kSpinLimit);
         ok = ok && tc::mbar_wait(&ready[s], (it >> 1) & 1, kSpinLimit);
         ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
         if (!ok) break;
@@ -210,13 +219,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
             const uint64_t a_lo = a_hi + (uint64_t)(kABytes >> 4);
             const uint64_t b_hi = db + (uint64_t)((256 * ks) >> 4);
             const uint64_t b_lo = b_hi + (uint64_t)(kBBytes >> 4);
-            tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, ks > 0 ? 1u : 0u);
+            tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, (ks > 0 || !first) ? 1u : 0u);
             tc::mma_tf32(dcol + m * kNB, a_hi, b_lo, idesc, 1u);
             tc::mma_tf32(dcol + m * kNB, a_lo, b_hi, idesc, 1u);
           }
-        tc::mma_commit(&done[set]);
+        tc::mma_commit(&afree[s]);
+        if (last) tc::mma_commit(&done[set]);
         // U / source buffer (it + 2) & 3 was last read by chunk it - 2: the tile of
-        // chunk it is ready only after every generating thread saw chunk it - 2 done
+        // chunk it is ready only after every generating thread saw chunk it - 2's MMAs done
         if (it + 2 < n_it) issue_load(it + 2);
       }
     }
@@ -231,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     const int row0 = 128 * mb + 2 * lt;
     const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
     const uint32_t tcol = ((uint32_t)(32 * wq) << 16) + wm * kNB + 32 * wh;
-    // synchronous read-back of chunk d (after the loop)
+    // synchronous read-back of group d (after the loop)
     auto drain = [&](int d) {
       ok = ok && tc::mbar_wait(&done[d % kSets], (d / kSets) & 1, kSpinLimit);
       if (!ok) return;
@@ -248,11 +258,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     for (int it = 0; it < n_it; ++it) {
       const int s = it & 1, q = it & 3;
       ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
-      // chunk it - 2: its MMAs read A buffer s, and its accumulators are read back below
-      const int d = it - 2;
+      // chunk it - 2's MMAs read A buffer s
+      if (it >= 2) ok = ok && tc::mbar_wait(&afree[s], ((it - 2) >> 1) & 1, kSpinLimit);
+      // the first chunk of group g reads back group g - 2 (long finished) while it is generated
+      const int d = it % kGroup == 0 ? it / kGroup - 2 : -1;
       if (d >= 0) ok = ok && tc::mbar_wait(&done[d % kSets], (d / kSets) & 1, kSpinLimit);
       if (!ok) break;
-      if (d >= 0) tc::fence_after_sync();
+      if (it >= 2) tc::fence_after_sync();
       const uint32_t dbase = tmem + tcol + ((d + kSets) % kSets) * (2 * kNB);
       const int j0 = (c0 + it) * kChunk;
       const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
@@ -299,7 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       tc::fence_proxy_async_smem();  // this thread's tile stores, visible to the tensor core
       mbar_arrive(&ready[s]);
     }
-    for (int d = max(0, n_it - 2); ok && d < n_it; ++d) drain(d);
+    const int n_groups = (n_it + kGroup - 1) / kGroup;
+    for (int d = max(0, n_groups - 2); ok && d < n_groups; ++d) drain(d);
   }
   const bool all_ok = __syncthreads_and(ok) != 0;
   if (!all_ok && tid == 0) atomicExch(err, 1);

@@ -531,19 +531,24 @@ def test_uneven_batch_one_launch_per_pass(bipb):
 
 
 # ---------------------------------------------------------------- autograd
-def test_autograd_energy_matches_oracle_and_finite_differences(bipb, orc):
+@pytest.mark.parametrize("device", ["cuda", "cpu"])
+def test_autograd_energy_matches_oracle_and_finite_differences(bipb, orc, device):
+    """CUDA tensors take the device entry points (charges, energy and gradient
+    never pass through the host); CPU tensors the host ones."""
     from paper_2312_10044_gb300.torch_ops import SolvationEnergy
 
     p = synth.protein_like_problem(level=3, radius=12.0, n_charges=6, seed=8)
     e_ref, dq_ref, dy_ref = orc.energy_gradient(p, method="direct")
     model = SolvationEnergy(p.centroids, p.normals, p.areas, tol=1e-12, precision=bipb.FP64)
-    q = torch.tensor(p.q[0], dtype=torch.float64, requires_grad=True)
-    pos = torch.tensor(p.charge_pos, dtype=torch.float64, requires_grad=True)
+    q = torch.tensor(p.q[0], dtype=torch.float64, device=device, requires_grad=True)
+    pos = torch.tensor(p.charge_pos, dtype=torch.float64, device=device, requires_grad=True)
     e = model(q, pos)
+    assert e.device.type == device
     e.backward()
+    assert q.grad.device.type == device and pos.grad.device.type == device
     assert e.item() == pytest.approx(e_ref, rel=1e-10)
-    np.testing.assert_allclose(q.grad.numpy(), dq_ref, rtol=1e-8)
-    np.testing.assert_allclose(pos.grad.numpy(), dy_ref, rtol=1e-7, atol=1e-9 * np.abs(dy_ref).max())
+    np.testing.assert_allclose(q.grad.cpu().numpy(), dq_ref, rtol=1e-8)
+    np.testing.assert_allclose(pos.grad.cpu().numpy(), dy_ref, rtol=1e-7, atol=1e-9 * np.abs(dy_ref).max())
     # central differences, h = 1e-4 A, on two atoms
     h = 1e-4
     for k in (0, 3):
@@ -556,6 +561,33 @@ def test_autograd_energy_matches_oracle_and_finite_differences(bipb, orc):
                 em = model(q.detach(), pp).item()
             fd = (ep - em) / (2 * h)
             assert pos.grad[k, a].item() == pytest.approx(fd, rel=1e-5, abs=1e-6 * np.abs(dy_ref).max())
+
+
+def test_device_charges_are_checked_on_the_device(bipb):
+    """bipb_charges_set_dev: the checks of bipb_charges_set run on the device
+    and the next solve reports a failure (and forgets the charges)."""
+    p = synth.born_problem(level=2)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        for bad in (p.centroids[17], np.array([np.nan, 0.0, 0.0])):
+            s.set_charges_dev(_dev(np.stack([[0.0, 0.0, 0.0], bad])), _dev([[1.0, -1.0]]))
+            with pytest.raises(bipb.BipbError) as ei:
+                s.solve(tol=1e-8, precision=bipb.FP64)
+            assert ei.value.status == bipb.BIPB_ERR_INVALID_ARG
+            with pytest.raises(bipb.BipbError):  # the charges are gone
+                s.solve(tol=1e-8, precision=bipb.FP64)
+        # good charges, two configurations with their own positions, match the host path
+        pos = np.array([[[0.1, 0.2, 0.0], [0.3, -0.2, 0.1]], [[0.0, 0.0, 0.5], [-0.4, 0.1, 0.0]]])
+        q = np.array([[1.0, -0.5], [0.3, 0.7]])
+        s.set_charges_dev(_dev(pos), _dev(q))
+        s.solve(tol=1e-12, precision=bipb.FP64)
+        e_dev = s.energy_dev().cpu().numpy()
+        dq_d, dy_d = (t.cpu().numpy() for t in s.energy_grad_dev(tol=1e-12, precision=bipb.FP64))
+        s.set_charges(pos, q)
+        s.solve(tol=1e-12, precision=bipb.FP64)
+        np.testing.assert_array_equal(s.energy(), e_dev)
+        dq_h, dy_h = s.energy_grad(tol=1e-12, precision=bipb.FP64)
+        np.testing.assert_array_equal(dq_h, dq_d)
+        np.testing.assert_array_equal(dy_h, dy_d)
 
 
 def test_autograd_batched_mixed(bipb):
