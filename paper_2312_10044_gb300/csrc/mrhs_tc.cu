@@ -1,37 +1,48 @@
 // Multi-right-hand-side mat-vec on the 5th-generation tensor cores.
 //
 // Y = A U for a block of up to 64 right-hand sides U (2N x B) on one
-// surface.  Per CTA (512 threads, four per target, each generating a quarter
-// of a chunk): 128 targets (two MMA tiles of M = 128 rows: target unknowns
-// phi_i, psi_i interleaved) against a range of source chunks of 16 sources
-// (K = 32 source unknowns phi_j, psi_j interleaved).  For every chunk the
-// CUDA cores generate the kernel tile once,
-//     [ K2 ds_j   K1 ds_j ]        (row phi_i)
-//     [ K4 ds_j   K3 ds_j ]        (row psi_i)     (Sec. 2.2.1, Eqs. 5-6)
-// split every FP32 value a into TF32 parts a_hi = tf32(a), a_lo = a - a_hi
-// and store both tiles in shared memory in the K-major core-matrix
-// layout; the matching U tiles (U_hi, U_lo, packed per chunk in global
-// memory by k_pack_u_tc) arrive by a bulk TMA copy; one thread then issues
-// tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8) for A_hi U_hi + A_hi U_lo +
-// A_lo U_hi into FP32 accumulators in tensor memory, which runs while the
-// next tile is being generated.
+// surface.  Per CTA: 128 targets (two MMA tiles of M = 128 rows: tile 0 the
+// phi_i rows, tile 1 the psi_i rows of the same targets) against a range of
+// source chunks of 16 sources (K = 32 source unknowns phi_j, psi_j
+// interleaved).  For every chunk the CUDA cores generate the kernel tile
+// once,
+//     [ K2 ds_j   K1 ds_j ]        (row phi_i, tile 0)
+//     [ K4 ds_j   K3 ds_j ]        (row psi_i, tile 1)     (Sec. 2.2.1, Eqs. 5-6)
+// split every FP32 value a into TF32 parts (a_hi: a rounded to 11
+// significant bits by Veltkamp's splitting, exact in TF32; a_lo = a - a_hi)
+// and write both into tensor memory, where the MMA reads its A operand: the
+// thread that owns TMEM lane r owns target r's row in both tiles, so it
+// computes a pair's four values once and writes each where it belongs (four
+// threads per target, one quarter of the chunk's sources each).  The U tile
+// of a chunk (U_hi in rows 0..63, U_lo in rows 64..127, packed per chunk in
+// global memory by k_pack_u_tc, K-major core-matrix layout) arrives by a bulk
+// copy into shared memory, and one thread issues, per K step of 8 and tile,
+// two tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8, A in TMEM, B in shared
+// memory): A_hi [U_hi | U_lo] and A_lo [U_hi | U_lo] into one FP32
+// accumulator of 128 columns, whose halves are added when it is read back.
+// That is A_hi U_hi + A_hi U_lo + A_lo U_hi (+ A_lo U_lo) in two MMAs: an
+// M = 128, K = 8 MMA takes as long for N = 128 as for N = 64 (about 96 SM
+// cycles measured on GB300), so this takes two thirds of the tensor-core time of three
+// N = 64 products.  The MMAs run while the next tile is being generated;
+// shared memory carries only the U tiles.
 //
-// Accuracy.  Three TF32 products ("3xTF32") drop only A_lo U_lo and the TF32
-// rounding of the low parts, both about 2^-22 of a product.  The tensor
-// core's FP32 accumulation, however, is not to be run over a whole source
-// range: summed over thousands of chunks its error grows with the length of
-// the sum and does not average out for smooth vectors (measured on the
-// protein-like surface at N = 81920: 1.7e-4 of the off-diagonal part for
-// phi = 1, against 1.2e-5 for the FP32 CUDA-core mat-vec).  So every group
-// of four chunks (K = 128) starts a fresh accumulator (three TMEM
-// accumulator sets in turn), and while the threads generate the first chunk
-// of group g they read the result of group g - 2 from TMEM (long finished,
-// the loads overlapping the generation) and add it to FP32 registers.  The
-// operator is then
-// accurate to FP32 level and the mixed refinement reaches 1e-8 in two steps.
-// The epilogue writes per-split partial sums that the FP64 reduction of
-// kernels.cu adds, so the kernel tile costs about the same as in the
-// single-RHS kernel while serving 64 right-hand sides.
+// TMEM (512 columns; lane r = target r of the CTA): A buffers 0, 1 at columns
+// [0, 128), [128, 256) (tile m at + 64 m: hi part + 0..31, lo part + 32..63);
+// the accumulator of tile m at [256 + 128 m, 384 + 128 m).
+//
+// Accuracy.  The products drop only the TF32 truncation of the low parts,
+// about 2^-22 of a product.  The tensor core's FP32 accumulation, however, is
+// not to be run over a whole source range: summed over thousands of chunks
+// its error grows with the length of the sum and does not average out for
+// smooth vectors (measured on the protein-like surface at N = 81920: 1.7e-4
+// of the off-diagonal part for phi = 1, against 1.2e-5 for the FP32
+// CUDA-core mat-vec).  So every group of eight chunks (K = 256) starts a
+// fresh accumulator: the threads read group g back (and add it to FP32
+// registers) at the second chunk of group g + 1, whose first MMAs wait for
+// that.  The operator is then accurate to FP32 level and the mixed refinement
+// reaches 1e-8 in two steps.  The epilogue writes per-split partial sums that
+// the FP64 reduction of kernels.cu adds, so the kernel tile costs about the
+// same as in the single-RHS kernel while serving 64 right-hand sides.
 //
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
 // flag that the host turns into BIPB_ERR_CUDA, and the kernel still frees its
@@ -49,23 +60,31 @@ constexpr int kNB = 64;          // right-hand sides per launch (MMA N)
 constexpr int kTgt = 128;        // targets per CTA (two M = 128 tiles)
 constexpr int kChunk = 16;       // sources per chunk
 constexpr int kK = 2 * kChunk;   // MMA K per chunk
-constexpr int kABytes = 2 * 128 * kK * 4;   // one TF32 part of the A tile of a chunk (both M tiles): 32 KB
 constexpr int kBBytes = kNB * kK * 4;       // one TF32 part of the U tile of a chunk: 8 KB
 constexpr int kSBytes = kChunk * 32;        // source records of one chunk: 512 B
-constexpr int kOffA = 0;                    // 2 A buffers, each [hi | lo]
-constexpr int kOffB = 4 * kABytes;          // 4 U buffers, each [hi | lo]
-constexpr int kOffS = kOffB + 8 * kBBytes;  // 4 source buffers
-constexpr int kOffBar = kOffS + 4 * kSBytes;
-constexpr int kSmemBytes = kOffBar + 16 * 8 + 16;
-constexpr int kGroup = 4;                   // chunks accumulated in one TMEM set before it is read back
-constexpr int kSets = 3;                    // TMEM accumulator sets (group g uses set g % 3)
-constexpr uint32_t kTmemCols = 512;         // three sets of 2 tiles x 64 columns, rounded to a power of 2
+constexpr int kRing = 8;                    // U and source buffers (chunk it in buffer it % 8)
+constexpr int kOffB = 0;                    // kRing U buffers, each [hi | lo]
+constexpr int kOffS = kOffB + kRing * 2 * kBBytes;  // kRing source buffers
+constexpr int kOffBar = kOffS + kRing * kSBytes;
+constexpr int kSmemBytes = kOffBar + (3 * kRing + 8) * 8 + 16;
+constexpr int kGroup = 8;                   // chunks accumulated in TMEM before it is read back (16 fails the FP32 bound)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColA = 0;               // A buffer s at kColA + 128 s
+constexpr uint32_t kColD = 256;             // accumulator of tile m at kColD + 128 m
 constexpr long kSpinLimit = 1L << 24;
 
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
+}
+
+// a rounded to 11 significant bits (Veltkamp's splitting with the factor
+// 2^13 + 1), exactly representable in TF32; a - split_hi(a) is exact in FP32.
+// The intrinsics keep the compiler from contracting the three operations.
+__device__ __forceinline__ float split_hi(float a) {
+  const float c = __fmul_rn(a, 8193.0f);
+  return __fsub_rn(c, __fsub_rn(c, a));
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -126,19 +145,13 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
 }
 
-// a -> (tf32(a), a - tf32(a)); a - tf32(a) is exact in FP32, and the tensor
-// core reads it as TF32 by dropping its low 13 mantissa bits (an error below
-// 2^-11 of the low part, i.e. about 2^-22 of a)
-__device__ __forceinline__ void split_tf32(float4 a, float4& hi, float4& lo) {
-  hi = make_float4(to_tf32(a.x), to_tf32(a.y), to_tf32(a.z), to_tf32(a.w));
-  lo = make_float4(a.x - hi.x, a.y - hi.y, a.z - hi.z, a.w - hi.w);
-}
-
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
 // Warps 0-15 generate tiles and accumulate; warp 16 (one lane) issues the
 // bulk copies and the MMAs, so no generating warp waits for the issue.
 constexpr int kGenThreads = 512;
-constexpr int kThreads = kGenThreads + 32;
+constexpr int kMmaWarp = kGenThreads / 32;     // warp 16: issues the MMAs (one lane)
+constexpr int kLoadWarp = kMmaWarp + 1;         // warp 17: issues the bulk copies (one lane)
+constexpr int kThreads = kGenThreads + 64;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -149,26 +162,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
                                                     float* __restrict__ part, PairConst<float> c,
                                                     int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOffBar);  // 4: U + sources of a chunk landed
-  uint64_t* ready = full + 4;                                     // 2: A tile of a chunk written (512 arrivals)
+  uint64_t* ufull = reinterpret_cast<uint64_t*>(smem + kOffBar);  // kRing: U tile of a chunk landed
+  uint64_t* sfull = ufull + kRing;                                 // kRing: source records of a chunk landed
+  uint64_t* ready = sfull + kRing;                                // 2: A tile of a chunk in TMEM (16 warp arrivals)
   uint64_t* afree = ready + 2;                                    // 2: MMAs of a chunk finished (per A buffer)
-  uint64_t* done = afree + 2;                                     // 3: MMAs of a group finished (per set)
-  uint64_t* drained = done + kSets;                               // 3: accumulator set read back (512 arrivals)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + kSets);
+  uint64_t* done = afree + 2;                                     // 1: MMAs of a group finished
+  uint64_t* drained = done + 1;                                   // 1: accumulators read back (16 warp arrivals)
+  uint64_t* bfree = drained + 1;                                  // kRing: MMAs of the buffer's chunk finished
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfree + kRing);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, c0 = item.y, c1 = item.z, split = item.w;
 
   if (tid == 0) {
-    for (int q = 0; q < 4; ++q) tc::mbar_init(&full[q], 1);
+    for (int q = 0; q < kRing; ++q) {
+      tc::mbar_init(&ufull[q], 1);
+      tc::mbar_init(&sfull[q], 1);
+      tc::mbar_init(&bfree[q], 1);
+    }
     for (int q = 0; q < 2; ++q) {
-      tc::mbar_init(&ready[q], kGenThreads);
+      tc::mbar_init(&ready[q], kGenThreads / 32);
       tc::mbar_init(&afree[q], 1);
     }
-    for (int q = 0; q < kSets; ++q) {
-      tc::mbar_init(&done[q], 1);
-      tc::mbar_init(&drained[q], kGenThreads);
-    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(drained, kGenThreads / 32);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
@@ -177,154 +194,186 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   const int n_it = c1 - c0;
+  const int n_groups = (n_it + kGroup - 1) / kGroup;
   bool ok = true;
-  // accumulation: TMEM lane quarter wq (the warp's own), tile wm, columns [32 wh, 32 wh + 32)
-  const int wq = warp & 3, wm = (warp >> 2) & 1, wh = (warp >> 3) & 1;
+  // a generating warp: TMEM lane quarter wq (the warp's own)
+  const int wq = warp & 3;
   float acc[32];
 #pragma unroll
   for (int x = 0; x < 32; ++x) acc[x] = 0.f;
 
-  if (warp == kGenThreads / 32) {
-    // ---------------------------------------------------------- issue warp
+  if (warp == kLoadWarp) {
+    // ---------------------------------------------------------- load warp
+    // Chunk x goes into buffer x % kRing once the buffer's previous chunk
+    // x - kRing is finished (its MMAs done, which comes after its sources were
+    // read: its tile was ready before they ran).  The buffer's next phase needs
+    // the copy issued after this wait, so the waits go through every buffer's
+    // phases in order.
     if (lane == 0) {
-      auto issue_load = [&](int it) {  // chunk c0 + it into buffer it & 3
-        const int ch = c0 + it, q = it & 3;
+      for (int x = 0; x < n_it; ++x) {
+        const int q = x % kRing;
+        if (x >= kRing) ok = ok && tc::mbar_wait(&bfree[q], ((x - kRing) / kRing) & 1, kSpinLimit);
+        if (!ok) break;
+        const int ch = c0 + x;
         const int cnt = min(kChunk, n - ch * kChunk);
-        arrive_expect_tx(&full[q], 2 * kBBytes + cnt * 32);
-        bulk_load(smem + kOffB + q * 2 * kBBytes, upk + (int64_t)ch * (2 * kNB * kK), 2 * kBBytes, &full[q]);
-        bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &full[q]);
+        arrive_expect_tx(&sfull[q], cnt * 32);
+        bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &sfull[q]);
+        arrive_expect_tx(&ufull[q], 2 * kBBytes);
+        bulk_load(smem + kOffB + q * 2 * kBBytes, upk + (int64_t)ch * (2 * kNB * kK), 2 * kBBytes, &ufull[q]);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    // ---------------------------------------------------------- MMA warp
+    if (lane == 0) {
+      // N = 128: the U tile's hi rows (0..63) and lo rows (64..127) in one operand
+      const uint32_t idesc = tc::idesc_tf32(128, 2 * kNB);
+      // MMAs p0 .. p1 - 1 of chunk it (p = 2 ks + m: K step ks, tile m)
+      auto issue = [&](int it, int p0, int p1) {
+        const int s = it & 1, q = it % kRing;
+        const bool first = it % kGroup == 0;
+        // descriptor of the chunk's first U core matrices; the others differ only
+        // in the start-address field (bits 0-13, in 16-byte units, no carry)
+        const uint64_t db = tc::smem_desc(tc::smem_u32(smem + kOffB + q * 2 * kBBytes), 128, (kK / 4) * 128);
+#pragma unroll
+        for (int p = 0; p < 2 * (kK / 8); ++p) {
+          if (p < p0 || p >= p1) continue;
+          const int ks = p >> 1, m = p & 1;
+          const uint32_t dcol = tmem + kColD + m * 128;
+          const uint32_t a_hi = tmem + kColA + s * 128 + m * 64 + 8 * ks, a_lo = a_hi + 32;
+          const uint64_t b = db + (uint64_t)((256 * ks) >> 4);
+          // columns 0..63: A_hi U_hi + A_lo U_hi; 64..127: A_hi U_lo + A_lo U_lo
+          tc::mma_tf32_ts(dcol, a_hi, b, idesc, (ks > 0 || !first) ? 1u : 0u);
+          tc::mma_tf32_ts(dcol, a_lo, b, idesc, 1u);
+        }
       };
-      if (n_it > 0) issue_load(0);
-      if (n_it > 1) issue_load(1);
-      const uint32_t idesc = tc::idesc_tf32(128, kNB);
-      for (int it = 0; it < n_it; ++it) {
-        const int s = it & 1, q = it & 3, g = it / kGroup, set = g % kSets;
+      for (int it = 0; it < n_it && ok; ++it) {
+        const int g = it / kGroup;
         const bool first = it % kGroup == 0, last = it % kGroup == kGroup - 1 || it == n_it - 1;
-        // accumulator set: group g - 3 read back; tile it written; U of chunk it landed
-        if (first && g >= kSets) ok = ok && tc::mbar_wait(&drained[set], ((g - kSets) / kSets) & 1, kSpinLimit);
-        ok = ok && tc::mbar_wait(&ready[s], (it >> 1) & 1, kSpinLimit);
-        ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
+        // accumulators: group g - 1 read back; the tile of chunk it in TMEM; its U tile landed
+        if (first && g >= 1) ok = ok && tc::mbar_wait(drained, (g - 1) & 1, kSpinLimit);
+        ok = ok && tc::mbar_wait(&ready[it & 1], (it >> 1) & 1, kSpinLimit);
+        ok = ok && tc::mbar_wait(&ufull[it % kRing], (it / kRing) & 1, kSpinLimit);
         if (!ok) break;
         tc::fence_after_sync();
-        // descriptors of the chunk's first core matrices; the others differ only in
-        // the start-address field (bits 0-13, in 16-byte units, no carry: smem < 256 KB)
-        const uint64_t da = tc::smem_desc(tc::smem_u32(smem + kOffA + s * 2 * kABytes), 128, (kK / 4) * 128);
-        const uint64_t db = tc::smem_desc(tc::smem_u32(smem + kOffB + q * 2 * kBBytes), 128, (kK / 4) * 128);
-        const uint32_t dcol = tmem + set * (2 * kNB);
-#pragma unroll
-        for (int m = 0; m < 2; ++m)
-#pragma unroll
-          for (int ks = 0; ks < kK / 8; ++ks) {
-            const uint64_t a_hi = da + (uint64_t)((m * (kABytes / 2) + 256 * ks) >> 4);
-            const uint64_t a_lo = a_hi + (uint64_t)(kABytes >> 4);
-            const uint64_t b_hi = db + (uint64_t)((256 * ks) >> 4);
-            const uint64_t b_lo = b_hi + (uint64_t)(kBBytes >> 4);
-            tc::mma_tf32(dcol + m * kNB, a_hi, b_hi, idesc, (ks > 0 || !first) ? 1u : 0u);
-            tc::mma_tf32(dcol + m * kNB, a_hi, b_lo, idesc, 1u);
-            tc::mma_tf32(dcol + m * kNB, a_lo, b_hi, idesc, 1u);
-          }
-        tc::mma_commit(&afree[s]);
-        if (last) tc::mma_commit(&done[set]);
-        // U / source buffer (it + 2) & 3 was last read by chunk it - 2: the tile of
-        // chunk it is ready only after every generating thread saw chunk it - 2's MMAs done
-        if (it + 2 < n_it) issue_load(it + 2);
+        issue(it, 0, 8);
+        tc::mma_commit(&afree[it & 1]);
+        tc::mma_commit(&bfree[it % kRing]);
+        if (last) tc::mma_commit(done);
       }
     }
     __syncwarp();
   } else {
     // ---------------------------------------------------------- generating warps
-    // this thread's target: rows 2 lt, 2 lt + 1 of M tile mb; quarter h of each chunk
-    const int mb = (tid >> 6) & 1, lt = tid & 63, h = tid >> 7;
-    const int ti = t0 + (tid & 127);
+    // this thread owns TMEM lane r = 32 wq + lane: target r of the CTA, whose phi
+    // row is row r of tile 0 and whose psi row is row r of tile 1.  It computes
+    // sources 4 sq .. 4 sq + 3 of every chunk and reads back accumulator columns
+    // 32 (sq & 1) .. + 31 of tile sq >> 1.
+    const int sq = warp >> 2;
+    const int ti = t0 + 32 * wq + lane;
     const bool tvalid = ti < n;
     const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
-    const int row0 = 128 * mb + 2 * lt;
-    const bool swap = (lt >> 2) & 1;  // alternate the store order across quarter-warps (no bank conflicts)
-    const uint32_t tcol = ((uint32_t)(32 * wq) << 16) + wm * kNB + 32 * wh;
-    // synchronous read-back of group d (after the loop)
+    const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+    const uint32_t dthr = tmem + lane_base + kColD + (sq >> 1) * 128 + 32 * (sq & 1);
+    const bool tile_edge = t0 + kTgt > n;
+    auto read_back = [&]() {  // acc += the U_hi and U_lo columns of this thread's 32 right-hand sides
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t v[16], w[16];
+        tc::tmem_ld16_async(dthr + 16 * h, v);  // both loads in flight, one wait
+        tc::tmem_ld16_async(dthr + 64 + 16 * h, w);
+        tc::tmem_wait_ld16(v);
+        tc::tmem_wait_ld16(w);
+#pragma unroll
+        for (int x = 0; x < 16; ++x) acc[16 * h + x] += __uint_as_float(v[x]) + __uint_as_float(w[x]);
+      }
+    };
+    // read-back of a group not read back in the loop (after it); the issue
+    // thread may be waiting for it to start the next group
     auto drain = [&](int d) {
-      ok = ok && tc::mbar_wait(&done[d % kSets], (d / kSets) & 1, kSpinLimit);
+      ok = ok && tc::mbar_wait(done, d & 1, kSpinLimit);
       if (!ok) return;
       tc::fence_after_sync();
-      float v[16];
-      const uint32_t base = tmem + tcol + (d % kSets) * (2 * kNB);
-      tc::tmem_ld16(base, v);
-#pragma unroll
-      for (int x = 0; x < 16; ++x) acc[x] += v[x];
-      tc::tmem_ld16(base + 16, v);
-#pragma unroll
-      for (int x = 0; x < 16; ++x) acc[16 + x] += v[x];
+      read_back();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(drained);
     };
+    int drained_groups = 0;
     for (int it = 0; it < n_it; ++it) {
-      const int s = it & 1, q = it & 3;
-      ok = ok && tc::mbar_wait(&full[q], (it >> 2) & 1, kSpinLimit);
+      const int s = it & 1, q = it % kRing;
+      ok = ok && tc::mbar_wait(&sfull[q], (it / kRing) & 1, kSpinLimit);
       // chunk it - 2's MMAs read A buffer s
       if (it >= 2) ok = ok && tc::mbar_wait(&afree[s], ((it - 2) >> 1) & 1, kSpinLimit);
-      // the first chunk of group g reads back group g - 2 (long finished) while it is generated
-      const int d = it % kGroup == 0 ? it / kGroup - 2 : -1;
-      if (d >= 0) ok = ok && tc::mbar_wait(&done[d % kSets], (d / kSets) & 1, kSpinLimit);
+      // the second chunk of group g + 1 reads back group g (its last MMAs were
+      // those of chunk it - 2, just waited for) before its tile is generated: the
+      // first chunk of group g + 1 waits for it
+      const int d = (it % kGroup == 1 && it > kGroup) ? it / kGroup - 1 : -1;
+      if (d >= 0) ok = ok && tc::mbar_wait(done, d & 1, kSpinLimit);
       if (!ok) break;
       if (it >= 2) tc::fence_after_sync();
-      const uint32_t dbase = tmem + tcol + ((d + kSets) % kSets) * (2 * kNB);
-      const int j0 = (c0 + it) * kChunk;
-      const bool edge = !tvalid || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
-      unsigned char* A = smem + kOffA + s * 2 * kABytes;  // hi part; the lo part kABytes further
-      const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
-#pragma unroll
-      for (int kk = 0; kk < kChunk / 8; ++kk) {
-        uint32_t v[16];
-        if (d >= 0) tc::tmem_ld16_async(dbase + 16 * kk, v);  // lands while this part is generated
-        const int kb = (kChunk / 8) * h + kk;
-        float va[4], vb[4];
-        const int ja = j0 + 2 * kb, jb = ja + 1;
-        const bool za = edge && (!tvalid || ja >= n || ja == ti);
-        const bool zb = edge && (!tvalid || jb >= n || jb == ti);
-        kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb], S[4 * kb + 1], za, c, va);
-        kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[4 * kb + 2], S[4 * kb + 3], zb, c, vb);
-        if (za) va[0] = va[1] = va[2] = va[3] = 0.f;
-        if (zb) vb[0] = vb[1] = vb[2] = vb[3] = 0.f;
-        float4 phi_hi, phi_lo, psi_hi, psi_lo;
-        split_tf32(make_float4(va[0], va[1], vb[0], vb[1]), phi_hi, phi_lo);
-        split_tf32(make_float4(va[2], va[3], vb[2], vb[3]), psi_hi, psi_lo);
-        const uint32_t ophi = tc::kmajor_offset(row0, 4 * kb, kK), opsi = tc::kmajor_offset(row0 + 1, 4 * kb, kK);
-        if (swap) {
-          *reinterpret_cast<float4*>(A + opsi) = psi_hi;
-          *reinterpret_cast<float4*>(A + ophi) = phi_hi;
-          *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
-          *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
-        } else {
-          *reinterpret_cast<float4*>(A + ophi) = phi_hi;
-          *reinterpret_cast<float4*>(A + opsi) = psi_hi;
-          *reinterpret_cast<float4*>(A + kABytes + ophi) = phi_lo;
-          *reinterpret_cast<float4*>(A + kABytes + opsi) = psi_lo;
-        }
-        if (d >= 0) {
-          tc::tmem_wait_ld16(v);
-#pragma unroll
-          for (int x = 0; x < 16; ++x) acc[16 * kk + x] += __uint_as_float(v[x]);
-        }
-      }
       if (d >= 0) {
+        read_back();
+        drained_groups = d + 1;
         tc::fence_before_sync();
-        mbar_arrive(&drained[d % kSets]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(drained);
       }
-      tc::fence_proxy_async_smem();  // this thread's tile stores, visible to the tensor core
-      mbar_arrive(&ready[s]);
+      const int j0 = (c0 + it) * kChunk;
+      // chunks at the end of the surface or over the CTA's own targets, and the
+      // last target tile, mask pairs (source past the end, self pair, no target)
+      const bool edge = tile_edge || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
+      const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
+      float ph[8], ps[8];  // the phi-row and psi-row values in K order (k = 2 u + c)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = 4 * sq + u;
+        float v[4];
+        if (edge) {
+          const bool z = !tvalid || j0 + jj >= n || j0 + jj == ti;
+          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], z, c, v);
+          if (z) v[0] = v[1] = v[2] = v[3] = 0.f;
+        } else {
+          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], false, c, v);
+        }
+        ph[2 * u] = v[0], ph[2 * u + 1] = v[1];  // K2, K1
+        ps[2 * u] = v[2], ps[2 * u + 1] = v[3];  // K4, K3
+      }
+      float hi[8];
+      const uint32_t acol = tmem + lane_base + kColA + s * 128 + 8 * sq;
+#pragma unroll
+      for (int x = 0; x < 8; ++x) hi[x] = split_hi(ph[x]);
+      tc::tmem_st8(acol, hi);
+#pragma unroll
+      for (int x = 0; x < 8; ++x) ph[x] -= hi[x];  // the low parts (exact in FP32)
+      tc::tmem_st8(acol + 32, ph);
+      float hs[8];
+#pragma unroll
+      for (int x = 0; x < 8; ++x) hs[x] = split_hi(ps[x]);
+      tc::tmem_st8(acol + 64, hs);
+#pragma unroll
+      for (int x = 0; x < 8; ++x) ps[x] -= hs[x];
+      tc::tmem_st8(acol + 96, ps);
+      tc::tmem_wait_st();
+      tc::fence_before_sync();
+      // one arrival per warp: 512 arrivals on one barrier word would serialise
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ready[s]);
     }
-    const int n_groups = (n_it + kGroup - 1) / kGroup;
-    for (int d = max(0, n_groups - 2); ok && d < n_groups; ++d) drain(d);
+    for (int d = drained_groups; ok && d < n_groups; ++d) drain(d);
   }
   const bool all_ok = __syncthreads_and(ok) != 0;
   if (!all_ok && tid == 0) atomicExch(err, 1);
 
-  // epilogue: TMEM lane r of tile m = row r = target 64 m + r / 2, component r % 2
-  if (all_ok && n_it > 0 && warp < kGenThreads / 32) {
-    const int r = 32 * wq + lane;
-    const int i = t0 + 64 * wm + (r >> 1), comp = r & 1;
+  // epilogue: this thread holds target 32 wq + lane, component sq >> 1 (tile),
+  // right-hand sides 32 (sq & 1) .. + 31
+  if (all_ok && n_it > 0 && warp < kMmaWarp) {
+    const int sq = warp >> 2;
+    const int i = t0 + 32 * wq + lane, comp = sq >> 1;
     if (i < n)
 #pragma unroll
       for (int x = 0; x < 32; ++x) {
-        const int b = 32 * wh + x;
+        const int b = 32 * (sq & 1) + x;
         if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x];
       }
   }
