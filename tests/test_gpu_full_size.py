@@ -9,7 +9,11 @@
   rows agrees with the residual the library reports.
 * The same surface with the split-TF32 tensor-core mat-vec (the batched
   configuration's Krylov operator) against the oracle on sampled rows, for
-  random and smooth right-hand sides.
+  random and smooth right-hand sides; the 64-charge-set solve of the batched
+  configuration and the uneven batch of eight surfaces, each checked by the
+  oracle's residual on sampled rows.
+* The far-field mat-vec on the protein-like surface and the level-7 mixed
+  solve that uses it.
 
 The oracle's level-5 solve takes about half a minute on 16 cores; these
 tests are GPU tests because the library side needs the device.
@@ -193,3 +197,49 @@ def test_mixed_tree_solve_level7_matches_direct_mixed_solve(bipb):
     assert it["converged"] and it["rel_residual"] <= 1e-8 and idr["converged"]
     assert e_tree == pytest.approx(e_dir, rel=1e-7)
     assert np.linalg.norm(phi_tree[0] - phi_dir[0]) / np.linalg.norm(phi_dir[0]) < 1e-7
+
+
+def _sampled_residual_rms(orc, p, u, q_row, pos, rows):
+    eps = p.eps_out / p.eps_in
+    b = orc.source(p.centroids, p.normals, pos, q_row, p.eps_in)
+    r = b[rows] - orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, u, rows)
+    return np.sqrt(np.mean(r * r)), np.linalg.norm(b) / np.sqrt(b.shape[0])
+
+
+def test_batched_64_rhs_tf32_solve_true_residual_on_sampled_rows(bipb, orc):
+    """The batched configuration at full size: 64 charge sets of 2000 charges
+    on the protein-like surface (N = 81920), solved together with the
+    tensor-core Krylov mat-vec (MIXED_TF32) to 1e-8.  For four of them the
+    oracle recomputes b - A u on 128 sampled rows: RMS within twice that of
+    a residual of 1e-8 ||b||."""
+    base = synth.protein_like_problem()
+    batch = synth.batched_charges(base, n_rhs=64, n_charges=2000)
+    with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
+        s.set_charges(batch.charge_pos, batch.q)
+        info = s.solve(eps_in=batch.eps_in, eps_out=batch.eps_out, kappa=batch.kappa, tol=1e-8,
+                       precision=bipb.MIXED_TF32)
+        phi, dphi = s.surface_potential()
+    assert all(i["converged"] and i["rel_residual"] <= 1e-8 for i in info)
+    rows = np.sort(np.random.default_rng(63).choice(2 * batch.n, 128, replace=False))
+    for r in (0, 21, 42, 63):
+        u = np.concatenate([phi[r], dphi[r]]) / bipb.KCAL
+        rms, scale = _sampled_residual_rms(orc, batch, u, batch.q[r], batch.charge_pos[r], rows)
+        assert rms <= 2e-8 * scale, (r, rms / scale, info[r]["rel_residual"])
+
+
+def test_uneven_batch_solve_true_residual_on_sampled_rows(bipb, orc):
+    """The uneven batch at full size: eight displaced spheres of 5120 to 81920
+    elements in one handle, solved together (MIXED_DF64) to 1e-8; the oracle
+    recomputes every surface's residual on 128 sampled rows."""
+    probs = synth.uneven_batch_problems()
+    with bipb.BatchSurface([(p.centroids, p.normals, p.areas) for p in probs]) as s:
+        s.set_charges([(p.charge_pos, p.q[0]) for p in probs])
+        info = s.solve(eps_in=probs[0].eps_in, eps_out=probs[0].eps_out, kappa=probs[0].kappa, tol=1e-8,
+                       precision=bipb.MIXED_DF64)
+        phi, dphi = s.surface_potential()
+    assert len(info) == 8 and all(i["converged"] and i["rel_residual"] <= 1e-8 for i in info)
+    for k, p in enumerate(probs):
+        rows = np.sort(np.random.default_rng(70 + k).choice(2 * p.n, 128, replace=False))
+        u = np.concatenate([phi[k], dphi[k]]) / bipb.KCAL
+        rms, scale = _sampled_residual_rms(orc, p, u, p.q[0], p.charge_pos, rows)
+        assert rms <= 2e-8 * scale, (k, rms / scale, info[k]["rel_residual"])
