@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--no-config3", action="store_true", help="skip the protein-like (N = 81920) solves")
+    ap.add_argument("--inner", default="direct", choices=["direct", "tree"],
+                    help="Krylov mat-vec of the step's mixed solve: the direct FP32 sum (the paper's pipeline) or "
+                         "the far-field treecode of Sec. 2.2.3 (MIXED_TREE; the residual stays direct)")
     ap.add_argument("--precond", default="none", choices=["none", "self"],
                     help="preconditioner of the step's solve (none: the paper's GPU pipeline; self: element "
                          "self blocks of Sec. 2.2.4)")
@@ -675,7 +678,7 @@ def main():
     prob, desc = workload(args.workload)
     n, nc = prob.n, prob.nc
     params = bipb.solve_params(prob.eps_in, prob.eps_out, prob.kappa, tol=TOL, restart=10,
-                               precision=bipb.MIXED_DF64,
+                               precision=bipb.MIXED_TREE if args.inner == "tree" else bipb.MIXED_DF64,
                                precond=bipb.PRECOND_SELF if args.precond == "self" else bipb.PRECOND_NONE)
     s = bipb.Surface(prob.centroids, prob.normals, prob.areas)
     s.set_charges(prob.charge_pos, prob.q)
@@ -722,18 +725,23 @@ def main():
     info0 = infos[-1][0]
     mv = info0["matvecs32"] + info0["matvecs64"]
     pairs_step = mv * n * (n - 1) + 2 * n * nc
+    tree_pairs = None
+    if args.inner == "tree":  # the Krylov mat-vecs evaluate the far-field operator's pairs only
+        tree_pairs = s.treecode_stats()[0]
+        pairs_step = info0["matvecs32"] * tree_pairs + info0["matvecs64"] * n * (n - 1) + 2 * n * nc
     value = replicas.whole_job_rate(args.steps * pairs_step, world, total_ms / 1e3) / 1e9
 
     # ---- dominant kernel and its roofline (from the events around each launch)
-    dom = max(timers, key=lambda k: timers[k][1])
+    # the dominant kernel; with the far-field Krylov mat-vec, the roofline is that kernel's
+    dom = "matvec_tree" if args.inner == "tree" else max(timers, key=lambda k: timers[k][1])
     cnt, tms = timers[dom]
     # launches that found their system converged return at once; average over the effective ones
-    eff = {"matvec32": info0["matvecs32"] * args.steps}.get(dom, cnt)
+    eff = {"matvec32": info0["matvecs32"] * args.steps, "matvec_tree": info0["matvecs32"] * args.steps}.get(dom, cnt)
     avg_ms = tms / max(min(cnt, eff), 1)
     f_mhz = clocks["sm_mhz"] if clocks else 2070.0
     lanes = FP64_LANES_PER_SM if dom.startswith("matvec64") else FP32_LANES_PER_SM
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    pairs_launch = n * (n - 1)
+    pairs_launch = tree_pairs if dom == "matvec_tree" else n * (n - 1)
     fp32 = lanes == FP32_LANES_PER_SM
     lanes_meas = FFMA_LANES_PER_SM_MEASURED if fp32 else lanes
     achieved = pairs_launch * PAIR_FLOPS / (avg_ms / 1e3) / 1e12
@@ -864,7 +872,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": desc, "n": n, "nc": nc, "tol": TOL, "restart": 10, "l2": "flushed",
                            "parallelism": f"replicas{world}", "matvec32_variant": variant,
-                           "precond": args.precond},
+                           "precond": args.precond, "inner": args.inner},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks}
         line.update(extra)
