@@ -756,7 +756,8 @@ def main():
     roofline = {"bound": "alu", "kernel": f"{dom} pair kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "pipe": "fp32" if fp32 else "fp64",
-                "definition": f"achieved = {PAIR_FLOPS} flops x N(N-1) ordered pairs per launch / mean launch time; "
+                "definition": f"achieved = {PAIR_FLOPS} flops x {pairs_launch} ordered (target, source) pairs per "
+                              "launch / mean launch time; "
                               f"peak = {nsm} SMs x {lanes_meas:.1f} measured {'FFMA' if fp32 else 'DFMA'} lanes per "
                               f"SM per clock x 2 flop x {f_mhz:.0f} MHz (median SM clock sampled in the timed "
                               "region); the symmetric kernel evaluates each unordered pair once for both rows, so "
