@@ -299,8 +299,12 @@ struct Surface {
   // per-pass scratch
   DevBuf<float4> rec32;
   DevBuf<float4> recdf;
-  DevBuf<float> upk;   // TF32 right-hand-side tiles of the tensor-core mat-vec
+  DevBuf<float> upk;   // FP16 right-hand-side tiles of the tensor-core mat-vec (raw storage)
   DevBuf<int> tc_err;  // set by the tensor-core kernel when a bounded wait ran out
+  DevBuf<unsigned> tc_colmax;  // tensor-core mat-vec: max |u| per right-hand side (FP32 bits)
+  DevBuf<int2> tc_rowexp;      // tensor-core mat-vec: per-row scale exponents of the phi and psi rows
+  float tc_rowexp_key[3] = {0.f, 0.f, -1.f};  // the medium (eps, 1/eps, kappa) tc_rowexp was computed for
+  int tc_rowexp_n = -1;
   DevBuf<double4_32a> rec64;
   DevBuf<float> part32;
   DevBuf<double> part64;

@@ -8,45 +8,57 @@
 // once,
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i, tile 0)
 //     [ K4 ds_j   K3 ds_j ]        (row psi_i, tile 1)     (Sec. 2.2.1, Eqs. 5-6)
-// split every FP32 value a into TF32 parts (a_hi: a rounded to 11
-// significant bits by Veltkamp's splitting, exact in TF32; a_lo = a - a_hi)
-// and write both into tensor memory, where the MMA reads its A operand: the
-// thread that owns TMEM lane r owns target r's row in both tiles, so it
-// computes a pair's four values once and writes each where it belongs (four
-// threads per target, one quarter of the chunk's sources each).  The U tile
-// of a chunk (U_hi in rows 0..63, U_lo in rows 64..127, packed per chunk in
-// global memory by k_pack_u_tc, K-major core-matrix layout) arrives by a bulk
-// copy into shared memory, and one thread issues, per K step of 8 and tile,
-// two tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8, A in TMEM, B in shared
-// memory): A_hi [U_hi | U_lo] and A_lo [U_hi | U_lo] into one FP32
-// accumulator of 128 columns, whose halves are added when it is read back.
-// That is A_hi U_hi + A_hi U_lo + A_lo U_hi (+ A_lo U_lo) in two MMAs: an
-// M = 128, K = 8 MMA takes as long for N = 128 as for N = 64 (about 96 SM
-// cycles measured on GB300), so this takes two thirds of the tensor-core time of three
-// N = 64 products.  The MMAs run while the next tile is being generated;
-// shared memory carries only the U tiles.
+// in FP32, scale every row by a power of two (below), split each value a into
+// two FP16 parts (a_hi = a rounded to FP16, a_lo = a - a_hi rounded to FP16:
+// 22 significant bits together) and write both into tensor memory, where the
+// MMA reads its A operand: the thread that owns TMEM lane r owns target r's
+// row in both tiles, so it computes a pair's four values once and writes each
+// where it belongs (four threads per target, one quarter of the chunk's
+// sources each).  The U tile of a chunk (U_hi in rows 0..63, U_lo in rows
+// 64..127, each column scaled by a power of two; packed per chunk in global
+// memory by k_pack_u_tc, K-major core-matrix layout) arrives by a bulk copy
+// into shared memory, and one thread issues, per K step of 16 and tile, two
+// tcgen05.mma kind::f16 (M = 128, N = 128, K = 16, A in TMEM, B in shared
+// memory, FP32 accumulator): A_hi [U_hi | U_lo] and A_lo [U_hi | U_lo] into
+// one accumulator of 128 columns, whose halves are added when it is read back.
+// That is A_hi U_hi + A_hi U_lo + A_lo U_hi (+ A_lo U_lo) in two MMAs.  On
+// GB300 an M = 128, N = 128 MMA takes about 117 SM cycles with K = 16 in FP16
+// and 111 with K = 8 in TF32 (measured, one thread issuing back to back), so
+// the FP16 split needs half the tensor-core time of a TF32 split of the same
+// accuracy.  The MMAs run while the next tiles are being generated (four A
+// buffers); shared memory carries only the U tiles.
 //
-// TMEM (512 columns; lane r = target r of the CTA): A buffers 0, 1 at columns
-// [0, 128), [128, 256) (tile m at + 64 m: hi part + 0..31, lo part + 32..63);
-// the accumulator of tile m at [256 + 128 m, 384 + 128 m).
+// Scaling.  FP16 holds 2^-14 .. 65504 at full precision, so both operands are
+// brought to a known range by exact powers of two: row i of tile m is
+// multiplied by 2^e(i, m), chosen once per surface and medium (k_tc_rowexp,
+// over all sources) so that its largest value lies in [2^14, 2^15), and
+// column b of U by 2^f(b), chosen per call from max |u_b| the same way.  The
+// epilogue multiplies each accumulated sum by 2^-(e + f).  A value far below
+// its row's largest loses relative precision in a_lo (FP16 subnormals), but
+// its absolute error stays below 2^-40 of that largest value.
 //
-// Accuracy.  The products drop only the TF32 truncation of the low parts,
-// about 2^-22 of a product.  The tensor core's FP32 accumulation, however, is
-// not to be run over a whole source range: summed over thousands of chunks
-// its error grows with the length of the sum and does not average out for
-// smooth vectors (measured on the protein-like surface at N = 81920: 1.7e-4
-// of the off-diagonal part for phi = 1, against 1.2e-5 for the FP32
-// CUDA-core mat-vec).  So every group of eight chunks (K = 256) starts a
-// fresh accumulator: the threads read group g back (and add it to FP32
-// registers) at the second chunk of group g + 1, whose first MMAs wait for
-// that.  The operator is then accurate to FP32 level and the mixed refinement
-// reaches 1e-8 in two steps.  The epilogue writes per-split partial sums that
-// the FP64 reduction of kernels.cu adds, so the kernel tile costs about the
-// same as in the single-RHS kernel while serving 64 right-hand sides.
+// TMEM (512 columns; lane r = target r of the CTA): A buffers 0..3 at columns
+// 64 s (tile m at + 32 m: hi part + 0..15, lo part + 16..31, two FP16 values
+// per column); the accumulator of tile m at [256 + 128 m, 384 + 128 m).
+//
+// Accuracy.  The tensor core's FP32 accumulation is not to be run over a
+// whole source range: summed over thousands of chunks its error grows with
+// the length of the sum and does not average out for smooth vectors
+// (measured on the protein-like surface at N = 81920: 1.7e-4 of the
+// off-diagonal part for phi = 1, against 1.2e-5 for the FP32 CUDA-core
+// mat-vec).  So every group of eight chunks (K = 256) starts a fresh
+// accumulator: the threads read group g back (and add it to FP32 registers)
+// at the second chunk of group g + 1, whose first MMAs wait for that.  The
+// operator is then accurate to FP32 level and the mixed refinement reaches
+// 1e-8 in two steps.  The epilogue writes per-split partial sums that the
+// FP64 reduction of kernels.cu adds, so the kernel tile costs about the same
+// as in the single-RHS kernel while serving 64 right-hand sides.
 //
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
 // flag that the host turns into BIPB_ERR_CUDA, and the kernel still frees its
 // tensor memory.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -56,35 +68,43 @@ namespace bipb {
 
 namespace {
 
-constexpr int kNB = 64;          // right-hand sides per launch (MMA N)
-constexpr int kTgt = 128;        // targets per CTA (two M = 128 tiles)
-constexpr int kChunk = 16;       // sources per chunk
-constexpr int kK = 2 * kChunk;   // MMA K per chunk
-constexpr int kBBytes = kNB * kK * 4;       // one TF32 part of the U tile of a chunk: 8 KB
+constexpr int kNB = 64;                     // right-hand sides per launch (MMA N = 2 kNB: hi and lo parts)
+constexpr int kTgt = 128;                   // targets per CTA (two M = 128 tiles)
+constexpr int kChunk = 16;                  // sources per chunk
+constexpr int kK = 2 * kChunk;              // MMA K per chunk (two K steps of 16)
+constexpr int kPartBytes = kNB * kK * 2;    // one FP16 part of the U tile of a chunk: 4 KB
+constexpr int kUBytes = 2 * kPartBytes;     // [U_hi | U_lo] of a chunk: 128 rows of 64 bytes
 constexpr int kSBytes = kChunk * 32;        // source records of one chunk: 512 B
 constexpr int kRing = 8;                    // U and source buffers (chunk it in buffer it % 8)
-constexpr int kOffB = 0;                    // kRing U buffers, each [hi | lo]
-constexpr int kOffS = kOffB + kRing * 2 * kBBytes;  // kRing source buffers
-constexpr int kOffBar = kOffS + kRing * kSBytes;
-constexpr int kSmemBytes = kOffBar + (3 * kRing + 8) * 8 + 16;
+constexpr int kABuf = 4;                    // A buffers in TMEM (chunk it in buffer it % 4)
+constexpr int kOffB = 0;                    // kRing U buffers
+constexpr int kOffS = kOffB + kRing * kUBytes;      // kRing source buffers
+constexpr int kOffCol = kOffS + kRing * kSBytes;    // kNB column unscale factors
+constexpr int kOffBar = kOffCol + kNB * 4;
+constexpr int kNumBars = 3 * kRing + 2 * kABuf + 2;
+constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
 constexpr int kGroup = 8;                   // chunks accumulated in TMEM before it is read back (16 fails the FP32 bound)
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColA = 0;               // A buffer s at kColA + 128 s
+constexpr uint32_t kColA = 0;               // A buffer s at kColA + 64 s
 constexpr uint32_t kColD = 256;             // accumulator of tile m at kColD + 128 m
-constexpr long kSpinLimit = 1L << 24;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait longer than 2 s is an error
+constexpr int kScaleTop = 14;               // scaled magnitudes lie in [2^14, 2^15)
+constexpr int kScaleClamp = 64;             // scale exponents are clamped to [-64, 64]
+static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
 
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+// The exponent e that brings a magnitude m into [2^14, 2^15) by m 2^e,
+// clamped to [-64, 64]; 64 for zero (and for FP32 subnormals).
+__device__ __forceinline__ int scale_exp(float m) {
+  const int lg = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m) for normal m
+  return max(-kScaleClamp, min(kScaleClamp, kScaleTop - lg));
 }
+// 2^k for |k| <= 126
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(127 + k) << 23); }
 
-// a rounded to 11 significant bits (Veltkamp's splitting with the factor
-// 2^13 + 1), exactly representable in TF32; a - split_hi(a) is exact in FP32.
-// The intrinsics keep the compiler from contracting the three operations.
-__device__ __forceinline__ float split_hi(float a) {
-  const float c = __fmul_rn(a, 8193.0f);
-  return __fsub_rn(c, __fsub_rn(c, a));
+// byte offset of element (row, k) of a chunk's FP16 U tile (K = 32, K-major,
+// no swizzle): core matrices of 8 rows x 8 values (16 bytes a row)
+__host__ __device__ __forceinline__ uint32_t kmajor16_offset(int row, int k) {
+  return (uint32_t)((((row >> 3) * (kK >> 3) + (k >> 3)) * 8 + (row & 7)) * 16 + (k & 7) * 2);
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -98,31 +118,47 @@ __device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) 
                : "memory");
 }
 
-// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, the TF32 tiles U_hi
-// and U_lo (one after the other) in the K-major core-matrix layout (row =
-// right-hand side, K = 2 j' + c).
-__global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __restrict__ u, float* __restrict__ upk) {
+// colmax[b] = max_e |u_b[e]| (as FP32 bits; colmax zeroed before): grid (x, nb)
+__global__ void k_colmax_u(int64_t len, const double* __restrict__ u, unsigned* __restrict__ colmax) {
+  const int b = blockIdx.y;
+  const double* ub = u + (int64_t)b * len;
+  float m = 0.f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf((float)ub[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(colmax + b, __float_as_uint(m));
+}
+
+// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, u 2^f(b) split into
+// FP16 parts U_hi (rows 0..63) and U_lo (rows 64..127) in the K-major
+// core-matrix layout (row = right-hand side, K = 2 j' + c).
+__global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __restrict__ u,
+                            const unsigned* __restrict__ colmax, __half* __restrict__ upk) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one per (chunk, b, k)
   if (e >= (int64_t)n_chunks * kNB * kK) return;
   const int ch = (int)(e / (kNB * kK));
   const int rem = (int)(e % (kNB * kK));
   const int b = rem / kK, k = rem % kK;
   const int j = ch * kChunk + (k >> 1), c = k & 1;
-  float hi = 0.f, lo = 0.f;
+  __half hi = __float2half_rn(0.f), lo = hi;
   if (b < n_rhs && j < n) {
-    const double v = u[(int64_t)b * 2 * n + (int64_t)c * n + j];
-    hi = to_tf32((float)v);
-    lo = to_tf32((float)(v - (double)hi));
+    const double v = u[(int64_t)b * 2 * n + (int64_t)c * n + j] * (double)pow2f(scale_exp(__uint_as_float(colmax[b])));
+    hi = __float2half_rn((float)v);
+    lo = __float2half_rn((float)(v - (double)__half2float(hi)));
   }
-  float* tile = upk + (int64_t)ch * (2 * kNB * kK);
-  tile[tc::kmajor_offset(b, k, kK) / 4] = hi;
-  tile[kNB * kK + tc::kmajor_offset(b, k, kK) / 4] = lo;
+  unsigned char* tile = reinterpret_cast<unsigned char*>(upk) + (int64_t)ch * kUBytes;
+  *reinterpret_cast<__half*>(tile + kmajor16_offset(b, k)) = hi;
+  *reinterpret_cast<__half*>(tile + kmajor16_offset(kNB + b, k)) = lo;
 }
 
 // The four kernel values of pair (target i, source j) times ds_j (times 4 pi),
 // in FP32: returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3].
+// With rs0 = rs1 = 1 the values are unscaled; otherwise (K2, K1) come times
+// rs0 and (K4, K3) times rs1 (powers of two: the scaling is exact).
 __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float nxi, float nyi, float nzi, float4 g,
-                                             float4 nv, bool zero, const PairConst<float>& c, float* v) {
+                                             float4 nv, bool zero, const PairConst<float>& c, float* v,
+                                             float rs0 = 1.f, float r10 = 1.f) {
   const float dx = xi - g.x, dy = yi - g.y, dz = zi - g.z;
   const float r2 = dx * dx + dy * dy + dz * dz;
   float s = fminf(rsqrt_approx(r2), kSMaxF);
@@ -136,18 +172,56 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   const float t = e * kr + e;
   const float tm1 = t - 1.f;
   const float wm3 = (t - e) * kr + 3.f * tm1;
-  const float sa = s * g.w;
+  const float sa = (s * g.w) * rs0;
   const float s2 = s * s;
   const float s3a = s2 * sa;
+  const float s3b = s3a * r10;
   v[1] = sa - e * sa;                                  // K1 ds = (1 - e) s ds
   v[0] = ((c.eps * t - 1.f) * cj) * s3a;               // K2 ds
-  v[3] = ((t * c.inveps - 1.f) * ci) * s3a;            // K3 ds
-  v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
+  v[3] = ((t * c.inveps - 1.f) * ci) * s3b;            // K3 ds
+  v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3b;   // K4 ds
+}
+
+// Row scale exponents: for target i, e(i, 0) from the largest |K2 ds|, |K1 ds|
+// and e(i, 1) from the largest |K4 ds|, |K3 ds| over all sources j != i (the
+// same FP32 values the tensor-core kernel generates).  One thread per target.
+__global__ void __launch_bounds__(128) k_tc_rowexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
+                                                   int2* __restrict__ rowexp) {
+  __shared__ float4 sh[2 * 128];
+  const int i = blockIdx.x * 128 + threadIdx.x;
+  const int ii = min(i, n - 1);
+  const float4 gi = tgt32[2 * ii], ni = tgt32[2 * ii + 1];
+  float m0 = 0.f, m1 = 0.f;
+  for (int j0 = 0; j0 < n; j0 += 128) {
+    __syncthreads();
+    const int jl = min(j0 + (int)threadIdx.x, n - 1);
+    sh[2 * threadIdx.x] = tgt32[2 * jl];
+    sh[2 * threadIdx.x + 1] = tgt32[2 * jl + 1];
+    __syncthreads();
+    const int cnt = min(128, n - j0);
+    for (int jj = 0; jj < cnt; ++jj) {
+      float v[4];
+      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, sh[2 * jj], sh[2 * jj + 1], j0 + jj == ii, c, v);
+      m0 = fmaxf(m0, fmaxf(fabsf(v[0]), fabsf(v[1])));
+      m1 = fmaxf(m1, fmaxf(fabsf(v[2]), fabsf(v[3])));
+    }
+  }
+  if (i < n) rowexp[i] = make_int2(scale_exp(m0), scale_exp(m1));
+}
+
+// two FP32 values (the lower k first) as FP16 parts: hi = round(a), lo = round(a - hi)
+__device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a0, a1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
-// Warps 0-15 generate tiles and accumulate; warp 16 (one lane) issues the
-// bulk copies and the MMAs, so no generating warp waits for the issue.
+// Warp specialisation: warps 0..15 generate the kernel tiles (and read the
+// accumulators back), warp 16 issues the MMAs, warp 17 the bulk copies, so no
+// generating warp waits for the issue.
 constexpr int kGenThreads = 512;
 constexpr int kMmaWarp = kGenThreads / 32;     // warp 16: issues the MMAs (one lane)
 constexpr int kLoadWarp = kMmaWarp + 1;         // warp 17: issues the bulk copies (one lane)
@@ -158,18 +232,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
-                                                    const float4* __restrict__ tgt32, const float* __restrict__ upk,
-                                                    float* __restrict__ part, PairConst<float> c,
-                                                    int* __restrict__ err) {
+                                                    const float4* __restrict__ tgt32, const int2* __restrict__ rowexp,
+                                                    const unsigned* __restrict__ colmax,
+                                                    const __half* __restrict__ upk, float* __restrict__ part,
+                                                    PairConst<float> c, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   uint64_t* ufull = reinterpret_cast<uint64_t*>(smem + kOffBar);  // kRing: U tile of a chunk landed
   uint64_t* sfull = ufull + kRing;                                 // kRing: source records of a chunk landed
-  uint64_t* ready = sfull + kRing;                                // 2: A tile of a chunk in TMEM (16 warp arrivals)
-  uint64_t* afree = ready + 2;                                    // 2: MMAs of a chunk finished (per A buffer)
-  uint64_t* done = afree + 2;                                     // 1: MMAs of a group finished
-  uint64_t* drained = done + 1;                                   // 1: accumulators read back (16 warp arrivals)
-  uint64_t* bfree = drained + 1;                                  // kRing: MMAs of the buffer's chunk finished
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfree + kRing);
+  uint64_t* bfree = sfull + kRing;                                 // kRing: MMAs of the buffer's chunk finished
+  uint64_t* ready = bfree + kRing;                                 // kABuf: A tile of a chunk in TMEM (16 warp arrivals)
+  uint64_t* afree = ready + kABuf;                                 // kABuf: MMAs of a chunk finished (per A buffer)
+  uint64_t* done = afree + kABuf;                                  // 1: MMAs of a group finished
+  uint64_t* drained = done + 1;                                    // 1: accumulators read back (16 warp arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
+  float* cinv = reinterpret_cast<float*>(smem + kOffCol);          // 2^-f(b)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, c0 = item.y, c1 = item.z, split = item.w;
@@ -180,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       tc::mbar_init(&sfull[q], 1);
       tc::mbar_init(&bfree[q], 1);
     }
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kABuf; ++q) {
       tc::mbar_init(&ready[q], kGenThreads / 32);
       tc::mbar_init(&afree[q], 1);
     }
@@ -188,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     tc::mbar_init(drained, kGenThreads / 32);
     tc::fence_mbar_init();
   }
+  if (tid < kNB) cinv[tid] = pow2f(-scale_exp(__uint_as_float(colmax[tid])));
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::fence_before_sync();
   __syncthreads();
@@ -212,14 +289,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     if (lane == 0) {
       for (int x = 0; x < n_it; ++x) {
         const int q = x % kRing;
-        if (x >= kRing) ok = ok && tc::mbar_wait(&bfree[q], ((x - kRing) / kRing) & 1, kSpinLimit);
+        if (x >= kRing) ok = ok && tc::mbar_wait_timed(&bfree[q], ((x - kRing) / kRing) & 1, kWaitLimitNs);
         if (!ok) break;
         const int ch = c0 + x;
         const int cnt = min(kChunk, n - ch * kChunk);
         arrive_expect_tx(&sfull[q], cnt * 32);
         bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &sfull[q]);
-        arrive_expect_tx(&ufull[q], 2 * kBBytes);
-        bulk_load(smem + kOffB + q * 2 * kBBytes, upk + (int64_t)ch * (2 * kNB * kK), 2 * kBBytes, &ufull[q]);
+        arrive_expect_tx(&ufull[q], kUBytes);
+        bulk_load(smem + kOffB + q * kUBytes, reinterpret_cast<const unsigned char*>(upk) + (int64_t)ch * kUBytes,
+                  kUBytes, &ufull[q]);
       }
     }
     __syncwarp();
@@ -227,38 +305,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     // ---------------------------------------------------------- MMA warp
     if (lane == 0) {
       // N = 128: the U tile's hi rows (0..63) and lo rows (64..127) in one operand
-      const uint32_t idesc = tc::idesc_tf32(128, 2 * kNB);
-      // MMAs p0 .. p1 - 1 of chunk it (p = 2 ks + m: K step ks, tile m)
-      auto issue = [&](int it, int p0, int p1) {
-        const int s = it & 1, q = it % kRing;
-        const bool first = it % kGroup == 0;
-        // descriptor of the chunk's first U core matrices; the others differ only
-        // in the start-address field (bits 0-13, in 16-byte units, no carry)
-        const uint64_t db = tc::smem_desc(tc::smem_u32(smem + kOffB + q * 2 * kBBytes), 128, (kK / 4) * 128);
-#pragma unroll
-        for (int p = 0; p < 2 * (kK / 8); ++p) {
-          if (p < p0 || p >= p1) continue;
-          const int ks = p >> 1, m = p & 1;
-          const uint32_t dcol = tmem + kColD + m * 128;
-          const uint32_t a_hi = tmem + kColA + s * 128 + m * 64 + 8 * ks, a_lo = a_hi + 32;
-          const uint64_t b = db + (uint64_t)((256 * ks) >> 4);
-          // columns 0..63: A_hi U_hi + A_lo U_hi; 64..127: A_hi U_lo + A_lo U_lo
-          tc::mma_tf32_ts(dcol, a_hi, b, idesc, (ks > 0 || !first) ? 1u : 0u);
-          tc::mma_tf32_ts(dcol, a_lo, b, idesc, 1u);
-        }
-      };
+      const uint32_t idesc = tc::idesc_f16(128, 2 * kNB);
       for (int it = 0; it < n_it && ok; ++it) {
-        const int g = it / kGroup;
+        const int g = it / kGroup, s = it % kABuf, q = it % kRing;
         const bool first = it % kGroup == 0, last = it % kGroup == kGroup - 1 || it == n_it - 1;
         // accumulators: group g - 1 read back; the tile of chunk it in TMEM; its U tile landed
-        if (first && g >= 1) ok = ok && tc::mbar_wait(drained, (g - 1) & 1, kSpinLimit);
-        ok = ok && tc::mbar_wait(&ready[it & 1], (it >> 1) & 1, kSpinLimit);
-        ok = ok && tc::mbar_wait(&ufull[it % kRing], (it / kRing) & 1, kSpinLimit);
+        if (first && g >= 1) ok = ok && tc::mbar_wait_timed(drained, (g - 1) & 1, kWaitLimitNs);
+        ok = ok && tc::mbar_wait_timed(&ready[s], (it / kABuf) & 1, kWaitLimitNs);
+        ok = ok && tc::mbar_wait_timed(&ufull[q], (it / kRing) & 1, kWaitLimitNs);
         if (!ok) break;
         tc::fence_after_sync();
-        issue(it, 0, 8);
-        tc::mma_commit(&afree[it & 1]);
-        tc::mma_commit(&bfree[it % kRing]);
+        // descriptor of the chunk's U tile: K-direction core matrices 128 bytes
+        // apart, 8-row groups kK / 8 core matrices apart; K step ks starts 256 ks
+        // bytes further (start-address field, 16-byte units, no carry)
+        const uint64_t db = tc::smem_desc(tc::smem_u32(smem + kOffB + q * kUBytes), 128, (kK / 8) * 128);
+#pragma unroll
+        for (int ks = 0; ks < kK / 16; ++ks)
+#pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            const uint32_t dcol = tmem + kColD + m * 128;
+            const uint32_t a_hi = tmem + kColA + s * 64 + m * 32 + 8 * ks, a_lo = a_hi + 16;
+            const uint64_t b = db + (uint64_t)((256 * ks) >> 4);
+            // columns 0..63: A_hi U_hi + A_lo U_hi; 64..127: A_hi U_lo + A_lo U_lo
+            tc::mma_f16_ts(dcol, a_hi, b, idesc, (ks > 0 || !first) ? 1u : 0u);
+            tc::mma_f16_ts(dcol, a_lo, b, idesc, 1u);
+          }
+        tc::mma_commit(&afree[s]);
+        tc::mma_commit(&bfree[q]);
         if (last) tc::mma_commit(done);
       }
     }
@@ -267,12 +340,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     // ---------------------------------------------------------- generating warps
     // this thread owns TMEM lane r = 32 wq + lane: target r of the CTA, whose phi
     // row is row r of tile 0 and whose psi row is row r of tile 1.  It computes
-    // sources 4 sq .. 4 sq + 3 of every chunk and reads back accumulator columns
-    // 32 (sq & 1) .. + 31 of tile sq >> 1.
+    // sources 4 sq .. 4 sq + 3 of every chunk (A columns 4 sq .. 4 sq + 3 of
+    // each part) and reads back accumulator columns 32 (sq & 1) .. + 31 of tile
+    // sq >> 1.
     const int sq = warp >> 2;
     const int ti = t0 + 32 * wq + lane;
     const bool tvalid = ti < n;
     const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
+    const int2 re = rowexp[min(ti, n - 1)];
+    const float rs0 = pow2f(re.x), r10 = pow2f(re.y - re.x);  // the psi row's scale relative to the phi row's
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
     const uint32_t dthr = tmem + lane_base + kColD + (sq >> 1) * 128 + 32 * (sq & 1);
     const bool tile_edge = t0 + kTgt > n;
@@ -291,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     // read-back of a group not read back in the loop (after it); the issue
     // thread may be waiting for it to start the next group
     auto drain = [&](int d) {
-      ok = ok && tc::mbar_wait(done, d & 1, kSpinLimit);
+      ok = ok && tc::mbar_wait_timed(done, d & 1, kWaitLimitNs);
       if (!ok) return;
       tc::fence_after_sync();
       read_back();
@@ -301,17 +377,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     };
     int drained_groups = 0;
     for (int it = 0; it < n_it; ++it) {
-      const int s = it & 1, q = it % kRing;
-      ok = ok && tc::mbar_wait(&sfull[q], (it / kRing) & 1, kSpinLimit);
-      // chunk it - 2's MMAs read A buffer s
-      if (it >= 2) ok = ok && tc::mbar_wait(&afree[s], ((it - 2) >> 1) & 1, kSpinLimit);
-      // the second chunk of group g + 1 reads back group g (its last MMAs were
-      // those of chunk it - 2, just waited for) before its tile is generated: the
-      // first chunk of group g + 1 waits for it
+      const int s = it % kABuf, q = it % kRing;
+      ok = ok && tc::mbar_wait_timed(&sfull[q], (it / kRing) & 1, kWaitLimitNs);
+      // chunk it - kABuf's MMAs read A buffer s
+      if (it >= kABuf) ok = ok && tc::mbar_wait_timed(&afree[s], ((it - kABuf) / kABuf) & 1, kWaitLimitNs);
+      // the second chunk of group g + 1 reads back group g before its tile is
+      // generated: the first chunk of group g + 1 waits for it
       const int d = (it % kGroup == 1 && it > kGroup) ? it / kGroup - 1 : -1;
-      if (d >= 0) ok = ok && tc::mbar_wait(done, d & 1, kSpinLimit);
+      if (d >= 0) ok = ok && tc::mbar_wait_timed(done, d & 1, kWaitLimitNs);
       if (!ok) break;
-      if (it >= 2) tc::fence_after_sync();
+      if (it >= kABuf) tc::fence_after_sync();
       if (d >= 0) {
         read_back();
         drained_groups = d + 1;
@@ -324,36 +399,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       // last target tile, mask pairs (source past the end, self pair, no target)
       const bool edge = tile_edge || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
       const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
-      float ph[8], ps[8];  // the phi-row and psi-row values in K order (k = 2 u + c)
+      uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int jj = 4 * sq + u;
         float v[4];
         if (edge) {
           const bool z = !tvalid || j0 + jj >= n || j0 + jj == ti;
-          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], z, c, v);
+          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], z, c, v, rs0, r10);
           if (z) v[0] = v[1] = v[2] = v[3] = 0.f;
         } else {
-          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], false, c, v);
+          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], false, c, v, rs0, r10);
         }
-        ph[2 * u] = v[0], ph[2 * u + 1] = v[1];  // K2, K1
-        ps[2 * u] = v[2], ps[2 * u + 1] = v[3];  // K4, K3
+        split_f16x2(v[0], v[1], h0[u], l0[u]);
+        split_f16x2(v[2], v[3], h1[u], l1[u]);
       }
-      float hi[8];
-      const uint32_t acol = tmem + lane_base + kColA + s * 128 + 8 * sq;
-#pragma unroll
-      for (int x = 0; x < 8; ++x) hi[x] = split_hi(ph[x]);
-      tc::tmem_st8(acol, hi);
-#pragma unroll
-      for (int x = 0; x < 8; ++x) ph[x] -= hi[x];  // the low parts (exact in FP32)
-      tc::tmem_st8(acol + 32, ph);
-      float hs[8];
-#pragma unroll
-      for (int x = 0; x < 8; ++x) hs[x] = split_hi(ps[x]);
-      tc::tmem_st8(acol + 64, hs);
-#pragma unroll
-      for (int x = 0; x < 8; ++x) ps[x] -= hs[x];
-      tc::tmem_st8(acol + 96, ps);
+      const uint32_t acol = tmem + lane_base + kColA + s * 64 + 4 * sq;
+      tc::tmem_st4(acol, h0);
+      tc::tmem_st4(acol + 16, l0);
+      tc::tmem_st4(acol + 32, h1);
+      tc::tmem_st4(acol + 48, l1);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
@@ -366,16 +431,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   if (!all_ok && tid == 0) atomicExch(err, 1);
 
   // epilogue: this thread holds target 32 wq + lane, component sq >> 1 (tile),
-  // right-hand sides 32 (sq & 1) .. + 31
-  if (all_ok && n_it > 0 && warp < kMmaWarp) {
+  // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-(e + f)
+  if (all_ok && n_it > 0 && warp < kMmaWarp) {  // the generating warps
     const int sq = warp >> 2;
     const int i = t0 + 32 * wq + lane, comp = sq >> 1;
-    if (i < n)
+    if (i < n) {
+      const int2 re = rowexp[i];
+      const float rinv = pow2f(-(comp ? re.y : re.x));
 #pragma unroll
       for (int x = 0; x < 32; ++x) {
         const int b = 32 * (sq & 1) + x;
-        if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x];
+        if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x] * rinv * cinv[b];
       }
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -433,11 +501,22 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     plan = it->second.get();
   }
   const int K = L.K;
-  s->grow(s->upk, (size_t)n_chunks * 2 * kNB * kK);
+  s->grow(s->upk, (size_t)n_chunks * kUBytes / sizeof(float));
   s->grow(s->part32, (size_t)std::min(K, kNB) * S * 2 * n);
+  s->grow(s->tc_colmax, (size_t)kNB);
   if (s->tc_err.cap == 0) {
     s->grow(s->tc_err, 1);
     BIPB_CUDA(cudaMemsetAsync(s->tc_err.p, 0, sizeof(int), s->stream));
+  }
+  // row scale exponents: once per surface and medium (a buffer that moved is recomputed)
+  const uint64_t gen0 = s->alloc_gen;
+  s->grow(s->tc_rowexp, (size_t)n);
+  if (s->alloc_gen != gen0 || s->tc_rowexp_n != n || s->tc_rowexp_key[0] != c.eps || s->tc_rowexp_key[1] != c.inveps ||
+      s->tc_rowexp_key[2] != c.kappa) {
+    k_tc_rowexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_rowexp.p);
+    BIPB_LAUNCHED(s);
+    s->tc_rowexp_n = n;
+    s->tc_rowexp_key[0] = c.eps, s->tc_rowexp_key[1] = c.inveps, s->tc_rowexp_key[2] = c.kappa;
   }
   // per block of up to 64 right-hand sides: pack, tensor-core pass, FP64 reduction
   for (int b0 = 0; b0 < K; b0 += kNB) {
@@ -459,12 +538,18 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     const double* ub = u + (int64_t)b0 * 2 * n;
     double* yb = y + (int64_t)b0 * 2 * n;
     const int64_t pk = (int64_t)n_chunks * kNB * kK;
-    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, s->upk.p);
+    __half* upk = reinterpret_cast<__half*>(s->upk.p);
+    BIPB_CUDA(cudaMemsetAsync(s->tc_colmax.p, 0, kNB * sizeof(unsigned), s->stream));
+    k_colmax_u<<<dim3((unsigned)std::min<int64_t>(64, (2 * (int64_t)n + 255) / 256), nb), 256, 0, s->stream>>>(
+        2 * (int64_t)n, ub, s->tc_colmax.p);
+    BIPB_LAUNCHED(s);
+    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, s->tc_colmax.p, upk);
     BIPB_LAUNCHED(s);
     {
       TimedLaunch tl(s, kTMvTC);
-      k_mrhs_tc<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p, s->upk.p,
-                                                               s->part32.p, c, s->tc_err.p);
+      k_mrhs_tc<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p,
+                                                               s->tc_rowexp.p, s->tc_colmax.p, upk, s->part32.p, c,
+                                                               s->tc_err.p);
       BIPB_LAUNCHED(s);
     }
     launch_reduce_matvec32(s, Lb, tt->second->tab.p, s->part32.p, ub, yb, dphi, dpsi,
