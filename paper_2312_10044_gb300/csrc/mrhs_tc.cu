@@ -3,7 +3,7 @@
 // Y = A U for a block of up to 64 right-hand sides U (2N x B) on one
 // surface.  Per CTA: 128 targets (two MMA tiles of M = 128 rows: tile 0 the
 // phi_i rows, tile 1 the psi_i rows of the same targets) against a range of
-// source chunks of 16 sources (K = 32 source unknowns phi_j, psi_j
+// source chunks of 32 sources (K = 64 source unknowns phi_j, psi_j
 // interleaved).  For every chunk the CUDA cores generate the kernel tile
 // once,
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i, tile 0)
@@ -25,7 +25,7 @@
 // GB300 an M = 128, N = 128 MMA takes about 117 SM cycles with K = 16 in FP16
 // and 111 with K = 8 in TF32 (measured, one thread issuing back to back), so
 // the FP16 split needs half the tensor-core time of a TF32 split of the same
-// accuracy.  The MMAs run while the next tiles are being generated (four A
+// accuracy.  The MMAs run while the next tile is being generated (two A
 // buffers); shared memory carries only the U tiles.
 //
 // Scaling.  FP16 holds 2^-14 .. 65504 at full precision, so both operands are
@@ -37,8 +37,8 @@
 // its row's largest loses relative precision in a_lo (FP16 subnormals), but
 // its absolute error stays below 2^-40 of that largest value.
 //
-// TMEM (512 columns; lane r = target r of the CTA): A buffers 0..3 at columns
-// 64 s (tile m at + 32 m: hi part + 0..15, lo part + 16..31, two FP16 values
+// TMEM (512 columns; lane r = target r of the CTA): A buffers 0, 1 at columns
+// 128 s (tile m at + 64 m: hi part + 0..31, lo part + 32..63, two FP16 values
 // per column); the accumulator of tile m at [256 + 128 m, 384 + 128 m).
 //
 // Accuracy.  The tensor core's FP32 accumulation is not to be run over a
@@ -46,8 +46,8 @@
 // the length of the sum and does not average out for smooth vectors
 // (measured on the protein-like surface at N = 81920: 1.7e-4 of the
 // off-diagonal part for phi = 1, against 1.2e-5 for the FP32 CUDA-core
-// mat-vec).  So every group of eight chunks (K = 256) starts a fresh
-// accumulator: the threads read group g back (and add it to FP32 registers)
+// mat-vec).  So every group of 128 sources (four chunks, K = 256) starts a
+// fresh accumulator: the threads read group g back (and add it to FP32 registers)
 // at the second chunk of group g + 1, whose first MMAs wait for that.  The
 // operator is then accurate to FP32 level and the mixed refinement reaches
 // 1e-8 in two steps.  The epilogue writes per-split partial sums that the
@@ -70,22 +70,24 @@ namespace {
 
 constexpr int kNB = 64;                     // right-hand sides per launch (MMA N = 2 kNB: hi and lo parts)
 constexpr int kTgt = 128;                   // targets per CTA (two M = 128 tiles)
-constexpr int kChunk = 16;                  // sources per chunk
-constexpr int kK = 2 * kChunk;              // MMA K per chunk (two K steps of 16)
-constexpr int kPartBytes = kNB * kK * 2;    // one FP16 part of the U tile of a chunk: 4 KB
-constexpr int kUBytes = 2 * kPartBytes;     // [U_hi | U_lo] of a chunk: 128 rows of 64 bytes
-constexpr int kSBytes = kChunk * 32;        // source records of one chunk: 512 B
+constexpr int kChunk = 32;                  // sources per chunk
+constexpr int kK = 2 * kChunk;              // MMA K per chunk (four K steps of 16)
+constexpr int kPerThread = kChunk / 4;      // sources of a chunk per generating thread
+constexpr int kPartBytes = kNB * kK * 2;    // one FP16 part of the U tile of a chunk: 8 KB
+constexpr int kUBytes = 2 * kPartBytes;     // [U_hi | U_lo] of a chunk: 128 rows of 128 bytes
+constexpr int kSBytes = kChunk * 32;        // source records of one chunk: 1 KB
 constexpr int kRing = 8;                    // U and source buffers (chunk it in buffer it % 8)
-constexpr int kABuf = 4;                    // A buffers in TMEM (chunk it in buffer it % 4)
+constexpr int kACols = 4 * kChunk;          // TMEM columns of one A buffer: 2 tiles x (hi, lo) x K / 2
+constexpr int kABuf = 256 / kACols;         // A buffers in TMEM (chunk it in buffer it % kABuf)
 constexpr int kOffB = 0;                    // kRing U buffers
 constexpr int kOffS = kOffB + kRing * kUBytes;      // kRing source buffers
 constexpr int kOffCol = kOffS + kRing * kSBytes;    // kNB column unscale factors
 constexpr int kOffBar = kOffCol + kNB * 4;
 constexpr int kNumBars = 3 * kRing + 2 * kABuf + 2;
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
-constexpr int kGroup = 8;                   // chunks accumulated in TMEM before it is read back (16 fails the FP32 bound)
+constexpr int kGroup = 128 / kChunk;        // chunks accumulated in TMEM before it is read back: 128 sources (256 fail the FP32 bound)
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColA = 0;               // A buffer s at kColA + 64 s
+constexpr uint32_t kColA = 0;               // A buffer s at kColA + kACols s
 constexpr uint32_t kColD = 256;             // accumulator of tile m at kColD + 128 m
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait longer than 2 s is an error
 constexpr int kScaleTop = 14;               // scaled magnitudes lie in [2^14, 2^15)
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
 #pragma unroll
           for (int m = 0; m < 2; ++m) {
             const uint32_t dcol = tmem + kColD + m * 128;
-            const uint32_t a_hi = tmem + kColA + s * 64 + m * 32 + 8 * ks, a_lo = a_hi + 16;
+            const uint32_t a_hi = tmem + kColA + s * kACols + m * 2 * kChunk + 8 * ks, a_lo = a_hi + kChunk;
             const uint64_t b = db + (uint64_t)((256 * ks) >> 4);
             // columns 0..63: A_hi U_hi + A_lo U_hi; 64..127: A_hi U_lo + A_lo U_lo
             tc::mma_f16_ts(dcol, a_hi, b, idesc, (ks > 0 || !first) ? 1u : 0u);
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     // ---------------------------------------------------------- generating warps
     // this thread owns TMEM lane r = 32 wq + lane: target r of the CTA, whose phi
     // row is row r of tile 0 and whose psi row is row r of tile 1.  It computes
-    // sources 4 sq .. 4 sq + 3 of every chunk (A columns 4 sq .. 4 sq + 3 of
+    // sources 8 sq .. 8 sq + 7 of every chunk (A columns 8 sq .. 8 sq + 7 of
     // each part) and reads back accumulator columns 32 (sq & 1) .. + 31 of tile
     // sq >> 1.
     const int sq = warp >> 2;
@@ -399,26 +401,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       // last target tile, mask pairs (source past the end, self pair, no target)
       const bool edge = tile_edge || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
       const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
-      uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
+      const float4* Sq = S + 2 * kPerThread * sq;
+      const int jq = j0 + kPerThread * sq;
+      const uint32_t acol = tmem + lane_base + kColA + s * kACols + kPerThread * sq;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int jj = 4 * sq + u;
-        float v[4];
-        if (edge) {
-          const bool z = !tvalid || j0 + jj >= n || j0 + jj == ti;
-          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], z, c, v, rs0, r10);
-          if (z) v[0] = v[1] = v[2] = v[3] = 0.f;
-        } else {
-          kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, S[2 * jj], S[2 * jj + 1], false, c, v, rs0, r10);
+      for (int hh = 0; hh < kPerThread / 4; ++hh) {
+        uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int jj = 4 * hh + u;
+          float v[4];
+          if (edge) {
+            const bool z = !tvalid || jq + jj >= n || jq + jj == ti;
+            kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], z, c, v, rs0, r10);
+            if (z) v[0] = v[1] = v[2] = v[3] = 0.f;
+          } else {
+            kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], false, c, v, rs0, r10);
+          }
+          split_f16x2(v[0], v[1], h0[u], l0[u]);
+          split_f16x2(v[2], v[3], h1[u], l1[u]);
         }
-        split_f16x2(v[0], v[1], h0[u], l0[u]);
-        split_f16x2(v[2], v[3], h1[u], l1[u]);
+        // tile 0 hi / lo at + 0 / + kChunk, tile 1 at + 2 kChunk / + 3 kChunk
+        tc::tmem_st4(acol + 4 * hh, h0);
+        tc::tmem_st4(acol + 4 * hh + kChunk, l0);
+        tc::tmem_st4(acol + 4 * hh + 2 * kChunk, h1);
+        tc::tmem_st4(acol + 4 * hh + 3 * kChunk, l1);
       }
-      const uint32_t acol = tmem + lane_base + kColA + s * 64 + 4 * sq;
-      tc::tmem_st4(acol, h0);
-      tc::tmem_st4(acol + 16, l0);
-      tc::tmem_st4(acol + 32, h1);
-      tc::tmem_st4(acol + 48, l1);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
