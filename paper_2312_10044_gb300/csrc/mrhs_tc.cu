@@ -220,6 +220,37 @@ __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, ui
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// This thread's kPerThread sources of a chunk (records Sq, first index jq)
+// against target ti: the scaled pair values, split into FP16 parts, written
+// into the thread's TMEM lane from column acol on (tile 0 hi / lo at + 0 /
+// + kChunk, tile 1 at + 2 kChunk / + 3 kChunk).  EDGE masks pairs with no
+// target, a source past the end or the self pair.
+template <bool EDGE>
+__device__ __forceinline__ void gen_chunk(const float4& gi, const float4& ni, const float4* Sq, int jq, int ti, int n,
+                                          bool tvalid, const PairConst<float>& c, float rs0, float r10, uint32_t acol) {
+#pragma unroll
+  for (int hh = 0; hh < kPerThread / 4; ++hh) {
+    uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int jj = 4 * hh + u;
+      const bool z = EDGE && (!tvalid || jq + jj >= n || jq + jj == ti);
+      float v[4];
+      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], z, c, v, rs0, r10);
+      if (EDGE) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = z ? 0.f : v[k];
+      }
+      split_f16x2(v[0], v[1], h0[u], l0[u]);
+      split_f16x2(v[2], v[3], h1[u], l1[u]);
+    }
+    tc::tmem_st4(acol + 4 * hh, h0);
+    tc::tmem_st4(acol + 4 * hh + kChunk, l0);
+    tc::tmem_st4(acol + 4 * hh + 2 * kChunk, h1);
+    tc::tmem_st4(acol + 4 * hh + 3 * kChunk, l1);
+  }
+}
+
 // items: {t0, c0, c1, split}; tgt32: 2 float4 per element (x, y, z, area), (n, 0).
 // Warp specialisation: warps 0..15 generate the kernel tiles (and read the
 // accumulators back), warp 16 issues the MMAs, warp 17 the bulk copies, so no
@@ -404,29 +435,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       const float4* Sq = S + 2 * kPerThread * sq;
       const int jq = j0 + kPerThread * sq;
       const uint32_t acol = tmem + lane_base + kColA + s * kACols + kPerThread * sq;
-#pragma unroll
-      for (int hh = 0; hh < kPerThread / 4; ++hh) {
-        uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int jj = 4 * hh + u;
-          float v[4];
-          if (edge) {
-            const bool z = !tvalid || jq + jj >= n || jq + jj == ti;
-            kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], z, c, v, rs0, r10);
-            if (z) v[0] = v[1] = v[2] = v[3] = 0.f;
-          } else {
-            kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], false, c, v, rs0, r10);
-          }
-          split_f16x2(v[0], v[1], h0[u], l0[u]);
-          split_f16x2(v[2], v[3], h1[u], l1[u]);
-        }
-        // tile 0 hi / lo at + 0 / + kChunk, tile 1 at + 2 kChunk / + 3 kChunk
-        tc::tmem_st4(acol + 4 * hh, h0);
-        tc::tmem_st4(acol + 4 * hh + kChunk, l0);
-        tc::tmem_st4(acol + 4 * hh + 2 * kChunk, h1);
-        tc::tmem_st4(acol + 4 * hh + 3 * kChunk, l1);
-      }
+      // one branch per chunk: the masked form only where a chunk needs it
+      if (edge)
+        gen_chunk<true>(gi, ni, Sq, jq, ti, n, tvalid, c, rs0, r10, acol);
+      else
+        gen_chunk<false>(gi, ni, Sq, jq, ti, n, tvalid, c, rs0, r10, acol);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
