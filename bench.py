@@ -308,7 +308,7 @@ def run_matvec_only(args):
 
     prob, desc = workload(args.workload)
     prec = {"matvec32": bipb.FP32, "matvec64": bipb.FP64, "matvecdf": bipb.DF64, "matvecdfm": bipb.DF64,
-            "matvectc": bipb.TF32, "matvectree": bipb.TREE32}[args.mode]
+            "matvectc": bipb.TENSOR, "matvectree": bipb.TREE32}[args.mode]
     n_vec = 64 if args.mode in ("matvectc", "matvecdfm") else 1
     med = bipb.medium(prob.eps_in, prob.eps_out, prob.kappa)
     with bipb.Surface(prob.centroids, prob.normals, prob.areas) as s:
@@ -413,17 +413,17 @@ def run_configs(args):
             U = torch.randn(64, 2 * n, dtype=torch.float64, device="cuda")
             Y = torch.empty_like(U)
             res = {"config": "batched: protein-like N=81920, 64 charge sets x 2000"}
-            for name, prec in (("tf32_tensor", bipb.TF32), ("fp32_cuda_cores", bipb.FP32)):
+            for name, prec in (("tensor", bipb.TENSOR), ("fp32_cuda_cores", bipb.FP32)):
                 s.matvec(U, Y, precision=prec, med=med)
                 ms, _ = _timed(lambda: s.matvec(U, Y, precision=prec, med=med), torch)
                 res[f"matvec64rhs_ms_{name}"] = ms
                 res[f"pair_rhs_per_s_{name}"] = 64 * n * (n - 1) / (ms / 1e3)
-            prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.MIXED_TF32)
+            prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, precision=bipb.MIXED_TENSOR)
             bipb.timer_enable(s, True)
             ms, info = _timed(lambda: s.solve(prm), torch)
             t = bipb.timer_read(s)
             bipb.timer_enable(s, False)
-            res["solve_ms_mixed_tf32_64rhs"] = ms
+            res["solve_ms_mixed_tensor_64rhs"] = ms
             res["kernel_ms"] = {k: v[1] for k, v in t.items() if v[0]}
             res["iters_max"] = max(i["iters"] for i in info)
             res["refine_steps_max"] = max(i["refine_steps"] for i in info)
@@ -436,7 +436,7 @@ def run_configs(args):
             ms, info = _timed(lambda: s.solve(prm), torch)
             t = bipb.timer_read(s)
             bipb.timer_enable(s, False)
-            res["solve_ms_mixed_tf32_64rhs_precond_self"] = ms
+            res["solve_ms_mixed_tensor_64rhs_precond_self"] = ms
             res["kernel_ms_precond_self"] = {k: v[1] for k, v in t.items() if v[0]}
             res["kernel_launches_precond_self"] = {k: v[0] for k, v in t.items() if v[0]}
             res["iters_max_precond_self"] = max(i["iters"] for i in info)
@@ -529,7 +529,7 @@ def config5_central_differences(bipb, torch):
     of the energy row c, so E(y +- h e_d) - E(y) = 1/2 [dc.u + c.du + dc.du]
     with A du = db, where db and dc are the source and energy row of the
     charge pair {(y_k +- h e_d, q_k), (y_k, -q_k)}.  The 192 pair systems are
-    solved together (TF32 Krylov + double-float residual, tol 1e-9), and each
+    solved together (tensor-core Krylov + double-float residual, tol 1e-9), and each
     term is a reaction-energy pass: no difference of two large energies is
     taken.  dE/dq_k (E is quadratic in q, so central differences are exact)
     = 1/2 (c_k.u + c.u_k) with u_k the solution for a unit charge at y_k.
@@ -564,7 +564,7 @@ def config5_central_differences(bipb, torch):
             q_sets.append([1.0, 0.0])
         B = len(q_sets)
         s.set_charges(np.array(pos_sets), np.array(q_sets))
-        prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=1e-9, precision=bipb.MIXED_TF32)
+        prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=1e-9, precision=bipb.MIXED_TENSOR)
         ms, info = _timed(lambda: s.solve(prm), torch)
         res["pair_solves"] = {"systems": B, "ms": ms, "converged": int(sum(i["converged"] for i in info)),
                               "rel_residual_max": max(i["rel_residual"] for i in info)}

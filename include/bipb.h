@@ -60,11 +60,15 @@ typedef enum {
   BIPB_DF64 = 3,       /* pair arithmetic in double-float (two FP32 words, ~48 bits) on the FP32
                           pipe, FP64 sums across tiles; as a solve: GMRES on that mat-vec */
   BIPB_MIXED_DF64 = 4, /* FP32 pair arithmetic inside GMRES, double-float refinement residual */
-  BIPB_TF32 = 5,       /* mat-vec only, right-hand sides of one surface: kernel tiles generated in
+  BIPB_TENSOR = 5,     /* mat-vec only, right-hand sides of one surface: kernel tiles generated in
                           FP32 and contracted against blocks of 64 right-hand sides on the tensor
-                          cores (each FP32 operand split into two TF32 parts, three TF32 products
-                          per tile, FP32 accumulation, FP64 sums across tiles: about FP32 accuracy) */
-  BIPB_MIXED_TF32 = 6, /* TF32 tensor-core mat-vec inside GMRES, double-float refinement residual */
+                          cores (rows and columns scaled by powers of two, each operand split into
+                          two FP16 parts, three products per tile, FP32 accumulation, FP64 sums
+                          across tiles: about FP32 accuracy for kernel values and right-hand sides
+                          within about 2^-86 .. 2^114 of their row's / column's largest) */
+  BIPB_MIXED_TENSOR = 6, /* tensor-core mat-vec inside GMRES, double-float refinement residual */
+  BIPB_TF32 = BIPB_TENSOR,             /* earlier name of BIPB_TENSOR */
+  BIPB_MIXED_TF32 = BIPB_MIXED_TENSOR, /* earlier name of BIPB_MIXED_TENSOR */
   BIPB_TREE32 = 7,     /* mat-vec only, forward, single-surface handles: the far-field (treecode) operator
                           of Sec. 2.2.3 in FP32 pair arithmetic, FP64 sums across work items
                           (bipb_treecode sets its parameters) */
@@ -85,7 +89,8 @@ typedef struct {
   double tol;          /* target ||b - A u||_2 / ||b||_2, 0 < tol < 1 */
   int restart;         /* GMRES restart length m, 1..200 (10 if 0) */
   int max_iter;        /* cap on GMRES iterations summed over restarts and refinement steps (1000 if 0) */
-  int precision;       /* bipb_precision: BIPB_FP64, BIPB_MIXED, BIPB_DF64, BIPB_MIXED_DF64 or BIPB_MIXED_TF32 */
+  int precision;       /* bipb_precision: BIPB_FP64, BIPB_MIXED, BIPB_DF64, BIPB_MIXED_DF64, BIPB_MIXED_TENSOR
+                          or BIPB_MIXED_TREE */
   int inner_max_iter;  /* MIXED: cap on inner iterations per refinement step (200 if 0) */
   double inner_tol;    /* MIXED: inner relative tolerance per refinement step (1e-6 if 0) */
   const double* x0;    /* optional warm start, host, n_rhs x 2N internal units, or NULL (zero) */
@@ -119,7 +124,7 @@ typedef struct {
   int iters;           /* GMRES iterations (inner iterations for MIXED) */
   int refine_steps;    /* mixed modes: refinement steps taken (0 for FP64 and DF64) */
   int matvecs64;       /* FP64 or double-float mat-vecs applied to this right-hand side */
-  int matvecs32;       /* FP32 (or TF32) mat-vecs applied to this right-hand side */
+  int matvecs32;       /* FP32 (CUDA-core, tensor-core or far-field) mat-vecs applied to this right-hand side */
   int reserved;
   double rel_residual; /* final ||b - A u|| / ||b||: the true residual, formed with the FP64 or
                           double-float mat-vec and FP64 vector arithmetic */
@@ -272,8 +277,10 @@ bipb_status bipb_energy_grad_dev(bipb_surface s, const bipb_solve_params* p, dou
  *   For a batch handle n_vec must be 1 and u, y are batched vectors (the
  *   block-diagonal operator of all surfaces).
  *   precision: BIPB_FP64, BIPB_FP32 (FP32 pair arithmetic per source tile,
- *   FP64 sums across tiles and for the diagonal), BIPB_DF64 or BIPB_TF32
- *   (single-surface handles; the tensor-core path of the multi-RHS mat-vec).
+ *   FP64 sums across tiles and for the diagonal), BIPB_DF64, BIPB_TENSOR
+ *   (single-surface handles, forward only; the tensor-core path of the
+ *   multi-RHS mat-vec) or BIPB_TREE32 (single-surface handles, forward only;
+ *   the far-field operator).
  */
 bipb_status bipb_matvec(bipb_surface s, const bipb_medium* m, int precision, int transpose,
                         int n_vec, const double* u, double* y);

@@ -31,8 +31,9 @@ MIXED = 1
 FP32 = 2
 DF64 = 3
 MIXED_DF64 = 4
-TF32 = 5
-MIXED_TF32 = 6
+TENSOR = 5
+MIXED_TENSOR = 6
+TF32, MIXED_TF32 = TENSOR, MIXED_TENSOR  # earlier names of the same values
 TREE32 = 7
 MIXED_TREE = 8
 

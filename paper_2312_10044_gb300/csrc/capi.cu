@@ -77,9 +77,9 @@ void validate_params(const bipb_solve_params* p) {
   BIPB_REQUIRE(p->restart >= 0 && p->restart <= kMaxRestart, "restart must lie in [1, 200] (0 = 10)");
   BIPB_REQUIRE(p->max_iter >= 0, "max_iter must be >= 0 (0 = 1000)");
   BIPB_REQUIRE(p->precision == BIPB_FP64 || p->precision == BIPB_MIXED || p->precision == BIPB_DF64 ||
-                   p->precision == BIPB_MIXED_DF64 || p->precision == BIPB_MIXED_TF32 ||
+                   p->precision == BIPB_MIXED_DF64 || p->precision == BIPB_MIXED_TENSOR ||
                    p->precision == BIPB_MIXED_TREE,
-               "precision must be FP64, MIXED, DF64, MIXED_DF64, MIXED_TF32 or MIXED_TREE");
+               "precision must be FP64, MIXED, DF64, MIXED_DF64, MIXED_TENSOR or MIXED_TREE");
   BIPB_REQUIRE(p->inner_max_iter >= 0, "inner_max_iter must be >= 0");
   BIPB_REQUIRE(std::isfinite(p->inner_tol) && p->inner_tol >= 0 && p->inner_tol < 1, "inner_tol must lie in [0, 1)");
   BIPB_REQUIRE(p->precond == BIPB_PRECOND_NONE || p->precond == BIPB_PRECOND_SELF, "unknown precond");
@@ -547,9 +547,9 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
     Surface* s = checked(h);
     validate_medium(m);
     BIPB_REQUIRE(precision == BIPB_FP64 || precision == BIPB_FP32 || precision == BIPB_DF64 ||
-                     precision == BIPB_TF32 || precision == BIPB_TREE32,
-                 "precision must be FP64, FP32, DF64, TF32 or TREE32");
-    BIPB_REQUIRE(precision != BIPB_TF32 || !s->batch, "the tensor-core mat-vec needs a single-surface handle");
+                     precision == BIPB_TENSOR || precision == BIPB_TREE32,
+                 "precision must be FP64, FP32, DF64, TENSOR or TREE32");
+    BIPB_REQUIRE(precision != BIPB_TENSOR || !s->batch, "the tensor-core mat-vec needs a single-surface handle");
     BIPB_REQUIRE(precision != BIPB_TREE32 || !s->batch, "the far-field mat-vec needs a single-surface handle");
     BIPB_REQUIRE(precision != BIPB_TREE32 || !transpose, "the far-field mat-vec has no transpose");
     BIPB_REQUIRE(n_vec >= 1 && n_vec <= 4096, "n_vec must lie in [1, 4096]");
@@ -558,9 +558,9 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
     BIPB_REQUIRE(u != y, "y must not alias u");
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    BIPB_REQUIRE(precision != BIPB_TF32 || !transpose, "the tensor-core mat-vec has no transpose");
+    BIPB_REQUIRE(precision != BIPB_TENSOR || !transpose, "the tensor-core mat-vec has no transpose");
     matvec(s, matvec_layout(s, n_vec), *m, precision, transpose != 0, u, y, nullptr, 0);
-    if (precision == BIPB_TF32) check_tc_error(s);
+    if (precision == BIPB_TENSOR) check_tc_error(s);
   });
 }
 
@@ -596,10 +596,10 @@ bipb_status bipb_solve(bipb_surface h, const bipb_solve_params* p, bipb_solve_in
     }
     s->have_solution = false;
     source_pass(s, L, p->medium, s->b.p);
-    BIPB_REQUIRE(p->precision != BIPB_MIXED_TF32 || !s->batch, "MIXED_TF32 needs a single-surface handle");
+    BIPB_REQUIRE(p->precision != BIPB_MIXED_TENSOR || !s->batch, "MIXED_TENSOR needs a single-surface handle");
     BIPB_REQUIRE(p->precision != BIPB_MIXED_TREE || !s->batch, "MIXED_TREE needs a single-surface handle");
     std::vector<SolveResult> res = gmres_solve(s, L, p->medium, *p, false, s->b.p, s->u.p, p->x0 != nullptr);
-    if (p->precision == BIPB_MIXED_TF32) check_tc_error(s);
+    if (p->precision == BIPB_MIXED_TENSOR) check_tc_error(s);
     reaction_pass(s, L, p->medium, s->u.p, nullptr, s->e_dev.p);
     for (auto& r : res)
       if (!r.converged) st = BIPB_ERR_NOT_CONVERGED;

@@ -546,7 +546,7 @@ void issue_cycle(Surface* s, const SysLayout& L, GmresWork* w, const bipb_medium
     matvec(s, L, med, precision, transpose, tz ? tz : vj, w->w.p, &w->st->skip, kStateInts);
     // CGS2 for FP64 and df64 Krylov mat-vecs: the first pass also takes the
     // dot products of the second, the second also forms the block norms.
-    // The FP32 / split-TF32 Krylov solve of the mixed modes stops at a
+    // The FP32 / split-FP16 tensor-core Krylov solve of the mixed modes stops at a
     // relative 1e-6 (its true residual is measured in higher precision by
     // the refinement), and its FP64 basis of at most m vectors loses
     // orthogonality in one classical pass only at about eps_64 cond(A)^2:
@@ -718,13 +718,13 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   const int64_t len = L.len;
   const int nb = grid_for(len);
   const std::vector<double> bnorm = norms(s, w, rhs);
-  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_MIXED_TF32 ||
+  const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_MIXED_TENSOR ||
                      p.precision == BIPB_MIXED_TREE;
   // arithmetic of the Krylov mat-vecs and of the residual r = b - A x (the
   // adjoint solve has neither a tensor-core nor a far-field transpose and
   // uses the direct FP32 mat-vec there)
   int inner = !mixed ? p.precision : BIPB_FP32;
-  if (p.precision == BIPB_MIXED_TF32 && !transpose) inner = BIPB_TF32;
+  if (p.precision == BIPB_MIXED_TENSOR && !transpose) inner = BIPB_TENSOR;
   if (p.precision == BIPB_MIXED_TREE && !transpose) inner = BIPB_TREE32;
   const int resid = (p.precision == BIPB_MIXED || p.precision == BIPB_FP64) ? BIPB_FP64 : BIPB_DF64;
   // r = rhs - A x (or rhs when starting from zero)
@@ -745,7 +745,7 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   for (int k = 0; k < K; ++k)
     if (bnorm[k] == 0.0) rel[k] = 0.0;
   // inner solves stop near the inner operator's own accuracy (about 1e-7 for
-  // FP32 pairs and for the split-TF32 tensor-core tiles): iterating further
+  // FP32 pairs and for the split-FP16 tensor-core tiles): iterating further
   // does not reduce the true residual
   const double inner_floor = p.inner_tol > 0 ? p.inner_tol : 1e-6;
   const int inner_cap = p.inner_max_iter > 0 ? p.inner_max_iter : 200;

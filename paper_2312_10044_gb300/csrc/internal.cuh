@@ -421,7 +421,7 @@ void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, cons
                  double dpsi, const int* skip, int skip_stride);
 // the far-field operator of the handle's parameters (built on first use; synchronises then)
 FarField* far_field(Surface* s);
-// y = A u for right-hand sides of one surface with the TF32 tensor-core kernel (mrhs_tc.cu)
+// y = A u for right-hand sides of one surface with the split-FP16 tensor-core kernel (mrhs_tc.cu)
 void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
                double dpsi, const int* skip, int skip_stride);
 // y = A u for right-hand sides of one surface, double-float arithmetic, kernel

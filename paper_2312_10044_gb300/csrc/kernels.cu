@@ -880,7 +880,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
             double* y, const int* skip, int skip_stride) {
   const double eps = m.eps_out / m.eps_in;
   const double dphi = 0.5 * (1.0 + eps), dpsi = 0.5 * (1.0 + 1.0 / eps);
-  if (precision == BIPB_TF32) {
+  if (precision == BIPB_TENSOR) {
     matvec_tc(s, L, pair_const<float>(m), u, y, dphi, dpsi, skip, skip_stride);
     return;
   }

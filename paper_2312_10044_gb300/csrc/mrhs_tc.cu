@@ -91,11 +91,11 @@ constexpr uint32_t kColA = 0;               // A buffer s at kColA + kACols s
 constexpr uint32_t kColD = 256;             // accumulator of tile m at kColD + 128 m
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait longer than 2 s is an error
 constexpr int kScaleTop = 14;               // scaled magnitudes lie in [2^14, 2^15)
-constexpr int kScaleClamp = 64;             // scale exponents are clamped to [-64, 64]
+constexpr int kScaleClamp = 100;            // scale exponents are clamped to [-100, 100]
 static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
 
 // The exponent e that brings a magnitude m into [2^14, 2^15) by m 2^e,
-// clamped to [-64, 64]; 64 for zero (and for FP32 subnormals).
+// clamped to [-100, 100] (exact for m in [2^-86, 2^114]); 100 for zero.
 __device__ __forceinline__ int scale_exp(float m) {
   const int lg = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m) for normal m
   return max(-kScaleClamp, min(kScaleClamp, kScaleTop - lg));

@@ -7,7 +7,7 @@
 * Protein-like surface, level 6 (N = 81920): after the mixed solve to 1e-8,
   the true residual b - A u recomputed by the oracle in FP64 on 256 sampled
   rows agrees with the residual the library reports.
-* The same surface with the split-TF32 tensor-core mat-vec (the batched
+* The same surface with the split-FP16 tensor-core mat-vec (the batched
   configuration's Krylov operator) against the oracle on sampled rows, for
   random and smooth right-hand sides; the 64-charge-set solve of the batched
   configuration and the uneven batch of eight surfaces, each checked by the
@@ -108,7 +108,7 @@ def test_protein_like_mixed_solve_true_residual_on_sampled_rows(bipb, orc):
 
 
 def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
-    """Split-TF32 tensor-core mat-vec at N = 81920 (about 5000 source chunks per
+    """Split-FP16 tensor-core mat-vec at N = 81920 (about 5000 source chunks per
     target tile), two random and two smooth right-hand sides, on 64 sampled
     rows: the FP32 mat-vec's bound on the whole output (2e-5 of the largest
     value), and on the off-diagonal sum alone no worse than twice the
@@ -125,7 +125,7 @@ def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
         ytc, y32 = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
-        s.matvec(ud, ytc, precision=bipb.TF32, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
+        s.matvec(ud, ytc, precision=bipb.TENSOR, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
         s.matvec(ud, y32, precision=bipb.FP32, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
         Ytc, Y32 = ytc.cpu().numpy(), y32.cpu().numpy()
     for v in range(U.shape[0]):
@@ -206,10 +206,10 @@ def _sampled_residual_rms(orc, p, u, q_row, pos, rows):
     return np.sqrt(np.mean(r * r)), np.linalg.norm(b) / np.sqrt(b.shape[0])
 
 
-def test_batched_64_rhs_tf32_solve_true_residual_on_sampled_rows(bipb, orc):
+def test_batched_64_rhs_tensor_solve_true_residual_on_sampled_rows(bipb, orc):
     """The batched configuration at full size: 64 charge sets of 2000 charges
     on the protein-like surface (N = 81920), solved together with the
-    tensor-core Krylov mat-vec (MIXED_TF32) to 1e-8.  For four of them the
+    tensor-core Krylov mat-vec (MIXED_TENSOR) to 1e-8.  For four of them the
     oracle recomputes b - A u on 128 sampled rows: RMS within twice that of
     a residual of 1e-8 ||b||."""
     base = synth.protein_like_problem()
@@ -217,7 +217,7 @@ def test_batched_64_rhs_tf32_solve_true_residual_on_sampled_rows(bipb, orc):
     with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
         s.set_charges(batch.charge_pos, batch.q)
         info = s.solve(eps_in=batch.eps_in, eps_out=batch.eps_out, kappa=batch.kappa, tol=1e-8,
-                       precision=bipb.MIXED_TF32)
+                       precision=bipb.MIXED_TENSOR)
         phi, dphi = s.surface_potential()
     assert all(i["converged"] and i["rel_residual"] <= 1e-8 for i in info)
     rows = np.sort(np.random.default_rng(63).choice(2 * batch.n, 128, replace=False))

@@ -8,7 +8,7 @@ Tolerances (each derived from the arithmetic of the path it checks):
   over one source split, FP64 across splits).
 * Double-float mat-vec: 2e-12 of the largest output (pairs in ~48-bit
   arithmetic; measured 4e-14).
-* Split-TF32 tensor-core mat-vec: the FP32 bounds.
+* Split-FP16 tensor-core mat-vec: the FP32 bounds.
 * Solves: energies and potentials within 1e-10 (FP64, both sides solved to
   1e-12) and within 1e-7 (mixed, refined to 1e-8 ... 1e-10); potentials at
   points off the surface within 1e-9 of the largest value (the difference
@@ -609,16 +609,16 @@ def test_autograd_batched_mixed(bipb):
 @pytest.mark.parametrize("n_rhs", [5, 70])
 def test_tensor_core_matvec_matches_oracle(bipb, orc, n_rhs):
     """Tensor-core mat-vec (kernel tile once per 64 right-hand sides, FP32
-    operands split into two TF32 parts, three TF32 products) vs the FP64
-    oracle: held to the FP32 mat-vec's bounds, 3e-6 in the 2-norm and 2e-5
-    of the largest output."""
+    operands scaled by powers of two and split into two FP16 parts, three
+    products) vs the FP64 oracle: held to the FP32 mat-vec's bounds, 3e-6 in
+    the 2-norm and 2e-5 of the largest output."""
     p = _ragged(3)
     eps = p.eps_out / p.eps_in
     U = np.random.default_rng(30 + n_rhs).standard_normal((n_rhs, 2 * p.n))
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
         yd = torch.full_like(ud, float("nan"))
-        s.matvec(ud, yd, precision=bipb.TF32, med=_med(bipb, p))
+        s.matvec(ud, yd, precision=bipb.TENSOR, med=_med(bipb, p))
         Y = yd.cpu().numpy()
     for r in (0, n_rhs // 2, n_rhs - 1):
         ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
@@ -627,12 +627,39 @@ def test_tensor_core_matvec_matches_oracle(bipb, orc, n_rhs):
         assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
 
 
-def test_mixed_tf32_solve_matches_oracle(bipb, orc):
+@pytest.mark.parametrize("geo_scale", [1e-3, 1.0, 1e3])
+def test_tensor_core_matvec_scaled_inputs(bipb, orc, geo_scale):
+    """The power-of-two row and column scaling of the tensor-core path:
+    right-hand sides of magnitude 1e-25, 1 and 1e25 side by side, one zero
+    right-hand side, and the surface in units 1e-3, 1 and 1e3 times as large
+    (kernel values from about 1e-9 to 1e6 of the unscaled ones).  Each
+    nonzero column is held to the FP32 bounds relative to its own size; the
+    zero column gives exact zeros."""
+    p = _ragged(3)
+    c, a = p.centroids * geo_scale, p.areas * geo_scale**2
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(41)
+    mags = [1e-25, 1.0, 1e25]
+    U = np.stack([m * rng.standard_normal(2 * p.n) for m in mags] + [np.zeros(2 * p.n)])
+    with bipb.Surface(c, p.normals, a) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TENSOR, med=_med(bipb, p))
+        Y = yd.cpu().numpy()
+    assert np.all(Y[3] == 0.0)
+    for r in range(3):
+        ref = orc.matvec(c, p.normals, a, eps, p.kappa, U[r])
+        assert np.all(np.isfinite(Y[r]))
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6, r
+        assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max(), r
+
+
+def test_mixed_tensor_solve_matches_oracle(bipb, orc):
     base = synth.protein_like_problem(level=4, n_charges=30)
     batch = synth.batched_charges(base, n_rhs=3, n_charges=30)
     with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
         s.set_charges(batch.charge_pos, batch.q)
-        info = s.solve(tol=1e-9, precision=bipb.MIXED_TF32)
+        info = s.solve(tol=1e-9, precision=bipb.MIXED_TENSOR)
         e = s.energy()
     for r in range(3):
         assert info[r]["converged"] and info[r]["rel_residual"] <= 1e-9
