@@ -79,7 +79,7 @@ def log(*a):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kirkwood", choices=["kirkwood", "protein_like", "adjoint"])
@@ -178,6 +178,16 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _load_for(step, seconds):
+    """Untimed steps for about `seconds` (keeps the GPU under load around the timed region)."""
+    import torch
+
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        step()
+        torch.cuda.synchronize()
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -700,14 +710,18 @@ def main():
         info, e = step()
     log(f"warm-up: {info} E={e:.6f} kcal/mol")
 
-    # ---- timed region: K steps, events per step, L2 flushed between steps
+    # ---- timed region: K steps, events per step, L2 flushed between steps.
+    # The clock sampler starts during untimed steps before the region and
+    # stops after untimed steps behind it, so that its samples (one per 100
+    # ms) cover the whole region with the GPU under load.
     cs = ClockSampler(local, args.clocks_csv)
+    cs.start()
+    _load_for(step, 0.6)
     bipb.timer_enable(s, True)
     launches0 = bipb.launch_count(s)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     replicas.barrier(world)
     torch.cuda.synchronize()
-    cs.start()
     infos = []
     for k in range(args.steps):
         flush.zero_()
@@ -715,11 +729,12 @@ def main():
         infos.append(step())
         evs[k][1].record()
     torch.cuda.synchronize()
-    clocks = cs.stop()
-    replicas.barrier(world)
     launches = bipb.launch_count(s) - launches0
     timers = bipb.timer_read(s)
     bipb.timer_enable(s, False)
+    _load_for(step, 0.3)
+    clocks = cs.stop()
+    replicas.barrier(world)
     ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = replicas.max_over_ranks(float(sum(ms)), world, dev)
     info0 = infos[-1][0]
