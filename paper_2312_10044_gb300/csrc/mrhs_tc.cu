@@ -211,13 +211,21 @@ __global__ void __launch_bounds__(128) k_tc_rowexp(int n, const float4* __restri
   if (i < n) rowexp[i] = make_int2(scale_exp(m0), scale_exp(m1));
 }
 
-// two FP32 values (the lower k first) as FP16 parts: hi = round(a), lo = round(a - hi)
+// two FP32 values (the lower k first) as FP16 parts: hi = round(a), lo =
+// round(a - hi).  a - hi comes from one mixed-precision addition of -hi
+// (FP16) and a (FP32), exact: |a - hi| is at most half an FP16 unit of hi.
 __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, uint32_t& lo) {
-  const __half2 h = __floats2half2_rn(a0, a1);
-  const float2 hf = __half22float2(h);
-  const __half2 l = __floats2half2_rn(a0 - hf.x, a1 - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
+  asm("{\n\t.reg .b32 hh;\n\t.reg .f16 h0, h1;\n\t.reg .f32 d0, d1;\n\t"
+      "cvt.rn.f16x2.f32 hh, %3, %2;\n\t"
+      "mov.b32 {h0, h1}, hh;\n\t"
+      "neg.f16 h0, h0;\n\t"
+      "neg.f16 h1, h1;\n\t"
+      "add.rn.f32.f16 d0, h0, %2;\n\t"
+      "add.rn.f32.f16 d1, h1, %3;\n\t"
+      "cvt.rn.f16x2.f32 %1, d1, d0;\n\t"
+      "mov.b32 %0, hh;\n\t}"
+      : "=r"(hi), "=r"(lo)
+      : "f"(a0), "f"(a1));
 }
 
 // This thread's kPerThread sources of a chunk (records Sq, first index jq)
