@@ -301,10 +301,11 @@ struct Surface {
   DevBuf<float4> recdf;
   DevBuf<float> upk;   // FP16 right-hand-side tiles of the tensor-core mat-vec (raw storage)
   DevBuf<int> tc_err;  // set by the tensor-core kernel when a bounded wait ran out
-  DevBuf<unsigned> tc_colmax;  // tensor-core mat-vec: max |u| per right-hand side (FP32 bits)
-  DevBuf<int2> tc_rowexp;      // tensor-core mat-vec: per-row scale exponents of the phi and psi rows
-  float tc_rowexp_key[3] = {0.f, 0.f, -1.f};  // the medium (eps, 1/eps, kappa) tc_rowexp was computed for
-  int tc_rowexp_n = -1;
+  DevBuf<int> tc_colmax;    // tensor-core mat-vec: per right-hand side, max over sources of log2|u| - e
+  DevBuf<int2> tc_srcexp;   // tensor-core mat-vec: scale exponents e of each source's phi and psi columns
+  DevBuf<float4> tc_src;    // tensor-core mat-vec: source records with the column scales folded in
+  float tc_src_key[3] = {0.f, 0.f, -1.f};  // the medium (eps, 1/eps, kappa) tc_src was computed for
+  int tc_src_n = -1;
   DevBuf<double4_32a> rec64;
   DevBuf<float> part32;
   DevBuf<double> part64;

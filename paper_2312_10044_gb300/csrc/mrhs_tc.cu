@@ -29,13 +29,19 @@
 // buffers); shared memory carries only the U tiles.
 //
 // Scaling.  FP16 holds 2^-14 .. 65504 at full precision, so both operands are
-// brought to a known range by exact powers of two: row i of tile m is
-// multiplied by 2^e(i, m), chosen once per surface and medium (k_tc_rowexp,
-// over all sources) so that its largest value lies in [2^14, 2^15), and
-// column b of U by 2^f(b), chosen per call from max |u_b| the same way.  The
-// epilogue multiplies each accumulated sum by 2^-(e + f).  A value far below
-// its row's largest loses relative precision in a_lo (FP16 subnormals), but
-// its absolute error stays below 2^-40 of that largest value.
+// brought to a known range by exact powers of two.  Column (j, c) of A (the
+// source unknown phi_j or psi_j) is multiplied by 2^e(j, c), chosen once per
+// surface and medium (k_tc_colexp, over all targets) so that its largest
+// value lies in [2^14, 2^15); the factors are folded into a scaled copy of
+// the source records (area times 2^e(j, 1), normal times 2^(e(j, 0) -
+// e(j, 1)): the K2 and K4 values are linear in n_j, the K1 and K3 values do
+// not depend on it), so generating a scaled value costs nothing extra.  Row
+// (j, c) of U is multiplied by 2^(f(b) - e(j, c)), f(b) chosen per call so
+// that the largest scaled value of right-hand side b lies in [2^14, 2^15).
+// The epilogue multiplies each sum by 2^-f(b).  A value far below its
+// column's (or right-hand side's) largest loses relative precision in its
+// low part (FP16 subnormals), but its absolute error stays below 2^-40 of
+// that largest value.
 //
 // TMEM (512 columns; lane r = target r of the CTA): A buffers 0, 1 at columns
 // 128 s (tile m at + 64 m: hi part + 0..31, lo part + 32..63, two FP16 values
@@ -94,14 +100,17 @@ constexpr int kScaleTop = 14;               // scaled magnitudes lie in [2^14, 2
 constexpr int kScaleClamp = 100;            // scale exponents are clamped to [-100, 100]
 static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
 
-// The exponent e that brings a magnitude m into [2^14, 2^15) by m 2^e,
-// clamped to [-100, 100] (exact for m in [2^-86, 2^114]); 100 for zero.
-__device__ __forceinline__ int scale_exp(float m) {
-  const int lg = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;  // floor(log2 m) for normal m
-  return max(-kScaleClamp, min(kScaleClamp, kScaleTop - lg));
+// floor(log2 |x|) of a normal double (-1023 for zero and subnormals, 1024
+// for infinities and NaN)
+__device__ __forceinline__ int ilog2_bits(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
 }
-// 2^k for |k| <= 126
+// The exponent e that brings a magnitude of floor(log2) lg into [2^14, 2^15)
+// by a factor 2^e, clamped to [-100, 100].
+__device__ __forceinline__ int scale_exp_lg(int lg) { return max(-kScaleClamp, min(kScaleClamp, kScaleTop - lg)); }
+// 2^k for |k| <= 126, and in FP64 for |k| <= 1022
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(127 + k) << 23); }
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
 
 // byte offset of element (row, k) of a chunk's FP16 U tile (K = 32, K-major,
 // no swizzle): core matrices of 8 rows x 8 values (16 bytes a row)
@@ -120,23 +129,34 @@ __device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) 
                : "memory");
 }
 
-// colmax[b] = max_e |u_b[e]| (as FP32 bits; colmax zeroed before): grid (x, nb)
-__global__ void k_colmax_u(int64_t len, const double* __restrict__ u, unsigned* __restrict__ colmax) {
+// colmax[b] = max over sources j and components c of floor(log2 |u_b(j, c)|)
+// - e(j, c), at least -1123 for a nonzero u (colmax preset to a value below
+// -2000 by a byte fill of 0x80): grid (x, nb)
+__global__ void k_colmax_u(int n, const double* __restrict__ u, const int2* __restrict__ srcexp,
+                           int* __restrict__ colmax) {
   const int b = blockIdx.y;
+  const int64_t len = 2 * (int64_t)n;
   const double* ub = u + (int64_t)b * len;
-  float m = 0.f;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x)
-    m = fmaxf(m, fabsf((float)ub[e]));
+  int m = INT_MIN;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = ub[e];
+    const int j = (int)(e < n ? e : e - n);
+    if (v != 0.0) m = max(m, ilog2_bits(v) - (e < n ? srcexp[j].x : srcexp[j].y));
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(colmax + b, __float_as_uint(m));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(colmax + b, m);
 }
 
-// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, u 2^f(b) split into
-// FP16 parts U_hi (rows 0..63) and U_lo (rows 64..127) in the K-major
-// core-matrix layout (row = right-hand side, K = 2 j' + c).
+// the scale exponent f(b) of right-hand side b from colmax[b] (100 for a zero column)
+__device__ __forceinline__ int rhs_exp(int cm) { return cm < -2000 ? kScaleClamp : scale_exp_lg(cm); }
+
+// U (FP64, system b at b * 2n: [phi; psi]) -> per chunk, u 2^(f(b) - e(j, c))
+// split into FP16 parts U_hi (rows 0..63) and U_lo (rows 64..127) in the
+// K-major core-matrix layout (row = right-hand side, K = 2 j' + c).
 __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __restrict__ u,
-                            const unsigned* __restrict__ colmax, __half* __restrict__ upk) {
+                            const int2* __restrict__ srcexp, const int* __restrict__ colmax,
+                            __half* __restrict__ upk) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // one per (chunk, b, k)
   if (e >= (int64_t)n_chunks * kNB * kK) return;
   const int ch = (int)(e / (kNB * kK));
@@ -145,7 +165,8 @@ __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __rest
   const int j = ch * kChunk + (k >> 1), c = k & 1;
   __half hi = __float2half_rn(0.f), lo = hi;
   if (b < n_rhs && j < n) {
-    const double v = u[(int64_t)b * 2 * n + (int64_t)c * n + j] * (double)pow2f(scale_exp(__uint_as_float(colmax[b])));
+    const int2 ej = srcexp[j];
+    const double v = u[(int64_t)b * 2 * n + (int64_t)c * n + j] * pow2d(rhs_exp(colmax[b]) - (c ? ej.y : ej.x));
     hi = __float2half_rn((float)v);
     lo = __float2half_rn((float)(v - (double)__half2float(hi)));
   }
@@ -156,11 +177,8 @@ __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __rest
 
 // The four kernel values of pair (target i, source j) times ds_j (times 4 pi),
 // in FP32: returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3].
-// With rs0 = rs1 = 1 the values are unscaled; otherwise (K2, K1) come times
-// rs0 and (K4, K3) times rs1 (powers of two: the scaling is exact).
 __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float nxi, float nyi, float nzi, float4 g,
-                                             float4 nv, bool zero, const PairConst<float>& c, float* v,
-                                             float rs0 = 1.f, float r10 = 1.f) {
+                                             float4 nv, bool zero, const PairConst<float>& c, float* v) {
   const float dx = xi - g.x, dy = yi - g.y, dz = zi - g.z;
   const float r2 = dx * dx + dy * dy + dz * dz;
   float s = fminf(rsqrt_approx(r2), kSMaxF);
@@ -174,41 +192,53 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   const float t = e * kr + e;
   const float tm1 = t - 1.f;
   const float wm3 = (t - e) * kr + 3.f * tm1;
-  const float sa = (s * g.w) * rs0;
+  const float sa = s * g.w;
   const float s2 = s * s;
   const float s3a = s2 * sa;
-  const float s3b = s3a * r10;
   v[1] = sa - e * sa;                                  // K1 ds = (1 - e) s ds
   v[0] = ((c.eps * t - 1.f) * cj) * s3a;               // K2 ds
-  v[3] = ((t * c.inveps - 1.f) * ci) * s3b;            // K3 ds
-  v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3b;   // K4 ds
+  v[3] = ((t * c.inveps - 1.f) * ci) * s3a;            // K3 ds
+  v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
 }
 
-// Row scale exponents: for target i, e(i, 0) from the largest |K2 ds|, |K1 ds|
-// and e(i, 1) from the largest |K4 ds|, |K3 ds| over all sources j != i (the
-// same FP32 values the tensor-core kernel generates).  One thread per target.
-__global__ void __launch_bounds__(128) k_tc_rowexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
-                                                   int2* __restrict__ rowexp) {
+// Column scale exponents: for source j, e(j, 0) from the largest |K2 ds_j|,
+// |K4 ds_j| and e(j, 1) from the largest |K1 ds_j|, |K3 ds_j| over all
+// targets i != j (the same FP32 values the tensor-core kernel generates), the
+// two kept within 2^60 of each other by lowering the larger (so that the
+// scaled normal stays a normal FP32 vector); and the scaled source records.
+// One thread per source.
+__global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
+                                                   int2* __restrict__ srcexp, float4* __restrict__ src) {
   __shared__ float4 sh[2 * 128];
-  const int i = blockIdx.x * 128 + threadIdx.x;
-  const int ii = min(i, n - 1);
-  const float4 gi = tgt32[2 * ii], ni = tgt32[2 * ii + 1];
+  const int j = blockIdx.x * 128 + threadIdx.x;
+  const int jj = min(j, n - 1);
+  const float4 gj = tgt32[2 * jj], nj = tgt32[2 * jj + 1];
   float m0 = 0.f, m1 = 0.f;
-  for (int j0 = 0; j0 < n; j0 += 128) {
+  for (int i0 = 0; i0 < n; i0 += 128) {
     __syncthreads();
-    const int jl = min(j0 + (int)threadIdx.x, n - 1);
-    sh[2 * threadIdx.x] = tgt32[2 * jl];
-    sh[2 * threadIdx.x + 1] = tgt32[2 * jl + 1];
+    const int il = min(i0 + (int)threadIdx.x, n - 1);
+    sh[2 * threadIdx.x] = tgt32[2 * il];
+    sh[2 * threadIdx.x + 1] = tgt32[2 * il + 1];
     __syncthreads();
-    const int cnt = min(128, n - j0);
-    for (int jj = 0; jj < cnt; ++jj) {
+    const int cnt = min(128, n - i0);
+    for (int ii = 0; ii < cnt; ++ii) {
+      const float4 g = sh[2 * ii], nv = sh[2 * ii + 1];
       float v[4];
-      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, sh[2 * jj], sh[2 * jj + 1], j0 + jj == ii, c, v);
-      m0 = fmaxf(m0, fmaxf(fabsf(v[0]), fabsf(v[1])));
-      m1 = fmaxf(m1, fmaxf(fabsf(v[2]), fabsf(v[3])));
+      kernel_block(g.x, g.y, g.z, nv.x, nv.y, nv.z, gj, nj, i0 + ii == jj, c, v);
+      m0 = fmaxf(m0, fmaxf(fabsf(v[0]), fabsf(v[2])));
+      m1 = fmaxf(m1, fmaxf(fabsf(v[1]), fabsf(v[3])));
     }
   }
-  if (i < n) rowexp[i] = make_int2(scale_exp(m0), scale_exp(m1));
+  if (j >= n) return;
+  // floor(log2 m) of a positive normal float (zero: a very small value)
+  auto lg = [](float m) { return m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xffu) - 127 : -1000; };
+  int e0 = scale_exp_lg(lg(m0)), e1 = scale_exp_lg(lg(m1));
+  if (e0 - e1 > 60) e0 = e1 + 60;
+  if (e1 - e0 > 60) e1 = e0 + 60;
+  srcexp[j] = make_int2(e0, e1);
+  const float r01 = pow2f(e0 - e1);
+  src[2 * j] = make_float4(gj.x, gj.y, gj.z, gj.w * pow2f(e1));
+  src[2 * j + 1] = make_float4(nj.x * r01, nj.y * r01, nj.z * r01, 0.f);
 }
 
 // two FP32 values (the lower k first) as FP16 parts: hi = round(a), lo =
@@ -235,7 +265,7 @@ __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, ui
 // target, a source past the end or the self pair.
 template <bool EDGE>
 __device__ __forceinline__ void gen_chunk(const float4& gi, const float4& ni, const float4* Sq, int jq, int ti, int n,
-                                          bool tvalid, const PairConst<float>& c, float rs0, float r10, uint32_t acol) {
+                                          bool tvalid, const PairConst<float>& c, uint32_t acol) {
 #pragma unroll
   for (int hh = 0; hh < kPerThread / 4; ++hh) {
     uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
@@ -244,7 +274,7 @@ __device__ __forceinline__ void gen_chunk(const float4& gi, const float4& ni, co
       const int jj = 4 * hh + u;
       const bool z = EDGE && (!tvalid || jq + jj >= n || jq + jj == ti);
       float v[4];
-      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], z, c, v, rs0, r10);
+      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], z, c, v);
       if (EDGE) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = z ? 0.f : v[k];
@@ -273,8 +303,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
-                                                    const float4* __restrict__ tgt32, const int2* __restrict__ rowexp,
-                                                    const unsigned* __restrict__ colmax,
+                                                    const float4* __restrict__ tgt32, const float4* __restrict__ src,
+                                                    const int* __restrict__ colmax,
                                                     const __half* __restrict__ upk, float* __restrict__ part,
                                                     PairConst<float> c, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -305,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     tc::mbar_init(drained, kGenThreads / 32);
     tc::fence_mbar_init();
   }
-  if (tid < kNB) cinv[tid] = pow2f(-scale_exp(__uint_as_float(colmax[tid])));
+  if (tid < kNB) cinv[tid] = pow2f(-rhs_exp(colmax[tid]));
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::fence_before_sync();
   __syncthreads();
@@ -335,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
         const int ch = c0 + x;
         const int cnt = min(kChunk, n - ch * kChunk);
         arrive_expect_tx(&sfull[q], cnt * 32);
-        bulk_load(smem + kOffS + q * kSBytes, tgt32 + 2 * (int64_t)ch * kChunk, cnt * 32, &sfull[q]);
+        bulk_load(smem + kOffS + q * kSBytes, src + 2 * (int64_t)ch * kChunk, cnt * 32, &sfull[q]);
         arrive_expect_tx(&ufull[q], kUBytes);
         bulk_load(smem + kOffB + q * kUBytes, reinterpret_cast<const unsigned char*>(upk) + (int64_t)ch * kUBytes,
                   kUBytes, &ufull[q]);
@@ -388,8 +418,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     const int ti = t0 + 32 * wq + lane;
     const bool tvalid = ti < n;
     const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
-    const int2 re = rowexp[min(ti, n - 1)];
-    const float rs0 = pow2f(re.x), r10 = pow2f(re.y - re.x);  // the psi row's scale relative to the phi row's
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
     const uint32_t dthr = tmem + lane_base + kColD + (sq >> 1) * 128 + 32 * (sq & 1);
     const bool tile_edge = t0 + kTgt > n;
@@ -445,9 +473,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       const uint32_t acol = tmem + lane_base + kColA + s * kACols + kPerThread * sq;
       // one branch per chunk: the masked form only where a chunk needs it
       if (edge)
-        gen_chunk<true>(gi, ni, Sq, jq, ti, n, tvalid, c, rs0, r10, acol);
+        gen_chunk<true>(gi, ni, Sq, jq, ti, n, tvalid, c, acol);
       else
-        gen_chunk<false>(gi, ni, Sq, jq, ti, n, tvalid, c, rs0, r10, acol);
+        gen_chunk<false>(gi, ni, Sq, jq, ti, n, tvalid, c, acol);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
@@ -460,19 +488,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   if (!all_ok && tid == 0) atomicExch(err, 1);
 
   // epilogue: this thread holds target 32 wq + lane, component sq >> 1 (tile),
-  // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-(e + f)
+  // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-f(b)
   if (all_ok && n_it > 0 && warp < kMmaWarp) {  // the generating warps
     const int sq = warp >> 2;
     const int i = t0 + 32 * wq + lane, comp = sq >> 1;
-    if (i < n) {
-      const int2 re = rowexp[i];
-      const float rinv = pow2f(-(comp ? re.y : re.x));
+    if (i < n)
 #pragma unroll
       for (int x = 0; x < 32; ++x) {
         const int b = 32 * (sq & 1) + x;
-        if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x] * rinv * cinv[b];
+        if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x] * cinv[b];
       }
-    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -537,15 +562,17 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     s->grow(s->tc_err, 1);
     BIPB_CUDA(cudaMemsetAsync(s->tc_err.p, 0, sizeof(int), s->stream));
   }
-  // row scale exponents: once per surface and medium (a buffer that moved is recomputed)
+  // column scale exponents and scaled source records: once per surface and
+  // medium (buffers that moved are recomputed)
   const uint64_t gen0 = s->alloc_gen;
-  s->grow(s->tc_rowexp, (size_t)n);
-  if (s->alloc_gen != gen0 || s->tc_rowexp_n != n || s->tc_rowexp_key[0] != c.eps || s->tc_rowexp_key[1] != c.inveps ||
-      s->tc_rowexp_key[2] != c.kappa) {
-    k_tc_rowexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_rowexp.p);
+  s->grow(s->tc_srcexp, (size_t)n);
+  s->grow(s->tc_src, (size_t)2 * n);
+  if (s->alloc_gen != gen0 || s->tc_src_n != n || s->tc_src_key[0] != c.eps || s->tc_src_key[1] != c.inveps ||
+      s->tc_src_key[2] != c.kappa) {
+    k_tc_colexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
     BIPB_LAUNCHED(s);
-    s->tc_rowexp_n = n;
-    s->tc_rowexp_key[0] = c.eps, s->tc_rowexp_key[1] = c.inveps, s->tc_rowexp_key[2] = c.kappa;
+    s->tc_src_n = n;
+    s->tc_src_key[0] = c.eps, s->tc_src_key[1] = c.inveps, s->tc_src_key[2] = c.kappa;
   }
   // per block of up to 64 right-hand sides: pack, tensor-core pass, FP64 reduction
   for (int b0 = 0; b0 < K; b0 += kNB) {
@@ -568,16 +595,17 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     double* yb = y + (int64_t)b0 * 2 * n;
     const int64_t pk = (int64_t)n_chunks * kNB * kK;
     __half* upk = reinterpret_cast<__half*>(s->upk.p);
-    BIPB_CUDA(cudaMemsetAsync(s->tc_colmax.p, 0, kNB * sizeof(unsigned), s->stream));
+    BIPB_CUDA(cudaMemsetAsync(s->tc_colmax.p, 0x80, kNB * sizeof(int), s->stream));
     k_colmax_u<<<dim3((unsigned)std::min<int64_t>(64, (2 * (int64_t)n + 255) / 256), nb), 256, 0, s->stream>>>(
-        2 * (int64_t)n, ub, s->tc_colmax.p);
+        n, ub, s->tc_srcexp.p, s->tc_colmax.p);
     BIPB_LAUNCHED(s);
-    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, s->tc_colmax.p, upk);
+    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, s->tc_srcexp.p,
+                                                                  s->tc_colmax.p, upk);
     BIPB_LAUNCHED(s);
     {
       TimedLaunch tl(s, kTMvTC);
       k_mrhs_tc<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p,
-                                                               s->tc_rowexp.p, s->tc_colmax.p, upk, s->part32.p, c,
+                                                               s->tc_src.p, s->tc_colmax.p, upk, s->part32.p, c,
                                                                s->tc_err.p);
       BIPB_LAUNCHED(s);
     }
