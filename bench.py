@@ -99,7 +99,7 @@ def parse():
                     help="FP32 mat-vec variant (default: autotuned; --mode matvec32: the handle's default)")
     ap.add_argument("--ordered-pairs", action="store_true",
                     help="FP64 / double-float mat-vecs visit every ordered pair (default: unordered pairs once)")
-    ap.add_argument("--configs", default="3,4a,4b,5",
+    ap.add_argument("--configs", default="3,4a,4b,4bs,5",
                     help="--mode configs: which larger configurations (5fd: the full-size central-difference check)")
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "matvec32", "matvec64", "matvecdf", "matvecdfm", "matvectc", "matvectree",
@@ -465,6 +465,29 @@ def run_configs(args):
                    "solve_ms_mixed_df64": ms, "iters": [i["iters"] for i in info],
                    "rel_residual_max": max(i["rel_residual"] for i in info)}
             # the same surfaces one at a time
+            tot = 0.0
+            for q in probs:
+                with bipb.Surface(q.centroids, q.normals, q.areas) as s1:
+                    s1.set_charges(q.charge_pos, q.q)
+                    s1.solve(prm)
+                    m1, _ = _timed(lambda: s1.solve(prm), torch)
+                    tot += m1
+            res["solve_ms_one_at_a_time"] = tot
+            emit(res)
+    if "4bs" in which:
+        # many small uneven surfaces, where one launch per pass over all of them
+        # (instead of one solve per surface) pays
+        probs = synth.uneven_batch_problems(levels=(2, 3, 3, 4) * 8, seed0=4200)
+        with bipb.BatchSurface([(q.centroids, q.normals, q.areas) for q in probs]) as s:
+            s.set_charges([(q.charge_pos, q.q[0]) for q in probs])
+            prm = bipb.solve_params(probs[0].eps_in, probs[0].eps_out, probs[0].kappa, tol=TOL,
+                                    precision=bipb.MIXED_DF64)
+            s.solve(prm)
+            ms, info = _timed(lambda: s.solve(prm), torch)
+            res = {"config": "uneven batch of small surfaces: 32 displaced spheres, levels 2,3,3,4 x 8",
+                   "sizes": [q.n for q in probs], "sum_n2": sum(q.n * q.n for q in probs),
+                   "solve_ms_mixed_df64": ms, "iters_max": max(i["iters"] for i in info),
+                   "rel_residual_max": max(i["rel_residual"] for i in info)}
             tot = 0.0
             for q in probs:
                 with bipb.Surface(q.centroids, q.normals, q.areas) as s1:

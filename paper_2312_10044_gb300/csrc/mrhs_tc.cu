@@ -8,14 +8,14 @@
 // once,
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i, tile 0)
 //     [ K4 ds_j   K3 ds_j ]        (row psi_i, tile 1)     (Sec. 2.2.1, Eqs. 5-6)
-// in FP32, scale every row by a power of two (below), split each value a into
-// two FP16 parts (a_hi = a rounded to FP16, a_lo = a - a_hi rounded to FP16:
+// in FP32 (each column scaled by a power of two through scaled source
+// records, below), split each value a into two FP16 parts (a_hi = a rounded to FP16, a_lo = a - a_hi rounded to FP16:
 // 22 significant bits together) and write both into tensor memory, where the
 // MMA reads its A operand: the thread that owns TMEM lane r owns target r's
 // row in both tiles, so it computes a pair's four values once and writes each
 // where it belongs (four threads per target, one quarter of the chunk's
 // sources each).  The U tile of a chunk (U_hi in rows 0..63, U_lo in rows
-// 64..127, each column scaled by a power of two; packed per chunk in global
+// 64..127, each row scaled by a power of two; packed per chunk in global
 // memory by k_pack_u_tc, K-major core-matrix layout) arrives by a bulk copy
 // into shared memory, and one thread issues, per K step of 16 and tile, two
 // tcgen05.mma kind::f16 (M = 128, N = 128, K = 16, A in TMEM, B in shared
