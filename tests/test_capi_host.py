@@ -102,6 +102,13 @@ def test_null_and_stale_handles_are_rejected(bipb):
     e = np.zeros(1)
     assert L.bipb_energy(ctypes.c_void_p(12345678), e.ctypes.data_as(ctypes.c_void_p)) == bipb.BIPB_ERR_STATE
     assert L.bipb_surface_size(None) == 0
+    # the device-pointer and far-field entry points check the handle first as well
+    stale = ctypes.c_void_p(12345678)
+    assert L.bipb_charges_set_dev(None, 1, None, 1, 1, None) == bipb.BIPB_ERR_STATE
+    assert L.bipb_energy_dev(stale, None) == bipb.BIPB_ERR_STATE
+    assert L.bipb_energy_grad_dev(None, None, None, None) == bipb.BIPB_ERR_STATE
+    assert L.bipb_treecode(stale, 0.5, 6, 256) == bipb.BIPB_ERR_STATE
+    assert L.bipb_treecode_stats(None, None, None, None) == bipb.BIPB_ERR_STATE
 
 
 def test_solve_params_layout_matches_header(bipb):
