@@ -654,6 +654,28 @@ def test_tensor_core_matvec_scaled_inputs(bipb, orc, geo_scale):
         assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max(), r
 
 
+@pytest.mark.parametrize("n_keep", [2, 7, 80, 200])
+def test_tensor_core_matvec_small_surfaces(bipb, orc, n_keep):
+    """Surfaces smaller than one source chunk (32) and one target tile (128):
+    two elements (the smallest surface the library takes), a ragged first chunk and
+    a partly filled tile, against the FP64 oracle at the FP32 bounds."""
+    p = synth.protein_like_problem(level=2, n_charges=5, seed=8)  # 320 elements
+    keep = np.sort(np.random.default_rng(n_keep).choice(p.n, n_keep, replace=False))
+    c, nv, a = p.centroids[keep], p.normals[keep], p.areas[keep]
+    eps = p.eps_out / p.eps_in
+    U = np.random.default_rng(50 + n_keep).standard_normal((3, 2 * n_keep))
+    with bipb.Surface(c, nv, a) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TENSOR, med=_med(bipb, p))
+        Y = yd.cpu().numpy()
+    for r in range(3):
+        ref = orc.matvec(c, nv, a, eps, p.kappa, U[r])
+        assert np.all(np.isfinite(Y[r]))
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6
+        assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
+
+
 def test_mixed_tensor_solve_matches_oracle(bipb, orc):
     base = synth.protein_like_problem(level=4, n_charges=30)
     batch = synth.batched_charges(base, n_rhs=3, n_charges=30)
