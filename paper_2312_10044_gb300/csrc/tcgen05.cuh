@@ -1,16 +1,16 @@
 // Thin inline-PTX wrappers for the 5th-generation tensor core (tcgen05) on
 // sm_103a: shared-memory matrix descriptors, instruction descriptors, TMEM
-// allocation, MMA issue and commit, TMEM loads, mbarriers and fences.
+// allocation, MMA issue and commit, TMEM loads and stores, mbarriers and
+// fences.
 //
-// Operand layout used here: "K-major, no swizzle".  A (M x K) and B (N x K,
-// i.e. the GEMM's K x N matrix stored with K contiguous) are tiled into core
-// matrices of 8 rows x 16 bytes (4 FP32/TF32 values); each core matrix is 128
-// contiguous bytes, rows 16 bytes apart.  Core matrix (g, c) of rows
-// [8g, 8g+8) and K-columns [4c, 4c+4) sits at byte ((g * KB + c) * 128) with
-// KB = K / 4 core matrices per row group, so the K-direction neighbour is
-// 128 bytes away (leading byte offset) and the next row group KB * 128 bytes
-// (stride byte offset).  One kind::tf32 MMA consumes K = 8 (two core
-// matrices); the k-th step starts 256 * k bytes further.
+// Operand layout used here: "K-major, no swizzle".  B (N x K, i.e. the GEMM's
+// K x N matrix stored with K contiguous) is tiled into core matrices of 8 rows
+// x 16 bytes (8 FP16 values); each core matrix is 128 contiguous bytes, rows
+// 16 bytes apart.  The K-direction neighbour of a core matrix is 128 bytes
+// away (leading byte offset) and the next group of 8 rows (K / 8) * 128 bytes
+// (stride byte offset).  One kind::f16 MMA consumes K = 16 (two core
+// matrices); the k-th K step starts 256 * k bytes further.  A sits in tensor
+// memory: lane = row, two FP16 values of consecutive k per 32-bit column.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,11 +20,6 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// byte offset of element (row, k) of a K-major, no-swizzle tile with K columns
-__host__ __device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int K) {
-  return (uint32_t)((((row >> 3) * (K >> 2) + (k >> 2)) * 8 + (row & 7)) * 16 + (k & 3) * 4);
 }
 
 // Shared-memory matrix descriptor: start address, leading and stride byte
@@ -38,37 +33,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
-// Instruction descriptor of kind::tf32: D in FP32 (bits 4-5 = 1), A and B in
-// TF32 (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in
-// bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 // Instruction descriptor of kind::f16 with FP16 A and B (bits 7-9 and 10-12 =
 // 0) and an FP32 accumulator (bits 4-5 = 1), both K-major.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// The same MMA with A in tensor memory (M rows in TMEM lanes, K in columns,
-// one 32-bit column per TF32 element) and B in shared memory.
-__device__ __forceinline__ void mma_tf32_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
 }
 
 // kind::f16 MMA (K = 16) with A in tensor memory: lane = row, each 32-bit
@@ -100,25 +68,10 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// make this thread's generic shared-memory writes visible to the tensor core
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32w .. 32w+31).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// The same load without its wait: the 16 registers may be read only after
-// tmem_wait_ld16 on them (which ties them to the wait, so the compiler
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
+// 32 (w % 4) .. + 31), without the wait: the 16 registers may be read only
+// after tmem_wait_ld16 on them (which ties them to the wait, so the compiler
 // cannot move their uses above it).
 __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
@@ -136,22 +89,6 @@ __device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16]) {
                : "memory");
 }
 
-// 16 consecutive FP32 columns into this thread's TMEM lane (warp w writes lanes
-// 32 (w % 4) .. 32 (w % 4) + 31); complete after tmem_wait_st.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};" ::"r"(taddr),
-      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
-      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15])
-      : "memory");
-}
-// 8 consecutive FP32 columns into this thread's TMEM lane.
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-               "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
-               : "memory");
-}
 // 4 consecutive 32-bit columns into this thread's TMEM lane.
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
@@ -164,31 +101,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Non-blocking test of a phase (no suspension: the caller spins).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded spin on mbar_test_wait: for a thread that must react at once.
-__device__ __forceinline__ bool mbar_spin(uint64_t* bar, uint32_t parity, long max_spins) {
-  for (long i = 0; i < max_spins; ++i)
-    if (mbar_test_wait(bar, parity)) return true;
-  return false;
-}
 // try_wait that may suspend the thread until the phase completes (or the
 // hint, in ns, runs out), so a waiting warp takes no issue slots.
 __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
@@ -213,12 +125,6 @@ __device__ __forceinline__ bool mbar_wait_timed(uint64_t* bar, uint32_t parity, 
   do {
     if (mbar_try_wait_hint(bar, parity, kHintNs)) return true;
   } while (globaltimer_ns() - t0 < limit_ns);
-  return false;
-}
-// Bounded wait: gives up after max_spins polls and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long max_spins) {
-  for (long i = 0; i < max_spins; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
 
