@@ -203,10 +203,11 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
 
 // Column scale exponents: for source j, e(j, 0) from the largest |K2 ds_j|,
 // |K4 ds_j| and e(j, 1) from the largest |K1 ds_j|, |K3 ds_j| over all
-// targets i != j (the same FP32 values the tensor-core kernel generates), the
-// two kept within 2^60 of each other by lowering the larger (so that the
-// scaled normal stays a normal FP32 vector); and the scaled source records.
-// One thread per source.
+// targets i != j (the same FP32 values the tensor-core kernel generates); 0
+// for a column of zeros (no dielectric contrast and kappa = 0), and the two
+// kept within 2^40 of each other by lowering the larger, so that the scaled
+// normal and the products formed from it stay far from the FP32 range.  Then
+// the scaled source records.  One thread per source.
 __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
                                                    int2* __restrict__ srcexp, float4* __restrict__ src) {
   __shared__ float4 sh[2 * 128];
@@ -230,11 +231,11 @@ __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restri
     }
   }
   if (j >= n) return;
-  // floor(log2 m) of a positive normal float (zero: a very small value)
-  auto lg = [](float m) { return m > 0.f ? (int)((__float_as_uint(m) >> 23) & 0xffu) - 127 : -1000; };
-  int e0 = scale_exp_lg(lg(m0)), e1 = scale_exp_lg(lg(m1));
-  if (e0 - e1 > 60) e0 = e1 + 60;
-  if (e1 - e0 > 60) e1 = e0 + 60;
+  // floor(log2 m) of a positive normal float
+  auto lg = [](float m) { return (int)((__float_as_uint(m) >> 23) & 0xffu) - 127; };
+  int e0 = m0 > 0.f ? scale_exp_lg(lg(m0)) : 0, e1 = m1 > 0.f ? scale_exp_lg(lg(m1)) : 0;
+  if (e0 - e1 > 40) e0 = e1 + 40;
+  if (e1 - e0 > 40) e1 = e0 + 40;
   srcexp[j] = make_int2(e0, e1);
   const float r01 = pow2f(e0 - e1);
   src[2 * j] = make_float4(gj.x, gj.y, gj.z, gj.w * pow2f(e1));

@@ -106,14 +106,16 @@ def test_degenerate_media(bipb, orc):
             f = orc.matvec_t if transpose else orc.matvec
             ref = np.stack([f(p.centroids, p.normals, p.areas, 80.0, 0.0, u) for u in U])
             for prec, variant, tol in ((bipb.FP64, 0, 1e-12), (bipb.DF64, 0, 2e-12), (bipb.FP32, 0, 2e-5),
-                                       (bipb.FP32, 7, 2e-5), (bipb.FP32, 9, 2e-5)):
+                                       (bipb.FP32, 7, 2e-5), (bipb.FP32, 9, 2e-5), (bipb.TENSOR, 9, 2e-5)):
+                if prec == bipb.TENSOR and transpose:
+                    continue  # the tensor-core path has no transpose
                 s.set_variant(variant)
                 yd = torch.full_like(ud, float("nan"))
                 s.matvec(ud, yd, precision=prec, transpose=transpose, med=med0)
                 err = np.abs(yd.cpu().numpy() - ref).max()
                 assert err < tol * np.abs(ref).max(), (prec, variant, transpose)
         unit = bipb.medium(1.0, 1.0, 0.0)
-        for prec in (bipb.FP64, bipb.DF64, bipb.FP32):
+        for prec in (bipb.FP64, bipb.DF64, bipb.FP32, bipb.TENSOR):
             yd = torch.full_like(ud, float("nan"))
             s.matvec(ud, yd, precision=prec, med=unit)
             assert torch.equal(yd, ud), prec
