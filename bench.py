@@ -523,9 +523,11 @@ def run_configs(args):
 
 def far_field_timings(bipb, torch, s, p):
     """The far-field (treecode) FP32 mat-vec of Sec. 2.2.3 with its default
-    parameters against the direct FP32 mat-vec, and the mixed solve with it
-    (MIXED_TREE, plain and with the self-block preconditioner) against the
-    direct mixed solve; s is a handle of problem p with its charges set."""
+    parameters (and its transpose) against the direct FP32 mat-vec, and the
+    mixed solve with it (MIXED_TREE, plain and with the self-block
+    preconditioner) against the direct mixed solve, plus the energy gradient
+    whose adjoint solve takes the far-field transpose; s is a handle of
+    problem p with its charges set."""
     n = p.n
     med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
     u = torch.randn(2 * n, dtype=torch.float64, device="cuda")
@@ -535,9 +537,11 @@ def far_field_timings(bipb, torch, s, p):
     out["tree_pairs_per_matvec"] = pairs
     out["tree_pairs_frac_of_direct"] = pairs / (n * (n - 1))
     out["tree_far_clusters"], out["tree_leaves"] = far, leaves
-    for name, prec, reps in (("tree32", bipb.TREE32, 10), ("fp32_direct", bipb.FP32, 5)):
-        s.matvec(u, y, precision=prec, med=med)
-        ms, _ = _timed(lambda: [s.matvec(u, y, precision=prec, med=med) for _ in range(reps)], torch)
+    for name, prec, reps, tr in (("tree32", bipb.TREE32, 10, False), ("fp32_direct", bipb.FP32, 5, False),
+                                 ("tree32_transpose", bipb.TREE32, 10, True),
+                                 ("fp32_direct_transpose", bipb.FP32, 5, True)):
+        s.matvec(u, y, precision=prec, transpose=tr, med=med)
+        ms, _ = _timed(lambda: [s.matvec(u, y, precision=prec, transpose=tr, med=med) for _ in range(reps)], torch)
         out[f"matvec_ms_{name}"] = ms / reps
     bipb.timer_enable(s, True)
     s.matvec(u, y, precision=bipb.TREE32, med=med)
@@ -552,6 +556,8 @@ def far_field_timings(bipb, torch, s, p):
         ms, info = _timed(lambda: s.solve(prm), torch)
         out[f"solve_ms_{name}"] = ms
         out[f"{name}_info"] = dict(info[0], energy_kcal=float(s.energy()[0]))
+        gms, _ = _timed(lambda: s.energy_grad(prm), torch)
+        out[f"energy_grad_ms_{name}"] = gms
     return out
 
 

@@ -69,12 +69,12 @@ typedef enum {
   BIPB_MIXED_TENSOR = 6, /* tensor-core mat-vec inside GMRES, double-float refinement residual */
   BIPB_TF32 = BIPB_TENSOR,             /* earlier name of BIPB_TENSOR */
   BIPB_MIXED_TF32 = BIPB_MIXED_TENSOR, /* earlier name of BIPB_MIXED_TENSOR */
-  BIPB_TREE32 = 7,     /* mat-vec only, forward, single-surface handles: the far-field (treecode) operator
-                          of Sec. 2.2.3 in FP32 pair arithmetic, FP64 sums across work items
-                          (bipb_treecode sets its parameters) */
-  BIPB_MIXED_TREE = 8  /* far-field FP32 mat-vec inside GMRES, double-float refinement residual (the
-                          residual stays the direct sum, so the solve still reaches tol on the exact
-                          discrete system); adjoint solves use the direct FP32 transpose inside */
+  BIPB_TREE32 = 7,     /* mat-vec only, single-surface handles: the far-field (treecode) operator of
+                          Sec. 2.2.3 (A u, or A^T u with the same tree, lists and proxies) in FP32 pair
+                          arithmetic, FP64 sums across work items (bipb_treecode sets its parameters) */
+  BIPB_MIXED_TREE = 8  /* far-field FP32 mat-vec inside GMRES (its transpose in adjoint solves),
+                          double-float refinement residual (the residual stays the direct sum, so the
+                          solve still reaches tol on the exact discrete system) */
 } bipb_precision;
 
 /* Dielectric medium (Sec. 2.1): eps_in > 0 inside, eps_out > 0 outside, kappa >= 0 (1/A). */
@@ -279,8 +279,8 @@ bipb_status bipb_energy_grad_dev(bipb_surface s, const bipb_solve_params* p, dou
  *   precision: BIPB_FP64, BIPB_FP32 (FP32 pair arithmetic per source tile,
  *   FP64 sums across tiles and for the diagonal), BIPB_DF64, BIPB_TENSOR
  *   (single-surface handles, forward only; the tensor-core path of the
- *   multi-RHS mat-vec) or BIPB_TREE32 (single-surface handles, forward only;
- *   the far-field operator).
+ *   multi-RHS mat-vec) or BIPB_TREE32 (single-surface handles, both
+ *   directions; the far-field operator).
  */
 bipb_status bipb_matvec(bipb_surface s, const bipb_medium* m, int precision, int transpose,
                         int n_vec, const double* u, double* y);

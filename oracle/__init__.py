@@ -63,6 +63,7 @@ def lib():
         L.orc_matvec_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
         L.orc_matvec_t_rows.argtypes = [I, P, P, P, D, D, P, I, P, P]
         L.orc_record_sums.argtypes = [I, P, P, P, I, P, P, P, P, D, D, P]
+        L.orc_record_sums_t.argtypes = [I, P, P, P, I, P, P, P, P, D, D, P]
         L.orc_assemble.argtypes = [I, P, P, P, D, D, P]
         L.orc_gesv.argtypes = [I, P, I, P]
         L.orc_gesv.restype = ctypes.c_int

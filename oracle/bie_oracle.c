@@ -248,6 +248,36 @@ void orc_record_sums(int64_t nt, const double* xt, const double* nrm_t, const in
   }
 }
 
+/*
+ * The same sums for A^T w.  Output element t (position x_t, normal n_t)
+ * gathers column t of A: the entries of row element i depend on n_i only
+ * through the kernels K3 and K4 (normal derivatives at x_i), linearly, so a
+ * record j carries a position y_j, w_j (wphi of an element) and a vector
+ * p_j (wpsi n_i of an element) in place of the row normal:
+ *   out[2t]     = sum_j [K2(y_j, x_t) w_j + K4(y_j, x_t; p_j)]   (phi output)
+ *   out[2t + 1] = sum_j [K1(y_j, x_t) w_j + K3(y_j, x_t; p_j)]   (psi output)
+ * with the kernels evaluated with y_j as the collocation point and x_t as the
+ * source, as in orc_matvec_t.  The output element's area multiplies the sums
+ * outside.  A record whose id equals the target's id is skipped.
+ */
+void orc_record_sums_t(int64_t nt, const double* xt, const double* nrm_t, const int64_t* tid, int64_t ns,
+                       const double* ys, const double* w, const double* p, const int64_t* sid, double eps,
+                       double kappa, double* out) {
+  int64_t t;
+#pragma omp parallel for schedule(static)
+  for (t = 0; t < nt; ++t) {
+    double zp = 0.0, zs = 0.0, K[4];
+    for (int64_t j = 0; j < ns; ++j) {
+      if (sid[j] == tid[t]) continue;
+      orc_kernels(ys + 3 * j, p + 3 * j, xt + 3 * t, nrm_t + 3 * t, eps, kappa, K);
+      zp += K[1] * w[j] + K[3];
+      zs += K[0] * w[j] + K[2];
+    }
+    out[2 * t] = zp;
+    out[2 * t + 1] = zs;
+  }
+}
+
 /* Dense A (2n x 2n, row-major), same entries as orc_matvec. */
 void orc_assemble(int64_t n, const double* x, const double* nrm, const double* area, double eps,
                   double kappa, double* A) {

@@ -185,26 +185,41 @@ def proxies(t, k, x, a, m, degree):
     return pos, Lk.T @ a[idx], Lk.T @ m[idx]
 
 
-def _record_sums(xt, nt, tid, ys, a, m, sid, eps, kappa):
-    """Per target: [sum (K1 a + K2(m)), sum (K3 a + K4(m))] over the records,
-    skipping a record whose id equals the target's (the self pair)."""
+def _record_sums(xt, nt, tid, ys, a, m, sid, eps, kappa, transpose=False):
+    """Per target: [sum (K1 a + K2(m)), sum (K3 a + K4(m))] over the records
+    (transpose: the phi and psi outputs of A^T, [sum (K2 w + K4(p)), sum (K1 w
+    + K3(p))] with a = w, m = p), skipping a record whose id equals the
+    target's (the self pair)."""
     xt, nt, ys, a, m = _c(xt), _c(nt), _c(ys), _c(a), _c(m)
     tid = np.ascontiguousarray(tid, dtype=np.int64)
     sid = np.ascontiguousarray(sid, dtype=np.int64)
     out = np.zeros((xt.shape[0], 2))
-    lib().orc_record_sums(xt.shape[0], _p(xt), _p(nt), tid.ctypes.data_as(ctypes.c_void_p), ys.shape[0], _p(ys),
-                          _p(a), _p(m), sid.ctypes.data_as(ctypes.c_void_p), eps, kappa, _p(out))
+    f = lib().orc_record_sums_t if transpose else lib().orc_record_sums
+    f(xt.shape[0], _p(xt), _p(nt), tid.ctypes.data_as(ctypes.c_void_p), ys.shape[0], _p(ys), _p(a), _p(m),
+      sid.ctypes.data_as(ctypes.c_void_p), eps, kappa, _p(out))
     return out
 
 
-def matvec(x, nrm, area, eps, kappa, u, theta, degree, leaf_size, rows=None, tree=None, lists=None):
-    """Treecode approximation of A u (Eqs. 5-6).  ``rows``: indices into [0, 2N)
-    to evaluate (default: all).  Returns the rows (or the full 2N vector)."""
+def matvec(x, nrm, area, eps, kappa, u, theta, degree, leaf_size, rows=None, tree=None, lists=None,
+           transpose=False):
+    """Treecode approximation of A u (Eqs. 5-6), or of A^T u (``transpose``).
+    ``rows``: indices into [0, 2N) to evaluate (default: all).  Returns the
+    rows (or the full 2N vector).
+
+    A^T u sums, for output element e, column e of A: the source records are
+    (x_j, w_j = phi_j, p_j = psi_j n_j) -- the kernels K3 and K4 of row
+    element j are linear in its normal, so p_j interpolates like a charge as
+    m_j does for A u -- and the sums are multiplied by the output element's
+    area.  The tree, the lists and the proxies are those of A u."""
     x, nrm, area, u = _c(x), _c(nrm), _c(area), _c(u)
     n = x.shape[0]
     phi, psi = u[:n], u[n:]
-    a = area * psi
-    m = (area * phi)[:, None] * nrm
+    if transpose:
+        a = phi.copy()
+        m = psi[:, None] * nrm
+    else:
+        a = area * psi
+        m = (area * phi)[:, None] * nrm
     t = tree if tree is not None else build_tree(x, leaf_size)
     L = lists if lists is not None else interaction_lists(t, theta, degree)
     want = np.arange(2 * n) if rows is None else np.asarray(rows, dtype=np.int64)
@@ -239,7 +254,9 @@ def matvec(x, nrm, area, eps, kappa, u, theta, degree, leaf_size, rows=None, tre
                 sid.append(np.full(pp.shape[0], -1, dtype=np.int64))
         es = np.array(es, dtype=np.int64)
         s = _record_sums(x[es], nrm[es], es, np.concatenate(ys), np.concatenate(aa), np.concatenate(mm),
-                         np.concatenate(sid), eps, kappa)
+                         np.concatenate(sid), eps, kappa, transpose)
+        if transpose:
+            s = s * area[es][:, None]
         for e, v in zip(es, s):
             sums[int(e)] = v
     out = np.empty(want.shape[0])

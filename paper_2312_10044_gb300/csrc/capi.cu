@@ -551,7 +551,6 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
                  "precision must be FP64, FP32, DF64, TENSOR or TREE32");
     BIPB_REQUIRE(precision != BIPB_TENSOR || !s->batch, "the tensor-core mat-vec needs a single-surface handle");
     BIPB_REQUIRE(precision != BIPB_TREE32 || !s->batch, "the far-field mat-vec needs a single-surface handle");
-    BIPB_REQUIRE(precision != BIPB_TREE32 || !transpose, "the far-field mat-vec has no transpose");
     BIPB_REQUIRE(n_vec >= 1 && n_vec <= 4096, "n_vec must lie in [1, 4096]");
     BIPB_REQUIRE(!s->batch || n_vec == 1, "a batch handle takes one batched vector (n_vec = 1)");
     BIPB_REQUIRE(u && y, "NULL vector");

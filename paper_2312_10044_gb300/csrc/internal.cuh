@@ -417,9 +417,9 @@ bool matvec_sym64(Surface* s, const SysLayout& L, const PairConst<double>& c, do
                   const double* u, double* y, double dphi, double dpsi, const int* skip, int skip_stride);
 bool matvec_sym_df(Surface* s, const SysLayout& L, const DFConst& c, double kappa, bool transpose, const double* u,
                    double* y, double dphi, double dpsi, const int* skip, int skip_stride);
-// y = A u for right-hand sides of one surface by the far-field treecode (tree.cu)
-void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
-                 double dpsi, const int* skip, int skip_stride);
+// y = A u (or A^T u) for right-hand sides of one surface by the far-field treecode (tree.cu)
+void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, const double* u, double* y,
+                 double dphi, double dpsi, const int* skip, int skip_stride);
 // the far-field operator of the handle's parameters (built on first use; synchronises then)
 FarField* far_field(Surface* s);
 // y = A u for right-hand sides of one surface with the split-FP16 tensor-core kernel (mrhs_tc.cu)

@@ -885,8 +885,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     return;
   }
   if (precision == BIPB_TREE32) {
-    BIPB_REQUIRE(!transpose, "the far-field mat-vec has no transpose");
-    matvec_tree(s, L, pair_const<float>(m), u, y, dphi, dpsi, skip, skip_stride);
+    matvec_tree(s, L, pair_const<float>(m), transpose, u, y, dphi, dpsi, skip, skip_stride);
     return;
   }
   if (precision == BIPB_DF64) {

@@ -2,7 +2,12 @@
 //
 // The mat-vec is an N-body sum per target over sources carrying
 // a_j = ds_j psi_j and m_j = ds_j phi_j n_j (K2 and K4 are linear in the
-// source normal, so m_j carries it).  The elements form a binary tree of
+// source normal, so m_j carries it).  The transpose A^T w is the same kind of
+// sum: output element t gathers column t of A, whose entries of row element
+// j depend on n_j only through K3 and K4, linearly, so the sources carry
+// a_j = wphi_j and m_j = wpsi_j n_j, the pair is the transposed one
+// (pair_transpose, pair.cuh) and the output element's area multiplies the
+// sums.  The tree, the lists and the proxies serve both directions.  The elements form a binary tree of
 // clusters; a cluster holding more than `leaf` elements is split in two at
 // the median of its longest box side (ties by element index), so every
 // cluster is one range of element positions in tree order.  Targets are
@@ -56,10 +61,12 @@ __device__ __forceinline__ bool tree_skipped(const int* skip, int stride, int sy
 }
 
 // ------------------------------------------------------------------ kernels
-// rec[k][t] = (x, a = ds psi), (m = ds phi n, 0) of element perm[t], system k
-__global__ void k_tree_pack(int n, int rec_stride, const int* __restrict__ perm, const double4_32a* __restrict__ tgt64,
-                            const int4* __restrict__ lay, const double* __restrict__ u, float4* __restrict__ rec,
-                            const int* __restrict__ skip, int skip_stride) {
+// rec[k][t] = (x, a = ds psi), (m = ds phi n, 0) of element perm[t], system k;
+// transposed: (x, a = wphi), (m = wpsi n, 0)
+__global__ void k_tree_pack(int n, int rec_stride, bool transpose, const int* __restrict__ perm,
+                            const double4_32a* __restrict__ tgt64, const int4* __restrict__ lay,
+                            const double* __restrict__ u, float4* __restrict__ rec, const int* __restrict__ skip,
+                            int skip_stride) {
   const int k = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n || tree_skipped(skip, skip_stride, k)) return;
@@ -67,7 +74,7 @@ __global__ void k_tree_pack(int n, int rec_stride, const int* __restrict__ perm,
   const int e = perm[t];
   const double4_32a g = tgt64[2 * (L.x + e)], v = tgt64[2 * (L.x + e) + 1];
   const double phi = u[L.z + e], psi = u[L.z + L.y + e];
-  const double a = g.w * psi, f = g.w * phi;
+  const double a = transpose ? phi : g.w * psi, f = transpose ? psi : g.w * phi;
   const size_t o = 2 * ((size_t)k * rec_stride + t);
   rec[o] = make_float4((float)g.x, (float)g.y, (float)g.z, (float)a);
   rec[o + 1] = make_float4((float)(f * v.x), (float)(f * v.y), (float)(f * v.z), 0.f);
@@ -174,9 +181,21 @@ __global__ void k_tree_proxy(int n_slots, const int2* __restrict__ up_tab, const
   rec[o + 1] = make_float4((float)s[1], (float)s[2], (float)s[3], 0.f);
 }
 
+// The ordered pair of the far-field pass: A u (pair_forward: accP, accQ the
+// phi and psi rows) or A^T w (pair_transpose: the phi and psi outputs).
+template <bool TRANS, bool MASK>
+__device__ __forceinline__ void tree_pair(const float4& g, const float4& v, const float4& A, const float4& B, bool self,
+                                          const PairConst<float>& c, float& accP, float& accQ) {
+  if (TRANS)
+    pair_transpose<MASK>(g.x, g.y, g.z, v.x, v.y, v.z, A.x, A.y, A.z, A.w, B.x, B.y, B.z, self, c, accP, accQ);
+  else
+    pair_forward<MASK>(g.x, g.y, g.z, v.x, v.y, v.z, A.x, A.y, A.z, A.w, B.x, B.y, B.z, self, c, accP, accQ);
+}
+
 // One work item: the targets of one leaf (thread t: position lf.x + t) against
 // the records of segments [it.y, it.z).  The self pair is masked in the
 // segments that overlap the leaf's own positions.
+template <bool TRANS>
 __global__ void __launch_bounds__(kMaxLeaf) k_tree_far(const int4* __restrict__ items, const int2* __restrict__ segs,
                                                       const int4* __restrict__ leaf_tab, const int* __restrict__ perm,
                                                       const float4* __restrict__ tgt32,
@@ -209,24 +228,13 @@ __global__ void __launch_bounds__(kMaxLeaf) k_tree_far(const int4* __restrict__ 
       if (!self) {
         if (m == kFarCH) {
 #pragma unroll 4
-          for (int jj = 0; jj < kFarCH; ++jj) {
-            const float4 A = sh[2 * jj], B = sh[2 * jj + 1];
-            pair_forward<false>(g.x, g.y, g.z, v.x, v.y, v.z, A.x, A.y, A.z, A.w, B.x, B.y, B.z, false, c, accP,
-                                accQ);
-          }
+          for (int jj = 0; jj < kFarCH; ++jj) tree_pair<TRANS, false>(g, v, sh[2 * jj], sh[2 * jj + 1], false, c, accP, accQ);
         } else {
-          for (int jj = 0; jj < m; ++jj) {
-            const float4 A = sh[2 * jj], B = sh[2 * jj + 1];
-            pair_forward<false>(g.x, g.y, g.z, v.x, v.y, v.z, A.x, A.y, A.z, A.w, B.x, B.y, B.z, false, c, accP,
-                                accQ);
-          }
+          for (int jj = 0; jj < m; ++jj) tree_pair<TRANS, false>(g, v, sh[2 * jj], sh[2 * jj + 1], false, c, accP, accQ);
         }
       } else {
-        for (int jj = 0; jj < m; ++jj) {
-          const float4 A = sh[2 * jj], B = sh[2 * jj + 1];
-          pair_forward<true>(g.x, g.y, g.z, v.x, v.y, v.z, A.x, A.y, A.z, A.w, B.x, B.y, B.z, S.x + j0 + jj == pos, c,
-                             accP, accQ);
-        }
+        for (int jj = 0; jj < m; ++jj)
+          tree_pair<TRANS, true>(g, v, sh[2 * jj], sh[2 * jj + 1], S.x + j0 + jj == pos, c, accP, accQ);
       }
     }
   }
@@ -237,12 +245,13 @@ __global__ void __launch_bounds__(kMaxLeaf) k_tree_far(const int4* __restrict__ 
   }
 }
 
-// y of element perm[t]: diag u - 1/(4 pi) (sum over the leaf's items in order)
+// y of element perm[t]: diag u - 1/(4 pi) (sum over the leaf's items in order),
+// the sum times the element's area for the transpose
 __global__ void k_tree_reduce(int n, const int* __restrict__ perm, const int* __restrict__ leaf_of,
                               const int4* __restrict__ leaf_tab, const float* __restrict__ part, int n_items,
-                              int lmax, const int4* __restrict__ lay, const double* __restrict__ u,
-                              double* __restrict__ y, double dphi, double dpsi, const int* __restrict__ skip,
-                              int skip_stride) {
+                              int lmax, const int4* __restrict__ lay, const double4_32a* __restrict__ area_of,
+                              const double* __restrict__ u, double* __restrict__ y, double dphi, double dpsi,
+                              const int* __restrict__ skip, int skip_stride) {
   const int k = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n || tree_skipped(skip, skip_stride, k)) return;
@@ -256,8 +265,9 @@ __global__ void k_tree_reduce(int n, const int* __restrict__ perm, const int* __
   }
   const int4 L = lay[k];
   const int e = perm[t];
-  y[L.z + e] = dphi * u[L.z + e] - kInv4PiT * sp;
-  y[L.z + L.y + e] = dpsi * u[L.z + L.y + e] - kInv4PiT * sq;
+  const double w = area_of != nullptr ? area_of[2 * (L.x + e)].w * kInv4PiT : kInv4PiT;
+  y[L.z + e] = dphi * u[L.z + e] - w * sp;
+  y[L.z + L.y + e] = dpsi * u[L.z + L.y + e] - w * sq;
 }
 
 // ------------------------------------------------------------------ host: tree and lists
@@ -362,9 +372,9 @@ void launch_proxy(const FarField* f, cudaStream_t st, int K, const int* skip, in
       f->n_slots, f->up_tab.p, f->nodes.p, f->upart.p, f->n_up, f->n, f->rec_stride, f->rec.p, skip, skip_stride);
 }
 
-int far_occupancy(int nt) {
+int far_occupancy(int nt) {  // both directions have the same shape; the forward kernel sets the plan
   int o = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tree_far, nt, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tree_far<false>, nt, 0) != cudaSuccess) {
     (void)cudaGetLastError();
     o = 1;
   }
@@ -524,8 +534,8 @@ FarField* far_field(Surface* s) {
   return s->far.get();
 }
 
-void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
-                 double dpsi, const int* skip, int skip_stride) {
+void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, const double* u, double* y,
+                 double dphi, double dpsi, const int* skip, int skip_stride) {
   for (int k = 0; k < L.K; ++k)
     BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == (int)s->n, "the far-field mat-vec covers one surface");
   FarField* f = far_field(s);
@@ -536,8 +546,8 @@ void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, cons
   if (f->upart.ensure(std::max<size_t>(1, 4 * (size_t)P * f->n_up * K), s->stream)) ++s->alloc_gen;
   const int4* lay = s->lay_dev(L);
   const int nb = (f->n + 255) / 256;
-  k_tree_pack<<<dim3(nb, K), 256, 0, s->stream>>>(f->n, f->rec_stride, f->perm.p, s->tgt64.p, lay, u, f->rec.p, skip,
-                                                  skip_stride);
+  k_tree_pack<<<dim3(nb, K), 256, 0, s->stream>>>(f->n, f->rec_stride, transpose, f->perm.p, s->tgt64.p, lay, u,
+                                                  f->rec.p, skip, skip_stride);
   BIPB_LAUNCHED(s);
   if (f->n_up > 0) {
     switch (f->degree) {
@@ -555,13 +565,21 @@ void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, cons
   }
   {
     TimedLaunch tl(s, kTMvTree);
-    k_tree_far<<<dim3(f->n_items, K), f->nt, 0, s->stream>>>(f->items.p, f->segs.p, f->leaf_tab.p, f->perm.p,
-                                                            s->tgt32.p, f->rec.p, f->rec_stride, f->part.p,
-                                                            f->n_items, f->lmax, c, skip, skip_stride);
+    if (transpose)
+      k_tree_far<true><<<dim3(f->n_items, K), f->nt, 0, s->stream>>>(f->items.p, f->segs.p, f->leaf_tab.p,
+                                                                    f->perm.p, s->tgt32.p, f->rec.p, f->rec_stride,
+                                                                    f->part.p, f->n_items, f->lmax, c, skip,
+                                                                    skip_stride);
+    else
+      k_tree_far<false><<<dim3(f->n_items, K), f->nt, 0, s->stream>>>(f->items.p, f->segs.p, f->leaf_tab.p,
+                                                                     f->perm.p, s->tgt32.p, f->rec.p, f->rec_stride,
+                                                                     f->part.p, f->n_items, f->lmax, c, skip,
+                                                                     skip_stride);
     BIPB_LAUNCHED(s);
   }
   k_tree_reduce<<<dim3(nb, K), 256, 0, s->stream>>>(f->n, f->perm.p, f->leaf_of.p, f->leaf_tab.p, f->part.p,
-                                                    f->n_items, f->lmax, lay, u, y, dphi, dpsi, skip, skip_stride);
+                                                    f->n_items, f->lmax, lay, transpose ? s->tgt64.p : nullptr, u, y,
+                                                    dphi, dpsi, skip, skip_stride);
   BIPB_LAUNCHED(s);
 }
 

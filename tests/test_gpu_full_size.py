@@ -140,8 +140,9 @@ def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
         assert e_tc <= 2 * e_32 + 1e-7 * scale, (v, e_tc / scale, e_32 / scale)
 
 
-def test_treecode_matvec_level6_sampled_rows(bipb, orc):
-    """The far-field mat-vec with its default parameters (theta 0.5, degree 6,
+@pytest.mark.parametrize("transpose", [False, True])
+def test_treecode_matvec_level6_sampled_rows(bipb, orc, transpose):
+    """The far-field mat-vec (A u, or A^T u) with its default parameters (theta 0.5, degree 6,
     leaves of 256) on the protein-like surface (N = 81920), at under 30 % of
     the direct pairs, on 64 sampled rows of a random and a smooth right-hand
     side.  Its approximation (the oracle's FP64 treecode on the same tree)
@@ -160,17 +161,18 @@ def test_treecode_matvec_level6_sampled_rows(bipb, orc):
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
         yt, y32 = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
-        s.matvec(ud, yt, precision=bipb.TREE32, med=med)
-        s.matvec(ud, y32, precision=bipb.FP32, med=med)
+        s.matvec(ud, yt, precision=bipb.TREE32, transpose=transpose, med=med)
+        s.matvec(ud, y32, precision=bipb.FP32, transpose=transpose, med=med)
         Yt, Y32 = yt.cpu().numpy(), y32.cpu().numpy()
         pairs, far, leaves = s.treecode_stats()
     assert far > 0 and pairs < 0.3 * p.n * p.n
     tree = orc.treecode.build_tree(p.centroids, 256)
     lists = orc.treecode.interaction_lists(tree, 0.5, 6)
     for v in range(U.shape[0]):
-        exact = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
+        rows_of = orc.matvec_t_rows if transpose else orc.matvec_rows
+        exact = rows_of(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
         ref_tc = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], 0.5, 6, 256, rows=rows,
-                                     tree=tree, lists=lists)
+                                     tree=tree, lists=lists, transpose=transpose)
         scale = np.abs(exact).max()
         approx = np.abs(ref_tc - exact).max() / scale
         assert approx < 1e-6, (v, approx)
@@ -183,7 +185,8 @@ def test_treecode_matvec_level6_sampled_rows(bipb, orc):
 def test_mixed_tree_solve_level7_matches_direct_mixed_solve(bipb):
     """Level 7 (N = 327680, 10000 charges): the mixed solve with far-field
     Krylov mat-vecs reaches 1e-8 on the exact system (its residual is the
-    direct double-float sum) and agrees with the direct mixed solve."""
+    direct double-float sum) and agrees with the direct mixed solve; so does
+    the energy gradient, whose adjoint solve takes the far-field transpose."""
     p = synth.adjoint_problem()
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         s.set_charges(p.charge_pos, p.q)
@@ -191,12 +194,16 @@ def test_mixed_tree_solve_level7_matches_direct_mixed_solve(bipb):
         it = s.solve(precision=bipb.MIXED_TREE, **kw)[0]
         e_tree = s.energy()[0]
         phi_tree, _ = s.surface_potential()
+        dq_tree, dy_tree = s.energy_grad(bipb.solve_params(precision=bipb.MIXED_TREE, **kw))
         idr = s.solve(precision=bipb.MIXED_DF64, **kw)[0]
         e_dir = s.energy()[0]
         phi_dir, _ = s.surface_potential()
+        dq_dir, dy_dir = s.energy_grad(bipb.solve_params(precision=bipb.MIXED_DF64, **kw))
     assert it["converged"] and it["rel_residual"] <= 1e-8 and idr["converged"]
     assert e_tree == pytest.approx(e_dir, rel=1e-7)
     assert np.linalg.norm(phi_tree[0] - phi_dir[0]) / np.linalg.norm(phi_dir[0]) < 1e-7
+    np.testing.assert_allclose(dq_tree, dq_dir, rtol=0, atol=1e-6 * np.abs(dq_dir).max())
+    np.testing.assert_allclose(dy_tree, dy_dir, rtol=0, atol=1e-6 * np.abs(dy_dir).max())
 
 
 def _sampled_residual_rms(orc, p, u, q_row, pos, rows):

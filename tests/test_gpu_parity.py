@@ -938,11 +938,13 @@ def _tc_vectors(p, seed):
                      np.concatenate([1.0 + 0.3 * x[:, 2], 0.5 - 0.2 * x[:, 0]])])
 
 
+@pytest.mark.parametrize("transpose", [False, True])
 @pytest.mark.parametrize("params", [(0.7, 4, 64), (0.8, 6, 64), (0.9, 8, 64), (0.8, 4, 256), (0.0, 6, 256)])
-def test_treecode_matvec_matches_oracle_treecode(bipb, orc, params):
-    """The far-field FP32 mat-vec against the oracle's treecode on the same
-    tree (FP64, every row): the FP32 mat-vec's bounds, 3e-6 in the 2-norm and
-    2e-5 of the largest output; theta = 0 is the direct mat-vec."""
+def test_treecode_matvec_matches_oracle_treecode(bipb, orc, params, transpose):
+    """The far-field FP32 mat-vec (A u, or A^T u) against the oracle's
+    treecode on the same tree (FP64, every row): the FP32 mat-vec's bounds,
+    3e-6 in the 2-norm and 2e-5 of the largest output; theta = 0 is the
+    direct mat-vec."""
     theta, deg, leaf = params
     p = _ragged(4)
     eps = p.eps_out / p.eps_in
@@ -951,13 +953,14 @@ def test_treecode_matvec_matches_oracle_treecode(bipb, orc, params):
         s.treecode(theta, deg, leaf)
         ud = _dev(U)
         yd = torch.full_like(ud, float("nan"))
-        s.matvec(ud, yd, precision=bipb.TREE32, med=_med(bipb, p))
+        s.matvec(ud, yd, precision=bipb.TREE32, transpose=transpose, med=_med(bipb, p))
         Y = yd.cpu().numpy()
         pairs, far, leaves = s.treecode_stats()
     assert (far > 0) == (theta > 0)
     assert leaves >= p.n // leaf and pairs <= p.n * p.n
     for r in range(U.shape[0]):
-        ref = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r], theta, deg, leaf)
+        ref = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r], theta, deg, leaf,
+                                  transpose=transpose)
         assert np.all(np.isfinite(Y[r]))
         assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6, (params, r)
         assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max(), (params, r)
@@ -969,9 +972,6 @@ def test_treecode_rejects_bad_use(bipb):
         for bad in ((1.0, 6, 256), (-0.1, 6, 256), (0.5, 5, 256), (0.5, 6, 16), (0.5, 6, 1024)):
             with pytest.raises(bipb.BipbError):
                 s.treecode(*bad)
-        u = _dev(np.ones(2 * p.n))
-        with pytest.raises(bipb.BipbError):
-            s.matvec(u, torch.empty_like(u), precision=bipb.TREE32, transpose=True)
     probs = [synth.born_problem(level=1), synth.born_problem(level=2)]
     with bipb.BatchSurface([(q.centroids, q.normals, q.areas) for q in probs]) as s:
         u = _dev(np.ones(sum(2 * q.n for q in probs)))
@@ -983,7 +983,8 @@ def test_mixed_tree_solve_matches_oracle(bipb, orc):
     """MIXED_TREE (far-field FP32 Krylov mat-vecs, direct double-float
     residual) reaches the exact discrete solution: energy and potentials of
     three charge sets against the oracle's GMRES to 1e-12 within 1e-7, and the
-    adjoint gradient (direct FP32 transpose inside) within 1e-5."""
+    adjoint gradient (far-field FP32 transpose inside, direct double-float
+    transpose residual) within 1e-5."""
     base = synth.protein_like_problem(level=4, n_charges=30)
     batch = synth.batched_charges(base, n_rhs=3, n_charges=30)
     with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:

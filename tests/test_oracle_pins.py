@@ -600,28 +600,34 @@ def test_treecode_proxies_reproduce_polynomial_moments(orc, tc_surface):
     assert tc.lagrange_1d(np.array([nodes[0][2]]), nodes[0], w)[0].tolist() == [0.0, 0.0, 1.0, 0.0, 0.0]
 
 
-def test_treecode_theta_zero_is_the_direct_matvec(orc, tc_surface):
-    """theta = 0: no cluster is far, every pair is summed directly."""
+@pytest.mark.parametrize("transpose", [False, True])
+def test_treecode_theta_zero_is_the_direct_matvec(orc, tc_surface, transpose):
+    """theta = 0: no cluster is far, every pair is summed directly (A u, and
+    A^T u against the oracle's transposed mat-vec)."""
     p = tc_surface
     eps = p.eps_out / p.eps_in
     u = np.random.default_rng(5).standard_normal(2 * p.n)
-    ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u)
-    got = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u, 0.0, 6, 64)
+    f = orc.matvec_t if transpose else orc.matvec
+    ref = f(p.centroids, p.normals, p.areas, eps, p.kappa, u)
+    got = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u, 0.0, 6, 64, transpose=transpose)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * np.abs(ref).max())
 
 
-def test_treecode_error_falls_with_degree(orc, tc_surface):
-    """The far-field approximation error against the direct mat-vec falls
-    geometrically with the interpolation degree (2, 4, 6) at fixed theta, on
-    a smooth field and a random one."""
+@pytest.mark.parametrize("transpose", [False, True])
+def test_treecode_error_falls_with_degree(orc, tc_surface, transpose):
+    """The far-field approximation error against the direct mat-vec (A u or
+    A^T u) falls geometrically with the interpolation degree (2, 4, 6) at
+    fixed theta, on a smooth field and a random one."""
     p = tc_surface
     eps = p.eps_out / p.eps_in
     x = p.centroids / 25.0
+    f = orc.matvec_t if transpose else orc.matvec
     for u in (np.concatenate([1.0 + 0.3 * x[:, 2], 0.5 - 0.2 * x[:, 0]]),
               np.random.default_rng(6).standard_normal(2 * p.n)):
-        ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u)
+        ref = f(p.centroids, p.normals, p.areas, eps, p.kappa, u)
         errs = []
         for deg in (2, 4, 6):
-            got = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u, 0.7, deg, 32)
+            got = orc.treecode.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, u, 0.7, deg, 32,
+                                      transpose=transpose)
             errs.append(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         assert errs[0] > 5 * errs[1] > 25 * errs[2] > 0, errs
