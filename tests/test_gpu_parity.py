@@ -229,7 +229,8 @@ def test_kirkwood_solve(bipb, orc, prec):
     p = synth.kirkwood_problem(level=4)
     ref = orc.solve(p, method="gmres", tol=1e-12)
     phi_ref, dphi_ref = ref.surface_potential()
-    P = {"fp64": bipb.FP64, "mixed": bipb.MIXED, "df64": bipb.DF64, "mixed_df64": bipb.MIXED_DF64}[prec]
+    P = {"fp64": bipb.FP64, "mixed": bipb.MIXED, "df64": bipb.DF64, "mixed_df64": bipb.MIXED_DF64,
+         "mixed_tensor": bipb.MIXED_TENSOR, "mixed_tree": bipb.MIXED_TREE}[prec]
     tol = 1e-12 if prec in ("fp64", "df64") else 1e-8
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         s.set_charges(p.charge_pos, p.q)
@@ -428,9 +429,10 @@ def test_long_restart_matches_oracle(bipb, orc):
 # ---------------------------------------------------------------- solute dielectric eps_in != 1
 def test_solute_dielectric_parity(bipb, orc):
     """eps_in = 2, eps_out = 80 (S1, S2 and the gradient's source column carry
-    1/eps_in, Sec. 2.2.1): the source term, FP64 and mixed double-float
-    solves, energy, surface potential, gradient and the potential at points
-    inside and outside against the oracle."""
+    1/eps_in, Sec. 2.2.1): the source term, FP64 and mixed solves (double-float
+    residual with CUDA-core, tensor-core and far-field Krylov mat-vecs),
+    energy, surface potential, gradient and the potential at points inside
+    and outside against the oracle."""
     p = synth.kirkwood_problem(level=3, radius=10.0, n_charges=6, charge_radius=7.0)
     p.eps_in = 2.0
     eps = p.eps_out / p.eps_in
@@ -449,7 +451,9 @@ def test_solute_dielectric_parity(bipb, orc):
         bd = torch.full((2 * p.n,), float("nan"), dtype=torch.float64, device="cuda")
         s.source(bd, med=_med(bipb, p))
         np.testing.assert_allclose(bd.cpu().numpy(), b_ref, rtol=0, atol=1e-12 * np.abs(b_ref).max())
-        for prec, tol, rt in ((bipb.FP64, 1e-12, 1e-10), (bipb.MIXED_DF64, 1e-10, 1e-7)):
+        s.treecode(0.7, 4, 64)  # far clusters on this small surface too
+        for prec, tol, rt in ((bipb.FP64, 1e-12, 1e-10), (bipb.MIXED_DF64, 1e-10, 1e-7), (bipb.MIXED_TENSOR, 1e-10, 1e-7),
+                              (bipb.MIXED_TREE, 1e-10, 1e-7)):
             info = s.solve(tol=tol, precision=prec, **kw)[0]
             assert info["converged"]
             assert s.energy()[0] == pytest.approx(ref.energy_kcal, rel=rt)
@@ -847,7 +851,7 @@ def test_potential_at_rejects_batch_handles(bipb):
 
 
 # ---------------------------------------------------------------- preconditioned solves
-@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed", "mixed_df64"])
+@pytest.mark.parametrize("prec", ["fp64", "df64", "mixed", "mixed_df64", "mixed_tensor", "mixed_tree"])
 def test_self_block_preconditioned_solve_matches_oracle(bipb, orc, prec):
     """GMRES with the element self-block preconditioner (Sec. 2.2.4, applied
     on the right) reaches the same solution as the oracle's unpreconditioned
@@ -855,7 +859,8 @@ def test_self_block_preconditioned_solve_matches_oracle(bipb, orc, prec):
     p = synth.kirkwood_problem(level=4)
     ref = orc.solve(p, method="gmres", tol=1e-12)
     phi_ref, _ = ref.surface_potential()
-    P = {"fp64": bipb.FP64, "mixed": bipb.MIXED, "df64": bipb.DF64, "mixed_df64": bipb.MIXED_DF64}[prec]
+    P = {"fp64": bipb.FP64, "mixed": bipb.MIXED, "df64": bipb.DF64, "mixed_df64": bipb.MIXED_DF64,
+         "mixed_tensor": bipb.MIXED_TENSOR, "mixed_tree": bipb.MIXED_TREE}[prec]
     tol = 1e-12 if prec in ("fp64", "df64") else 1e-8
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         s.set_charges(p.charge_pos, p.q)
