@@ -358,6 +358,14 @@ bipb_status bipb_matvec_variant(bipb_surface s, int variant);
  * large for the symmetric work list use the ordered form either way. */
 bipb_status bipb_symmetric_pairs(bipb_surface s, int symmetric);
 
+/* How the double-float mat-vec applies one surface's kernel to 16 or more
+ * right-hand sides (the refinement residual of batched solves): tensor = 1
+ * (the default) digitises the df64 kernel values and right-hand sides into
+ * seven exact base-128 FP16 digits and multiplies them on the tensor cores
+ * with exact FP32 accumulation; tensor = 0 runs df64 multiply-adds on the
+ * CUDA cores.  Both reach about 1e-14 of the largest output. */
+bipb_status bipb_exact_tensor_residual(bipb_surface s, int tensor);
+
 /*
  * Parameters of the far-field (treecode) mat-vec, Sec. 2.2.3 (BIPB_TREE32,
  * BIPB_MIXED_TREE).  The elements form a binary tree of clusters: a cluster

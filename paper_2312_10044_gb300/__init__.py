@@ -45,7 +45,7 @@ EXPORTED = (
     "bipb_source", "bipb_reaction", "bipb_last_error", "bipb_status_string", "bipb_version",
     "bipb_timer_enable", "bipb_timer_read", "bipb_launch_count", "bipb_matvec32_static",
     "bipb_autotune", "bipb_matvec_variant", "bipb_surface_create_batch", "bipb_charges_set_batch",
-    "bipb_symmetric_pairs", "bipb_potential_at", "bipb_energy_free", "bipb_treecode", "bipb_treecode_stats",
+    "bipb_symmetric_pairs", "bipb_exact_tensor_residual", "bipb_potential_at", "bipb_energy_free", "bipb_treecode", "bipb_treecode_stats",
     "bipb_charges_set_dev", "bipb_energy_dev", "bipb_energy_grad_dev",
 )
 MATVEC32_VARIANTS = 10
@@ -138,6 +138,7 @@ def load_library():
         "bipb_charges_set_batch": ([P, P, P, P], st),
         "bipb_matvec_variant": ([P, I], st),
         "bipb_symmetric_pairs": ([P, I], st),
+        "bipb_exact_tensor_residual": ([P, I], st),
         "bipb_potential_at": ([P, I, I64, P, P], st),
         "bipb_energy_free": ([P, P, P], st),
         "bipb_treecode": ([P, D, I, I], st),
@@ -388,6 +389,10 @@ class Surface:
         pairs, far, leaves = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
         _check(self._L.bipb_treecode_stats(self._h, ctypes.byref(pairs), ctypes.byref(far), ctypes.byref(leaves)))
         return pairs.value, far.value, leaves.value
+
+    def exact_tensor_residual(self, on=True):
+        """Double-float mat-vec of 16 or more right-hand sides on the tensor cores (exact digits) or not."""
+        _check(self._L.bipb_exact_tensor_residual(self._h, int(bool(on))))
 
     def symmetric_pairs(self, on=True):
         """FP64 / double-float mat-vecs: visit every unordered pair once (True) or every ordered pair."""

@@ -854,6 +854,14 @@ bipb_status bipb_symmetric_pairs(bipb_surface h, int symmetric) {
   });
 }
 
+bipb_status bipb_exact_tensor_residual(bipb_surface h, int tensor) {
+  return guarded([&] {
+    Surface* s = checked(h);
+    BIPB_REQUIRE(tensor == 0 || tensor == 1, "tensor must be 0 or 1");
+    s->tcx_enabled = tensor != 0;
+  });
+}
+
 bipb_status bipb_treecode(bipb_surface h, double theta, int degree, int leaf_size) {
   return guarded([&] {
     Surface* s = checked(h);

@@ -312,6 +312,12 @@ struct Surface {
   DevBuf<int> rhs_idx;  // right-hand-side indices of a compacted multi-RHS pass
   DevBuf<float4> geodf;  // multi-RHS df64 pass: geometry as df64 records (4 float4 each)
   DevBuf<float4> udf;    // multi-RHS df64 pass: right-hand sides as df64 (phi, psi) pairs
+  DevBuf<int2> tcx_rowexp;   // exact tensor-core df64 pass: row scale exponents (phi row, psi row)
+  DevBuf<unsigned> tcx_colmax;  // exact tensor-core df64 pass: max |u| per right-hand side (FP32 bits)
+  DevBuf<float> tcx_upk;     // exact tensor-core df64 pass: digit tiles of the right-hand sides (raw storage)
+  DevBuf<int> tcx_err;       // set by the exact tensor-core kernel when a bounded wait ran out
+  float tcx_key[4] = {0.f, 0.f, -1.f, 0.f};  // the medium (eps and kappa as df64) tcx_rowexp was computed for
+  int tcx_n = -1;
   DevBuf<double4_32a> pts, pts2;  // points of bipb_potential_at: (p, 0); (p, 0), (0, 0)
   DevBuf<double> pot;             // their potentials, n_rhs x n_pts
   DevBuf<double> coul;            // Coulomb block sums
@@ -354,6 +360,7 @@ struct Surface {
 
   int mv32_variant = kFirstSymVariant + 2;  // FP32 mat-vec variant (the autotuner may change it)
   bool sym_pairs = true;  // FP64 / double-float mat-vecs visit unordered pairs once (sym.cu)
+  bool tcx_enabled = true;  // the double-float multi-RHS mat-vec on the tensor cores (mrhs_df.cu)
   GmresWork* gw = nullptr;
   // far-field mat-vec: parameters (bipb_treecode) and the built operator
   double far_theta = 0.5;

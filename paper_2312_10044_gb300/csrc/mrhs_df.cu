@@ -15,8 +15,11 @@
 // FP64 and added by the FP64 reduction of kernels.cu.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "df64.cuh"
 #include "internal.cuh"
+#include "tcgen05.cuh"
 
 namespace bipb {
 
@@ -26,6 +29,7 @@ constexpr int kNB = 64;     // right-hand sides per launch (at most)
 constexpr int kGB = 8;      // right-hand sides per group (per thread)
 constexpr int kTgt = 32;    // targets per CTA
 constexpr int kCh = 16;     // sources per shared-memory chunk
+constexpr int kTcxMinRHS = 16;  // the exact tensor-core form from this many right-hand sides on
 
 // Double-float copies made once per pass, so that the hot loop stages plain
 // float4 records and never converts from FP64 (GB300 runs FP64 and its
@@ -197,6 +201,491 @@ ItemPlan* mrhs_df_plan(Surface* s, int n, int G, int slots, int* S_out) {
   return it->second.get();
 }
 
+
+// ------------------------------------------------------------------ exact tensor-core form
+// The same product with the multiply-adds on the tensor cores, exactly.  Row
+// i of tile m (the phi rows, then the psi rows of 128 targets) is scaled by
+// 2^e(i, m) and right-hand side b by 2^f(b) so that every value lies below
+// 64 in magnitude; each df64 kernel value a and each right-hand-side value u
+// is then written as seven signed base-128 digits,
+//     a = sum_k d_k 128^-k,   u = sum_l t_l 128^-l,   |d_k|, |t_l| <= 68,
+// which FP16 holds exactly.  A kind::f16 MMA of digit planes multiplies
+// integers exactly and its FP32 accumulator adds them exactly while every
+// sum stays below 2^24 (checked on GB300 by a probe), so level L = k + l of
+// the product, sum_{k+l=L} d_k t_l, is accumulated without rounding in its
+// own 32 TMEM columns: per K step and tile, seven MMAs A_k [T_0 | .. |
+// T_{6-k}] (N = 32 (7 - k)) write levels k .. 6.  Levels above 6 (below
+// 2^-46 of the largest product) are dropped.  Every 32 K steps (512 K,
+// which bounds the sums by 512 x 7 x 68 x 64 < 2^24) the generating threads
+// read the levels back and add sum_L v_L 128^-L to df64 accumulators.  The
+// result matches the CUDA-core df64 kernel's accuracy at a fraction of its
+// instructions: the df64 kernel values are generated once per CTA of 32
+// right-hand sides, and the multiply-adds cost nothing on the CUDA cores.
+namespace tcx {
+
+constexpr int kRHS = 32;                        // right-hand sides per CTA
+constexpr int kLv = 7;                          // digits per value = accumulation levels
+constexpr int kTgt = 128;                       // targets per CTA (two M = 128 tiles)
+constexpr int kStep = 8;                        // sources per K step
+constexpr int kK = 2 * kStep;                   // K of one step (one kind::f16 MMA)
+constexpr int kPlane = kTgt * kK * 2;           // one digit plane of one tile: 4 KB
+constexpr int kAStage = 2 * kLv * kPlane;       // A of one K step: 56 KB
+constexpr int kBRows = kLv * kRHS;              // 224 rows: digit plane l of U in rows 32 l ..
+constexpr int kBBytes = kBRows * kK * 2;        // 7 KB
+constexpr int kSRec = kStep * 64;               // source records of one K step: 512 B
+constexpr int kRing = 8;                        // B and source buffers (step it in buffer it % 8)
+constexpr int kGroup = 32;                      // K steps per exact accumulation group (K = 512)
+constexpr int kOffA = 0;                        // two A stages
+constexpr int kOffB = kOffA + 2 * kAStage;
+constexpr int kOffS = kOffB + kRing * kBBytes;
+constexpr int kOffTab = kOffS + kRing * kSRec;
+constexpr int kOffF = kOffTab + kExpTab * 8;    // 2^-f(b) of the CTA's right-hand sides
+constexpr int kOffBar = kOffF + kRHS * 4;
+constexpr int kNumBars = 3 * kRing + 2 * 2 + 2;
+constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
+constexpr int kGenThreads = 512;
+constexpr int kMmaWarp = kGenThreads / 32;      // warp 16: issues the MMAs
+constexpr int kLoadWarp = kMmaWarp + 1;         // warp 17: issues the bulk copies
+constexpr int kThreads = kGenThreads + 64;
+constexpr uint32_t kTmemCols = 512;             // tile m's levels at 256 m + 32 L
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+static_assert(kOffBar % 8 == 0 && kOffTab % 16 == 0, "alignment");
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+
+// byte offset of element (row, k) of a K-major, no-swizzle FP16 tile with K = 16
+__host__ __device__ __forceinline__ uint32_t koff(int row, int k) {
+  return (uint32_t)((((row >> 3) * 2 + (k >> 3)) * 8 + (row & 7)) * 16 + (k & 7) * 2);
+}
+// 2^k in FP32 (|k| <= 126) and FP64 (|k| <= 1022)
+__device__ __forceinline__ float p2f(int k) { return __uint_as_float((uint32_t)(127 + k) << 23); }
+__device__ __forceinline__ double p2d(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+// the exponent that brings a largest magnitude with floor(log2) lg below 64 (2^5 <= m 2^e < 2^6),
+// clamped to [-100, 100]; 0 for zero
+__device__ __forceinline__ int scale_exp(float m) {
+  if (!(m > 0.f)) return 0;
+  const int lg = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;
+  return max(-100, min(100, 5 - lg));
+}
+
+// a (df64, |a| below 64 up to rounding) as seven base-128 digits, exactly
+// up to 2^-43: a = sum_k d[k] 128^-k + rest.  The leading part gives three
+// digits by exact FP32 steps; the trailing part (at most 2^-19) joins at the
+// fourth, which may then reach 68 in magnitude.
+__device__ __forceinline__ void digits7(df a, float* d) {
+  float r = a.hi;
+  d[0] = rintf(r);
+  r = __fsub_rn(r, d[0]);
+  d[1] = rintf(__fmul_rn(r, 128.f));
+  r = __fsub_rn(__fmul_rn(r, 128.f), d[1]);
+  d[2] = rintf(__fmul_rn(r, 128.f));
+  r = __fsub_rn(__fmul_rn(r, 128.f), d[2]);
+  const df t = two_sum(__fmul_rn(r, 128.f), __fmul_rn(a.lo, 2097152.f));  // units 128^-3
+  d[3] = rintf(t.hi);
+  r = __fadd_rn(__fsub_rn(t.hi, d[3]), t.lo);
+  d[4] = rintf(__fmul_rn(r, 128.f));
+  r = __fsub_rn(__fmul_rn(r, 128.f), d[4]);
+  d[5] = rintf(__fmul_rn(r, 128.f));
+  r = __fsub_rn(__fmul_rn(r, 128.f), d[5]);
+  d[6] = rintf(__fmul_rn(r, 128.f));
+}
+
+// Row scale exponents: for target i the largest |K2 ds|, |K1 ds| (phi row)
+// and |K4 ds|, |K3 ds| (psi row) over all sources j != i, in df64 (the same
+// values the kernel digitises).  One thread per target.
+__global__ void __launch_bounds__(128) k_tcx_rowexp(int n, const float4* __restrict__ geo, DFConst c,
+                                                    int2* __restrict__ rowexp) {
+  __shared__ float4 sh[4 * 64];
+  __shared__ __align__(16) df tab[kExpTab];
+  df_load_exp_table(tab, c);
+  const int i = blockIdx.x * 128 + threadIdx.x;
+  const int ii = min(i, n - 1);
+  df xi[3], ni[3];
+  {
+    const float4 A = geo[4 * (size_t)ii], B = geo[4 * (size_t)ii + 1], C = geo[4 * (size_t)ii + 2],
+                 D = geo[4 * (size_t)ii + 3];
+    xi[0] = df{A.x, B.x}, xi[1] = df{A.y, B.y}, xi[2] = df{A.z, B.z};
+    ni[0] = df{C.x, D.x}, ni[1] = df{C.y, D.y}, ni[2] = df{C.z, D.z};
+  }
+  float m0 = 0.f, m1 = 0.f;
+  for (int j0 = 0; j0 < n; j0 += 64) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4 * 64; e += 128) sh[e] = geo[4 * (size_t)min(j0 + e / 4, n - 1) + e % 4];
+    __syncthreads();
+    const int cnt = min(64, n - j0);
+    for (int q = 0; q < cnt; ++q) {
+      const float4 A = sh[4 * q], B = sh[4 * q + 1], C = sh[4 * q + 2], D = sh[4 * q + 3];
+      const df xj[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+      const df nj[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
+      df k[4];
+      df_kernel_block<true>(xi, ni, xj, nj, df{A.w, B.w}, j0 + q == ii, c, tab, k);
+      m0 = fmaxf(m0, fmaxf(fabsf(k[0].hi), fabsf(k[1].hi)));
+      m1 = fmaxf(m1, fmaxf(fabsf(k[2].hi), fabsf(k[3].hi)));
+    }
+  }
+  if (i < n) rowexp[i] = make_int2(scale_exp(m0), scale_exp(m1));
+}
+
+// colmax[b] = max |u_b| over the 2n values (FP32 bits; colmax zeroed before): grid (x, nb)
+__global__ void k_tcx_colmax(int n, const double* __restrict__ u, const int* __restrict__ rhs,
+                             unsigned* __restrict__ colmax) {
+  const int b = blockIdx.y;
+  const double* ub = u + (int64_t)(rhs ? rhs[b] : b) * 2 * n;
+  float m = 0.f;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 2 * n; e += gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf((float)ub[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(colmax + b, __float_as_uint(m));
+}
+
+// U digit tiles: for K step x and right-hand-side half h, row 32 l + b holds
+// digit l of u_b 2^f(b) (b = 32 h + b'), K = 2 j' + c (phi_j, psi_j of the
+// step's sources), K-major.  One thread per (x, h, b', k).
+__global__ void k_tcx_pack_u(int n, int nb, int n_steps, int halves, const double* __restrict__ u,
+                             const int* __restrict__ rhs, const unsigned* __restrict__ colmax,
+                             __half* __restrict__ upk) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n_steps * halves * kRHS * kK) return;
+  const int k = (int)(e % kK), bl = (int)((e / kK) % kRHS);
+  const int h = (int)((e / (kK * kRHS)) % halves);
+  const int64_t x = e / ((int64_t)kK * kRHS * halves);
+  const int b = kRHS * h + bl;
+  const int j = (int)(x * kStep) + (k >> 1), c = k & 1;
+  double v = 0.0;
+  if (b < nb && j < n)
+    v = u[(int64_t)(rhs ? rhs[b] : b) * 2 * n + (int64_t)c * n + j] * p2d(scale_exp(__uint_as_float(colmax[b])));
+  unsigned char* tile = reinterpret_cast<unsigned char*>(upk) + (x * halves + h) * (int64_t)kBBytes;
+#pragma unroll
+  for (int l = 0; l < kLv; ++l) {
+    const double d = rint(v);
+    *reinterpret_cast<__half*>(tile + koff(kRHS * l + bl, k)) = __float2half_rn((float)d);
+    v = (v - d) * 128.0;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// This thread's two sources of a K step (records Sq, first index jq) against
+// target ti: the df64 block, scaled per row, as digit planes written into A
+// stage `a` (tile m, digit k at a + (7 m + k) kPlane; K columns 4 sq ..).
+template <bool EDGE>
+__device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4* Sq, int jq, int ti, int n,
+                                        bool tvalid, const DFConst& c, const df* tab, float r0, float r1,
+                                        unsigned char* a, uint32_t off) {
+  float dg[2][4][kLv];  // [source][value: K2, K1, K4, K3][digit]
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const float4 A = Sq[4 * u], B = Sq[4 * u + 1], C = Sq[4 * u + 2], D = Sq[4 * u + 3];
+    const df xj[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
+    const df nj[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
+    const bool z = EDGE && (!tvalid || jq + u >= n || jq + u == ti);
+    df k[4];
+    df_kernel_block<EDGE>(xi, ni, xj, nj, df{A.w, B.w}, z, c, tab, k);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      df w = df_scale(k[v], v < 2 ? r0 : r1);
+      if (EDGE && z) w = df{0.f, 0.f};
+      digits7(w, dg[u][v]);
+    }
+  }
+  // tile 0: (K2, K1) of sources 0, 1 in K columns 4 sq .. 4 sq + 3; tile 1: (K4, K3)
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int k = 0; k < kLv; ++k) {
+      const __half2 p0 = __floats2half2_rn(dg[0][2 * m][k], dg[0][2 * m + 1][k]);
+      const __half2 p1 = __floats2half2_rn(dg[1][2 * m][k], dg[1][2 * m + 1][k]);
+      uint2 w;
+      w.x = *reinterpret_cast<const uint32_t*>(&p0);
+      w.y = *reinterpret_cast<const uint32_t*>(&p1);
+      *reinterpret_cast<uint2*>(a + (m * kLv + k) * kPlane + off) = w;
+    }
+}
+
+// items: {t0, first K step, end K step, split}; blockIdx.y: right-hand-side half;
+// part: [b][split][2n] for the nb right-hand sides of this pass.
+__global__ void __launch_bounds__(kThreads, 1)
+    k_mrhs_tcx(int n, int nb, int n_splits, int halves, const int4* __restrict__ items, const float4* __restrict__ geo,
+               const int2* __restrict__ rowexp, const unsigned* __restrict__ colmax, const __half* __restrict__ upk,
+               double* __restrict__ part, DFConst c, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* ufull = reinterpret_cast<uint64_t*>(smem + kOffBar);  // kRing: U digit tile landed
+  uint64_t* sfull = ufull + kRing;                                 // kRing: source records landed
+  uint64_t* bfree = sfull + kRing;                                 // kRing: MMAs of the buffer's step finished
+  uint64_t* ready = bfree + kRing;                                 // 2: A stage written (16 warp arrivals)
+  uint64_t* afree = ready + 2;                                     // 2: MMAs of an A stage finished
+  uint64_t* done = afree + 2;                                      // MMAs of a group finished
+  uint64_t* drained = done + 1;                                    // levels read back (16 warp arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 1);
+  df* tab = reinterpret_cast<df*>(smem + kOffTab);
+  float* finv = reinterpret_cast<float*>(smem + kOffF);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int4 item = items[blockIdx.x];
+  const int t0 = item.x, x0 = item.y, x1 = item.z, split = item.w;
+  const int h = blockIdx.y;
+  if (tid == 0) {
+    for (int q = 0; q < kRing; ++q) {
+      tc::mbar_init(&ufull[q], 1);
+      tc::mbar_init(&sfull[q], 1);
+      tc::mbar_init(&bfree[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(&ready[q], kGenThreads / 32);
+      tc::mbar_init(&afree[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(drained, kGenThreads / 32);
+    tc::fence_mbar_init();
+  }
+  if (tid < kRHS) {
+    const int b = kRHS * h + tid;
+    finv[tid] = b < nb ? p2f(-scale_exp(__uint_as_float(colmax[b]))) : 0.f;
+  }
+  df_load_exp_table(tab, c);
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const int n_it = x1 - x0;
+  const int n_groups = (n_it + kGroup - 1) / kGroup;
+  bool ok = true;
+  const int wq = warp & 3;
+  if (warp == kLoadWarp) {
+    if (lane == 0) {
+      for (int x = 0; x < n_it; ++x) {
+        const int q = x % kRing;
+        if (x >= kRing) ok = ok && tc::mbar_wait_timed(&bfree[q], ((x - kRing) / kRing) & 1, kWaitLimitNs);
+        if (!ok) break;
+        const int st = x0 + x;
+        const int cnt = min(kStep, n - st * kStep);
+        arrive_expect_tx(&sfull[q], cnt * 64);
+        bulk_load(smem + kOffS + q * kSRec, geo + 4 * (int64_t)st * kStep, cnt * 64, &sfull[q]);
+        arrive_expect_tx(&ufull[q], kBBytes);
+        bulk_load(smem + kOffB + q * kBBytes,
+                  reinterpret_cast<const unsigned char*>(upk) + ((int64_t)st * halves + h) * kBBytes, kBBytes,
+                  &ufull[q]);
+      }
+    }
+    __syncwarp();
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      for (int it = 0; it < n_it && ok; ++it) {
+        const int g = it / kGroup, s = it & 1, q = it % kRing;
+        const bool first = it % kGroup == 0, last = it % kGroup == kGroup - 1 || it == n_it - 1;
+        if (first && g >= 1) ok = ok && tc::mbar_wait_timed(drained, (g - 1) & 1, kWaitLimitNs);
+        ok = ok && tc::mbar_wait_timed(&ready[s], (it >> 1) & 1, kWaitLimitNs);
+        ok = ok && tc::mbar_wait_timed(&ufull[q], (it / kRing) & 1, kWaitLimitNs);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t bbase = tc::smem_u32(smem + kOffB + q * kBBytes);
+        const uint64_t db = tc::smem_desc(bbase, 128, 256);
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+          for (int k = 0; k < kLv; ++k) {
+            const uint64_t da = tc::smem_desc(tc::smem_u32(smem + kOffA + s * kAStage + (m * kLv + k) * kPlane), 128, 256);
+            // digit k of A against digit planes 0 .. 6 - k of U: levels k .. 6
+            tc::mma_f16_ss(tmem + m * 256 + kRHS * k, da, db, tc::idesc_f16(128, kRHS * (kLv - k)),
+                           (k > 0 || !first) ? 1u : 0u);
+          }
+        tc::mma_commit(&afree[s]);
+        tc::mma_commit(&bfree[q]);
+        if (last) tc::mma_commit(done);
+      }
+    }
+    __syncwarp();
+  } else {
+    // generating warps: thread of TMEM lane r = 32 wq + lane owns target r; it
+    // generates sources 2 sq, 2 sq + 1 of every K step and reads back tile
+    // sq >> 1, right-hand sides 16 (sq & 1) .. + 15
+    const int sq = warp >> 2;
+    const int ti = t0 + 32 * wq + lane;
+    const bool tvalid = ti < n;
+    df xi[3], ni[3];
+    {
+      const int64_t r = 4 * (int64_t)min(ti, n - 1);
+      const float4 A = geo[r], B = geo[r + 1], C = geo[r + 2], D = geo[r + 3];
+      xi[0] = df{A.x, B.x}, xi[1] = df{A.y, B.y}, xi[2] = df{A.z, B.z};
+      ni[0] = df{C.x, D.x}, ni[1] = df{C.y, D.y}, ni[2] = df{C.z, D.z};
+    }
+    const int2 re = rowexp[min(ti, n - 1)];
+    const float r0 = p2f(re.x), r1 = p2f(re.y);
+    const uint32_t off = koff(32 * wq + lane, 4 * sq);
+    const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+    const uint32_t dthr = tmem + lane_base + (sq >> 1) * 256 + 16 * (sq & 1);
+    const bool tile_edge = t0 + kTgt > n;
+    df acc[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) acc[b] = df{0.f, 0.f};
+    auto read_back = [&]() {  // acc += sum_L level L 128^-L, exact levels, df64 sums
+#pragma unroll
+      for (int L = 0; L < kLv; ++L) {
+        uint32_t v[16];
+        tc::tmem_ld16_async(dthr + kRHS * L, v);
+        tc::tmem_wait_ld16(v);
+        const float sc = p2f(-7 * L);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) acc[b] = df_add_f(acc[b], __fmul_rn(__uint_as_float(v[b]), sc));
+      }
+    };
+    auto drain = [&](int d) {
+      ok = ok && tc::mbar_wait_timed(done, d & 1, kWaitLimitNs);
+      if (!ok) return;
+      tc::fence_after_sync();
+      read_back();
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(drained);
+    };
+    int drained_groups = 0;
+    for (int it = 0; it < n_it; ++it) {
+      const int s = it & 1, q = it % kRing;
+      ok = ok && tc::mbar_wait_timed(&sfull[q], (it / kRing) & 1, kWaitLimitNs);
+      if (it >= 2) ok = ok && tc::mbar_wait_timed(&afree[s], ((it - 2) >> 1) & 1, kWaitLimitNs);
+      const int d = (it % kGroup == 1 && it > kGroup) ? it / kGroup - 1 : -1;
+      if (d >= 0) ok = ok && tc::mbar_wait_timed(done, d & 1, kWaitLimitNs);
+      if (!ok) break;
+      if (it >= 2) tc::fence_after_sync();
+      if (d >= 0) {
+        read_back();
+        drained_groups = d + 1;
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(drained);
+      }
+      const int j0 = (x0 + it) * kStep;
+      const bool edge = tile_edge || (j0 + kStep > n) || (j0 < t0 + kTgt && j0 + kStep > t0);
+      const float4* Sq = reinterpret_cast<const float4*>(smem + kOffS + q * kSRec) + 4 * 2 * sq;
+      unsigned char* a = smem + kOffA + s * kAStage;
+      if (edge)
+        tcx_gen<true>(xi, ni, Sq, j0 + 2 * sq, ti, n, tvalid, c, tab, r0, r1, a, off);
+      else
+        tcx_gen<false>(xi, ni, Sq, j0 + 2 * sq, ti, n, tvalid, c, tab, r0, r1, a, off);
+      tc::fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ready[s]);
+    }
+    for (int d = drained_groups; ok && d < n_groups; ++d) drain(d);
+    // unscale by 2^-(e + f) and write this split's partial sums
+    const bool all_valid = ok && tvalid && n_it > 0;
+    if (all_valid) {
+      const int comp = sq >> 1;
+      const int e = comp ? re.y : re.x;
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const int bl = 16 * (sq & 1) + b, bg = kRHS * h + bl;
+        if (bg < nb) {
+          const df w = df_scale(df_scale(acc[b], p2f(-e)), finv[bl]);
+          part[((int64_t)bg * n_splits + split) * 2 * n + (int64_t)comp * n + ti] = df_to_double(w);
+        }
+      }
+    }
+  }
+  const bool all_ok = __syncthreads_and(ok) != 0;
+  if (!all_ok && tid == 0) atomicExch(err, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace tcx
+
+// Work list of the exact tensor-core pass: target tiles x source splits (whole
+// K steps) filling whole waves of one CTA per SM, for `halves` groups of 32
+// right-hand sides.
+ItemPlan* tcx_plan(Surface* s, int n, int halves, int* S_out) {
+  const int n_steps = (n + tcx::kStep - 1) / tcx::kStep;
+  const int tiles = (n + tcx::kTgt - 1) / tcx::kTgt;
+  const int slots = s->num_sms;
+  int S = 1;
+  double best = 0.0;
+  for (int sp = 1; sp <= std::min(16, std::max(1, n_steps / tcx::kGroup)); ++sp) {
+    const long ctas = (long)tiles * sp * halves, waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / ((double)waves * slots);
+    if (eff > best * 1.02) best = eff, S = sp;
+  }
+  *S_out = S;
+  const uint64_t key = 0x7b0000000000ull ^ ((uint64_t)n << 12) ^ (uint64_t)S;
+  auto it = s->plans.find(key);
+  if (it == s->plans.end()) {
+    auto p = std::make_unique<ItemPlan>();
+    std::vector<int4> items;
+    for (int t = 0; t < tiles; ++t)
+      for (int sp = 0; sp < S; ++sp)
+        items.push_back(make_int4(t * tcx::kTgt, (int)((int64_t)sp * n_steps / S),
+                                  (int)((int64_t)(sp + 1) * n_steps / S), sp));
+    p->n_items = (int)items.size();
+    p->items.ensure(items.size(), s->stream);
+    BIPB_CUDA(cudaMemcpyAsync(p->items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                              s->stream));
+    BIPB_CUDA(cudaStreamSynchronize(s->stream));
+    ++s->alloc_gen;
+    it = s->plans.emplace(key, std::move(p)).first;
+  }
+  return it->second.get();
+}
+
+// The exact tensor-core pass for nb right-hand sides (u at ub, or the rows
+// rhs[b] of u when rhs is given): row exponents (cached per surface and
+// medium), right-hand-side digits, the kernel; writes part64 [b][split][2n]
+// and returns the number of splits.
+int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, const DFConst& c) {
+  const int halves = (nb + tcx::kRHS - 1) / tcx::kRHS;
+  const int n_steps = (n + tcx::kStep - 1) / tcx::kStep;
+  s->grow(s->geodf, (size_t)4 * n);
+  k_pack_mrhs_df<<<dim3((n + 255) / 256, 1), 256, 0, s->stream>>>(n, 0, s->tgt64.p, ub, rhs, s->geodf.p, s->udf.p);
+  BIPB_LAUNCHED(s);
+  const uint64_t gen0 = s->alloc_gen;
+  s->grow(s->tcx_rowexp, (size_t)n);
+  if (s->alloc_gen != gen0 || s->tcx_n != n || s->tcx_key[0] != c.eps.hi || s->tcx_key[1] != c.eps.lo ||
+      s->tcx_key[2] != c.kappa.hi || s->tcx_key[3] != c.kappa.lo) {
+    tcx::k_tcx_rowexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->geodf.p, c, s->tcx_rowexp.p);
+    BIPB_LAUNCHED(s);
+    s->tcx_n = n;
+    s->tcx_key[0] = c.eps.hi, s->tcx_key[1] = c.eps.lo, s->tcx_key[2] = c.kappa.hi, s->tcx_key[3] = c.kappa.lo;
+  }
+  s->grow(s->tcx_colmax, (size_t)kNB);
+  BIPB_CUDA(cudaMemsetAsync(s->tcx_colmax.p, 0, kNB * sizeof(unsigned), s->stream));
+  tcx::k_tcx_colmax<<<dim3((unsigned)std::min(64, (2 * n + 255) / 256), nb), 256, 0, s->stream>>>(n, ub, rhs,
+                                                                                                  s->tcx_colmax.p);
+  BIPB_LAUNCHED(s);
+  const int64_t pk = (int64_t)n_steps * halves * tcx::kRHS * tcx::kK;
+  s->grow(s->tcx_upk, (size_t)n_steps * halves * tcx::kBBytes / sizeof(float));
+  __half* upk = reinterpret_cast<__half*>(s->tcx_upk.p);
+  tcx::k_tcx_pack_u<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_steps, halves, ub, rhs,
+                                                                      s->tcx_colmax.p, upk);
+  BIPB_LAUNCHED(s);
+  int S = 1;
+  ItemPlan* plan = tcx_plan(s, n, halves, &S);
+  s->grow(s->part64, (size_t)nb * S * 2 * n);
+  if (s->tc_err.cap == 0) {
+    s->grow(s->tc_err, 1);
+    BIPB_CUDA(cudaMemsetAsync(s->tc_err.p, 0, sizeof(int), s->stream));
+  }
+  BIPB_CUDA(cudaFuncSetAttribute(tcx::k_mrhs_tcx, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::kSmemBytes));
+  {
+    TimedLaunch tl(s, kTMvDF);
+    tcx::k_mrhs_tcx<<<dim3(plan->n_items, halves), tcx::kThreads, tcx::kSmemBytes, s->stream>>>(
+        n, nb, S, halves, plan->items.p, s->geodf.p, s->tcx_rowexp.p, s->tcx_colmax.p, upk, s->part64.p, c,
+        s->tc_err.p);
+    BIPB_LAUNCHED(s);
+  }
+  return S;
+}
+
 }  // namespace
 
 void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
@@ -220,14 +709,19 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
   const int n_act = (int)act.size();
   for (int g0 = 0; g0 < n_act; g0 += kNB) {
     const int nb = std::min(kNB, n_act - g0);
+    // 16 or more right-hand sides: the exact tensor-core form; fewer: df64 on the CUDA cores
+    const bool tensor = nb >= kTcxMinRHS && s->tcx_enabled;
     const int G = nb <= kGB ? 1 : nb <= 2 * kGB ? 2 : nb <= 4 * kGB ? 4 : 8;
-    const int slots = s->num_sms * (G == 1   ? mrhs_df_occupancy<1>()
-                                    : G == 2 ? mrhs_df_occupancy<2>()
-                                    : G == 4 ? mrhs_df_occupancy<4>()
-                                             : mrhs_df_occupancy<8>());
     int S = 1;
-    ItemPlan* plan = mrhs_df_plan(s, n, G, slots, &S);
-    s->grow(s->part64, (size_t)nb * S * 2 * n);
+    ItemPlan* plan = nullptr;
+    if (!tensor) {
+      const int slots = s->num_sms * (G == 1   ? mrhs_df_occupancy<1>()
+                                      : G == 2 ? mrhs_df_occupancy<2>()
+                                      : G == 4 ? mrhs_df_occupancy<4>()
+                                               : mrhs_df_occupancy<8>());
+      plan = mrhs_df_plan(s, n, G, slots, &S);
+      s->grow(s->part64, (size_t)nb * S * 2 * n);
+    }
     // reduction layout: right-hand side b of this group at vec_off = act[g0 + b] * 2n of u and y
     SysLayout Lb;
     Lb.K = nb;
@@ -244,6 +738,16 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
     Lb.len = (int64_t)nb * 2 * n;
     Lb.max_n = n;
     Lb.key = h;
+    const int* rhs = nullptr;
+    const double* ub = u + (int64_t)act[g0] * 2 * n;
+    if (act[g0 + nb - 1] - act[g0] != nb - 1) {  // not contiguous: pass the indices
+      s->grow(s->rhs_idx, (size_t)nb);
+      BIPB_CUDA(cudaMemcpyAsync(s->rhs_idx.p, act.data() + g0, nb * sizeof(int), cudaMemcpyHostToDevice, s->stream));
+      BIPB_CUDA(cudaStreamSynchronize(s->stream));
+      rhs = s->rhs_idx.p;
+      ub = u;
+    }
+    if (tensor) S = launch_tcx(s, n, nb, ub, rhs, c);
     const uint64_t tkey = 0x7f0000000000ull ^ ((uint64_t)n << 16) ^ ((uint64_t)S << 8) ^ (uint64_t)nb;
     auto tt = s->plans.find(tkey);
     if (tt == s->plans.end()) {
@@ -256,14 +760,9 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
       ++s->alloc_gen;
       tt = s->plans.emplace(tkey, std::move(p)).first;
     }
-    const int* rhs = nullptr;
-    const double* ub = u + (int64_t)act[g0] * 2 * n;
-    if (act[g0 + nb - 1] - act[g0] != nb - 1) {  // not contiguous: pass the indices
-      s->grow(s->rhs_idx, (size_t)nb);
-      BIPB_CUDA(cudaMemcpyAsync(s->rhs_idx.p, act.data() + g0, nb * sizeof(int), cudaMemcpyHostToDevice, s->stream));
-      BIPB_CUDA(cudaStreamSynchronize(s->stream));
-      rhs = s->rhs_idx.p;
-      ub = u;
+    if (tensor) {
+      launch_reduce_matvec64(s, Lb, tt->second->tab.p, s->part64.p, u, y, dphi, dpsi, nullptr, 0);
+      continue;
     }
     s->grow(s->geodf, (size_t)4 * n);
     s->grow(s->udf, (size_t)nb * n);

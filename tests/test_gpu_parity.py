@@ -788,6 +788,35 @@ def test_multi_rhs_df64_matvec_matches_oracle(bipb, orc, n_rhs):
         np.testing.assert_allclose(Y[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
 
 
+def test_exact_tensor_residual_matches_cuda_core_df64(bipb, orc):
+    """The double-float mat-vec of 40 right-hand sides (one full group of 32
+    and a partial one) on the tensor cores (exact base-128 digits) against
+    the same on the CUDA cores and against the oracle: right-hand sides of
+    magnitude 1e-20 .. 1e20 and one zero right-hand side."""
+    p = _ragged(3)
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(77)
+    mags = 10.0 ** rng.uniform(-20, 20, 40)
+    U = rng.standard_normal((40, 2 * p.n)) * mags[:, None]
+    U[11] = 0.0
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yt, yc = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
+        s.matvec(ud, yt, precision=bipb.DF64, med=_med(bipb, p))
+        s.exact_tensor_residual(False)
+        s.matvec(ud, yc, precision=bipb.DF64, med=_med(bipb, p))
+        Yt, Yc = yt.cpu().numpy(), yc.cpu().numpy()
+    assert np.all(Yt[11] == 0.0)
+    for r in range(40):
+        if r == 11:
+            continue
+        scale = np.abs(Yc[r]).max()
+        np.testing.assert_allclose(Yt[r], Yc[r], rtol=0, atol=1e-13 * scale, err_msg=str(r))
+    for r in (0, 23, 39):
+        ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
+        np.testing.assert_allclose(Yt[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
+
+
 # ---------------------------------------------------------------- potential at points, free energy
 def _ball(rng, n, r0, r1):
     """n points with radii uniform in [r0, r1) and uniform directions."""
