@@ -1,5 +1,7 @@
 // Multi-right-hand-side mat-vec in double-float arithmetic (the refinement
-// residual of batched solves).
+// residual of batched solves), in two forms: df64 multiply-adds on the CUDA
+// cores (below; fewer than 16 right-hand sides) and exact digit products on
+// the tensor cores (namespace tcx further down; 16 or more).
 //
 // Y = A U for up to 64 right-hand sides of one surface.  A CTA covers 32
 // targets and G groups of 8 right-hand sides (G = 1, 2, 4 or 8, 32 G
