@@ -381,7 +381,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // This thread's two sources of a K step (records Sq, first index jq) against
 // target ti: the df64 block, scaled per row, as digit planes written into A
-// stage `a` (tile m, digit k at a + (7 m + k) kPlane; K columns 4 sq ..).
+// stage `a` (tile m, digit k at a + (7 m + k) kPlane; byte offset off of the
+// target's row and the sources' K columns).
 template <bool EDGE>
 __device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4* Sq, int jq, int ti, int n,
                                         bool tvalid, const DFConst& c, const df* tab, float r0, float r1,
@@ -510,22 +511,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    // generating warps: thread of TMEM lane r = 32 wq + lane owns target r; it
-    // generates sources 2 sq, 2 sq + 1 of every K step and reads back tile
-    // sq >> 1, right-hand sides 16 (sq & 1) .. + 15
+    // generating warps.  Generation: warp w covers targets 8 w .. 8 w + 7
+    // (lane & 7) and source pairs lane >> 3 (sources 2 sp, 2 sp + 1 of every
+    // K step), so that each half-warp's 8-byte digit stores fill 128
+    // contiguous bytes (no bank conflict).  Read-back: the thread of TMEM
+    // lane r = 32 wq + lane owns target r's accumulators of tile sq >> 1,
+    // right-hand sides 16 (sq & 1) .. + 15.
     const int sq = warp >> 2;
-    const int ti = t0 + 32 * wq + lane;
-    const bool tvalid = ti < n;
+    const int rg = 8 * warp + (lane & 7), sp = lane >> 3;
+    const int tg = t0 + rg;  // the generated target
+    const bool gvalid = tg < n;
     df xi[3], ni[3];
     {
-      const int64_t r = 4 * (int64_t)min(ti, n - 1);
+      const int64_t r = 4 * (int64_t)min(tg, n - 1);
       const float4 A = geo[r], B = geo[r + 1], C = geo[r + 2], D = geo[r + 3];
       xi[0] = df{A.x, B.x}, xi[1] = df{A.y, B.y}, xi[2] = df{A.z, B.z};
       ni[0] = df{C.x, D.x}, ni[1] = df{C.y, D.y}, ni[2] = df{C.z, D.z};
     }
-    const int2 re = rowexp[min(ti, n - 1)];
-    const float r0 = p2f(re.x), r1 = p2f(re.y);
-    const uint32_t off = koff(32 * wq + lane, 4 * sq);
+    const int2 rg_e = rowexp[min(tg, n - 1)];
+    const float r0 = p2f(rg_e.x), r1 = p2f(rg_e.y);
+    const uint32_t off = koff(rg, 4 * sp);
+    const int ti = t0 + 32 * wq + lane;  // the read-back target
+    const bool tvalid = ti < n;
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
     const uint32_t dthr = tmem + lane_base + (sq >> 1) * 256 + 16 * (sq & 1);
     const bool tile_edge = t0 + kTgt > n;
@@ -570,12 +577,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       const int j0 = (x0 + it) * kStep;
       const bool edge = tile_edge || (j0 + kStep > n) || (j0 < t0 + kTgt && j0 + kStep > t0);
-      const float4* Sq = reinterpret_cast<const float4*>(smem + kOffS + q * kSRec) + 4 * 2 * sq;
+      const float4* Sq = reinterpret_cast<const float4*>(smem + kOffS + q * kSRec) + 4 * 2 * sp;
       unsigned char* a = smem + kOffA + s * kAStage;
       if (edge)
-        tcx_gen<true>(xi, ni, Sq, j0 + 2 * sq, ti, n, tvalid, c, tab, r0, r1, a, off);
+        tcx_gen<true>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, off);
       else
-        tcx_gen<false>(xi, ni, Sq, j0 + 2 * sq, ti, n, tvalid, c, tab, r0, r1, a, off);
+        tcx_gen<false>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, off);
       tc::fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
       __syncwarp();
       if (lane == 0) mbar_arrive(&ready[s]);
@@ -585,6 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool all_valid = ok && tvalid && n_it > 0;
     if (all_valid) {
       const int comp = sq >> 1;
+      const int2 re = rowexp[ti];
       const int e = comp ? re.y : re.x;
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
