@@ -67,6 +67,7 @@
 
 #include <algorithm>
 
+#include "f32x2.cuh"
 #include "internal.cuh"
 #include "tcgen05.cuh"
 
@@ -201,13 +202,57 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
 }
 
+// kernel_block for the two sources of a record pair at once, in packed FP32
+// (two results per instruction).  Source records are pair-interleaved:
+// P0 = (x0, x1, y0, y1), P1 = (z0, z1, w0, w1), P2 = (nx0, nx1, ny0, ny1),
+// P3 = (nz0, nz1, -, -); T holds the target's x, y, z, nx, ny, nz as splats.
+// v[k] holds value k (K2, K1, K4, K3 times ds) of both sources; z0, z1 mask
+// a source as `zero` does in kernel_block.
+template <bool EDGE>
+__device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, const float4& P1, const float4& P2,
+                                              const float4& P3, bool z0, bool z1, const PairConst<float>& c, f2* v) {
+  const f2 one = f2_splat(1.f), three = f2_splat(3.f);
+  const f2 dx = f2_sub(T[0], f2_make(P0.x, P0.y));
+  const f2 dy = f2_sub(T[1], f2_make(P0.z, P0.w));
+  const f2 dz = f2_sub(T[2], f2_make(P1.x, P1.y));
+  const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+  float ra, rb;
+  f2_get(r2, ra, rb);
+  float sa0 = fminf(rsqrt_approx(ra), kSMaxF), sb0 = fminf(rsqrt_approx(rb), kSMaxF);
+  if (EDGE) {
+    sa0 = z0 ? 0.f : sa0;
+    sb0 = z1 ? 0.f : sb0;
+  }
+  const f2 s = f2_make(sa0, sb0);
+  const f2 r = f2_mul(r2, s);
+  float ea, eb;
+  f2_get(f2_mul(r, f2_splat(c.nkl2e)), ea, eb);
+  const f2 e = f2_make(ex2_approx(ea), ex2_approx(eb));
+  const f2 kr = f2_mul(r, f2_splat(c.kappa));
+  const f2 nx = f2_make(P2.x, P2.y), ny = f2_make(P2.z, P2.w), nz = f2_make(P3.x, P3.y);
+  const f2 ci = f2_fma(T[3], dx, f2_fma(T[4], dy, f2_mul(T[5], dz)));
+  const f2 cj = f2_fma(nx, dx, f2_fma(ny, dy, f2_mul(nz, dz)));
+  const f2 cij = f2_fma(T[3], nx, f2_fma(T[4], ny, f2_mul(T[5], nz)));
+  const f2 t = f2_fma(e, kr, e);
+  const f2 tm1 = f2_sub(t, one);
+  const f2 wm3 = f2_fma(f2_sub(t, e), kr, f2_mul(three, tm1));
+  const f2 sa = f2_mul(s, f2_make(P1.z, P1.w));
+  const f2 s2 = f2_mul(s, s);
+  const f2 s3a = f2_mul(s2, sa);
+  v[1] = f2_mul(f2_sub(one, e), sa);                                                             // K1 ds
+  v[0] = f2_mul(f2_mul(f2_fma(f2_splat(c.eps), t, f2_splat(-1.f)), cj), s3a);                    // K2 ds
+  v[3] = f2_mul(f2_mul(f2_fma(t, f2_splat(c.inveps), f2_splat(-1.f)), ci), s3a);                 // K3 ds
+  v[2] = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3, f2_mul(f2_mul(ci, cj), s2))), s3a);         // K4 ds
+}
+
 // Column scale exponents: for source j, e(j, 0) from the largest |K2 ds_j|,
 // |K4 ds_j| and e(j, 1) from the largest |K1 ds_j|, |K3 ds_j| over all
 // targets i != j (the same FP32 values the tensor-core kernel generates); 0
 // for a column of zeros (no dielectric contrast and kappa = 0), and the two
 // kept within 2^40 of each other by lowering the larger, so that the scaled
 // normal and the products formed from it stay far from the FP32 range.  Then
-// the scaled source records.  One thread per source.
+// the scaled source records, pair-interleaved for kernel_block2.  One thread
+// per source.
 __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
                                                    int2* __restrict__ srcexp, float4* __restrict__ src) {
   __shared__ float4 sh[2 * 128];
@@ -238,8 +283,10 @@ __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restri
   if (e1 - e0 > 40) e1 = e0 + 40;
   srcexp[j] = make_int2(e0, e1);
   const float r01 = pow2f(e0 - e1);
-  src[2 * j] = make_float4(gj.x, gj.y, gj.z, gj.w * pow2f(e1));
-  src[2 * j + 1] = make_float4(nj.x * r01, nj.y * r01, nj.z * r01, 0.f);
+  // pair-interleaved records (kernel_block2): element j in slot j & 1 of pair j >> 1
+  float* o = reinterpret_cast<float*>(src) + 16 * (j >> 1) + (j & 1);
+  o[0] = gj.x, o[2] = gj.y, o[4] = gj.z, o[6] = gj.w * pow2f(e1);
+  o[8] = nj.x * r01, o[10] = nj.y * r01, o[12] = nj.z * r01, o[14] = 0.f;
 }
 
 // two FP32 values (the lower k first) as FP16 parts: hi = round(a), lo =
@@ -259,29 +306,38 @@ __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, ui
       : "f"(a0), "f"(a1));
 }
 
-// This thread's kPerThread sources of a chunk (records Sq, first index jq)
-// against target ti: the scaled pair values, split into FP16 parts, written
-// into the thread's TMEM lane from column acol on (tile 0 hi / lo at + 0 /
-// + kChunk, tile 1 at + 2 kChunk / + 3 kChunk).  EDGE masks pairs with no
-// target, a source past the end or the self pair.
+// This thread's kPerThread sources of a chunk (pair records Sp, first index
+// jq) against target ti (splats T): the scaled pair values, two sources per
+// packed evaluation, split into FP16 parts and written into the thread's TMEM
+// lane from column acol on (tile 0 hi / lo at + 0 / + kChunk, tile 1 at
+// + 2 kChunk / + 3 kChunk).  EDGE masks pairs with no target, a source past
+// the end or the self pair.
 template <bool EDGE>
-__device__ __forceinline__ void gen_chunk(const float4& gi, const float4& ni, const float4* Sq, int jq, int ti, int n,
-                                          bool tvalid, const PairConst<float>& c, uint32_t acol) {
+__device__ __forceinline__ void gen_chunk(const f2* T, const float4* Sp, int jq, int ti, int n, bool tvalid,
+                                          const PairConst<float>& c, uint32_t acol) {
 #pragma unroll
   for (int hh = 0; hh < kPerThread / 4; ++hh) {
     uint32_t h0[4], l0[4], h1[4], l1[4];  // per source: the phi-row pair (K2, K1) and psi-row pair (K4, K3)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int jj = 4 * hh + u;
-      const bool z = EDGE && (!tvalid || jq + jj >= n || jq + jj == ti);
-      float v[4];
-      kernel_block(gi.x, gi.y, gi.z, ni.x, ni.y, ni.z, Sq[2 * jj], Sq[2 * jj + 1], z, c, v);
-      if (EDGE) {
+    for (int pp = 0; pp < 2; ++pp) {
+      const int p = 2 * hh + pp;
+      const int ja = jq + 2 * p, jb = ja + 1;
+      const bool za = EDGE && (!tvalid || ja >= n || ja == ti), zb = EDGE && (!tvalid || jb >= n || jb == ti);
+      f2 v[4];
+      kernel_block2<EDGE>(T, Sp[4 * p], Sp[4 * p + 1], Sp[4 * p + 2], Sp[4 * p + 3], za, zb, c, v);
+      float a[4], b[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = z ? 0.f : v[k];
+      for (int k = 0; k < 4; ++k) {
+        f2_get(v[k], a[k], b[k]);
+        if (EDGE) {
+          a[k] = za ? 0.f : a[k];
+          b[k] = zb ? 0.f : b[k];
+        }
       }
-      split_f16x2(v[0], v[1], h0[u], l0[u]);
-      split_f16x2(v[2], v[3], h1[u], l1[u]);
+      split_f16x2(a[0], a[1], h0[2 * pp], l0[2 * pp]);
+      split_f16x2(a[2], a[3], h1[2 * pp], l1[2 * pp]);
+      split_f16x2(b[0], b[1], h0[2 * pp + 1], l0[2 * pp + 1]);
+      split_f16x2(b[2], b[3], h1[2 * pp + 1], l1[2 * pp + 1]);
     }
     tc::tmem_st4(acol + 4 * hh, h0);
     tc::tmem_st4(acol + 4 * hh + kChunk, l0);
@@ -365,8 +421,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
         if (!ok) break;
         const int ch = c0 + x;
         const int cnt = min(kChunk, n - ch * kChunk);
-        arrive_expect_tx(&sfull[q], cnt * 32);
-        bulk_load(smem + kOffS + q * kSBytes, src + 2 * (int64_t)ch * kChunk, cnt * 32, &sfull[q]);
+        arrive_expect_tx(&sfull[q], 64 * ((cnt + 1) / 2));
+        // pair records: 64 bytes per pair of sources
+        bulk_load(smem + kOffS + q * kSBytes, src + 2 * (int64_t)ch * kChunk, 64 * ((cnt + 1) / 2), &sfull[q]);
         arrive_expect_tx(&ufull[q], kUBytes);
         bulk_load(smem + kOffB + q * kUBytes, reinterpret_cast<const unsigned char*>(upk) + (int64_t)ch * kUBytes,
                   kUBytes, &ufull[q]);
@@ -419,6 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     const int ti = t0 + 32 * wq + lane;
     const bool tvalid = ti < n;
     const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
+    const f2 T[6] = {f2_splat(gi.x), f2_splat(gi.y), f2_splat(gi.z), f2_splat(ni.x), f2_splat(ni.y), f2_splat(ni.z)};
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
     const uint32_t dthr = tmem + lane_base + kColD + (sq >> 1) * 128 + 32 * (sq & 1);
     const bool tile_edge = t0 + kTgt > n;
@@ -468,15 +526,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       // chunks at the end of the surface or over the CTA's own targets, and the
       // last target tile, mask pairs (source past the end, self pair, no target)
       const bool edge = tile_edge || (j0 + kChunk > n) || (j0 < t0 + kTgt && j0 + kChunk > t0);
-      const float4* S = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes);
-      const float4* Sq = S + 2 * kPerThread * sq;
+      const float4* Sp = reinterpret_cast<const float4*>(smem + kOffS + q * kSBytes) + 2 * kPerThread * sq;
       const int jq = j0 + kPerThread * sq;
       const uint32_t acol = tmem + lane_base + kColA + s * kACols + kPerThread * sq;
       // one branch per chunk: the masked form only where a chunk needs it
       if (edge)
-        gen_chunk<true>(gi, ni, Sq, jq, ti, n, tvalid, c, acol);
+        gen_chunk<true>(T, Sp, jq, ti, n, tvalid, c, acol);
       else
-        gen_chunk<false>(gi, ni, Sq, jq, ti, n, tvalid, c, acol);
+        gen_chunk<false>(T, Sp, jq, ti, n, tvalid, c, acol);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
@@ -567,7 +624,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
   // medium (buffers that moved are recomputed)
   const uint64_t gen0 = s->alloc_gen;
   s->grow(s->tc_srcexp, (size_t)n);
-  s->grow(s->tc_src, (size_t)2 * n);
+  s->grow(s->tc_src, (size_t)4 * ((n + 1) / 2));  // 4 float4 per pair of sources
   if (s->alloc_gen != gen0 || s->tc_src_n != n || s->tc_src_key[0] != c.eps || s->tc_src_key[1] != c.inveps ||
       s->tc_src_key[2] != c.kappa) {
     k_tc_colexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
