@@ -9,7 +9,8 @@
 //     [ K2 ds_j   K1 ds_j ]        (row phi_i, tile 0)
 //     [ K4 ds_j   K3 ds_j ]        (row psi_i, tile 1)     (Sec. 2.2.1, Eqs. 5-6)
 // in FP32 (each column scaled by a power of two through scaled source
-// records, below), split each value a into two FP16 parts (a_hi = a rounded to FP16, a_lo = a - a_hi rounded to FP16:
+// records, below; two sources per packed-FP32 instruction, f32x2.cuh, from
+// source records interleaved by pairs), split each value a into two FP16 parts (a_hi = a rounded to FP16, a_lo = a - a_hi rounded to FP16:
 // 22 significant bits together) and write both into tensor memory, where the
 // MMA reads its A operand: the thread that owns TMEM lane r owns target r's
 // row in both tiles, so it computes a pair's four values once and writes each
