@@ -251,6 +251,7 @@ constexpr int kLoadWarp = kMmaWarp + 1;         // warp 17: issues the bulk copi
 constexpr int kThreads = kGenThreads + 64;
 constexpr uint32_t kTmemCols = 512;             // tile m's levels at 256 m + 32 L
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kDrainLimitNs = 100000000ull;  // per wait while draining after a time-out
 static_assert(kOffBar % 8 == 0 && kOffTab % 16 == 0, "alignment");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n_it = x1 - x0;
   const int n_groups = (n_it + kGroup - 1) / kGroup;
   bool ok = true;
+  int issued = 0, mma_last = -1;  // K steps whose copies / MMAs this CTA has issued
   const int wq = warp & 3;
   if (warp == kLoadWarp) {
     if (lane == 0) {
@@ -480,6 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         bulk_load(smem + kOffB + q * kBBytes,
                   reinterpret_cast<const unsigned char*>(upk) + ((int64_t)st * halves + h) * kBBytes, kBBytes,
                   &ufull[q]);
+        issued = x + 1;
       }
     }
     __syncwarp();
@@ -507,6 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::mma_commit(&afree[s]);
         tc::mma_commit(&bfree[q]);
         if (last) tc::mma_commit(done);
+        mma_last = it;
       }
     }
     __syncwarp();
@@ -605,7 +609,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   }
   const bool all_ok = __syncthreads_and(ok) != 0;
-  if (!all_ok && tid == 0) atomicExch(err, 1);
+  if (!all_ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // a wait ran out: the copies and MMAs this CTA issued land before its
+    // shared and tensor memory are given up (each wait bounded again)
+    if (warp == kLoadWarp && lane == 0)
+      for (int x = max(0, issued - kRing); x < issued; ++x) {
+        tc::mbar_wait_timed(&sfull[x % kRing], (x / kRing) & 1, kDrainLimitNs);
+        tc::mbar_wait_timed(&ufull[x % kRing], (x / kRing) & 1, kDrainLimitNs);
+      }
+    if (warp == kMmaWarp && lane == 0 && mma_last >= 0)
+      tc::mbar_wait_timed(&bfree[mma_last % kRing], (mma_last / kRing) & 1, kDrainLimitNs);
+  }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);

@@ -98,6 +98,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kColA = 0;               // A buffer s at kColA + kACols s
 constexpr uint32_t kColD = 256;             // accumulator of tile m at kColD + 128 m
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait longer than 2 s is an error
+constexpr uint64_t kDrainLimitNs = 100000000ull;  // per wait while draining after a time-out
 constexpr int kScaleTop = 14;               // scaled magnitudes lie in [2^14, 2^15)
 constexpr int kScaleClamp = 100;            // scale exponents are clamped to [-100, 100]
 static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
@@ -402,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   const int n_it = c1 - c0;
   const int n_groups = (n_it + kGroup - 1) / kGroup;
   bool ok = true;
+  int issued = 0, mma_last = -1;  // chunks whose copies / MMAs this CTA has issued
   // a generating warp: TMEM lane quarter wq (the warp's own)
   const int wq = warp & 3;
   float acc[32];
@@ -428,6 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
         arrive_expect_tx(&ufull[q], kUBytes);
         bulk_load(smem + kOffB + q * kUBytes, reinterpret_cast<const unsigned char*>(upk) + (int64_t)ch * kUBytes,
                   kUBytes, &ufull[q]);
+        issued = x + 1;
       }
     }
     __syncwarp();
@@ -463,6 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
         tc::mma_commit(&afree[s]);
         tc::mma_commit(&bfree[q]);
         if (last) tc::mma_commit(done);
+        mma_last = it;
       }
     }
     __syncwarp();
@@ -544,7 +548,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     for (int d = drained_groups; ok && d < n_groups; ++d) drain(d);
   }
   const bool all_ok = __syncthreads_and(ok) != 0;
-  if (!all_ok && tid == 0) atomicExch(err, 1);
+  if (!all_ok) {
+    if (tid == 0) atomicExch(err, 1);
+    // a wait ran out: the copies and MMAs this CTA issued land before its
+    // shared and tensor memory are given up (each wait bounded again)
+    if (warp == kLoadWarp && lane == 0)
+      for (int x = max(0, issued - kRing); x < issued; ++x) {
+        tc::mbar_wait_timed(&sfull[x % kRing], (x / kRing) & 1, kDrainLimitNs);
+        tc::mbar_wait_timed(&ufull[x % kRing], (x / kRing) & 1, kDrainLimitNs);
+      }
+    if (warp == kMmaWarp && lane == 0 && mma_last >= 0)
+      tc::mbar_wait_timed(&bfree[mma_last % kRing], (mma_last / kRing) & 1, kDrainLimitNs);
+  }
 
   // epilogue: this thread holds target 32 wq + lane, component sq >> 1 (tile),
   // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-f(b)
