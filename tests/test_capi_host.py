@@ -65,7 +65,7 @@ def geom():
 
 
 @pytest.mark.parametrize("case", ["nan_centroid", "zero_area", "neg_area", "bad_normal", "duplicate", "too_small",
-                                  "inf_normal", "duplicate_fp32"])
+                                  "empty", "inf_normal", "duplicate_fp32"])
 def test_create_rejects_bad_geometry(bipb, geom, case):
     c, n, a = (v.copy() for v in geom)
     if case == "nan_centroid":
@@ -80,6 +80,8 @@ def test_create_rejects_bad_geometry(bipb, geom, case):
         c[5] = c[9]
     elif case == "too_small":
         c, n, a = c[:1], n[:1], a[:1]
+    elif case == "empty":
+        c, n, a = c[:0], n[:0], a[:0]
     elif case == "inf_normal":
         n[4, 0] = np.inf
     elif case == "duplicate_fp32":
