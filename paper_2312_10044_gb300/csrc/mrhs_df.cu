@@ -206,42 +206,50 @@ ItemPlan* mrhs_df_plan(Surface* s, int n, int G, int slots, int* S_out) {
 
 // ------------------------------------------------------------------ exact tensor-core form
 // The same product with the multiply-adds on the tensor cores, exactly.  Row
-// i of tile m (the phi rows, then the psi rows of 128 targets) is scaled by
-// 2^e(i, m) and right-hand side b by 2^f(b) so that every value lies below
-// 64 in magnitude; each df64 kernel value a and each right-hand-side value u
-// is then written as seven signed base-128 digits,
+// i (the phi or psi row of a target) is scaled by 2^e(i) and right-hand side
+// b by 2^f(b) so that every value lies below 64 in magnitude; each df64
+// kernel value a and each right-hand-side value u is then written as seven
+// signed base-128 digits,
 //     a = sum_k d_k 128^-k,   u = sum_l t_l 128^-l,   |d_k|, |t_l| <= 68,
 // which FP16 holds exactly.  A kind::f16 MMA of digit planes multiplies
 // integers exactly and its FP32 accumulator adds them exactly while every
 // sum stays below 2^24 (checked on GB300 by a probe), so level L = k + l of
 // the product, sum_{k+l=L} d_k t_l, is accumulated without rounding in its
-// own 32 TMEM columns: per K step and tile, seven MMAs A_k [T_0 | .. |
-// T_{6-k}] (N = 32 (7 - k)) write levels k .. 6.  Levels above 6 (below
-// 2^-46 of the largest product) are dropped.  Every 32 K steps (512 K,
-// which bounds the sums by 512 x 7 x 68 x 64 < 2^24) the generating threads
-// read the levels back and add sum_L v_L 128^-L to df64 accumulators.  The
-// result matches the CUDA-core df64 kernel's accuracy at a fraction of its
-// instructions: the df64 kernel values are generated once per CTA of 32
-// right-hand sides, and the multiply-adds cost nothing on the CUDA cores.
+// own 64 TMEM columns (one per right-hand side): per K chunk of 8 sources,
+// MMAs A_k [T_0 | .. | T_{6-k}] (N = 64 (7 - k), cut into pieces of at most
+// 256) write levels k .. 6.  Levels above 6 (below 2^-46 of the largest
+// product) are dropped.  Every 32 K chunks (512 K, which bounds the sums by
+// 512 x 7 x 68 x 64 < 2^24) the generating threads read the levels back and
+// add sum_L v_L 128^-L to df64 accumulators.
+//
+// The M = 128 rows of the MMA are the phi rows (0..63) and the psi rows
+// (64..127) of 64 targets, so that the seven levels of all 64 right-hand
+// sides fit tensor memory (448 of its 512 columns): every df64 kernel block
+// is generated once for all 64 right-hand sides, and the multiply-adds cost
+// nothing on the CUDA cores.
 namespace tcx {
 
-constexpr int kRHS = 32;                        // right-hand sides per CTA
+constexpr int kRHS = 64;                        // right-hand sides per CTA (all of a launch)
 constexpr int kLv = 7;                          // digits per value = accumulation levels
-constexpr int kTgt = 128;                       // targets per CTA (two M = 128 tiles)
-constexpr int kStep = 8;                        // sources per K step
-constexpr int kK = 2 * kStep;                   // K of one step (one kind::f16 MMA)
-constexpr int kPlane = kTgt * kK * 2;           // one digit plane of one tile: 4 KB
-constexpr int kAStage = 2 * kLv * kPlane;       // A of one K step: 56 KB
-constexpr int kBRows = kLv * kRHS;              // 224 rows: digit plane l of U in rows 32 l ..
-constexpr int kBBytes = kBRows * kK * 2;        // 7 KB
-constexpr int kSRec = kStep * 64;               // source records of one K step: 512 B
-constexpr int kRing = 8;                        // B and source buffers (step it in buffer it % 8)
-constexpr int kGroup = 32;                      // K steps per exact accumulation group (K = 512)
+constexpr int kTgt = 64;                        // targets per CTA: rows t (phi) and 64 + t (psi)
+constexpr int kStep = 16;                       // sources per step: two K chunks
+constexpr int kKC = 16;                         // K of one chunk (8 sources x phi, psi; one kind::f16 MMA)
+constexpr int kChunks = kStep * 2 / kKC;        // K chunks per step
+constexpr int kPlane = 128 * kKC * 2;           // one digit plane of one K chunk: 4 KB
+constexpr int kAStage = kChunks * kLv * kPlane; // A of one step: 56 KB
+constexpr int kBRows = kLv * kRHS;              // 448 rows: digit plane l of U in rows 64 l ..
+constexpr int kBChunk = kBRows * kKC * 2;       // 14 KB per K chunk
+constexpr int kBBytes = kChunks * kBChunk;      // 28 KB per step
+constexpr int kSRec = kStep * 64;               // source records of one step: 1 KB
+constexpr int kRing = 3;                        // B and source buffers (step it in buffer it % 3)
+constexpr int kGroupChunks = 32;                // K chunks per exact accumulation group (K = 512)
+constexpr int kGroup = kGroupChunks / kChunks;  // steps per group
+constexpr int kMaxN = 256;                      // largest N of one MMA
 constexpr int kOffA = 0;                        // two A stages
 constexpr int kOffB = kOffA + 2 * kAStage;
 constexpr int kOffS = kOffB + kRing * kBBytes;
 constexpr int kOffTab = kOffS + kRing * kSRec;
-constexpr int kOffF = kOffTab + kExpTab * 8;    // 2^-f(b) of the CTA's right-hand sides
+constexpr int kOffF = kOffTab + kExpTab * 8;    // 2^-f(b) of the right-hand sides
 constexpr int kOffBar = kOffF + kRHS * 4;
 constexpr int kNumBars = 3 * kRing + 2 * 2 + 2;
 constexpr int kSmemBytes = kOffBar + kNumBars * 8 + 16;
@@ -249,11 +257,15 @@ constexpr int kGenThreads = 512;
 constexpr int kMmaWarp = kGenThreads / 32;      // warp 16: issues the MMAs
 constexpr int kLoadWarp = kMmaWarp + 1;         // warp 17: issues the bulk copies
 constexpr int kThreads = kGenThreads + 64;
-constexpr uint32_t kTmemCols = 512;             // tile m's levels at 256 m + 32 L
+constexpr uint32_t kTmemCols = 512;             // level L at columns 64 L
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 100000000ull;  // per wait while draining after a time-out
+static_assert(kChunks == 2 && kGroup * kChunks == kGroupChunks, "steps of two K chunks");
+static_assert(kGenThreads == kTgt * kStep / 2, "one thread per (target, source pair) of a step");
+static_assert(kOffB % 1024 == 0 && kBChunk % 16 == 0 && kSRec % 16 == 0, "bulk-copy alignment");
 static_assert(kOffBar % 8 == 0 && kOffTab % 16 == 0, "alignment");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(kLv * kRHS <= (int)kTmemCols, "levels fit tensor memory");
 
 // byte offset of element (row, k) of a K-major, no-swizzle FP16 tile with K = 16
 __host__ __device__ __forceinline__ uint32_t koff(int row, int k) {
@@ -341,27 +353,25 @@ __global__ void k_tcx_colmax(int n, const double* __restrict__ u, const int* __r
   if ((threadIdx.x & 31) == 0) atomicMax(colmax + b, __float_as_uint(m));
 }
 
-// U digit tiles: for K step x and right-hand-side half h, row 32 l + b holds
-// digit l of u_b 2^f(b) (b = 32 h + b'), K = 2 j' + c (phi_j, psi_j of the
-// step's sources), K-major.  One thread per (x, h, b', k).
-__global__ void k_tcx_pack_u(int n, int nb, int n_steps, int halves, const double* __restrict__ u,
-                             const int* __restrict__ rhs, const unsigned* __restrict__ colmax,
-                             __half* __restrict__ upk) {
+// U digit tiles: for step x and K chunk kc, row 64 l + b holds digit l of
+// u_b 2^f(b), K = 2 j' + c (phi_j, psi_j of the chunk's sources), K-major.
+// One thread per (x, kc, b, k).
+__global__ void k_tcx_pack_u(int n, int nb, int n_steps, const double* __restrict__ u, const int* __restrict__ rhs,
+                             const unsigned* __restrict__ colmax, __half* __restrict__ upk) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)n_steps * halves * kRHS * kK) return;
-  const int k = (int)(e % kK), bl = (int)((e / kK) % kRHS);
-  const int h = (int)((e / (kK * kRHS)) % halves);
-  const int64_t x = e / ((int64_t)kK * kRHS * halves);
-  const int b = kRHS * h + bl;
-  const int j = (int)(x * kStep) + (k >> 1), c = k & 1;
+  if (e >= (int64_t)n_steps * kChunks * kRHS * kKC) return;
+  const int k = (int)(e % kKC), b = (int)((e / kKC) % kRHS);
+  const int kc = (int)((e / (kKC * kRHS)) % kChunks);
+  const int64_t x = e / ((int64_t)kKC * kRHS * kChunks);
+  const int j = (int)(x * kStep) + kc * (kKC / 2) + (k >> 1), c = k & 1;
   double v = 0.0;
   if (b < nb && j < n)
     v = u[(int64_t)(rhs ? rhs[b] : b) * 2 * n + (int64_t)c * n + j] * p2d(scale_exp(__uint_as_float(colmax[b])));
-  unsigned char* tile = reinterpret_cast<unsigned char*>(upk) + (x * halves + h) * (int64_t)kBBytes;
+  unsigned char* tile = reinterpret_cast<unsigned char*>(upk) + x * (int64_t)kBBytes + kc * kBChunk;
 #pragma unroll
   for (int l = 0; l < kLv; ++l) {
     const double d = rint(v);
-    *reinterpret_cast<__half*>(tile + koff(kRHS * l + bl, k)) = __float2half_rn((float)d);
+    *reinterpret_cast<__half*>(tile + koff(kRHS * l + b, k)) = __float2half_rn((float)d);
     v = (v - d) * 128.0;
   }
 }
@@ -380,21 +390,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-// This thread's two sources of a K step (records Sq, first index jq) against
-// target ti: the df64 block, scaled per row, as digit planes written into A
-// stage `a` (tile m, digit k at a + (7 m + k) kPlane; byte offset off of the
-// target's row and the sources' K columns).
+// This thread's source pair of a step (records Sq, first index jq) against
+// target tg: the df64 block, scaled per row, as digit planes written into
+// the K chunk's planes at `a` (digit k at a + k kPlane; byte offsets offp and
+// offq of the target's phi and psi rows at the pair's K columns).
 template <bool EDGE>
-__device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4* Sq, int jq, int ti, int n,
+__device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4* Sq, int jq, int tg, int n,
                                         bool tvalid, const DFConst& c, const df* tab, float r0, float r1,
-                                        unsigned char* a, uint32_t off) {
+                                        unsigned char* a, uint32_t offp, uint32_t offq) {
   float dg[2][4][kLv];  // [source][value: K2, K1, K4, K3][digit]
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const float4 A = Sq[4 * u], B = Sq[4 * u + 1], C = Sq[4 * u + 2], D = Sq[4 * u + 3];
     const df xj[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
     const df nj[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
-    const bool z = EDGE && (!tvalid || jq + u >= n || jq + u == ti);
+    const bool z = EDGE && (!tvalid || jq + u >= n || jq + u == tg);
     df k[4];
     df_kernel_block<EDGE>(xi, ni, xj, nj, df{A.w, B.w}, z, c, tab, k);
 #pragma unroll
@@ -404,7 +414,7 @@ __device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4
       digits7(w, dg[u][v]);
     }
   }
-  // tile 0: (K2, K1) of sources 0, 1 in K columns 4 sq .. 4 sq + 3; tile 1: (K4, K3)
+  // phi row: (K2, K1) of sources 0, 1 in the pair's four K columns; psi row: (K4, K3)
 #pragma unroll
   for (int m = 0; m < 2; ++m)
 #pragma unroll
@@ -414,18 +424,18 @@ __device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4
       uint2 w;
       w.x = *reinterpret_cast<const uint32_t*>(&p0);
       w.y = *reinterpret_cast<const uint32_t*>(&p1);
-      *reinterpret_cast<uint2*>(a + (m * kLv + k) * kPlane + off) = w;
+      *reinterpret_cast<uint2*>(a + k * kPlane + (m ? offq : offp)) = w;
     }
 }
 
-// items: {t0, first K step, end K step, split}; blockIdx.y: right-hand-side half;
-// part: [b][split][2n] for the nb right-hand sides of this pass.
+// items: {t0, first step, end step, split}; part: [b][split][2n] for the nb
+// right-hand sides of this pass.
 __global__ void __launch_bounds__(kThreads, 1)
-    k_mrhs_tcx(int n, int nb, int n_splits, int halves, const int4* __restrict__ items, const float4* __restrict__ geo,
+    k_mrhs_tcx(int n, int nb, int n_splits, const int4* __restrict__ items, const float4* __restrict__ geo,
                const int2* __restrict__ rowexp, const unsigned* __restrict__ colmax, const __half* __restrict__ upk,
                double* __restrict__ part, DFConst c, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  uint64_t* ufull = reinterpret_cast<uint64_t*>(smem + kOffBar);  // kRing: U digit tile landed
+  uint64_t* ufull = reinterpret_cast<uint64_t*>(smem + kOffBar);  // kRing: U digit tiles landed
   uint64_t* sfull = ufull + kRing;                                 // kRing: source records landed
   uint64_t* bfree = sfull + kRing;                                 // kRing: MMAs of the buffer's step finished
   uint64_t* ready = bfree + kRing;                                 // 2: A stage written (16 warp arrivals)
@@ -438,7 +448,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int4 item = items[blockIdx.x];
   const int t0 = item.x, x0 = item.y, x1 = item.z, split = item.w;
-  const int h = blockIdx.y;
   if (tid == 0) {
     for (int q = 0; q < kRing; ++q) {
       tc::mbar_init(&ufull[q], 1);
@@ -453,10 +462,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc::mbar_init(drained, kGenThreads / 32);
     tc::fence_mbar_init();
   }
-  if (tid < kRHS) {
-    const int b = kRHS * h + tid;
-    finv[tid] = b < nb ? p2f(-scale_exp(__uint_as_float(colmax[b]))) : 0.f;
-  }
+  if (tid < kRHS) finv[tid] = tid < nb ? p2f(-scale_exp(__uint_as_float(colmax[tid]))) : 0.f;
   df_load_exp_table(tab, c);
   if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
   tc::fence_before_sync();
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n_it = x1 - x0;
   const int n_groups = (n_it + kGroup - 1) / kGroup;
   bool ok = true;
-  int issued = 0, mma_last = -1;  // K steps whose copies / MMAs this CTA has issued
+  int issued = 0, mma_last = -1;  // steps whose copies / MMAs this CTA has issued
   const int wq = warp & 3;
   if (warp == kLoadWarp) {
     if (lane == 0) {
@@ -479,9 +485,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         arrive_expect_tx(&sfull[q], cnt * 64);
         bulk_load(smem + kOffS + q * kSRec, geo + 4 * (int64_t)st * kStep, cnt * 64, &sfull[q]);
         arrive_expect_tx(&ufull[q], kBBytes);
-        bulk_load(smem + kOffB + q * kBBytes,
-                  reinterpret_cast<const unsigned char*>(upk) + ((int64_t)st * halves + h) * kBBytes, kBBytes,
-                  &ufull[q]);
+        bulk_load(smem + kOffB + q * kBBytes, reinterpret_cast<const unsigned char*>(upk) + (int64_t)st * kBBytes,
+                  kBBytes, &ufull[q]);
         issued = x + 1;
       }
     }
@@ -496,17 +501,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = ok && tc::mbar_wait_timed(&ufull[q], (it / kRing) & 1, kWaitLimitNs);
         if (!ok) break;
         tc::fence_after_sync();
-        const uint32_t bbase = tc::smem_u32(smem + kOffB + q * kBBytes);
-        const uint64_t db = tc::smem_desc(bbase, 128, 256);
 #pragma unroll
-        for (int m = 0; m < 2; ++m)
+        for (int kc = 0; kc < kChunks; ++kc) {
+          const uint32_t bbase = tc::smem_u32(smem + kOffB + q * kBBytes + kc * kBChunk);
 #pragma unroll
           for (int k = 0; k < kLv; ++k) {
-            const uint64_t da = tc::smem_desc(tc::smem_u32(smem + kOffA + s * kAStage + (m * kLv + k) * kPlane), 128, 256);
-            // digit k of A against digit planes 0 .. 6 - k of U: levels k .. 6
-            tc::mma_f16_ss(tmem + m * 256 + kRHS * k, da, db, tc::idesc_f16(128, kRHS * (kLv - k)),
-                           (k > 0 || !first) ? 1u : 0u);
+            const uint64_t da =
+                tc::smem_desc(tc::smem_u32(smem + kOffA + s * kAStage + (kc * kLv + k) * kPlane), 128, 256);
+            // digit k of A against digit planes 0 .. 6 - k of U (rows 0 .. 64 (7 - k) - 1): levels k .. 6,
+            // in pieces of at most 256 rows (8-row groups 256 bytes apart)
+#pragma unroll
+            for (int n0 = 0; n0 < kRHS * (kLv - k); n0 += kMaxN) {
+              const int nn = min(kMaxN, kRHS * (kLv - k) - n0);
+              const uint64_t db = tc::smem_desc(bbase + (uint32_t)(n0 / 8) * 256u, 128, 256);
+              tc::mma_f16_ss(tmem + kRHS * k + n0, da, db, tc::idesc_f16(128, nn),
+                             (k > 0 || kc > 0 || !first) ? 1u : 0u);
+            }
           }
+        }
         tc::mma_commit(&afree[s]);
         tc::mma_commit(&bfree[q]);
         if (last) tc::mma_commit(done);
@@ -515,15 +527,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncwarp();
   } else {
-    // generating warps.  Generation: warp w covers targets 8 w .. 8 w + 7
-    // (lane & 7) and source pairs lane >> 3 (sources 2 sp, 2 sp + 1 of every
-    // K step), so that each half-warp's 8-byte digit stores fill 128
-    // contiguous bytes (no bank conflict).  Read-back: the thread of TMEM
-    // lane r = 32 wq + lane owns target r's accumulators of tile sq >> 1,
-    // right-hand sides 16 (sq & 1) .. + 15.
-    const int sq = warp >> 2;
-    const int rg = 8 * warp + (lane & 7), sp = lane >> 3;
-    const int tg = t0 + rg;  // the generated target
+    // generating warps.  Generation: warp w covers targets 8 (w & 7) + (lane
+    // & 7) and source pair sp = 4 (w >> 3) + (lane >> 3) of every step (K
+    // chunk sp >> 2, K columns 4 (sp & 3) .. + 3), so that each half-warp's
+    // 8-byte digit stores fill 128 contiguous bytes (no bank conflict).
+    // Read-back: the thread of TMEM lane r = 32 wq + lane owns row r (the
+    // phi row of target r for r < 64, the psi row of target r - 64 after)
+    // for right-hand sides 16 (w >> 2) .. + 15.
+    const int tr = 8 * (warp & 7) + (lane & 7), sp = 4 * (warp >> 3) + (lane >> 3);
+    const int tg = t0 + tr;  // the generated target
     const bool gvalid = tg < n;
     df xi[3], ni[3];
     {
@@ -534,11 +546,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const int2 rg_e = rowexp[min(tg, n - 1)];
     const float r0 = p2f(rg_e.x), r1 = p2f(rg_e.y);
-    const uint32_t off = koff(rg, 4 * sp);
-    const int ti = t0 + 32 * wq + lane;  // the read-back target
+    const uint32_t offp = koff(tr, 4 * (sp & 3)), offq = koff(kTgt + tr, 4 * (sp & 3));
+    const int rr = 32 * wq + lane;                      // the read-back row
+    const int ti = t0 + (rr & (kTgt - 1));              // its target
     const bool tvalid = ti < n;
+    const int cb = warp >> 2;                           // its right-hand sides 16 cb .. 16 cb + 15
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
-    const uint32_t dthr = tmem + lane_base + (sq >> 1) * 256 + 16 * (sq & 1);
+    const uint32_t dthr = tmem + lane_base + 16 * cb;
     const bool tile_edge = t0 + kTgt > n;
     df acc[16];
 #pragma unroll
@@ -582,27 +596,26 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int j0 = (x0 + it) * kStep;
       const bool edge = tile_edge || (j0 + kStep > n) || (j0 < t0 + kTgt && j0 + kStep > t0);
       const float4* Sq = reinterpret_cast<const float4*>(smem + kOffS + q * kSRec) + 4 * 2 * sp;
-      unsigned char* a = smem + kOffA + s * kAStage;
+      unsigned char* a = smem + kOffA + s * kAStage + (sp >> 2) * kLv * kPlane;
       if (edge)
-        tcx_gen<true>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, off);
+        tcx_gen<true>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, offp, offq);
       else
-        tcx_gen<false>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, off);
+        tcx_gen<false>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, offp, offq);
       tc::fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
       __syncwarp();
       if (lane == 0) mbar_arrive(&ready[s]);
     }
     for (int d = drained_groups; ok && d < n_groups; ++d) drain(d);
     // unscale by 2^-(e + f) and write this split's partial sums
-    const bool all_valid = ok && tvalid && n_it > 0;
-    if (all_valid) {
-      const int comp = sq >> 1;
+    if (ok && tvalid && n_it > 0) {
+      const int comp = rr / kTgt;
       const int2 re = rowexp[ti];
       const int e = comp ? re.y : re.x;
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
-        const int bl = 16 * (sq & 1) + b, bg = kRHS * h + bl;
+        const int bg = 16 * cb + b;
         if (bg < nb) {
-          const df w = df_scale(df_scale(acc[b], p2f(-e)), finv[bl]);
+          const df w = df_scale(df_scale(acc[b], p2f(-e)), finv[bg]);
           part[((int64_t)bg * n_splits + split) * 2 * n + (int64_t)comp * n + ti] = df_to_double(w);
         }
       }
@@ -628,17 +641,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace tcx
 
-// Work list of the exact tensor-core pass: target tiles x source splits (whole
-// K steps) filling whole waves of one CTA per SM, for `halves` groups of 32
-// right-hand sides.
-ItemPlan* tcx_plan(Surface* s, int n, int halves, int* S_out) {
+// Work list of the exact tensor-core pass: target tiles of 64 x source
+// splits (whole steps) filling whole waves of one CTA per SM.
+ItemPlan* tcx_plan(Surface* s, int n, int* S_out) {
   const int n_steps = (n + tcx::kStep - 1) / tcx::kStep;
   const int tiles = (n + tcx::kTgt - 1) / tcx::kTgt;
   const int slots = s->num_sms;
   int S = 1;
   double best = 0.0;
   for (int sp = 1; sp <= std::min(16, std::max(1, n_steps / tcx::kGroup)); ++sp) {
-    const long ctas = (long)tiles * sp * halves, waves = (ctas + slots - 1) / slots;
+    const long ctas = (long)tiles * sp, waves = (ctas + slots - 1) / slots;
     const double eff = (double)ctas / ((double)waves * slots);
     if (eff > best * 1.02) best = eff, S = sp;
   }
@@ -663,12 +675,11 @@ ItemPlan* tcx_plan(Surface* s, int n, int halves, int* S_out) {
   return it->second.get();
 }
 
-// The exact tensor-core pass for nb right-hand sides (u at ub, or the rows
-// rhs[b] of u when rhs is given): row exponents (cached per surface and
+// The exact tensor-core pass for nb <= 64 right-hand sides (u at ub, or the
+// rows rhs[b] of u when rhs is given): row exponents (cached per surface and
 // medium), right-hand-side digits, the kernel; writes part64 [b][split][2n]
 // and returns the number of splits.
 int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, const DFConst& c) {
-  const int halves = (nb + tcx::kRHS - 1) / tcx::kRHS;
   const int n_steps = (n + tcx::kStep - 1) / tcx::kStep;
   s->grow(s->geodf, (size_t)4 * n);
   k_pack_mrhs_df<<<dim3((n + 255) / 256, 1), 256, 0, s->stream>>>(n, 0, s->tgt64.p, ub, rhs, s->geodf.p, s->udf.p);
@@ -687,14 +698,13 @@ int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, cons
   tcx::k_tcx_colmax<<<dim3((unsigned)std::min(64, (2 * n + 255) / 256), nb), 256, 0, s->stream>>>(n, ub, rhs,
                                                                                                   s->tcx_colmax.p);
   BIPB_LAUNCHED(s);
-  const int64_t pk = (int64_t)n_steps * halves * tcx::kRHS * tcx::kK;
-  s->grow(s->tcx_upk, (size_t)n_steps * halves * tcx::kBBytes / sizeof(float));
+  const int64_t pk = (int64_t)n_steps * tcx::kChunks * tcx::kRHS * tcx::kKC;
+  s->grow(s->tcx_upk, (size_t)n_steps * tcx::kBBytes / sizeof(float));
   __half* upk = reinterpret_cast<__half*>(s->tcx_upk.p);
-  tcx::k_tcx_pack_u<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_steps, halves, ub, rhs,
-                                                                      s->tcx_colmax.p, upk);
+  tcx::k_tcx_pack_u<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_steps, ub, rhs, s->tcx_colmax.p, upk);
   BIPB_LAUNCHED(s);
   int S = 1;
-  ItemPlan* plan = tcx_plan(s, n, halves, &S);
+  ItemPlan* plan = tcx_plan(s, n, &S);
   s->grow(s->part64, (size_t)nb * S * 2 * n);
   if (s->tc_err.cap == 0) {
     s->grow(s->tc_err, 1);
@@ -703,9 +713,8 @@ int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, cons
   BIPB_CUDA(cudaFuncSetAttribute(tcx::k_mrhs_tcx, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::kSmemBytes));
   {
     TimedLaunch tl(s, kTMvDF);
-    tcx::k_mrhs_tcx<<<dim3(plan->n_items, halves), tcx::kThreads, tcx::kSmemBytes, s->stream>>>(
-        n, nb, S, halves, plan->items.p, s->geodf.p, s->tcx_rowexp.p, s->tcx_colmax.p, upk, s->part64.p, c,
-        s->tc_err.p);
+    tcx::k_mrhs_tcx<<<plan->n_items, tcx::kThreads, tcx::kSmemBytes, s->stream>>>(
+        n, nb, S, plan->items.p, s->geodf.p, s->tcx_rowexp.p, s->tcx_colmax.p, upk, s->part64.p, c, s->tc_err.p);
     BIPB_LAUNCHED(s);
   }
   return S;

@@ -788,16 +788,18 @@ def test_multi_rhs_df64_matvec_matches_oracle(bipb, orc, n_rhs):
         np.testing.assert_allclose(Y[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
 
 
-def test_exact_tensor_residual_matches_cuda_core_df64(bipb, orc):
-    """The double-float mat-vec of 40 right-hand sides (one full group of 32
-    and a partial one) on the tensor cores (exact base-128 digits) against
-    the same on the CUDA cores and against the oracle: right-hand sides of
-    magnitude 1e-20 .. 1e20 and one zero right-hand side."""
+@pytest.mark.parametrize("n_rhs", [16, 40, 64])
+def test_exact_tensor_residual_matches_cuda_core_df64(bipb, orc, n_rhs):
+    """The double-float mat-vec of 16, 40 and 64 right-hand sides (the fewest
+    the tensor-core form takes, a partly filled block of 64 columns, a full
+    one) on the tensor cores (exact base-128 digits) against the same on the
+    CUDA cores and against the oracle: right-hand sides of magnitude
+    1e-20 .. 1e20 and one zero right-hand side."""
     p = _ragged(3)
     eps = p.eps_out / p.eps_in
     rng = np.random.default_rng(77)
-    mags = 10.0 ** rng.uniform(-20, 20, 40)
-    U = rng.standard_normal((40, 2 * p.n)) * mags[:, None]
+    mags = 10.0 ** rng.uniform(-20, 20, n_rhs)
+    U = rng.standard_normal((n_rhs, 2 * p.n)) * mags[:, None]
     U[11] = 0.0
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
@@ -807,12 +809,12 @@ def test_exact_tensor_residual_matches_cuda_core_df64(bipb, orc):
         s.matvec(ud, yc, precision=bipb.DF64, med=_med(bipb, p))
         Yt, Yc = yt.cpu().numpy(), yc.cpu().numpy()
     assert np.all(Yt[11] == 0.0)
-    for r in range(40):
+    for r in range(n_rhs):
         if r == 11:
             continue
         scale = np.abs(Yc[r]).max()
         np.testing.assert_allclose(Yt[r], Yc[r], rtol=0, atol=1e-13 * scale, err_msg=str(r))
-    for r in (0, 23, 39):
+    for r in (0, n_rhs // 2 + 3, n_rhs - 1):
         ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
         np.testing.assert_allclose(Yt[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
 
