@@ -101,6 +101,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // a wait longer than 2 s is a
 constexpr uint64_t kDrainLimitNs = 100000000ull;  // per wait while draining after a time-out
 constexpr int kScaleTop = 14;               // scaled magnitudes lie in [2^14, 2^15)
 constexpr int kScaleClamp = 100;            // scale exponents are clamped to [-100, 100]
+constexpr double kTcKappaMin = 1e-6;        // the kappa-scaled form from this kappa on (1/A)
 static_assert(kOffBar % 8 == 0, "mbarriers need 8-byte alignment");
 
 // floor(log2 |x|) of a normal double (-1023 for zero and subnormals, 1024
@@ -180,28 +181,34 @@ __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __rest
 
 // The four kernel values of pair (target i, source j) times ds_j (times 4 pi),
 // in FP32: returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3].
+// SCALED: positions, area and normal in the kappa-scaled units described at
+// k_tc_colexp (kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e; the psi
+// row comes out divided by kappa); c.nkl2e and c.smax are then -log2(e) and
+// the 1/r cap in those units.
+template <bool SCALED>
 __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float nxi, float nyi, float nzi, float4 g,
                                              float4 nv, bool zero, const PairConst<float>& c, float* v) {
   const float dx = xi - g.x, dy = yi - g.y, dz = zi - g.z;
   const float r2 = dx * dx + dy * dy + dz * dz;
-  float s = fminf(rsqrt_approx(r2), kSMaxF);
+  float s = fminf(rsqrt_approx(r2), c.smax);
   s = zero ? 0.f : s;
   const float r = r2 * s;
   const float e = ex2_approx(r * c.nkl2e);
-  const float kr = r * c.kappa;
+  const float kr = SCALED ? r : r * c.kappa;
   const float ci = nxi * dx + nyi * dy + nzi * dz;
   const float cj = nv.x * dx + nv.y * dy + nv.z * dz;
   const float cij = nxi * nv.x + nyi * nv.y + nzi * nv.z;
   const float t = e * kr + e;
   const float tm1 = t - 1.f;
-  const float wm3 = (t - e) * kr + 3.f * tm1;
   const float sa = s * g.w;
   const float s2 = s * s;
   const float s3a = s2 * sa;
+  // (w - 3) s^2
+  const float wm3s2 = SCALED ? (3.f * tm1) * s2 + e : ((t - e) * kr + 3.f * tm1) * s2;
   v[1] = sa - e * sa;                                  // K1 ds = (1 - e) s ds
   v[0] = ((c.eps * t - 1.f) * cj) * s3a;               // K2 ds
   v[3] = ((t * c.inveps - 1.f) * ci) * s3a;            // K3 ds
-  v[2] = (tm1 * cij - wm3 * ((ci * cj) * s2)) * s3a;   // K4 ds
+  v[2] = (tm1 * cij - wm3s2 * (ci * cj)) * s3a;        // K4 ds
 }
 
 // kernel_block for the two sources of a record pair at once, in packed FP32
@@ -210,7 +217,7 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
 // P3 = (nz0, nz1, -, -); T holds the target's x, y, z, nx, ny, nz as splats.
 // v[k] holds value k (K2, K1, K4, K3 times ds) of both sources; z0, z1 mask
 // a source as `zero` does in kernel_block.
-template <bool EDGE>
+template <bool EDGE, bool SCALED>
 __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, const float4& P1, const float4& P2,
                                               const float4& P3, bool z0, bool z1, const PairConst<float>& c, f2* v) {
   const f2 one = f2_splat(1.f), three = f2_splat(3.f);
@@ -220,7 +227,7 @@ __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, con
   const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
   float ra, rb;
   f2_get(r2, ra, rb);
-  float sa0 = fminf(rsqrt_approx(ra), kSMaxF), sb0 = fminf(rsqrt_approx(rb), kSMaxF);
+  float sa0 = fminf(rsqrt_approx(ra), c.smax), sb0 = fminf(rsqrt_approx(rb), c.smax);
   if (EDGE) {
     sa0 = z0 ? 0.f : sa0;
     sb0 = z1 ? 0.f : sb0;
@@ -230,21 +237,26 @@ __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, con
   float ea, eb;
   f2_get(f2_mul(r, f2_splat(c.nkl2e)), ea, eb);
   const f2 e = f2_make(ex2_approx(ea), ex2_approx(eb));
-  const f2 kr = f2_mul(r, f2_splat(c.kappa));
+  const f2 kr = SCALED ? r : f2_mul(r, f2_splat(c.kappa));
   const f2 nx = f2_make(P2.x, P2.y), ny = f2_make(P2.z, P2.w), nz = f2_make(P3.x, P3.y);
   const f2 ci = f2_fma(T[3], dx, f2_fma(T[4], dy, f2_mul(T[5], dz)));
   const f2 cj = f2_fma(nx, dx, f2_fma(ny, dy, f2_mul(nz, dz)));
   const f2 cij = f2_fma(T[3], nx, f2_fma(T[4], ny, f2_mul(T[5], nz)));
   const f2 t = f2_fma(e, kr, e);
   const f2 tm1 = f2_sub(t, one);
-  const f2 wm3 = f2_fma(f2_sub(t, e), kr, f2_mul(three, tm1));
   const f2 sa = f2_mul(s, f2_make(P1.z, P1.w));
   const f2 s2 = f2_mul(s, s);
   const f2 s3a = f2_mul(s2, sa);
   v[1] = f2_mul(f2_sub(one, e), sa);                                                             // K1 ds
   v[0] = f2_mul(f2_mul(f2_fma(f2_splat(c.eps), t, f2_splat(-1.f)), cj), s3a);                    // K2 ds
   v[3] = f2_mul(f2_mul(f2_fma(t, f2_splat(c.inveps), f2_splat(-1.f)), ci), s3a);                 // K3 ds
-  v[2] = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3, f2_mul(f2_mul(ci, cj), s2))), s3a);         // K4 ds
+  if (SCALED) {  // (w - 3) s^2 = 3 (t - 1) s^2 + e
+    const f2 wm3s2 = f2_fma(f2_mul(three, tm1), s2, e);
+    v[2] = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3s2, f2_mul(ci, cj))), s3a);                 // K4 ds
+  } else {
+    const f2 wm3 = f2_fma(f2_sub(t, e), kr, f2_mul(three, tm1));
+    v[2] = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3, f2_mul(f2_mul(ci, cj), s2))), s3a);       // K4 ds
+  }
 }
 
 // Column scale exponents: for source j, e(j, 0) from the largest |K2 ds_j|,
@@ -255,12 +267,23 @@ __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, con
 // normal and the products formed from it stay far from the FP32 range.  Then
 // the scaled source records, pair-interleaved for kernel_block2.  One thread
 // per source.
+//
+// SCALED (kappa >= kTcKappaMin): positions are multiplied by kappa, and so
+// are the source's area and normal.  With d, r and s in Debye lengths the
+// four values come out as K2 ds and K1 ds for the phi row but K4 ds / kappa
+// and K3 ds / kappa for the psi row (a row factor, undone in the epilogue),
+// while kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e save three FP32
+// operations per pair.
+template <bool SCALED>
 __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
                                                    int2* __restrict__ srcexp, float4* __restrict__ src) {
   __shared__ float4 sh[2 * 128];
+  const float ks = SCALED ? c.kappa : 1.f;
   const int j = blockIdx.x * 128 + threadIdx.x;
   const int jj = min(j, n - 1);
-  const float4 gj = tgt32[2 * jj], nj = tgt32[2 * jj + 1];
+  float4 gj = tgt32[2 * jj], nj = tgt32[2 * jj + 1];
+  gj = make_float4(ks * gj.x, ks * gj.y, ks * gj.z, ks * gj.w);
+  nj = make_float4(ks * nj.x, ks * nj.y, ks * nj.z, 0.f);
   float m0 = 0.f, m1 = 0.f;
   for (int i0 = 0; i0 < n; i0 += 128) {
     __syncthreads();
@@ -272,7 +295,7 @@ __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restri
     for (int ii = 0; ii < cnt; ++ii) {
       const float4 g = sh[2 * ii], nv = sh[2 * ii + 1];
       float v[4];
-      kernel_block(g.x, g.y, g.z, nv.x, nv.y, nv.z, gj, nj, i0 + ii == jj, c, v);
+      kernel_block<SCALED>(ks * g.x, ks * g.y, ks * g.z, nv.x, nv.y, nv.z, gj, nj, i0 + ii == jj, c, v);
       m0 = fmaxf(m0, fmaxf(fabsf(v[0]), fabsf(v[2])));
       m1 = fmaxf(m1, fmaxf(fabsf(v[1]), fabsf(v[3])));
     }
@@ -314,7 +337,7 @@ __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, ui
 // lane from column acol on (tile 0 hi / lo at + 0 / + kChunk, tile 1 at
 // + 2 kChunk / + 3 kChunk).  EDGE masks pairs with no target, a source past
 // the end or the self pair.
-template <bool EDGE>
+template <bool EDGE, bool SCALED>
 __device__ __forceinline__ void gen_chunk(const f2* T, const float4* Sp, int jq, int ti, int n, bool tvalid,
                                           const PairConst<float>& c, uint32_t acol) {
 #pragma unroll
@@ -326,7 +349,7 @@ __device__ __forceinline__ void gen_chunk(const f2* T, const float4* Sp, int jq,
       const int ja = jq + 2 * p, jb = ja + 1;
       const bool za = EDGE && (!tvalid || ja >= n || ja == ti), zb = EDGE && (!tvalid || jb >= n || jb == ti);
       f2 v[4];
-      kernel_block2<EDGE>(T, Sp[4 * p], Sp[4 * p + 1], Sp[4 * p + 2], Sp[4 * p + 3], za, zb, c, v);
+      kernel_block2<EDGE, SCALED>(T, Sp[4 * p], Sp[4 * p + 1], Sp[4 * p + 2], Sp[4 * p + 3], za, zb, c, v);
       float a[4], b[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -361,6 +384,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
+template <bool SCALED>
 __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
                                                     const float4* __restrict__ tgt32, const float4* __restrict__ src,
                                                     const int* __restrict__ colmax,
@@ -481,7 +505,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
     const int ti = t0 + 32 * wq + lane;
     const bool tvalid = ti < n;
     const float4 gi = tgt32[2 * min(ti, n - 1)], ni = tgt32[2 * min(ti, n - 1) + 1];
-    const f2 T[6] = {f2_splat(gi.x), f2_splat(gi.y), f2_splat(gi.z), f2_splat(ni.x), f2_splat(ni.y), f2_splat(ni.z)};
+    const float ks = SCALED ? c.kappa : 1.f;  // positions in Debye lengths (k_tc_colexp)
+    const f2 T[6] = {f2_splat(ks * gi.x), f2_splat(ks * gi.y), f2_splat(ks * gi.z),
+                     f2_splat(ni.x),      f2_splat(ni.y),      f2_splat(ni.z)};
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
     const uint32_t dthr = tmem + lane_base + kColD + (sq >> 1) * 128 + 32 * (sq & 1);
     const bool tile_edge = t0 + kTgt > n;
@@ -536,9 +562,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       const uint32_t acol = tmem + lane_base + kColA + s * kACols + kPerThread * sq;
       // one branch per chunk: the masked form only where a chunk needs it
       if (edge)
-        gen_chunk<true>(T, Sp, jq, ti, n, tvalid, c, acol);
+        gen_chunk<true, SCALED>(T, Sp, jq, ti, n, tvalid, c, acol);
       else
-        gen_chunk<false>(T, Sp, jq, ti, n, tvalid, c, acol);
+        gen_chunk<false, SCALED>(T, Sp, jq, ti, n, tvalid, c, acol);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
@@ -563,14 +589,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
 
   // epilogue: this thread holds target 32 wq + lane, component sq >> 1 (tile),
   // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-f(b)
+  // (and the psi rows of the kappa-scaled form multiplied by kappa)
   if (all_ok && n_it > 0 && warp < kMmaWarp) {  // the generating warps
     const int sq = warp >> 2;
     const int i = t0 + 32 * wq + lane, comp = sq >> 1;
+    const float rowf = (SCALED && comp) ? c.kappa : 1.f;
     if (i < n)
 #pragma unroll
       for (int x = 0; x < 32; ++x) {
         const int b = 32 * (sq & 1) + x;
-        if (b < n_rhs) part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x] * cinv[b];
+        if (b < n_rhs)
+          part[((int64_t)b * n_splits + split) * 2 * n + (int64_t)comp * n + i] = acc[x] * (cinv[b] * rowf);
       }
   }
   tc::fence_before_sync();
@@ -582,15 +611,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
 
 int matvec_tc_block() { return kNB; }
 
-void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
+void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c0, const double* u, double* y, double dphi,
                double dpsi, const int* skip, int skip_stride) {
   const int n = L.n[0];
   for (int k = 0; k < L.K; ++k)
     BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == n && L.vec_off[k] == 2 * n * k,
                  "the tensor-core mat-vec needs right-hand sides of one surface");
-  BIPB_CUDA(cudaFuncSetAttribute(k_mrhs_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+  // the kappa-scaled form where its 1/r^3 stays far from the FP32 range
+  const bool scaled = c0.kappa >= kTcKappaMin;
+  PairConst<float> c = c0;
+  c.nkl2e = scaled ? -1.4426950408889634f : c0.nkl2e;
+  c.smax = scaled ? (float)(kSMaxD / (double)c0.kappa) : kSMaxF;
+  auto kernel = scaled ? k_mrhs_tc<true> : k_mrhs_tc<false>;
+  BIPB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   int occ = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mrhs_tc, kThreads, kSmemBytes) != cudaSuccess || occ < 1) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, kSmemBytes) != cudaSuccess || occ < 1) {
     (void)cudaGetLastError();
     occ = 1;
   }
@@ -643,7 +678,10 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
   s->grow(s->tc_src, (size_t)4 * ((n + 1) / 2));  // 4 float4 per pair of sources
   if (s->alloc_gen != gen0 || s->tc_src_n != n || s->tc_src_key[0] != c.eps || s->tc_src_key[1] != c.inveps ||
       s->tc_src_key[2] != c.kappa) {
-    k_tc_colexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
+    if (scaled)
+      k_tc_colexp<true><<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
+    else
+      k_tc_colexp<false><<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
     BIPB_LAUNCHED(s);
     s->tc_src_n = n;
     s->tc_src_key[0] = c.eps, s->tc_src_key[1] = c.inveps, s->tc_src_key[2] = c.kappa;
@@ -678,7 +716,7 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const 
     BIPB_LAUNCHED(s);
     {
       TimedLaunch tl(s, kTMvTC);
-      k_mrhs_tc<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p,
+      kernel<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p,
                                                                s->tc_src.p, s->tc_colmax.p, upk, s->part32.p, c,
                                                                s->tc_err.p);
       BIPB_LAUNCHED(s);

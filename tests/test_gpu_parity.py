@@ -639,6 +639,27 @@ def test_tensor_core_matvec_matches_oracle(bipb, orc, n_rhs):
         assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("kappa", [1e-7, 1e-6, 2.5])
+def test_tensor_core_matvec_kappa_range(bipb, orc, kappa):
+    """Both forms of the tensor-core kernel at the ends of their kappa range:
+    plain units below 1e-6 / A (1e-7), kappa-scaled positions from 1e-6 on
+    (1e-6, where the scaled 1/r^3 is largest, and a short Debye length of
+    0.4 A), held to the FP32 bounds against the oracle."""
+    p = _ragged(3)
+    eps = p.eps_out / p.eps_in
+    U = np.random.default_rng(41).standard_normal((6, 2 * p.n))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TENSOR, med=bipb.medium(p.eps_in, p.eps_out, kappa))
+        Y = yd.cpu().numpy()
+    for r in (0, 3, 5):
+        ref = orc.matvec(p.centroids, p.normals, p.areas, eps, kappa, U[r])
+        assert np.all(np.isfinite(Y[r]))
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6
+        assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("geo_scale", [1e-3, 1.0, 1e3])
 def test_tensor_core_matvec_scaled_inputs(bipb, orc, geo_scale):
     """The power-of-two row and column scaling of the tensor-core path:
