@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--no-config3", action="store_true", help="skip the protein-like (N = 81920) solves")
+    ap.add_argument("--no-config4a", action="store_true",
+                    help="skip the batched 64-charge-set solves on the tensor cores")
     ap.add_argument("--inner", default="direct", choices=["direct", "tree"],
                     help="Krylov mat-vec of the step's mixed solve: the direct FP32 sum (the paper's pipeline) or "
                          "the far-field treecode of Sec. 2.2.3 (MIXED_TREE; the residual stays direct)")
@@ -664,6 +666,40 @@ def config3_solves(bipb, torch):
     return out
 
 
+def config4a_solves(bipb, torch):
+    """The batched configuration: 64 charge sets of 2000 charges (each with its
+    own positions) on the protein-like surface, solved together with the
+    tensor-core Krylov mat-vec and the exact tensor-core double-float
+    residual (BIPB_MIXED_TENSOR) to 1e-8, plain and with the element
+    self-block preconditioner, each timed once after an untimed run of the
+    same call; the 64-RHS mat-vec and residual timed alone."""
+    import synth
+
+    base = synth.protein_like_problem()
+    p = synth.batched_charges(base, n_rhs=64, n_charges=2000)
+    med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
+    out = {"config4a_workload": "protein-like surface (N=81920), 64 charge sets x 2000 charges, eps 1/80, "
+                                "kappa 0.1257/A, tol 1e-8"}
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        s.set_charges(p.charge_pos, p.q)
+        U = torch.randn(64, 2 * p.n, dtype=torch.float64, device="cuda")
+        Y = torch.empty_like(U)
+        for key, prec in (("tensor", bipb.TENSOR), ("df64_tensor", bipb.DF64)):
+            s.matvec(U, Y, precision=prec, med=med)
+            ms, _ = _timed(lambda: s.matvec(U, Y, precision=prec, med=med), torch)
+            out[f"config4a_matvec64rhs_ms_{key}"] = ms
+        for key, pre in (("mixed_tensor", bipb.PRECOND_NONE), ("mixed_tensor_precond_self", bipb.PRECOND_SELF)):
+            prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, restart=10,
+                                    precision=bipb.MIXED_TENSOR, precond=pre)
+            s.solve(prm)
+            ms, info = _timed(lambda: s.solve(prm), torch)
+            out[f"config4a_solve_ms_{key}"] = ms
+            out[f"config4a_{key}_iters_max"] = max(i["iters"] for i in info)
+            out[f"config4a_{key}_refine_steps_max"] = max(i["refine_steps"] for i in info)
+            out[f"config4a_{key}_rel_residual_max"] = max(i["rel_residual"] for i in info)
+    return out
+
+
 def run_peaks(args):
     """Measured throughput of the FP32 FFMA, FP64 DFMA and MUFU pipes (the
     microbenchmark microbench/alu_peaks.cu, built here with nvcc), against the
@@ -883,6 +919,8 @@ def main():
     extra["energy_kcal"] = infos[-1][1]
     if args.workload == "kirkwood" and not args.no_config3:
         extra.update(config3_solves(bipb, torch))
+    if args.workload == "kirkwood" and not args.no_config4a:
+        extra.update(config4a_solves(bipb, torch))
 
     # ---- end to end through the host API: geometry + charges from pinned host
     # memory, create, solve, energy back to the host, destroy
