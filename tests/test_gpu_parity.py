@@ -793,9 +793,12 @@ def test_central_differences_by_solution_differences(bipb, orc):
     np.testing.assert_allclose(dq_fd, dq_ref[atoms], rtol=1e-9)
 
 
-@pytest.mark.parametrize("n_rhs", [5, 70])
+@pytest.mark.parametrize("n_rhs", [5, 70, 80])
 def test_multi_rhs_df64_matvec_matches_oracle(bipb, orc, n_rhs):
-    """The batched double-float mat-vec (kernel block shared by 16 right-hand sides)."""
+    """The batched double-float mat-vec in blocks of up to 64 right-hand
+    sides: 5 (df64 multiply-adds on the CUDA cores), 70 (a block of 64 on the
+    tensor cores and one of 6 on the CUDA cores), 80 (blocks of 64 and 16,
+    both on the tensor cores)."""
     p = _ragged(3)
     eps = p.eps_out / p.eps_in
     U = np.random.default_rng(40 + n_rhs).standard_normal((n_rhs, 2 * p.n))
