@@ -672,7 +672,8 @@ def config4a_solves(bipb, torch):
     tensor-core Krylov mat-vec and the exact tensor-core double-float
     residual (BIPB_MIXED_TENSOR) to 1e-8, plain and with the element
     self-block preconditioner, each timed once after an untimed run of the
-    same call; the 64-RHS mat-vec and residual timed alone."""
+    same call, and the 64 energy gradients (forward and adjoint solves); the
+    64-RHS mat-vec, its transpose and the residual timed alone."""
     import synth
 
     base = synth.protein_like_problem()
@@ -684,9 +685,10 @@ def config4a_solves(bipb, torch):
         s.set_charges(p.charge_pos, p.q)
         U = torch.randn(64, 2 * p.n, dtype=torch.float64, device="cuda")
         Y = torch.empty_like(U)
-        for key, prec in (("tensor", bipb.TENSOR), ("df64_tensor", bipb.DF64)):
-            s.matvec(U, Y, precision=prec, med=med)
-            ms, _ = _timed(lambda: s.matvec(U, Y, precision=prec, med=med), torch)
+        for key, prec, tr in (("tensor", bipb.TENSOR, False), ("tensor_transpose", bipb.TENSOR, True),
+                              ("df64_tensor", bipb.DF64, False)):
+            s.matvec(U, Y, precision=prec, transpose=tr, med=med)
+            ms, _ = _timed(lambda: s.matvec(U, Y, precision=prec, transpose=tr, med=med), torch)
             out[f"config4a_matvec64rhs_ms_{key}"] = ms
         for key, pre in (("mixed_tensor", bipb.PRECOND_NONE), ("mixed_tensor_precond_self", bipb.PRECOND_SELF)):
             prm = bipb.solve_params(p.eps_in, p.eps_out, p.kappa, tol=TOL, restart=10,
@@ -697,6 +699,10 @@ def config4a_solves(bipb, torch):
             out[f"config4a_{key}_iters_max"] = max(i["iters"] for i in info)
             out[f"config4a_{key}_refine_steps_max"] = max(i["refine_steps"] for i in info)
             out[f"config4a_{key}_rel_residual_max"] = max(i["rel_residual"] for i in info)
+            if pre == bipb.PRECOND_NONE:  # the 64 energy gradients: forward and adjoint solves on the tensor cores
+                s.energy_grad(prm)
+                gms, _ = _timed(lambda: s.energy_grad(prm), torch)
+                out["config4a_energy_grad_ms_mixed_tensor"] = gms
     return out
 
 

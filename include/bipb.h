@@ -60,13 +60,15 @@ typedef enum {
   BIPB_DF64 = 3,       /* pair arithmetic in double-float (two FP32 words, ~48 bits) on the FP32
                           pipe, FP64 sums across tiles; as a solve: GMRES on that mat-vec */
   BIPB_MIXED_DF64 = 4, /* FP32 pair arithmetic inside GMRES, double-float refinement residual */
-  BIPB_TENSOR = 5,     /* mat-vec only, right-hand sides of one surface: kernel tiles generated in
-                          FP32 and contracted against blocks of 64 right-hand sides on the tensor
-                          cores (rows and columns scaled by powers of two, each operand split into
-                          two FP16 parts, three products per tile, FP32 accumulation, FP64 sums
-                          across tiles: about FP32 accuracy for kernel values and right-hand sides
-                          within about 2^-86 .. 2^114 of their row's / column's largest) */
-  BIPB_MIXED_TENSOR = 6, /* tensor-core mat-vec inside GMRES, double-float refinement residual */
+  BIPB_TENSOR = 5,     /* mat-vec only, right-hand sides of one surface, A u or A^T u: kernel tiles
+                          generated in FP32 and contracted against blocks of 64 right-hand sides on
+                          the tensor cores (rows and columns scaled by powers of two, each operand
+                          split into two FP16 parts, three products per tile, FP32 accumulation,
+                          FP64 sums across tiles: about FP32 accuracy for kernel values and
+                          right-hand sides within about 2^-86 .. 2^114 of their row's / column's
+                          largest) */
+  BIPB_MIXED_TENSOR = 6, /* tensor-core mat-vec inside GMRES (its transpose in adjoint solves),
+                            double-float refinement residual */
   BIPB_TF32 = BIPB_TENSOR,             /* earlier name of BIPB_TENSOR */
   BIPB_MIXED_TF32 = BIPB_MIXED_TENSOR, /* earlier name of BIPB_MIXED_TENSOR */
   BIPB_TREE32 = 7,     /* mat-vec only, single-surface handles: the far-field (treecode) operator of
@@ -278,7 +280,7 @@ bipb_status bipb_energy_grad_dev(bipb_surface s, const bipb_solve_params* p, dou
  *   block-diagonal operator of all surfaces).
  *   precision: BIPB_FP64, BIPB_FP32 (FP32 pair arithmetic per source tile,
  *   FP64 sums across tiles and for the diagonal), BIPB_DF64, BIPB_TENSOR
- *   (single-surface handles, forward only; the tensor-core path of the
+ *   (single-surface handles, both directions; the tensor-core path of the
  *   multi-RHS mat-vec) or BIPB_TREE32 (single-surface handles, both
  *   directions; the far-field operator).
  */

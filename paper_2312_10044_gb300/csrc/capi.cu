@@ -557,7 +557,6 @@ bipb_status bipb_matvec(bipb_surface h, const bipb_medium* m, int precision, int
     BIPB_REQUIRE(u != y, "y must not alias u");
     DeviceGuard dg(s->device);
     StreamJoin sj(s);
-    BIPB_REQUIRE(precision != BIPB_TENSOR || !transpose, "the tensor-core mat-vec has no transpose");
     matvec(s, matvec_layout(s, n_vec), *m, precision, transpose != 0, u, y, nullptr, 0);
     if (precision == BIPB_TENSOR) check_tc_error(s);
   });

@@ -250,8 +250,12 @@ namespace bipb {
 // The four kernel values of pair (target i, source j) times ds_j (times 4 pi)
 // in df64: k[0] = K2 ds, k[1] = K1 ds, k[2] = K4 ds, k[3] = K3 ds (the 2 x 2
 // block that maps (phi_j, psi_j) to the (phi_i, psi_i) rows).  s = 0 for the
-// self pair when MASK and self.
-template <bool MASK>
+// self pair when MASK and self.  TRANS: the block of A^T instead, output
+// element i gathering input element j (the transposed pair of pair.cuh, d =
+// x_i - x_j): k[0] = K2_ji, k[1] = K4_ji (the phi row), k[2] = K1_ji, k[3] =
+// K3_ji (the psi row), i.e. ((1 - eps t) c_i s^3, K4, (1 - e) s,
+// (1 - t/eps) c_j s^3), times `area` (the output's area goes on the sums).
+template <bool MASK, bool TRANS = false>
 __device__ __forceinline__ void df_kernel_block(const df* xi, const df* ni, const df* xj, const df* nj, df area,
                                                 bool self, const DFConst& c, const df* tab, df* k) {
   const df dx = df_sub(xi[0], xj[0]), dy = df_sub(xi[1], xj[1]), dz = df_sub(xi[2], xj[2]);
@@ -270,10 +274,19 @@ __device__ __forceinline__ void df_kernel_block(const df* xi, const df* ni, cons
   const df sa = df_mul(s, area);
   const df s2 = df_sqr(s);
   const df s3a = df_mul(s2, sa);
-  k[1] = df_mul(df_one_minus(e), sa);                                     // K1 ds
-  k[0] = df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cj), s3a);                // K2 ds
-  k[3] = df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), ci), s3a);             // K3 ds
-  k[2] = df_mul(df_sub(df_mul(tm1, cij), df_mul(wm3, df_mul(df_mul(ci, cj), s2))), s3a);  // K4 ds
+  const df k1 = df_mul(df_one_minus(e), sa);                                          // K1 ds
+  const df k4 = df_mul(df_sub(df_mul(tm1, cij), df_mul(wm3, df_mul(df_mul(ci, cj), s2))), s3a);  // K4 ds
+  if (!TRANS) {
+    k[1] = k1;
+    k[0] = df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), cj), s3a);                // K2 ds
+    k[3] = df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), ci), s3a);             // K3 ds
+    k[2] = k4;
+  } else {
+    k[0] = df_neg(df_mul(df_mul(df_add_f(df_mul(c.eps, t), -1.0f), ci), s3a));        // K2_ji
+    k[1] = k4;                                                                        // K4_ji
+    k[2] = k1;                                                                        // K1_ji
+    k[3] = df_neg(df_mul(df_mul(df_add_f(df_mul(t, c.inveps), -1.0f), cj), s3a));     // K3_ji
+  }
 }
 
 // acc += a * b with an exact leading product and an unnormalised trailing

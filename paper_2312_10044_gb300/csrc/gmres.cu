@@ -720,11 +720,9 @@ std::vector<SolveResult> gmres_solve(Surface* s, const SysLayout& L, const bipb_
   const std::vector<double> bnorm = norms(s, w, rhs);
   const bool mixed = p.precision == BIPB_MIXED || p.precision == BIPB_MIXED_DF64 || p.precision == BIPB_MIXED_TENSOR ||
                      p.precision == BIPB_MIXED_TREE;
-  // arithmetic of the Krylov mat-vecs and of the residual r = b - A x (the
-  // adjoint solve has no tensor-core transpose and uses the direct FP32
-  // mat-vec there)
+  // arithmetic of the Krylov mat-vecs and of the residual r = b - A x
   int inner = !mixed ? p.precision : BIPB_FP32;
-  if (p.precision == BIPB_MIXED_TENSOR && !transpose) inner = BIPB_TENSOR;
+  if (p.precision == BIPB_MIXED_TENSOR) inner = BIPB_TENSOR;
   if (p.precision == BIPB_MIXED_TREE) inner = BIPB_TREE32;
   const int resid = (p.precision == BIPB_MIXED || p.precision == BIPB_FP64) ? BIPB_FP64 : BIPB_DF64;
   // r = rhs - A x (or rhs when starting from zero)

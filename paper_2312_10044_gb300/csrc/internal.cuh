@@ -302,22 +302,26 @@ struct Surface {
   DevBuf<float> upk;   // FP16 right-hand-side tiles of the tensor-core mat-vec (raw storage)
   DevBuf<int> tc_err;  // set by the tensor-core kernel when a bounded wait ran out
   DevBuf<int> tc_colmax;    // tensor-core mat-vec: per right-hand side, max over sources of log2|u| - e
-  DevBuf<int2> tc_srcexp;   // tensor-core mat-vec: scale exponents e of each source's phi and psi columns
-  DevBuf<float4> tc_src;    // tensor-core mat-vec: source records with the column scales folded in
-  float tc_src_key[3] = {0.f, 0.f, -1.f};  // the medium (eps, 1/eps, kappa) tc_src was computed for
-  int tc_src_n = -1;
+  // tensor-core mat-vec, per direction (0: A u, 1: A^T u): the scale exponents e
+  // of each source's phi and psi columns, the source records with the column
+  // scales folded in, and the medium (eps, 1/eps, kappa) and size they were
+  // computed for
+  DevBuf<int2> tc_srcexp[2];
+  DevBuf<float4> tc_src[2];
+  float tc_src_key[2][3] = {{0.f, 0.f, -1.f}, {0.f, 0.f, -1.f}};
+  int tc_src_n[2] = {-1, -1};
   DevBuf<double4_32a> rec64;
   DevBuf<float> part32;
   DevBuf<double> part64;
   DevBuf<int> rhs_idx;  // right-hand-side indices of a compacted multi-RHS pass
   DevBuf<float4> geodf;  // multi-RHS df64 pass: geometry as df64 records (4 float4 each)
   DevBuf<float4> udf;    // multi-RHS df64 pass: right-hand sides as df64 (phi, psi) pairs
-  DevBuf<int2> tcx_rowexp;   // exact tensor-core df64 pass: row scale exponents (phi row, psi row)
+  DevBuf<int2> tcx_rowexp[2];  // exact tensor-core df64 pass, per direction (A u, A^T u): row scale exponents (phi, psi row)
   DevBuf<unsigned> tcx_colmax;  // exact tensor-core df64 pass: max |u| per right-hand side (FP32 bits)
   DevBuf<float> tcx_upk;     // exact tensor-core df64 pass: digit tiles of the right-hand sides (raw storage)
   DevBuf<int> tcx_err;       // set by the exact tensor-core kernel when a bounded wait ran out
-  float tcx_key[4] = {0.f, 0.f, -1.f, 0.f};  // the medium (eps and kappa as df64) tcx_rowexp was computed for
-  int tcx_n = -1;
+  float tcx_key[2][4] = {{0.f, 0.f, -1.f, 0.f}, {0.f, 0.f, -1.f, 0.f}};  // the medium (eps, kappa as df64) of tcx_rowexp
+  int tcx_n[2] = {-1, -1};
   DevBuf<double4_32a> pts, pts2;  // points of bipb_potential_at: (p, 0); (p, 0), (0, 0)
   DevBuf<double> pot;             // their potentials, n_rhs x n_pts
   DevBuf<double> coul;            // Coulomb block sums
@@ -429,13 +433,14 @@ void matvec_tree(Surface* s, const SysLayout& L, const PairConst<float>& c, bool
                  double dphi, double dpsi, const int* skip, int skip_stride);
 // the far-field operator of the handle's parameters (built on first use; synchronises then)
 FarField* far_field(Surface* s);
-// y = A u for right-hand sides of one surface with the split-FP16 tensor-core kernel (mrhs_tc.cu)
-void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, const double* u, double* y, double dphi,
-               double dpsi, const int* skip, int skip_stride);
+// y = A u (or A^T u) for right-hand sides of one surface with the split-FP16
+// tensor-core kernel (mrhs_tc.cu)
+void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c, bool transpose, const double* u, double* y,
+               double dphi, double dpsi, const int* skip, int skip_stride);
 // y = A u for right-hand sides of one surface, double-float arithmetic, kernel
 // blocks shared by 16 right-hand sides (mrhs_df.cu)
-void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
-                    double dpsi, const int* skip, int skip_stride);
+void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
+                    double dphi, double dpsi, const int* skip, int skip_stride);
 // FP64 reduction of FP64 per-split partials (kernels.cu), tab[k] = {n, splits, offset, 0}
 void launch_reduce_matvec64(Surface* s, const SysLayout& L, const int4* tab, const double* part, const double* u,
                             double* y, double dphi, double dpsi, const int* skip, int skip_stride);

@@ -881,7 +881,7 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
   const double eps = m.eps_out / m.eps_in;
   const double dphi = 0.5 * (1.0 + eps), dpsi = 0.5 * (1.0 + 1.0 / eps);
   if (precision == BIPB_TENSOR) {
-    matvec_tc(s, L, pair_const<float>(m), u, y, dphi, dpsi, skip, skip_stride);
+    matvec_tc(s, L, pair_const<float>(m), transpose, u, y, dphi, dpsi, skip, skip_stride);
     return;
   }
   if (precision == BIPB_TREE32) {
@@ -893,8 +893,8 @@ void matvec(Surface* s, const SysLayout& L, const bipb_medium& m, int precision,
     bool shared_surface = L.K >= 4;
     for (int k = 0; k < L.K && shared_surface; ++k)
       shared_surface = L.geo_off[k] == 0 && L.n[k] == L.n[0] && L.vec_off[k] == 2 * L.n[0] * k;
-    if (shared_surface && !transpose) {  // kernel blocks shared by 16 right-hand sides
-      matvec_df_mrhs(s, L, c, u, y, dphi, dpsi, skip, skip_stride);
+    if (shared_surface && (!transpose || s->tcx_enabled)) {  // kernel blocks shared by the right-hand sides
+      matvec_df_mrhs(s, L, c, transpose, u, y, dphi, dpsi, skip, skip_stride);
       return;
     }
     if (s->sym_pairs && matvec_sym_df(s, L, c, m.kappa, transpose, u, y, dphi, dpsi, skip, skip_stride)) return;

@@ -307,6 +307,7 @@ __device__ __forceinline__ void digits7(df a, float* d) {
 // Row scale exponents: for target i the largest |K2 ds|, |K1 ds| (phi row)
 // and |K4 ds|, |K3 ds| (psi row) over all sources j != i, in df64 (the same
 // values the kernel digitises).  One thread per target.
+template <bool TRANS>
 __global__ void __launch_bounds__(128) k_tcx_rowexp(int n, const float4* __restrict__ geo, DFConst c,
                                                     int2* __restrict__ rowexp) {
   __shared__ float4 sh[4 * 64];
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(128) k_tcx_rowexp(int n, const float4* __restr
       const df xj[3] = {df{A.x, B.x}, df{A.y, B.y}, df{A.z, B.z}};
       const df nj[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
       df k[4];
-      df_kernel_block<true>(xi, ni, xj, nj, df{A.w, B.w}, j0 + q == ii, c, tab, k);
+      df_kernel_block<true, TRANS>(xi, ni, xj, nj, TRANS ? df{1.f, 0.f} : df{A.w, B.w}, j0 + q == ii, c, tab, k);
       m0 = fmaxf(m0, fmaxf(fabsf(k[0].hi), fabsf(k[1].hi)));
       m1 = fmaxf(m1, fmaxf(fabsf(k[2].hi), fabsf(k[3].hi)));
     }
@@ -394,7 +395,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // target tg: the df64 block, scaled per row, as digit planes written into
 // the K chunk's planes at `a` (digit k at a + k kPlane; byte offsets offp and
 // offq of the target's phi and psi rows at the pair's K columns).
-template <bool EDGE>
+template <bool EDGE, bool TRANS>
 __device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4* Sq, int jq, int tg, int n,
                                         bool tvalid, const DFConst& c, const df* tab, float r0, float r1,
                                         unsigned char* a, uint32_t offp, uint32_t offq) {
@@ -406,7 +407,7 @@ __device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4
     const df nj[3] = {df{C.x, D.x}, df{C.y, D.y}, df{C.z, D.z}};
     const bool z = EDGE && (!tvalid || jq + u >= n || jq + u == tg);
     df k[4];
-    df_kernel_block<EDGE>(xi, ni, xj, nj, df{A.w, B.w}, z, c, tab, k);
+    df_kernel_block<EDGE, TRANS>(xi, ni, xj, nj, TRANS ? df{1.f, 0.f} : df{A.w, B.w}, z, c, tab, k);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       df w = df_scale(k[v], v < 2 ? r0 : r1);
@@ -430,6 +431,7 @@ __device__ __forceinline__ void tcx_gen(const df* xi, const df* ni, const float4
 
 // items: {t0, first step, end step, split}; part: [b][split][2n] for the nb
 // right-hand sides of this pass.
+template <bool TRANS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_mrhs_tcx(int n, int nb, int n_splits, const int4* __restrict__ items, const float4* __restrict__ geo,
                const int2* __restrict__ rowexp, const unsigned* __restrict__ colmax, const __half* __restrict__ upk,
@@ -598,25 +600,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       const float4* Sq = reinterpret_cast<const float4*>(smem + kOffS + q * kSRec) + 4 * 2 * sp;
       unsigned char* a = smem + kOffA + s * kAStage + (sp >> 2) * kLv * kPlane;
       if (edge)
-        tcx_gen<true>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, offp, offq);
+        tcx_gen<true, TRANS>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, offp, offq);
       else
-        tcx_gen<false>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, offp, offq);
+        tcx_gen<false, TRANS>(xi, ni, Sq, j0 + 2 * sp, tg, n, gvalid, c, tab, r0, r1, a, offp, offq);
       tc::fence_proxy_async_smem();  // the generic stores, before the tensor core reads them
       __syncwarp();
       if (lane == 0) mbar_arrive(&ready[s]);
     }
     for (int d = drained_groups; ok && d < n_groups; ++d) drain(d);
-    // unscale by 2^-(e + f) and write this split's partial sums
+    // unscale by 2^-(e + f) and write this split's partial sums (those of
+    // A^T times the output element's area)
     if (ok && tvalid && n_it > 0) {
       const int comp = rr / kTgt;
       const int2 re = rowexp[ti];
       const int e = comp ? re.y : re.x;
+      const double area = TRANS ? (double)geo[4 * (int64_t)ti].w + (double)geo[4 * (int64_t)ti + 1].w : 1.0;
 #pragma unroll
       for (int b = 0; b < 16; ++b) {
         const int bg = 16 * cb + b;
         if (bg < nb) {
           const df w = df_scale(df_scale(acc[b], p2f(-e)), finv[bg]);
-          part[((int64_t)bg * n_splits + split) * 2 * n + (int64_t)comp * n + ti] = df_to_double(w);
+          part[((int64_t)bg * n_splits + split) * 2 * n + (int64_t)comp * n + ti] = df_to_double(w) * area;
         }
       }
     }
@@ -679,19 +683,25 @@ ItemPlan* tcx_plan(Surface* s, int n, int* S_out) {
 // rows rhs[b] of u when rhs is given): row exponents (cached per surface and
 // medium), right-hand-side digits, the kernel; writes part64 [b][split][2n]
 // and returns the number of splits.
-int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, const DFConst& c) {
+int launch_tcx(Surface* s, int n, int nb, bool transpose, const double* ub, const int* rhs, const DFConst& c) {
+  const int dir = transpose ? 1 : 0;
   const int n_steps = (n + tcx::kStep - 1) / tcx::kStep;
   s->grow(s->geodf, (size_t)4 * n);
   k_pack_mrhs_df<<<dim3((n + 255) / 256, 1), 256, 0, s->stream>>>(n, 0, s->tgt64.p, ub, rhs, s->geodf.p, s->udf.p);
   BIPB_LAUNCHED(s);
   const uint64_t gen0 = s->alloc_gen;
-  s->grow(s->tcx_rowexp, (size_t)n);
-  if (s->alloc_gen != gen0 || s->tcx_n != n || s->tcx_key[0] != c.eps.hi || s->tcx_key[1] != c.eps.lo ||
-      s->tcx_key[2] != c.kappa.hi || s->tcx_key[3] != c.kappa.lo) {
-    tcx::k_tcx_rowexp<<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->geodf.p, c, s->tcx_rowexp.p);
+  s->grow(s->tcx_rowexp[dir], (size_t)n);
+  int2* rowexp = s->tcx_rowexp[dir].p;
+  float* key = s->tcx_key[dir];
+  if (s->alloc_gen != gen0 || s->tcx_n[dir] != n || key[0] != c.eps.hi || key[1] != c.eps.lo ||
+      key[2] != c.kappa.hi || key[3] != c.kappa.lo) {
+    if (transpose)
+      tcx::k_tcx_rowexp<true><<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->geodf.p, c, rowexp);
+    else
+      tcx::k_tcx_rowexp<false><<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->geodf.p, c, rowexp);
     BIPB_LAUNCHED(s);
-    s->tcx_n = n;
-    s->tcx_key[0] = c.eps.hi, s->tcx_key[1] = c.eps.lo, s->tcx_key[2] = c.kappa.hi, s->tcx_key[3] = c.kappa.lo;
+    s->tcx_n[dir] = n;
+    key[0] = c.eps.hi, key[1] = c.eps.lo, key[2] = c.kappa.hi, key[3] = c.kappa.lo;
   }
   s->grow(s->tcx_colmax, (size_t)kNB);
   BIPB_CUDA(cudaMemsetAsync(s->tcx_colmax.p, 0, kNB * sizeof(unsigned), s->stream));
@@ -710,11 +720,12 @@ int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, cons
     s->grow(s->tc_err, 1);
     BIPB_CUDA(cudaMemsetAsync(s->tc_err.p, 0, sizeof(int), s->stream));
   }
-  BIPB_CUDA(cudaFuncSetAttribute(tcx::k_mrhs_tcx, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::kSmemBytes));
+  auto kernel = transpose ? tcx::k_mrhs_tcx<true> : tcx::k_mrhs_tcx<false>;
+  BIPB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcx::kSmemBytes));
   {
-    TimedLaunch tl(s, kTMvDF);
-    tcx::k_mrhs_tcx<<<plan->n_items, tcx::kThreads, tcx::kSmemBytes, s->stream>>>(
-        n, nb, S, plan->items.p, s->geodf.p, s->tcx_rowexp.p, s->tcx_colmax.p, upk, s->part64.p, c, s->tc_err.p);
+    TimedLaunch tl(s, transpose ? kTMvDFT : kTMvDF);
+    kernel<<<plan->n_items, tcx::kThreads, tcx::kSmemBytes, s->stream>>>(
+        n, nb, S, plan->items.p, s->geodf.p, rowexp, s->tcx_colmax.p, upk, s->part64.p, c, s->tc_err.p);
     BIPB_LAUNCHED(s);
   }
   return S;
@@ -722,8 +733,9 @@ int launch_tcx(Surface* s, int n, int nb, const double* ub, const int* rhs, cons
 
 }  // namespace
 
-void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const double* u, double* y, double dphi,
-                    double dpsi, const int* skip, int skip_stride) {
+void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, bool transpose, const double* u, double* y,
+                    double dphi, double dpsi, const int* skip, int skip_stride) {
+  BIPB_REQUIRE(!transpose || s->tcx_enabled, "the multi-RHS double-float transpose runs on the tensor cores only");
   const int n = L.n[0];
   for (int k = 0; k < L.K; ++k)
     BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == n && L.vec_off[k] == 2 * n * k,
@@ -743,8 +755,8 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
   const int n_act = (int)act.size();
   for (int g0 = 0; g0 < n_act; g0 += kNB) {
     const int nb = std::min(kNB, n_act - g0);
-    // 16 or more right-hand sides: the exact tensor-core form; fewer: df64 on the CUDA cores
-    const bool tensor = nb >= kTcxMinRHS && s->tcx_enabled;
+    // 16 or more right-hand sides, or A^T: the exact tensor-core form; fewer: df64 on the CUDA cores
+    const bool tensor = (nb >= kTcxMinRHS || transpose) && s->tcx_enabled;
     const int G = nb <= kGB ? 1 : nb <= 2 * kGB ? 2 : nb <= 4 * kGB ? 4 : 8;
     int S = 1;
     ItemPlan* plan = nullptr;
@@ -781,7 +793,7 @@ void matvec_df_mrhs(Surface* s, const SysLayout& L, const DFConst& c, const doub
       rhs = s->rhs_idx.p;
       ub = u;
     }
-    if (tensor) S = launch_tcx(s, n, nb, ub, rhs, c);
+    if (tensor) S = launch_tcx(s, n, nb, transpose, ub, rhs, c);
     const uint64_t tkey = 0x7f0000000000ull ^ ((uint64_t)n << 16) ^ ((uint64_t)S << 8) ^ (uint64_t)nb;
     auto tt = s->plans.find(tkey);
     if (tt == s->plans.end()) {

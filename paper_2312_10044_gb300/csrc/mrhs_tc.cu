@@ -181,11 +181,16 @@ __global__ void k_pack_u_tc(int n, int n_rhs, int n_chunks, const double* __rest
 
 // The four kernel values of pair (target i, source j) times ds_j (times 4 pi),
 // in FP32: returns (K2, K1) in v[0], v[1] and (K4, K3) in v[2], v[3].
+// TRANS: the block of A^T instead, output element i gathering input element
+// j (pair_transpose of pair.cuh with d = x_i - x_j): the phi row (K2_ji,
+// K4_ji) in v[0], v[1], the psi row (K1_ji, K3_ji) in v[2], v[3], times the
+// record's area field (the output's area is applied to the sums), i.e.
+// ((1 - eps t) c_i s^3, K4, (1 - e) s, (1 - t/eps) c_j s^3).
 // SCALED: positions, area and normal in the kappa-scaled units described at
-// k_tc_colexp (kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e; the psi
-// row comes out divided by kappa); c.nkl2e and c.smax are then -log2(e) and
-// the 1/r cap in those units.
-template <bool SCALED>
+// k_tc_colexp (kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e; one row
+// comes out with an extra power of kappa); c.nkl2e and c.smax are then
+// -log2(e) and the 1/r cap in those units.
+template <bool SCALED, bool TRANS>
 __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float nxi, float nyi, float nzi, float4 g,
                                              float4 nv, bool zero, const PairConst<float>& c, float* v) {
   const float dx = xi - g.x, dy = yi - g.y, dz = zi - g.z;
@@ -205,10 +210,18 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
   const float s3a = s2 * sa;
   // (w - 3) s^2
   const float wm3s2 = SCALED ? (3.f * tm1) * s2 + e : ((t - e) * kr + 3.f * tm1) * s2;
-  v[1] = sa - e * sa;                                  // K1 ds = (1 - e) s ds
-  v[0] = ((c.eps * t - 1.f) * cj) * s3a;               // K2 ds
-  v[3] = ((t * c.inveps - 1.f) * ci) * s3a;            // K3 ds
-  v[2] = (tm1 * cij - wm3s2 * (ci * cj)) * s3a;        // K4 ds
+  const float k4 = (tm1 * cij - wm3s2 * (ci * cj)) * s3a;
+  if (!TRANS) {
+    v[1] = sa - e * sa;                                  // K1 ds = (1 - e) s ds
+    v[0] = ((c.eps * t - 1.f) * cj) * s3a;               // K2 ds
+    v[3] = ((t * c.inveps - 1.f) * ci) * s3a;            // K3 ds
+    v[2] = k4;                                           // K4 ds
+  } else {
+    v[0] = ((1.f - c.eps * t) * ci) * s3a;               // K2_ji
+    v[1] = k4;                                           // K4_ji
+    v[2] = sa - e * sa;                                  // K1_ji
+    v[3] = ((1.f - t * c.inveps) * cj) * s3a;            // K3_ji
+  }
 }
 
 // kernel_block for the two sources of a record pair at once, in packed FP32
@@ -217,7 +230,7 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
 // P3 = (nz0, nz1, -, -); T holds the target's x, y, z, nx, ny, nz as splats.
 // v[k] holds value k (K2, K1, K4, K3 times ds) of both sources; z0, z1 mask
 // a source as `zero` does in kernel_block.
-template <bool EDGE, bool SCALED>
+template <bool EDGE, bool SCALED, bool TRANS>
 __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, const float4& P1, const float4& P2,
                                               const float4& P3, bool z0, bool z1, const PairConst<float>& c, f2* v) {
   const f2 one = f2_splat(1.f), three = f2_splat(3.f);
@@ -247,34 +260,52 @@ __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, con
   const f2 sa = f2_mul(s, f2_make(P1.z, P1.w));
   const f2 s2 = f2_mul(s, s);
   const f2 s3a = f2_mul(s2, sa);
-  v[1] = f2_mul(f2_sub(one, e), sa);                                                             // K1 ds
-  v[0] = f2_mul(f2_mul(f2_fma(f2_splat(c.eps), t, f2_splat(-1.f)), cj), s3a);                    // K2 ds
-  v[3] = f2_mul(f2_mul(f2_fma(t, f2_splat(c.inveps), f2_splat(-1.f)), ci), s3a);                 // K3 ds
+  f2 k4;
   if (SCALED) {  // (w - 3) s^2 = 3 (t - 1) s^2 + e
     const f2 wm3s2 = f2_fma(f2_mul(three, tm1), s2, e);
-    v[2] = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3s2, f2_mul(ci, cj))), s3a);                 // K4 ds
+    k4 = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3s2, f2_mul(ci, cj))), s3a);
   } else {
     const f2 wm3 = f2_fma(f2_sub(t, e), kr, f2_mul(three, tm1));
-    v[2] = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3, f2_mul(f2_mul(ci, cj), s2))), s3a);       // K4 ds
+    k4 = f2_mul(f2_sub(f2_mul(tm1, cij), f2_mul(wm3, f2_mul(f2_mul(ci, cj), s2))), s3a);
+  }
+  const f2 k1 = f2_mul(f2_sub(one, e), sa);
+  if (!TRANS) {
+    v[1] = k1;                                                                                   // K1 ds
+    v[0] = f2_mul(f2_mul(f2_fma(f2_splat(c.eps), t, f2_splat(-1.f)), cj), s3a);                  // K2 ds
+    v[3] = f2_mul(f2_mul(f2_fma(t, f2_splat(c.inveps), f2_splat(-1.f)), ci), s3a);               // K3 ds
+    v[2] = k4;                                                                                   // K4 ds
+  } else {
+    v[0] = f2_mul(f2_mul(f2_fma(f2_splat(-c.eps), t, one), ci), s3a);                            // K2_ji
+    v[1] = k4;                                                                                   // K4_ji
+    v[2] = k1;                                                                                   // K1_ji
+    v[3] = f2_mul(f2_mul(f2_fma(t, f2_splat(-c.inveps), one), cj), s3a);                         // K3_ji
   }
 }
 
-// Column scale exponents: for source j, e(j, 0) from the largest |K2 ds_j|,
-// |K4 ds_j| and e(j, 1) from the largest |K1 ds_j|, |K3 ds_j| over all
-// targets i != j (the same FP32 values the tensor-core kernel generates); 0
-// for a column of zeros (no dielectric contrast and kappa = 0), and the two
-// kept within 2^40 of each other by lowering the larger, so that the scaled
+// Column scale exponents: for source j, e(j, 0) and e(j, 1) from the
+// largest magnitude in its phi and psi column (K2 ds_j, K4 ds_j and K1 ds_j,
+// K3 ds_j; for A^T the columns of the transposed blocks) over all targets
+// i != j (the same FP32 values the tensor-core kernel generates); 0 for a
+// column of zeros (no dielectric contrast and kappa = 0), and the two kept
+// within 2^40 of each other by lowering the larger, so that the scaled
 // normal and the products formed from it stay far from the FP32 range.  Then
 // the scaled source records, pair-interleaved for kernel_block2.  One thread
 // per source.
 //
+// A column whose values are linear in the source normal takes its scale
+// through the normal, the other through the area field: for A u the phi
+// column (K2, K4) is linear in n_j, so the area carries 2^e(j, 1) and the
+// normal 2^(e(j, 0) - e(j, 1)); for A^T the psi column (K4, K3) is, and the
+// area field (1 instead of ds_j, whose place the output's area takes)
+// carries 2^e(j, 0), the normal 2^(e(j, 1) - e(j, 0)).
+//
 // SCALED (kappa >= kTcKappaMin): positions are multiplied by kappa, and so
-// are the source's area and normal.  With d, r and s in Debye lengths the
-// four values come out as K2 ds and K1 ds for the phi row but K4 ds / kappa
-// and K3 ds / kappa for the psi row (a row factor, undone in the epilogue),
-// while kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e save three FP32
-// operations per pair.
-template <bool SCALED>
+// are the source normal and the area field (by kappa^2 for A^T).  With d, r
+// and s in Debye lengths the phi row comes out exact and the psi row
+// divided (A u) or multiplied (A^T) by kappa, a row factor undone in the
+// epilogue, while kappa r = r2 s and (w - 3) s^2 = 3 (t - 1) s^2 + e save
+// three FP32 operations per pair.
+template <bool SCALED, bool TRANS>
 __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restrict__ tgt32, PairConst<float> c,
                                                    int2* __restrict__ srcexp, float4* __restrict__ src) {
   __shared__ float4 sh[2 * 128];
@@ -282,7 +313,7 @@ __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restri
   const int j = blockIdx.x * 128 + threadIdx.x;
   const int jj = min(j, n - 1);
   float4 gj = tgt32[2 * jj], nj = tgt32[2 * jj + 1];
-  gj = make_float4(ks * gj.x, ks * gj.y, ks * gj.z, ks * gj.w);
+  gj = make_float4(ks * gj.x, ks * gj.y, ks * gj.z, TRANS ? ks * ks : ks * gj.w);
   nj = make_float4(ks * nj.x, ks * nj.y, ks * nj.z, 0.f);
   float m0 = 0.f, m1 = 0.f;
   for (int i0 = 0; i0 < n; i0 += 128) {
@@ -295,7 +326,7 @@ __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restri
     for (int ii = 0; ii < cnt; ++ii) {
       const float4 g = sh[2 * ii], nv = sh[2 * ii + 1];
       float v[4];
-      kernel_block<SCALED>(ks * g.x, ks * g.y, ks * g.z, nv.x, nv.y, nv.z, gj, nj, i0 + ii == jj, c, v);
+      kernel_block<SCALED, TRANS>(ks * g.x, ks * g.y, ks * g.z, nv.x, nv.y, nv.z, gj, nj, i0 + ii == jj, c, v);
       m0 = fmaxf(m0, fmaxf(fabsf(v[0]), fabsf(v[2])));
       m1 = fmaxf(m1, fmaxf(fabsf(v[1]), fabsf(v[3])));
     }
@@ -307,11 +338,11 @@ __global__ void __launch_bounds__(128) k_tc_colexp(int n, const float4* __restri
   if (e0 - e1 > 40) e0 = e1 + 40;
   if (e1 - e0 > 40) e1 = e0 + 40;
   srcexp[j] = make_int2(e0, e1);
-  const float r01 = pow2f(e0 - e1);
+  const float fa = pow2f(TRANS ? e0 : e1), fn = pow2f(TRANS ? e1 - e0 : e0 - e1);
   // pair-interleaved records (kernel_block2): element j in slot j & 1 of pair j >> 1
   float* o = reinterpret_cast<float*>(src) + 16 * (j >> 1) + (j & 1);
-  o[0] = gj.x, o[2] = gj.y, o[4] = gj.z, o[6] = gj.w * pow2f(e1);
-  o[8] = nj.x * r01, o[10] = nj.y * r01, o[12] = nj.z * r01, o[14] = 0.f;
+  o[0] = gj.x, o[2] = gj.y, o[4] = gj.z, o[6] = gj.w * fa;
+  o[8] = nj.x * fn, o[10] = nj.y * fn, o[12] = nj.z * fn, o[14] = 0.f;
 }
 
 // two FP32 values (the lower k first) as FP16 parts: hi = round(a), lo =
@@ -337,7 +368,7 @@ __device__ __forceinline__ void split_f16x2(float a0, float a1, uint32_t& hi, ui
 // lane from column acol on (tile 0 hi / lo at + 0 / + kChunk, tile 1 at
 // + 2 kChunk / + 3 kChunk).  EDGE masks pairs with no target, a source past
 // the end or the self pair.
-template <bool EDGE, bool SCALED>
+template <bool EDGE, bool SCALED, bool TRANS>
 __device__ __forceinline__ void gen_chunk(const f2* T, const float4* Sp, int jq, int ti, int n, bool tvalid,
                                           const PairConst<float>& c, uint32_t acol) {
 #pragma unroll
@@ -349,7 +380,7 @@ __device__ __forceinline__ void gen_chunk(const f2* T, const float4* Sp, int jq,
       const int ja = jq + 2 * p, jb = ja + 1;
       const bool za = EDGE && (!tvalid || ja >= n || ja == ti), zb = EDGE && (!tvalid || jb >= n || jb == ti);
       f2 v[4];
-      kernel_block2<EDGE, SCALED>(T, Sp[4 * p], Sp[4 * p + 1], Sp[4 * p + 2], Sp[4 * p + 3], za, zb, c, v);
+      kernel_block2<EDGE, SCALED, TRANS>(T, Sp[4 * p], Sp[4 * p + 1], Sp[4 * p + 2], Sp[4 * p + 3], za, zb, c, v);
       float a[4], b[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -384,7 +415,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-template <bool SCALED>
+template <bool SCALED, bool TRANS>
 __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n_splits, const int4* __restrict__ items,
                                                     const float4* __restrict__ tgt32, const float4* __restrict__ src,
                                                     const int* __restrict__ colmax,
@@ -562,9 +593,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
       const uint32_t acol = tmem + lane_base + kColA + s * kACols + kPerThread * sq;
       // one branch per chunk: the masked form only where a chunk needs it
       if (edge)
-        gen_chunk<true, SCALED>(T, Sp, jq, ti, n, tvalid, c, acol);
+        gen_chunk<true, SCALED, TRANS>(T, Sp, jq, ti, n, tvalid, c, acol);
       else
-        gen_chunk<false, SCALED>(T, Sp, jq, ti, n, tvalid, c, acol);
+        gen_chunk<false, SCALED, TRANS>(T, Sp, jq, ti, n, tvalid, c, acol);
       tc::tmem_wait_st();
       tc::fence_before_sync();
       // one arrival per warp: 512 arrivals on one barrier word would serialise
@@ -588,12 +619,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
   }
 
   // epilogue: this thread holds target 32 wq + lane, component sq >> 1 (tile),
-  // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-f(b)
-  // (and the psi rows of the kappa-scaled form multiplied by kappa)
+  // right-hand sides 32 (sq & 1) .. + 31; the sums are unscaled by 2^-f(b),
+  // the psi rows of the kappa-scaled form by kappa (A u) or 1/kappa (A^T),
+  // and the sums of A^T take the output element's area
   if (all_ok && n_it > 0 && warp < kMmaWarp) {  // the generating warps
     const int sq = warp >> 2;
     const int i = t0 + 32 * wq + lane, comp = sq >> 1;
-    const float rowf = (SCALED && comp) ? c.kappa : 1.f;
+    float rowf = (SCALED && comp) ? (TRANS ? 1.f / c.kappa : c.kappa) : 1.f;
+    if (TRANS) rowf *= tgt32[2 * min(i, n - 1)].w;
     if (i < n)
 #pragma unroll
       for (int x = 0; x < 32; ++x) {
@@ -611,8 +644,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mrhs_tc(int n, int n_rhs, int n
 
 int matvec_tc_block() { return kNB; }
 
-void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c0, const double* u, double* y, double dphi,
-               double dpsi, const int* skip, int skip_stride) {
+void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c0, bool transpose, const double* u, double* y,
+               double dphi, double dpsi, const int* skip, int skip_stride) {
   const int n = L.n[0];
   for (int k = 0; k < L.K; ++k)
     BIPB_REQUIRE(L.geo_off[k] == 0 && L.n[k] == n && L.vec_off[k] == 2 * n * k,
@@ -622,7 +655,9 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c0, const
   PairConst<float> c = c0;
   c.nkl2e = scaled ? -1.4426950408889634f : c0.nkl2e;
   c.smax = scaled ? (float)(kSMaxD / (double)c0.kappa) : kSMaxF;
-  auto kernel = scaled ? k_mrhs_tc<true> : k_mrhs_tc<false>;
+  auto kernel = scaled ? (transpose ? k_mrhs_tc<true, true> : k_mrhs_tc<true, false>)
+                      : (transpose ? k_mrhs_tc<false, true> : k_mrhs_tc<false, false>);
+  const int dir = transpose ? 1 : 0;
   BIPB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
   int occ = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, kSmemBytes) != cudaSuccess || occ < 1) {
@@ -674,17 +709,25 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c0, const
   // column scale exponents and scaled source records: once per surface and
   // medium (buffers that moved are recomputed)
   const uint64_t gen0 = s->alloc_gen;
-  s->grow(s->tc_srcexp, (size_t)n);
-  s->grow(s->tc_src, (size_t)4 * ((n + 1) / 2));  // 4 float4 per pair of sources
-  if (s->alloc_gen != gen0 || s->tc_src_n != n || s->tc_src_key[0] != c.eps || s->tc_src_key[1] != c.inveps ||
-      s->tc_src_key[2] != c.kappa) {
-    if (scaled)
-      k_tc_colexp<true><<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
+  s->grow(s->tc_srcexp[dir], (size_t)n);
+  s->grow(s->tc_src[dir], (size_t)4 * ((n + 1) / 2));  // 4 float4 per pair of sources
+  int2* srcexp = s->tc_srcexp[dir].p;
+  float4* src = s->tc_src[dir].p;
+  float* key3 = s->tc_src_key[dir];
+  if (s->alloc_gen != gen0 || s->tc_src_n[dir] != n || key3[0] != c.eps || key3[1] != c.inveps ||
+      key3[2] != c.kappa) {
+    const int nbk = (n + 127) / 128;
+    if (scaled && transpose)
+      k_tc_colexp<true, true><<<nbk, 128, 0, s->stream>>>(n, s->tgt32.p, c, srcexp, src);
+    else if (scaled)
+      k_tc_colexp<true, false><<<nbk, 128, 0, s->stream>>>(n, s->tgt32.p, c, srcexp, src);
+    else if (transpose)
+      k_tc_colexp<false, true><<<nbk, 128, 0, s->stream>>>(n, s->tgt32.p, c, srcexp, src);
     else
-      k_tc_colexp<false><<<(n + 127) / 128, 128, 0, s->stream>>>(n, s->tgt32.p, c, s->tc_srcexp.p, s->tc_src.p);
+      k_tc_colexp<false, false><<<nbk, 128, 0, s->stream>>>(n, s->tgt32.p, c, srcexp, src);
     BIPB_LAUNCHED(s);
-    s->tc_src_n = n;
-    s->tc_src_key[0] = c.eps, s->tc_src_key[1] = c.inveps, s->tc_src_key[2] = c.kappa;
+    s->tc_src_n[dir] = n;
+    key3[0] = c.eps, key3[1] = c.inveps, key3[2] = c.kappa;
   }
   // per block of up to 64 right-hand sides: pack, tensor-core pass, FP64 reduction
   for (int b0 = 0; b0 < K; b0 += kNB) {
@@ -709,15 +752,15 @@ void matvec_tc(Surface* s, const SysLayout& L, const PairConst<float>& c0, const
     __half* upk = reinterpret_cast<__half*>(s->upk.p);
     BIPB_CUDA(cudaMemsetAsync(s->tc_colmax.p, 0x80, kNB * sizeof(int), s->stream));
     k_colmax_u<<<dim3((unsigned)std::min<int64_t>(64, (2 * (int64_t)n + 255) / 256), nb), 256, 0, s->stream>>>(
-        n, ub, s->tc_srcexp.p, s->tc_colmax.p);
+        n, ub, srcexp, s->tc_colmax.p);
     BIPB_LAUNCHED(s);
-    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, s->tc_srcexp.p,
+    k_pack_u_tc<<<(int)((pk + 255) / 256), 256, 0, s->stream>>>(n, nb, n_chunks, ub, srcexp,
                                                                   s->tc_colmax.p, upk);
     BIPB_LAUNCHED(s);
     {
       TimedLaunch tl(s, kTMvTC);
       kernel<<<plan->n_items, kThreads, kSmemBytes, s->stream>>>(n, nb, S, plan->items.p, s->tgt32.p,
-                                                               s->tc_src.p, s->tc_colmax.p, upk, s->part32.p, c,
+                                                               src, s->tc_colmax.p, upk, s->part32.p, c,
                                                                s->tc_err.p);
       BIPB_LAUNCHED(s);
     }

@@ -107,8 +107,6 @@ def test_degenerate_media(bipb, orc):
             ref = np.stack([f(p.centroids, p.normals, p.areas, 80.0, 0.0, u) for u in U])
             for prec, variant, tol in ((bipb.FP64, 0, 1e-12), (bipb.DF64, 0, 2e-12), (bipb.FP32, 0, 2e-5),
                                        (bipb.FP32, 7, 2e-5), (bipb.FP32, 9, 2e-5), (bipb.TENSOR, 9, 2e-5)):
-                if prec == bipb.TENSOR and transpose:
-                    continue  # the tensor-core path has no transpose
                 s.set_variant(variant)
                 yd = torch.full_like(ud, float("nan"))
                 s.matvec(ud, yd, precision=prec, transpose=transpose, med=med0)
@@ -709,17 +707,44 @@ def test_tensor_core_matvec_small_surfaces(bipb, orc, n_keep):
         assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("n_rhs,kappa", [(5, 0.1257), (70, 0.1257), (6, 1e-7), (6, 2.5)])
+def test_tensor_core_transpose_matches_oracle(bipb, orc, n_rhs, kappa):
+    """A^T U on the tensor cores (the transposed blocks generated in FP32 with
+    the output's area applied to the sums; plain units below kappa = 1e-6,
+    kappa-scaled above) vs the oracle's transpose, held to the FP32 bounds."""
+    p = _ragged(3)
+    eps = p.eps_out / p.eps_in
+    U = np.random.default_rng(50 + n_rhs).standard_normal((n_rhs, 2 * p.n))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.TENSOR, transpose=True, med=bipb.medium(p.eps_in, p.eps_out, kappa))
+        Y = yd.cpu().numpy()
+    for r in (0, n_rhs // 2, n_rhs - 1):
+        ref = orc.matvec_t(p.centroids, p.normals, p.areas, eps, kappa, U[r])
+        assert np.all(np.isfinite(Y[r]))
+        assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6
+        assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
+
+
 def test_mixed_tensor_solve_matches_oracle(bipb, orc):
+    """Three charge sets solved together with tensor-core Krylov mat-vecs and
+    the double-float residual: energies, and the adjoint gradient (whose
+    Krylov solve takes the tensor-core transpose), against the oracle."""
     base = synth.protein_like_problem(level=4, n_charges=30)
     batch = synth.batched_charges(base, n_rhs=3, n_charges=30)
     with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
         s.set_charges(batch.charge_pos, batch.q)
         info = s.solve(tol=1e-9, precision=bipb.MIXED_TENSOR)
         e = s.energy()
+        dq, dy = s.energy_grad(tol=1e-10, precision=bipb.MIXED_TENSOR)
     for r in range(3):
         assert info[r]["converged"] and info[r]["rel_residual"] <= 1e-9
         ref = orc.solve(batch, rhs=r, method="gmres", tol=1e-12)
         assert e[r] == pytest.approx(ref.energy_kcal, rel=1e-7)
+        e_ref, dq_ref, dy_ref = orc.energy_gradient(batch, rhs=r, method="gmres", tol=1e-12)
+        np.testing.assert_allclose(dq[r], dq_ref, rtol=0, atol=1e-7 * np.abs(dq_ref).max())
+        np.testing.assert_allclose(dy[r], dy_ref, rtol=0, atol=1e-7 * np.abs(dy_ref).max())
 
 
 def test_adjoint_config_level4_copy_matches_oracle(bipb, orc):
@@ -840,6 +865,38 @@ def test_exact_tensor_residual_matches_cuda_core_df64(bipb, orc, n_rhs):
         np.testing.assert_allclose(Yt[r], Yc[r], rtol=0, atol=1e-13 * scale, err_msg=str(r))
     for r in (0, n_rhs // 2 + 3, n_rhs - 1):
         ref = orc.matvec(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
+        np.testing.assert_allclose(Yt[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n_rhs", [4, 40])
+def test_exact_tensor_residual_transpose_matches_oracle(bipb, orc, n_rhs):
+    """The double-float A^T U of a batch of right-hand sides on the tensor cores
+    (the transposed blocks as exact base-128 digits, the output's area on the
+    sums) against the single-system double-float transpose on the CUDA cores
+    and against the oracle's transpose: right-hand sides of magnitude
+    1e-20 .. 1e20 and one zero right-hand side."""
+    p = _ragged(3)
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(88 + n_rhs)
+    mags = 10.0 ** rng.uniform(-20, 20, n_rhs)
+    U = rng.standard_normal((n_rhs, 2 * p.n)) * mags[:, None]
+    U[1] = 0.0
+    med = _med(bipb, p)
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yt = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yt, precision=bipb.DF64, transpose=True, med=med)
+        yc = torch.full_like(ud, float("nan"))
+        for r in range(n_rhs):  # one system at a time: the symmetric double-float kernel
+            s.matvec(ud[r], yc[r], precision=bipb.DF64, transpose=True, med=med)
+        Yt, Yc = yt.cpu().numpy(), yc.cpu().numpy()
+    assert np.all(Yt[1] == 0.0)
+    for r in range(n_rhs):
+        if r == 1:
+            continue
+        np.testing.assert_allclose(Yt[r], Yc[r], rtol=0, atol=1e-13 * np.abs(Yc[r]).max(), err_msg=str(r))
+    for r in (0, n_rhs - 1):
+        ref = orc.matvec_t(p.centroids, p.normals, p.areas, eps, p.kappa, U[r])
         np.testing.assert_allclose(Yt[r], ref, rtol=0, atol=2e-12 * np.abs(ref).max())
 
 
