@@ -361,11 +361,13 @@ bipb_status bipb_matvec_variant(bipb_surface s, int variant);
 bipb_status bipb_symmetric_pairs(bipb_surface s, int symmetric);
 
 /* How the double-float mat-vec applies one surface's kernel to 16 or more
- * right-hand sides (the refinement residual of batched solves): tensor = 1
- * (the default) digitises the df64 kernel values and right-hand sides into
- * seven exact base-128 FP16 digits and multiplies them on the tensor cores
- * with exact FP32 accumulation; tensor = 0 runs df64 multiply-adds on the
- * CUDA cores.  Both reach about 1e-14 of the largest output. */
+ * right-hand sides (the refinement residual of batched solves; for A^T, to
+ * four or more): tensor = 1 (the default) digitises the df64 kernel values
+ * and right-hand sides into seven exact base-128 FP16 digits and multiplies
+ * them on the tensor cores with exact FP32 accumulation, in both directions;
+ * tensor = 0 runs df64 multiply-adds on the CUDA cores for A u and the
+ * single-system double-float kernel for A^T.  All reach about 1e-14 of the
+ * largest output. */
 bipb_status bipb_exact_tensor_residual(bipb_surface s, int tensor);
 
 /*
