@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-API measurement")
     ap.add_argument("--no-extra", action="store_true", help="skip the single mat-vec timings")
     ap.add_argument("--no-config3", action="store_true", help="skip the protein-like (N = 81920) solves")
+    ap.add_argument("--cuda-core-residual", action="store_true",
+                    help="--mode matvecdfm: df64 multiply-adds on the CUDA cores instead of exact tensor-core digits")
     ap.add_argument("--no-config4a", action="store_true",
                     help="skip the batched 64-charge-set solves on the tensor cores")
     ap.add_argument("--inner", default="direct", choices=["direct", "tree"],
@@ -328,6 +330,8 @@ def run_matvec_only(args):
             s.set_variant(args.variant)
         if args.ordered_pairs:
             s.symmetric_pairs(False)
+        if args.cuda_core_residual:
+            s.exact_tensor_residual(False)
         u = torch.randn(n_vec, 2 * prob.n, dtype=torch.float64, device="cuda")
         y = torch.empty_like(u)
         for _ in range(args.warmup):
