@@ -228,8 +228,9 @@ __device__ __forceinline__ void kernel_block(float xi, float yi, float zi, float
 // (two results per instruction).  Source records are pair-interleaved:
 // P0 = (x0, x1, y0, y1), P1 = (z0, z1, w0, w1), P2 = (nx0, nx1, ny0, ny1),
 // P3 = (nz0, nz1, -, -); T holds the target's x, y, z, nx, ny, nz as splats.
-// v[k] holds value k (K2, K1, K4, K3 times ds) of both sources; z0, z1 mask
-// a source as `zero` does in kernel_block.
+// v[k] holds value k (K2, K1, K4, K3 times ds; for TRANS the transposed
+// block in kernel_block's order) of both sources; z0, z1 mask a source as
+// `zero` does in kernel_block.
 template <bool EDGE, bool SCALED, bool TRANS>
 __device__ __forceinline__ void kernel_block2(const f2* T, const float4& P0, const float4& P1, const float4& P2,
                                               const float4& P3, bool z0, bool z1, const PairConst<float>& c, f2* v) {
