@@ -1,7 +1,8 @@
 // Multi-right-hand-side mat-vec in double-float arithmetic (the refinement
 // residual of batched solves), in two forms: df64 multiply-adds on the CUDA
-// cores (below; fewer than 16 right-hand sides) and exact digit products on
-// the tensor cores (namespace tcx further down; 16 or more).
+// cores (below; A U for fewer than 16 right-hand sides) and exact digit
+// products on the tensor cores (namespace tcx further down; A U for 16 or
+// more right-hand sides, and A^T U).
 //
 // Y = A U for up to 64 right-hand sides of one surface.  A CTA covers 32
 // targets and G groups of 8 right-hand sides (G = 1, 2, 4 or 8, 32 G
@@ -226,7 +227,9 @@ ItemPlan* mrhs_df_plan(Surface* s, int n, int G, int slots, int* S_out) {
 // (64..127) of 64 targets, so that the seven levels of all 64 right-hand
 // sides fit tensor memory (448 of its 512 columns): every df64 kernel block
 // is generated once for all 64 right-hand sides, and the multiply-adds cost
-// nothing on the CUDA cores.
+// nothing on the CUDA cores.  A^T U is the same pass over the transposed
+// blocks (df_kernel_block<.., true>, area 1), with its own row scales and the
+// output element's area applied to the FP64 sums.
 namespace tcx {
 
 constexpr int kRHS = 64;                        // right-hand sides per CTA (all of a launch)
