@@ -107,12 +107,13 @@ def test_protein_like_mixed_solve_true_residual_on_sampled_rows(bipb, orc):
     assert rms <= bound, (rms, bound, info["rel_residual"])
 
 
-def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
-    """Split-FP16 tensor-core mat-vec at N = 81920 (about 5000 source chunks per
-    target tile), two random and two smooth right-hand sides, on 64 sampled
-    rows: the FP32 mat-vec's bound on the whole output (2e-5 of the largest
-    value), and on the off-diagonal sum alone no worse than twice the
-    CUDA-core FP32 mat-vec's error on the same rows."""
+@pytest.mark.parametrize("transpose", [False, True])
+def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc, transpose):
+    """Split-FP16 tensor-core mat-vec (A U, or A^T U) at N = 81920 (about 2500
+    source chunks per target tile), two random and two smooth right-hand
+    sides, on 64 sampled rows: the FP32 mat-vec's bound on the whole output
+    (2e-5 of the largest value), and on the off-diagonal sum alone no worse
+    than twice the CUDA-core FP32 mat-vec's error on the same rows."""
     p = synth.protein_like_problem()
     eps = p.eps_out / p.eps_in
     rng = np.random.default_rng(61)
@@ -125,11 +126,13 @@ def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         ud = _dev(U)
         ytc, y32 = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
-        s.matvec(ud, ytc, precision=bipb.TENSOR, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
-        s.matvec(ud, y32, precision=bipb.FP32, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
+        med = bipb.medium(p.eps_in, p.eps_out, p.kappa)
+        s.matvec(ud, ytc, precision=bipb.TENSOR, transpose=transpose, med=med)
+        s.matvec(ud, y32, precision=bipb.FP32, transpose=transpose, med=med)
         Ytc, Y32 = ytc.cpu().numpy(), y32.cpu().numpy()
+    rows_of = orc.matvec_t_rows if transpose else orc.matvec_rows
     for v in range(U.shape[0]):
-        ref = orc.matvec_rows(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
+        ref = rows_of(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
         assert np.all(np.isfinite(Ytc[v]))
         err = np.abs(Ytc[v][rows] - ref).max() / np.abs(ref).max()
         assert err < 2e-5, (v, err)
@@ -138,6 +141,29 @@ def test_tensor_core_matvec_full_size_sampled_rows(bipb, orc):
         e_32 = np.sqrt(np.mean((Y32[v][rows] - ref) ** 2))
         scale = np.sqrt(np.mean(off_ref ** 2))
         assert e_tc <= 2 * e_32 + 1e-7 * scale, (v, e_tc / scale, e_32 / scale)
+
+
+@pytest.mark.parametrize("transpose", [False, True])
+def test_exact_tensor_residual_full_size_sampled_rows(bipb, orc, transpose):
+    """The double-float mat-vec of 16 right-hand sides on the tensor cores
+    (exact base-128 digit products; A U, or A^T U) at N = 81920 against the
+    oracle on 64 sampled rows of three of them: within 2e-12 of the largest
+    value, as the single-RHS double-float kernel."""
+    p = synth.protein_like_problem()
+    eps = p.eps_out / p.eps_in
+    rng = np.random.default_rng(71)
+    U = rng.standard_normal((16, 2 * p.n))
+    rows = np.sort(rng.choice(2 * p.n, 64, replace=False))
+    with bipb.Surface(p.centroids, p.normals, p.areas) as s:
+        ud = _dev(U)
+        yd = torch.full_like(ud, float("nan"))
+        s.matvec(ud, yd, precision=bipb.DF64, transpose=transpose, med=bipb.medium(p.eps_in, p.eps_out, p.kappa))
+        Y = yd.cpu().numpy()
+    rows_of = orc.matvec_t_rows if transpose else orc.matvec_rows
+    for v in (0, 7, 15):
+        ref = rows_of(p.centroids, p.normals, p.areas, eps, p.kappa, U[v], rows)
+        err = np.abs(Y[v][rows] - ref).max() / np.abs(ref).max()
+        assert err < 2e-12, (v, err)
 
 
 @pytest.mark.parametrize("transpose", [False, True])
