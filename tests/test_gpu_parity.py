@@ -686,25 +686,31 @@ def test_tensor_core_matvec_scaled_inputs(bipb, orc, geo_scale):
 
 
 @pytest.mark.parametrize("n_keep", [2, 7, 80, 200])
-def test_tensor_core_matvec_small_surfaces(bipb, orc, n_keep):
+@pytest.mark.parametrize("transpose", [False, True])
+def test_tensor_core_matvec_small_surfaces(bipb, orc, n_keep, transpose):
     """Surfaces smaller than one source chunk (32) and one target tile (128):
     two elements (the smallest surface the library takes), a ragged first chunk and
-    a partly filled tile, against the FP64 oracle at the FP32 bounds."""
+    a partly filled tile, against the FP64 oracle at the FP32 bounds (A U and
+    A^T U); and the exact double-float pass of 16 right-hand sides on the same
+    surfaces (steps of 16 sources, tiles of 64 targets) at 2e-12."""
     p = synth.protein_like_problem(level=2, n_charges=5, seed=8)  # 320 elements
     keep = np.sort(np.random.default_rng(n_keep).choice(p.n, n_keep, replace=False))
     c, nv, a = p.centroids[keep], p.normals[keep], p.areas[keep]
     eps = p.eps_out / p.eps_in
-    U = np.random.default_rng(50 + n_keep).standard_normal((3, 2 * n_keep))
+    U = np.random.default_rng(50 + n_keep).standard_normal((16, 2 * n_keep))
     with bipb.Surface(c, nv, a) as s:
         ud = _dev(U)
-        yd = torch.full_like(ud, float("nan"))
-        s.matvec(ud, yd, precision=bipb.TENSOR, med=_med(bipb, p))
-        Y = yd.cpu().numpy()
+        yd, yx = torch.full_like(ud, float("nan")), torch.full_like(ud, float("nan"))
+        s.matvec(ud[:3], yd[:3], precision=bipb.TENSOR, transpose=transpose, med=_med(bipb, p))
+        s.matvec(ud, yx, precision=bipb.DF64, transpose=transpose, med=_med(bipb, p))
+        Y, X = yd.cpu().numpy(), yx.cpu().numpy()
+    f = orc.matvec_t if transpose else orc.matvec
     for r in range(3):
-        ref = orc.matvec(c, nv, a, eps, p.kappa, U[r])
+        ref = f(c, nv, a, eps, p.kappa, U[r])
         assert np.all(np.isfinite(Y[r]))
         assert np.linalg.norm(Y[r] - ref) / np.linalg.norm(ref) < 3e-6
         assert np.abs(Y[r] - ref).max() < 2e-5 * np.abs(ref).max()
+        assert np.abs(X[r] - ref).max() < 2e-12 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("n_rhs,kappa", [(5, 0.1257), (70, 0.1257), (6, 1e-7), (6, 2.5)])
