@@ -157,15 +157,17 @@ def test_autotune_picks_a_variant(bipb):
 
 def test_matvec_is_deterministic(bipb):
     """Every mat-vec sums in a fixed order: repeated calls agree bit for bit
-    (the tensor-core path with several right-hand sides, the far-field one
-    in both directions)."""
+    (the tensor-core paths with several right-hand sides in both directions,
+    the far-field one in both directions)."""
     p = _ragged(3)
     u = _dev(np.random.default_rng(0).standard_normal(2 * p.n))
     U = _dev(np.random.default_rng(1).standard_normal((5, 2 * p.n)))
+    W = _dev(np.random.default_rng(2).standard_normal((16, 2 * p.n)))
     with bipb.Surface(p.centroids, p.normals, p.areas) as s:
         s.treecode(0.7, 4, 64)
         for prec, v, tr in ((bipb.FP64, u, False), (bipb.FP32, u, False), (bipb.DF64, u, False),
-                            (bipb.TENSOR, U, False), (bipb.TREE32, u, False), (bipb.TREE32, u, True)):
+                            (bipb.TENSOR, U, False), (bipb.TENSOR, U, True), (bipb.DF64, W, False),
+                            (bipb.DF64, W, True), (bipb.TREE32, u, False), (bipb.TREE32, u, True)):
             a, b = torch.empty_like(v), torch.empty_like(v)
             s.matvec(v, a, precision=prec, transpose=tr)
             s.matvec(v, b, precision=prec, transpose=tr)
