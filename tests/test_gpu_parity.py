@@ -1002,14 +1002,19 @@ def test_self_block_preconditioned_solve_matches_oracle(bipb, orc, prec):
     assert np.linalg.norm(phi[0] - phi_ref) / np.linalg.norm(phi_ref) < rt
 
 
-def test_self_block_preconditioned_batch_and_adjoint(bipb, orc):
-    """Three charge sets solved together with the preconditioner (MIXED_DF64)
-    and the adjoint gradient taken with it, against the unpreconditioned run."""
+@pytest.mark.parametrize("prec", ["mixed_df64", "mixed_tensor"])
+def test_self_block_preconditioned_batch_and_adjoint(bipb, orc, prec):
+    """Charge sets solved together with the preconditioner (MIXED_DF64 with
+    three sets; MIXED_TENSOR with five, so that the adjoint's residual takes
+    the exact tensor-core transpose) and the adjoint gradient taken with it,
+    against the unpreconditioned run."""
+    n_rhs = 3 if prec == "mixed_df64" else 5
+    precision = bipb.MIXED_DF64 if prec == "mixed_df64" else bipb.MIXED_TENSOR
     base = synth.protein_like_problem(level=3, n_charges=40)
-    batch = synth.batched_charges(base, n_rhs=3, n_charges=40)
+    batch = synth.batched_charges(base, n_rhs=n_rhs, n_charges=40)
     with bipb.Surface(batch.centroids, batch.normals, batch.areas) as s:
         s.set_charges(batch.charge_pos, batch.q)
-        prm = bipb.solve_params(batch.eps_in, batch.eps_out, batch.kappa, tol=1e-10, precision=bipb.MIXED_DF64)
+        prm = bipb.solve_params(batch.eps_in, batch.eps_out, batch.kappa, tol=1e-10, precision=precision)
         s.solve(prm)
         e0 = s.energy()
         dq0, dy0 = s.energy_grad(prm)
