@@ -53,7 +53,7 @@ namespace {
 constexpr double kInv4PiT = 1.0 / (4.0 * kPi);
 constexpr int kUpPiece = 2048;  // elements per piece of the upward pass
 constexpr int kUpChunk = 32;    // elements staged per step of the upward pass
-constexpr int kFarCH = 128;     // records per shared-memory chunk of the far-field kernel
+constexpr int kFarCH = 256;     // records per shared-memory chunk of the far-field kernel
 constexpr int kMaxLeaf = 512;
 
 __device__ __forceinline__ bool tree_skipped(const int* skip, int stride, int sys) {
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kMaxLeaf) k_tree_far(const int4* __restrict__ 
       if (!active) continue;
       if (!self) {
         if (m == kFarCH) {
-#pragma unroll 4
+#pragma unroll 8
           for (int jj = 0; jj < kFarCH; ++jj) tree_pair<TRANS, false>(g, v, sh[2 * jj], sh[2 * jj + 1], false, c, accP, accQ);
         } else {
           for (int jj = 0; jj < m; ++jj) tree_pair<TRANS, false>(g, v, sh[2 * jj], sh[2 * jj + 1], false, c, accP, accQ);
